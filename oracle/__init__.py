@@ -1,0 +1,298 @@
+"""Oracle of the signed-particle Wigner branching random walk (arXiv:1709.02121).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product library
+(``paper_1709_02121_gb300``) neither imports nor links anything here, and this
+package imports nothing from it.
+
+Contents
+--------
+* ``wbrw_oracle.c`` -- plain FP64 C implementation of Alg. 1 (per interval),
+  the signed histogram (Eq. signed_histogram), Alg. 3 and the signed residual
+  bootstrap (Alg. 2 with Eq. lambda / double_bootstrap / boostrap_histogram),
+  with its own Philox4x32-10.  Loaded here through ctypes.
+* ``refs.py`` -- independent numerical references used to pin it: quadrature
+  of the Wigner-kernel definition (Eq. 2), a split-step solver of the
+  Schroedinger equation and a deterministic grid solver of the truncated Wigner
+  equation (Eq. 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wbrw_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libwbrw_oracle.so")
+
+SP1 = 1
+SP2 = 2
+
+# counter word 2 of the reserved streams (documented in wbrw_oracle.c)
+STEP_INIT = 0xFFFFFFFF
+STEP_REGEN = 0xFFFFFFFE
+STEP_BOOT = 0xFFFFFFFD
+STEP_ROUND = 0xFFFFFFFC
+
+LEDGER = ("events", "kill_plus", "kill_minus", "out_plus", "out_minus",
+          "particle_steps", "_6", "_7")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no FMA contraction, no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("hbar", ctypes.c_double), ("mass", ctypes.c_double),
+                ("dt", ctypes.c_double), ("gamma0", ctypes.c_double),
+                ("H", ctypes.c_double), ("w", ctypes.c_double),
+                ("xc", ctypes.c_double),
+                ("nx", ctypes.c_int), ("nk", ctypes.c_int),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
+                ("strategy", ctypes.c_int),
+                ("n_alpha", ctypes.c_longlong),
+                ("seed", ctypes.c_ulonglong)]
+
+
+EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"),
+                        ("pid_minus", "<u8"), ("step", "<u4"), ("j", "<u4"),
+                        ("t", "<f8"), ("xe", "<f8"), ("kappa", "<f8"),
+                        ("factor", "<f8"), ("kill_plus", "<i4"),
+                        ("kill_minus", "<i4")])
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        D = ctypes.c_double
+        LL = ctypes.c_longlong
+        U32 = ctypes.c_uint32
+        L.orc_philox4x32_10.argtypes = [P, P, P]
+        L.orc_u53.argtypes = [U32, U32]
+        L.orc_u53.restype = D
+        L.orc_vw_gauss.argtypes = [D] * 6
+        L.orc_vw_gauss.restype = D
+        L.orc_xi_gauss.argtypes = [D] * 5
+        L.orc_xi_gauss.restype = D
+        L.orc_create.argtypes = [ctypes.POINTER(_Config)]
+        L.orc_create.restype = P
+        L.orc_destroy.argtypes = [P]
+        L.orc_cacc_ok.argtypes = [P]
+        L.orc_gamma0.argtypes = [P]
+        L.orc_gamma0.restype = D
+        L.orc_enable_log.argtypes = [P, ctypes.c_int]
+        L.orc_init_gauss.argtypes = [P, LL, D, D, D]
+        L.orc_set_particles.argtypes = [P, LL, P, P, P, P, LL]
+        L.orc_step.argtypes = [P, ctypes.c_int]
+        L.orc_annihilate.argtypes = [P]
+        L.orc_histogram.argtypes = [P, P, P]
+        L.orc_observables.argtypes = [P, P, P, P, P]
+        L.orc_count.argtypes = [P]
+        L.orc_count.restype = LL
+        L.orc_step_index.argtypes = [P]
+        L.orc_step_index.restype = LL
+        L.orc_epoch.argtypes = [P]
+        L.orc_epoch.restype = LL
+        L.orc_get_particles.argtypes = [P, P, P, P, P]
+        L.orc_get_grid.argtypes = [P, P]
+        L.orc_set_grid.argtypes = [P, P, LL]
+        L.orc_regenerate.argtypes = [P]
+        L.orc_get_ledger.argtypes = [P, P]
+        L.orc_get_wkill.argtypes = [P, P]
+        L.orc_get_boot.argtypes = [P, P, P, P, P]
+        L.orc_get_boot_counts.argtypes = [P, P, P]
+        L.orc_log_count.argtypes = [P]
+        L.orc_log_count.restype = LL
+        L.orc_get_log.argtypes = [P, P]
+        L.orc_event_size.restype = LL
+        L.orc_event_outcome.argtypes = [P, ctypes.c_uint64, U32, U32, D,
+                                        P, P, P]
+        assert L.orc_event_size() == EVENT_DTYPE.itemsize
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of one counter (4 x uint32) under one key (2 x uint32)."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def u53(a, b):
+    return lib().orc_u53(int(a), int(b))
+
+
+def vw_gauss(H, w, xc, hbar, x, kappa):
+    return lib().orc_vw_gauss(H, w, xc, hbar, x, kappa)
+
+
+def xi_gauss(H, w, xc, hbar, x):
+    return lib().orc_xi_gauss(H, w, xc, hbar, x)
+
+
+class Oracle:
+    """One run of the FP64 oracle: a particle list plus its histogram state."""
+
+    def __init__(self, *, hbar=1.0, mass=1.0, dt=0.1, gamma0=0.0, H=1.0,
+                 w=1.0, xc=0.0, nx=240, nk=128, xmin=-60.0, xmax=60.0,
+                 kmin=-6.4, kmax=6.4, strategy=SP1, n_alpha=200000, seed=0):
+        self.cfg = _Config(hbar, mass, dt, gamma0, H, w, xc, nx, nk, xmin,
+                           xmax, kmin, kmax, strategy, n_alpha, seed)
+        self.nx, self.nk = nx, nk
+        self.n_alpha = n_alpha
+        self._s = lib().orc_create(ctypes.byref(self.cfg))
+        if not self._s:
+            raise ValueError("oracle rejected the configuration")
+
+    def __del__(self):
+        s = getattr(self, "_s", None)
+        if s and _lib is not None:
+            _lib.orc_destroy(s)
+            self._s = None
+
+    # ---- set-up ---------------------------------------------------------
+    @property
+    def gamma0(self):
+        return lib().orc_gamma0(self._s)
+
+    def enable_log(self, on=True):
+        lib().orc_enable_log(self._s, 1 if on else 0)
+
+    def init_gauss(self, n, x0, sigma_x, k0):
+        if lib().orc_init_gauss(self._s, n, x0, sigma_x, k0):
+            raise MemoryError
+
+    def set_particles(self, x, k, w, pid, step=0):
+        x = np.ascontiguousarray(x, np.float64)
+        k = np.ascontiguousarray(k, np.float64)
+        w = np.ascontiguousarray(w, np.float64)
+        pid = np.ascontiguousarray(pid, np.uint64)
+        if lib().orc_set_particles(self._s, len(x), _ptr(x), _ptr(k), _ptr(w),
+                                   _ptr(pid), step):
+            raise MemoryError
+
+    # ---- the method -----------------------------------------------------
+    def step(self, n=1):
+        if lib().orc_step(self._s, n):
+            raise MemoryError
+
+    def annihilate(self):
+        if lib().orc_annihilate(self._s):
+            raise MemoryError
+
+    def set_grid(self, grid, epoch):
+        g = np.ascontiguousarray(grid, np.int32).reshape(-1)
+        lib().orc_set_grid(self._s, _ptr(g), epoch)
+
+    def regenerate(self):
+        if lib().orc_regenerate(self._s):
+            raise MemoryError
+
+    # ---- read-out -------------------------------------------------------
+    @property
+    def n(self):
+        return lib().orc_count(self._s)
+
+    @property
+    def step_index(self):
+        return lib().orc_step_index(self._s)
+
+    @property
+    def epoch(self):
+        return lib().orc_epoch(self._s)
+
+    def particles(self):
+        n = self.n
+        x = np.empty(n)
+        k = np.empty(n)
+        w = np.empty(n)
+        pid = np.empty(n, np.uint64)
+        lib().orc_get_particles(self._s, _ptr(x), _ptr(k), _ptr(w), _ptr(pid))
+        return x, k, w, pid
+
+    def grid(self):
+        g = np.empty(self.nx * self.nk, np.int32)
+        lib().orc_get_grid(self._s, _ptr(g))
+        return g.reshape(self.nx, self.nk)
+
+    def histogram(self):
+        """Signed counts and FP64 weight sums of the current particles."""
+        c = np.empty(self.nx * self.nk, np.int32)
+        ws = np.empty(self.nx * self.nk, np.float64)
+        lib().orc_histogram(self._s, _ptr(c), _ptr(ws))
+        return c.reshape(self.nx, self.nk), ws.reshape(self.nx, self.nk)
+
+    def observables(self, counts):
+        c = np.ascontiguousarray(counts, np.int32).reshape(-1)
+        dens = np.empty(self.nx * self.nk)
+        marg = np.empty(self.nx)
+        T = np.zeros(1)
+        lib().orc_observables(self._s, _ptr(c), _ptr(dens), _ptr(marg),
+                              _ptr(T))
+        return dens.reshape(self.nx, self.nk), marg, float(T[0])
+
+    def ledger(self):
+        out = np.zeros(8, np.int64)
+        lib().orc_get_ledger(self._s, _ptr(out))
+        return dict(zip(LEDGER, out.tolist()))
+
+    def killed_weight(self):
+        out = np.zeros(2)
+        lib().orc_get_wkill(self._s, _ptr(out))
+        return out
+
+    def boot_stats(self):
+        n = np.zeros(2, np.int64)
+        keep = np.zeros(2, np.int64)
+        nr = np.zeros(2, np.int64)
+        wfix = np.zeros(2, np.uint64)
+        lib().orc_get_boot(self._s, _ptr(n), _ptr(keep), _ptr(nr), _ptr(wfix))
+        return dict(n=n, keep=keep, nr=nr, wfix=wfix)
+
+    def boot_counts(self):
+        p = np.zeros(self.nx * self.nk, np.int64)
+        m = np.zeros(self.nx * self.nk, np.int64)
+        lib().orc_get_boot_counts(self._s, _ptr(p), _ptr(m))
+        return p.reshape(self.nx, self.nk), m.reshape(self.nx, self.nk)
+
+    def event_log(self):
+        n = lib().orc_log_count(self._s)
+        out = np.zeros(n, EVENT_DTYPE)
+        if n:
+            lib().orc_get_log(self._s, out.ctypes.data_as(ctypes.c_void_p))
+        return out
+
+    def event_outcome(self, pid, step, j, xe):
+        kap = ctypes.c_double()
+        f = ctypes.c_double()
+        gap = ctypes.c_double()
+        emit = lib().orc_event_outcome(self._s, pid, step, j, xe,
+                                       ctypes.byref(kap), ctypes.byref(f),
+                                       ctypes.byref(gap))
+        return bool(emit), kap.value, f.value, gap.value
