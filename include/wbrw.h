@@ -1,0 +1,212 @@
+/*
+ * wbrw.h -- C ABI of the GB300 (sm_103a) signed-particle Wigner branching
+ * random walk.
+ *
+ * The method is that of Xiong & Shao, "The Wigner branching random walk:
+ * efficient implementation and performance evaluation" (arXiv:1709.02121):
+ * signed particles of the Wigner equation (Eq. 1) with the kernel V_W of Eq. 2
+ * are propagated interval by interval (Alg. 1) and resampled every T_A steps,
+ * either by annihilation in the signed histogram (sp1, Eq. signed_histogram)
+ * or by the signed residual bootstrap (sp2, Alg. 2 with Eq. lambda,
+ * double_bootstrap and boostrap_histogram), followed by importance sampling
+ * from the histogram (Alg. 3).
+ *
+ * Conventions
+ *  - Every call returns a wbrw_status.  Plain C types only; no exception ever
+ *    crosses this boundary.
+ *  - The caller owns all device memory (particle arrays, histogram, scratch,
+ *    optional event log) and the CUDA stream.  The library owns only the
+ *    opaque context.  It never allocates, reallocates or frees device memory.
+ *  - All GPU work is enqueued on the caller's stream.  wbrw_init, wbrw_step,
+ *    wbrw_annihilate and wbrw_run do not wait for the GPU.  wbrw_density,
+ *    wbrw_particles, wbrw_counters and wbrw_sync_status synchronise the stream.
+ *  - Device-side faults are latched in a device error word: particle or queue
+ *    capacity exceeded, or offspring nesting too deep.  The next synchronising
+ *    call reports them.  After any error the context refuses further work
+ *    with WBRW_ERR_STATE; only wbrw_last_error and wbrw_destroy remain valid.
+ *  - Random numbers are Philox4x32-10 keyed by config.seed and indexed by
+ *    (particle id, step, draw).  Results therefore do not depend on the order
+ *    in which the GPU processes particles.
+ */
+#ifndef WBRW_H
+#define WBRW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wbrw_ctx wbrw_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  WBRW_OK = 0,
+  WBRW_ERR_ARG = -1,      /* invalid argument or configuration             */
+  WBRW_ERR_CAPACITY = -2, /* particle, queue, record or nesting capacity   */
+  WBRW_ERR_CUDA = -3,     /* a CUDA runtime call failed                    */
+  WBRW_ERR_STATE = -4,    /* context already failed, or call out of order  */
+  WBRW_ERR_TIMEOUT = -5,  /* reserved: a bounded device wait gave up       */
+  WBRW_ERR_NUMERIC = -6   /* reserved: non-finite state detected           */
+} wbrw_status;
+
+typedef enum { WBRW_SP1_PAIR = 1, WBRW_SP2_BOOTSTRAP = 2 } wbrw_strategy;
+typedef enum { WBRW_FP64 = 0, WBRW_FP32 = 1 } wbrw_precision;
+typedef enum { WBRW_POT_GAUSSIAN = 0 } wbrw_potential_kind;
+
+/* Potential (Sec. 4.2, symmetric about xc): V(x) = H exp(-(x-xc)^2/(2 w^2)).
+ * Its Wigner kernel (Eq. 2) is V_W(x,k) = (2/(pi hbar)) Vhat(2k)
+ * sin(2 (x-xc) k) with Vhat(q) = H w sqrt(2 pi) exp(-q^2 w^2/2). */
+typedef struct {
+  int kind;        /* WBRW_POT_GAUSSIAN                                     */
+  double H, w, xc; /* height (any sign), width (> 0), centre                */
+} wbrw_potential;
+
+/* Problem statement (Sec. 2 and Sec. 4): hbar, mass, interval dt of the
+ * time partition (Eq. def.time_partition), constant auxiliary rate gamma0
+ * (Sec. 3.2; <= 0 selects the majorant rate C/2 = |H|/hbar, and values below
+ * C/2 are rejected), the histogram = truncation domain K (Sec. 4.3, uniform
+ * cells, x-major with k contiguous), the resampling period T_A in steps, and
+ * the sample size N_alpha of the estimator (Eq. estimator). */
+typedef struct {
+  int dim;                  /* 2: one position and one wavevector            */
+  int precision;            /* wbrw_precision: particle state and arithmetic */
+  int strategy;             /* wbrw_strategy                                 */
+  double hbar, mass, dt, gamma0;
+  int nx, nk;               /* cells; nx * nk < 2^31                          */
+  double xmin, xmax, kmin, kmax;
+  int resample_every;       /* steps per T_A for wbrw_run; 0 = never          */
+  long long n_alpha;        /* N_alpha (> 0)                                 */
+  unsigned long long seed;  /* Philox key                                    */
+} wbrw_config;
+
+/* Caller-owned device buffers, structure of arrays, `capacity` elements each:
+ *   x, k : positions and wavevectors, double (WBRW_FP64) or float (WBRW_FP32)
+ *   s    : signs +1 / -1 (int8)
+ *   w    : signed weights (sp2 only; same type as x; NULL for sp1)
+ *   grid : nx*nk int32 signed counts c_nu (grid_cells >= nx*nk), valid after
+ *          a resampling
+ *   scratch : >= wbrw_scratch_bytes(config, capacity) bytes, 256-byte aligned
+ *   event_log : optional (NULL disables): event_log_capacity wbrw_event
+ *          records of accepted events, for parity checks.
+ * The arrays stay owned by the caller.  Between calls they hold the current
+ * particles only after wbrw_step or wbrw_particles; wbrw_run keeps the
+ * particle state implicit in the histogram. */
+typedef struct {
+  void* x;
+  void* k;
+  signed char* s;
+  void* w;
+  long long capacity;
+  int* grid;
+  long long grid_cells;
+  void* scratch;
+  size_t scratch_bytes;
+  void* event_log;
+  long long event_log_capacity;
+} wbrw_buffers;
+
+/* One accepted branching event (Alg. 1 item 3), as logged for parity tests.
+ * kappa is the oriented kick: the + child is at k + kappa, the - child at
+ * k - kappa.  factor = cacc |sin(2 (xe - xc) kappa)|. */
+typedef struct {
+  unsigned long long pid, pid_plus, pid_minus;
+  unsigned int step, j;
+  double t, xe, kappa, factor;
+  int kill_plus, kill_minus;
+} wbrw_event;
+
+/* Counter slots returned by wbrw_counters. */
+enum {
+  WBRW_C_LIVE = 0,        /* materialised particles (or implied by the grid) */
+  WBRW_C_EVENTS = 1,      /* accepted events (pairs emitted), cumulative     */
+  WBRW_C_KILL_PLUS = 2,   /* + offspring killed outside K, cumulative        */
+  WBRW_C_KILL_MINUS = 3,
+  WBRW_C_OUT_PLUS = 4,    /* + particles outside the grid at resampling      */
+  WBRW_C_OUT_MINUS = 5,
+  WBRW_C_PARTICLE_STEPS = 6, /* sum over steps of particles alive at start   */
+  WBRW_C_LOG_LEN = 7,     /* events written to event_log                     */
+  WBRW_C_STEP = 8,        /* index of the next interval                      */
+  WBRW_C_EPOCH = 9,       /* resamplings so far                              */
+  WBRW_C_LAUNCHES = 10,   /* kernels launched by this context                */
+  WBRW_C_BOOT_NPLUS = 11, /* last sp2 filter: N^+, N^-, N_r^+, N_r^-          */
+  WBRW_C_BOOT_NMINUS = 12,
+  WBRW_C_BOOT_NRPLUS = 13,
+  WBRW_C_BOOT_NRMINUS = 14,
+  WBRW_C_BOOT_WPLUS = 15, /* last sp2 filter: W^+ and W^- in Q1.31           */
+  WBRW_C_BOOT_WMINUS = 16,
+  WBRW_C_NONZERO_CELLS = 17,
+  WBRW_C_ERROR = 18,      /* device error word                               */
+  WBRW_C_COUNT = 24
+};
+
+/* Scratch bytes the library needs for `capacity` particles of `config`.
+ * Returns 0 for an invalid configuration. */
+size_t wbrw_scratch_bytes(const wbrw_config* config, long long capacity);
+
+/* Create a context and draw n_init initial particles from the Wigner
+ * function of a Gaussian wavepacket,
+ *   f0(x,k) = (1/pi) exp(-(x-x0)^2/(2 sigma_x^2) - 2 sigma_x^2 (k-k0)^2),
+ * which is positive: x ~ N(x0, sigma_x^2), k ~ N(k0, 1/(4 sigma_x^2)),
+ * sign +1 (Sec. 4.1: f0 is its own instrumental density).
+ * cuda_stream is a cudaStream_t (NULL = legacy default stream).  On success
+ * *out receives the context; on failure *out is NULL and the status says
+ * why. */
+wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
+                      const wbrw_buffers* buffers, long long n_init,
+                      double x0, double sigma_x, double k0, void* cuda_stream,
+                      wbrw_ctx** out);
+
+/* Advance nsteps intervals [t_l, t_{l+1}] (Alg. 1) without resampling and
+ * leave the particles in the caller's arrays (offspring appended).  Async. */
+wbrw_status wbrw_step(wbrw_ctx* ctx, int nsteps);
+
+/* Resample now: sp1 signed histogram, or sp2 signed bootstrap + histogram +
+ * Alg. 3 rounding, into buffers.grid.  The particle set becomes the one
+ * Alg. 3 regenerates from the grid.  A second call with no step in between
+ * does nothing.  Async. */
+wbrw_status wbrw_annihilate(wbrw_ctx* ctx);
+
+/* Advance nsteps intervals and resample whenever the interval index reaches
+ * a multiple of config.resample_every (the schedule of Sec. 4.3 with period
+ * T_A).  Each period fuses regeneration, flight and histogram in one pass, so
+ * particles only reach the arrays if nsteps ends between two resamplings.
+ * Equivalent, bit for bit, to the same sequence of wbrw_step and
+ * wbrw_annihilate.  Async. */
+wbrw_status wbrw_run(wbrw_ctx* ctx, int nsteps);
+
+/* Observables (Eq. estimator) of the current state:
+ *   density_host [nx*nk]: c_nu / (N_alpha dx dk)   (or NULL)
+ *   marginal_x_host [nx]: sum_k c_nu / (N_alpha dx) (or NULL)
+ *   transmission: sum over cells with centre x > 0 of c_nu / N_alpha
+ *   live_particles: particles now (or NULL)
+ * After a resampling c_nu is the grid.  Otherwise the current particles are
+ * histogrammed on the fly (sp2: signed weights in Q1.31) without changing
+ * the state.  Synchronises the stream. */
+wbrw_status wbrw_density(wbrw_ctx* ctx, double* density_host,
+                         double* marginal_x_host, double* transmission,
+                         long long* live_particles);
+
+/* Materialise the particles into the caller's arrays (regenerating them from
+ * the grid if needed), write their count to *n_host and, if pid_dev is not
+ * NULL, their 64-bit stream ids to pid_dev[0..n) (device memory).
+ * Synchronises the stream. */
+wbrw_status wbrw_particles(wbrw_ctx* ctx, long long* n_host,
+                           unsigned long long* pid_dev);
+
+/* Copy the counters (WBRW_C_*) to out[0..WBRW_C_COUNT).  Synchronises. */
+wbrw_status wbrw_counters(wbrw_ctx* ctx, long long* out);
+
+/* Synchronise the stream and report the device error word. */
+wbrw_status wbrw_sync_status(wbrw_ctx* ctx);
+
+/* Human-readable description of the last error of ctx (never NULL). */
+const char* wbrw_last_error(const wbrw_ctx* ctx);
+
+/* Release the context (not the caller's buffers).  NULL is allowed. */
+void wbrw_destroy(wbrw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WBRW_H */

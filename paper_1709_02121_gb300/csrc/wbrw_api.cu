@@ -1,0 +1,444 @@
+// wbrw_api.cu -- the C ABI of include/wbrw.h: argument checks, the carve-up
+// of the caller's scratch buffer, the resampling schedule of Sec. 4.3 and
+// the state machine between "particles in the arrays" and "histogram".
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "wbrw.h"
+#include "wbrw_internal.h"
+
+using namespace wbrw;
+
+struct wbrw_ctx : public Ctx {};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
+
+size_t elem_size(int precision) { return precision == WBRW_FP64 ? 8 : 4; }
+
+// F-queue entry {u64 pid; T x, k, w; int l;} and E-queue entry
+// {u64 pid; T x, k, w; int ls; unsigned mask;} as laid out by the device code.
+size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
+size_t eentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 32; }
+
+struct Layout {
+  size_t counters, cpid, fq0, fq1, eq, nz_cell, nz_start, scan_bsum, scan_bnz,
+      tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
+      rec_a, keep0, keep1, res0, res1, total;
+  long long qcap, ecap, rec_cap, scan_blocks;
+};
+
+bool config_ok(const wbrw_config* c, char* why, size_t n) {
+  auto fail = [&](const char* m) {
+    if (why) snprintf(why, n, "invalid configuration: %s", m);
+    return false;
+  };
+  if (!c) return fail("NULL config");
+  if (c->dim != 2) return fail("dim must be 2");
+  if (c->precision != WBRW_FP64 && c->precision != WBRW_FP32) return fail("precision");
+  if (c->strategy != WBRW_SP1_PAIR && c->strategy != WBRW_SP2_BOOTSTRAP) return fail("strategy");
+  if (!(c->hbar > 0) || !(c->mass > 0) || !(c->dt > 0)) return fail("hbar, mass and dt must be > 0");
+  if (c->nx <= 0 || c->nk <= 0) return fail("nx and nk must be > 0");
+  if ((long long)c->nx * (long long)c->nk >= (1ll << 31)) return fail("nx*nk must be < 2^31");
+  if (!(c->xmax > c->xmin) || !(c->kmax > c->kmin)) return fail("empty domain");
+  if (c->resample_every < 0) return fail("resample_every must be >= 0");
+  if (c->n_alpha <= 0) return fail("n_alpha must be > 0");
+  return true;
+}
+
+Layout layout(const wbrw_config* c, long long capacity) {
+  Layout L;
+  const long long nh = (long long)c->nx * c->nk;
+  L.qcap = capacity;
+  L.ecap = capacity / 16 + 4096;
+  L.rec_cap = c->strategy == WBRW_SP2_BOOTSTRAP ? 4 * capacity : 0;
+  L.scan_blocks = (nh + kScanTile - 1) / kScanTile;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  L.counters = take(sizeof(Counters));
+  L.cpid = take((size_t)capacity * 8);
+  L.fq0 = take((size_t)L.qcap * fentry_size(c->precision));
+  L.fq1 = take((size_t)L.qcap * fentry_size(c->precision));
+  L.eq = take((size_t)L.ecap * eentry_size(c->precision));
+  L.nz_cell = take((size_t)nh * 4);
+  L.nz_start = take((size_t)nh * 8);
+  L.scan_bsum = take((size_t)(L.scan_blocks + 1) * 8);
+  L.scan_bnz = take((size_t)(L.scan_blocks + 1) * 4);
+  L.tmp_grid = take((size_t)nh * 4);
+  L.tmp_wsum = take((size_t)nh * 8);
+  L.obs_density = take((size_t)nh * 8);
+  L.obs_marg = take((size_t)c->nx * 8);
+  L.obs_col = take((size_t)c->nx * 8);
+  L.obs_scalar = take(64);
+  L.rec_cell = take((size_t)L.rec_cap * 4);
+  L.rec_a = take((size_t)L.rec_cap * 4);
+  const bool sp2 = c->strategy == WBRW_SP2_BOOTSTRAP;
+  L.keep0 = take(sp2 ? (size_t)nh * 4 : 0);
+  L.keep1 = take(sp2 ? (size_t)nh * 4 : 0);
+  L.res0 = take(sp2 ? (size_t)nh * 8 : 0);
+  L.res1 = take(sp2 ? (size_t)nh * 8 : 0);
+  L.total = off;
+  return L;
+}
+
+wbrw_status seterr(wbrw_ctx* c, wbrw_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->err, sizeof(c->err), fmt, ap);
+  va_end(ap);
+  if (st != WBRW_ERR_ARG) c->failed = 1;
+  return st;
+}
+
+wbrw_status cuda_check(wbrw_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return WBRW_OK;
+  return seterr(c, WBRW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+const Driver* drv(const wbrw_ctx* c) {
+  return c->cfg.precision == WBRW_FP64 ? driver_fp64() : driver_fp32();
+}
+
+#define WBRW_TRY(c, expr, what)                           \
+  do {                                                    \
+    wbrw_status st_ = cuda_check((c), (expr), (what));    \
+    if (st_ != WBRW_OK) return st_;                       \
+  } while (0)
+
+// Translate the device error word.
+wbrw_status device_status(wbrw_ctx* c) {
+  int err = 0;
+  WBRW_TRY(c, cudaMemcpyAsync(&err, &c->cnt->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "read device error word");
+  WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (err == 0) return WBRW_OK;
+  return seterr(c, WBRW_ERR_CAPACITY,
+                "device error 0x%x:%s%s%s%s%s", err,
+                (err & ERR_CAP_PARTICLES) ? " particle capacity exceeded;" : "",
+                (err & ERR_CAP_QUEUE) ? " offspring queue capacity exceeded;" : "",
+                (err & ERR_CAP_EQUEUE) ? " candidate queue capacity exceeded;" : "",
+                (err & ERR_NESTING) ? " offspring nesting within one interval too deep;" : "",
+                (err & ERR_CAP_RECORDS) ? " bootstrap record capacity exceeded;" : "");
+}
+
+// Histogram the particles of the arrays into c->buf.grid (sp1) or run the
+// signed bootstrap (sp2), then build the regeneration plan.  c->epoch has
+// already been advanced.
+wbrw_status resample_from_arrays(wbrw_ctx* c) {
+  const Driver* d = drv(c);
+  if (c->cfg.strategy == WBRW_SP1_PAIR) {
+    WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
+    WBRW_TRY(c, d->bin(c, DST_BIN1, c->buf.grid, 1), "bin");
+  } else {
+    WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
+    for (int s = 0; s < 2; ++s) {
+      WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
+      WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
+    }
+    WBRW_TRY(c, d->bin(c, DST_BIN2, c->buf.grid, 1), "records");
+    WBRW_TRY(c, launch_boot(c), "bootstrap");
+  }
+  WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+  return WBRW_OK;
+}
+
+wbrw_status ensure_particles(wbrw_ctx* c) {
+  if (c->state == ST_PARTICLES) return WBRW_OK;
+  WBRW_TRY(c, drv(c)->materialize(c), "regenerate");
+  c->state = ST_PARTICLES;
+  return WBRW_OK;
+}
+
+wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
+  wbrw_status st = ensure_particles(c);
+  if (st != WBRW_OK) return st;
+  while (nsteps > 0) {
+    const int ch = nsteps < kMaxChunk ? nsteps : kMaxChunk;
+    WBRW_TRY(c, drv(c)->chunk(c, (int)c->step, (int)c->step + ch, SRC_ARRAY, DST_ARRAY), "step");
+    c->step += ch;
+    nsteps -= ch;
+    c->fresh = 0;
+  }
+  return WBRW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t wbrw_scratch_bytes(const wbrw_config* config, long long capacity) {
+  if (!config_ok(config, nullptr, 0) || capacity <= 0) return 0;
+  return layout(config, capacity).total;
+}
+
+wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
+                      const wbrw_buffers* b, long long n_init, double x0,
+                      double sigma_x, double k0, void* cuda_stream,
+                      wbrw_ctx** out) {
+  if (!out) return WBRW_ERR_ARG;
+  *out = nullptr;
+  char why[256];
+  if (!config_ok(config, why, sizeof(why))) return WBRW_ERR_ARG;
+  if (!pot || pot->kind != WBRW_POT_GAUSSIAN || !(pot->w > 0) || !isfinite(pot->H) ||
+      !isfinite(pot->xc))
+    return WBRW_ERR_ARG;
+  if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0)
+    return WBRW_ERR_ARG;
+  if (config->strategy == WBRW_SP2_BOOTSTRAP && !b->w) return WBRW_ERR_ARG;
+  if (b->grid_cells < (long long)config->nx * config->nk) return WBRW_ERR_ARG;
+  if (((uintptr_t)b->scratch & (kAlign - 1)) != 0) return WBRW_ERR_ARG;
+  if (n_init < 0 || n_init > b->capacity || !(sigma_x > 0)) return WBRW_ERR_ARG;
+  if (b->event_log && b->event_log_capacity <= 0) return WBRW_ERR_ARG;
+  const Layout L = layout(config, b->capacity);
+  if (b->scratch_bytes < L.total) return WBRW_ERR_ARG;
+
+  // constants of Sec. 4.2 / Remark 3 / Sec. 3.2
+  const double C = 2.0 * fabs(pot->H) / config->hbar;
+  double gamma0 = config->gamma0 > 0 ? config->gamma0 : 0.5 * C;
+  if (gamma0 <= 0) gamma0 = 1.0;  // H = 0: no pair is ever accepted
+  const double cacc = C / (2.0 * gamma0);
+  if (cacc > 1.0) return WBRW_ERR_ARG;  // gamma0 below the majorant rate C/2
+
+  wbrw_ctx* c = new (std::nothrow) wbrw_ctx();
+  if (!c) return WBRW_ERR_ARG;
+  c->cfg = *config;
+  c->pot = *pot;
+  c->buf = *b;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->C = C;
+  c->sig_k = 1.0 / (2.0 * pot->w);
+  c->gamma0 = gamma0;
+  c->cacc = cacc;
+  c->hm = config->hbar / config->mass;
+  c->dtv = config->dt * c->hm;
+  c->p_any = -expm1(-gamma0 * config->dt);
+  c->dx = (config->xmax - config->xmin) / (double)config->nx;
+  c->dk = (config->kmax - config->kmin) / (double)config->nk;
+  c->inv_dx = (double)config->nx / (config->xmax - config->xmin);
+  c->inv_dk = (double)config->nk / (config->kmax - config->kmin);
+  c->nh = (long long)config->nx * config->nk;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
+          cudaSuccess) {
+    delete c;
+    return WBRW_ERR_CUDA;
+  }
+  char* base = (char*)b->scratch;
+  c->cnt = (Counters*)(base + L.counters);
+  c->cpid = (unsigned long long*)(base + L.cpid);
+  c->fq[0] = base + L.fq0;
+  c->fq[1] = base + L.fq1;
+  c->qcap = L.qcap;
+  c->eq = base + L.eq;
+  c->ecap = L.ecap;
+  c->nz_cell = (uint32_t*)(base + L.nz_cell);
+  c->nz_start = (unsigned long long*)(base + L.nz_start);
+  c->scan_bsum = (unsigned long long*)(base + L.scan_bsum);
+  c->scan_bnz = (unsigned int*)(base + L.scan_bnz);
+  c->scan_blocks = L.scan_blocks;
+  c->tmp_grid = (int*)(base + L.tmp_grid);
+  c->tmp_wsum = (long long*)(base + L.tmp_wsum);
+  c->obs_density = (double*)(base + L.obs_density);
+  c->obs_marg = (double*)(base + L.obs_marg);
+  c->obs_col = (long long*)(base + L.obs_col);
+  c->obs_scalar = (double*)(base + L.obs_scalar);
+  c->rec_cell = (uint32_t*)(base + L.rec_cell);
+  c->rec_a = (uint32_t*)(base + L.rec_a);
+  c->rec_cap = L.rec_cap;
+  c->boot_keep[0] = (int*)(base + L.keep0);
+  c->boot_keep[1] = (int*)(base + L.keep1);
+  c->boot_res[0] = (unsigned long long*)(base + L.res0);
+  c->boot_res[1] = (unsigned long long*)(base + L.res1);
+  c->state = ST_PARTICLES;
+  c->step = 0;
+  c->epoch = 0;
+  c->fresh = 0;
+  c->failed = 0;
+  c->launches = 0;
+  c->err[0] = 0;
+
+  cudaError_t e = cudaMemsetAsync(c->cnt, 0, sizeof(Counters), c->stream);
+  if (e == cudaSuccess) e = drv(c)->init(c, n_init, x0, sigma_x, k0);
+  if (e != cudaSuccess) {
+    delete c;
+    return WBRW_ERR_CUDA;
+  }
+  *out = c;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_step(wbrw_ctx* c, int nsteps) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (nsteps < 0) return seterr(c, WBRW_ERR_ARG, "nsteps must be >= 0");
+  return step_impl(c, nsteps);
+}
+
+wbrw_status wbrw_annihilate(wbrw_ctx* c) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (c->fresh) return WBRW_OK;
+  wbrw_status st = ensure_particles(c);
+  if (st != WBRW_OK) return st;
+  c->epoch += 1;
+  st = resample_from_arrays(c);
+  if (st != WBRW_OK) return st;
+  c->state = ST_HISTOGRAM;
+  c->fresh = 1;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_run(wbrw_ctx* c, int nsteps) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (nsteps < 0) return seterr(c, WBRW_ERR_ARG, "nsteps must be >= 0");
+  const int T = c->cfg.resample_every;
+  if (T <= 0) return step_impl(c, nsteps);
+  while (nsteps > 0) {
+    const int to_boundary = T - (int)(c->step % T);
+    if (nsteps < to_boundary || to_boundary > kMaxChunk) {
+      // no resampling inside this piece: plain steps into the arrays
+      int ch = nsteps < to_boundary ? nsteps : to_boundary - kMaxChunk;
+      if (ch > kMaxChunk) ch = kMaxChunk;
+      wbrw_status st = step_impl(c, ch);
+      if (st != WBRW_OK) return st;
+      nsteps -= ch;
+      continue;
+    }
+    // one fused period: (regenerate) + fly to the boundary + histogram
+    const Driver* d = drv(c);
+    const int src = c->state == ST_HISTOGRAM ? SRC_REGEN : SRC_ARRAY;
+    const int l0 = (int)c->step, L = l0 + to_boundary;
+    const long long regen_epoch = c->epoch;
+    c->epoch += 1;  // the histogram this period produces
+    if (c->cfg.strategy == WBRW_SP1_PAIR) {
+      WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
+    } else {
+      WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
+      for (int s = 0; s < 2; ++s) {
+        WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
+        WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
+      }
+    }
+    // the regeneration of the previous histogram uses its own epoch's ids
+    const long long keep_epoch = c->epoch;
+    c->epoch = regen_epoch;
+    cudaError_t e = d->chunk(c, l0, L, src,
+                             c->cfg.strategy == WBRW_SP1_PAIR ? DST_BIN1 : DST_BIN2);
+    c->epoch = keep_epoch;
+    WBRW_TRY(c, e, "period");
+    if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c), "bootstrap");
+    WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+    c->step = L;
+    c->state = ST_HISTOGRAM;
+    c->fresh = 1;
+    nsteps -= to_boundary;
+  }
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_density(wbrw_ctx* c, double* density_host, double* marginal_x_host,
+                         double* transmission, long long* live_particles) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  wbrw_status st;
+  if (c->state == ST_HISTOGRAM) {
+    WBRW_TRY(c, launch_observables(c, c->buf.grid, nullptr), "observables");
+  } else if (c->cfg.strategy == WBRW_SP1_PAIR) {
+    WBRW_TRY(c, launch_zero(c, c->tmp_grid, (size_t)c->nh * 4), "zero");
+    WBRW_TRY(c, drv(c)->bin(c, DST_BIN1, c->tmp_grid, 0), "bin");
+    WBRW_TRY(c, launch_observables(c, c->tmp_grid, nullptr), "observables");
+  } else {
+    WBRW_TRY(c, launch_zero(c, c->tmp_wsum, (size_t)c->nh * 8), "zero");
+    WBRW_TRY(c, drv(c)->bin(c, DST_WSUM, c->tmp_grid, 0), "bin");
+    WBRW_TRY(c, launch_observables(c, nullptr, c->tmp_wsum), "observables");
+  }
+  if (density_host)
+    WBRW_TRY(c, cudaMemcpyAsync(density_host, c->obs_density, (size_t)c->nh * 8,
+                                cudaMemcpyDeviceToHost, c->stream), "copy density");
+  if (marginal_x_host)
+    WBRW_TRY(c, cudaMemcpyAsync(marginal_x_host, c->obs_marg, (size_t)c->cfg.nx * 8,
+                                cudaMemcpyDeviceToHost, c->stream), "copy marginal");
+  double T = 0;
+  unsigned long long live = 0;
+  WBRW_TRY(c, cudaMemcpyAsync(&T, c->obs_scalar, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  WBRW_TRY(c, cudaMemcpyAsync(&live, c->state == ST_HISTOGRAM ? &c->cnt->regen_total : &c->cnt->n,
+                              8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  st = device_status(c);
+  if (st != WBRW_OK) return st;
+  if (transmission) *transmission = T;
+  if (live_particles) *live_particles = (long long)live;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_particles(wbrw_ctx* c, long long* n_host, unsigned long long* pid_dev) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  wbrw_status st = ensure_particles(c);
+  if (st != WBRW_OK) return st;
+  if (pid_dev) WBRW_TRY(c, drv(c)->pids(c, pid_dev), "ids");
+  unsigned long long n = 0;
+  WBRW_TRY(c, cudaMemcpyAsync(&n, &c->cnt->n, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  st = device_status(c);
+  if (st != WBRW_OK) return st;
+  if (n_host) *n_host = (long long)n;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_counters(wbrw_ctx* c, long long* out) {
+  if (!c || !out) return WBRW_ERR_ARG;
+  Counters h;
+  WBRW_TRY(c, cudaMemcpyAsync(&h, c->cnt, sizeof(Counters), cudaMemcpyDeviceToHost, c->stream),
+           "copy counters");
+  WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  for (int i = 0; i < WBRW_C_COUNT; ++i) out[i] = 0;
+  out[WBRW_C_LIVE] = (long long)(c->state == ST_HISTOGRAM ? h.regen_total : h.n);
+  out[WBRW_C_EVENTS] = (long long)h.ledger[LG_EVENTS];
+  out[WBRW_C_KILL_PLUS] = (long long)h.ledger[LG_KILL_P];
+  out[WBRW_C_KILL_MINUS] = (long long)h.ledger[LG_KILL_M];
+  out[WBRW_C_OUT_PLUS] = (long long)h.ledger[LG_OUT_P];
+  out[WBRW_C_OUT_MINUS] = (long long)h.ledger[LG_OUT_M];
+  out[WBRW_C_PARTICLE_STEPS] = (long long)h.ledger[LG_PSTEPS];
+  out[WBRW_C_LOG_LEN] = (long long)h.log_len;
+  out[WBRW_C_STEP] = c->step;
+  out[WBRW_C_EPOCH] = c->epoch;
+  out[WBRW_C_LAUNCHES] = c->launches;
+  out[WBRW_C_BOOT_NPLUS] = (long long)h.boot_n[0];
+  out[WBRW_C_BOOT_NMINUS] = (long long)h.boot_n[1];
+  out[WBRW_C_BOOT_NRPLUS] = (long long)h.boot_nr[0];
+  out[WBRW_C_BOOT_NRMINUS] = (long long)h.boot_nr[1];
+  out[WBRW_C_BOOT_WPLUS] = (long long)h.boot_w[0];
+  out[WBRW_C_BOOT_WMINUS] = (long long)h.boot_w[1];
+  out[WBRW_C_NONZERO_CELLS] = (long long)h.nz_count;
+  out[WBRW_C_ERROR] = h.err;
+  if (h.err) return device_status(c);
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_sync_status(wbrw_ctx* c) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  return device_status(c);
+}
+
+const char* wbrw_last_error(const wbrw_ctx* c) {
+  if (!c) return "NULL context";
+  return c->err;
+}
+
+void wbrw_destroy(wbrw_ctx* c) { delete c; }
+
+}  // extern "C"

@@ -1,0 +1,444 @@
+// wbrw_common.cu -- precision-independent kernels of the resampling step:
+// the cell scans that turn a signed histogram into the regeneration plan of
+// Alg. 3, the signed residual bootstrap of sp2 (Alg. 2 with Eq. lambda and
+// Eq. double_bootstrap / boostrap_histogram) and the observables of
+// Eq. estimator.  All counts are integers and all sums that decide a count
+// are in fixed point, so the results do not depend on thread order.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wbrw_internal.h"
+
+namespace wbrw {
+
+namespace {
+
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2,
+                                        uint32_t c3, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t n0 = hi1 ^ c1 ^ k0;
+    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
+  return __dmul_rn(__dadd_rn(__dmul_rn((double)(a >> 5), 67108864.0),
+                             (double)(b >> 6)),
+                   1.0 / 9007199254740992.0);
+}
+
+constexpr uint32_t kStepBoot = 0xFFFFFFFDu;
+constexpr uint32_t kStepRound = 0xFFFFFFFCu;
+
+// ---------------------------------------------------------------------------
+// Counter set-up (one thread).
+// ---------------------------------------------------------------------------
+__global__ void k_setup(Counters* c, int op, unsigned long long a,
+                        unsigned long long b) {
+  (void)b;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  switch (op) {
+    case SETUP_CHUNK:
+      c->n_src = c->n;
+      for (int i = 0; i < kMaxChunk + 2; ++i) {
+        c->q[i] = 0;
+        c->e[i] = 0;
+      }
+      break;
+    case SETUP_AFTER_REGEN:
+      c->n = c->regen_total;
+      c->n_base = c->regen_total;
+      c->base_pid = a;
+      break;
+    case SETUP_INIT:
+      c->n = a;
+      c->n_base = a;
+      c->base_pid = 0;
+      break;
+    case SETUP_BOOT:
+      c->rec_len = 0;
+      for (int s = 0; s < 2; ++s) {
+        c->boot_n[s] = c->boot_w[s] = c->boot_keep[s] = c->boot_nr[s] = 0;
+        c->boot_R[s] = 0;
+      }
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one u64 per thread (kBlock threads).
+// ---------------------------------------------------------------------------
+__device__ unsigned long long block_exscan(unsigned long long v,
+                                           unsigned long long* red,
+                                           unsigned long long& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) red[wid] = inc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int i = 0; i < kBlock / 32; ++i) {
+      const unsigned long long t = red[i];
+      red[i] = run;
+      run += t;
+    }
+    red[kBlock / 32] = run;
+  }
+  __syncthreads();
+  const unsigned long long ex = red[wid] + inc - v;
+  total = red[kBlock / 32];
+  __syncthreads();
+  return ex;
+}
+
+// ---------------------------------------------------------------------------
+// Histogram -> regeneration plan (Alg. 3 without rounding): n_nu = |c_nu|,
+// exclusive scan over cells, compact list of the nonzero cells with their
+// first slot.  Three passes over tiles of kScanTile cells.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_cells_a(const int* grid, long long nh,
+                                                    unsigned long long* bsum,
+                                                    unsigned int* bnz) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned long long s = 0, z = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const long long c = base + i;
+    if (c < nh) {
+      const int v = grid[c];
+      s += (unsigned long long)(v < 0 ? -(long long)v : (long long)v);
+      z += v != 0;
+    }
+  }
+  unsigned long long ts, tz;
+  block_exscan(s, red, ts);
+  block_exscan(z, red, tz);
+  if (threadIdx.x == 0) {
+    bsum[blockIdx.x] = ts;
+    bnz[blockIdx.x] = (unsigned int)tz;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
+                                                    unsigned int* bnz,
+                                                    long long nb, Counters* c) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  unsigned long long carry_s = 0, carry_z = 0;
+  for (long long b0 = 0; b0 < nb; b0 += kBlock) {
+    const long long b = b0 + threadIdx.x;
+    const unsigned long long s = b < nb ? bsum[b] : 0, z = b < nb ? bnz[b] : 0;
+    unsigned long long ts, tz;
+    const unsigned long long es = block_exscan(s, red, ts);
+    const unsigned long long ez = block_exscan(z, red, tz);
+    if (b < nb) {
+      bsum[b] = carry_s + es;
+      bnz[b] = (unsigned int)(carry_z + ez);
+    }
+    carry_s += ts;
+    carry_z += tz;
+  }
+  if (threadIdx.x == 0) {
+    c->regen_total = carry_s;
+    c->nz_count = carry_z;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_cells_c(const int* grid, long long nh,
+                                                    const unsigned long long* bsum,
+                                                    const unsigned int* bnz,
+                                                    uint32_t* nz_cell,
+                                                    unsigned long long* nz_start) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  int v[kScanItems];
+  unsigned long long s = 0, z = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    const long long c = base + i;
+    v[i] = c < nh ? grid[c] : 0;
+    s += (unsigned long long)(v[i] < 0 ? -(long long)v[i] : (long long)v[i]);
+    z += v[i] != 0;
+  }
+  unsigned long long ts, tz;
+  unsigned long long os = block_exscan(s, red, ts) + bsum[blockIdx.x];
+  unsigned long long oz = block_exscan(z, red, tz) + bnz[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    if (v[i] != 0) {
+      nz_cell[oz] = (uint32_t)(base + i) | (v[i] < 0 ? 0x80000000u : 0u);
+      nz_start[oz] = os;
+      ++oz;
+      os += (unsigned long long)(v[i] < 0 ? -(long long)v[i] : (long long)v[i]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// In-place inclusive scan of a u64 array (per-cell bootstrap residuals).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_u64_a(const unsigned long long* a, long long n,
+                                                  unsigned long long* bsum) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += a[base + i];
+  unsigned long long t;
+  block_exscan(s, red, t);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kBlock) k_u64_b(unsigned long long* bsum, long long nb,
+                                                  unsigned long long* total) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  unsigned long long carry = 0;
+  for (long long b0 = 0; b0 < nb; b0 += kBlock) {
+    const long long b = b0 + threadIdx.x;
+    const unsigned long long s = b < nb ? bsum[b] : 0;
+    unsigned long long t;
+    const unsigned long long e = block_exscan(s, red, t);
+    if (b < nb) bsum[b] = carry + e;
+    carry += t;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long long n,
+                                                  const unsigned long long* bsum) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned long long v[kScanItems];
+  unsigned long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < n ? a[base + i] : 0;
+    s += v[i];
+  }
+  unsigned long long t;
+  unsigned long long run = block_exscan(s, red, t) + bsum[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    run += v[i];
+    if (base + i < n) a[base + i] = run;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sp2 bootstrap (Alg. 2 per side).  Records hold (cell | side << 31, a) with
+// a = floor(|w| 2^31); N^s and W^s = sum a were tallied with the records.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t* rec_cell,
+                                                     const uint32_t* rec_a, long long rec_cap,
+                                                     int* keep0, int* keep1,
+                                                     unsigned long long* res0,
+                                                     unsigned long long* res1) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const unsigned long long n = min(c->rec_len, (unsigned long long)rec_cap);
+  double ratio[2];
+  for (int s = 0; s < 2; ++s)
+    ratio[s] = c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
+  unsigned long long ks[2] = {0, 0};
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * kBlock) {
+    const uint32_t rc = rec_cell[i];
+    const int side = rc >> 31;
+    const uint32_t cell = rc & 0x7FFFFFFFu;
+    const double q = __dmul_rn((double)rec_a[i], ratio[side]);
+    const double fl = floor(q);
+    const unsigned long long res =
+        (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
+    const int kf = (int)fl;
+    if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
+    if (res) atomicAdd((side ? res1 : res0) + cell, res);
+    ks[side] += (unsigned long long)kf;
+  }
+  for (int s = 0; s < 2; ++s) {
+    unsigned long long t;
+    block_exscan(ks[s], red, t);
+    if (threadIdx.x == 0 && t) atomicAdd(&c->boot_keep[s], t);
+  }
+}
+
+// N_r^s = N^s - sum floor(q_i) draws per side, each an upper-bound search of
+// U = floor(r R / 2^64) in the inclusive residual prefix.
+__global__ void __launch_bounds__(kBlock) k_boot_draw(Counters* c, long long nh,
+                                                      const unsigned long long* pre0,
+                                                      const unsigned long long* pre1,
+                                                      int* keep0, int* keep1,
+                                                      uint32_t key0, uint32_t key1,
+                                                      unsigned long long epoch) {
+  unsigned long long nr[2];
+  for (int s = 0; s < 2; ++s) {
+    const long long d = (long long)c->boot_n[s] - (long long)c->boot_keep[s];
+    nr[s] = d > 0 ? (unsigned long long)d : 0ull;
+    if (c->boot_R[s] == 0) nr[s] = 0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->boot_nr[0] = nr[0];
+    c->boot_nr[1] = nr[1];
+  }
+  const unsigned long long total = nr[0] + nr[1];
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * kBlock) {
+    const int side = i < nr[0] ? 0 : 1;
+    const unsigned long long d = side ? i - nr[0] : i;
+    const uint4 r = philox((uint32_t)d, (uint32_t)(d >> 32), kStepBoot,
+                           (uint32_t)((epoch << 1) | (unsigned long long)side), key0, key1);
+    const unsigned long long r64 = ((unsigned long long)r.y << 32) | r.x;
+    const unsigned long long U = __umul64hi(r64, c->boot_R[side]);
+    const unsigned long long* pre = side ? pre1 : pre0;
+    long long lo = 0, hi = nh - 1;  // first cell with pre > U
+    while (lo < hi) {
+      const long long mid = lo + (hi - lo) / 2;
+      if (pre[mid] > U) hi = mid; else lo = mid + 1;
+    }
+    atomicAdd((side ? keep1 : keep0) + lo, 1);
+  }
+}
+
+// m_nu = (W^+/N^+) n~+ - (W^-/N^-) n~- (= N_alpha mu d_nu), rounded as Alg. 3.
+__global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long long nh,
+                                                         const int* keep0, const int* keep1,
+                                                         int* grid, uint32_t key0,
+                                                         uint32_t key1, unsigned long long epoch) {
+  double amp[2];
+  for (int s = 0; s < 2; ++s)
+    amp[s] = c->boot_n[s] > 0
+                 ? __ddiv_rn(__dmul_rn((double)c->boot_w[s], 1.0 / 2147483648.0),
+                             (double)c->boot_n[s])
+                 : 0.0;
+  for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
+       nu += (long long)gridDim.x * kBlock) {
+    const double m = __dsub_rn(__dmul_rn((double)keep0[nu], amp[0]),
+                               __dmul_rn((double)keep1[nu], amp[1]));
+    const double am = fabs(m);
+    const double fl = floor(am);
+    const uint4 r = philox((uint32_t)nu, (uint32_t)((unsigned long long)nu >> 32), kStepRound,
+                           (uint32_t)epoch, key0, key1);
+    const double u = u53(r.x, r.y);
+    const long long cnt = (long long)fl + (u < __dsub_rn(am, fl) ? 1 : 0);
+    grid[nu] = (int)(m < 0 ? -cnt : cnt);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Observables: one warp per x-column.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_obs_cols(const int* counts, const long long* wsum,
+                                                     int nx, int nk, double na, double dx,
+                                                     double dk, double* density, double* marg,
+                                                     long long* col) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kBlock) >> 5;
+  const double scale = wsum ? 1.0 / 2147483648.0 : 1.0;
+  for (long long ix = warp; ix < nx; ix += nwarps) {
+    long long s = 0;
+    for (int ik = lane; ik < nk; ik += 32) {
+      const long long nu = ix * nk + ik;
+      const long long v = wsum ? wsum[nu] : (long long)counts[nu];
+      s += v;
+      if (density)
+        density[nu] = __ddiv_rn(__dmul_rn((double)v, scale), __dmul_rn(__dmul_rn(na, dx), dk));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) {
+      col[ix] = s;
+      marg[ix] = __ddiv_rn(__dmul_rn((double)s, scale), __dmul_rn(na, dx));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_obs_total(const long long* col, int nx, double xmin,
+                                                      double dx, double na, double scale,
+                                                      double* out) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  long long s = 0;
+  for (int ix = threadIdx.x; ix < nx; ix += kBlock) {
+    const double centre = __dadd_rn(xmin, __dmul_rn(__dadd_rn((double)ix, 0.5), dx));
+    if (centre > 0.0) s += col[ix];
+  }
+  unsigned long long t;
+  block_exscan((unsigned long long)s, red, t);
+  if (threadIdx.x == 0)
+    out[0] = __ddiv_rn(__dmul_rn((double)(long long)t, scale), na);
+}
+
+int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
+
+}  // namespace
+
+cudaError_t launch_setup(Ctx* c, int op, unsigned long long a, unsigned long long b) {
+  k_setup<<<1, 32, 0, c->stream>>>(c->cnt, op, a, b);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(Ctx* c, void* p, size_t bytes) {
+  return cudaMemsetAsync(p, 0, bytes, c->stream);
+}
+
+cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
+  const long long nb = c->scan_blocks;
+  k_cells_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz);
+  k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt);
+  k_cells_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz,
+                                                   c->nz_cell, c->nz_start);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+// Called after the records of the period are written and tallied.
+cudaError_t launch_boot(Ctx* c) {
+  const long long nh = c->nh, nb = c->scan_blocks;
+  const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
+  const unsigned long long epoch = (unsigned long long)c->epoch;
+  const int g = grid_cap(c, 8);
+  k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rec_cap,
+                                          c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
+                                          c->boot_res[1]);
+  c->launches++;
+  for (int s = 0; s < 2; ++s) {
+    k_u64_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
+    k_u64_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, nb, &c->cnt->boot_R[s]);
+    k_u64_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
+    c->launches += 3;
+  }
+  k_boot_draw<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_res[0], c->boot_res[1],
+                                           c->boot_keep[0], c->boot_keep[1], key0, key1, epoch);
+  k_boot_combine<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_keep[0], c->boot_keep[1],
+                                              c->buf.grid, key0, key1, epoch);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observables(Ctx* c, const int* counts, const long long* wsum) {
+  const double na = (double)c->cfg.n_alpha;
+  const int g = grid_cap(c, 4);
+  k_obs_cols<<<g, kBlock, 0, c->stream>>>(counts, wsum, c->cfg.nx, c->cfg.nk, na, c->dx, c->dk,
+                                          c->obs_density, c->obs_marg, c->obs_col);
+  k_obs_total<<<1, kBlock, 0, c->stream>>>(c->obs_col, c->cfg.nx, c->cfg.xmin, c->dx, na,
+                                           wsum ? 1.0 / 2147483648.0 : 1.0, c->obs_scalar);
+  c->launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace wbrw

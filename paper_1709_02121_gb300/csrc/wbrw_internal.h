@@ -1,0 +1,125 @@
+// wbrw_internal.h -- host-side context shared by the C-ABI translation unit
+// and the per-precision kernel drivers.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "wbrw.h"
+
+namespace wbrw {
+
+constexpr int kBlock = 256;      // threads per block of every particle kernel
+constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
+constexpr int kScanItems = 8;    // cells per thread in the cell scans
+constexpr int kScanTile = kBlock * kScanItems;
+
+enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2 };
+enum Dst { DST_ARRAY = 0, DST_BIN1 = 1, DST_BIN2 = 2, DST_WSUM = 3 };
+
+// device error bits (Counters::err)
+enum : int {
+  ERR_CAP_PARTICLES = 1,
+  ERR_CAP_QUEUE = 2,
+  ERR_CAP_EQUEUE = 4,
+  ERR_NESTING = 8,
+  ERR_CAP_RECORDS = 16,
+};
+
+// ledger slots (Counters::ledger)
+enum { LG_EVENTS = 0, LG_KILL_P, LG_KILL_M, LG_OUT_P, LG_OUT_M, LG_PSTEPS, LG_N = 8 };
+
+// Device-resident counters: every count the host would otherwise need lives
+// here, so no launch waits for the host.
+struct Counters {
+  unsigned long long n;            // particles in the arrays
+  unsigned long long n_src;        // snapshot of n at the start of a chunk
+  unsigned long long n_base;       // slots < n_base have pid = base_pid + slot
+  unsigned long long base_pid;
+  unsigned long long q[kMaxChunk + 2];  // F-queue entries for round r
+  unsigned long long e[kMaxChunk + 2];  // overflow candidate entries, round r
+  unsigned long long nz_count;     // nonzero cells of the last histogram
+  unsigned long long regen_total;  // particles implied by the histogram
+  unsigned long long log_len;
+  unsigned long long rec_len;      // sp2 records
+  unsigned long long ledger[LG_N];
+  unsigned long long boot_n[2], boot_w[2], boot_keep[2], boot_nr[2];
+  unsigned long long boot_R[2];    // total residual (Q0.32) per side
+  long long obs_total;             // observables: transmission numerator
+  int err;
+  int pad[3];
+};
+
+struct Ctx {
+  wbrw_config cfg;
+  wbrw_potential pot;
+  wbrw_buffers buf;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  // constants (Sec. 4.2 / Remark 3 / Sec. 3.2), host FP64
+  double C, sig_k, gamma0, cacc, hm, dtv, p_any, dx, dk, inv_dx, inv_dk;
+  long long nh;  // cells
+  // scratch carve-up
+  Counters* cnt;
+  unsigned long long* cpid;
+  void* fq[2];
+  long long qcap;
+  void* eq;
+  long long ecap;
+  uint32_t* nz_cell;
+  unsigned long long* nz_start;
+  unsigned long long* scan_bsum;
+  unsigned int* scan_bnz;
+  long long scan_blocks;
+  int* tmp_grid;
+  long long* tmp_wsum;
+  double* obs_density;
+  double* obs_marg;
+  long long* obs_col;
+  double* obs_scalar;
+  uint32_t* rec_cell;
+  uint32_t* rec_a;
+  long long rec_cap;
+  int* boot_keep[2];
+  unsigned long long* boot_res[2];
+  // state
+  int state;  // 0 = particles in the arrays, 1 = histogram (grid + nz lists)
+  long long step;
+  long long epoch;
+  int fresh;
+  int failed;
+  long long launches;
+  char err[512];
+};
+
+enum { ST_PARTICLES = 0, ST_HISTOGRAM = 1 };
+
+// Per-precision drivers (wbrw_fp64.cu / wbrw_fp32.cu).
+struct Driver {
+  cudaError_t (*init)(Ctx*, long long n, double x0, double sx, double k0);
+  // Fly [l0, L) from the source, offspring in waves, finals to dst.
+  cudaError_t (*chunk)(Ctx*, int l0, int L, int src, int dst);
+  // Histogram the arrays (no flight): dst = DST_BIN1 into grid / DST_BIN2
+  // records / DST_WSUM into tmp_wsum; count_ledger = tally out-of-grid.
+  cudaError_t (*bin)(Ctx*, int dst, int* grid, int count_ledger);
+  // Regenerate the histogram into the arrays (Alg. 3).
+  cudaError_t (*materialize)(Ctx*);
+  cudaError_t (*pids)(Ctx*, unsigned long long* out);
+};
+
+const Driver* driver_fp64();
+const Driver* driver_fp32();
+
+// Precision-independent launches (wbrw_common.cu).
+cudaError_t launch_setup(Ctx*, int op, unsigned long long a,
+                         unsigned long long b);
+cudaError_t launch_scan_cells(Ctx*, const int* grid);
+cudaError_t launch_boot(Ctx*);
+cudaError_t launch_observables(Ctx*, const int* counts, const long long* wsum);
+cudaError_t launch_zero(Ctx*, void* p, size_t bytes);
+
+enum { SETUP_CHUNK = 0, SETUP_AFTER_REGEN = 1, SETUP_INIT = 2,
+       SETUP_BOOT = 3 };
+
+}  // namespace wbrw

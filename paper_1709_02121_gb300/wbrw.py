@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in include/wbrw.h (argument marshalling only).
+
+The functions below carry the C names and forward to ``libwbrw.so`` through
+ctypes; every step of the method runs in the library's CUDA kernels.  PyTorch
+supplies device memory and the stream.  There is no CPU fallback: if the
+library has not been built, loading it raises.
+
+``Simulation`` bundles a context with the device buffers it needs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwbrw.so")
+
+OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NUMERIC = 0, -1, -2, -3, -4, -5, -6
+SP1_PAIR, SP2_BOOTSTRAP = 1, 2
+FP64, FP32 = 0, 1
+POT_GAUSSIAN = 0
+
+# counter slots (WBRW_C_*)
+COUNTERS = ("live", "events", "kill_plus", "kill_minus", "out_plus", "out_minus",
+            "particle_steps", "log_len", "step", "epoch", "launches",
+            "boot_nplus", "boot_nminus", "boot_nrplus", "boot_nrminus",
+            "boot_wplus", "boot_wminus", "nonzero_cells", "error")
+C_COUNT = 24
+
+SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
+           "wbrw_run", "wbrw_density", "wbrw_particles", "wbrw_counters",
+           "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("precision", ctypes.c_int),
+                ("strategy", ctypes.c_int),
+                ("hbar", ctypes.c_double), ("mass", ctypes.c_double),
+                ("dt", ctypes.c_double), ("gamma0", ctypes.c_double),
+                ("nx", ctypes.c_int), ("nk", ctypes.c_int),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
+                ("resample_every", ctypes.c_int),
+                ("n_alpha", ctypes.c_longlong),
+                ("seed", ctypes.c_ulonglong)]
+
+
+class Potential(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("H", ctypes.c_double),
+                ("w", ctypes.c_double), ("xc", ctypes.c_double)]
+
+
+class Buffers(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("k", ctypes.c_void_p),
+                ("s", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("capacity", ctypes.c_longlong),
+                ("grid", ctypes.c_void_p), ("grid_cells", ctypes.c_longlong),
+                ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_size_t),
+                ("event_log", ctypes.c_void_p),
+                ("event_log_capacity", ctypes.c_longlong)]
+
+
+EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"), ("pid_minus", "<u8"),
+                        ("step", "<u4"), ("j", "<u4"), ("t", "<f8"), ("xe", "<f8"),
+                        ("kappa", "<f8"), ("factor", "<f8"), ("kill_plus", "<i4"),
+                        ("kill_minus", "<i4")])
+
+_lib = None
+
+
+class WbrwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("wbrw status %d: %s" % (status, msg))
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libwbrw.so (built by paper_1709_02121_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libwbrw.so is not built (%s); run "
+                           "paper_1709_02121_gb300.build.build() first" % path)
+    L = ctypes.CDLL(path)
+    P, LL, I = ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int
+    L.wbrw_scratch_bytes.argtypes = [ctypes.POINTER(Config), LL]
+    L.wbrw_scratch_bytes.restype = ctypes.c_size_t
+    L.wbrw_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Potential),
+                            ctypes.POINTER(Buffers), LL, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_double, P,
+                            ctypes.POINTER(P)]
+    for name in ("wbrw_init", "wbrw_step", "wbrw_annihilate", "wbrw_run",
+                 "wbrw_density", "wbrw_particles", "wbrw_counters",
+                 "wbrw_sync_status"):
+        getattr(L, name).restype = I
+    L.wbrw_step.argtypes = [P, I]
+    L.wbrw_annihilate.argtypes = [P]
+    L.wbrw_run.argtypes = [P, I]
+    L.wbrw_density.argtypes = [P, P, P, P, P]
+    L.wbrw_particles.argtypes = [P, P, P]
+    L.wbrw_counters.argtypes = [P, P]
+    L.wbrw_sync_status.argtypes = [P]
+    L.wbrw_last_error.argtypes = [P]
+    L.wbrw_last_error.restype = ctypes.c_char_p
+    L.wbrw_destroy.argtypes = [P]
+    L.wbrw_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(ctx, st):
+    if st != OK:
+        msg = load().wbrw_last_error(ctx).decode() if ctx else ""
+        raise WbrwError(st, msg)
+
+
+# ---- the C calls, same names ------------------------------------------------
+def wbrw_scratch_bytes(cfg: Config, capacity: int) -> int:
+    return load().wbrw_scratch_bytes(ctypes.byref(cfg), capacity)
+
+
+def wbrw_init(cfg, pot, bufs, n_init, x0, sigma_x, k0, stream_ptr):
+    ctx = ctypes.c_void_p()
+    st = load().wbrw_init(ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(bufs),
+                          n_init, x0, sigma_x, k0, ctypes.c_void_p(stream_ptr),
+                          ctypes.byref(ctx))
+    if st != OK:
+        raise WbrwError(st, "wbrw_init rejected its arguments")
+    return ctx
+
+
+def wbrw_step(ctx, nsteps):
+    _check(ctx, load().wbrw_step(ctx, nsteps))
+
+
+def wbrw_annihilate(ctx):
+    _check(ctx, load().wbrw_annihilate(ctx))
+
+
+def wbrw_run(ctx, nsteps):
+    _check(ctx, load().wbrw_run(ctx, nsteps))
+
+
+def wbrw_density(ctx, nx, nk):
+    dens = np.empty(nx * nk, np.float64)
+    marg = np.empty(nx, np.float64)
+    T = ctypes.c_double()
+    live = ctypes.c_longlong()
+    _check(ctx, load().wbrw_density(ctx, dens.ctypes.data, marg.ctypes.data,
+                                    ctypes.byref(T), ctypes.byref(live)))
+    return dens.reshape(nx, nk), marg, T.value, live.value
+
+
+def wbrw_particles(ctx, pid_dev_ptr=None):
+    n = ctypes.c_longlong()
+    _check(ctx, load().wbrw_particles(ctx, ctypes.byref(n),
+                                      ctypes.c_void_p(pid_dev_ptr) if pid_dev_ptr else None))
+    return n.value
+
+
+def wbrw_counters(ctx):
+    out = np.zeros(C_COUNT, np.int64)
+    _check(ctx, load().wbrw_counters(ctx, out.ctypes.data))
+    return dict(zip(COUNTERS, out.tolist()))
+
+
+def wbrw_sync_status(ctx):
+    return load().wbrw_sync_status(ctx)
+
+
+def wbrw_last_error(ctx):
+    return load().wbrw_last_error(ctx).decode()
+
+
+def wbrw_destroy(ctx):
+    if ctx:
+        load().wbrw_destroy(ctx)
+
+
+# ---- convenience: a context plus its torch-owned buffers --------------------
+class Simulation:
+    """One WBRW run on the current CUDA device.
+
+    ``wl`` is a workload dict (see workloads.py); ``capacity`` bounds the
+    particles held at once (and each offspring wave).
+    """
+
+    def __init__(self, wl: dict, capacity: int, *, event_log: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.wl = dict(wl)
+        prec = FP64 if wl["precision"] == "fp64" else FP32
+        strat = SP1_PAIR if wl["strategy"] == "sp1" else SP2_BOOTSTRAP
+        self.cfg = Config(2, prec, strat, wl["hbar"], wl["mass"], wl["dt"], wl["gamma0"],
+                          wl["nx"], wl["nk"], wl["xmin"], wl["xmax"], wl["kmin"], wl["kmax"],
+                          wl["resample_every"], int(wl["n_alpha"]), int(wl["seed"]))
+        self.pot = Potential(POT_GAUSSIAN, wl["H"], wl["w"], wl["xc"])
+        dev = torch.device("cuda", torch.cuda.current_device())
+        fdt = torch.float64 if prec == FP64 else torch.float32
+        self.nx, self.nk = wl["nx"], wl["nk"]
+        self.capacity = int(capacity)
+        self.x = torch.empty(self.capacity, dtype=fdt, device=dev)
+        self.k = torch.empty(self.capacity, dtype=fdt, device=dev)
+        self.s = torch.empty(self.capacity, dtype=torch.int8, device=dev)
+        self.w = torch.empty(self.capacity, dtype=fdt, device=dev) if strat == SP2_BOOTSTRAP else None
+        self.grid = torch.zeros(self.nx * self.nk, dtype=torch.int32, device=dev)
+        nbytes = wbrw_scratch_bytes(self.cfg, self.capacity)
+        if nbytes == 0:
+            raise ValueError("invalid configuration")
+        self.scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.log = (torch.zeros(event_log * EVENT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+                    if event_log else None)
+        self.bufs = Buffers(self.x.data_ptr(), self.k.data_ptr(), self.s.data_ptr(),
+                            self.w.data_ptr() if self.w is not None else None,
+                            self.capacity, self.grid.data_ptr(), self.nx * self.nk,
+                            self.scratch.data_ptr(), nbytes,
+                            self.log.data_ptr() if self.log is not None else None,
+                            event_log)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = wbrw_init(self.cfg, self.pot, self.bufs, int(wl["n_alpha"]),
+                             wl["x0"], wl["sigma_x"], wl["k0"], self.stream.cuda_stream)
+
+    def step(self, n=1):
+        wbrw_step(self.ctx, n)
+
+    def annihilate(self):
+        wbrw_annihilate(self.ctx)
+
+    def run(self, n):
+        wbrw_run(self.ctx, n)
+
+    def density(self):
+        return wbrw_density(self.ctx, self.nx, self.nk)
+
+    def counters(self):
+        return wbrw_counters(self.ctx)
+
+    def particles(self, with_pids=True):
+        """(x, k, s, w, pid) of the current particles as host numpy arrays."""
+        torch = self.torch
+        n = wbrw_particles(self.ctx)
+        pid = None
+        if with_pids:
+            pid_t = torch.empty(max(n, 1), dtype=torch.int64, device=self.x.device)
+            wbrw_particles(self.ctx, pid_t.data_ptr())
+            pid = pid_t[:n].cpu().numpy().view(np.uint64)
+        x = self.x[:n].cpu().numpy()
+        k = self.k[:n].cpu().numpy()
+        s = self.s[:n].cpu().numpy()
+        w = self.w[:n].cpu().numpy() if self.w is not None else s.astype(x.dtype)
+        return x, k, s, w, pid
+
+    def grid_counts(self):
+        return self.grid.view(self.nx, self.nk).cpu().numpy()
+
+    def event_log(self):
+        c = self.counters()
+        n = min(c["log_len"], self.bufs.event_log_capacity)
+        if self.log is None or n == 0:
+            return np.zeros(0, EVENT_DTYPE)
+        raw = self.log[: n * EVENT_DTYPE.itemsize].cpu().numpy()
+        return raw.view(EVENT_DTYPE).copy()
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            wbrw_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
