@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Benchmark of the signed-particle WBRW hot path on GB300.
+
+One bench step is one resampling period of the workload: regenerate the
+particles from the histogram (Alg. 3), stream and branch them through
+`resample_every` intervals (Alg. 1), and resample (sp1 annihilation or the sp2
+signed bootstrap).  The default workload is the 2D Gaussian barrier at scale:
+1e8 particles, FP32 state, 1200 x 512 cells, dt = 0.05, resampling every 10
+intervals; 10 warm-up + 30 timed periods cover its 400 intervals.
+
+metric: signed-particle steps per second including annihilation, i.e. the sum
+over intervals of the particles alive at the start of the interval, divided
+by the device time of all flight and resampling work.
+
+`--impl reference` times the plain FP64 CPU oracle on the host instead,
+on a bounded sample of the same workload.
+Multi-GPU (`torchrun`): independent replicas, one per GPU, different seeds.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "signed-particle steps/s incl. annihilation (2D, 4D); batched+grad vs plain"
+UNIT = "particle-steps/s"
+L2_FLUSH_BYTES = 512 << 20      # > 129 MB of L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2"])
+    ap.add_argument("--workload", default="gauss2d_fp32_n1e8",
+                    choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5"])
+    ap.add_argument("--particles", type=float, default=0,
+                    help="override the particle count (profiling small cases)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    base = (workloads.GAUSS_2D_FP32_1E8 if args.workload == "gauss2d_fp32_n1e8"
+            else workloads.GAUSS_2D_FP64_2E5)
+    wl = workloads.scaled(base, strategy=args.strategy)
+    if args.particles:
+        wl["n_alpha"] = int(args.particles)
+    return wl
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.gpu = gpu_index
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host: CPU baseline and the reference arm
+# ---------------------------------------------------------------------------
+def oracle_period_rate(wl, n_sample, budget_s, max_periods=None):
+    """Time the FP64 oracle, as it stands, on a sample of the workload:
+    n_sample initial particles, full periods until budget_s has elapsed."""
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(hbar=wl["hbar"], mass=wl["mass"], dt=wl["dt"], gamma0=wl["gamma0"],
+                      H=wl["H"], w=wl["w"], xc=wl["xc"], nx=wl["nx"], nk=wl["nk"],
+                      xmin=wl["xmin"], xmax=wl["xmax"], kmin=wl["kmin"], kmax=wl["kmax"],
+                      strategy=oracle.SP1 if wl["strategy"] == "sp1" else oracle.SP2,
+                      n_alpha=n_sample, seed=wl["seed"])
+    o.init_gauss(n_sample, wl["x0"], wl["sigma_x"], wl["k0"])
+    times, psteps = [], []
+    t_all = time.perf_counter()
+    while True:
+        p0 = o.ledger()["particle_steps"]
+        t0 = time.perf_counter()
+        o.step(wl["resample_every"])
+        o.annihilate()
+        times.append(time.perf_counter() - t0)
+        psteps.append(o.ledger()["particle_steps"] - p0)
+        if time.perf_counter() - t_all > budget_s or (max_periods and len(times) >= max_periods):
+            break
+    return times, psteps
+
+
+def reference_arm(args, wl):
+    ws, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    n_sample = 200_000
+    times, psteps = oracle_period_rate(wl, n_sample, budget_s=1e9,
+                                       max_periods=args.warmup + args.steps)
+    t = sum(times[args.warmup:])
+    ps = sum(psteps[args.warmup:])
+    value = ps / t if t > 0 else 0.0
+    sample = ("%d-particle sample (of %d) of the same workload, %d-interval periods "
+              "incl. annihilation, FP64 oracle, single thread"
+              % (n_sample, int(wl["n_alpha"]), wl["resample_every"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(wl, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, args):
+    return {"workload": wl["name"], "particles": int(wl["n_alpha"]),
+            "grid": [wl["nx"], wl["nk"]], "dt": wl["dt"],
+            "intervals_per_step": wl["resample_every"], "strategy": wl["strategy"],
+            "precision": wl["precision"], "potential": "gaussian H=%g w=%g" % (wl["H"], wl["w"]),
+            "l2": "flushed (512 MiB write) between timed steps",
+            "parallelism": "replicas x%d" % args.gpus}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def ours(args, wl):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1709_02121_gb300 import build
+    build.build()
+    from paper_1709_02121_gb300 import Simulation, wbrw
+
+    wl = workloads.scaled(wl, seed=wl["seed"] + rank)
+    n = int(wl["n_alpha"])
+    cap = int(4.0 * n) + (1 << 20)
+    sim = Simulation(wl, capacity=cap)
+    stream = sim.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P = wl["resample_every"]
+    for _ in range(args.warmup):
+        sim.run(P)
+    barrier()
+
+    c0 = sim.counters()
+    wbrw.wbrw_profile(sim.ctx, True)
+    clocks = Clocks(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i)  # evict the histogram and plan from L2
+        starts[i].record(stream)
+        sim.run(P)
+        ends[i].record(stream)
+    barrier()
+    clk = clocks.stop()
+    kern_ms, kern_n = wbrw.wbrw_profile_read(sim.ctx)
+    wbrw.wbrw_profile(sim.ctx, False)
+    c1 = sim.counters()
+    t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    psteps = c1["particle_steps"] - c0["particle_steps"]
+    psteps_first = c1["particle_steps_first"] - c0["particle_steps_first"]
+    launches = c1["launches"] - c0["launches"]
+
+    # ---- end to end: host checkpoint in, one period, checkpoint + observables out
+    e2e = None
+    if not args.no_e2e:
+        grid_h = torch.empty((wl["nx"], wl["nk"]), dtype=torch.int32).pin_memory()
+        g0, step0, epoch0 = sim.checkpoint(grid_h.numpy())
+        e2e_steps = min(args.steps, 10)
+        barrier()
+        pe0 = sim.counters()["particle_steps"]
+        t0 = time.perf_counter()
+        T_last = None
+        for i in range(e2e_steps):
+            sim.restore(grid_h.numpy(), step0 if i == 0 else step, epoch0 if i == 0 else epoch)
+            sim.run(P)
+            _, step, epoch = sim.checkpoint(grid_h.numpy())
+            _, _, T_last, _ = wbrw.wbrw_density(sim.ctx, wl["nx"], wl["nk"])
+        te = time.perf_counter() - t0
+        pe = sim.counters()["particle_steps"] - pe0
+        e2e = {"value": pe / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(wl["nx"] * wl["nk"] * 4),
+               "d2h_bytes_per_step": int(wl["nx"] * wl["nk"] * 4 + wl["nx"] * wl["nk"] * 8
+                                         + wl["nx"] * 8 + 16),
+               "steps": e2e_steps, "transmission_last": T_last}
+
+    # ---- reduce over ranks
+    t_max = t_ms
+    ps_all = psteps
+    if ws > 1:
+        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        pp = torch.tensor([psteps], dtype=torch.float64, device="cuda")
+        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+        ps_all = float(pp.item())
+        if e2e is not None:
+            ev = torch.tensor([e2e["value"]], dtype=torch.float64, device="cuda")
+            dist.all_reduce(ev, op=dist.ReduceOp.SUM)
+            e2e["value"] = float(ev.item())
+
+    if rank == 0:
+        value = ps_all / (t_max / 1e3)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        roof = roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if wl["precision"] == "fp32" else "f64",
+                "data": "synthetic", "config": config_of(wl, args),
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "clocks": clk,
+                "live_particles_end": c1["live"],
+                "particle_steps": psteps}
+        if not args.no_cpu_baseline and ws == 1:
+            times, pst = oracle_period_rate(wl, 1_000_000 if n >= 1_000_000 else n, budget_s=15.0)
+            line["cpu_baseline"] = {
+                "value": sum(pst) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d of the %d particles, %d full %d-interval periods incl. "
+                          "annihilation, FP64 oracle, single thread"
+                          % (min(n, 1_000_000), n, len(times), P)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    sim.close()
+
+
+def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
+    """The dominant kernel is the fused regenerate + flight + histogram pass
+    that carries the particles present at the start of each period (the first
+    wave).  Its work is lane arithmetic: the particle state stays in registers
+    and HBM is touched only for the offspring queue.  Achieved = algorithmic
+    lane-operations per launch (OPS_PER_PSTEP, derived in the design doc, times the
+    first-wave particle-steps of one launch) / the launch's average CUDA-event
+    duration.  Peak = 152 SMs x 128 lanes x the median SM clock sampled during
+    the timed region (one lane-operation per lane per cycle)."""
+    if not kern_n or kern_ms <= 0:
+        return None
+    ops = OPS_PER_PSTEP[wl["precision"]]
+    per_launch_ms = kern_ms / kern_n
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+    ach = ops * (psteps_first / kern_n) / (per_launch_ms / 1e3) / 1e12
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlane-op/s",
+            "frac": ach / peak, "traffic": None,
+            "kernel": "k_flight<%s,regen,bin>" % wl["precision"],
+            "launch_ms": per_launch_ms, "launches": kern_n,
+            "first_wave_particle_steps_per_launch": psteps_first / kern_n,
+            "ops_per_particle_step": ops,
+            "peak_basis": "152 SM x 128 lanes x %.0f MHz (median SM clock sampled in the "
+                          "timed region)" % sm_mhz}
+
+
+# algorithmic lane-operations per first-wave particle-step
+OPS_PER_PSTEP = {"fp32": 71.0, "fp64": 150.0}
+
+
+def main():
+    args = parse()
+    wl = workload(args)
+    if args.impl == "reference":
+        reference_arm(args, wl)
+    else:
+        ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

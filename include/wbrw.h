@@ -136,6 +136,8 @@ enum {
   WBRW_C_BOOT_WMINUS = 16,
   WBRW_C_NONZERO_CELLS = 17,
   WBRW_C_ERROR = 18,      /* device error word                               */
+  WBRW_C_PARTICLE_STEPS_FIRST = 19, /* the part carried by the first wave of  */
+                                    /* each chunk (particles present at its start) */
   WBRW_C_COUNT = 24
 };
 
@@ -192,6 +194,34 @@ wbrw_status wbrw_density(wbrw_ctx* ctx, double* density_host,
  * Synchronises the stream. */
 wbrw_status wbrw_particles(wbrw_ctx* ctx, long long* n_host,
                            unsigned long long* pid_dev);
+
+/* Checkpoint.  The histogram is the whole state of the method between two
+ * periods (the pipeline of Sec. 4).  Right after a
+ * resampling, copy the signed counts c_nu (nx*nk int32, x-major) to grid_out,
+ * which may be host or device memory, and return the interval index and the
+ * number of resamplings so far.  Returns WBRW_ERR_STATE if the particles have
+ * moved since the last resampling.  Synchronises the stream. */
+wbrw_status wbrw_checkpoint(wbrw_ctx* ctx, int* grid_out, long long* step,
+                            long long* epoch);
+
+/* Resume from a checkpoint: load the counts c_nu (host or device memory,
+ * nx*nk int32), the interval index and the resampling count.  The particle
+ * set becomes the regeneration of that histogram by Alg. 3, so a resumed run
+ * is bit-identical to the uninterrupted one.  Ledger counters are kept.
+ * Async. */
+wbrw_status wbrw_restore(wbrw_ctx* ctx, const int* grid, long long step,
+                         long long epoch);
+
+/* Timing of the flight kernel that carries the particles present at the
+ * start of each chunk of intervals.  This is the first wave of every chunk,
+ * and in wbrw_run it is the fused regeneration + flight + histogram pass.
+ * While enabled, each such launch is bracketed by CUDA events on the
+ * context's stream (at most 4096 launches are kept).  wbrw_profile_read
+ * synchronises and returns the summed milliseconds and the launch count since
+ * the last read or enable. */
+wbrw_status wbrw_profile(wbrw_ctx* ctx, int enable);
+wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
+                              long long* launches);
 
 /* Copy the counters (WBRW_C_*) to out[0..WBRW_C_COUNT).  Synchronises. */
 wbrw_status wbrw_counters(wbrw_ctx* ctx, long long* out);

@@ -177,6 +177,18 @@ wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
 
 }  // namespace
 
+namespace wbrw {
+void prof_begin(Ctx* c) {
+  if (!c->prof_on || c->prof_n >= 4096) return;
+  cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+}
+void prof_end(Ctx* c) {
+  if (!c->prof_on || c->prof_n >= 4096) return;
+  cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+  c->prof_n += 1;
+}
+}  // namespace wbrw
+
 extern "C" {
 
 size_t wbrw_scratch_bytes(const wbrw_config* config, long long capacity) {
@@ -411,7 +423,8 @@ wbrw_status wbrw_counters(wbrw_ctx* c, long long* out) {
   out[WBRW_C_KILL_MINUS] = (long long)h.ledger[LG_KILL_M];
   out[WBRW_C_OUT_PLUS] = (long long)h.ledger[LG_OUT_P];
   out[WBRW_C_OUT_MINUS] = (long long)h.ledger[LG_OUT_M];
-  out[WBRW_C_PARTICLE_STEPS] = (long long)h.ledger[LG_PSTEPS];
+  out[WBRW_C_PARTICLE_STEPS] = (long long)(h.ledger[LG_PSTEPS] + h.ledger[LG_PSTEPS0]);
+  out[WBRW_C_PARTICLE_STEPS_FIRST] = (long long)h.ledger[LG_PSTEPS0];
   out[WBRW_C_LOG_LEN] = (long long)h.log_len;
   out[WBRW_C_STEP] = c->step;
   out[WBRW_C_EPOCH] = c->epoch;
@@ -439,6 +452,66 @@ const char* wbrw_last_error(const wbrw_ctx* c) {
   return c->err;
 }
 
-void wbrw_destroy(wbrw_ctx* c) { delete c; }
+wbrw_status wbrw_checkpoint(wbrw_ctx* c, int* grid_out, long long* step, long long* epoch) {
+  if (!c || !grid_out) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (!c->fresh) return seterr(c, WBRW_ERR_STATE, "checkpoint needs a resampling first");
+  WBRW_TRY(c, cudaMemcpyAsync(grid_out, c->buf.grid, (size_t)c->nh * 4, cudaMemcpyDefault,
+                              c->stream), "copy grid");
+  wbrw_status st = device_status(c);
+  if (st != WBRW_OK) return st;
+  if (step) *step = c->step;
+  if (epoch) *epoch = c->epoch;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_restore(wbrw_ctx* c, const int* grid, long long step, long long epoch) {
+  if (!c || !grid) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (step < 0 || step >= (1ll << 31) || epoch < 0 || epoch >= (1ll << 23))
+    return seterr(c, WBRW_ERR_ARG, "step or epoch out of range");
+  WBRW_TRY(c, cudaMemcpyAsync(c->buf.grid, grid, (size_t)c->nh * 4, cudaMemcpyDefault,
+                              c->stream), "copy grid");
+  WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+  c->step = step;
+  c->epoch = epoch;
+  c->state = ST_HISTOGRAM;
+  c->fresh = 1;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_profile(wbrw_ctx* c, int enable) {
+  if (!c) return WBRW_ERR_ARG;
+  if (enable && !c->prof_created) {
+    for (int i = 0; i < 2 * 4096; ++i)
+      WBRW_TRY(c, cudaEventCreate(&c->prof_ev[i]), "create events");
+    c->prof_created = 1;
+  }
+  c->prof_on = enable ? 1 : 0;
+  c->prof_n = 0;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_profile_read(wbrw_ctx* c, double* total_ms, long long* launches) {
+  if (!c) return WBRW_ERR_ARG;
+  WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  double t = 0;
+  for (int i = 0; i < c->prof_n; ++i) {
+    float ms = 0;
+    WBRW_TRY(c, cudaEventElapsedTime(&ms, c->prof_ev[2 * i], c->prof_ev[2 * i + 1]), "elapsed");
+    t += ms;
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = c->prof_n;
+  c->prof_n = 0;
+  return WBRW_OK;
+}
+
+void wbrw_destroy(wbrw_ctx* c) {
+  if (!c) return;
+  if (c->prof_created)
+    for (int i = 0; i < 2 * 4096; ++i) cudaEventDestroy(c->prof_ev[i]);
+  delete c;
+}
 
 }  // extern "C"

@@ -113,6 +113,9 @@ struct EEntry {  // candidate intervals that did not fit the block's list
   unsigned mask;  // bit b: candidate in interval l0 + b
 };
 
+static_assert(sizeof(FEntry<double>) == 40 && sizeof(FEntry<float>) == 24, "FEntry layout");
+static_assert(sizeof(EEntry<double>) == 40 && sizeof(EEntry<float>) == 32, "EEntry layout");
+
 // Kernel parameters (by value, parameter space).
 template <class P>
 struct KP {
@@ -781,7 +784,7 @@ __global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
   }
 
   // ---- tallies ------------------------------------------------------------
-  block_reduce_add<T>(sm, acc.psteps, &p.cnt->ledger[LG_PSTEPS]);
+  block_reduce_add<T>(sm, acc.psteps, &p.cnt->ledger[SRC == SRC_QUEUE ? LG_PSTEPS : LG_PSTEPS0]);
   block_reduce_add<T>(sm, acc.events, &p.cnt->ledger[LG_EVENTS]);
   block_reduce_add<T>(sm, acc.kill_p, &p.cnt->ledger[LG_KILL_P]);
   block_reduce_add<T>(sm, acc.kill_m, &p.cnt->ledger[LG_KILL_M]);
@@ -1032,7 +1035,9 @@ struct DriverImpl {
       p.round = r;
       p.fq_in = (FEntry<typename P::T>*)c->fq[r & 1];
       p.fq_out = (FEntry<typename P::T>*)c->fq[(r + 1) & 1];
+      if (r == 0) prof_begin(c);
       e = flight_any<P>(c, p, r == 0 ? src : (int)SRC_QUEUE, dst);
+      if (r == 0) prof_end(c);
       if (e != cudaSuccess) return e;
       if (L > l0) {
         e = events_any<P>(c, p, dst);

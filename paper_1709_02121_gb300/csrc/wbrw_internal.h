@@ -27,7 +27,7 @@ enum : int {
 };
 
 // ledger slots (Counters::ledger)
-enum { LG_EVENTS = 0, LG_KILL_P, LG_KILL_M, LG_OUT_P, LG_OUT_M, LG_PSTEPS, LG_N = 8 };
+enum { LG_EVENTS = 0, LG_KILL_P, LG_KILL_M, LG_OUT_P, LG_OUT_M, LG_PSTEPS, LG_PSTEPS0, LG_N = 8 };
 
 // Device-resident counters: every count the host would otherwise need lives
 // here, so no launch waits for the host.
@@ -90,12 +90,21 @@ struct Ctx {
   int fresh;
   int failed;
   long long launches;
+  // CUDA-event timing of the first flight wave of each chunk
+  int prof_on;
+  int prof_n;
+  cudaEvent_t prof_ev[2 * 4096];
+  int prof_created;
   char err[512];
 };
 
 enum { ST_PARTICLES = 0, ST_HISTOGRAM = 1 };
 
 // Per-precision drivers (wbrw_fp64.cu / wbrw_fp32.cu).
+// Event pair around a profiled launch (no-ops while profiling is off).
+void prof_begin(Ctx*);
+void prof_end(Ctx*);
+
 struct Driver {
   cudaError_t (*init)(Ctx*, long long n, double x0, double sx, double k0);
   // Fly [l0, L) from the source, offspring in waves, finals to dst.

@@ -26,11 +26,12 @@ POT_GAUSSIAN = 0
 COUNTERS = ("live", "events", "kill_plus", "kill_minus", "out_plus", "out_minus",
             "particle_steps", "log_len", "step", "epoch", "launches",
             "boot_nplus", "boot_nminus", "boot_nrplus", "boot_nrminus",
-            "boot_wplus", "boot_wminus", "nonzero_cells", "error")
+            "boot_wplus", "boot_wminus", "nonzero_cells", "error", "particle_steps_first")
 C_COUNT = 24
 
 SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
-           "wbrw_run", "wbrw_density", "wbrw_particles", "wbrw_counters",
+           "wbrw_run", "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
+           "wbrw_restore", "wbrw_profile", "wbrw_profile_read", "wbrw_counters",
            "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy")
 
 
@@ -93,9 +94,14 @@ def load(path: str = LIB_PATH):
                             ctypes.c_double, ctypes.c_double, P,
                             ctypes.POINTER(P)]
     for name in ("wbrw_init", "wbrw_step", "wbrw_annihilate", "wbrw_run",
-                 "wbrw_density", "wbrw_particles", "wbrw_counters",
-                 "wbrw_sync_status"):
+                 "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
+                 "wbrw_restore", "wbrw_profile", "wbrw_profile_read",
+                 "wbrw_counters", "wbrw_sync_status"):
         getattr(L, name).restype = I
+    L.wbrw_checkpoint.argtypes = [P, P, P, P]
+    L.wbrw_restore.argtypes = [P, P, LL, LL]
+    L.wbrw_profile.argtypes = [P, I]
+    L.wbrw_profile_read.argtypes = [P, P, P]
     L.wbrw_step.argtypes = [P, I]
     L.wbrw_annihilate.argtypes = [P]
     L.wbrw_run.argtypes = [P, I]
@@ -159,6 +165,29 @@ def wbrw_particles(ctx, pid_dev_ptr=None):
     _check(ctx, load().wbrw_particles(ctx, ctypes.byref(n),
                                       ctypes.c_void_p(pid_dev_ptr) if pid_dev_ptr else None))
     return n.value
+
+
+def wbrw_checkpoint(ctx, grid_out_ptr):
+    step = ctypes.c_longlong()
+    epoch = ctypes.c_longlong()
+    _check(ctx, load().wbrw_checkpoint(ctx, ctypes.c_void_p(grid_out_ptr), ctypes.byref(step),
+                                       ctypes.byref(epoch)))
+    return step.value, epoch.value
+
+
+def wbrw_restore(ctx, grid_ptr, step, epoch):
+    _check(ctx, load().wbrw_restore(ctx, ctypes.c_void_p(grid_ptr), step, epoch))
+
+
+def wbrw_profile(ctx, enable=True):
+    _check(ctx, load().wbrw_profile(ctx, 1 if enable else 0))
+
+
+def wbrw_profile_read(ctx):
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(ctx, load().wbrw_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
 
 
 def wbrw_counters(ctx):
@@ -237,6 +266,24 @@ class Simulation:
 
     def counters(self):
         return wbrw_counters(self.ctx)
+
+    def checkpoint(self, grid_out=None):
+        """Copy the histogram into grid_out (host or device int32 array-like
+        with a data pointer; a new host array if None); returns (grid, step, epoch)."""
+        if grid_out is None:
+            grid_out = np.empty((self.nx, self.nk), np.int32)
+        ptr = grid_out.ctypes.data if isinstance(grid_out, np.ndarray) else grid_out.data_ptr()
+        step, epoch = wbrw_checkpoint(self.ctx, ptr)
+        return grid_out, step, epoch
+
+    def restore(self, grid, step, epoch):
+        if isinstance(grid, np.ndarray):
+            grid = np.ascontiguousarray(grid, np.int32)
+            self._restore_keep = grid
+            ptr = grid.ctypes.data
+        else:
+            ptr = grid.data_ptr()
+        wbrw_restore(self.ctx, ptr, step, epoch)
 
     def particles(self, with_pids=True):
         """(x, k, s, w, pid) of the current particles as host numpy arrays."""

@@ -266,3 +266,30 @@ def test_runs_are_deterministic():
     b.run(20)
     assert np.array_equal(a.grid_counts(), b.grid_counts())
     assert a.counters()["events"] == b.counters()["events"]
+
+
+def test_checkpoint_restore_is_bit_identical():
+    wl = small(resample_every=5)
+    a, b = sim_of(wl), sim_of(wl)
+    a.run(10)
+    grid, step, epoch = a.checkpoint()
+    assert step == 10 and epoch == 2
+    a.run(10)
+    b.restore(grid, step, epoch)      # host memory
+    b.run(10)
+    assert np.array_equal(a.grid_counts(), b.grid_counts())
+    # from device memory, then the particles themselves
+    import torch
+    c = sim_of(wl)
+    c.restore(torch.from_numpy(grid.copy()).cuda(), step, epoch)
+    c.run(3)
+    a2 = sim_of(wl)
+    a2.run(13)
+    xa, ka, _, _, pa = a2.particles()
+    xc, kc, _, _, pc = c.particles()
+    ia, ic = np.argsort(pa), np.argsort(pc)
+    assert np.array_equal(pa[ia], pc[ic]) and np.array_equal(xa[ia], xc[ic])
+    # a checkpoint between resamplings is refused
+    from paper_1709_02121_gb300 import WbrwError
+    with pytest.raises(WbrwError):
+        c.checkpoint()
