@@ -223,6 +223,34 @@ wbrw_status wbrw_profile(wbrw_ctx* ctx, int enable);
 wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
                               long long* launches);
 
+/* Observables of a signed histogram without any allocation and without a
+ * context.  The paper has no counterpart: this is an interface for callers
+ * that cannot call cudaMalloc, such as code running inside a fixed device
+ * memory pool owned by someone else, or a host process that is not allowed to
+ * grow the device footprint after start-up.  Such callers cannot hand the
+ * library a scratch buffer on every call.  It computes what wbrw_density
+ * computes from a histogram (density c_nu/(N_alpha dx dk), x-marginal, and
+ * the transmission over cells with centre x > 0) for the counts `grid`
+ * (nx*nk int32, x-major, device memory).  Outputs are device memory owned by
+ * the caller: density (nx*nk doubles, or NULL), marginal_x (nx doubles) and
+ * transmission (1 double).  Work is enqueued on cuda_stream; nothing waits.
+ *
+ * Its only scratch, the per-column sums, lives in a static device array of
+ * WBRW_STATIC_MAX_NX int64 entries (512 KiB) that every GPU loading the
+ * library keeps until the process exits.  nx above that maximum is refused
+ * with WBRW_ERR_CAPACITY; invalid arguments give WBRW_ERR_ARG.  The first
+ * call on each device looks up the array's device address on that device
+ * (make that first call before any stream capture).  All calls share the
+ * array: calls whose GPU work overlaps (other streams, other threads) race
+ * and must be serialised by the caller.  Each call overwrites every entry it
+ * reads, so nothing needs clearing between calls. */
+#define WBRW_STATIC_MAX_NX 65536
+wbrw_status wbrw_observables_static(const int* grid, int nx, int nk,
+                                    double xmin, double xmax, double kmin,
+                                    double kmax, long long n_alpha,
+                                    double* density, double* marginal_x,
+                                    double* transmission, void* cuda_stream);
+
 /* Copy the counters (WBRW_C_*) to out[0..WBRW_C_COUNT).  Synchronises. */
 wbrw_status wbrw_counters(wbrw_ctx* ctx, long long* out);
 

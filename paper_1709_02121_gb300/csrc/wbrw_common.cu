@@ -442,3 +442,55 @@ cudaError_t launch_observables(Ctx* c, const int* counts, const long long* wsum)
 }
 
 }  // namespace wbrw
+
+// ---------------------------------------------------------------------------
+// Allocation-free observables (wbrw_observables_static in include/wbrw.h).
+// For callers that cannot call cudaMalloc: the per-column scratch of the
+// observables kernels is a file-scope device array of fixed size, looked up
+// once per device with cudaGetSymbolAddress.  Host code must never pass the
+// array's name itself to a kernel: on the host it names a stand-in, not the
+// device copy.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+constexpr int kStaticMaxDevices = 64;
+static __device__ __align__(256) long long g_obs_col_static[WBRW_STATIC_MAX_NX];
+std::mutex g_static_mu;
+long long* g_static_col[kStaticMaxDevices];  // device address, per device
+}  // namespace
+
+extern "C" wbrw_status wbrw_observables_static(const int* grid, int nx, int nk, double xmin,
+                                               double xmax, double kmin, double kmax,
+                                               long long n_alpha, double* density,
+                                               double* marginal_x, double* transmission,
+                                               void* cuda_stream) {
+  if (!grid || !marginal_x || !transmission || nx <= 0 || nk <= 0 || n_alpha <= 0 ||
+      !(xmax > xmin) || !(kmax > kmin) || (long long)nx * (long long)nk >= (1ll << 31))
+    return WBRW_ERR_ARG;
+  if (nx > WBRW_STATIC_MAX_NX) return WBRW_ERR_CAPACITY;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
+    return WBRW_ERR_CUDA;
+  long long* col = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_col[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_obs_col_static) != cudaSuccess || !ptr)
+        return WBRW_ERR_CUDA;
+      g_static_col[dev] = (long long*)ptr;
+    }
+    col = g_static_col[dev];
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const double na = (double)n_alpha;
+  const double dx = (xmax - xmin) / (double)nx, dk = (kmax - kmin) / (double)nk;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return WBRW_ERR_CUDA;
+  wbrw::k_obs_cols<<<4 * sms, wbrw::kBlock, 0, s>>>(grid, nullptr, nx, nk, na, dx, dk, density,
+                                                    marginal_x, col);
+  wbrw::k_obs_total<<<1, wbrw::kBlock, 0, s>>>(col, nx, xmin, dx, na, 1.0, transmission);
+  return cudaGetLastError() == cudaSuccess ? WBRW_OK : WBRW_ERR_CUDA;
+}

@@ -32,7 +32,8 @@ C_COUNT = 24
 SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_run", "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
            "wbrw_restore", "wbrw_profile", "wbrw_profile_read", "wbrw_counters",
-           "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy")
+           "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy",
+           "wbrw_observables_static")
 
 
 class Config(ctypes.Structure):
@@ -113,6 +114,9 @@ def load(path: str = LIB_PATH):
     L.wbrw_last_error.restype = ctypes.c_char_p
     L.wbrw_destroy.argtypes = [P]
     L.wbrw_destroy.restype = None
+    D = ctypes.c_double
+    L.wbrw_observables_static.argtypes = [P, I, I, D, D, D, D, LL, P, P, P, P]
+    L.wbrw_observables_static.restype = I
     _lib = L
     return L
 
@@ -202,6 +206,16 @@ def wbrw_sync_status(ctx):
 
 def wbrw_last_error(ctx):
     return load().wbrw_last_error(ctx).decode()
+
+
+def wbrw_observables_static(grid_ptr, nx, nk, xmin, xmax, kmin, kmax, n_alpha,
+                            density_ptr, marginal_ptr, transmission_ptr, stream_ptr):
+    """Allocation-free observables of a device histogram (device outputs)."""
+    return load().wbrw_observables_static(
+        ctypes.c_void_p(grid_ptr), nx, nk, xmin, xmax, kmin, kmax, n_alpha,
+        ctypes.c_void_p(density_ptr) if density_ptr else None,
+        ctypes.c_void_p(marginal_ptr), ctypes.c_void_p(transmission_ptr),
+        ctypes.c_void_p(stream_ptr))
 
 
 def wbrw_destroy(ctx):
