@@ -25,16 +25,14 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 size_t elem_size(int precision) { return precision == WBRW_FP64 ? 8 : 4; }
 
-// F-queue entry {u64 pid; T x, k, w; int l;} and E-queue entry
-// {u64 pid; T x, k, w; int ls; unsigned mask;} as laid out by the device code.
+// Queue entry {u64 pid; T x, k, w; int l;} as laid out by the device code.
 size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
-size_t eentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 32; }
 
 struct Layout {
-  size_t counters, cpid, fq0, fq1, eq, nz_cell, nz_start, scan_bsum, scan_bnz,
+  size_t counters, cpid, fq0, fq1, eq, nz_cell, nz_start, tile_nz, scan_bsum, scan_bnz,
       tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
       rec_a, keep0, keep1, res0, res1, total;
-  long long qcap, ecap, rec_cap, scan_blocks;
+  long long qcap, ecap, rec_cap, scan_blocks, tile_cap;
 };
 
 bool config_ok(const wbrw_config* c, char* why, size_t n) {
@@ -58,9 +56,11 @@ bool config_ok(const wbrw_config* c, char* why, size_t n) {
 Layout layout(const wbrw_config* c, long long capacity) {
   Layout L;
   const long long nh = (long long)c->nx * c->nk;
-  L.qcap = capacity;
-  L.ecap = capacity / 16 + 4096;
-  L.rec_cap = c->strategy == WBRW_SP2_BOOTSTRAP ? 4 * capacity : 0;
+  // offspring queues and sp2 records are split into kSeg equal segments
+  L.qcap = ((capacity + kSeg - 1) / kSeg) * kSeg;
+  L.tile_cap = capacity / 32 + 2;
+  L.ecap = 2 * L.qcap;  // about one candidate interval per particle per flight
+  L.rec_cap = c->strategy == WBRW_SP2_BOOTSTRAP ? 4 * L.qcap : 0;
   L.scan_blocks = (nh + kScanTile - 1) / kScanTile;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -72,9 +72,10 @@ Layout layout(const wbrw_config* c, long long capacity) {
   L.cpid = take((size_t)capacity * 8);
   L.fq0 = take((size_t)L.qcap * fentry_size(c->precision));
   L.fq1 = take((size_t)L.qcap * fentry_size(c->precision));
-  L.eq = take((size_t)L.ecap * eentry_size(c->precision));
+  L.eq = take((size_t)L.ecap * fentry_size(c->precision));
   L.nz_cell = take((size_t)nh * 4);
   L.nz_start = take((size_t)nh * 8);
+  L.tile_nz = take((size_t)L.tile_cap * 4);
   L.scan_bsum = take((size_t)(L.scan_blocks + 1) * 8);
   L.scan_bnz = take((size_t)(L.scan_blocks + 1) * 4);
   L.tmp_grid = take((size_t)nh * 4);
@@ -166,7 +167,7 @@ wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
   wbrw_status st = ensure_particles(c);
   if (st != WBRW_OK) return st;
   while (nsteps > 0) {
-    const int ch = nsteps < kMaxChunk ? nsteps : kMaxChunk;
+    const int ch = nsteps < c->max_chunk ? nsteps : c->max_chunk;
     WBRW_TRY(c, drv(c)->chunk(c, (int)c->step, (int)c->step + ch, SRC_ARRAY, DST_ARRAY), "step");
     c->step += ch;
     nsteps -= ch;
@@ -237,6 +238,11 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
   c->hm = config->hbar / config->mass;
   c->dtv = config->dt * c->hm;
   c->p_any = -expm1(-gamma0 * config->dt);
+  // flights short enough that a particle expects at most one candidate
+  // interval, so the candidate queue (two entries per particle) holds them
+  c->max_chunk = c->p_any > 0 ? (int)floor(1.0 / c->p_any) : kMaxChunk;
+  if (c->max_chunk > kMaxChunk) c->max_chunk = kMaxChunk;
+  if (c->max_chunk < 1) c->max_chunk = 1;
   c->dx = (config->xmax - config->xmin) / (double)config->nx;
   c->dk = (config->kmax - config->kmin) / (double)config->nk;
   c->inv_dx = (double)config->nx / (config->xmax - config->xmin);
@@ -258,6 +264,8 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
   c->ecap = L.ecap;
   c->nz_cell = (uint32_t*)(base + L.nz_cell);
   c->nz_start = (unsigned long long*)(base + L.nz_start);
+  c->tile_nz = (uint32_t*)(base + L.tile_nz);
+  c->tile_cap = L.tile_cap;
   c->scan_bsum = (unsigned long long*)(base + L.scan_bsum);
   c->scan_bnz = (unsigned int*)(base + L.scan_bnz);
   c->scan_blocks = L.scan_blocks;
@@ -321,10 +329,10 @@ wbrw_status wbrw_run(wbrw_ctx* c, int nsteps) {
   if (T <= 0) return step_impl(c, nsteps);
   while (nsteps > 0) {
     const int to_boundary = T - (int)(c->step % T);
-    if (nsteps < to_boundary || to_boundary > kMaxChunk) {
+    if (nsteps < to_boundary || to_boundary > c->max_chunk) {
       // no resampling inside this piece: plain steps into the arrays
-      int ch = nsteps < to_boundary ? nsteps : to_boundary - kMaxChunk;
-      if (ch > kMaxChunk) ch = kMaxChunk;
+      int ch = nsteps < to_boundary ? nsteps : to_boundary - c->max_chunk;
+      if (ch > c->max_chunk) ch = c->max_chunk;
       wbrw_status st = step_impl(c, ch);
       if (st != WBRW_OK) return st;
       nsteps -= ch;

@@ -51,8 +51,10 @@ __global__ void k_setup(Counters* c, int op, unsigned long long a,
     case SETUP_CHUNK:
       c->n_src = c->n;
       for (int i = 0; i < kMaxChunk + 2; ++i) {
-        c->q[i] = 0;
-        c->e[i] = 0;
+        for (int s = 0; s < kSeg; ++s) {
+          c->qs[i][s] = 0;
+          c->es[i][s] = 0;
+        }
       }
       break;
     case SETUP_AFTER_REGEN:
@@ -66,7 +68,7 @@ __global__ void k_setup(Counters* c, int op, unsigned long long a,
       c->base_pid = 0;
       break;
     case SETUP_BOOT:
-      c->rec_len = 0;
+      for (int s = 0; s < kSeg; ++s) c->recs[s] = 0;
       for (int s = 0; s < 2; ++s) {
         c->boot_n[s] = c->boot_w[s] = c->boot_keep[s] = c->boot_nr[s] = 0;
         c->boot_R[s] = 0;
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(kBlock) k_cells_a(const int* grid, long long n
 
 __global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
                                                     unsigned int* bnz,
-                                                    long long nb, Counters* c) {
+                                                    long long nb, Counters* c,
+                                                    long long tile_cap) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   unsigned long long carry_s = 0, carry_z = 0;
   for (long long b0 = 0; b0 < nb; b0 += kBlock) {
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
   if (threadIdx.x == 0) {
     c->regen_total = carry_s;
     c->nz_count = carry_z;
+    if (carry_s > (unsigned long long)tile_cap * 32ull) atomicOr(&c->err, ERR_CAP_PARTICLES);
   }
 }
 
@@ -163,7 +167,8 @@ __global__ void __launch_bounds__(kBlock) k_cells_c(const int* grid, long long n
                                                     const unsigned long long* bsum,
                                                     const unsigned int* bnz,
                                                     uint32_t* nz_cell,
-                                                    unsigned long long* nz_start) {
+                                                    unsigned long long* nz_start,
+                                                    uint32_t* tile_nz, long long tile_cap) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
   int v[kScanItems];
@@ -181,10 +186,14 @@ __global__ void __launch_bounds__(kBlock) k_cells_c(const int* grid, long long n
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (v[i] != 0) {
+      const unsigned long long m = (unsigned long long)(v[i] < 0 ? -(long long)v[i] : (long long)v[i]);
       nz_cell[oz] = (uint32_t)(base + i) | (v[i] < 0 ? 0x80000000u : 0u);
       nz_start[oz] = os;
+      // every 32-slot tile whose first slot falls in this cell starts here
+      const unsigned long long t_end = min((os + m + 31) >> 5, (unsigned long long)tile_cap);
+      for (unsigned long long t = (os + 31) >> 5; t < t_end; ++t) tile_nz[t] = (uint32_t)oz;
       ++oz;
-      os += (unsigned long long)(v[i] < 0 ? -(long long)v[i] : (long long)v[i]);
+      os += m;
     }
   }
 }
@@ -245,22 +254,38 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 // a = floor(|w| 2^31); N^s and W^s = sum a were tallied with the records.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t* rec_cell,
-                                                     const uint32_t* rec_a, long long rec_cap,
+                                                     const uint32_t* rec_a, long long rseg,
                                                      int* keep0, int* keep1,
                                                      unsigned long long* res0,
                                                      unsigned long long* res1) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
-  const unsigned long long n = min(c->rec_len, (unsigned long long)rec_cap);
+  __shared__ unsigned long long pre[kSeg + 1];  // records are in kSeg segments
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int s = 0; s < kSeg; ++s) {
+      pre[s] = run;
+      run += min(c->recs[s], (unsigned long long)rseg);
+    }
+    pre[kSeg] = run;
+  }
+  __syncthreads();
+  const unsigned long long n = pre[kSeg];
   double ratio[2];
   for (int s = 0; s < 2; ++s)
     ratio[s] = c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
   unsigned long long ks[2] = {0, 0};
   for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * kBlock) {
-    const uint32_t rc = rec_cell[i];
+    int lo = 0, hi = kSeg - 1;  // segment of record i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (pre[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const long long ri = (long long)lo * rseg + (long long)(i - pre[lo]);
+    const uint32_t rc = rec_cell[ri];
     const int side = rc >> 31;
     const uint32_t cell = rc & 0x7FFFFFFFu;
-    const double q = __dmul_rn((double)rec_a[i], ratio[side]);
+    const double q = __dmul_rn((double)rec_a[ri], ratio[side]);
     const double fl = floor(q);
     const unsigned long long res =
         (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
@@ -399,9 +424,10 @@ cudaError_t launch_zero(Ctx* c, void* p, size_t bytes) {
 cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
   const long long nb = c->scan_blocks;
   k_cells_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz);
-  k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt);
+  k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt, c->tile_cap);
   k_cells_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz,
-                                                   c->nz_cell, c->nz_start);
+                                                   c->nz_cell, c->nz_start, c->tile_nz,
+                                                   c->tile_cap);
   c->launches += 3;
   return cudaGetLastError();
 }
@@ -412,7 +438,7 @@ cudaError_t launch_boot(Ctx* c) {
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
   const unsigned long long epoch = (unsigned long long)c->epoch;
   const int g = grid_cap(c, 8);
-  k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rec_cap,
+  k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rec_cap / kSeg,
                                           c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
                                           c->boot_res[1]);
   c->launches++;

@@ -8,17 +8,19 @@
 //           SRC_QUEUE  offspring waiting at the start of a later interval
 //   flight  free streaming x <- x + (hbar/m) k dt per interval (Eq. 1) and
 //           the candidate clock of constant rate gamma0 (Sec. 3.2)
-//   events  candidate intervals are queued per block in shared memory and
-//           processed block-cooperatively: the kick of Remark 3, the
+//   events  candidate intervals are queued per warp in shared memory and
+//           processed warp-cooperatively: the kick of Remark 3, the
 //           acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair of
 //           Alg. 1 item 3 and the offspring's own events in the same interval
 //   sink    DST_ARRAY  back to the arrays (offspring appended)
 //           DST_BIN1   signed histogram c_nu (Eq. signed_histogram)
 //           DST_BIN2   (cell, |w| in Q1.31) records for the sp2 bootstrap
 //           DST_WSUM   signed weights per cell in Q1.31 (observables)
-// Offspring that live into a later interval are staged in shared memory and
-// appended to a queue with one global atomic per block iteration.  The next
-// wave, a launch of the same kernel with SRC_QUEUE, carries them on.
+// Offspring that live into a later interval are staged in the warp's shared
+// memory and appended to one of kSeg queue segments with one atomic per warp
+// iteration.  The next wave, a launch of the same kernel with SRC_QUEUE,
+// carries them on.  No barrier is taken inside the main loop: each warp owns
+// its 32 slots per iteration.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,20 +34,25 @@ namespace wbrw {
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11), written from its definition.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2,
-                                        uint32_t c3, uint32_t k0, uint32_t k1) {
+// The key schedule is precomputed on the host (the keys of round r are
+// key + r * (0x9E3779B9, 0xBB67AE85)) and read from the kernel's parameter
+// space.
+struct KeySched {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ uint4 philox_ks(const KeySched& ks, uint32_t c0, uint32_t c1,
+                                           uint32_t c2, uint32_t c3) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
     const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t n0 = hi1 ^ c1 ^ k0;
-    const uint32_t n2 = hi0 ^ c3 ^ k1;
+    const uint32_t n0 = hi1 ^ c1 ^ ks.k0[r];
+    const uint32_t n2 = hi0 ^ c3 ^ ks.k1[r];
     c0 = n0;
     c1 = lo1;
     c2 = n2;
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   return make_uint4(c0, c1, c2, c3);
 }
@@ -105,16 +112,7 @@ struct FEntry {  // offspring waiting at the start of interval l
   int l;
 };
 
-template <class T>
-struct EEntry {  // candidate intervals that did not fit the block's list
-  unsigned long long pid;
-  T x, k, w;  // x at the start of interval ls
-  int ls;
-  unsigned mask;  // bit b: candidate in interval l0 + b
-};
-
 static_assert(sizeof(FEntry<double>) == 40 && sizeof(FEntry<float>) == 24, "FEntry layout");
-static_assert(sizeof(EEntry<double>) == 40 && sizeof(EEntry<float>) == 32, "EEntry layout");
 
 // Kernel parameters (by value, parameter space).
 template <class P>
@@ -126,8 +124,8 @@ struct KP {
   double p_hi;      // FP64: u0 < p_hi may start an event in the interval
   float p_any_f;    // FP32: P(candidate) per interval
   unsigned p16;     // FP32: floor(65536 p_any)
-  float p16_frac;   // FP32: 65536 p_any - p16
-  uint32_t key0, key1;
+  unsigned p16_frac8;  // FP32: floor(256 (65536 p_any - p16)), tie refinement
+  KeySched ks;      // Philox key schedule of the run seed
   int strategy;     // 1 = sp1, 2 = sp2
   int l0, L, round;
   unsigned long long regen_base;  // epoch << 40 of the histogram's particles
@@ -139,27 +137,28 @@ struct KP {
   unsigned long long* cpid;
   FEntry<T>* fq_in;
   FEntry<T>* fq_out;
-  long long qcap;
-  EEntry<T>* eq;
-  long long ecap;
+  long long qseg;   // entries per queue segment
+  FEntry<T>* eq;    // candidate intervals: x at the interval's start, l
+  long long eseg;   // entries per event-queue segment
   int* grid;
   long long* wsum;
   uint32_t* rec_cell;
   uint32_t* rec_a;
-  long long rec_cap;
+  long long rseg;   // records per record segment
   const uint32_t* nz_cell;
   const unsigned long long* nz_start;
+  const uint32_t* tile_nz;  // first nonzero cell of each 32-slot tile
+  long long tile_cap;
   Counters* cnt;
   wbrw_event* log;
   long long log_cap;
   int count_ledger;
 };
 
-constexpr int kItemCap = 768;   // candidate intervals per block iteration
-constexpr int kStageF = 320;    // staged offspring for the next wave
-constexpr int kStageOut = 192;  // staged offspring finals
-constexpr int kStack = 32;      // pending offspring frames per thread
-constexpr unsigned kNoItem = 0xFFFFFFFFu;
+constexpr int kWarps = kBlock / 32;
+constexpr int kWStage = 64;   // staged offspring per warp iteration
+constexpr int kStack = 32;    // pending offspring frames per thread
+constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Per-thread tallies, reduced once per block at the end of a kernel.
 struct Acc {
@@ -171,20 +170,12 @@ struct Acc {
   }
 };
 
+// Offspring staged by one warp of the event kernel before they are appended
+// to a queue segment with a single atomic.
 template <class T>
-struct Smem {
-  T x[kBlock], k[kBlock], w[kBlock];
-  unsigned long long pid[kBlock];
-  int ls[kBlock];
-  unsigned items[kItemCap];
-  FEntry<T> stage_f[kStageF];
-  FEntry<T> stage_out[kStageOut];
-  unsigned long long win_start[kBlock + 1];
-  uint32_t win_cell[kBlock + 1];
-  unsigned long long red[kBlock / 32];
-  unsigned long long base, total;
-  int nitems, nstage_f, nstage_out;
-  unsigned long long win_a;
+struct WarpStage {
+  FEntry<T> e[kWStage];
+  int n;
 };
 
 // ---------------------------------------------------------------------------
@@ -205,78 +196,81 @@ __device__ __forceinline__ bool cell_of(const KP<P>& p, typename P::T x,
   return true;
 }
 
-// Block-wide exclusive offset of `want` items per thread into a global
-// counter: one atomic per block.  Every thread of the block must call it.
-template <class T>
-__device__ unsigned long long block_append(Smem<T>& sm, unsigned want,
-                                           unsigned long long* counter,
-                                           unsigned long long& total_out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned v = want;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    unsigned t = __shfl_up_sync(0xFFFFFFFFu, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) sm.red[wid] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int i = 0; i < kBlock / 32; ++i) {
-      unsigned long long t = sm.red[i];
-      sm.red[i] = run;
-      run += t;
-    }
-    sm.base = run ? atomicAdd(counter, run) : 0ull;
-    sm.total = run;
-  }
-  __syncthreads();
-  const unsigned long long off = sm.base + sm.red[wid] + (v - want);
-  total_out = sm.total;
-  __syncthreads();
-  return off;
-}
-
-template <class T>
-__device__ void block_reduce_add(Smem<T>& sm, unsigned long long v,
+__device__ __forceinline__ void block_reduce_add(unsigned long long* red, unsigned long long v,
                                  unsigned long long* dst) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
   __syncthreads();
-  if (lane == 0) sm.red[wid] = v;
+  if (lane == 0) red[wid] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
-    for (int i = 0; i < kBlock / 32; ++i) t += sm.red[i];
+    for (int i = 0; i < kWarps; ++i) t += red[i];
     if (t) atomicAdd(dst, t);
   }
 }
 
+// Segment of the queues and record buffers a warp appends to: spreading the
+// appends over kSeg counters keeps any one counter's atomics rare.
+__device__ __forceinline__ int my_segment() {
+  return (int)((blockIdx.x * kWarps + (threadIdx.x >> 5)) & (kSeg - 1));
+}
+
+// Block-wide prefix of kSeg segment lengths (clamped to the segment size).
+__device__ __forceinline__ unsigned long long load_segments(unsigned long long* pre, const unsigned long long* len,
+                                            long long seg_cap) {
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int s = 0; s < kSeg; ++s) {
+      pre[s] = run;
+      run += min(len[s], (unsigned long long)seg_cap);
+    }
+    pre[kSeg] = run;
+  }
+  __syncthreads();
+  return pre[kSeg];
+}
+
+// Index in the segmented buffer of the i-th entry overall.
+__device__ __forceinline__ long long segmented_index(const unsigned long long* pre,
+                                                     unsigned long long i, long long seg_cap) {
+  int lo = 0, hi = kSeg - 1;  // last s with pre[s] <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return (long long)lo * seg_cap + (long long)(i - pre[lo]);
+}
+
 // ---------------------------------------------------------------------------
-// Per-precision draws of the parity contract
+// Per-precision draws.  A "segment" is a particle's part of interval l from
+// time `to` on (0 for a particle present at t_l, its birth time for an
+// offspring).  Draw<P>::first gives the time of the segment's first event
+// (>= dt when there is none); Draw<P>::event gives event j's kick, sign
+// factor, acceptance uniform and next gap.
 // ---------------------------------------------------------------------------
 template <class P>
 struct Draw;
 
+// FP64: the parity contract shared with the oracle.  u0 of (pid, l, 0)
+// gives the first life-length from `to`; event j uses (pid, l, 1+2j) and
+// (pid, l, 2+2j).  Offspring draw their first life-length the same way.
 template <>
 struct Draw<P64> {
-  // Time of the first event of a segment starting at `to` (Sec. 3.2).
-  __device__ static double first(const KP<P64>& p, unsigned long long pid,
-                                 int l, double to, bool /*root*/) {
-    const uint4 r = philox((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
-                           0u, p.key0, p.key1);
+  struct State {};
+  __device__ static double first(const KP<P64>& p, unsigned long long pid, int l, double to,
+                                 bool /*root*/, State&) {
+    const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
     const double u0 = u53(r.x, r.y);
     return P64::add(to, P64::div(-log1p(-u0), p.gamma0));
   }
-  // Event j: kick kappa ~ N(0, sig_k^2), sg = sin(2 (xe - xc) kappa),
-  // acceptance uniform and the next exponential gap.
-  __device__ static void event(const KP<P64>& p, unsigned long long pid,
-                               int l, unsigned j, double xe, double& kap,
-                               double& sg, double& u3, double& gap) {
+  __device__ static void event(const KP<P64>& p, unsigned long long pid, int l, unsigned j,
+                               double xe, const State&, double& kap, double& sg, double& u3,
+                               double& gap) {
     const uint32_t lo = (uint32_t)pid, hi = (uint32_t)(pid >> 32);
-    const uint4 a = philox(lo, hi, (uint32_t)l, 1u + 2u * j, p.key0, p.key1);
-    const uint4 b = philox(lo, hi, (uint32_t)l, 2u + 2u * j, p.key0, p.key1);
+    const uint4 a = philox_ks(p.ks, lo, hi, (uint32_t)l, 1u + 2u * j);
+    const uint4 b = philox_ks(p.ks, lo, hi, (uint32_t)l, 2u + 2u * j);
     const double u1 = u53(a.x, a.y), u2 = u53(a.z, a.w);
     u3 = u53(b.x, b.y);
     const double u4 = u53(b.z, b.w);
@@ -288,24 +282,52 @@ struct Draw<P64> {
   }
 };
 
+// FP32: the production contract, checked in law.
+//  - Root segments (the interval is a known candidate): one call (pid, l, 0)
+//    serves both the first life-length, drawn from the exponential truncated
+//    to the interval, tau = -log1p(-p_any U24(w0))/gamma0, and event 0
+//    (u1..u3 = U24(w1..w3), u4 from the low bytes of w0..w2).
+//  - Offspring segments (from their birth time tb): whether an event falls in
+//    the rest of the interval is decided by the offspring's own random id,
+//    whose low 32 bits are a uniform: hit iff they are below
+//    p_r 2^32, p_r = 1 - exp(-gamma0 (dt - tb)).  Only a hit draws the call
+//    (pid, l, 0), which then serves as for a root, with p_r for p_any.
+//  - Event j >= 1 of a segment uses the call (pid, l, 1+j): U24 of w0..w3.
 template <>
 struct Draw<P32> {
-  __device__ static float first(const KP<P32>& p, unsigned long long pid,
-                                int l, float to, bool root) {
-    const uint4 r = philox((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
-                           0u, p.key0, p.key1);
-    float u = u24(r.x);
-    if (root) u *= p.p_any_f;  // the interval is known to hold an event
-    return to + (-log1pf(-u)) / p.gamma0;
+  struct State {
+    uint4 r;
+  };
+  __device__ static float first(const KP<P32>& p, unsigned long long pid, int l, float to,
+                                bool root, State& st) {
+    float pr;
+    if (root) {
+      pr = p.p_any_f;
+    } else {
+      pr = -expm1f(-p.gamma0 * (p.dt - to));
+      if (!((float)(uint32_t)pid < pr * 4294967296.0f)) return p.dt;  // no event
+    }
+    st.r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
+    return to + (-log1pf(-pr * u24(st.r.x))) / p.gamma0;
   }
-  __device__ static void event(const KP<P32>& p, unsigned long long pid,
-                               int l, unsigned j, float xe, float& kap,
-                               float& sg, float& u3, float& gap) {
-    const uint4 a = philox((uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
-                           1u + j, p.key0, p.key1);
-    const float u1 = u24(a.x), u2 = u24(a.y);
-    u3 = u24(a.z);
-    const float u4 = u24(a.w);
+  __device__ static void event(const KP<P32>& p, unsigned long long pid, int l, unsigned j,
+                               float xe, const State& st, float& kap, float& sg, float& u3,
+                               float& gap) {
+    float u1, u2, u4;
+    if (j == 0) {
+      const uint4 r = st.r;
+      u1 = u24(r.y);
+      u2 = u24(r.z);
+      u3 = u24(r.w);
+      u4 = (float)(((r.x & 0xFFu) << 16) | ((r.y & 0xFFu) << 8) | (r.z & 0xFFu)) *
+           (1.0f / 16777216.0f);
+    } else {
+      const uint4 a = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 1u + j);
+      u1 = u24(a.x);
+      u2 = u24(a.y);
+      u3 = u24(a.z);
+      u4 = u24(a.w);
+    }
     const float z = sqrtf(-2.0f * log1pf(-u1)) * cospif(2.0f * u2);
     kap = p.sig_k * z;
     sg = sinf(2.0f * (xe - p.xc) * kap);
@@ -322,38 +344,44 @@ __device__ __forceinline__ uint32_t q131(typename P::T w) {
   return (uint32_t)floor(fabs((double)w) * 2147483648.0);
 }
 
-// A final (end-of-chunk) state produced inside the divergent event code:
-// histogram sinks act directly; record / array sinks are staged.
+template <class P>
+__device__ __forceinline__ void tally_out(const KP<P>& p, Acc& acc, typename P::T w) {
+  if (p.count_ledger) {
+    if (w > (typename P::T)0) ++acc.out_p;
+    else if (w < (typename P::T)0) ++acc.out_m;
+  }
+}
+
+template <class P>
+__device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long idx, int cell,
+                                           typename P::T w) {
+  const uint32_t a = q131<P>(w);
+  p.rec_cell[idx] = (uint32_t)cell | (w < (typename P::T)0 ? 0x80000000u : 0u);
+  p.rec_a[idx] = a;
+  if (w > (typename P::T)0) { ++acc.n_plus; acc.w_plus += a; } else { ++acc.n_minus; acc.w_minus += a; }
+}
+
+// An end-of-chunk state produced inside the divergent event code.
 template <class P, int DST>
-__device__ void emit_child_final(const KP<P>& p, Smem<typename P::T>& sm,
-                                 Acc& acc, unsigned long long pid,
-                                 typename P::T x, typename P::T k,
-                                 typename P::T w) {
+__device__ void emit_child_final(const KP<P>& p, Acc& acc, unsigned long long pid,
+                                 typename P::T x, typename P::T k, typename P::T w) {
   using T = typename P::T;
-  if constexpr (DST == DST_BIN1 || DST == DST_WSUM) {
-    int cell;
-    if (cell_of<P>(p, x, k, cell)) {
-      if constexpr (DST == DST_BIN1) atomicAdd(p.grid + cell, w > (T)0 ? 1 : -1);
-      else atomicAdd((unsigned long long*)(p.wsum + cell),
-                     (unsigned long long)llrint((double)w * 2147483648.0));
-    } else if (p.count_ledger) {
-      if (w > (T)0) ++acc.out_p; else if (w < (T)0) ++acc.out_m;
-    }
-    return;
-  }
-  const int pos = atomicAdd(&sm.nstage_out, 1);
-  FEntry<T> e;
-  e.pid = pid;
-  e.x = x;
-  e.k = k;
-  e.w = w;
-  e.l = p.L;
-  if (pos < kStageOut) {
-    sm.stage_out[pos] = e;
-    return;
-  }
-  // rare: the stage is full, append on our own
-  if constexpr (DST == DST_ARRAY) {
+  int cell;
+  if constexpr (DST == DST_BIN1) {
+    if (cell_of<P>(p, x, k, cell)) atomicAdd(p.grid + cell, w > (T)0 ? 1 : -1);
+    else tally_out<P>(p, acc, w);
+  } else if constexpr (DST == DST_WSUM) {
+    if (cell_of<P>(p, x, k, cell))
+      atomicAdd((unsigned long long*)(p.wsum + cell),
+                (unsigned long long)llrint((double)w * 2147483648.0));
+  } else if constexpr (DST == DST_BIN2) {
+    if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
+    if (w == (T)0) return;
+    const int seg = my_segment();
+    const unsigned long long r = atomicAdd(&p.cnt->recs[seg], 1ull);
+    if (r >= (unsigned long long)p.rseg) { set_err(p.cnt, ERR_CAP_RECORDS); return; }
+    put_record<P>(p, acc, (long long)seg * p.rseg + (long long)r, cell, w);
+  } else {  // DST_ARRAY
     const unsigned long long slot = atomicAdd(&p.cnt->n, 1ull);
     if (slot >= (unsigned long long)p.capacity) { set_err(p.cnt, ERR_CAP_PARTICLES); return; }
     p.x[slot] = x;
@@ -361,234 +389,230 @@ __device__ void emit_child_final(const KP<P>& p, Smem<typename P::T>& sm,
     p.s[slot] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
     if (p.w) p.w[slot] = w;
     p.cpid[slot - p.cnt->n_base] = pid;
-  } else {  // DST_BIN2
-    int cell;
-    if (!cell_of<P>(p, x, k, cell)) {
-      if (p.count_ledger) { if (w > (T)0) ++acc.out_p; else if (w < (T)0) ++acc.out_m; }
-      return;
-    }
-    if (w == (T)0) return;
-    const unsigned long long r = atomicAdd(&p.cnt->rec_len, 1ull);
-    if (r >= (unsigned long long)p.rec_cap) { set_err(p.cnt, ERR_CAP_RECORDS); return; }
-    const uint32_t a = q131<P>(w);
-    p.rec_cell[r] = (uint32_t)cell | (w < (T)0 ? 0x80000000u : 0u);
-    p.rec_a[r] = a;
-    if (w > (T)0) { ++acc.n_plus; acc.w_plus += a; } else { ++acc.n_minus; acc.w_minus += a; }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Events of one candidate interval (Alg. 1 item 3), with every offspring's
-// own events in the rest of the interval.  The root frame is the particle
-// itself: its end-of-interval state belongs to the flight, not to here.
+// own events in the rest of the interval.  The root segment is the particle
+// itself: its end-of-interval state belongs to the flight.  Each offspring's
+// first event time is drawn at birth; the common offspring, with no event
+// left in the interval, is settled at once (staged for the next wave, or
+// sent to the sink in the chunk's last interval); only offspring with events
+// of their own wait on the stack.
 // ---------------------------------------------------------------------------
-template <class T>
+template <class P>
 struct Frame {
-  T xo, to, k, w;
+  using T = typename P::T;
+  T xo, to, k, w, t1;  // origin, birth time, wavevector, weight, first event
   unsigned long long pid;
-  int root;
+  typename Draw<P>::State st;
 };
 
+// An offspring's state at the end of interval l: the next wave's input, or
+// the sink's in the chunk's last interval.
 template <class P, int DST>
-__device__ void process_interval(const KP<P>& p, Smem<typename P::T>& sm,
-                                 Acc& acc, unsigned long long pid0,
-                                 typename P::T x_start, typename P::T k0,
-                                 typename P::T w0, int l) {
+__device__ __forceinline__ void settle(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
+                                       unsigned long long pid, typename P::T xo,
+                                       typename P::T to, typename P::T k, typename P::T w,
+                                       int l) {
   using T = typename P::T;
-  Frame<T> stack[kStack];
-  int sp = 0;
-  stack[sp++] = Frame<T>{x_start, (T)0, k0, w0, pid0, 1};
-  while (sp > 0) {
-    const Frame<T> f = stack[--sp];
-    T t = Draw<P>::first(p, f.pid, l, f.to, f.root != 0);
-    unsigned j = 0;
-    while (t < p.dt) {
-      const T xe = P::add(f.xo, P::mul(f.k, P::mul(P::sub(t, f.to), p.hm)));
-      T kap, sg, u3, gap;
-      Draw<P>::event(p, f.pid, l, j, xe, kap, sg, u3, gap);
-      const T fac = P::mul(p.cacc, (T)fabs(sg));
-      const bool emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
-      if (emit) {
-        if (sg < (T)0) kap = -kap;
-        const uint4 h = philox((uint32_t)f.pid, (uint32_t)(f.pid >> 32),
-                               (uint32_t)l, kDrawPids | j, p.key0, p.key1);
-        const unsigned long long pid_p =
-            (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
-        const unsigned long long pid_m =
-            (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
-        const T kp = P::add(f.k, kap), km = P::sub(f.k, kap);
-        const bool kill_p = !(kp >= p.kmin && kp < p.kmax);
-        const bool kill_m = !(km >= p.kmin && km < p.kmax);
-        const T wc = p.strategy == 1 ? f.w : P::mul(f.w, fac);
-        const T wp = wc, wm = -wc;
-        ++acc.events;
-        if (kill_p) { if (wp > (T)0) ++acc.kill_p; else if (wp < (T)0) ++acc.kill_m; }
-        if (kill_m) { if (wm > (T)0) ++acc.kill_p; else if (wm < (T)0) ++acc.kill_m; }
-        if (p.log) {
-          const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
-          if (idx < (unsigned long long)p.log_cap) {
-            wbrw_event ev;
-            ev.pid = f.pid;
-            ev.pid_plus = pid_p;
-            ev.pid_minus = pid_m;
-            ev.step = (unsigned)l;
-            ev.j = j;
-            ev.t = (double)t;
-            ev.xe = (double)xe;
-            ev.kappa = (double)kap;
-            ev.factor = (double)fac;
-            ev.kill_plus = kill_p;
-            ev.kill_minus = kill_m;
-            p.log[idx] = ev;
-          }
-        }
-        if (!kill_p) {
-          if (sp < kStack) stack[sp++] = Frame<T>{xe, t, kp, wp, pid_p, 0};
-          else set_err(p.cnt, ERR_NESTING);
-        }
-        if (!kill_m) {
-          if (sp < kStack) stack[sp++] = Frame<T>{xe, t, km, wm, pid_m, 0};
-          else set_err(p.cnt, ERR_NESTING);
-        }
-      }
-      t = P::add(t, gap);
-      ++j;
+  const T xf = P::add(xo, P::mul(k, P::mul(P::sub(p.dt, to), p.hm)));
+  if (l + 1 < p.L) {
+    FEntry<T> e;
+    e.pid = pid;
+    e.x = xf;
+    e.k = k;
+    e.w = w;
+    e.l = l + 1;
+    const int pos = atomicAdd(&ws.n, 1);
+    if (pos < kWStage) {
+      ws.e[pos] = e;
+    } else {  // rare: the warp's stage is full, append on our own
+      const int seg = my_segment();
+      const unsigned long long q = atomicAdd(&p.cnt->qs[p.round + 1][seg], 1ull);
+      if (q < (unsigned long long)p.qseg) p.fq_out[(long long)seg * p.qseg + (long long)q] = e;
+      else set_err(p.cnt, ERR_CAP_QUEUE);
     }
-    if (!f.root) {
-      // the offspring's position at the end of interval l
-      const T xf = P::add(f.xo, P::mul(f.k, P::mul(P::sub(p.dt, f.to), p.hm)));
-      if (l + 1 < p.L) {
-        FEntry<T> e;
-        e.pid = f.pid;
-        e.x = xf;
-        e.k = f.k;
-        e.w = f.w;
-        e.l = l + 1;
-        const int pos = atomicAdd(&sm.nstage_f, 1);
-        if (pos < kStageF) {
-          sm.stage_f[pos] = e;
-        } else {
-          const unsigned long long q = atomicAdd(&p.cnt->q[p.round + 1], 1ull);
-          if (q < (unsigned long long)p.qcap) p.fq_out[q] = e;
-          else set_err(p.cnt, ERR_CAP_QUEUE);
-        }
-      } else {
-        emit_child_final<P, DST>(p, sm, acc, f.pid, xf, f.k, f.w);
-      }
-    }
+  } else {
+    emit_child_final<P, DST>(p, acc, pid, xf, k, w);
   }
 }
 
-// Flush the block's staged offspring (every thread calls).
 template <class P, int DST>
-__device__ void flush_stages(const KP<P>& p, Smem<typename P::T>& sm,
-                             Acc& acc) {
+__device__ void run_segment(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
+                            const Frame<P>& f, int l, Frame<P>* stack, int& sp) {
   using T = typename P::T;
-  __syncthreads();
-  const int nf = min(sm.nstage_f, kStageF);
-  const int no = min(sm.nstage_out, kStageOut);
-  if (threadIdx.x == 0) {
-    sm.base = nf ? atomicAdd(&p.cnt->q[p.round + 1], (unsigned long long)nf) : 0ull;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nf; i += kBlock) {
-    const unsigned long long q = sm.base + i;
-    if (q < (unsigned long long)p.qcap) p.fq_out[q] = sm.stage_f[i];
-    else set_err(p.cnt, ERR_CAP_QUEUE);
-  }
-  __syncthreads();
-  if (DST == DST_ARRAY && no > 0) {
-    if (threadIdx.x == 0) sm.base = atomicAdd(&p.cnt->n, (unsigned long long)no);
-    __syncthreads();
-    for (int i = threadIdx.x; i < no; i += kBlock) {
-      const FEntry<T> e = sm.stage_out[i];
-      const unsigned long long slot = sm.base + i;
-      if (slot >= (unsigned long long)p.capacity) { set_err(p.cnt, ERR_CAP_PARTICLES); continue; }
-      p.x[slot] = e.x;
-      p.k[slot] = e.k;
-      p.s[slot] = e.w > (T)0 ? 1 : (e.w < (T)0 ? -1 : 0);
-      if (p.w) p.w[slot] = e.w;
-      p.cpid[slot - p.cnt->n_base] = e.pid;
-    }
-  } else if (DST == DST_BIN2 && no > 0) {
-    // records of staged finals: compact the in-grid nonzero ones
-    for (int i = threadIdx.x; i < no; i += kBlock) {
-      const FEntry<T> e = sm.stage_out[i];
-      int cell;
-      if (!cell_of<P>(p, e.x, e.k, cell)) {
-        if (p.count_ledger) { if (e.w > (T)0) ++acc.out_p; else if (e.w < (T)0) ++acc.out_m; }
-        continue;
+  T t = f.t1;
+  unsigned j = 0;
+  while (t < p.dt) {
+    const T xe = P::add(f.xo, P::mul(f.k, P::mul(P::sub(t, f.to), p.hm)));
+    T kap, sg, u3, gap;
+    Draw<P>::event(p, f.pid, l, j, xe, f.st, kap, sg, u3, gap);
+    const T fac = P::mul(p.cacc, (T)fabs(sg));
+    const bool emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
+    if (emit) {
+      if (sg < (T)0) kap = -kap;
+      const uint4 h = philox_ks(p.ks, (uint32_t)f.pid, (uint32_t)(f.pid >> 32), (uint32_t)l,
+                                kDrawPids | j);
+      const unsigned long long pid_p =
+          (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
+      const unsigned long long pid_m =
+          (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
+      const T kp = P::add(f.k, kap), km = P::sub(f.k, kap);
+      const bool kill_p = !(kp >= p.kmin && kp < p.kmax);
+      const bool kill_m = !(km >= p.kmin && km < p.kmax);
+      const T wc = p.strategy == 1 ? f.w : P::mul(f.w, fac);
+      const T wp = wc, wm = -wc;
+      ++acc.events;
+      if (kill_p) { if (wp > (T)0) ++acc.kill_p; else if (wp < (T)0) ++acc.kill_m; }
+      if (kill_m) { if (wm > (T)0) ++acc.kill_p; else if (wm < (T)0) ++acc.kill_m; }
+      if (p.log) {
+        const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
+        if (idx < (unsigned long long)p.log_cap) {
+          wbrw_event ev;
+          ev.pid = f.pid;
+          ev.pid_plus = pid_p;
+          ev.pid_minus = pid_m;
+          ev.step = (unsigned)l;
+          ev.j = j;
+          ev.t = (double)t;
+          ev.xe = (double)xe;
+          ev.kappa = (double)kap;
+          ev.factor = (double)fac;
+          ev.kill_plus = kill_p;
+          ev.kill_minus = kill_m;
+          p.log[idx] = ev;
+        }
       }
-      if (e.w == (T)0) continue;
-      const unsigned long long r = atomicAdd(&p.cnt->rec_len, 1ull);
-      if (r >= (unsigned long long)p.rec_cap) { set_err(p.cnt, ERR_CAP_RECORDS); continue; }
-      const uint32_t a = q131<P>(e.w);
-      p.rec_cell[r] = (uint32_t)cell | (e.w < (T)0 ? 0x80000000u : 0u);
-      p.rec_a[r] = a;
-      if (e.w > (T)0) { ++acc.n_plus; acc.w_plus += a; } else { ++acc.n_minus; acc.w_minus += a; }
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const bool killed = c == 0 ? kill_p : kill_m;
+        if (killed) continue;
+        Frame<P> ch;
+        ch.xo = xe;
+        ch.to = t;
+        ch.k = c == 0 ? kp : km;
+        ch.w = c == 0 ? wp : wm;
+        ch.pid = c == 0 ? pid_p : pid_m;
+        ch.t1 = Draw<P>::first(p, ch.pid, l, t, false, ch.st);
+        if (ch.t1 < p.dt) {
+          if (sp < kStack) stack[sp++] = ch;
+          else set_err(p.cnt, ERR_NESTING);
+        } else {
+          settle<P, DST>(p, ws, acc, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
+        }
+      }
+    }
+    t = P::add(t, gap);
+    ++j;
+  }
+}
+
+template <class P, int DST>
+__device__ void process_interval(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
+                                 unsigned long long pid0, typename P::T x_start,
+                                 typename P::T k0, typename P::T w0, int l) {
+  using T = typename P::T;
+  Frame<P> stack[kStack];
+  int sp = 0;
+  Frame<P> root;
+  root.xo = x_start;
+  root.to = (T)0;
+  root.k = k0;
+  root.w = w0;
+  root.pid = pid0;
+  root.t1 = Draw<P>::first(p, pid0, l, (T)0, true, root.st);
+  run_segment<P, DST>(p, ws, acc, root, l, stack, sp);
+  while (sp > 0) {
+    const Frame<P> f = stack[--sp];
+    run_segment<P, DST>(p, ws, acc, f, l, stack, sp);
+    settle<P, DST>(p, ws, acc, f.pid, f.xo, f.to, f.k, f.w, l);
+  }
+}
+
+// Append the warp's staged offspring to its queue segment (whole warp).
+template <class P>
+__device__ void flush_stage(const KP<P>& p, WarpStage<typename P::T>& ws) {
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  const int n = min(ws.n, kWStage);
+  if (n > 0) {
+    const int seg = my_segment();
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.cnt->qs[p.round + 1][seg], (unsigned long long)n);
+    base = __shfl_sync(kFull, base, 0);
+    for (int i = lane; i < n; i += 32) {
+      const unsigned long long q = base + i;
+      if (q < (unsigned long long)p.qseg) p.fq_out[(long long)seg * p.qseg + (long long)q] = ws.e[i];
+      else set_err(p.cnt, ERR_CAP_QUEUE);
     }
   }
-  __syncthreads();
+  __syncwarp();
+  if (lane == 0) ws.n = 0;
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// The flight kernel
+// The flight kernel.  Warp-centric: each warp owns 32 consecutive slots per
+// iteration and never waits for the other warps of its block.  It carries
+// every particle through [ls, L) -- streaming plus the candidate clock -- and
+// leaves the rare candidate intervals to k_event: each becomes one entry
+// (pid, x at the interval's start, k, w, l) of the segmented event queue, so
+// that the event kernel runs with every lane busy.
 // ---------------------------------------------------------------------------
 template <class P, int SRC, int DST>
-__global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, 4) k_flight(const KP<P> p) {
   using T = typename P::T;
-  __shared__ Smem<T> sm;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
+  __shared__ unsigned long long pre[kSeg + 1];
+  __shared__ unsigned long long red[kWarps];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
   Acc acc;
   acc.zero();
 
   unsigned long long n;
-  if (SRC == SRC_ARRAY) n = p.cnt->n_src;
-  else if (SRC == SRC_REGEN) n = p.cnt->regen_total;
-  else n = min(p.cnt->q[p.round], (unsigned long long)p.qcap);
+  if constexpr (SRC == SRC_ARRAY) {
+    n = p.cnt->n_src;
+  } else if constexpr (SRC == SRC_REGEN) {
+    n = min(p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
+  } else {
+    n = load_segments(pre, p.cnt->qs[p.round], p.qseg);
+  }
   const unsigned long long n_base = p.cnt->n_base, base_pid = p.cnt->base_pid;
   const unsigned long long nz = (SRC == SRC_REGEN) ? p.cnt->nz_count : 0ull;
+  const int seg = my_segment();
 
-  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < n;
-       base += (unsigned long long)gridDim.x * kBlock) {
-    const unsigned long long slot = base + tid;
+  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + wid;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
+    const unsigned long long slot = base + lane;
     const bool act = slot < n;
     T x = (T)0, k = (T)0, w = (T)0;
     unsigned long long pid = 0;
     int ls = p.L;
 
     if constexpr (SRC == SRC_REGEN) {
-      // Alg. 3: slot -> its cell through the exclusive scan of |c_nu| over
-      // the nonzero cells.  The block's 256 slots span at most 257 of them.
-      if (tid == 0) {
-        unsigned long long lo = 0, hi = nz - 1;  // last a: nz_start[a] <= base
-        while (lo < hi) {
-          const unsigned long long mid = lo + (hi - lo + 1) / 2;
-          if (p.nz_start[mid] <= base) lo = mid; else hi = mid - 1;
-        }
-        sm.win_a = lo;
+      // Alg. 3: the cell of each slot.  The tile's first nonzero cell comes
+      // from the plan; the 32 slots of a tile lie in at most 32 nonzero
+      // cells, searched with shuffles.
+      const unsigned long long a0 = p.tile_nz[base >> 5];
+      const unsigned long long idx = a0 + lane;
+      const unsigned long long st = idx < nz ? p.nz_start[idx] : ~0ull;
+      const uint32_t cw = idx < nz ? p.nz_cell[idx] : 0u;
+      int lo = 0, hi = 31;  // last i with start_i <= slot
+#pragma unroll
+      for (int it = 0; it < 5; ++it) {
+        const int mid = (lo + hi + 1) >> 1;
+        const unsigned long long sv = __shfl_sync(kFull, st, mid);
+        if (sv <= slot) lo = mid; else hi = mid - 1;
       }
-      __syncthreads();
-      const unsigned long long a0 = sm.win_a;
-      for (int i = tid; i <= kBlock; i += kBlock) {
-        const unsigned long long idx = a0 + i;
-        sm.win_start[i] = idx < nz ? p.nz_start[idx] : ~0ull;
-        sm.win_cell[i] = idx < nz ? p.nz_cell[idx] : 0u;
-      }
-      __syncthreads();
+      const uint32_t cwl = __shfl_sync(kFull, cw, lo);
       if (act) {
-        int lo = 0, hi = kBlock;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (sm.win_start[mid] <= slot) lo = mid; else hi = mid - 1;
-        }
-        const uint32_t cw = sm.win_cell[lo];
-        const int cell = (int)(cw & 0x7FFFFFFFu);
+        const int cell = (int)(cwl & 0x7FFFFFFFu);
         const int ix = cell / p.nk, ik = cell - ix * p.nk;
         pid = p.regen_base | slot;
-        const uint4 r = philox((uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen,
-                               0u, p.key0, p.key1);
+        const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
         T ux, uk;
         if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
         else { ux = (T)u24(r.x); uk = (T)u24(r.y); }
@@ -599,18 +623,20 @@ __global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
         for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) < (T)ix; ++it) x = P::next_up(x);
         for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) > (T)ik; ++it) k = P::next_dn(k);
         for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) < (T)ik; ++it) k = P::next_up(k);
-        w = (cw >> 31) ? (T)-1 : (T)1;
+        w = (cwl >> 31) ? (T)-1 : (T)1;
         ls = p.l0;
       }
-    } else if (act) {
-      if constexpr (SRC == SRC_ARRAY) {
+    } else if constexpr (SRC == SRC_ARRAY) {
+      if (act) {
         x = p.x[slot];
         k = p.k[slot];
         w = p.w ? p.w[slot] : (T)p.s[slot];
         pid = slot < n_base ? base_pid + slot : p.cpid[slot - n_base];
         ls = p.l0;
-      } else {
-        const FEntry<T> e = p.fq_in[slot];
+      }
+    } else {
+      if (act) {
+        const FEntry<T> e = p.fq_in[segmented_index(pre, slot, p.qseg)];
         x = e.x;
         k = e.k;
         w = e.w;
@@ -626,50 +652,38 @@ __global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
       const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
       if constexpr (P::is64) {
         for (int l = ls; l < p.L; ++l) {
-          const uint4 r = philox(plo, phi, (uint32_t)l, 0u, p.key0, p.key1);
+          const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
           if (u53(r.x, r.y) < p.p_hi) mask |= 1u << (l - p.l0);
           x = P::stream(x, k, p.dtv);
         }
       } else {
-        uint4 q = make_uint4(0, 0, 0, 0);
-        int qb = -1;
-        for (int l = ls; l < p.L; ++l) {
-          const int b = l >> 3;
-          if (b != qb) {
-            q = philox(plo, phi, (uint32_t)b, kDrawCoins, p.key0, p.key1);
-            qb = b;
+        // eight 16-bit coins per Philox call, for the intervals 8b .. 8b+7
+        for (int b = ls >> 3; (b << 3) < p.L; ++b) {
+          const uint4 q = philox_ks(p.ks, plo, phi, (uint32_t)b, kDrawCoins);
+          const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int l = (b << 3) + jj;
+            if (l >= ls && l < p.L) {
+              const uint32_t coin = (jj & 1) ? (wv[jj >> 1] >> 16) : (wv[jj >> 1] & 0xFFFFu);
+              bool cand = coin < p.p16;
+              if (coin == p.p16) {  // tie: refine with 8 more bits
+                const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
+                cand = (r.w & 0xFFu) < p.p16_frac8;
+              }
+              if (cand) mask |= 1u << (l - p.l0);
+              x = P::stream(x, k, p.dtv);
+            }
           }
-          const int wi = (l & 7) >> 1;
-          const uint32_t word = wi == 0 ? q.x : (wi == 1 ? q.y : (wi == 2 ? q.z : q.w));
-          const uint32_t coin = (l & 1) ? (word >> 16) : (word & 0xFFFFu);
-          bool cand = coin < p.p16;
-          if (coin == p.p16) {
-            const uint4 r = philox(plo, phi, (uint32_t)l, 0u, p.key0, p.key1);
-            cand = u24(r.y) < p.p16_frac;
-          }
-          if (cand) mask |= 1u << (l - p.l0);
-          x = P::stream(x, k, p.dtv);
         }
       }
       acc.psteps += (unsigned long long)(p.L - ls);
     }
 
-    if (tid == 0) {
-      sm.nitems = 0;
-      sm.nstage_f = 0;
-      sm.nstage_out = 0;
-    }
-    sm.x[tid] = x_start;
-    sm.k[tid] = k;
-    sm.w[tid] = w;
-    sm.pid[tid] = pid;
-    sm.ls[tid] = ls;
-
     // ---- the particle's own final state --------------------------------
     if constexpr (DST == DST_ARRAY) {
       if constexpr (SRC == SRC_ARRAY) {
         if (act) p.x[slot] = x;
-        __syncthreads();
       } else if constexpr (SRC == SRC_REGEN) {
         if (act && slot >= (unsigned long long)p.capacity) {
           set_err(p.cnt, ERR_CAP_PARTICLES);
@@ -679,10 +693,11 @@ __global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
           p.s[slot] = w > (T)0 ? 1 : -1;
           if (p.w) p.w[slot] = w;
         }
-        __syncthreads();
       } else {
-        unsigned long long tot;
-        const unsigned long long off = block_append<T>(sm, act ? 1u : 0u, &p.cnt->n, tot);
+        const unsigned bal = __ballot_sync(kFull, act);
+        unsigned long long off = 0;
+        if (lane == 0 && bal) off = atomicAdd(&p.cnt->n, (unsigned long long)__popc(bal));
+        off = __shfl_sync(kFull, off, 0) + __popc(bal & ((1u << lane) - 1u));
         if (act) {
           if (off >= (unsigned long long)p.capacity) {
             set_err(p.cnt, ERR_CAP_PARTICLES);
@@ -700,12 +715,11 @@ __global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
       if (act) {
         int cell;
         if (cell_of<P>(p, x, k, cell)) key = 2ll * cell + (w > (T)0 ? 1 : 0);
-        else if (p.count_ledger) { if (w > (T)0) ++acc.out_p; else ++acc.out_m; }
+        else tally_out<P>(p, acc, w);
       }
-      const unsigned grp = __match_any_sync(0xFFFFFFFFu, (unsigned long long)key);
+      const unsigned grp = __match_any_sync(kFull, (unsigned long long)key);
       if (key >= 0 && lane == __ffs(grp) - 1)
         atomicAdd(p.grid + (key >> 1), (key & 1) ? __popc(grp) : -__popc(grp));
-      __syncthreads();
     } else if constexpr (DST == DST_WSUM) {
       if (act) {
         int cell;
@@ -713,132 +727,113 @@ __global__ void __launch_bounds__(kBlock) k_flight(const KP<P> p) {
           atomicAdd((unsigned long long*)(p.wsum + cell),
                     (unsigned long long)llrint((double)w * 2147483648.0));
       }
-      __syncthreads();
-    } else {  // DST_BIN2
+    } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
       int cell = -1;
       if (act) {
-        if (!cell_of<P>(p, x, k, cell)) {
-          cell = -1;
-          if (p.count_ledger) { if (w > (T)0) ++acc.out_p; else if (w < (T)0) ++acc.out_m; }
-        } else if (w == (T)0) {
-          cell = -1;
-        }
+        if (!cell_of<P>(p, x, k, cell)) { cell = -1; tally_out<P>(p, acc, w); }
+        else if (w == (T)0) cell = -1;
       }
-      unsigned long long tot;
-      const unsigned long long r = block_append<T>(sm, cell >= 0 ? 1u : 0u, &p.cnt->rec_len, tot);
-      if (cell >= 0) {
-        if (r >= (unsigned long long)p.rec_cap) {
-          set_err(p.cnt, ERR_CAP_RECORDS);
-        } else {
-          const uint32_t a = q131<P>(w);
-          p.rec_cell[r] = (uint32_t)cell | (w < (T)0 ? 0x80000000u : 0u);
-          p.rec_a[r] = a;
-          if (w > (T)0) { ++acc.n_plus; acc.w_plus += a; } else { ++acc.n_minus; acc.w_minus += a; }
+      const unsigned bal = __ballot_sync(kFull, cell >= 0);
+      if (bal) {
+        unsigned long long off = 0;
+        if (lane == 0) off = atomicAdd(&p.cnt->recs[seg], (unsigned long long)__popc(bal));
+        off = __shfl_sync(kFull, off, 0) + __popc(bal & ((1u << lane) - 1u));
+        if (cell >= 0) {
+          if (off >= (unsigned long long)p.rseg) set_err(p.cnt, ERR_CAP_RECORDS);
+          else put_record<P>(p, acc, (long long)seg * p.rseg + (long long)off, cell, w);
         }
       }
     }
 
-    // ---- candidate intervals -> the block's list (or the overflow queue)
-    const int cnt = __popc(mask);
-    if (cnt) {
-      const int pos = atomicAdd(&sm.nitems, cnt);
-      if (pos + cnt <= kItemCap) {
-        unsigned m = mask;
-        for (int i = 0; i < cnt; ++i) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          sm.items[pos + i] = (unsigned)tid | ((unsigned)b << 16);
-        }
-      } else {
-        for (int i = pos; i < kItemCap; ++i) sm.items[i] = kNoItem;
-        const unsigned long long e = atomicAdd(&p.cnt->e[p.round], 1ull);
-        if (e < (unsigned long long)p.ecap) {
-          EEntry<T> ee;
-          ee.pid = pid;
-          ee.x = x_start;
-          ee.k = k;
-          ee.w = w;
-          ee.ls = ls;
-          ee.mask = mask;
-          p.eq[e] = ee;
+    // ---- candidate intervals -> the segmented event queue --------------
+    const unsigned cnt = __popc(mask);
+    unsigned inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned t = __shfl_up_sync(kFull, inc, o);
+      if (lane >= o) inc += t;
+    }
+    const unsigned total = __shfl_sync(kFull, inc, 31);
+    if (total) {
+      unsigned long long q0 = 0;
+      if (lane == 0) q0 = atomicAdd(&p.cnt->es[p.round][seg], (unsigned long long)total);
+      q0 = __shfl_sync(kFull, q0, 0) + (inc - cnt);
+      T xs = x_start;
+      int ll = ls;
+      unsigned m = mask;
+      for (unsigned i = 0; i < cnt; ++i) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int l = p.l0 + b;
+        for (; ll < l; ++ll) xs = P::stream(xs, k, p.dtv);
+        const unsigned long long q = q0 + i;
+        if (q < (unsigned long long)p.eseg) {
+          FEntry<T> e;
+          e.pid = pid;
+          e.x = xs;
+          e.k = k;
+          e.w = w;
+          e.l = l;
+          p.eq[(long long)seg * p.eseg + (long long)q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
         }
       }
     }
-    __syncthreads();
-
-    // ---- process them, one per thread ----------------------------------
-    const int ni = min(sm.nitems, kItemCap);
-    for (int i = tid; i < ni; i += kBlock) {
-      const unsigned it = sm.items[i];
-      if (it == kNoItem) continue;
-      const int owner = (int)(it & 0xFFFFu);
-      const int l = p.l0 + (int)(it >> 16);
-      const T ko = sm.k[owner];
-      T xs = sm.x[owner];
-      for (int ll = sm.ls[owner]; ll < l; ++ll) xs = P::stream(xs, ko, p.dtv);
-      process_interval<P, DST>(p, sm, acc, sm.pid[owner], xs, ko, sm.w[owner], l);
-    }
-    flush_stages<P, DST>(p, sm, acc);
   }
 
   // ---- tallies ------------------------------------------------------------
-  block_reduce_add<T>(sm, acc.psteps, &p.cnt->ledger[SRC == SRC_QUEUE ? LG_PSTEPS : LG_PSTEPS0]);
-  block_reduce_add<T>(sm, acc.events, &p.cnt->ledger[LG_EVENTS]);
-  block_reduce_add<T>(sm, acc.kill_p, &p.cnt->ledger[LG_KILL_P]);
-  block_reduce_add<T>(sm, acc.kill_m, &p.cnt->ledger[LG_KILL_M]);
-  block_reduce_add<T>(sm, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
-  block_reduce_add<T>(sm, acc.out_m, &p.cnt->ledger[LG_OUT_M]);
+  block_reduce_add(red, acc.psteps, &p.cnt->ledger[SRC == SRC_QUEUE ? LG_PSTEPS : LG_PSTEPS0]);
+  block_reduce_add(red, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
+  block_reduce_add(red, acc.out_m, &p.cnt->ledger[LG_OUT_M]);
   if constexpr (DST == DST_BIN2) {
-    block_reduce_add<T>(sm, acc.n_plus, &p.cnt->boot_n[0]);
-    block_reduce_add<T>(sm, acc.n_minus, &p.cnt->boot_n[1]);
-    block_reduce_add<T>(sm, acc.w_plus, &p.cnt->boot_w[0]);
-    block_reduce_add<T>(sm, acc.w_minus, &p.cnt->boot_w[1]);
+    block_reduce_add(red, acc.n_plus, &p.cnt->boot_n[0]);
+    block_reduce_add(red, acc.n_minus, &p.cnt->boot_n[1]);
+    block_reduce_add(red, acc.w_plus, &p.cnt->boot_w[0]);
+    block_reduce_add(red, acc.w_minus, &p.cnt->boot_w[1]);
   }
 }
 
-// Candidate intervals that overflowed a block's list in round `p.round`.
+// ---------------------------------------------------------------------------
+// The event kernel: one candidate interval per lane (Alg. 1 item 3 with the
+// offspring's own events in the rest of the interval).  Offspring alive at
+// the end of the interval are staged per warp and appended to the next
+// wave's queue segment; in the last interval of the chunk they go to the
+// sink instead.
+// ---------------------------------------------------------------------------
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock) k_event(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, 3) k_event(const KP<P> p) {
   using T = typename P::T;
-  __shared__ Smem<T> sm;
+  __shared__ WarpStage<T> stage[kWarps];
+  __shared__ unsigned long long pre[kSeg + 1];
+  __shared__ unsigned long long red[kWarps];
+  const int lane = threadIdx.x & 31;
+  WarpStage<T>& ws = stage[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  const unsigned long long n = min(p.cnt->e[p.round], (unsigned long long)p.ecap);
-  for (unsigned long long base = (unsigned long long)blockIdx.x * kBlock; base < n;
-       base += (unsigned long long)gridDim.x * kBlock) {
-    if (threadIdx.x == 0) {
-      sm.nstage_f = 0;
-      sm.nstage_out = 0;
-    }
-    __syncthreads();
-    const unsigned long long i = base + threadIdx.x;
+  if (lane == 0) ws.n = 0;
+  __syncwarp();
+  const unsigned long long n = load_segments(pre, p.cnt->es[p.round], p.eseg);
+  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
+    const unsigned long long i = base + lane;
     if (i < n) {
-      const EEntry<T> e = p.eq[i];
-      unsigned m = e.mask;
-      T xs = e.x;
-      int ll = e.ls;
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int l = p.l0 + b;
-        for (; ll < l; ++ll) xs = P::stream(xs, e.k, p.dtv);
-        process_interval<P, DST>(p, sm, acc, e.pid, xs, e.k, e.w, l);
-      }
+      const FEntry<T> e = p.eq[segmented_index(pre, i, p.eseg)];
+      process_interval<P, DST>(p, ws, acc, e.pid, e.x, e.k, e.w, e.l);
     }
-    flush_stages<P, DST>(p, sm, acc);
+    flush_stage<P>(p, ws);
   }
-  block_reduce_add<T>(sm, acc.events, &p.cnt->ledger[LG_EVENTS]);
-  block_reduce_add<T>(sm, acc.kill_p, &p.cnt->ledger[LG_KILL_P]);
-  block_reduce_add<T>(sm, acc.kill_m, &p.cnt->ledger[LG_KILL_M]);
-  block_reduce_add<T>(sm, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
-  block_reduce_add<T>(sm, acc.out_m, &p.cnt->ledger[LG_OUT_M]);
+  block_reduce_add(red, acc.events, &p.cnt->ledger[LG_EVENTS]);
+  block_reduce_add(red, acc.kill_p, &p.cnt->ledger[LG_KILL_P]);
+  block_reduce_add(red, acc.kill_m, &p.cnt->ledger[LG_KILL_M]);
+  block_reduce_add(red, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
+  block_reduce_add(red, acc.out_m, &p.cnt->ledger[LG_OUT_M]);
   if constexpr (DST == DST_BIN2) {
-    block_reduce_add<T>(sm, acc.n_plus, &p.cnt->boot_n[0]);
-    block_reduce_add<T>(sm, acc.n_minus, &p.cnt->boot_n[1]);
-    block_reduce_add<T>(sm, acc.w_plus, &p.cnt->boot_w[0]);
-    block_reduce_add<T>(sm, acc.w_minus, &p.cnt->boot_w[1]);
+    block_reduce_add(red, acc.n_plus, &p.cnt->boot_n[0]);
+    block_reduce_add(red, acc.n_minus, &p.cnt->boot_n[1]);
+    block_reduce_add(red, acc.w_plus, &p.cnt->boot_w[0]);
+    block_reduce_add(red, acc.w_minus, &p.cnt->boot_w[1]);
   }
 }
 
@@ -852,8 +847,7 @@ __global__ void __launch_bounds__(kBlock) k_init(const KP<P> p,
   using T = typename P::T;
   for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * kBlock) {
-    const uint4 r = philox((uint32_t)i, (uint32_t)(i >> 32), kStepInit, 0u,
-                           p.key0, p.key1);
+    const uint4 r = philox_ks(p.ks, (uint32_t)i, (uint32_t)(i >> 32), kStepInit, 0u);
     T x, k;
     if constexpr (P::is64) {
       const double ua = u53(r.x, r.y), ub = u53(r.z, r.w);
@@ -919,9 +913,11 @@ KP<P> make_kp(const Ctx* c) {
   const double sc = c->p_any * 65536.0;
   const double fl = floor(sc);
   p.p16 = (unsigned)fl;
-  p.p16_frac = (float)(sc - fl);
-  p.key0 = (uint32_t)g.seed;
-  p.key1 = (uint32_t)(g.seed >> 32);
+  p.p16_frac8 = (unsigned)floor((sc - fl) * 256.0);
+  for (int r = 0; r < 10; ++r) {
+    p.ks.k0[r] = (uint32_t)g.seed + (uint32_t)r * 0x9E3779B9u;
+    p.ks.k1[r] = (uint32_t)(g.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+  }
   p.strategy = g.strategy;
   p.l0 = p.L = (int)c->step;
   p.round = 0;
@@ -934,16 +930,18 @@ KP<P> make_kp(const Ctx* c) {
   p.cpid = c->cpid;
   p.fq_in = (FEntry<T>*)c->fq[0];
   p.fq_out = (FEntry<T>*)c->fq[1];
-  p.qcap = c->qcap;
-  p.eq = (EEntry<T>*)c->eq;
-  p.ecap = c->ecap;
+  p.qseg = c->qcap / kSeg;
+  p.eq = (FEntry<T>*)c->eq;
+  p.eseg = c->ecap / kSeg;
   p.grid = c->buf.grid;
   p.wsum = c->tmp_wsum;
   p.rec_cell = c->rec_cell;
   p.rec_a = c->rec_a;
-  p.rec_cap = c->rec_cap;
+  p.rseg = c->rec_cap / kSeg;
   p.nz_cell = c->nz_cell;
   p.nz_start = c->nz_start;
+  p.tile_nz = c->tile_nz;
+  p.tile_cap = c->tile_cap;
   p.cnt = c->cnt;
   p.log = (wbrw_event*)c->buf.event_log;
   p.log_cap = c->buf.event_log ? c->buf.event_log_capacity : 0;

@@ -13,6 +13,7 @@ constexpr int kBlock = 256;      // threads per block of every particle kernel
 constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
 constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
+constexpr int kSeg = 64;         // segments of the offspring queues and records
 
 enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2 };
 enum Dst { DST_ARRAY = 0, DST_BIN1 = 1, DST_BIN2 = 2, DST_WSUM = 3 };
@@ -36,12 +37,12 @@ struct Counters {
   unsigned long long n_src;        // snapshot of n at the start of a chunk
   unsigned long long n_base;       // slots < n_base have pid = base_pid + slot
   unsigned long long base_pid;
-  unsigned long long q[kMaxChunk + 2];  // F-queue entries for round r
-  unsigned long long e[kMaxChunk + 2];  // overflow candidate entries, round r
+  unsigned long long qs[kMaxChunk + 2][kSeg];  // F-queue entries, round r, segment
+  unsigned long long es[kMaxChunk + 2][kSeg];  // candidate intervals, round r, segment
   unsigned long long nz_count;     // nonzero cells of the last histogram
   unsigned long long regen_total;  // particles implied by the histogram
   unsigned long long log_len;
-  unsigned long long rec_len;      // sp2 records
+  unsigned long long recs[kSeg];   // sp2 records per segment
   unsigned long long ledger[LG_N];
   unsigned long long boot_n[2], boot_w[2], boot_keep[2], boot_nr[2];
   unsigned long long boot_R[2];    // total residual (Q0.32) per side
@@ -66,9 +67,12 @@ struct Ctx {
   void* fq[2];
   long long qcap;
   void* eq;
-  long long ecap;
+  long long ecap;     // candidate-interval queue entries (kSeg segments)
+  int max_chunk;      // steps per flight: about one candidate per particle
   uint32_t* nz_cell;
   unsigned long long* nz_start;
+  uint32_t* tile_nz;  // first nonzero cell of each 32-slot tile of the plan
+  long long tile_cap;
   unsigned long long* scan_bsum;
   unsigned int* scan_bnz;
   long long scan_blocks;
