@@ -29,10 +29,10 @@ size_t elem_size(int precision) { return precision == WBRW_FP64 ? 8 : 4; }
 size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
 
 struct Layout {
-  size_t counters, cpid, fq0, fq1, eq, nz_cell, nz_start, tile_nz, scan_bsum, scan_bnz,
+  size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum, scan_bnz,
       tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
       rec_a, keep0, keep1, res0, res1, total;
-  long long qcap, ecap, rec_cap, scan_blocks, tile_cap;
+  long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
 bool config_ok(const wbrw_config* c, char* why, size_t n) {
@@ -60,6 +60,7 @@ Layout layout(const wbrw_config* c, long long capacity) {
   L.qcap = ((capacity + kSeg - 1) / kSeg) * kSeg;
   L.tile_cap = capacity / 32 + 2;
   L.ecap = 2 * L.qcap;  // about one candidate interval per particle per flight
+  L.dcap = L.ecap / 4;  // deferred segments: a few per cent of the events
   L.rec_cap = c->strategy == WBRW_SP2_BOOTSTRAP ? 4 * L.qcap : 0;
   L.scan_blocks = (nh + kScanTile - 1) / kScanTile;
   size_t off = 0;
@@ -73,6 +74,8 @@ Layout layout(const wbrw_config* c, long long capacity) {
   L.fq0 = take((size_t)L.qcap * fentry_size(c->precision));
   L.fq1 = take((size_t)L.qcap * fentry_size(c->precision));
   L.eq = take((size_t)L.ecap * fentry_size(c->precision));
+  L.dq0 = take((size_t)L.dcap * 64);  // deferred segment entry: 64 bytes
+  L.dq1 = take((size_t)L.dcap * 64);
   L.nz_cell = take((size_t)nh * 4);
   L.nz_start = take((size_t)nh * 8);
   L.tile_nz = take((size_t)L.tile_cap * 4);
@@ -262,6 +265,9 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
   c->qcap = L.qcap;
   c->eq = base + L.eq;
   c->ecap = L.ecap;
+  c->dq[0] = base + L.dq0;
+  c->dq[1] = base + L.dq1;
+  c->dcap = L.dcap;
   c->nz_cell = (uint32_t*)(base + L.nz_cell);
   c->nz_start = (unsigned long long*)(base + L.nz_start);
   c->tile_nz = (uint32_t*)(base + L.tile_nz);

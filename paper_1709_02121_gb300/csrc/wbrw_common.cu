@@ -46,17 +46,18 @@ constexpr uint32_t kStepRound = 0xFFFFFFFCu;
 __global__ void k_setup(Counters* c, int op, unsigned long long a,
                         unsigned long long b) {
   (void)b;
+  if (op == SETUP_CHUNK) {  // every thread clears a share of the queue counters
+    for (int i = threadIdx.x; i < (kMaxChunk + 2) * kSeg; i += blockDim.x) {
+      (&c->qs[0][0])[i] = 0;
+      (&c->es[0][0])[i] = 0;
+    }
+    for (int i = threadIdx.x; i < (kMaxChunk + 2) * 5 * kSeg; i += blockDim.x)
+      (&c->ds[0][0][0])[i] = 0;
+    if (threadIdx.x == 0) c->n_src = c->n;
+    return;
+  }
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   switch (op) {
-    case SETUP_CHUNK:
-      c->n_src = c->n;
-      for (int i = 0; i < kMaxChunk + 2; ++i) {
-        for (int s = 0; s < kSeg; ++s) {
-          c->qs[i][s] = 0;
-          c->es[i][s] = 0;
-        }
-      }
-      break;
     case SETUP_AFTER_REGEN:
       c->n = c->regen_total;
       c->n_base = c->regen_total;
@@ -412,7 +413,7 @@ int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
 }  // namespace
 
 cudaError_t launch_setup(Ctx* c, int op, unsigned long long a, unsigned long long b) {
-  k_setup<<<1, 32, 0, c->stream>>>(c->cnt, op, a, b);
+  k_setup<<<1, kBlock, 0, c->stream>>>(c->cnt, op, a, b);
   c->launches++;
   return cudaGetLastError();
 }

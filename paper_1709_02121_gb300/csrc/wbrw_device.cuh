@@ -114,6 +114,9 @@ struct FEntry {  // offspring waiting at the start of interval l
 
 static_assert(sizeof(FEntry<double>) == 40 && sizeof(FEntry<float>) == 24, "FEntry layout");
 
+template <class P>
+struct SEntry;
+
 // Kernel parameters (by value, parameter space).
 template <class P>
 struct KP {
@@ -140,6 +143,8 @@ struct KP {
   long long qseg;   // entries per queue segment
   FEntry<T>* eq;    // candidate intervals: x at the interval's start, l
   long long eseg;   // entries per event-queue segment
+  SEntry<P>* dq[2]; // deferred segments (levels alternate between the two)
+  long long dseg;   // entries per deferred-queue segment
   int* grid;
   long long* wsum;
   uint32_t* rec_cell;
@@ -393,21 +398,30 @@ __device__ void emit_child_final(const KP<P>& p, Acc& acc, unsigned long long pi
 }
 
 // ---------------------------------------------------------------------------
-// Events of one candidate interval (Alg. 1 item 3), with every offspring's
-// own events in the rest of the interval.  The root segment is the particle
-// itself: its end-of-interval state belongs to the flight.  Each offspring's
-// first event time is drawn at birth; the common offspring, with no event
-// left in the interval, is settled at once (staged for the next wave, or
-// sent to the sink in the chunk's last interval); only offspring with events
-// of their own wait on the stack.
+// Events (Alg. 1 item 3).  A segment is a particle's part of interval l from
+// time `to` (0 for a particle present at t_l, its birth time for an
+// offspring).  Processing is split into passes so that the lanes of a warp
+// follow the same path: each pass performs ONE event of each of its
+// segments; a segment with another event left in the interval, and an
+// offspring born with an event of its own, are deferred to the next pass.
+// Offspring with no event left are settled at once: staged for the next
+// wave, or sent to the sink in the chunk's last interval.  After the last
+// pass a drain kernel finishes whatever remains with a full recursion.
 // ---------------------------------------------------------------------------
 template <class P>
-struct Frame {
+struct SEntry {  // a deferred segment, with the time and index of its next event
   using T = typename P::T;
-  T xo, to, k, w, t1;  // origin, birth time, wavevector, weight, first event
   unsigned long long pid;
+  T xo, to, k, w, t;
+  int l;
+  unsigned j;   // bits 0..30: index of the next event; bit 31: the root segment
   typename Draw<P>::State st;
 };
+
+static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
+
+constexpr unsigned kRootFlag = 0x80000000u;
+constexpr int kLevels = 5;  // deferred segments: levels 1..3 in passes, 4 drained
 
 // An offspring's state at the end of interval l: the next wave's input, or
 // the sink's in the chunk's last interval.
@@ -439,95 +453,106 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpStage<typename P::T>&
   }
 }
 
-template <class P, int DST>
-__device__ void run_segment(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
-                            const Frame<P>& f, int l, Frame<P>* stack, int& sp) {
-  using T = typename P::T;
-  T t = f.t1;
-  unsigned j = 0;
-  while (t < p.dt) {
-    const T xe = P::add(f.xo, P::mul(f.k, P::mul(P::sub(t, f.to), p.hm)));
-    T kap, sg, u3, gap;
-    Draw<P>::event(p, f.pid, l, j, xe, f.st, kap, sg, u3, gap);
-    const T fac = P::mul(p.cacc, (T)fabs(sg));
-    const bool emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
-    if (emit) {
-      if (sg < (T)0) kap = -kap;
-      const uint4 h = philox_ks(p.ks, (uint32_t)f.pid, (uint32_t)(f.pid >> 32), (uint32_t)l,
-                                kDrawPids | j);
-      const unsigned long long pid_p =
-          (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
-      const unsigned long long pid_m =
-          (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
-      const T kp = P::add(f.k, kap), km = P::sub(f.k, kap);
-      const bool kill_p = !(kp >= p.kmin && kp < p.kmax);
-      const bool kill_m = !(km >= p.kmin && km < p.kmax);
-      const T wc = p.strategy == 1 ? f.w : P::mul(f.w, fac);
-      const T wp = wc, wm = -wc;
-      ++acc.events;
-      if (kill_p) { if (wp > (T)0) ++acc.kill_p; else if (wp < (T)0) ++acc.kill_m; }
-      if (kill_m) { if (wm > (T)0) ++acc.kill_p; else if (wm < (T)0) ++acc.kill_m; }
-      if (p.log) {
-        const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
-        if (idx < (unsigned long long)p.log_cap) {
-          wbrw_event ev;
-          ev.pid = f.pid;
-          ev.pid_plus = pid_p;
-          ev.pid_minus = pid_m;
-          ev.step = (unsigned)l;
-          ev.j = j;
-          ev.t = (double)t;
-          ev.xe = (double)xe;
-          ev.kappa = (double)kap;
-          ev.factor = (double)fac;
-          ev.kill_plus = kill_p;
-          ev.kill_minus = kill_m;
-          p.log[idx] = ev;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const bool killed = c == 0 ? kill_p : kill_m;
-        if (killed) continue;
-        Frame<P> ch;
-        ch.xo = xe;
-        ch.to = t;
-        ch.k = c == 0 ? kp : km;
-        ch.w = c == 0 ? wp : wm;
-        ch.pid = c == 0 ? pid_p : pid_m;
-        ch.t1 = Draw<P>::first(p, ch.pid, l, t, false, ch.st);
-        if (ch.t1 < p.dt) {
-          if (sp < kStack) stack[sp++] = ch;
-          else set_err(p.cnt, ERR_NESTING);
-        } else {
-          settle<P, DST>(p, ws, acc, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
-        }
-      }
-    }
-    t = P::add(t, gap);
-    ++j;
-  }
+// Append a segment to the deferred level `level` (one atomic per entry:
+// deferred segments are a few per cent of the events).
+template <class P>
+__device__ __forceinline__ void defer(const KP<P>& p, int level, const SEntry<P>& s) {
+  const int seg = my_segment();
+  const unsigned long long q = atomicAdd(&p.cnt->ds[p.round][level][seg], 1ull);
+  if (q < (unsigned long long)p.dseg)
+    p.dq[level & 1][(long long)seg * p.dseg + (long long)q] = s;
+  else
+    set_err(p.cnt, ERR_CAP_EQUEUE);
 }
 
-template <class P, int DST>
-__device__ void process_interval(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
-                                 unsigned long long pid0, typename P::T x_start,
-                                 typename P::T k0, typename P::T w0, int l) {
+// Event j of a segment at time t: the kick of Remark 3, the acceptance
+// (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair.  Offspring are settled
+// or, when they have an event of their own in the interval, handed to
+// `later`.  Returns the gap to the segment's next event.
+template <class P, int DST, class Later>
+__device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpStage<typename P::T>& ws,
+                                                  Acc& acc, unsigned long long pid,
+                                                  typename P::T xo, typename P::T to,
+                                                  typename P::T k, typename P::T w,
+                                                  const typename Draw<P>::State& st, int l,
+                                                  unsigned j, typename P::T t, Later later) {
   using T = typename P::T;
-  Frame<P> stack[kStack];
+  const T xe = P::add(xo, P::mul(k, P::mul(P::sub(t, to), p.hm)));
+  T kap, sg, u3, gap;
+  Draw<P>::event(p, pid, l, j, xe, st, kap, sg, u3, gap);
+  const T fac = P::mul(p.cacc, (T)fabs(sg));
+  const bool emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
+  if (emit) {
+    if (sg < (T)0) kap = -kap;
+    const uint4 h = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
+                              kDrawPids | j);
+    const unsigned long long pid_p = (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
+    const unsigned long long pid_m = (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
+    const T kp = P::add(k, kap), km = P::sub(k, kap);
+    const bool kill_p = !(kp >= p.kmin && kp < p.kmax);
+    const bool kill_m = !(km >= p.kmin && km < p.kmax);
+    const T wc = p.strategy == 1 ? w : P::mul(w, fac);
+    ++acc.events;
+    if (kill_p) { if (wc > (T)0) ++acc.kill_p; else if (wc < (T)0) ++acc.kill_m; }
+    if (kill_m) { if (-wc > (T)0) ++acc.kill_p; else if (-wc < (T)0) ++acc.kill_m; }
+    if (p.log) {
+      const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
+      if (idx < (unsigned long long)p.log_cap) {
+        wbrw_event ev;
+        ev.pid = pid;
+        ev.pid_plus = pid_p;
+        ev.pid_minus = pid_m;
+        ev.step = (unsigned)l;
+        ev.j = j;
+        ev.t = (double)t;
+        ev.xe = (double)xe;
+        ev.kappa = (double)kap;
+        ev.factor = (double)fac;
+        ev.kill_plus = kill_p;
+        ev.kill_minus = kill_m;
+        p.log[idx] = ev;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (c == 0 ? kill_p : kill_m) continue;
+      SEntry<P> ch;
+      ch.pid = c == 0 ? pid_p : pid_m;
+      ch.xo = xe;
+      ch.to = t;
+      ch.k = c == 0 ? kp : km;
+      ch.w = c == 0 ? wc : -wc;
+      ch.l = l;
+      ch.j = 0;
+      ch.t = Draw<P>::first(p, ch.pid, l, t, false, ch.st);
+      if (ch.t < p.dt) later(ch);
+      else settle<P, DST>(p, ws, acc, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
+    }
+  }
+  return gap;
+}
+
+// All remaining events of a deferred segment, recursively (drain).
+template <class P, int DST>
+__device__ void finish_segment(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
+                               const SEntry<P>& s0) {
+  SEntry<P> stack[kStack];
   int sp = 0;
-  Frame<P> root;
-  root.xo = x_start;
-  root.to = (T)0;
-  root.k = k0;
-  root.w = w0;
-  root.pid = pid0;
-  root.t1 = Draw<P>::first(p, pid0, l, (T)0, true, root.st);
-  run_segment<P, DST>(p, ws, acc, root, l, stack, sp);
+  stack[sp++] = s0;
   while (sp > 0) {
-    const Frame<P> f = stack[--sp];
-    run_segment<P, DST>(p, ws, acc, f, l, stack, sp);
-    settle<P, DST>(p, ws, acc, f.pid, f.xo, f.to, f.k, f.w, l);
+    SEntry<P> s = stack[--sp];
+    unsigned j = s.j & ~kRootFlag;
+    auto later = [&](const SEntry<P>& ch) {
+      if (sp < kStack) stack[sp++] = ch;
+      else set_err(p.cnt, ERR_NESTING);
+    };
+    while (s.t < p.dt) {
+      const typename P::T gap = do_event<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
+                                                 s.l, j, s.t, later);
+      s.t = P::add(s.t, gap);
+      ++j;
+    }
+    if (!(s.j & kRootFlag)) settle<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
   }
 }
 
@@ -795,12 +820,28 @@ __global__ void __launch_bounds__(kBlock, 4) k_flight(const KP<P> p) {
 }
 
 // ---------------------------------------------------------------------------
-// The event kernel: one candidate interval per lane (Alg. 1 item 3 with the
-// offspring's own events in the rest of the interval).  Offspring alive at
-// the end of the interval are staged per warp and appended to the next
-// wave's queue segment; in the last interval of the chunk they go to the
-// sink instead.
+// Event kernels.  k_event takes the candidate intervals of the flight (one
+// per lane) and performs their first event; k_cont performs one more event
+// of each deferred segment of a level; k_drain finishes the last level.
+// Offspring alive at the end of their interval are staged per warp and
+// appended to the next wave's queue segment.
 // ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, const Acc& acc,
+                                                     Counters* c, bool bin2) {
+  block_reduce_add(red, acc.events, &c->ledger[LG_EVENTS]);
+  block_reduce_add(red, acc.kill_p, &c->ledger[LG_KILL_P]);
+  block_reduce_add(red, acc.kill_m, &c->ledger[LG_KILL_M]);
+  block_reduce_add(red, acc.out_p, &c->ledger[LG_OUT_P]);
+  block_reduce_add(red, acc.out_m, &c->ledger[LG_OUT_M]);
+  if (bin2) {
+    block_reduce_add(red, acc.n_plus, &c->boot_n[0]);
+    block_reduce_add(red, acc.n_minus, &c->boot_n[1]);
+    block_reduce_add(red, acc.w_plus, &c->boot_w[0]);
+    block_reduce_add(red, acc.w_minus, &c->boot_w[1]);
+  }
+}
+
 template <class P, int DST>
 __global__ void __launch_bounds__(kBlock, 3) k_event(const KP<P> p) {
   using T = typename P::T;
@@ -816,25 +857,94 @@ __global__ void __launch_bounds__(kBlock, 3) k_event(const KP<P> p) {
   const unsigned long long n = load_segments(pre, p.cnt->es[p.round], p.eseg);
   const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  auto later = [&](const SEntry<P>& ch) { defer<P>(p, 1, ch); };
   for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
     const unsigned long long i = base + lane;
     if (i < n) {
       const FEntry<T> e = p.eq[segmented_index(pre, i, p.eseg)];
-      process_interval<P, DST>(p, ws, acc, e.pid, e.x, e.k, e.w, e.l);
+      SEntry<P> s;
+      s.pid = e.pid;
+      s.xo = e.x;
+      s.to = (T)0;
+      s.k = e.k;
+      s.w = e.w;
+      s.l = e.l;
+      s.t = Draw<P>::first(p, e.pid, e.l, (T)0, true, s.st);
+      if (s.t < p.dt) {
+        const T gap = do_event<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, 0u,
+                                       s.t, later);
+        s.t = P::add(s.t, gap);
+        if (s.t < p.dt) {
+          s.j = 1u | kRootFlag;
+          defer<P>(p, 1, s);
+        }
+      }
     }
     flush_stage<P>(p, ws);
   }
-  block_reduce_add(red, acc.events, &p.cnt->ledger[LG_EVENTS]);
-  block_reduce_add(red, acc.kill_p, &p.cnt->ledger[LG_KILL_P]);
-  block_reduce_add(red, acc.kill_m, &p.cnt->ledger[LG_KILL_M]);
-  block_reduce_add(red, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
-  block_reduce_add(red, acc.out_m, &p.cnt->ledger[LG_OUT_M]);
-  if constexpr (DST == DST_BIN2) {
-    block_reduce_add(red, acc.n_plus, &p.cnt->boot_n[0]);
-    block_reduce_add(red, acc.n_minus, &p.cnt->boot_n[1]);
-    block_reduce_add(red, acc.w_plus, &p.cnt->boot_w[0]);
-    block_reduce_add(red, acc.w_minus, &p.cnt->boot_w[1]);
+  reduce_event_tallies<T>(red, acc, p.cnt, DST == DST_BIN2);
+}
+
+template <class P, int DST>
+__global__ void __launch_bounds__(kBlock, 3) k_cont(const KP<P> p, int level) {
+  using T = typename P::T;
+  __shared__ WarpStage<T> stage[kWarps];
+  __shared__ unsigned long long pre[kSeg + 1];
+  __shared__ unsigned long long red[kWarps];
+  const int lane = threadIdx.x & 31;
+  WarpStage<T>& ws = stage[threadIdx.x >> 5];
+  Acc acc;
+  acc.zero();
+  if (lane == 0) ws.n = 0;
+  __syncwarp();
+  const unsigned long long n = load_segments(pre, p.cnt->ds[p.round][level], p.dseg);
+  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  const SEntry<P>* in = p.dq[level & 1];
+  auto later = [&](const SEntry<P>& ch) { defer<P>(p, level + 1, ch); };
+  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
+    const unsigned long long i = base + lane;
+    if (i < n) {
+      SEntry<P> s = in[segmented_index(pre, i, p.dseg)];
+      const unsigned j = s.j & ~kRootFlag;
+      const T gap = do_event<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, j,
+                                     s.t, later);
+      s.t = P::add(s.t, gap);
+      if (s.t < p.dt) {
+        s.j = (j + 1) | (s.j & kRootFlag);
+        defer<P>(p, level + 1, s);
+      } else if (!(s.j & kRootFlag)) {
+        settle<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
+      }
+    }
+    flush_stage<P>(p, ws);
   }
+  reduce_event_tallies<T>(red, acc, p.cnt, DST == DST_BIN2);
+}
+
+template <class P, int DST>
+__global__ void __launch_bounds__(kBlock, 3) k_drain(const KP<P> p) {
+  using T = typename P::T;
+  __shared__ WarpStage<T> stage[kWarps];
+  __shared__ unsigned long long pre[kSeg + 1];
+  __shared__ unsigned long long red[kWarps];
+  const int lane = threadIdx.x & 31;
+  WarpStage<T>& ws = stage[threadIdx.x >> 5];
+  Acc acc;
+  acc.zero();
+  if (lane == 0) ws.n = 0;
+  __syncwarp();
+  const int level = kLevels - 1;
+  const unsigned long long n = load_segments(pre, p.cnt->ds[p.round][level], p.dseg);
+  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  const SEntry<P>* in = p.dq[level & 1];
+  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
+    const unsigned long long i = base + lane;
+    if (i < n) finish_segment<P, DST>(p, ws, acc, in[segmented_index(pre, i, p.dseg)]);
+    flush_stage<P>(p, ws);
+  }
+  reduce_event_tallies<T>(red, acc, p.cnt, DST == DST_BIN2);
 }
 
 // Initial particles from the Gaussian-wavepacket Wigner function (positive):
@@ -933,6 +1043,9 @@ KP<P> make_kp(const Ctx* c) {
   p.qseg = c->qcap / kSeg;
   p.eq = (FEntry<T>*)c->eq;
   p.eseg = c->ecap / kSeg;
+  p.dq[0] = (SEntry<P>*)c->dq[0];
+  p.dq[1] = (SEntry<P>*)c->dq[1];
+  p.dseg = c->dcap / kSeg;
   p.grid = c->buf.grid;
   p.wsum = c->tmp_wsum;
   p.rec_cell = c->rec_cell;
@@ -969,10 +1082,17 @@ cudaError_t flight(Ctx* c, const KP<P>& p) {
 
 template <class P, int DST>
 cudaError_t events(Ctx* c, const KP<P>& p) {
-  static int grid = 0;
-  if (!grid) grid = grid_for(c, k_event<P, DST>);
-  k_event<P, DST><<<grid, kBlock, 0, c->stream>>>(p);
-  c->launches++;
+  static int g_ev = 0, g_cont = 0, g_drain = 0;
+  if (!g_ev) {
+    g_ev = grid_for(c, k_event<P, DST>);
+    g_cont = grid_for(c, k_cont<P, DST>);
+    g_drain = grid_for(c, k_drain<P, DST>);
+  }
+  k_event<P, DST><<<g_ev, kBlock, 0, c->stream>>>(p);
+  for (int level = 1; level < kLevels - 1; ++level)
+    k_cont<P, DST><<<g_cont, kBlock, 0, c->stream>>>(p, level);
+  k_drain<P, DST><<<g_drain, kBlock, 0, c->stream>>>(p);
+  c->launches += kLevels;
   return cudaGetLastError();
 }
 

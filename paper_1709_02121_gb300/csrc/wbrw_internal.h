@@ -39,6 +39,7 @@ struct Counters {
   unsigned long long base_pid;
   unsigned long long qs[kMaxChunk + 2][kSeg];  // F-queue entries, round r, segment
   unsigned long long es[kMaxChunk + 2][kSeg];  // candidate intervals, round r, segment
+  unsigned long long ds[kMaxChunk + 2][5][kSeg];  // deferred segments, round, level, segment
   unsigned long long nz_count;     // nonzero cells of the last histogram
   unsigned long long regen_total;  // particles implied by the histogram
   unsigned long long log_len;
@@ -68,6 +69,8 @@ struct Ctx {
   long long qcap;
   void* eq;
   long long ecap;     // candidate-interval queue entries (kSeg segments)
+  void* dq[2];
+  long long dcap;     // deferred-segment queue entries, per buffer
   int max_chunk;      // steps per flight: about one candidate per particle
   uint32_t* nz_cell;
   unsigned long long* nz_start;
