@@ -72,7 +72,7 @@ typedef struct {
   int precision;            /* wbrw_precision: particle state and arithmetic */
   int strategy;             /* wbrw_strategy                                 */
   double hbar, mass, dt, gamma0;
-  int nx, nk;               /* cells; nx * nk < 2^31                          */
+  int nx, nk;               /* cells; nx * nk < 2^30                          */
   double xmin, xmax, kmin, kmax;
   int resample_every;       /* steps per T_A for wbrw_run; 0 = never          */
   long long n_alpha;        /* N_alpha (> 0)                                 */

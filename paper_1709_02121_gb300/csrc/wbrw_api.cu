@@ -20,18 +20,15 @@ struct wbrw_ctx : public Ctx {};
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kLevelsHost = 5;  // deferred-segment levels (kLevels of the device code)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
-size_t elem_size(int precision) { return precision == WBRW_FP64 ? 8 : 4; }
-
-// Queue entry {u64 pid; T x, k, w; int l;} as laid out by the device code.
-size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
 
 struct Layout {
-  size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum, scan_bnz,
-      tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, total;
+  size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
+      scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
+      rec_a, keep0, keep1, res0, res1, seg_counts, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
@@ -46,21 +43,28 @@ bool config_ok(const wbrw_config* c, char* why, size_t n) {
   if (c->strategy != WBRW_SP1_PAIR && c->strategy != WBRW_SP2_BOOTSTRAP) return fail("strategy");
   if (!(c->hbar > 0) || !(c->mass > 0) || !(c->dt > 0)) return fail("hbar, mass and dt must be > 0");
   if (c->nx <= 0 || c->nk <= 0) return fail("nx and nk must be > 0");
-  if ((long long)c->nx * (long long)c->nk >= (1ll << 31)) return fail("nx*nk must be < 2^31");
+  if ((long long)c->nx * (long long)c->nk >= (1ll << 30)) return fail("nx*nk must be < 2^30");
   if (!(c->xmax > c->xmin) || !(c->kmax > c->kmin)) return fail("empty domain");
   if (c->resample_every < 0) return fail("resample_every must be >= 0");
   if (c->n_alpha <= 0) return fail("n_alpha must be > 0");
   return true;
 }
 
+// Queue entries: {u64 pid; T x, k, w; int l;} for offspring waves and
+// candidate intervals; deferred segments take 64 bytes.  Every queue is cut
+// into one segment per producer warp (at most kMaxSeg); each segment gets at
+// least kMinSeg entries so that small runs cannot starve a warp.
+constexpr long long kMinSeg = 64;
+size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
+
 Layout layout(const wbrw_config* c, long long capacity) {
   Layout L;
   const long long nh = (long long)c->nx * c->nk;
-  // offspring queues and sp2 records are split into kSeg equal segments
-  L.qcap = ((capacity + kSeg - 1) / kSeg) * kSeg;
-  L.tile_cap = capacity / 32 + 2;
+  const long long floor_entries = (long long)kMaxSeg * kMinSeg;
+  L.qcap = capacity > floor_entries ? capacity : floor_entries;
   L.ecap = 2 * L.qcap;  // about one candidate interval per particle per flight
   L.dcap = L.ecap / 4;  // deferred segments: a few per cent of the events
+  L.tile_cap = capacity / 32 + 2;
   L.rec_cap = c->strategy == WBRW_SP2_BOOTSTRAP ? 4 * L.qcap : 0;
   L.scan_blocks = (nh + kScanTile - 1) / kScanTile;
   size_t off = 0;
@@ -70,11 +74,12 @@ Layout layout(const wbrw_config* c, long long capacity) {
     return at;
   };
   L.counters = take(sizeof(Counters));
+  L.seg_counts = take((size_t)(1 + 2 + kLevelsHost + 1) * kMaxSeg * sizeof(unsigned));
   L.cpid = take((size_t)capacity * 8);
   L.fq0 = take((size_t)L.qcap * fentry_size(c->precision));
   L.fq1 = take((size_t)L.qcap * fentry_size(c->precision));
   L.eq = take((size_t)L.ecap * fentry_size(c->precision));
-  L.dq0 = take((size_t)L.dcap * 64);  // deferred segment entry: 64 bytes
+  L.dq0 = take((size_t)L.dcap * 64);
   L.dq1 = take((size_t)L.dcap * 64);
   L.nz_cell = take((size_t)nh * 4);
   L.nz_start = take((size_t)nh * 8);
@@ -148,6 +153,7 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
     WBRW_TRY(c, d->bin(c, DST_BIN1, c->buf.grid, 1), "bin");
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
+    WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
     for (int s = 0; s < 2; ++s) {
       WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
       WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
@@ -260,14 +266,27 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
   char* base = (char*)b->scratch;
   c->cnt = (Counters*)(base + L.counters);
   c->cpid = (unsigned long long*)(base + L.cpid);
+  // one queue segment per producer warp: at most kMaxBlocksPerSm blocks per SM
+  c->nseg = kMaxBlocksPerSm * c->num_sms * (kBlock / 32);
+  if (c->nseg > kMaxSeg) c->nseg = kMaxSeg;
+  unsigned* counts = (unsigned*)(base + L.seg_counts);
+  c->ecnt = counts;
+  c->fcnt[0] = counts + kMaxSeg;
+  c->fcnt[1] = counts + 2 * kMaxSeg;
+  c->dcnt = counts + 3 * kMaxSeg;
+  c->rcnt = counts + (3 + kLevelsHost) * kMaxSeg;
   c->fq[0] = base + L.fq0;
   c->fq[1] = base + L.fq1;
   c->qcap = L.qcap;
+  c->qseg = L.qcap / c->nseg;
   c->eq = base + L.eq;
   c->ecap = L.ecap;
+  c->eseg = L.ecap / c->nseg;
   c->dq[0] = base + L.dq0;
   c->dq[1] = base + L.dq1;
   c->dcap = L.dcap;
+  c->dseg = L.dcap / c->nseg;
+  c->rseg = L.rec_cap / c->nseg;
   c->nz_cell = (uint32_t*)(base + L.nz_cell);
   c->nz_start = (unsigned long long*)(base + L.nz_start);
   c->tile_nz = (uint32_t*)(base + L.tile_nz);
@@ -354,6 +373,7 @@ wbrw_status wbrw_run(wbrw_ctx* c, int nsteps) {
       WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
     } else {
       WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
+      WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
       for (int s = 0; s < 2; ++s) {
         WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
         WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");

@@ -46,18 +46,11 @@ constexpr uint32_t kStepRound = 0xFFFFFFFCu;
 __global__ void k_setup(Counters* c, int op, unsigned long long a,
                         unsigned long long b) {
   (void)b;
-  if (op == SETUP_CHUNK) {  // every thread clears a share of the queue counters
-    for (int i = threadIdx.x; i < (kMaxChunk + 2) * kSeg; i += blockDim.x) {
-      (&c->qs[0][0])[i] = 0;
-      (&c->es[0][0])[i] = 0;
-    }
-    for (int i = threadIdx.x; i < (kMaxChunk + 2) * 5 * kSeg; i += blockDim.x)
-      (&c->ds[0][0][0])[i] = 0;
-    if (threadIdx.x == 0) c->n_src = c->n;
-    return;
-  }
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   switch (op) {
+    case SETUP_CHUNK:
+      c->n_src = c->n;
+      break;
     case SETUP_AFTER_REGEN:
       c->n = c->regen_total;
       c->n_base = c->regen_total;
@@ -69,7 +62,6 @@ __global__ void k_setup(Counters* c, int op, unsigned long long a,
       c->base_pid = 0;
       break;
     case SETUP_BOOT:
-      for (int s = 0; s < kSeg; ++s) c->recs[s] = 0;
       for (int s = 0; s < 2; ++s) {
         c->boot_n[s] = c->boot_w[s] = c->boot_keep[s] = c->boot_nr[s] = 0;
         c->boot_R[s] = 0;
@@ -255,45 +247,36 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 // a = floor(|w| 2^31); N^s and W^s = sum a were tallied with the records.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t* rec_cell,
-                                                     const uint32_t* rec_a, long long rseg,
+                                                     const uint32_t* rec_a, const unsigned* rcnt,
+                                                     int nseg, long long rseg,
                                                      int* keep0, int* keep1,
                                                      unsigned long long* res0,
                                                      unsigned long long* res1) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
-  __shared__ unsigned long long pre[kSeg + 1];  // records are in kSeg segments
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int s = 0; s < kSeg; ++s) {
-      pre[s] = run;
-      run += min(c->recs[s], (unsigned long long)rseg);
-    }
-    pre[kSeg] = run;
-  }
-  __syncthreads();
-  const unsigned long long n = pre[kSeg];
   double ratio[2];
   for (int s = 0; s < 2; ++s)
     ratio[s] = c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
   unsigned long long ks[2] = {0, 0};
-  for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * kBlock) {
-    int lo = 0, hi = kSeg - 1;  // segment of record i
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (pre[mid] <= i) lo = mid; else hi = mid - 1;
+  // records sit in one segment per producer warp; a warp takes a segment
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kBlock) >> 5;
+  for (long long sg = gw; sg < nseg; sg += nw) {
+    const unsigned n = min(rcnt[sg], (unsigned)rseg);
+    for (unsigned i = lane; i < n; i += 32) {
+      const long long ri = sg * rseg + i;
+      const uint32_t rc = rec_cell[ri];
+      const int side = rc >> 31;
+      const uint32_t cell = rc & 0x7FFFFFFFu;
+      const double q = __dmul_rn((double)rec_a[ri], ratio[side]);
+      const double fl = floor(q);
+      const unsigned long long res =
+          (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
+      const int kf = (int)fl;
+      if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
+      if (res) atomicAdd((side ? res1 : res0) + cell, res);
+      ks[side] += (unsigned long long)kf;
     }
-    const long long ri = (long long)lo * rseg + (long long)(i - pre[lo]);
-    const uint32_t rc = rec_cell[ri];
-    const int side = rc >> 31;
-    const uint32_t cell = rc & 0x7FFFFFFFu;
-    const double q = __dmul_rn((double)rec_a[ri], ratio[side]);
-    const double fl = floor(q);
-    const unsigned long long res =
-        (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
-    const int kf = (int)fl;
-    if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
-    if (res) atomicAdd((side ? res1 : res0) + cell, res);
-    ks[side] += (unsigned long long)kf;
   }
   for (int s = 0; s < 2; ++s) {
     unsigned long long t;
@@ -413,7 +396,7 @@ int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
 }  // namespace
 
 cudaError_t launch_setup(Ctx* c, int op, unsigned long long a, unsigned long long b) {
-  k_setup<<<1, kBlock, 0, c->stream>>>(c->cnt, op, a, b);
+  k_setup<<<1, 32, 0, c->stream>>>(c->cnt, op, a, b);
   c->launches++;
   return cudaGetLastError();
 }
@@ -439,7 +422,7 @@ cudaError_t launch_boot(Ctx* c) {
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
   const unsigned long long epoch = (unsigned long long)c->epoch;
   const int g = grid_cap(c, 8);
-  k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rec_cap / kSeg,
+  k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg,
                                           c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
                                           c->boot_res[1]);
   c->launches++;

@@ -16,11 +16,11 @@
 //           DST_BIN1   signed histogram c_nu (Eq. signed_histogram)
 //           DST_BIN2   (cell, |w| in Q1.31) records for the sp2 bootstrap
 //           DST_WSUM   signed weights per cell in Q1.31 (observables)
-// Offspring that live into a later interval are staged in the warp's shared
-// memory and appended to one of kSeg queue segments with one atomic per warp
-// iteration.  The next wave, a launch of the same kernel with SRC_QUEUE,
-// carries them on.  No barrier is taken inside the main loop: each warp owns
-// its 32 slots per iteration.
+// Candidate intervals go to k_event and its follow-up passes (one event per
+// lane per pass).  Offspring that live into a later interval are appended to
+// the next wave, a launch of k_flight with SRC_QUEUE.  Every queue has one
+// private segment per producer warp, so appending takes no global atomic,
+// and no barrier is taken inside any main loop.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -106,7 +106,8 @@ struct P32 {
 };
 
 template <class T>
-struct FEntry {  // offspring waiting at the start of interval l
+struct FEntry {  // a particle at the start of interval l (offspring waves),
+                 // or a candidate interval l with x at its start
   unsigned long long pid;
   T x, k, w;
   int l;
@@ -117,13 +118,25 @@ static_assert(sizeof(FEntry<double>) == 40 && sizeof(FEntry<float>) == 24, "FEnt
 template <class P>
 struct SEntry;
 
+constexpr int kLevels = 5;  // deferred segments: levels 1..3 in passes, 4 drained
+
 // Kernel parameters (by value, parameter space).
+//
+// Queues.  Every queue is split into one private segment per producer warp
+// (nseg segments of *seg entries; warp g of any producing kernel owns
+// segment g).  A producing warp keeps its running count in shared memory and
+// writes it back once at the end of the kernel, so no global atomic is ever
+// taken to append.  Kernels of one round that feed the same queue run one
+// after the other and continue each other's counts.  Consumers walk the
+// segments one warp at a time.
 template <class P>
 struct KP {
   using T = typename P::T;
   T dt, dtv, hm, gamma0, cacc, sig_k, xc;
   T xmin, kmin, kmax, dx, dk, inv_dx, inv_dk;
   int nx, nk;
+  float inv_nk;     // 1/nk, for cell -> (ix, ik)
+  int nh_big;       // nx nk >= 2^24: use an integer division instead
   double p_hi;      // FP64: u0 < p_hi may start an event in the interval
   float p_any_f;    // FP32: P(candidate) per interval
   unsigned p16;     // FP32: floor(65536 p_any)
@@ -138,21 +151,27 @@ struct KP {
   T* w;
   long long capacity;
   unsigned long long* cpid;
-  FEntry<T>* fq_in;
-  FEntry<T>* fq_out;
-  long long qseg;   // entries per queue segment
-  FEntry<T>* eq;    // candidate intervals: x at the interval's start, l
-  long long eseg;   // entries per event-queue segment
-  SEntry<P>* dq[2]; // deferred segments (levels alternate between the two)
-  long long dseg;   // entries per deferred-queue segment
+  int nseg;                  // segments per queue (producer warps)
+  FEntry<T>* fq_in;          // offspring of the previous wave
+  const unsigned* fcnt_in;
+  FEntry<T>* fq_out;         // offspring for the next wave
+  unsigned* fcnt_out;
+  long long qseg;
+  FEntry<T>* eq;             // candidate intervals
+  unsigned* ecnt;
+  long long eseg;
+  SEntry<P>* dq[2];          // deferred segments; level L lives in dq[L & 1]
+  unsigned* dcnt;            // kLevels x nseg counts
+  long long dseg;
+  uint32_t* rec_cell;        // sp2 records (cell | side << 31, |w| in Q1.31)
+  uint32_t* rec_a;
+  unsigned* rcnt;
+  long long rseg;
   int* grid;
   long long* wsum;
-  uint32_t* rec_cell;
-  uint32_t* rec_a;
-  long long rseg;   // records per record segment
   const uint32_t* nz_cell;
   const unsigned long long* nz_start;
-  const uint32_t* tile_nz;  // first nonzero cell of each 32-slot tile
+  const uint32_t* tile_nz;   // first nonzero cell of each 32-slot tile
   long long tile_cap;
   Counters* cnt;
   wbrw_event* log;
@@ -161,8 +180,7 @@ struct KP {
 };
 
 constexpr int kWarps = kBlock / 32;
-constexpr int kWStage = 64;   // staged offspring per warp iteration
-constexpr int kStack = 32;    // pending offspring frames per thread
+constexpr int kStack = 32;    // pending offspring frames per thread (drain)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Per-thread tallies, reduced once per block at the end of a kernel.
@@ -175,12 +193,9 @@ struct Acc {
   }
 };
 
-// Offspring staged by one warp of the event kernel before they are appended
-// to a queue segment with a single atomic.
-template <class T>
-struct WarpStage {
-  FEntry<T> e[kWStage];
-  int n;
+// A warp's running counts in the queues it produces into.
+struct WarpCounts {
+  unsigned f, e, d, r;
 };
 
 // ---------------------------------------------------------------------------
@@ -188,6 +203,10 @@ struct WarpStage {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void set_err(Counters* c, int bit) {
   atomicOr(&c->err, bit);
+}
+
+__device__ __forceinline__ unsigned long long global_warp() {
+  return (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
 }
 
 template <class P>
@@ -201,8 +220,9 @@ __device__ __forceinline__ bool cell_of(const KP<P>& p, typename P::T x,
   return true;
 }
 
+// Sum of one value over the block, added to a global counter by one thread.
 __device__ __forceinline__ void block_reduce_add(unsigned long long* red, unsigned long long v,
-                                 unsigned long long* dst) {
+                                                 unsigned long long* dst) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
@@ -216,36 +236,30 @@ __device__ __forceinline__ void block_reduce_add(unsigned long long* red, unsign
   }
 }
 
-// Segment of the queues and record buffers a warp appends to: spreading the
-// appends over kSeg counters keeps any one counter's atomics rare.
-__device__ __forceinline__ int my_segment() {
-  return (int)((blockIdx.x * kWarps + (threadIdx.x >> 5)) & (kSeg - 1));
+template <class P>
+__device__ __forceinline__ void load_counts(const KP<P>& p, WarpCounts& wc, int level_out) {
+  const unsigned long long g = global_warp();
+  if ((threadIdx.x & 31) == 0) {
+    const bool own = g < (unsigned long long)p.nseg;
+    wc.f = own && p.fcnt_out ? p.fcnt_out[g] : 0u;
+    wc.e = own && p.ecnt ? p.ecnt[g] : 0u;
+    wc.d = own && level_out > 0 ? p.dcnt[(long long)level_out * p.nseg + g] : 0u;
+    wc.r = own && p.rcnt ? p.rcnt[g] : 0u;
+  }
+  __syncwarp();
 }
 
-// Block-wide prefix of kSeg segment lengths (clamped to the segment size).
-__device__ __forceinline__ unsigned long long load_segments(unsigned long long* pre, const unsigned long long* len,
-                                            long long seg_cap) {
-  if (threadIdx.x == 0) {
-    unsigned long long run = 0;
-    for (int s = 0; s < kSeg; ++s) {
-      pre[s] = run;
-      run += min(len[s], (unsigned long long)seg_cap);
-    }
-    pre[kSeg] = run;
+template <class P>
+__device__ __forceinline__ void store_counts(const KP<P>& p, const WarpCounts& wc, int level_out,
+                                             bool f, bool e, bool r) {
+  __syncwarp();
+  const unsigned long long g = global_warp();
+  if ((threadIdx.x & 31) == 0 && g < (unsigned long long)p.nseg) {
+    if (f && p.fcnt_out) p.fcnt_out[g] = wc.f;
+    if (e && p.ecnt) p.ecnt[g] = wc.e;
+    if (level_out > 0) p.dcnt[(long long)level_out * p.nseg + g] = wc.d;
+    if (r && p.rcnt) p.rcnt[g] = wc.r;
   }
-  __syncthreads();
-  return pre[kSeg];
-}
-
-// Index in the segmented buffer of the i-th entry overall.
-__device__ __forceinline__ long long segmented_index(const unsigned long long* pre,
-                                                     unsigned long long i, long long seg_cap) {
-  int lo = 0, hi = kSeg - 1;  // last s with pre[s] <= i
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (pre[mid] <= i) lo = mid; else hi = mid - 1;
-  }
-  return (long long)lo * seg_cap + (long long)(i - pre[lo]);
 }
 
 // ---------------------------------------------------------------------------
@@ -345,8 +359,10 @@ struct Draw<P32> {
 // ---------------------------------------------------------------------------
 template <class P>
 __device__ __forceinline__ uint32_t q131(typename P::T w) {
-  // |w| in Q1.31 (|w| <= 1): floor(|w| 2^31), exact in FP64
-  return (uint32_t)floor(fabs((double)w) * 2147483648.0);
+  // |w| in Q1.31 (|w| <= 1): floor(|w| 2^31); scaling by 2^31 is exact in
+  // either precision and the conversion truncates
+  if constexpr (P::is64) return (uint32_t)floor(fabs(w) * 2147483648.0);
+  else return (uint32_t)(fabsf(w) * 2147483648.0f);
 }
 
 template <class P>
@@ -368,8 +384,9 @@ __device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long i
 
 // An end-of-chunk state produced inside the divergent event code.
 template <class P, int DST>
-__device__ void emit_child_final(const KP<P>& p, Acc& acc, unsigned long long pid,
-                                 typename P::T x, typename P::T k, typename P::T w) {
+__device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc,
+                                 unsigned long long pid, typename P::T x, typename P::T k,
+                                 typename P::T w) {
   using T = typename P::T;
   int cell;
   if constexpr (DST == DST_BIN1) {
@@ -382,10 +399,13 @@ __device__ void emit_child_final(const KP<P>& p, Acc& acc, unsigned long long pi
   } else if constexpr (DST == DST_BIN2) {
     if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
     if (w == (T)0) return;
-    const int seg = my_segment();
-    const unsigned long long r = atomicAdd(&p.cnt->recs[seg], 1ull);
-    if (r >= (unsigned long long)p.rseg) { set_err(p.cnt, ERR_CAP_RECORDS); return; }
-    put_record<P>(p, acc, (long long)seg * p.rseg + (long long)r, cell, w);
+    const unsigned long long g = global_warp();
+    const unsigned r = atomicAdd(&wc.r, 1u);
+    if (g >= (unsigned long long)p.nseg || r >= (unsigned long long)p.rseg) {
+      set_err(p.cnt, ERR_CAP_RECORDS);
+      return;
+    }
+    put_record<P>(p, acc, (long long)g * p.rseg + (long long)r, cell, w);
   } else {  // DST_ARRAY
     const unsigned long long slot = atomicAdd(&p.cnt->n, 1ull);
     if (slot >= (unsigned long long)p.capacity) { set_err(p.cnt, ERR_CAP_PARTICLES); return; }
@@ -404,7 +424,7 @@ __device__ void emit_child_final(const KP<P>& p, Acc& acc, unsigned long long pi
 // follow the same path: each pass performs ONE event of each of its
 // segments; a segment with another event left in the interval, and an
 // offspring born with an event of its own, are deferred to the next pass.
-// Offspring with no event left are settled at once: staged for the next
+// Offspring with no event left are settled at once: appended to the next
 // wave, or sent to the sink in the chunk's last interval.  After the last
 // pass a drain kernel finishes whatever remains with a full recursion.
 // ---------------------------------------------------------------------------
@@ -421,12 +441,11 @@ struct SEntry {  // a deferred segment, with the time and index of its next even
 static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
 
 constexpr unsigned kRootFlag = 0x80000000u;
-constexpr int kLevels = 5;  // deferred segments: levels 1..3 in passes, 4 drained
 
 // An offspring's state at the end of interval l: the next wave's input, or
 // the sink's in the chunk's last interval.
 template <class P, int DST>
-__device__ __forceinline__ void settle(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
+__device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
                                        unsigned long long pid, typename P::T xo,
                                        typename P::T to, typename P::T k, typename P::T w,
                                        int l) {
@@ -439,28 +458,25 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpStage<typename P::T>&
     e.k = k;
     e.w = w;
     e.l = l + 1;
-    const int pos = atomicAdd(&ws.n, 1);
-    if (pos < kWStage) {
-      ws.e[pos] = e;
-    } else {  // rare: the warp's stage is full, append on our own
-      const int seg = my_segment();
-      const unsigned long long q = atomicAdd(&p.cnt->qs[p.round + 1][seg], 1ull);
-      if (q < (unsigned long long)p.qseg) p.fq_out[(long long)seg * p.qseg + (long long)q] = e;
-      else set_err(p.cnt, ERR_CAP_QUEUE);
-    }
+    const unsigned long long g = global_warp();
+    const unsigned q = atomicAdd(&wc.f, 1u);
+    if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.qseg)
+      p.fq_out[(long long)g * p.qseg + (long long)q] = e;
+    else
+      set_err(p.cnt, ERR_CAP_QUEUE);
   } else {
-    emit_child_final<P, DST>(p, acc, pid, xf, k, w);
+    emit_child_final<P, DST>(p, wc, acc, pid, xf, k, w);
   }
 }
 
-// Append a segment to the deferred level `level` (one atomic per entry:
-// deferred segments are a few per cent of the events).
+// Append a segment to the deferred level `level` (the one the kernel feeds).
 template <class P>
-__device__ __forceinline__ void defer(const KP<P>& p, int level, const SEntry<P>& s) {
-  const int seg = my_segment();
-  const unsigned long long q = atomicAdd(&p.cnt->ds[p.round][level][seg], 1ull);
-  if (q < (unsigned long long)p.dseg)
-    p.dq[level & 1][(long long)seg * p.dseg + (long long)q] = s;
+__device__ __forceinline__ void defer(const KP<P>& p, WarpCounts& wc, int level,
+                                      const SEntry<P>& s) {
+  const unsigned long long g = global_warp();
+  const unsigned q = atomicAdd(&wc.d, 1u);
+  if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.dseg)
+    p.dq[level & 1][(long long)g * p.dseg + (long long)q] = s;
   else
     set_err(p.cnt, ERR_CAP_EQUEUE);
 }
@@ -470,10 +486,10 @@ __device__ __forceinline__ void defer(const KP<P>& p, int level, const SEntry<P>
 // or, when they have an event of their own in the interval, handed to
 // `later`.  Returns the gap to the segment's next event.
 template <class P, int DST, class Later>
-__device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpStage<typename P::T>& ws,
-                                                  Acc& acc, unsigned long long pid,
-                                                  typename P::T xo, typename P::T to,
-                                                  typename P::T k, typename P::T w,
+__device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpCounts& wc, Acc& acc,
+                                                  unsigned long long pid, typename P::T xo,
+                                                  typename P::T to, typename P::T k,
+                                                  typename P::T w,
                                                   const typename Draw<P>::State& st, int l,
                                                   unsigned j, typename P::T t, Later later) {
   using T = typename P::T;
@@ -491,10 +507,10 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpStage<type
     const T kp = P::add(k, kap), km = P::sub(k, kap);
     const bool kill_p = !(kp >= p.kmin && kp < p.kmax);
     const bool kill_m = !(km >= p.kmin && km < p.kmax);
-    const T wc = p.strategy == 1 ? w : P::mul(w, fac);
+    const T wc_ = p.strategy == 1 ? w : P::mul(w, fac);
     ++acc.events;
-    if (kill_p) { if (wc > (T)0) ++acc.kill_p; else if (wc < (T)0) ++acc.kill_m; }
-    if (kill_m) { if (-wc > (T)0) ++acc.kill_p; else if (-wc < (T)0) ++acc.kill_m; }
+    if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
+    if (kill_m) { if (-wc_ > (T)0) ++acc.kill_p; else if (-wc_ < (T)0) ++acc.kill_m; }
     if (p.log) {
       const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
       if (idx < (unsigned long long)p.log_cap) {
@@ -521,12 +537,12 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpStage<type
       ch.xo = xe;
       ch.to = t;
       ch.k = c == 0 ? kp : km;
-      ch.w = c == 0 ? wc : -wc;
+      ch.w = c == 0 ? wc_ : -wc_;
       ch.l = l;
       ch.j = 0;
       ch.t = Draw<P>::first(p, ch.pid, l, t, false, ch.st);
       if (ch.t < p.dt) later(ch);
-      else settle<P, DST>(p, ws, acc, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
+      else settle<P, DST>(p, wc, acc, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
     }
   }
   return gap;
@@ -534,8 +550,7 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpStage<type
 
 // All remaining events of a deferred segment, recursively (drain).
 template <class P, int DST>
-__device__ void finish_segment(const KP<P>& p, WarpStage<typename P::T>& ws, Acc& acc,
-                               const SEntry<P>& s0) {
+__device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const SEntry<P>& s0) {
   SEntry<P> stack[kStack];
   int sp = 0;
   stack[sp++] = s0;
@@ -547,267 +562,275 @@ __device__ void finish_segment(const KP<P>& p, WarpStage<typename P::T>& ws, Acc
       else set_err(p.cnt, ERR_NESTING);
     };
     while (s.t < p.dt) {
-      const typename P::T gap = do_event<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
-                                                 s.l, j, s.t, later);
+      const typename P::T gap =
+          do_event<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, j, s.t, later);
       s.t = P::add(s.t, gap);
       ++j;
     }
-    if (!(s.j & kRootFlag)) settle<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
+    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
   }
-}
-
-// Append the warp's staged offspring to its queue segment (whole warp).
-template <class P>
-__device__ void flush_stage(const KP<P>& p, WarpStage<typename P::T>& ws) {
-  __syncwarp();
-  const int lane = threadIdx.x & 31;
-  const int n = min(ws.n, kWStage);
-  if (n > 0) {
-    const int seg = my_segment();
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.cnt->qs[p.round + 1][seg], (unsigned long long)n);
-    base = __shfl_sync(kFull, base, 0);
-    for (int i = lane; i < n; i += 32) {
-      const unsigned long long q = base + i;
-      if (q < (unsigned long long)p.qseg) p.fq_out[(long long)seg * p.qseg + (long long)q] = ws.e[i];
-      else set_err(p.cnt, ERR_CAP_QUEUE);
-    }
-  }
-  __syncwarp();
-  if (lane == 0) ws.n = 0;
-  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// The flight kernel.  Warp-centric: each warp owns 32 consecutive slots per
-// iteration and never waits for the other warps of its block.  It carries
-// every particle through [ls, L) -- streaming plus the candidate clock -- and
-// leaves the rare candidate intervals to k_event: each becomes one entry
-// (pid, x at the interval's start, k, w, l) of the segmented event queue, so
-// that the event kernel runs with every lane busy.
+// The flight kernel.  Warp-centric: a warp carries 32 particles at a time
+// and never waits for the other warps of its block.  Every particle goes
+// through [ls, L) -- streaming plus the candidate clock -- and ends in the
+// sink.  The rare candidate intervals become entries (pid, x at the
+// interval's start, k, w, l) of the warp's segment of the candidate queue,
+// for k_event.
 // ---------------------------------------------------------------------------
 template <class P, int SRC, int DST>
-__global__ void __launch_bounds__(kBlock, 4) k_flight(const KP<P> p) {
+__device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
+                                            unsigned long long slot, typename P::T x,
+                                            typename P::T k, typename P::T w,
+                                            unsigned long long pid, int ls) {
   using T = typename P::T;
-  __shared__ unsigned long long pre[kSeg + 1];
-  __shared__ unsigned long long red[kWarps];
   const int lane = threadIdx.x & 31;
-  const int wid = threadIdx.x >> 5;
-  Acc acc;
-  acc.zero();
+  const unsigned long long g = global_warp();
 
-  unsigned long long n;
-  if constexpr (SRC == SRC_ARRAY) {
-    n = p.cnt->n_src;
-  } else if constexpr (SRC == SRC_REGEN) {
-    n = min(p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
-  } else {
-    n = load_segments(pre, p.cnt->qs[p.round], p.qseg);
-  }
-  const unsigned long long n_base = p.cnt->n_base, base_pid = p.cnt->base_pid;
-  const unsigned long long nz = (SRC == SRC_REGEN) ? p.cnt->nz_count : 0ull;
-  const int seg = my_segment();
-
-  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + wid;
-  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
-  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
-    const unsigned long long slot = base + lane;
-    const bool act = slot < n;
-    T x = (T)0, k = (T)0, w = (T)0;
-    unsigned long long pid = 0;
-    int ls = p.L;
-
-    if constexpr (SRC == SRC_REGEN) {
-      // Alg. 3: the cell of each slot.  The tile's first nonzero cell comes
-      // from the plan; the 32 slots of a tile lie in at most 32 nonzero
-      // cells, searched with shuffles.
-      const unsigned long long a0 = p.tile_nz[base >> 5];
-      const unsigned long long idx = a0 + lane;
-      const unsigned long long st = idx < nz ? p.nz_start[idx] : ~0ull;
-      const uint32_t cw = idx < nz ? p.nz_cell[idx] : 0u;
-      int lo = 0, hi = 31;  // last i with start_i <= slot
-#pragma unroll
-      for (int it = 0; it < 5; ++it) {
-        const int mid = (lo + hi + 1) >> 1;
-        const unsigned long long sv = __shfl_sync(kFull, st, mid);
-        if (sv <= slot) lo = mid; else hi = mid - 1;
-      }
-      const uint32_t cwl = __shfl_sync(kFull, cw, lo);
-      if (act) {
-        const int cell = (int)(cwl & 0x7FFFFFFFu);
-        const int ix = cell / p.nk, ik = cell - ix * p.nk;
-        pid = p.regen_base | slot;
-        const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
-        T ux, uk;
-        if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
-        else { ux = (T)u24(r.x); uk = (T)u24(r.y); }
-        x = P::add(p.xmin, P::mul(P::add((T)ix, ux), p.dx));
-        k = P::add(p.kmin, P::mul(P::add((T)ik, uk), p.dk));
-        // move by single ulps back into the cell if rounding left it
-        for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) > (T)ix; ++it) x = P::next_dn(x);
-        for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) < (T)ix; ++it) x = P::next_up(x);
-        for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) > (T)ik; ++it) k = P::next_dn(k);
-        for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) < (T)ik; ++it) k = P::next_up(k);
-        w = (cwl >> 31) ? (T)-1 : (T)1;
-        ls = p.l0;
-      }
-    } else if constexpr (SRC == SRC_ARRAY) {
-      if (act) {
-        x = p.x[slot];
-        k = p.k[slot];
-        w = p.w ? p.w[slot] : (T)p.s[slot];
-        pid = slot < n_base ? base_pid + slot : p.cpid[slot - n_base];
-        ls = p.l0;
+  // ---- candidate clock over [ls, L) (Sec. 3.2): which intervals hold an
+  // event.  Bit b of mask is interval l0 + b.
+  const T x_start = x;
+  unsigned mask = 0;
+  const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
+  if (act) {
+    if constexpr (P::is64) {
+      for (int l = ls; l < p.L; ++l) {
+        const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
+        if (u53(r.x, r.y) < p.p_hi) mask |= 1u << (l - p.l0);
       }
     } else {
-      if (act) {
-        const FEntry<T> e = p.fq_in[segmented_index(pre, slot, p.qseg)];
-        x = e.x;
-        k = e.k;
-        w = e.w;
-        pid = e.pid;
-        ls = e.l;
-      }
-    }
-
-    // ---- flight over [ls, L): streaming plus the candidate clock -------
-    const T x_start = x;
-    unsigned mask = 0;
-    if (act) {
-      const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
-      if constexpr (P::is64) {
-        for (int l = ls; l < p.L; ++l) {
-          const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
-          if (u53(r.x, r.y) < p.p_hi) mask |= 1u << (l - p.l0);
-          x = P::stream(x, k, p.dtv);
-        }
-      } else {
-        // eight 16-bit coins per Philox call, for the intervals 8b .. 8b+7
-        for (int b = ls >> 3; (b << 3) < p.L; ++b) {
-          const uint4 q = philox_ks(p.ks, plo, phi, (uint32_t)b, kDrawCoins);
-          const uint32_t wv[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int l = (b << 3) + jj;
-            if (l >= ls && l < p.L) {
-              const uint32_t coin = (jj & 1) ? (wv[jj >> 1] >> 16) : (wv[jj >> 1] & 0xFFFFu);
-              bool cand = coin < p.p16;
-              if (coin == p.p16) {  // tie: refine with 8 more bits
-                const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
-                cand = (r.w & 0xFFu) < p.p16_frac8;
-              }
-              if (cand) mask |= 1u << (l - p.l0);
-              x = P::stream(x, k, p.dtv);
-            }
+      // eight 16-bit coins per Philox call for the intervals 8b .. 8b+7,
+      // compared two at a time against floor(65536 p_any)
+      const unsigned thr = p.p16 | (p.p16 << 16);
+      for (int b = ls >> 3; (b << 3) < p.L; ++b) {
+        const uint4 q = philox_ks(p.ks, plo, phi, (uint32_t)b, kDrawCoins);
+        const unsigned c0 = __vcmpltu2(q.x, thr), c1 = __vcmpltu2(q.y, thr);
+        const unsigned c2 = __vcmpltu2(q.z, thr), c3 = __vcmpltu2(q.w, thr);
+        unsigned hit = (c0 & 1u) | ((c0 >> 15) & 2u) | ((c1 & 1u) << 2) | ((c1 >> 13) & 8u) |
+                       ((c2 & 1u) << 4) | ((c2 >> 11) & 32u) | ((c3 & 1u) << 6) |
+                       ((c3 >> 9) & 128u);
+        const unsigned e0 = __vcmpeq2(q.x, thr), e1 = __vcmpeq2(q.y, thr);
+        const unsigned e2 = __vcmpeq2(q.z, thr), e3 = __vcmpeq2(q.w, thr);
+        if ((e0 | e1 | e2 | e3) != 0u) {  // a tie: refine with 8 more bits
+          const unsigned tie = (e0 & 1u) | ((e0 >> 15) & 2u) | ((e1 & 1u) << 2) |
+                               ((e1 >> 13) & 8u) | ((e2 & 1u) << 4) | ((e2 >> 11) & 32u) |
+                               ((e3 & 1u) << 6) | ((e3 >> 9) & 128u);
+          for (unsigned t = tie; t; t &= t - 1) {
+            const int jj = __ffs(t) - 1;
+            const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)((b << 3) + jj), 0u);
+            if ((r.w & 0xFFu) < p.p16_frac8) hit |= 1u << jj;
           }
         }
+        const int sh = (b << 3) - p.l0;
+        mask |= sh >= 0 ? (hit << sh) : (hit >> (-sh));
       }
-      acc.psteps += (unsigned long long)(p.L - ls);
+      if (p.p16 >= 65536u) mask = ~0u;  // p_any rounds to one: every interval
+      const int lo = ls - p.l0, hi = p.L - p.l0;
+      mask &= (hi >= 32 ? ~0u : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
     }
+    acc.psteps += (unsigned long long)(p.L - ls);
+  }
 
-    // ---- the particle's own final state --------------------------------
-    if constexpr (DST == DST_ARRAY) {
-      if constexpr (SRC == SRC_ARRAY) {
-        if (act) p.x[slot] = x;
-      } else if constexpr (SRC == SRC_REGEN) {
-        if (act && slot >= (unsigned long long)p.capacity) {
-          set_err(p.cnt, ERR_CAP_PARTICLES);
-        } else if (act) {
-          p.x[slot] = x;
-          p.k[slot] = k;
-          p.s[slot] = w > (T)0 ? 1 : -1;
-          if (p.w) p.w[slot] = w;
-        }
-      } else {
-        const unsigned bal = __ballot_sync(kFull, act);
-        unsigned long long off = 0;
-        if (lane == 0 && bal) off = atomicAdd(&p.cnt->n, (unsigned long long)__popc(bal));
-        off = __shfl_sync(kFull, off, 0) + __popc(bal & ((1u << lane) - 1u));
-        if (act) {
-          if (off >= (unsigned long long)p.capacity) {
-            set_err(p.cnt, ERR_CAP_PARTICLES);
-          } else {
-            p.x[off] = x;
-            p.k[off] = k;
-            p.s[off] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
-            if (p.w) p.w[off] = w;
-            p.cpid[off - n_base] = pid;
-          }
-        }
-      }
-    } else if constexpr (DST == DST_BIN1) {
-      long long key = -1;
-      if (act) {
-        int cell;
-        if (cell_of<P>(p, x, k, cell)) key = 2ll * cell + (w > (T)0 ? 1 : 0);
-        else tally_out<P>(p, acc, w);
-      }
-      const unsigned grp = __match_any_sync(kFull, (unsigned long long)key);
-      if (key >= 0 && lane == __ffs(grp) - 1)
-        atomicAdd(p.grid + (key >> 1), (key & 1) ? __popc(grp) : -__popc(grp));
-    } else if constexpr (DST == DST_WSUM) {
-      if (act) {
-        int cell;
-        if (cell_of<P>(p, x, k, cell))
-          atomicAdd((unsigned long long*)(p.wsum + cell),
-                    (unsigned long long)llrint((double)w * 2147483648.0));
-      }
-    } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
-      int cell = -1;
-      if (act) {
-        if (!cell_of<P>(p, x, k, cell)) { cell = -1; tally_out<P>(p, acc, w); }
-        else if (w == (T)0) cell = -1;
-      }
-      const unsigned bal = __ballot_sync(kFull, cell >= 0);
-      if (bal) {
-        unsigned long long off = 0;
-        if (lane == 0) off = atomicAdd(&p.cnt->recs[seg], (unsigned long long)__popc(bal));
-        off = __shfl_sync(kFull, off, 0) + __popc(bal & ((1u << lane) - 1u));
-        if (cell >= 0) {
-          if (off >= (unsigned long long)p.rseg) set_err(p.cnt, ERR_CAP_RECORDS);
-          else put_record<P>(p, acc, (long long)seg * p.rseg + (long long)off, cell, w);
-        }
-      }
-    }
-
-    // ---- candidate intervals -> the segmented event queue --------------
-    const unsigned cnt = __popc(mask);
-    unsigned inc = cnt;
+  // ---- offsets of this warp's candidate entries --------------------------
+  const unsigned cnt = __popc(mask);
+  unsigned inc = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned t = __shfl_up_sync(kFull, inc, o);
-      if (lane >= o) inc += t;
-    }
-    const unsigned total = __shfl_sync(kFull, inc, 31);
-    if (total) {
-      unsigned long long q0 = 0;
-      if (lane == 0) q0 = atomicAdd(&p.cnt->es[p.round][seg], (unsigned long long)total);
-      q0 = __shfl_sync(kFull, q0, 0) + (inc - cnt);
-      T xs = x_start;
-      int ll = ls;
-      unsigned m = mask;
-      for (unsigned i = 0; i < cnt; ++i) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int l = p.l0 + b;
-        for (; ll < l; ++ll) xs = P::stream(xs, k, p.dtv);
-        const unsigned long long q = q0 + i;
-        if (q < (unsigned long long)p.eseg) {
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned t = __shfl_up_sync(kFull, inc, o);
+    if (lane >= o) inc += t;
+  }
+  const unsigned total = __shfl_sync(kFull, inc, 31);
+  unsigned q = wc.e + (inc - cnt);
+
+  // ---- free streaming x <- x + (hbar/m) k dt, one rounding per interval;
+  // a candidate interval is entered with x at its start ------------------
+  if (act) {
+    for (int l = ls; l < p.L; ++l) {
+      if ((mask >> (l - p.l0)) & 1u) {
+        if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
           FEntry<T> e;
           e.pid = pid;
-          e.x = xs;
+          e.x = x;
           e.k = k;
           e.w = w;
           e.l = l;
-          p.eq[(long long)seg * p.eseg + (long long)q] = e;
+          p.eq[(long long)g * p.eseg + (long long)q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
         }
+        ++q;
       }
+      x = P::stream(x, k, p.dtv);
+    }
+  }
+  (void)x_start;
+  if (total) {
+    __syncwarp();
+    if (lane == 0) wc.e += total;
+    __syncwarp();
+  }
+
+  // ---- the particle's own final state ----------------------------------
+  if constexpr (DST == DST_ARRAY) {
+    if constexpr (SRC == SRC_ARRAY) {
+      if (act) p.x[slot] = x;
+    } else if constexpr (SRC == SRC_REGEN) {
+      if (act && slot >= (unsigned long long)p.capacity) {
+        set_err(p.cnt, ERR_CAP_PARTICLES);
+      } else if (act) {
+        p.x[slot] = x;
+        p.k[slot] = k;
+        p.s[slot] = w > (T)0 ? 1 : -1;
+        if (p.w) p.w[slot] = w;
+      }
+    } else {
+      const unsigned bal = __ballot_sync(kFull, act);
+      unsigned long long off = 0;
+      if (lane == 0 && bal) off = atomicAdd(&p.cnt->n, (unsigned long long)__popc(bal));
+      off = __shfl_sync(kFull, off, 0) + __popc(bal & ((1u << lane) - 1u));
+      if (act) {
+        if (off >= (unsigned long long)p.capacity) {
+          set_err(p.cnt, ERR_CAP_PARTICLES);
+        } else {
+          p.x[off] = x;
+          p.k[off] = k;
+          p.s[off] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
+          if (p.w) p.w[off] = w;
+          p.cpid[off - p.cnt->n_base] = pid;
+        }
+      }
+    }
+  } else if constexpr (DST == DST_BIN1) {
+    // lanes that hit the same cell with the same sign add once (the key is
+    // 2 cell + sign, or ~0 for none; 2 nx nk < 2^32 is checked on the host)
+    unsigned key = ~0u;
+    if (act) {
+      int cell;
+      if (cell_of<P>(p, x, k, cell)) key = 2u * (unsigned)cell + (w > (T)0 ? 1u : 0u);
+      else tally_out<P>(p, acc, w);
+    }
+    const unsigned grp = __match_any_sync(kFull, key);
+    if (key != ~0u && lane == __ffs(grp) - 1)
+      atomicAdd(p.grid + (key >> 1), (key & 1u) ? __popc(grp) : -__popc(grp));
+  } else if constexpr (DST == DST_WSUM) {
+    if (act) {
+      int cell;
+      if (cell_of<P>(p, x, k, cell))
+        atomicAdd((unsigned long long*)(p.wsum + cell),
+                  (unsigned long long)llrint((double)w * 2147483648.0));
+    }
+  } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
+    int cell = -1;
+    if (act) {
+      if (!cell_of<P>(p, x, k, cell)) { cell = -1; tally_out<P>(p, acc, w); }
+      else if (w == (T)0) cell = -1;
+    }
+    const unsigned bal = __ballot_sync(kFull, cell >= 0);
+    if (bal) {
+      const unsigned off = wc.r + __popc(bal & ((1u << lane) - 1u));
+      if (cell >= 0) {
+        if (g >= (unsigned long long)p.nseg || off >= (unsigned long long)p.rseg)
+          set_err(p.cnt, ERR_CAP_RECORDS);
+        else
+          put_record<P>(p, acc, (long long)g * p.rseg + (long long)off, cell, w);
+      }
+      __syncwarp();
+      if (lane == 0) wc.r += __popc(bal);
+      __syncwarp();
     }
   }
 
-  // ---- tallies ------------------------------------------------------------
+}
+
+template <class P, int SRC, int DST>
+__global__ void __launch_bounds__(kBlock, 4) k_flight(const KP<P> p) {
+  using T = typename P::T;
+  __shared__ unsigned long long red[kWarps];
+  __shared__ WarpCounts s_wc[kWarps];
+  const int lane = threadIdx.x & 31;
+  WarpCounts& wc = s_wc[threadIdx.x >> 5];
+  Acc acc;
+  acc.zero();
+  load_counts(p, wc, 0);
+  const unsigned long long g = global_warp();
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+
+  if constexpr (SRC == SRC_QUEUE) {
+    // the previous wave's offspring, one producer segment at a time
+    for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+      const unsigned n = min(p.fcnt_in[sg], (unsigned)p.qseg);
+      for (unsigned b = 0; b < n; b += 32) {
+        const unsigned i = b + lane;
+        const bool act = i < n;
+        FEntry<T> e;
+        e.pid = 0;
+        e.x = e.k = e.w = (T)0;
+        e.l = p.L;
+        if (act) e = p.fq_in[(long long)sg * p.qseg + i];
+        flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, e.l);
+      }
+    }
+  } else {
+    unsigned long long n;
+    if constexpr (SRC == SRC_ARRAY) n = p.cnt->n_src;
+    else n = min(p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
+    const unsigned long long n_base = p.cnt->n_base, base_pid = p.cnt->base_pid;
+    const unsigned long long nz = (SRC == SRC_REGEN) ? p.cnt->nz_count : 0ull;
+    for (unsigned long long base = g * 32ull; base < n; base += nwarps * 32ull) {
+      const unsigned long long slot = base + lane;
+      const bool act = slot < n;
+      T x = (T)0, k = (T)0, w = (T)0;
+      unsigned long long pid = 0;
+      if constexpr (SRC == SRC_REGEN) {
+        // Alg. 3: the cell of each slot.  The tile's first nonzero cell comes
+        // from the plan; the 32 slots of a tile lie in at most 32 nonzero
+        // cells, searched with shuffles.
+        const unsigned long long a0 = p.tile_nz[base >> 5];
+        const unsigned long long idx = a0 + lane;
+        const unsigned long long st = idx < nz ? p.nz_start[idx] : ~0ull;
+        const uint32_t cw = idx < nz ? p.nz_cell[idx] : 0u;
+        int lo = 0, hi = 31;  // last i with start_i <= slot
+#pragma unroll
+        for (int it = 0; it < 5; ++it) {
+          const int mid = (lo + hi + 1) >> 1;
+          const unsigned long long sv = __shfl_sync(kFull, st, mid);
+          if (sv <= slot) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t cwl = __shfl_sync(kFull, cw, lo);
+        if (act) {
+          const int cell = (int)(cwl & 0x7FFFFFFFu);
+          int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
+          if (p.nh_big) ix = cell / p.nk;
+          int ik = cell - ix * p.nk;
+          if (ik < 0) { --ix; ik += p.nk; } else if (ik >= p.nk) { ++ix; ik -= p.nk; }
+          pid = p.regen_base | slot;
+          const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
+          T ux, uk;
+          if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
+          else { ux = (T)u24(r.x); uk = (T)u24(r.y); }
+          x = P::add(p.xmin, P::mul(P::add((T)ix, ux), p.dx));
+          k = P::add(p.kmin, P::mul(P::add((T)ik, uk), p.dk));
+          // move by single ulps back into the cell if rounding left it
+          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) > (T)ix; ++it) x = P::next_dn(x);
+          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) < (T)ix; ++it) x = P::next_up(x);
+          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) > (T)ik; ++it) k = P::next_dn(k);
+          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) < (T)ik; ++it) k = P::next_up(k);
+          w = (cwl >> 31) ? (T)-1 : (T)1;
+        }
+      } else {
+        if (act) {
+          x = p.x[slot];
+          k = p.k[slot];
+          w = p.w ? p.w[slot] : (T)p.s[slot];
+          pid = slot < n_base ? base_pid + slot : p.cpid[slot - n_base];
+        }
+      }
+      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L);
+    }
+  }
+
+  store_counts(p, wc, 0, false, true, DST == DST_BIN2);
   block_reduce_add(red, acc.psteps, &p.cnt->ledger[SRC == SRC_QUEUE ? LG_PSTEPS : LG_PSTEPS0]);
   block_reduce_add(red, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
   block_reduce_add(red, acc.out_m, &p.cnt->ledger[LG_OUT_M]);
@@ -823,10 +846,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_flight(const KP<P> p) {
 // Event kernels.  k_event takes the candidate intervals of the flight (one
 // per lane) and performs their first event; k_cont performs one more event
 // of each deferred segment of a level; k_drain finishes the last level.
-// Offspring alive at the end of their interval are staged per warp and
-// appended to the next wave's queue segment.
 // ---------------------------------------------------------------------------
-template <class T>
 __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, const Acc& acc,
                                                      Counters* c, bool bin2) {
   block_reduce_add(red, acc.events, &c->ledger[LG_EVENTS]);
@@ -845,106 +865,105 @@ __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, co
 template <class P, int DST>
 __global__ void __launch_bounds__(kBlock, 3) k_event(const KP<P> p) {
   using T = typename P::T;
-  __shared__ WarpStage<T> stage[kWarps];
-  __shared__ unsigned long long pre[kSeg + 1];
   __shared__ unsigned long long red[kWarps];
+  __shared__ WarpCounts s_wc[kWarps];
   const int lane = threadIdx.x & 31;
-  WarpStage<T>& ws = stage[threadIdx.x >> 5];
+  WarpCounts& wc = s_wc[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  if (lane == 0) ws.n = 0;
-  __syncwarp();
-  const unsigned long long n = load_segments(pre, p.cnt->es[p.round], p.eseg);
-  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  load_counts(p, wc, 1);
+  const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
-  auto later = [&](const SEntry<P>& ch) { defer<P>(p, 1, ch); };
-  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
-    const unsigned long long i = base + lane;
-    if (i < n) {
-      const FEntry<T> e = p.eq[segmented_index(pre, i, p.eseg)];
-      SEntry<P> s;
-      s.pid = e.pid;
-      s.xo = e.x;
-      s.to = (T)0;
-      s.k = e.k;
-      s.w = e.w;
-      s.l = e.l;
-      s.t = Draw<P>::first(p, e.pid, e.l, (T)0, true, s.st);
-      if (s.t < p.dt) {
-        const T gap = do_event<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, 0u,
-                                       s.t, later);
-        s.t = P::add(s.t, gap);
+  auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
+  for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+    const unsigned n = min(p.ecnt[sg], (unsigned)p.eseg);
+    for (unsigned b = 0; b < n; b += 32) {
+      const unsigned i = b + lane;
+      if (i < n) {
+        const FEntry<T> e = p.eq[(long long)sg * p.eseg + i];
+        SEntry<P> s;
+        s.pid = e.pid;
+        s.xo = e.x;
+        s.to = (T)0;
+        s.k = e.k;
+        s.w = e.w;
+        s.l = e.l;
+        s.t = Draw<P>::first(p, e.pid, e.l, (T)0, true, s.st);
         if (s.t < p.dt) {
-          s.j = 1u | kRootFlag;
-          defer<P>(p, 1, s);
+          const T gap = do_event<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, 0u,
+                                         s.t, later);
+          s.t = P::add(s.t, gap);
+          if (s.t < p.dt) {
+            s.j = 1u | kRootFlag;
+            defer<P>(p, wc, 1, s);
+          }
         }
       }
     }
-    flush_stage<P>(p, ws);
   }
-  reduce_event_tallies<T>(red, acc, p.cnt, DST == DST_BIN2);
+  store_counts(p, wc, 1, true, false, DST == DST_BIN2);
+  reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
 template <class P, int DST>
 __global__ void __launch_bounds__(kBlock, 3) k_cont(const KP<P> p, int level) {
   using T = typename P::T;
-  __shared__ WarpStage<T> stage[kWarps];
-  __shared__ unsigned long long pre[kSeg + 1];
   __shared__ unsigned long long red[kWarps];
+  __shared__ WarpCounts s_wc[kWarps];
   const int lane = threadIdx.x & 31;
-  WarpStage<T>& ws = stage[threadIdx.x >> 5];
+  WarpCounts& wc = s_wc[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  if (lane == 0) ws.n = 0;
-  __syncwarp();
-  const unsigned long long n = load_segments(pre, p.cnt->ds[p.round][level], p.dseg);
-  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  load_counts(p, wc, level + 1);
+  const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   const SEntry<P>* in = p.dq[level & 1];
-  auto later = [&](const SEntry<P>& ch) { defer<P>(p, level + 1, ch); };
-  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
-    const unsigned long long i = base + lane;
-    if (i < n) {
-      SEntry<P> s = in[segmented_index(pre, i, p.dseg)];
-      const unsigned j = s.j & ~kRootFlag;
-      const T gap = do_event<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, j,
-                                     s.t, later);
-      s.t = P::add(s.t, gap);
-      if (s.t < p.dt) {
-        s.j = (j + 1) | (s.j & kRootFlag);
-        defer<P>(p, level + 1, s);
-      } else if (!(s.j & kRootFlag)) {
-        settle<P, DST>(p, ws, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
+  const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
+  auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, level + 1, ch); };
+  for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+    const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
+    for (unsigned b = 0; b < n; b += 32) {
+      const unsigned i = b + lane;
+      if (i < n) {
+        SEntry<P> s = in[(long long)sg * p.dseg + i];
+        const unsigned j = s.j & ~kRootFlag;
+        const T gap = do_event<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, j,
+                                       s.t, later);
+        s.t = P::add(s.t, gap);
+        if (s.t < p.dt) {
+          s.j = (j + 1) | (s.j & kRootFlag);
+          defer<P>(p, wc, level + 1, s);
+        } else if (!(s.j & kRootFlag)) {
+          settle<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
+        }
       }
     }
-    flush_stage<P>(p, ws);
   }
-  reduce_event_tallies<T>(red, acc, p.cnt, DST == DST_BIN2);
+  store_counts(p, wc, level + 1, true, false, DST == DST_BIN2);
+  reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
 template <class P, int DST>
 __global__ void __launch_bounds__(kBlock, 3) k_drain(const KP<P> p) {
-  using T = typename P::T;
-  __shared__ WarpStage<T> stage[kWarps];
-  __shared__ unsigned long long pre[kSeg + 1];
   __shared__ unsigned long long red[kWarps];
+  __shared__ WarpCounts s_wc[kWarps];
   const int lane = threadIdx.x & 31;
-  WarpStage<T>& ws = stage[threadIdx.x >> 5];
+  WarpCounts& wc = s_wc[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  if (lane == 0) ws.n = 0;
-  __syncwarp();
-  const int level = kLevels - 1;
-  const unsigned long long n = load_segments(pre, p.cnt->ds[p.round][level], p.dseg);
-  const unsigned long long gwarp = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  load_counts(p, wc, 0);
+  const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  const int level = kLevels - 1;
   const SEntry<P>* in = p.dq[level & 1];
-  for (unsigned long long base = gwarp * 32ull; base < n; base += nwarps * 32ull) {
-    const unsigned long long i = base + lane;
-    if (i < n) finish_segment<P, DST>(p, ws, acc, in[segmented_index(pre, i, p.dseg)]);
-    flush_stage<P>(p, ws);
+  const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
+  for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+    const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
+    for (unsigned i = lane; i < n; i += 32)
+      finish_segment<P, DST>(p, wc, acc, in[(long long)sg * p.dseg + i]);
   }
-  reduce_event_tallies<T>(red, acc, p.cnt, DST == DST_BIN2);
+  store_counts(p, wc, 0, true, false, DST == DST_BIN2);
+  reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
 // Initial particles from the Gaussian-wavepacket Wigner function (positive):
@@ -1018,6 +1037,8 @@ KP<P> make_kp(const Ctx* c) {
   p.inv_dk = (T)c->inv_dk;
   p.nx = g.nx;
   p.nk = g.nk;
+  p.inv_nk = 1.0f / (float)g.nk;
+  p.nh_big = (long long)g.nx * g.nk >= (1ll << 24);
   p.p_hi = c->p_any * (1.0 + 1e-9) + 1e-300;
   p.p_any_f = (float)c->p_any;
   const double sc = c->p_any * 65536.0;
@@ -1038,19 +1059,27 @@ KP<P> make_kp(const Ctx* c) {
   p.w = g.strategy == WBRW_SP2_BOOTSTRAP ? (T*)c->buf.w : nullptr;
   p.capacity = c->buf.capacity;
   p.cpid = c->cpid;
+  p.nseg = c->nseg;
   p.fq_in = (FEntry<T>*)c->fq[0];
+  p.fcnt_in = c->fcnt[0];
   p.fq_out = (FEntry<T>*)c->fq[1];
-  p.qseg = c->qcap / kSeg;
+  p.fcnt_out = c->fcnt[1];
+  p.qseg = c->qseg;
   p.eq = (FEntry<T>*)c->eq;
-  p.eseg = c->ecap / kSeg;
+  p.ecnt = c->ecnt;
+  p.eseg = c->eseg;
   p.dq[0] = (SEntry<P>*)c->dq[0];
   p.dq[1] = (SEntry<P>*)c->dq[1];
-  p.dseg = c->dcap / kSeg;
+  p.dcnt = c->dcnt;
+  p.dseg = c->dseg;
+  p.rec_cell = c->rec_cell;
+  p.rec_a = c->rec_a;
+  p.rcnt = c->cfg.strategy == WBRW_SP2_BOOTSTRAP ? c->rcnt : nullptr;
+  p.rseg = c->rseg;
   p.grid = c->buf.grid;
   p.wsum = c->tmp_wsum;
   p.rec_cell = c->rec_cell;
   p.rec_a = c->rec_a;
-  p.rseg = c->rec_cap / kSeg;
   p.nz_cell = c->nz_cell;
   p.nz_start = c->nz_start;
   p.tile_nz = c->tile_nz;
@@ -1062,13 +1091,18 @@ KP<P> make_kp(const Ctx* c) {
   return p;
 }
 
+// Grids hold at most kMaxBlocksPerSm resident blocks per SM: every producer
+// warp owns a queue segment, and there are nseg of them.
 template <class K>
 int grid_for(Ctx* c, K kern) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  return per_sm * c->num_sms;
+  if (per_sm > kMaxBlocksPerSm) per_sm = kMaxBlocksPerSm;
+  int g = per_sm * c->num_sms;
+  if (g * kWarps > c->nseg) g = c->nseg / kWarps;
+  return g;
 }
 
 template <class P, int SRC, int DST>
@@ -1149,15 +1183,21 @@ struct DriverImpl {
     p.l0 = l0;
     p.L = L;
     const int rounds = L > l0 ? L - l0 : 1;
+    const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
     for (int r = 0; r < rounds; ++r) {
       p.round = r;
       p.fq_in = (FEntry<typename P::T>*)c->fq[r & 1];
+      p.fcnt_in = c->fcnt[r & 1];
       p.fq_out = (FEntry<typename P::T>*)c->fq[(r + 1) & 1];
+      p.fcnt_out = c->fcnt[(r + 1) & 1];
+      if ((e = launch_zero(c, c->ecnt, cnt_bytes)) != cudaSuccess) return e;
       if (r == 0) prof_begin(c);
       e = flight_any<P>(c, p, r == 0 ? src : (int)SRC_QUEUE, dst);
       if (r == 0) prof_end(c);
       if (e != cudaSuccess) return e;
       if (L > l0) {
+        if ((e = launch_zero(c, p.fcnt_out, cnt_bytes)) != cudaSuccess) return e;
+        if ((e = launch_zero(c, c->dcnt, kLevels * cnt_bytes)) != cudaSuccess) return e;
         e = events_any<P>(c, p, dst);
         if (e != cudaSuccess) return e;
       }

@@ -13,7 +13,8 @@ constexpr int kBlock = 256;      // threads per block of every particle kernel
 constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
 constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
-constexpr int kSeg = 64;         // segments of the offspring queues and records
+constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
+constexpr int kMaxBlocksPerSm = 4;  // resident blocks per SM of producer kernels
 
 enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2 };
 enum Dst { DST_ARRAY = 0, DST_BIN1 = 1, DST_BIN2 = 2, DST_WSUM = 3 };
@@ -37,13 +38,9 @@ struct Counters {
   unsigned long long n_src;        // snapshot of n at the start of a chunk
   unsigned long long n_base;       // slots < n_base have pid = base_pid + slot
   unsigned long long base_pid;
-  unsigned long long qs[kMaxChunk + 2][kSeg];  // F-queue entries, round r, segment
-  unsigned long long es[kMaxChunk + 2][kSeg];  // candidate intervals, round r, segment
-  unsigned long long ds[kMaxChunk + 2][5][kSeg];  // deferred segments, round, level, segment
   unsigned long long nz_count;     // nonzero cells of the last histogram
   unsigned long long regen_total;  // particles implied by the histogram
   unsigned long long log_len;
-  unsigned long long recs[kSeg];   // sp2 records per segment
   unsigned long long ledger[LG_N];
   unsigned long long boot_n[2], boot_w[2], boot_keep[2], boot_nr[2];
   unsigned long long boot_R[2];    // total residual (Q0.32) per side
@@ -65,12 +62,20 @@ struct Ctx {
   // scratch carve-up
   Counters* cnt;
   unsigned long long* cpid;
-  void* fq[2];
-  long long qcap;
-  void* eq;
-  long long ecap;     // candidate-interval queue entries (kSeg segments)
-  void* dq[2];
-  long long dcap;     // deferred-segment queue entries, per buffer
+  // queues, each with one private segment per producer warp: entries per
+  // segment (*seg) and per-segment counts (*cnt)
+  int nseg;
+  void* fq[2];        // offspring waves (double buffered)
+  unsigned* fcnt[2];
+  long long qcap, qseg;
+  void* eq;           // candidate intervals
+  unsigned* ecnt;
+  long long ecap, eseg;
+  void* dq[2];        // deferred segments, levels alternating
+  unsigned* dcnt;     // kLevels x nseg
+  long long dcap, dseg;
+  unsigned* rcnt;     // sp2 records per segment
+  long long rseg;
   int max_chunk;      // steps per flight: about one candidate per particle
   uint32_t* nz_cell;
   unsigned long long* nz_start;
