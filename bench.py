@@ -48,6 +48,8 @@ def parse():
                     choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5"])
     ap.add_argument("--particles", type=float, default=0,
                     help="override the particle count (profiling small cases)")
+    ap.add_argument("--capacity-factor", type=float, default=4.0,
+                    help="particle capacity as a multiple of the particle count")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -201,7 +203,7 @@ def ours(args, wl):
 
     wl = workloads.scaled(wl, seed=wl["seed"] + rank)
     n = int(wl["n_alpha"])
-    cap = int(4.0 * n) + (1 << 20)
+    cap = int(args.capacity_factor * n) + (1 << 20)
     sim = Simulation(wl, capacity=cap)
     stream = sim.stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -260,20 +262,11 @@ def ours(args, wl):
                                          + wl["nx"] * 8 + 16),
                "steps": e2e_steps, "transmission_last": T_last}
 
-    # ---- reduce over ranks
-    t_max = t_ms
-    ps_all = psteps
-    if ws > 1:
-        tt = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        pp = torch.tensor([psteps], dtype=torch.float64, device="cuda")
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        ps_all = float(pp.item())
-        if e2e is not None:
-            ev = torch.tensor([e2e["value"]], dtype=torch.float64, device="cuda")
-            dist.all_reduce(ev, op=dist.ReduceOp.SUM)
-            e2e["value"] = float(ev.item())
+    # ---- reduce over ranks: max time, summed particle-steps and e2e rate
+    t_max, ps_all, e2e_sum = reduce_over_ranks(ws, t_ms, psteps, e2e["value"] if e2e else 0.0,
+                                               "cuda")
+    if e2e is not None:
+        e2e["value"] = e2e_sum
 
     if rank == 0:
         value = ps_all / (t_max / 1e3)
@@ -306,34 +299,57 @@ def ours(args, wl):
     sim.close()
 
 
+def reduce_over_ranks(ws, t_ms, psteps, e2e_value, device):
+    """Whole-job numbers of the replicas: the slowest rank's time, and the
+    particle-steps and end-to-end rates of all ranks summed."""
+    if ws <= 1:
+        return t_ms, psteps, e2e_value
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    sums = torch.tensor([float(psteps), float(e2e_value)], dtype=torch.float64, device=device)
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(sums[0].item()), float(sums[1].item())
+
+
 def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
-    """The dominant kernel is the fused regenerate + flight + histogram pass
-    that carries the particles present at the start of each period (the first
-    wave).  Its work is lane arithmetic: the particle state stays in registers
-    and HBM is touched only for the offspring queue.  Achieved = algorithmic
-    lane-operations per launch (OPS_PER_PSTEP, derived in the design doc, times the
-    first-wave particle-steps of one launch) / the launch's average CUDA-event
-    duration.  Peak = 152 SMs x 128 lanes x the median SM clock sampled during
-    the timed region (one lane-operation per lane per cycle)."""
+    """Roofline of the dominant kernel: the fused regenerate + flight +
+    histogram pass that carries the particles present at the start of each
+    period (the first wave).  The particle state never leaves registers and
+    HBM sees only the candidate queue, so the pass is bound by the integer
+    pipe (Philox4x32-10 is 32-bit multiplies and XORs).
+
+    achieved = INT_OPS_PER_PSTEP (the algorithm's integer operations per
+    first-wave particle-step, derived in the design doc) x the first-wave
+    particle-steps of one launch / the launch's average CUDA-event time.
+    peak = 152 SMs x 64 INT32 lanes x the median SM clock sampled during the
+    timed region (one integer operation per lane per cycle)."""
     if not kern_n or kern_ms <= 0:
         return None
-    ops = OPS_PER_PSTEP[wl["precision"]]
+    ops = INT_OPS_PER_PSTEP[wl["precision"]]
     per_launch_ms = kern_ms / kern_n
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak = 152 * 128 * sm_mhz * 1e6 / 1e12
-    ach = ops * (psteps_first / kern_n) / (per_launch_ms / 1e3) / 1e12
-    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tlane-op/s",
-            "frac": ach / peak, "traffic": None,
+    peak = 152 * 64 * sm_mhz * 1e6 / 1e9
+    ach = ops * (psteps_first / kern_n) / (per_launch_ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
+            "frac": ach / peak, "traffic": TRAFFIC_PER_PSTEP.get(wl["precision"]) and
+            TRAFFIC_PER_PSTEP[wl["precision"]] * psteps_first / kern_n,
             "kernel": "k_flight<%s,regen,bin>" % wl["precision"],
             "launch_ms": per_launch_ms, "launches": kern_n,
             "first_wave_particle_steps_per_launch": psteps_first / kern_n,
-            "ops_per_particle_step": ops,
-            "peak_basis": "152 SM x 128 lanes x %.0f MHz (median SM clock sampled in the "
+            "int_ops_per_particle_step": ops,
+            "peak_basis": "152 SM x 64 INT32 lanes x %.0f MHz (median SM clock sampled in the "
                           "timed region)" % sm_mhz}
 
 
-# algorithmic lane-operations per first-wave particle-step (DESIGN.md, sec. 6)
-OPS_PER_PSTEP = {"fp32": 71.0, "fp64": 150.0}
+# Integer operations per first-wave particle-step of a 10-interval period
+# (DESIGN.md, "Roofline of the first wave"): three Philox4x32-10 calls per
+# particle per period at 100 operations each, the coin tests, the cell decode
+# of the regeneration and the histogram index.
+INT_OPS_PER_PSTEP = {"fp32": 33.6, "fp64": 63.0}
+# DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
+TRAFFIC_PER_PSTEP = {"fp32": 0.83, "fp64": None}
 
 
 def main():
