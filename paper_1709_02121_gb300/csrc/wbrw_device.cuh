@@ -744,7 +744,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
 }
 
 template <class P, int SRC, int DST>
-__global__ void __launch_bounds__(kBlock, 4) k_flight(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> p) {
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -863,7 +863,7 @@ __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, co
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, 3) k_event(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p) {
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_event(const KP<P> p) {
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, 3) k_cont(const KP<P> p, int level) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p, int level) {
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -944,7 +944,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_cont(const KP<P> p, int level) {
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, 3) k_drain(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p) {
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
   const int lane = threadIdx.x & 31;
@@ -1091,8 +1091,9 @@ KP<P> make_kp(const Ctx* c) {
   return p;
 }
 
-// Grids hold at most kMaxBlocksPerSm resident blocks per SM: every producer
-// warp owns a queue segment, and there are nseg of them.
+// Every queue kernel runs exactly kMaxBlocksPerSm resident blocks per SM:
+// producer warp g owns queue segment g and consumer warp g reads it, so equal
+// grids keep the segments matched one to one (nseg of them).
 template <class K>
 int grid_for(Ctx* c, K kern) {
   int per_sm = 0;

@@ -14,7 +14,7 @@ constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
 constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
-constexpr int kMaxBlocksPerSm = 4;  // resident blocks per SM of producer kernels
+constexpr int kMaxBlocksPerSm = 3;  // resident blocks per SM of every queue kernel
 
 enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2 };
 enum Dst { DST_ARRAY = 0, DST_BIN1 = 1, DST_BIN2 = 2, DST_WSUM = 3 };
