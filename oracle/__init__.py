@@ -66,7 +66,8 @@ class _Config(ctypes.Structure):
                 ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
                 ("strategy", ctypes.c_int),
                 ("n_alpha", ctypes.c_longlong),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong),
+                ("instance", ctypes.c_int)]
 
 
 EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"),
@@ -161,9 +162,10 @@ class Oracle:
 
     def __init__(self, *, hbar=1.0, mass=1.0, dt=0.1, gamma0=0.0, H=1.0,
                  w=1.0, xc=0.0, nx=240, nk=128, xmin=-60.0, xmax=60.0,
-                 kmin=-6.4, kmax=6.4, strategy=SP1, n_alpha=200000, seed=0):
+                 kmin=-6.4, kmax=6.4, strategy=SP1, n_alpha=200000, seed=0,
+                 instance=0):
         self.cfg = _Config(hbar, mass, dt, gamma0, H, w, xc, nx, nk, xmin,
-                           xmax, kmin, kmax, strategy, n_alpha, seed)
+                           xmax, kmin, kmax, strategy, n_alpha, seed, instance)
         self.nx, self.nk = nx, nk
         self.n_alpha = n_alpha
         self._s = lib().orc_create(ctypes.byref(self.cfg))

@@ -134,6 +134,7 @@ typedef struct {
   int strategy;                  /* 1 = sp1 (pair generation), 2 = sp2       */
   long long n_alpha;             /* sample size N_alpha of the estimator     */
   unsigned long long seed;
+  int instance;                  /* id salt 0..255: a run as instance i of a batch */
 } orc_config;
 
 typedef struct {
@@ -201,7 +202,7 @@ static int push(orc_particle** a, long long* n, long long* cap,
 }
 
 orc_state* orc_create(const orc_config* c) {
-  if (c->nx <= 0 || c->nk <= 0 || !(c->xmax > c->xmin) ||
+  if (c->instance < 0 || c->instance >= 256 || c->nx <= 0 || c->nk <= 0 || !(c->xmax > c->xmin) ||
       !(c->kmax > c->kmin) || c->dt <= 0 || c->hbar <= 0 || c->mass <= 0 ||
       (c->strategy != 1 && c->strategy != 2) || c->n_alpha <= 0 || c->w <= 0)
     return NULL;
@@ -243,7 +244,8 @@ void orc_enable_log(orc_state* s, int on) { s->log_on = on; }
 /* ------------------------------------------------------------------------ */
 /* Initial data: N particles from the Gaussian-wavepacket Wigner function     */
 /* f0 = (1/pi) exp(-(x-x0)^2/(2 sx^2) - 2 sx^2 (k-k0)^2), which is positive:  */
-/* x ~ N(x0, sx^2), k ~ N(k0, (1/(2 sx))^2), weight +1, pid = index.          */
+/* x ~ N(x0, sx^2), k ~ N(k0, (1/(2 sx))^2), weight +1,                      */
+/* pid = (instance << 32) | index.                                           */
 /* ------------------------------------------------------------------------ */
 
 int orc_init_gauss(orc_state* s, long long n, double x0, double sx,
@@ -252,7 +254,8 @@ int orc_init_gauss(orc_state* s, long long n, double x0, double sx,
   s->n = 0;
   for (long long i = 0; i < n; ++i) {
     uint32_t r[4];
-    draw4(s, (uint64_t)i, ORC_STEP_INIT, 0u, r);
+    const uint64_t pid0 = ((uint64_t)s->c.instance << 32) | (uint64_t)i;
+    draw4(s, pid0, ORC_STEP_INIT, 0u, r);
     double ua = orc_u53(r[0], r[1]);
     double ub = orc_u53(r[2], r[3]);
     double rad = sqrt(-2.0 * log1p(-ua));
@@ -261,7 +264,7 @@ int orc_init_gauss(orc_state* s, long long n, double x0, double sx,
     p.x = x0 + sx * (rad * cos(th));
     p.k = k0 + sk * (rad * sin(th));
     p.w = 1.0;
-    p.pid = (uint64_t)i;
+    p.pid = pid0;
     if (push(&s->p, &s->n, &s->cap, p)) return -1;
   }
   s->step = 0;
@@ -439,8 +442,8 @@ static double bin_k(const orc_state* s, double k) {
 
 /* Alg. 3 for the signed counts c_nu already in s->grid: |c_nu| particles of
  * sign sign(c_nu), uniform in D_nu.  Particle j of the new list (cells in
- * order) gets pid = (epoch << 40) | j and its two offsets from its own
- * stream.  A coordinate that rounds onto a neighbouring cell is moved by
+ * order) gets pid = (epoch << 40) | (instance << 32) | j and its two
+ * offsets from its own stream.  A coordinate that rounds onto a neighbouring cell is moved by
  * single ulps back into D_nu, so that binning the regenerated set gives the
  * same counts. */
 static int regenerate(orc_state* s) {
@@ -454,7 +457,7 @@ static int regenerate(orc_state* s) {
     long long m = cnt > 0 ? cnt : -(long long)cnt;
     double sign = cnt > 0 ? 1.0 : -1.0;
     for (long long r = 0; r < m; ++r, ++j) {
-      uint64_t pid = ((uint64_t)s->epoch << 40) | j;
+      uint64_t pid = ((uint64_t)s->epoch << 40) | ((uint64_t)s->c.instance << 32) | j;
       uint32_t h[4];
       draw4(s, pid, ORC_STEP_REGEN, 0u, h);
       double ux = orc_u53(h[0], h[1]);

@@ -12,7 +12,8 @@ def make_oracle(wl, **over):
                          gamma0=w["gamma0"], H=w["H"], w=w["w"], xc=w["xc"],
                          nx=w["nx"], nk=w["nk"], xmin=w["xmin"],
                          xmax=w["xmax"], kmin=w["kmin"], kmax=w["kmax"],
-                         strategy=strat, n_alpha=w["n_alpha"], seed=w["seed"])
+                         strategy=strat, n_alpha=w["n_alpha"], seed=w["seed"],
+                         instance=w.get("instance", 0))
 
 
 def net_sign(w):
