@@ -302,9 +302,10 @@ int orc_set_particles(orc_state* s, long long n, const double* x,
 /*        weights +w and -w;                                                 */
 /*   sp2 (wp propagation): a pair is always produced with weights            */
 /*        +w cacc |sg| and -w cacc |sg| (importance weight);                 */
-/*   the pair is oriented by the sign of sg (the pair identity for           */
-/*   2 V_W/|V_W| in Sec. 3.1): + child at k + kappa', - child at k - kappa', */
-/*   kappa' = sign(sg) kappa.                                                */
+/*   the pair is oriented by the sign of V_W(x, kappa) = sign(H) sign(sg)    */
+/*   (Eq. 2: V_W carries the sign of Vhat, hence of H; the pair identity    */
+/*   for 2 V_W/|V_W| in Sec. 3.1): + child at k + kappa', - child at        */
+/*   k - kappa', kappa' = sign(H sg) kappa.                                 */
 /* Offspring outside K are killed one by one (weight 0, Alg. 1 item 3).      */
 /* Surviving offspring continue the same interval from their birth time.     */
 /* ------------------------------------------------------------------------ */
@@ -340,7 +341,7 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
       wc = w * f;
     }
     if (emit) {
-      if (sg < 0.0) kap = -kap;
+      if (c->H < 0.0 ? sg > 0.0 : sg < 0.0) kap = -kap;
       uint32_t h[4];
       draw4(s, pid, l, ORC_DRAW_PIDS | j, h);
       uint64_t pid_p =
@@ -746,7 +747,7 @@ int orc_event_outcome(const orc_state* s, uint64_t pid, uint32_t l, uint32_t j,
   double sg = sin(2.0 * (xe - s->c.xc) * kap);
   double f = s->cacc * fabs(sg);
   int emit = s->c.strategy == 1 ? (u3 < f) : (f > 0.0);
-  if (sg < 0.0) kap = -kap;
+  if (s->c.H < 0.0 ? sg > 0.0 : sg < 0.0) kap = -kap;
   *kappa = kap;
   *factor = f;
   *gap = -log1p(-u4) / s->gamma0;

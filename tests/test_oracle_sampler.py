@@ -87,3 +87,33 @@ def test_accepted_events_per_interval_are_poisson_xi_dt(oracle_mod):
     assert abs(counts.var() - lam) < 0.05 * lam
     # event times of parents are uniform over the interval
     assert stats.kstest(par["t"] / wl["dt"], "uniform").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("H", [-1.0, -0.6, 0.6])
+def test_kick_law_follows_the_sign_of_the_potential(oracle_mod, H):
+    # Eq. 2: V_W carries the sign of Vhat, i.e. of H.  A well (H < 0) has
+    # V_W^+ where H sin(2 (x - xc) q) > 0, so the + child's kick follows
+    # max(V_W(x, .), 0)/xi for either sign of H.
+    from oracle import refs
+    x = 0.7
+    o = make_oracle(workloads.GAUSS_2D_FP64_2E5, H=H, n_alpha=10)
+    emit, kap, _, _ = _outcomes(o, x, 50000)
+    q = kap[emit]
+    assert np.all(H * np.sin(2 * x * q) >= 0)
+    vw = refs.gauss_vw_closed(H, 1.0, 0.0, 1.0)
+    xi = integrate.quad(lambda k: max(vw(x, k), 0.0), -8, 8, limit=2000)[0]
+    edges = np.linspace(-2.5, 2.5, 41)
+    h, _ = np.histogram(q, bins=edges)
+    p = np.array([integrate.quad(lambda k: max(vw(x, k), 0.0) / xi, a, b)[0]
+                  for a, b in zip(edges[:-1], edges[1:])])
+    exp = p * len(q)
+    keep = exp > 10
+    chi = np.sum((h[keep] - exp[keep]) ** 2 / exp[keep])
+    assert stats.chi2.sf(chi, keep.sum() - 1) > 1e-3
+    # the mean kick of the + child, against an independent Fourier quadrature
+    # of the potential itself
+    V = refs.gauss_potential(H, 1.0, 0.0)
+    qs = np.linspace(-3.0, 3.0, 241)
+    vq = np.array([max(refs.vw_quadrature(V, x, k), 0.0) for k in qs])
+    m = np.trapezoid(qs * vq, qs) / np.trapezoid(vq, qs)
+    assert abs(q.mean() - m) < 5 * q.std() / np.sqrt(len(q)) + 2e-3
