@@ -45,7 +45,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2"])
     ap.add_argument("--workload", default="gauss2d_fp32_n1e8",
-                    choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5"])
+                    choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5", "batch2d_fp32_256"])
+    ap.add_argument("--n-scale", type=float, default=1.0,
+                    help="batched workload: scale every instance's particle count")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="batched workload: skip the plain per-instance comparison")
     ap.add_argument("--particles", type=float, default=0,
                     help="override the particle count (profiling small cases)")
     ap.add_argument("--capacity-factor", type=float, default=4.0,
@@ -56,6 +60,8 @@ def parse():
 
 
 def workload(args):
+    if args.workload == "batch2d_fp32_256":
+        return workloads.scaled(workloads.BATCH_2D_FP32_256)
     base = (workloads.GAUSS_2D_FP32_1E8 if args.workload == "gauss2d_fp32_n1e8"
             else workloads.GAUSS_2D_FP64_2E5)
     wl = workloads.scaled(base, strategy=args.strategy)
@@ -299,6 +305,169 @@ def ours(args, wl):
     sim.close()
 
 
+def ours_batch(args, spec):
+    """The batched workload: all instances in one context and the same
+    launches, timed like the plain workload; then the plain per-instance path
+    (one context per instance, run one after the other on the same GPU) for
+    the same periods, for comparison."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1709_02121_gb300 import build
+    build.build()
+    from paper_1709_02121_gb300 import Batch, Simulation, wbrw
+
+    wl = workloads.scaled(spec, seed=spec["seed"] + rank)
+    insts = workloads.batch_instances(wl, args.n_scale)
+    n_total = sum(v["n_init"] for v in insts)
+    cap = int(args.capacity_factor * n_total) + (1 << 20)
+    sim = Batch(wl, insts, capacity=cap)
+    stream = sim.stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P = wl["resample_every"]
+    for _ in range(args.warmup):
+        sim.run(P)
+    barrier()
+    c0 = sim.counters()
+    wbrw.wbrw_profile(sim.ctx, True)
+    clocks = Clocks(local)
+    clocks.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i)
+        starts[i].record(stream)
+        sim.run(P)
+        ends[i].record(stream)
+    barrier()
+    clk = clocks.stop()
+    kern_ms, kern_n = wbrw.wbrw_profile_read(sim.ctx)
+    wbrw.wbrw_profile(sim.ctx, False)
+    c1 = sim.counters()
+    t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    psteps = c1["particle_steps"] - c0["particle_steps"]
+    psteps_first = c1["particle_steps_first"] - c0["particle_steps_first"]
+    launches = c1["launches"] - c0["launches"]
+    T_batch = sim.transmissions()
+
+    # ---- end to end: every period resumes from the host checkpoint of all
+    # instances and returns it, with the transmissions of every instance
+    e2e = None
+    if not args.no_e2e:
+        m = len(insts)
+        grid_h = torch.empty((m, wl["nx"], wl["nk"]), dtype=torch.int32).pin_memory()
+        _, step, epoch = sim.checkpoint(grid_h.numpy())
+        e2e_steps = min(args.steps, 5)
+        barrier()
+        pe0 = sim.counters()["particle_steps"]
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            sim.restore(grid_h.numpy(), step, epoch)
+            sim.run(P)
+            _, step, epoch = sim.checkpoint(grid_h.numpy())
+            T_last = sim.transmissions()
+        te = time.perf_counter() - t0
+        pe = sim.counters()["particle_steps"] - pe0
+        e2e = {"value": pe / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(m * wl["nx"] * wl["nk"] * 4),
+               "d2h_bytes_per_step": int(m * wl["nx"] * wl["nk"] * 4 + m * 8),
+               "steps": e2e_steps, "transmission_mean_last": float(np.mean(T_last))}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # ---- the plain per-instance path: one context per instance on shared
+    # buffers sized for the largest instance, the same warm-up and timed
+    # periods, device time summed over the instances' timed periods
+    plain = None
+    if not args.no_plain:
+        nmax = max(v["n_init"] for v in insts)
+        base = workloads.scaled(wl, n_alpha=nmax)
+        host = Simulation.__new__(Simulation)
+        host.ninst = 1
+        host._buffers(base, int(args.capacity_factor * nmax) + (1 << 20), 0, None)
+        t_plain, ps_plain = 0.0, 0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for v in insts:
+            cfg = wbrw.Config(2, host.cfg.precision, host.cfg.strategy, wl["hbar"], wl["mass"],
+                              wl["dt"], 0.0, wl["nx"], wl["nk"], wl["xmin"], wl["xmax"],
+                              wl["kmin"], wl["kmax"], P, int(v["n_alpha"]), int(wl["seed"]))
+            pot = wbrw.Potential(wbrw.POT_GAUSSIAN, v["H"], v["w"], v["xc"])
+            ctx = wbrw.wbrw_init(cfg, pot, host.bufs, int(v["n_init"]), v["x0"], v["sigma_x"],
+                                 v["k0"], host.stream.cuda_stream)
+            for _ in range(args.warmup):
+                wbrw.wbrw_run(ctx, P)
+            p0 = wbrw.wbrw_counters(ctx)["particle_steps"]
+            flush.fill_(0)
+            ev[0].record(host.stream)
+            for _ in range(args.steps):
+                wbrw.wbrw_run(ctx, P)
+            ev[1].record(host.stream)
+            torch.cuda.synchronize()
+            t_plain += ev[0].elapsed_time(ev[1])
+            ps_plain += wbrw.wbrw_counters(ctx)["particle_steps"] - p0
+            wbrw.wbrw_destroy(ctx)
+        plain = {"value": ps_plain / (t_plain / 1e3), "unit": UNIT,
+                 "ms_per_step": t_plain / args.steps, "particle_steps": ps_plain,
+                 "path": "one context per instance, instances one after the other"}
+
+    t_max, ps_all, e2e_sum = reduce_over_ranks(ws, t_ms, psteps, e2e["value"] if e2e else 0.0,
+                                               "cuda")
+    if e2e is not None:
+        e2e["value"] = e2e_sum
+    if rank == 0:
+        value = ps_all / (t_max / 1e3)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except Exception:
+            pass
+        roof = roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk)
+        ns = [v["n_init"] for v in insts]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "instances": len(insts),
+                           "particles": int(n_total), "particles_min_max": [min(ns), max(ns)],
+                           "grid_per_instance": [wl["nx"], wl["nk"]], "dt": wl["dt"],
+                           "intervals_per_step": P, "strategy": "sp1", "precision": "fp32",
+                           "l2": "flushed (512 MiB write) between timed steps",
+                           "parallelism": "replicas x%d" % ws},
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+                "live_particles_end": c1["live"], "particle_steps": psteps,
+                "transmission_mean": float(np.mean(T_batch))}
+        if plain is not None:
+            plain["speedup_of_batch"] = plain["ms_per_step"] / (t_ms / args.steps)
+            line["plain_per_instance"] = plain
+        if not args.no_cpu_baseline and ws == 1:
+            # the oracle on one instance of the batch (the first), sampled
+            v = insts[0]
+            one = workloads.scaled(wl, H=v["H"], w=v["w"], k0=v["k0"])
+            n_s = min(v["n_init"], 200_000)
+            times, pst = oracle_period_rate(one, n_s, budget_s=15.0)
+            line["cpu_baseline"] = {
+                "value": sum(pst) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "instance 0 (H=%.3g, w=%.3g, k0=%.3g), %d initial particles, %d "
+                          "full %d-interval periods incl. annihilation, FP64 oracle, single "
+                          "thread" % (v["H"], v["w"], v["k0"], n_s, len(times), P)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def reduce_over_ranks(ws, t_ms, psteps, e2e_value, device):
     """Whole-job numbers of the replicas: the slowest rank's time, and the
     particle-steps and end-to-end rates of all ranks summed."""
@@ -357,6 +526,8 @@ def main():
     wl = workload(args)
     if args.impl == "reference":
         reference_arm(args, wl)
+    elif args.workload == "batch2d_fp32_256":
+        ours_batch(args, wl)
     else:
         ours(args, wl)
 

@@ -251,6 +251,65 @@ wbrw_status wbrw_observables_static(const int* grid, int nx, int nk,
                                     double* density, double* marginal_x,
                                     double* transmission, void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems in the same launches.
+ *
+ * The paper treats one problem at a time; running many of them side by side
+ * is an extension for throughput.  Each instance of a batch is the run that
+ * wbrw_init would make for its own potential, initial wavepacket, rate and
+ * N_alpha, with the shared config (hbar, mass, dt, grid, resample_every,
+ * seed, precision) -- except that its particles are labelled
+ * (instance << 32) | index at start and (epoch << 40) | (instance << 32) | j
+ * after a resampling, so instances draw from disjoint random streams.
+ * Instance 0 of a batch is therefore bit-identical to the plain run.
+ *
+ * The histogram buffer holds the instances one after the other:
+ * instance i owns grid[i*nx*nk .. (i+1)*nx*nk), x-major with k contiguous;
+ * buffers.grid_cells >= ninst*nx*nk, and ninst*nx*nk < 2^30.  The particle
+ * arrays are shared: initial particles of instance i occupy the slots after
+ * those of instances 0..i-1.  Batches use sp1 (WBRW_SP1_PAIR) only.
+ * wbrw_step, wbrw_annihilate, wbrw_run, wbrw_particles, wbrw_checkpoint
+ * (all instances' counts), wbrw_restore, wbrw_counters (sums over
+ * instances), wbrw_profile and wbrw_destroy work on a batch unchanged;
+ * wbrw_density reports instance 0.
+ * ------------------------------------------------------------------------ */
+#define WBRW_MAX_INSTANCES 256
+
+typedef struct {
+  wbrw_potential pot;       /* the instance's potential                      */
+  double x0, sigma_x, k0;   /* initial Gaussian wavepacket (see wbrw_init)   */
+  long long n_init;         /* initial particles, 0 .. 2^32 - 1              */
+  long long n_alpha;        /* N_alpha of its estimator (> 0)                */
+  double gamma0;            /* <= 0: the majorant rate C/2 of its potential  */
+} wbrw_instance;
+
+/* Scratch bytes for a batch of ninst instances sharing `capacity` particle
+ * slots (config->gamma0 and config->n_alpha are ignored).  0 if invalid. */
+size_t wbrw_batch_scratch_bytes(const wbrw_config* config, int ninst, long long capacity);
+
+/* Create a batch context: ninst (1..WBRW_MAX_INSTANCES) instances described
+ * by inst[0..ninst) (host memory, copied), initial particles drawn as in
+ * wbrw_init.  Sum of n_init <= buffers.capacity.  Async; *out as in
+ * wbrw_init. */
+wbrw_status wbrw_batch_init(const wbrw_config* config, int ninst, const wbrw_instance* inst,
+                            const wbrw_buffers* buffers, void* cuda_stream, wbrw_ctx** out);
+
+/* wbrw_density for instance `instance` of a batch (0 for a plain context):
+ * density and marginal from its own cells and N_alpha, its transmission and
+ * its live particle count.  Synchronises the stream. */
+wbrw_status wbrw_instance_density(wbrw_ctx* ctx, int instance, double* density_host,
+                                  double* marginal_x_host, double* transmission,
+                                  long long* live_particles);
+
+/* Transmission (Eq. estimator with A = 1{x > 0}) of every instance, read
+ * from the histogram right after a resampling: out_host[0..ninst).
+ * WBRW_ERR_STATE if the particles moved since.  Synchronises the stream. */
+wbrw_status wbrw_transmissions(wbrw_ctx* ctx, double* out_host);
+
+/* After wbrw_particles: the instance of every materialised particle,
+ * inst_dev[0..n) (device memory).  Synchronises the stream. */
+wbrw_status wbrw_particle_instances(wbrw_ctx* ctx, unsigned int* inst_dev);
+
 /* Copy the counters (WBRW_C_*) to out[0..WBRW_C_COUNT).  Synchronises. */
 wbrw_status wbrw_counters(wbrw_ctx* ctx, long long* out);
 

@@ -28,11 +28,12 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
   size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, seg_counts, total;
+      rec_a, keep0, keep1, res0, res1, seg_counts, tabs, cinst, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
-bool config_ok(const wbrw_config* c, char* why, size_t n) {
+// ninst = 0: a plain run (config->n_alpha is used); ninst >= 1: a batch.
+bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
   auto fail = [&](const char* m) {
     if (why) snprintf(why, n, "invalid configuration: %s", m);
     return false;
@@ -43,10 +44,13 @@ bool config_ok(const wbrw_config* c, char* why, size_t n) {
   if (c->strategy != WBRW_SP1_PAIR && c->strategy != WBRW_SP2_BOOTSTRAP) return fail("strategy");
   if (!(c->hbar > 0) || !(c->mass > 0) || !(c->dt > 0)) return fail("hbar, mass and dt must be > 0");
   if (c->nx <= 0 || c->nk <= 0) return fail("nx and nk must be > 0");
-  if ((long long)c->nx * (long long)c->nk >= (1ll << 30)) return fail("nx*nk must be < 2^30");
+  if (ninst < 0 || ninst > kMaxInst) return fail("instances must be 1..WBRW_MAX_INSTANCES");
+  if ((long long)c->nx * (long long)c->nk * (ninst > 0 ? ninst : 1) >= (1ll << 30))
+    return fail("cells of all instances must be < 2^30");
+  if (ninst > 1 && c->strategy != WBRW_SP1_PAIR) return fail("batches use sp1 only");
   if (!(c->xmax > c->xmin) || !(c->kmax > c->kmin)) return fail("empty domain");
   if (c->resample_every < 0) return fail("resample_every must be >= 0");
-  if (c->n_alpha <= 0) return fail("n_alpha must be > 0");
+  if (ninst == 0 && c->n_alpha <= 0) return fail("n_alpha must be > 0");
   return true;
 }
 
@@ -57,9 +61,9 @@ bool config_ok(const wbrw_config* c, char* why, size_t n) {
 constexpr long long kMinSeg = 64;
 size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
 
-Layout layout(const wbrw_config* c, long long capacity) {
+Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   Layout L;
-  const long long nh = (long long)c->nx * c->nk;
+  const long long nh = (long long)c->nx * c->nk * ninst;
   const long long floor_entries = (long long)kMaxSeg * kMinSeg;
   L.qcap = capacity > floor_entries ? capacity : floor_entries;
   L.ecap = 2 * L.qcap;  // about one candidate interval per particle per flight
@@ -88,7 +92,7 @@ Layout layout(const wbrw_config* c, long long capacity) {
   L.scan_bnz = take((size_t)(L.scan_blocks + 1) * 4);
   L.tmp_grid = take((size_t)nh * 4);
   L.tmp_wsum = take((size_t)nh * 8);
-  L.obs_density = take((size_t)nh * 8);
+  L.obs_density = take((size_t)c->nx * c->nk * 8);
   L.obs_marg = take((size_t)c->nx * 8);
   L.obs_col = take((size_t)c->nx * 8);
   L.obs_scalar = take(64);
@@ -99,8 +103,48 @@ Layout layout(const wbrw_config* c, long long capacity) {
   L.keep1 = take(sp2 ? (size_t)nh * 4 : 0);
   L.res0 = take(sp2 ? (size_t)nh * 8 : 0);
   L.res1 = take(sp2 ? (size_t)nh * 8 : 0);
+  L.tabs = take(kTabBytes);
+  L.cinst = take(ninst > 1 ? (size_t)capacity * 4 : 0);
   L.total = off;
   return L;
+}
+
+// Constants of one instance (Sec. 4.2 / Remark 3 / Sec. 3.2): C = 2|H|/hbar,
+// kick scale 1/(2w), rate gamma0 (default C/2), acceptance factor
+// C/(2 gamma0) <= 1, P(candidate in an interval) = 1 - exp(-gamma0 dt).
+bool make_instance(const wbrw_config* cfg, const wbrw_potential* pot, double gamma0_in,
+                   double x0, double sx, double k0, long long n_init, long long n_alpha,
+                   InstHost* q) {
+  if (!pot || pot->kind != WBRW_POT_GAUSSIAN || !(pot->w > 0) || !isfinite(pot->w) ||
+      !isfinite(pot->H) || !isfinite(pot->xc))
+    return false;
+  if (!(sx > 0) || !isfinite(sx) || !isfinite(x0) || !isfinite(k0)) return false;
+  if (n_init < 0 || n_alpha <= 0) return false;
+  q->H = pot->H;
+  q->w = pot->w;
+  q->xc = pot->xc;
+  q->C = 2.0 * fabs(pot->H) / cfg->hbar;
+  double g = gamma0_in > 0 ? gamma0_in : 0.5 * q->C;
+  if (g <= 0) g = 1.0;  // H = 0: no pair is ever accepted
+  q->gamma0 = g;
+  q->cacc = q->C / (2.0 * g);
+  if (q->cacc > 1.0) return false;  // gamma0 below the majorant rate C/2
+  q->sig_k = 1.0 / (2.0 * pot->w);
+  q->p_any = -expm1(-g * cfg->dt);
+  q->x0 = x0;
+  q->sx = sx;
+  q->k0 = k0;
+  q->n_init = n_init;
+  q->n_alpha = n_alpha;
+  q->start = 0;
+  return true;
+}
+
+void free_ctx(wbrw_ctx* c) {
+  if (!c) return;
+  free(c->ih);
+  free(c->host_tab);
+  delete c;
 }
 
 wbrw_status seterr(wbrw_ctx* c, wbrw_status st, const char* fmt, ...) {
@@ -203,64 +247,71 @@ extern "C" {
 
 size_t wbrw_scratch_bytes(const wbrw_config* config, long long capacity) {
   if (!config_ok(config, nullptr, 0) || capacity <= 0) return 0;
-  return layout(config, capacity).total;
+  return layout(config, 1, capacity).total;
 }
 
-wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
-                      const wbrw_buffers* b, long long n_init, double x0,
-                      double sigma_x, double k0, void* cuda_stream,
-                      wbrw_ctx** out) {
-  if (!out) return WBRW_ERR_ARG;
-  *out = nullptr;
-  char why[256];
-  if (!config_ok(config, why, sizeof(why))) return WBRW_ERR_ARG;
-  if (!pot || pot->kind != WBRW_POT_GAUSSIAN || !(pot->w > 0) || !isfinite(pot->H) ||
-      !isfinite(pot->xc))
-    return WBRW_ERR_ARG;
-  if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0)
-    return WBRW_ERR_ARG;
-  if (config->strategy == WBRW_SP2_BOOTSTRAP && !b->w) return WBRW_ERR_ARG;
-  if (b->grid_cells < (long long)config->nx * config->nk) return WBRW_ERR_ARG;
-  if (((uintptr_t)b->scratch & (kAlign - 1)) != 0) return WBRW_ERR_ARG;
-  if (n_init < 0 || n_init > b->capacity || !(sigma_x > 0)) return WBRW_ERR_ARG;
-  if (b->event_log && b->event_log_capacity <= 0) return WBRW_ERR_ARG;
-  const Layout L = layout(config, b->capacity);
-  if (b->scratch_bytes < L.total) return WBRW_ERR_ARG;
+size_t wbrw_batch_scratch_bytes(const wbrw_config* config, int ninst, long long capacity) {
+  if (ninst < 1 || !config_ok(config, nullptr, 0, ninst) || capacity <= 0) return 0;
+  return layout(config, ninst, capacity).total;
+}
 
-  // constants of Sec. 4.2 / Remark 3 / Sec. 3.2
-  const double C = 2.0 * fabs(pot->H) / config->hbar;
-  double gamma0 = config->gamma0 > 0 ? config->gamma0 : 0.5 * C;
-  if (gamma0 <= 0) gamma0 = 1.0;  // H = 0: no pair is ever accepted
-  const double cacc = C / (2.0 * gamma0);
-  if (cacc > 1.0) return WBRW_ERR_ARG;  // gamma0 below the majorant rate C/2
+}  // extern "C"
+
+namespace {
+
+// Create a context for ninst instances (records q, starts filled in here)
+// and enqueue the initial sampling.  Takes ownership of q.
+wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw_buffers* b,
+                   void* cuda_stream, wbrw_ctx** out) {
+  if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0 ||
+      (config->strategy == WBRW_SP2_BOOTSTRAP && !b->w) ||
+      b->grid_cells < (long long)config->nx * config->nk * ninst ||
+      ((uintptr_t)b->scratch & (kAlign - 1)) != 0 ||
+      (b->event_log && b->event_log_capacity <= 0)) {
+    free(q);
+    return WBRW_ERR_ARG;
+  }
+  long long n_total = 0;
+  double p_max = 0;
+  for (int i = 0; i < ninst; ++i) {
+    if (q[i].n_init >= (1ll << 32)) { free(q); return WBRW_ERR_ARG; }
+    q[i].start = (unsigned long long)n_total;
+    n_total += q[i].n_init;
+    if (q[i].p_any > p_max) p_max = q[i].p_any;
+  }
+  const Layout L = layout(config, ninst, b->capacity);
+  if (n_total > b->capacity || b->scratch_bytes < L.total) { free(q); return WBRW_ERR_ARG; }
 
   wbrw_ctx* c = new (std::nothrow) wbrw_ctx();
-  if (!c) return WBRW_ERR_ARG;
+  if (!c) { free(q); return WBRW_ERR_ARG; }
+  c->ih = q;
+  c->host_tab = calloc(1, kTabBytes);
+  if (!c->host_tab) { free_ctx(c); return WBRW_ERR_ARG; }
+  c->ninst = ninst;
   c->cfg = *config;
-  c->pot = *pot;
+  c->pot.kind = WBRW_POT_GAUSSIAN;
+  c->pot.H = q[0].H;
+  c->pot.w = q[0].w;
+  c->pot.xc = q[0].xc;
   c->buf = *b;
   c->stream = (cudaStream_t)cuda_stream;
-  c->C = C;
-  c->sig_k = 1.0 / (2.0 * pot->w);
-  c->gamma0 = gamma0;
-  c->cacc = cacc;
   c->hm = config->hbar / config->mass;
   c->dtv = config->dt * c->hm;
-  c->p_any = -expm1(-gamma0 * config->dt);
   // flights short enough that a particle expects at most one candidate
   // interval, so the candidate queue (two entries per particle) holds them
-  c->max_chunk = c->p_any > 0 ? (int)floor(1.0 / c->p_any) : kMaxChunk;
+  c->max_chunk = p_max > 0 ? (int)floor(1.0 / p_max) : kMaxChunk;
   if (c->max_chunk > kMaxChunk) c->max_chunk = kMaxChunk;
   if (c->max_chunk < 1) c->max_chunk = 1;
   c->dx = (config->xmax - config->xmin) / (double)config->nx;
   c->dk = (config->kmax - config->kmin) / (double)config->nk;
   c->inv_dx = (double)config->nx / (config->xmax - config->xmin);
   c->inv_dk = (double)config->nk / (config->kmax - config->kmin);
-  c->nh = (long long)config->nx * config->nk;
+  c->nhi = (long long)config->nx * config->nk;
+  c->nh = c->nhi * ninst;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
           cudaSuccess) {
-    delete c;
+    free_ctx(c);
     return WBRW_ERR_CUDA;
   }
   char* base = (char*)b->scratch;
@@ -307,6 +358,11 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
   c->boot_keep[1] = (int*)(base + L.keep1);
   c->boot_res[0] = (unsigned long long*)(base + L.res0);
   c->boot_res[1] = (unsigned long long*)(base + L.res1);
+  c->inst_tab = base + L.tabs;
+  c->inst_slot = (unsigned long long*)(base + L.tabs + kTabSlotOff);
+  c->inst_na = (double*)(base + L.tabs + kTabNaOff);
+  c->inst_trans = (double*)(base + L.tabs + kTabTransOff);
+  c->cinst = ninst > 1 ? (unsigned*)(base + L.cinst) : nullptr;
   c->state = ST_PARTICLES;
   c->step = 0;
   c->epoch = 0;
@@ -316,13 +372,51 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
   c->err[0] = 0;
 
   cudaError_t e = cudaMemsetAsync(c->cnt, 0, sizeof(Counters), c->stream);
-  if (e == cudaSuccess) e = drv(c)->init(c, n_init, x0, sigma_x, k0);
+  if (e == cudaSuccess) e = drv(c)->init(c, n_total);
   if (e != cudaSuccess) {
-    delete c;
+    free_ctx(c);
     return WBRW_ERR_CUDA;
   }
   *out = c;
   return WBRW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
+                      const wbrw_buffers* b, long long n_init, double x0,
+                      double sigma_x, double k0, void* cuda_stream,
+                      wbrw_ctx** out) {
+  if (!out) return WBRW_ERR_ARG;
+  *out = nullptr;
+  if (!config_ok(config, nullptr, 0)) return WBRW_ERR_ARG;
+  InstHost* q = (InstHost*)calloc(1, sizeof(InstHost));
+  if (!q) return WBRW_ERR_ARG;
+  if (!make_instance(config, pot, config->gamma0, x0, sigma_x, k0, n_init, config->n_alpha, q)) {
+    free(q);
+    return WBRW_ERR_ARG;
+  }
+  return create(config, 1, q, b, cuda_stream, out);
+}
+
+wbrw_status wbrw_batch_init(const wbrw_config* config, int ninst, const wbrw_instance* inst,
+                            const wbrw_buffers* b, void* cuda_stream, wbrw_ctx** out) {
+  if (!out) return WBRW_ERR_ARG;
+  *out = nullptr;
+  if (ninst < 1 || !inst || !config_ok(config, nullptr, 0, ninst)) return WBRW_ERR_ARG;
+  InstHost* q = (InstHost*)calloc((size_t)ninst, sizeof(InstHost));
+  if (!q) return WBRW_ERR_ARG;
+  for (int i = 0; i < ninst; ++i) {
+    const wbrw_instance& v = inst[i];
+    if (!make_instance(config, &v.pot, v.gamma0, v.x0, v.sigma_x, v.k0, v.n_init, v.n_alpha,
+                       &q[i])) {
+      free(q);
+      return WBRW_ERR_ARG;
+    }
+  }
+  return create(config, ninst, q, b, cuda_stream, out);
 }
 
 wbrw_status wbrw_step(wbrw_ctx* c, int nsteps) {
@@ -396,24 +490,26 @@ wbrw_status wbrw_run(wbrw_ctx* c, int nsteps) {
   return WBRW_OK;
 }
 
-wbrw_status wbrw_density(wbrw_ctx* c, double* density_host, double* marginal_x_host,
-                         double* transmission, long long* live_particles) {
+wbrw_status wbrw_instance_density(wbrw_ctx* c, int inst, double* density_host,
+                                  double* marginal_x_host, double* transmission,
+                                  long long* live_particles) {
   if (!c) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
+  if (inst < 0 || inst >= c->ninst) return seterr(c, WBRW_ERR_ARG, "no instance %d", inst);
   wbrw_status st;
   if (c->state == ST_HISTOGRAM) {
-    WBRW_TRY(c, launch_observables(c, c->buf.grid, nullptr), "observables");
+    WBRW_TRY(c, launch_observables(c, inst, c->buf.grid, nullptr), "observables");
   } else if (c->cfg.strategy == WBRW_SP1_PAIR) {
     WBRW_TRY(c, launch_zero(c, c->tmp_grid, (size_t)c->nh * 4), "zero");
     WBRW_TRY(c, drv(c)->bin(c, DST_BIN1, c->tmp_grid, 0), "bin");
-    WBRW_TRY(c, launch_observables(c, c->tmp_grid, nullptr), "observables");
+    WBRW_TRY(c, launch_observables(c, inst, c->tmp_grid, nullptr), "observables");
   } else {
     WBRW_TRY(c, launch_zero(c, c->tmp_wsum, (size_t)c->nh * 8), "zero");
     WBRW_TRY(c, drv(c)->bin(c, DST_WSUM, c->tmp_grid, 0), "bin");
-    WBRW_TRY(c, launch_observables(c, nullptr, c->tmp_wsum), "observables");
+    WBRW_TRY(c, launch_observables(c, inst, nullptr, c->tmp_wsum), "observables");
   }
   if (density_host)
-    WBRW_TRY(c, cudaMemcpyAsync(density_host, c->obs_density, (size_t)c->nh * 8,
+    WBRW_TRY(c, cudaMemcpyAsync(density_host, c->obs_density, (size_t)c->nhi * 8,
                                 cudaMemcpyDeviceToHost, c->stream), "copy density");
   if (marginal_x_host)
     WBRW_TRY(c, cudaMemcpyAsync(marginal_x_host, c->obs_marg, (size_t)c->cfg.nx * 8,
@@ -421,8 +517,22 @@ wbrw_status wbrw_density(wbrw_ctx* c, double* density_host, double* marginal_x_h
   double T = 0;
   unsigned long long live = 0;
   WBRW_TRY(c, cudaMemcpyAsync(&T, c->obs_scalar, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
-  WBRW_TRY(c, cudaMemcpyAsync(&live, c->state == ST_HISTOGRAM ? &c->cnt->regen_total : &c->cnt->n,
-                              8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  if (c->ninst == 1) {
+    WBRW_TRY(c, cudaMemcpyAsync(&live, c->state == ST_HISTOGRAM ? &c->cnt->regen_total
+                                                                : &c->cnt->n,
+                                8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  } else if (c->state == ST_HISTOGRAM) {
+    unsigned long long se[2];
+    WBRW_TRY(c, cudaMemcpyAsync(se, c->inst_slot + inst, 16, cudaMemcpyDeviceToHost, c->stream),
+             "copy");
+    WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+    live = se[1] - se[0];
+  } else {
+    unsigned long long* d = (unsigned long long*)(c->obs_scalar + 1);
+    WBRW_TRY(c, launch_zero(c, d, 8), "zero");
+    WBRW_TRY(c, launch_live_instance(c, inst, d), "count");
+    WBRW_TRY(c, cudaMemcpyAsync(&live, d, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
+  }
   st = device_status(c);
   if (st != WBRW_OK) return st;
   if (transmission) *transmission = T;
@@ -430,12 +540,38 @@ wbrw_status wbrw_density(wbrw_ctx* c, double* density_host, double* marginal_x_h
   return WBRW_OK;
 }
 
+wbrw_status wbrw_density(wbrw_ctx* c, double* density_host, double* marginal_x_host,
+                         double* transmission, long long* live_particles) {
+  return wbrw_instance_density(c, 0, density_host, marginal_x_host, transmission,
+                               live_particles);
+}
+
+wbrw_status wbrw_transmissions(wbrw_ctx* c, double* out_host) {
+  if (!c || !out_host) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (c->state != ST_HISTOGRAM)
+    return seterr(c, WBRW_ERR_STATE, "transmissions need a resampling first");
+  WBRW_TRY(c, launch_transmissions(c, c->buf.grid, c->inst_trans), "transmissions");
+  WBRW_TRY(c, cudaMemcpyAsync(out_host, c->inst_trans, (size_t)c->ninst * 8,
+                              cudaMemcpyDeviceToHost, c->stream), "copy");
+  return device_status(c);
+}
+
+wbrw_status wbrw_particle_instances(wbrw_ctx* c, unsigned int* inst_dev) {
+  if (!c || !inst_dev) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (c->state != ST_PARTICLES)
+    return seterr(c, WBRW_ERR_STATE, "particles are not materialised");
+  WBRW_TRY(c, drv(c)->pids(c, nullptr, inst_dev), "instances");
+  return device_status(c);
+}
+
 wbrw_status wbrw_particles(wbrw_ctx* c, long long* n_host, unsigned long long* pid_dev) {
   if (!c) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
   wbrw_status st = ensure_particles(c);
   if (st != WBRW_OK) return st;
-  if (pid_dev) WBRW_TRY(c, drv(c)->pids(c, pid_dev), "ids");
+  if (pid_dev) WBRW_TRY(c, drv(c)->pids(c, pid_dev, nullptr), "ids");
   unsigned long long n = 0;
   WBRW_TRY(c, cudaMemcpyAsync(&n, &c->cnt->n, 8, cudaMemcpyDeviceToHost, c->stream), "copy");
   st = device_status(c);
@@ -545,7 +681,7 @@ void wbrw_destroy(wbrw_ctx* c) {
   if (!c) return;
   if (c->prof_created)
     for (int i = 0; i < 2 * 4096; ++i) cudaEventDestroy(c->prof_ev[i]);
-  delete c;
+  free_ctx(c);
 }
 
 }  // extern "C"

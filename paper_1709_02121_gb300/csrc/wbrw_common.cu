@@ -133,7 +133,8 @@ __global__ void __launch_bounds__(kBlock) k_cells_a(const int* grid, long long n
 __global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
                                                     unsigned int* bnz,
                                                     long long nb, Counters* c,
-                                                    long long tile_cap) {
+                                                    long long tile_cap,
+                                                    unsigned long long* inst_end) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   unsigned long long carry_s = 0, carry_z = 0;
   for (long long b0 = 0; b0 < nb; b0 += kBlock) {
@@ -152,16 +153,21 @@ __global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
   if (threadIdx.x == 0) {
     c->regen_total = carry_s;
     c->nz_count = carry_z;
+    *inst_end = carry_s;
     if (carry_s > (unsigned long long)tile_cap * 32ull) atomicOr(&c->err, ERR_CAP_PARTICLES);
   }
 }
 
+// Also records the first slot of each instance (cells i nhi .. (i+1) nhi - 1
+// belong to instance i) in inst_slot.
 __global__ void __launch_bounds__(kBlock) k_cells_c(const int* grid, long long nh,
                                                     const unsigned long long* bsum,
                                                     const unsigned int* bnz,
                                                     uint32_t* nz_cell,
                                                     unsigned long long* nz_start,
-                                                    uint32_t* tile_nz, long long tile_cap) {
+                                                    uint32_t* tile_nz, long long tile_cap,
+                                                    long long nhi,
+                                                    unsigned long long* inst_slot) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
   int v[kScanItems];
@@ -176,8 +182,13 @@ __global__ void __launch_bounds__(kBlock) k_cells_c(const int* grid, long long n
   unsigned long long ts, tz;
   unsigned long long os = block_exscan(s, red, ts) + bsum[blockIdx.x];
   unsigned long long oz = block_exscan(z, red, tz) + bnz[blockIdx.x];
+  long long next_inst = (base + nhi - 1) / nhi * nhi;  // first instance boundary >= base
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
+    if (base + i == next_inst && next_inst < nh) {
+      inst_slot[next_inst / nhi] = os;
+      next_inst += nhi;
+    }
     if (v[i] != 0) {
       const unsigned long long m = (unsigned long long)(v[i] < 0 ? -(long long)v[i] : (long long)v[i]);
       nz_cell[oz] = (uint32_t)(base + i) | (v[i] < 0 ? 0x80000000u : 0u);
@@ -391,6 +402,48 @@ __global__ void __launch_bounds__(kBlock) k_obs_total(const long long* col, int 
     out[0] = __ddiv_rn(__dmul_rn((double)(long long)t, scale), na);
 }
 
+// Transmission of each instance (one block each): the sum of its counts
+// over the cells with centre x > 0, divided by its N_alpha.  The cells with
+// centre x > 0 are the columns ix >= ix0, a contiguous range.
+__global__ void __launch_bounds__(kBlock) k_obs_trans(const int* counts, int nx, int nk,
+                                                      double xmin, double dx, const double* na,
+                                                      double* out) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  __shared__ int s_ix0;
+  if (threadIdx.x == 0) {
+    int ix0 = nx;
+    for (int ix = 0; ix < nx; ++ix)
+      if (__dadd_rn(xmin, __dmul_rn(__dadd_rn((double)ix, 0.5), dx)) > 0.0) { ix0 = ix; break; }
+    s_ix0 = ix0;
+  }
+  __syncthreads();
+  const long long nhi = (long long)nx * nk;
+  const int* g = counts + (long long)blockIdx.x * nhi;
+  long long s = 0;
+  for (long long nu = (long long)s_ix0 * nk + threadIdx.x; nu < nhi; nu += kBlock) s += g[nu];
+  unsigned long long t;
+  block_exscan((unsigned long long)s, red, t);
+  if (threadIdx.x == 0) out[blockIdx.x] = __ddiv_rn((double)(long long)t, na[blockIdx.x]);
+}
+
+// Particles of one instance in the arrays: its base slots plus the offspring
+// labelled with it.
+__global__ void __launch_bounds__(kBlock) k_live_inst(const Counters* c,
+                                                      const unsigned long long* inst_slot,
+                                                      const unsigned* cinst, int inst,
+                                                      unsigned long long* out) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const unsigned long long n = c->n, nb = c->n_base;
+  unsigned long long s = 0;
+  for (unsigned long long i = nb + (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * kBlock)
+    s += cinst[i - nb] == (unsigned)inst;
+  if (blockIdx.x == 0 && threadIdx.x == 0) s += inst_slot[inst + 1] - inst_slot[inst];
+  unsigned long long t;
+  block_exscan(s, red, t);
+  if (threadIdx.x == 0 && t) atomicAdd(out, t);
+}
+
 int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
 
 }  // namespace
@@ -408,10 +461,11 @@ cudaError_t launch_zero(Ctx* c, void* p, size_t bytes) {
 cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
   const long long nb = c->scan_blocks;
   k_cells_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz);
-  k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt, c->tile_cap);
+  k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt, c->tile_cap,
+                                         c->inst_slot + c->ninst);
   k_cells_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz,
                                                    c->nz_cell, c->nz_start, c->tile_nz,
-                                                   c->tile_cap);
+                                                   c->tile_cap, c->nhi, c->inst_slot);
   c->launches += 3;
   return cudaGetLastError();
 }
@@ -440,14 +494,29 @@ cudaError_t launch_boot(Ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_observables(Ctx* c, const int* counts, const long long* wsum) {
-  const double na = (double)c->cfg.n_alpha;
+cudaError_t launch_observables(Ctx* c, int inst, const int* counts, const long long* wsum) {
+  const double na = (double)c->ih[inst].n_alpha;
   const int g = grid_cap(c, 4);
-  k_obs_cols<<<g, kBlock, 0, c->stream>>>(counts, wsum, c->cfg.nx, c->cfg.nk, na, c->dx, c->dk,
-                                          c->obs_density, c->obs_marg, c->obs_col);
+  const long long off = (long long)inst * c->nhi;
+  k_obs_cols<<<g, kBlock, 0, c->stream>>>(counts ? counts + off : nullptr,
+                                          wsum ? wsum + off : nullptr, c->cfg.nx, c->cfg.nk, na,
+                                          c->dx, c->dk, c->obs_density, c->obs_marg, c->obs_col);
   k_obs_total<<<1, kBlock, 0, c->stream>>>(c->obs_col, c->cfg.nx, c->cfg.xmin, c->dx, na,
                                            wsum ? 1.0 / 2147483648.0 : 1.0, c->obs_scalar);
   c->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transmissions(Ctx* c, const int* counts, double* out) {
+  k_obs_trans<<<c->ninst, kBlock, 0, c->stream>>>(counts, c->cfg.nx, c->cfg.nk, c->cfg.xmin,
+                                                  c->dx, c->inst_na, out);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_live_instance(Ctx* c, int inst, unsigned long long* out) {
+  k_live_inst<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->cnt, c->inst_slot, c->cinst, inst, out);
+  c->launches++;
   return cudaGetLastError();
 }
 

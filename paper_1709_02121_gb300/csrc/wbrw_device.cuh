@@ -120,6 +120,28 @@ struct SEntry;
 
 constexpr int kLevels = 5;  // deferred segments: levels 1..3 in passes, 4 drained
 
+// Physics of one instance of a batch (a single run is a batch of one).
+template <class T>
+struct Inst {
+  T gamma0, cacc, sig_k, xc;  // rate, acceptance factor C/(2 gamma0), kick scale, centre
+  double p_hi;                // FP64: u0 < p_hi may start an event in an interval
+  float p_any_f;              // FP32: P(candidate) per interval
+  unsigned p16, p16_frac8;    // FP32 coin threshold and tie refinement
+  int well;                   // H < 0: V_W has the sign of -sin (Eq. 2)
+};
+
+// Initial sampling of one instance: slots [start, start + n) of the arrays.
+struct InitInst {
+  double x0, sx, k0, sk;
+  unsigned long long start;
+};
+
+// Queue entries carry the interval and the instance in one word.
+constexpr int kLBits = 24;
+__device__ __forceinline__ int ent_l(int v) { return v & ((1 << kLBits) - 1); }
+__device__ __forceinline__ int ent_inst(int v) { return (int)((unsigned)v >> kLBits); }
+__device__ __forceinline__ int ent_pack(int l, int inst) { return l | (inst << kLBits); }
+
 // Kernel parameters (by value, parameter space).
 //
 // Queues.  Every queue is split into one private segment per producer warp
@@ -132,15 +154,17 @@ constexpr int kLevels = 5;  // deferred segments: levels 1..3 in passes, 4 drain
 template <class P>
 struct KP {
   using T = typename P::T;
-  T dt, dtv, hm, gamma0, cacc, sig_k, xc;
+  T dt, dtv, hm;
   T xmin, kmin, kmax, dx, dk, inv_dx, inv_dk;
   int nx, nk;
   float inv_nk;     // 1/nk, for cell -> (ix, ik)
   int nh_big;       // nx nk >= 2^24: use an integer division instead
-  double p_hi;      // FP64: u0 < p_hi may start an event in the interval
-  float p_any_f;    // FP32: P(candidate) per interval
-  unsigned p16;     // FP32: floor(65536 p_any)
-  unsigned p16_frac8;  // FP32: floor(256 (65536 p_any - p16)), tie refinement
+  int ninst;        // instances in the batch (1 for a single run)
+  int nhi;          // cells per instance (nx nk); instance i owns [i nhi, (i+1) nhi)
+  const Inst<T>* inst;                    // per-instance physics
+  const unsigned long long* inst_slot;    // first array slot of each base instance
+  const unsigned long long* regen_start;  // first regenerated slot of each instance
+  unsigned* cinst;                        // instance of offspring appended to the arrays
   KeySched ks;      // Philox key schedule of the run seed
   int strategy;     // 1 = sp1, 2 = sp2
   int l0, L, round;
@@ -278,15 +302,16 @@ struct Draw;
 template <>
 struct Draw<P64> {
   struct State {};
-  __device__ static double first(const KP<P64>& p, unsigned long long pid, int l, double to,
-                                 bool /*root*/, State&) {
+  __device__ static double first(const KP<P64>& p, const Inst<double>& ip,
+                                 unsigned long long pid, int l, double to, bool /*root*/,
+                                 State&) {
     const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
     const double u0 = u53(r.x, r.y);
-    return P64::add(to, P64::div(-log1p(-u0), p.gamma0));
+    return P64::add(to, P64::div(-log1p(-u0), ip.gamma0));
   }
-  __device__ static void event(const KP<P64>& p, unsigned long long pid, int l, unsigned j,
-                               double xe, const State&, double& kap, double& sg, double& u3,
-                               double& gap) {
+  __device__ static void event(const KP<P64>& p, const Inst<double>& ip, unsigned long long pid,
+                               int l, unsigned j, double xe, const State&, double& kap,
+                               double& sg, double& u3, double& gap) {
     const uint32_t lo = (uint32_t)pid, hi = (uint32_t)(pid >> 32);
     const uint4 a = philox_ks(p.ks, lo, hi, (uint32_t)l, 1u + 2u * j);
     const uint4 b = philox_ks(p.ks, lo, hi, (uint32_t)l, 2u + 2u * j);
@@ -295,9 +320,9 @@ struct Draw<P64> {
     const double u4 = u53(b.z, b.w);
     const double z = __dmul_rn(__dsqrt_rn(__dmul_rn(-2.0, log1p(-u1))),
                                cos(__dmul_rn(6.283185307179586476925286766559, u2)));
-    kap = __dmul_rn(p.sig_k, z);
-    sg = sin(__dmul_rn(__dmul_rn(2.0, __dsub_rn(xe, p.xc)), kap));
-    gap = __ddiv_rn(-log1p(-u4), p.gamma0);
+    kap = __dmul_rn(ip.sig_k, z);
+    sg = sin(__dmul_rn(__dmul_rn(2.0, __dsub_rn(xe, ip.xc)), kap));
+    gap = __ddiv_rn(-log1p(-u4), ip.gamma0);
   }
 };
 
@@ -317,21 +342,21 @@ struct Draw<P32> {
   struct State {
     uint4 r;
   };
-  __device__ static float first(const KP<P32>& p, unsigned long long pid, int l, float to,
-                                bool root, State& st) {
+  __device__ static float first(const KP<P32>& p, const Inst<float>& ip, unsigned long long pid,
+                                int l, float to, bool root, State& st) {
     float pr;
     if (root) {
-      pr = p.p_any_f;
+      pr = ip.p_any_f;
     } else {
-      pr = -expm1f(-p.gamma0 * (p.dt - to));
+      pr = -expm1f(-ip.gamma0 * (p.dt - to));
       if (!((float)(uint32_t)pid < pr * 4294967296.0f)) return p.dt;  // no event
     }
     st.r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
-    return to + (-log1pf(-pr * u24(st.r.x))) / p.gamma0;
+    return to + (-log1pf(-pr * u24(st.r.x))) / ip.gamma0;
   }
-  __device__ static void event(const KP<P32>& p, unsigned long long pid, int l, unsigned j,
-                               float xe, const State& st, float& kap, float& sg, float& u3,
-                               float& gap) {
+  __device__ static void event(const KP<P32>& p, const Inst<float>& ip, unsigned long long pid,
+                               int l, unsigned j, float xe, const State& st, float& kap,
+                               float& sg, float& u3, float& gap) {
     float u1, u2, u4;
     if (j == 0) {
       const uint4 r = st.r;
@@ -348,9 +373,9 @@ struct Draw<P32> {
       u4 = u24(a.w);
     }
     const float z = sqrtf(-2.0f * log1pf(-u1)) * cospif(2.0f * u2);
-    kap = p.sig_k * z;
-    sg = sinf(2.0f * (xe - p.xc) * kap);
-    gap = (-log1pf(-u4)) / p.gamma0;
+    kap = ip.sig_k * z;
+    sg = sinf(2.0f * (xe - ip.xc) * kap);
+    gap = (-log1pf(-u4)) / ip.gamma0;
   }
 };
 
@@ -384,17 +409,18 @@ __device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long i
 
 // An end-of-chunk state produced inside the divergent event code.
 template <class P, int DST>
-__device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc,
+__device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                  unsigned long long pid, typename P::T x, typename P::T k,
                                  typename P::T w) {
   using T = typename P::T;
   int cell;
+  const int cbase = inst * p.nhi;
   if constexpr (DST == DST_BIN1) {
-    if (cell_of<P>(p, x, k, cell)) atomicAdd(p.grid + cell, w > (T)0 ? 1 : -1);
+    if (cell_of<P>(p, x, k, cell)) atomicAdd(p.grid + cbase + cell, w > (T)0 ? 1 : -1);
     else tally_out<P>(p, acc, w);
   } else if constexpr (DST == DST_WSUM) {
     if (cell_of<P>(p, x, k, cell))
-      atomicAdd((unsigned long long*)(p.wsum + cell),
+      atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
                 (unsigned long long)llrint((double)w * 2147483648.0));
   } else if constexpr (DST == DST_BIN2) {
     if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
@@ -414,6 +440,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc,
     p.s[slot] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
     if (p.w) p.w[slot] = w;
     p.cpid[slot - p.cnt->n_base] = pid;
+    if (p.ninst > 1) p.cinst[slot - p.cnt->n_base] = (unsigned)inst;
   }
 }
 
@@ -445,7 +472,7 @@ constexpr unsigned kRootFlag = 0x80000000u;
 // An offspring's state at the end of interval l: the next wave's input, or
 // the sink's in the chunk's last interval.
 template <class P, int DST>
-__device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
+__device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                        unsigned long long pid, typename P::T xo,
                                        typename P::T to, typename P::T k, typename P::T w,
                                        int l) {
@@ -457,7 +484,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
     e.x = xf;
     e.k = k;
     e.w = w;
-    e.l = l + 1;
+    e.l = ent_pack(l + 1, inst);
     const unsigned long long g = global_warp();
     const unsigned q = atomicAdd(&wc.f, 1u);
     if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.qseg)
@@ -465,7 +492,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
     else
       set_err(p.cnt, ERR_CAP_QUEUE);
   } else {
-    emit_child_final<P, DST>(p, wc, acc, pid, xf, k, w);
+    emit_child_final<P, DST>(p, wc, acc, inst, pid, xf, k, w);
   }
 }
 
@@ -486,7 +513,9 @@ __device__ __forceinline__ void defer(const KP<P>& p, WarpCounts& wc, int level,
 // or, when they have an event of their own in the interval, handed to
 // `later`.  Returns the gap to the segment's next event.
 template <class P, int DST, class Later>
-__device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpCounts& wc, Acc& acc,
+__device__ __forceinline__ typename P::T do_event(const KP<P>& p,
+                                                  const Inst<typename P::T>& ip, int inst,
+                                                  WarpCounts& wc, Acc& acc,
                                                   unsigned long long pid, typename P::T xo,
                                                   typename P::T to, typename P::T k,
                                                   typename P::T w,
@@ -495,11 +524,11 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpCounts& wc
   using T = typename P::T;
   const T xe = P::add(xo, P::mul(k, P::mul(P::sub(t, to), p.hm)));
   T kap, sg, u3, gap;
-  Draw<P>::event(p, pid, l, j, xe, st, kap, sg, u3, gap);
-  const T fac = P::mul(p.cacc, (T)fabs(sg));
+  Draw<P>::event(p, ip, pid, l, j, xe, st, kap, sg, u3, gap);
+  const T fac = P::mul(ip.cacc, (T)fabs(sg));
   const bool emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
   if (emit) {
-    if (sg < (T)0) kap = -kap;
+    if (ip.well ? sg > (T)0 : sg < (T)0) kap = -kap;  // orient by sign(V_W)
     const uint4 h = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
                               kDrawPids | j);
     const unsigned long long pid_p = (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
@@ -538,11 +567,11 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p, WarpCounts& wc
       ch.to = t;
       ch.k = c == 0 ? kp : km;
       ch.w = c == 0 ? wc_ : -wc_;
-      ch.l = l;
+      ch.l = ent_pack(l, inst);
       ch.j = 0;
-      ch.t = Draw<P>::first(p, ch.pid, l, t, false, ch.st);
+      ch.t = Draw<P>::first(p, ip, ch.pid, l, t, false, ch.st);
       if (ch.t < p.dt) later(ch);
-      else settle<P, DST>(p, wc, acc, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
+      else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
     }
   }
   return gap;
@@ -557,17 +586,19 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
   while (sp > 0) {
     SEntry<P> s = stack[--sp];
     unsigned j = s.j & ~kRootFlag;
+    const int inst = ent_inst(s.l), l = ent_l(s.l);
+    const Inst<typename P::T>& ip = p.inst[inst];
     auto later = [&](const SEntry<P>& ch) {
       if (sp < kStack) stack[sp++] = ch;
       else set_err(p.cnt, ERR_NESTING);
     };
     while (s.t < p.dt) {
-      const typename P::T gap =
-          do_event<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, j, s.t, later);
+      const typename P::T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k,
+                                                 s.w, s.st, l, j, s.t, later);
       s.t = P::add(s.t, gap);
       ++j;
     }
-    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
+    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l);
   }
 }
 
@@ -579,14 +610,29 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
 // interval's start, k, w, l) of the warp's segment of the candidate queue,
 // for k_event.
 // ---------------------------------------------------------------------------
+// Instance of a slot of the base region: the last instance whose first slot
+// is <= slot (empty instances share their start with the next one).
+template <class P>
+__device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long slot) {
+  if (p.ninst <= 1) return 0;
+  int lo = 0, hi = p.ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.inst_slot[mid] <= slot) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 template <class P, int SRC, int DST>
 __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
                                             unsigned long long slot, typename P::T x,
                                             typename P::T k, typename P::T w,
-                                            unsigned long long pid, int ls) {
+                                            unsigned long long pid, int ls, int inst) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   const unsigned long long g = global_warp();
+  const Inst<T>& ip = p.inst[inst];
+  const int cbase = inst * p.nhi;
 
   // ---- candidate clock over [ls, L) (Sec. 3.2): which intervals hold an
   // event.  Bit b of mask is interval l0 + b.
@@ -597,12 +643,13 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     if constexpr (P::is64) {
       for (int l = ls; l < p.L; ++l) {
         const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
-        if (u53(r.x, r.y) < p.p_hi) mask |= 1u << (l - p.l0);
+        if (u53(r.x, r.y) < ip.p_hi) mask |= 1u << (l - p.l0);
       }
     } else {
       // eight 16-bit coins per Philox call for the intervals 8b .. 8b+7,
       // compared two at a time against floor(65536 p_any)
-      const unsigned thr = p.p16 | (p.p16 << 16);
+      const unsigned p16 = ip.p16;
+      const unsigned thr = p16 | (p16 << 16);
       for (int b = ls >> 3; (b << 3) < p.L; ++b) {
         const uint4 q = philox_ks(p.ks, plo, phi, (uint32_t)b, kDrawCoins);
         const unsigned c0 = __vcmpltu2(q.x, thr), c1 = __vcmpltu2(q.y, thr);
@@ -619,13 +666,13 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
           for (unsigned t = tie; t; t &= t - 1) {
             const int jj = __ffs(t) - 1;
             const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)((b << 3) + jj), 0u);
-            if ((r.w & 0xFFu) < p.p16_frac8) hit |= 1u << jj;
+            if ((r.w & 0xFFu) < ip.p16_frac8) hit |= 1u << jj;
           }
         }
         const int sh = (b << 3) - p.l0;
         mask |= sh >= 0 ? (hit << sh) : (hit >> (-sh));
       }
-      if (p.p16 >= 65536u) mask = ~0u;  // p_any rounds to one: every interval
+      if (p16 >= 65536u) mask = ~0u;  // p_any rounds to one: every interval
       const int lo = ls - p.l0, hi = p.L - p.l0;
       mask &= (hi >= 32 ? ~0u : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
     }
@@ -654,7 +701,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
           e.x = x;
           e.k = k;
           e.w = w;
-          e.l = l;
+          e.l = ent_pack(l, inst);
           p.eq[(long long)g * p.eseg + (long long)q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
@@ -698,6 +745,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
           p.s[off] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
           if (p.w) p.w[off] = w;
           p.cpid[off - p.cnt->n_base] = pid;
+          if (p.ninst > 1) p.cinst[off - p.cnt->n_base] = (unsigned)inst;
         }
       }
     }
@@ -707,7 +755,8 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     unsigned key = ~0u;
     if (act) {
       int cell;
-      if (cell_of<P>(p, x, k, cell)) key = 2u * (unsigned)cell + (w > (T)0 ? 1u : 0u);
+      if (cell_of<P>(p, x, k, cell))
+        key = 2u * (unsigned)(cbase + cell) + (w > (T)0 ? 1u : 0u);
       else tally_out<P>(p, acc, w);
     }
     const unsigned grp = __match_any_sync(kFull, key);
@@ -717,7 +766,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     if (act) {
       int cell;
       if (cell_of<P>(p, x, k, cell))
-        atomicAdd((unsigned long long*)(p.wsum + cell),
+        atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
                   (unsigned long long)llrint((double)w * 2147483648.0));
     }
   } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
@@ -768,7 +817,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         e.x = e.k = e.w = (T)0;
         e.l = p.L;
         if (act) e = p.fq_in[(long long)sg * p.qseg + i];
-        flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, e.l);
+        flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
+                                 ent_inst(e.l));
       }
     }
   } else {
@@ -782,6 +832,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       const bool act = slot < n;
       T x = (T)0, k = (T)0, w = (T)0;
       unsigned long long pid = 0;
+      int inst = 0;
       if constexpr (SRC == SRC_REGEN) {
         // Alg. 3: the cell of each slot.  The tile's first nonzero cell comes
         // from the plan; the 32 slots of a tile lie in at most 32 nonzero
@@ -799,12 +850,17 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         }
         const uint32_t cwl = __shfl_sync(kFull, cw, lo);
         if (act) {
-          const int cell = (int)(cwl & 0x7FFFFFFFu);
+          int cell = (int)(cwl & 0x7FFFFFFFu);
+          if (p.ninst > 1) {
+            inst = (int)((unsigned)cell / (unsigned)p.nhi);
+            cell -= inst * p.nhi;
+          }
           int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
           if (p.nh_big) ix = cell / p.nk;
           int ik = cell - ix * p.nk;
           if (ik < 0) { --ix; ik += p.nk; } else if (ik >= p.nk) { ++ix; ik -= p.nk; }
           pid = p.regen_base | slot;
+          if (p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | (slot - p.inst_slot[inst]);
           const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
           T ux, uk;
           if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
@@ -823,10 +879,19 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
           x = p.x[slot];
           k = p.k[slot];
           w = p.w ? p.w[slot] : (T)p.s[slot];
-          pid = slot < n_base ? base_pid + slot : p.cpid[slot - n_base];
+          if (slot < n_base) {
+            pid = base_pid + slot;
+            if (p.ninst > 1) {
+              inst = base_instance(p, slot);
+              pid = base_pid + ((unsigned long long)inst << 32) + (slot - p.inst_slot[inst]);
+            }
+          } else {
+            pid = p.cpid[slot - n_base];
+            if (p.ninst > 1) inst = (int)p.cinst[slot - n_base];
+          }
         }
       }
-      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L);
+      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst);
     }
   }
 
@@ -881,6 +946,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
       const unsigned i = b + lane;
       if (i < n) {
         const FEntry<T> e = p.eq[(long long)sg * p.eseg + i];
+        const int l = ent_l(e.l), inst = ent_inst(e.l);
+        const Inst<T>& ip = p.inst[inst];
         SEntry<P> s;
         s.pid = e.pid;
         s.xo = e.x;
@@ -888,10 +955,10 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         s.k = e.k;
         s.w = e.w;
         s.l = e.l;
-        s.t = Draw<P>::first(p, e.pid, e.l, (T)0, true, s.st);
+        s.t = Draw<P>::first(p, ip, e.pid, l, (T)0, true, s.st);
         if (s.t < p.dt) {
-          const T gap = do_event<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, 0u,
-                                         s.t, later);
+          const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w,
+                                         s.st, l, 0u, s.t, later);
           s.t = P::add(s.t, gap);
           if (s.t < p.dt) {
             s.j = 1u | kRootFlag;
@@ -927,14 +994,16 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p,
       if (i < n) {
         SEntry<P> s = in[(long long)sg * p.dseg + i];
         const unsigned j = s.j & ~kRootFlag;
-        const T gap = do_event<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, s.l, j,
-                                       s.t, later);
+        const int l = ent_l(s.l), inst = ent_inst(s.l);
+        const Inst<T>& ip = p.inst[inst];
+        const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
+                                       l, j, s.t, later);
         s.t = P::add(s.t, gap);
         if (s.t < p.dt) {
           s.j = (j + 1) | (s.j & kRootFlag);
           defer<P>(p, wc, level + 1, s);
         } else if (!(s.j & kRootFlag)) {
-          settle<P, DST>(p, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.l);
+          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l);
         }
       }
     }
@@ -967,30 +1036,32 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p
 }
 
 // Initial particles from the Gaussian-wavepacket Wigner function (positive):
-// Box-Muller on the init stream of pid = slot, x ~ N(x0, sx^2), k ~ N(k0, sk^2).
+// Box-Muller on the init stream of pid = (instance << 32) | index, with
+// x ~ N(x0, sx^2), k ~ N(k0, sk^2) of the slot's instance.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_init(const KP<P> p,
-                                                 unsigned long long n,
-                                                 double x0, double sx,
-                                                 double k0, double sk) {
+__global__ void __launch_bounds__(kBlock) k_init(const KP<P> p, const InitInst* ini,
+                                                 unsigned long long n) {
   using T = typename P::T;
   for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * kBlock) {
-    const uint4 r = philox_ks(p.ks, (uint32_t)i, (uint32_t)(i >> 32), kStepInit, 0u);
+    const int inst = base_instance(p, i);
+    const InitInst g = ini[inst];
+    const unsigned long long pid = ((unsigned long long)inst << 32) | (i - g.start);
+    const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepInit, 0u);
     T x, k;
     if constexpr (P::is64) {
       const double ua = u53(r.x, r.y), ub = u53(r.z, r.w);
       const double rad = __dsqrt_rn(__dmul_rn(-2.0, log1p(-ua)));
       const double th = __dmul_rn(6.283185307179586476925286766559, ub);
-      x = (T)__dadd_rn(x0, __dmul_rn(sx, __dmul_rn(rad, cos(th))));
-      k = (T)__dadd_rn(k0, __dmul_rn(sk, __dmul_rn(rad, sin(th))));
+      x = (T)__dadd_rn(g.x0, __dmul_rn(g.sx, __dmul_rn(rad, cos(th))));
+      k = (T)__dadd_rn(g.k0, __dmul_rn(g.sk, __dmul_rn(rad, sin(th))));
     } else {
       const float ua = u24(r.x), ub = u24(r.y);
       const float rad = sqrtf(-2.0f * log1pf(-ua));
       float sn, cs;
       sincospif(2.0f * ub, &sn, &cs);
-      x = (T)(x0 + sx * (double)(rad * cs));
-      k = (T)(k0 + sk * (double)(rad * sn));
+      x = (T)(g.x0 + g.sx * (double)(rad * cs));
+      k = (T)(g.k0 + g.sk * (double)(rad * sn));
     }
     p.x[i] = x;
     p.k[i] = k;
@@ -999,14 +1070,26 @@ __global__ void __launch_bounds__(kBlock) k_init(const KP<P> p,
   }
 }
 
-// Stream ids of the materialised particles.
+// Stream ids (and instances, if inst_out is not NULL) of the materialised
+// particles.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_pids(const KP<P> p,
-                                                 unsigned long long* out) {
+__global__ void __launch_bounds__(kBlock) k_pids(const KP<P> p, unsigned long long* out,
+                                                 unsigned* inst_out) {
   const unsigned long long n = p.cnt->n, nb = p.cnt->n_base, bp = p.cnt->base_pid;
   for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * kBlock)
-    out[i] = i < nb ? bp + i : p.cpid[i - nb];
+       i += (unsigned long long)gridDim.x * kBlock) {
+    int inst = 0;
+    unsigned long long pid;
+    if (i < nb) {
+      inst = base_instance(p, i);
+      pid = bp + ((unsigned long long)inst << 32) + (i - p.inst_slot[inst]);
+    } else {
+      pid = p.cpid[i - nb];
+      if (p.ninst > 1) inst = (int)p.cinst[i - nb];
+    }
+    if (out) out[i] = pid;
+    if (inst_out) inst_out[i] = (unsigned)inst;
+  }
 }
 
 }  // namespace wbrw
@@ -1024,10 +1107,6 @@ KP<P> make_kp(const Ctx* c) {
   p.dt = (T)g.dt;
   p.dtv = (T)c->dtv;
   p.hm = (T)c->hm;
-  p.gamma0 = (T)c->gamma0;
-  p.cacc = (T)c->cacc;
-  p.sig_k = (T)c->sig_k;
-  p.xc = (T)c->pot.xc;
   p.xmin = (T)g.xmin;
   p.kmin = (T)g.kmin;
   p.kmax = (T)g.kmax;
@@ -1039,12 +1118,11 @@ KP<P> make_kp(const Ctx* c) {
   p.nk = g.nk;
   p.inv_nk = 1.0f / (float)g.nk;
   p.nh_big = (long long)g.nx * g.nk >= (1ll << 24);
-  p.p_hi = c->p_any * (1.0 + 1e-9) + 1e-300;
-  p.p_any_f = (float)c->p_any;
-  const double sc = c->p_any * 65536.0;
-  const double fl = floor(sc);
-  p.p16 = (unsigned)fl;
-  p.p16_frac8 = (unsigned)floor((sc - fl) * 256.0);
+  p.ninst = c->ninst;
+  p.nhi = (int)c->nhi;
+  p.inst = (const Inst<T>*)c->inst_tab;
+  p.inst_slot = c->inst_slot;
+  p.cinst = c->cinst;
   for (int r = 0; r < 10; ++r) {
     p.ks.k0[r] = (uint32_t)g.seed + (uint32_t)r * 0x9E3779B9u;
     p.ks.k1[r] = (uint32_t)(g.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
@@ -1162,14 +1240,53 @@ cudaError_t events_any(Ctx* c, const KP<P>& p, int dst) {
 
 template <class P>
 struct DriverImpl {
-  static cudaError_t init(Ctx* c, long long n, double x0, double sx, double k0) {
-    cudaError_t e = launch_setup(c, SETUP_INIT, (unsigned long long)n, 0);
+  // The per-instance tables (physics, initial sampling, first slots) are
+  // staged in c->host_tab and copied to the scratch before the first launch.
+  static cudaError_t init(Ctx* c, long long n) {
+    using T = typename P::T;
+    char* h = (char*)c->host_tab;
+    Inst<T>* it = (Inst<T>*)h;
+    InitInst* ii = (InitInst*)(h + kInstTabBytes);
+    unsigned long long* is = (unsigned long long*)(h + kTabSlotOff);
+    double* na = (double*)(h + kTabNaOff);
+    for (int i = 0; i < c->ninst; ++i) {
+      const InstHost& q = c->ih[i];
+      Inst<T> v;
+      v.gamma0 = (T)q.gamma0;
+      v.cacc = (T)q.cacc;
+      v.sig_k = (T)q.sig_k;
+      v.xc = (T)q.xc;
+      v.well = q.H < 0.0;
+      v.p_hi = q.p_any * (1.0 + 1e-9) + 1e-300;
+      v.p_any_f = (float)q.p_any;
+      const double sc = q.p_any * 65536.0;
+      const double fl = floor(sc);
+      v.p16 = (unsigned)fl;
+      v.p16_frac8 = (unsigned)floor((sc - fl) * 256.0);
+      it[i] = v;
+      InitInst g;
+      g.x0 = q.x0;
+      g.sx = q.sx;
+      g.k0 = q.k0;
+      g.sk = 1.0 / (2.0 * q.sx);
+      g.start = q.start;
+      ii[i] = g;
+      is[i] = q.start;
+      na[i] = (double)q.n_alpha;
+    }
+    is[c->ninst] = (unsigned long long)n;
+    static_assert(sizeof(Inst<double>) <= kInstBytes && sizeof(Inst<float>) <= kInstBytes,
+                  "instance record size");
+    static_assert(sizeof(InitInst) <= kInstBytes, "instance record size");
+    cudaError_t e = cudaMemcpyAsync(c->inst_tab, h, kTabTransOff, cudaMemcpyHostToDevice,
+                                    c->stream);
     if (e != cudaSuccess) return e;
+    if ((e = launch_setup(c, SETUP_INIT, (unsigned long long)n, 0)) != cudaSuccess) return e;
     KP<P> p = make_kp<P>(c);
     static int grid = 0;
     if (!grid) grid = grid_for(c, k_init<P>);
-    const double sk = 1.0 / (2.0 * sx);
-    k_init<P><<<grid, kBlock, 0, c->stream>>>(p, (unsigned long long)n, x0, sx, k0, sk);
+    k_init<P><<<grid, kBlock, 0, c->stream>>>(p, (const InitInst*)((char*)c->inst_tab + kInstTabBytes),
+                                              (unsigned long long)n);
     c->launches++;
     return cudaGetLastError();
   }
@@ -1223,11 +1340,11 @@ struct DriverImpl {
     return flight<P, SRC_REGEN, DST_ARRAY>(c, p);
   }
 
-  static cudaError_t pids(Ctx* c, unsigned long long* out) {
+  static cudaError_t pids(Ctx* c, unsigned long long* out, unsigned* inst_out) {
     KP<P> p = make_kp<P>(c);
     static int grid = 0;
     if (!grid) grid = grid_for(c, k_pids<P>);
-    k_pids<P><<<grid, kBlock, 0, c->stream>>>(p, out);
+    k_pids<P><<<grid, kBlock, 0, c->stream>>>(p, out, inst_out);
     c->launches++;
     return cudaGetLastError();
   }

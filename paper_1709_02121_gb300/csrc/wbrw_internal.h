@@ -15,6 +15,16 @@ constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
 constexpr int kMaxBlocksPerSm = 3;  // resident blocks per SM of every queue kernel
+constexpr int kMaxInst = WBRW_MAX_INSTANCES;  // instances of a batch (8 id bits)
+constexpr int kInstBytes = 64;                // one per-instance record on the device
+constexpr size_t kInstTabBytes = (size_t)kMaxInst * kInstBytes;
+// device tables: physics records, initial-sampling records, first slots,
+// N_alpha (double) and the transmissions read-out, in this order; the host
+// stages all but the last
+constexpr size_t kTabSlotOff = 2 * kInstTabBytes;
+constexpr size_t kTabNaOff = kTabSlotOff + (size_t)(kMaxInst + 1) * 8;
+constexpr size_t kTabTransOff = kTabNaOff + (size_t)kMaxInst * 8;
+constexpr size_t kTabBytes = kTabTransOff + (size_t)kMaxInst * 8;
 
 enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2 };
 enum Dst { DST_ARRAY = 0, DST_BIN1 = 1, DST_BIN2 = 2, DST_WSUM = 3 };
@@ -49,6 +59,15 @@ struct Counters {
   int pad[3];
 };
 
+// One instance of a batch, host FP64 (Sec. 4.2 / Remark 3 / Sec. 3.2).
+struct InstHost {
+  double H, w, xc;             // potential
+  double C, sig_k, gamma0, cacc, p_any;
+  double x0, sx, k0;           // initial wavepacket
+  long long n_init, n_alpha;
+  unsigned long long start;    // first slot of its initial particles
+};
+
 struct Ctx {
   wbrw_config cfg;
   wbrw_potential pot;
@@ -56,9 +75,18 @@ struct Ctx {
   cudaStream_t stream;
   int device;
   int num_sms;
-  // constants (Sec. 4.2 / Remark 3 / Sec. 3.2), host FP64
-  double C, sig_k, gamma0, cacc, hm, dtv, p_any, dx, dk, inv_dx, inv_dk;
-  long long nh;  // cells
+  // constants (Sec. 4.2 / Remark 3 / Sec. 3.2), host FP64; per instance in ih
+  double hm, dtv, dx, dk, inv_dx, inv_dk;
+  int ninst;          // instances (1 for wbrw_init)
+  InstHost* ih;       // ninst records (host)
+  void* host_tab;     // staging copy of the device tables (kTabBytes)
+  long long nhi;      // cells per instance
+  long long nh;       // cells of all instances (ninst nhi)
+  void* inst_tab;     // device tables (kTabBytes, in the scratch)
+  unsigned long long* inst_slot;  // first slot of each instance's base particles (+ total)
+  unsigned* cinst;    // instance of each appended offspring (batches only)
+  double* inst_na;    // N_alpha of each instance (device)
+  double* inst_trans; // transmissions read-out (device)
   // scratch carve-up
   Counters* cnt;
   unsigned long long* cpid;
@@ -118,7 +146,7 @@ void prof_begin(Ctx*);
 void prof_end(Ctx*);
 
 struct Driver {
-  cudaError_t (*init)(Ctx*, long long n, double x0, double sx, double k0);
+  cudaError_t (*init)(Ctx*, long long n);
   // Fly [l0, L) from the source, offspring in waves, finals to dst.
   cudaError_t (*chunk)(Ctx*, int l0, int L, int src, int dst);
   // Histogram the arrays (no flight): dst = DST_BIN1 into grid / DST_BIN2
@@ -126,7 +154,7 @@ struct Driver {
   cudaError_t (*bin)(Ctx*, int dst, int* grid, int count_ledger);
   // Regenerate the histogram into the arrays (Alg. 3).
   cudaError_t (*materialize)(Ctx*);
-  cudaError_t (*pids)(Ctx*, unsigned long long* out);
+  cudaError_t (*pids)(Ctx*, unsigned long long* out, unsigned* inst_out);
 };
 
 const Driver* driver_fp64();
@@ -137,8 +165,15 @@ cudaError_t launch_setup(Ctx*, int op, unsigned long long a,
                          unsigned long long b);
 cudaError_t launch_scan_cells(Ctx*, const int* grid);
 cudaError_t launch_boot(Ctx*);
-cudaError_t launch_observables(Ctx*, const int* counts, const long long* wsum);
+// Observables of instance `inst` from the counts / Q1.31 weight sums of all
+// instances (one of the two is NULL).
+cudaError_t launch_observables(Ctx*, int inst, const int* counts, const long long* wsum);
+// Transmission of every instance into out (ninst doubles, device).
+cudaError_t launch_transmissions(Ctx*, const int* counts, double* out);
 cudaError_t launch_zero(Ctx*, void* p, size_t bytes);
+// Materialised particles of instance `inst` (base region + offspring) added
+// to *out (device).
+cudaError_t launch_live_instance(Ctx*, int inst, unsigned long long* out);
 
 enum { SETUP_CHUNK = 0, SETUP_AFTER_REGEN = 1, SETUP_INIT = 2,
        SETUP_BOOT = 3 };

@@ -33,7 +33,9 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_run", "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
            "wbrw_restore", "wbrw_profile", "wbrw_profile_read", "wbrw_counters",
            "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy",
-           "wbrw_observables_static")
+           "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
+           "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances")
+MAX_INSTANCES = 256
 
 
 class Config(ctypes.Structure):
@@ -52,6 +54,12 @@ class Config(ctypes.Structure):
 class Potential(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("H", ctypes.c_double),
                 ("w", ctypes.c_double), ("xc", ctypes.c_double)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("pot", Potential), ("x0", ctypes.c_double), ("sigma_x", ctypes.c_double),
+                ("k0", ctypes.c_double), ("n_init", ctypes.c_longlong),
+                ("n_alpha", ctypes.c_longlong), ("gamma0", ctypes.c_double)]
 
 
 class Buffers(ctypes.Structure):
@@ -94,10 +102,19 @@ def load(path: str = LIB_PATH):
                             ctypes.POINTER(Buffers), LL, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, P,
                             ctypes.POINTER(P)]
+    L.wbrw_batch_scratch_bytes.argtypes = [ctypes.POINTER(Config), I, LL]
+    L.wbrw_batch_scratch_bytes.restype = ctypes.c_size_t
+    L.wbrw_batch_init.argtypes = [ctypes.POINTER(Config), I, ctypes.POINTER(Instance),
+                                  ctypes.POINTER(Buffers), P, ctypes.POINTER(P)]
+    L.wbrw_instance_density.argtypes = [P, I, P, P, P, P]
+    L.wbrw_transmissions.argtypes = [P, P]
+    L.wbrw_particle_instances.argtypes = [P, P]
     for name in ("wbrw_init", "wbrw_step", "wbrw_annihilate", "wbrw_run",
                  "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
                  "wbrw_restore", "wbrw_profile", "wbrw_profile_read",
-                 "wbrw_counters", "wbrw_sync_status"):
+                 "wbrw_counters", "wbrw_sync_status", "wbrw_batch_init",
+                 "wbrw_instance_density", "wbrw_transmissions",
+                 "wbrw_particle_instances"):
         getattr(L, name).restype = I
     L.wbrw_checkpoint.argtypes = [P, P, P, P]
     L.wbrw_restore.argtypes = [P, P, LL, LL]
@@ -140,6 +157,40 @@ def wbrw_init(cfg, pot, bufs, n_init, x0, sigma_x, k0, stream_ptr):
     if st != OK:
         raise WbrwError(st, "wbrw_init rejected its arguments")
     return ctx
+
+
+def wbrw_batch_scratch_bytes(cfg: Config, ninst: int, capacity: int) -> int:
+    return load().wbrw_batch_scratch_bytes(ctypes.byref(cfg), ninst, capacity)
+
+
+def wbrw_batch_init(cfg, instances, bufs, stream_ptr):
+    arr = (Instance * len(instances))(*instances)
+    ctx = ctypes.c_void_p()
+    st = load().wbrw_batch_init(ctypes.byref(cfg), len(instances), arr, ctypes.byref(bufs),
+                                ctypes.c_void_p(stream_ptr), ctypes.byref(ctx))
+    if st != OK:
+        raise WbrwError(st, "wbrw_batch_init rejected its arguments")
+    return ctx
+
+
+def wbrw_instance_density(ctx, inst, nx, nk):
+    dens = np.empty(nx * nk, np.float64)
+    marg = np.empty(nx, np.float64)
+    T = ctypes.c_double()
+    live = ctypes.c_longlong()
+    _check(ctx, load().wbrw_instance_density(ctx, inst, dens.ctypes.data, marg.ctypes.data,
+                                             ctypes.byref(T), ctypes.byref(live)))
+    return dens.reshape(nx, nk), marg, T.value, live.value
+
+
+def wbrw_transmissions(ctx, ninst):
+    out = np.empty(ninst, np.float64)
+    _check(ctx, load().wbrw_transmissions(ctx, out.ctypes.data))
+    return out
+
+
+def wbrw_particle_instances(ctx, inst_dev_ptr):
+    _check(ctx, load().wbrw_particle_instances(ctx, ctypes.c_void_p(inst_dev_ptr)))
 
 
 def wbrw_step(ctx, nsteps):
@@ -231,7 +282,15 @@ class Simulation:
     particles held at once (and each offspring wave).
     """
 
+    ninst = 1
+
     def __init__(self, wl: dict, capacity: int, *, event_log: int = 0, stream=None):
+        self._buffers(wl, capacity, event_log, stream)
+        self.pot = Potential(POT_GAUSSIAN, wl["H"], wl["w"], wl["xc"])
+        self.ctx = wbrw_init(self.cfg, self.pot, self.bufs, int(wl["n_alpha"]),
+                             wl["x0"], wl["sigma_x"], wl["k0"], self.stream.cuda_stream)
+
+    def _buffers(self, wl, capacity, event_log, stream):
         import torch
         self.torch = torch
         self.wl = dict(wl)
@@ -240,7 +299,6 @@ class Simulation:
         self.cfg = Config(2, prec, strat, wl["hbar"], wl["mass"], wl["dt"], wl["gamma0"],
                           wl["nx"], wl["nk"], wl["xmin"], wl["xmax"], wl["kmin"], wl["kmax"],
                           wl["resample_every"], int(wl["n_alpha"]), int(wl["seed"]))
-        self.pot = Potential(POT_GAUSSIAN, wl["H"], wl["w"], wl["xc"])
         dev = torch.device("cuda", torch.cuda.current_device())
         fdt = torch.float64 if prec == FP64 else torch.float32
         self.nx, self.nk = wl["nx"], wl["nk"]
@@ -249,8 +307,10 @@ class Simulation:
         self.k = torch.empty(self.capacity, dtype=fdt, device=dev)
         self.s = torch.empty(self.capacity, dtype=torch.int8, device=dev)
         self.w = torch.empty(self.capacity, dtype=fdt, device=dev) if strat == SP2_BOOTSTRAP else None
-        self.grid = torch.zeros(self.nx * self.nk, dtype=torch.int32, device=dev)
-        nbytes = wbrw_scratch_bytes(self.cfg, self.capacity)
+        cells = self.ninst * self.nx * self.nk
+        self.grid = torch.zeros(cells, dtype=torch.int32, device=dev)
+        nbytes = (wbrw_scratch_bytes(self.cfg, self.capacity) if type(self) is Simulation
+                  else wbrw_batch_scratch_bytes(self.cfg, self.ninst, self.capacity))
         if nbytes == 0:
             raise ValueError("invalid configuration")
         self.scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -258,13 +318,11 @@ class Simulation:
                     if event_log else None)
         self.bufs = Buffers(self.x.data_ptr(), self.k.data_ptr(), self.s.data_ptr(),
                             self.w.data_ptr() if self.w is not None else None,
-                            self.capacity, self.grid.data_ptr(), self.nx * self.nk,
+                            self.capacity, self.grid.data_ptr(), cells,
                             self.scratch.data_ptr(), nbytes,
                             self.log.data_ptr() if self.log is not None else None,
                             event_log)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.ctx = wbrw_init(self.cfg, self.pot, self.bufs, int(wl["n_alpha"]),
-                             wl["x0"], wl["sigma_x"], wl["k0"], self.stream.cuda_stream)
 
     def step(self, n=1):
         wbrw_step(self.ctx, n)
@@ -285,7 +343,8 @@ class Simulation:
         """Copy the histogram into grid_out (host or device int32 array-like
         with a data pointer; a new host array if None); returns (grid, step, epoch)."""
         if grid_out is None:
-            grid_out = np.empty((self.nx, self.nk), np.int32)
+            grid_out = np.empty(((self.ninst,) if self.ninst > 1 else ()) + (self.nx, self.nk),
+                                np.int32)
         ptr = grid_out.ctypes.data if isinstance(grid_out, np.ndarray) else grid_out.data_ptr()
         step, epoch = wbrw_checkpoint(self.ctx, ptr)
         return grid_out, step, epoch
@@ -315,6 +374,8 @@ class Simulation:
         return x, k, s, w, pid
 
     def grid_counts(self):
+        if self.ninst > 1:
+            return self.grid.view(self.ninst, self.nx, self.nk).cpu().numpy()
         return self.grid.view(self.nx, self.nk).cpu().numpy()
 
     def event_log(self):
@@ -335,3 +396,34 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+class Batch(Simulation):
+    """Many independent problems in the same launches (sp1 only).
+
+    ``wl`` gives the shared configuration (precision, dt, grid, seed, ...);
+    ``instances`` is a list of dicts with keys H, w, xc, x0, sigma_x, k0,
+    n_init, n_alpha and optionally gamma0 (default: the majorant C/2).
+    """
+
+    def __init__(self, wl: dict, instances, capacity: int, *, event_log: int = 0, stream=None):
+        self.ninst = len(instances)
+        self._buffers(wl, capacity, event_log, stream)
+        self.instances = [dict(v) for v in instances]
+        recs = [Instance(Potential(POT_GAUSSIAN, v["H"], v["w"], v.get("xc", 0.0)),
+                         v["x0"], v["sigma_x"], v["k0"], int(v["n_init"]), int(v["n_alpha"]),
+                         v.get("gamma0", 0.0)) for v in instances]
+        self.ctx = wbrw_batch_init(self.cfg, recs, self.bufs, self.stream.cuda_stream)
+
+    def density(self, inst=0):
+        return wbrw_instance_density(self.ctx, inst, self.nx, self.nk)
+
+    def transmissions(self):
+        return wbrw_transmissions(self.ctx, self.ninst)
+
+    def particles(self, with_pids=True):
+        """(x, k, s, w, pid, inst) of the current particles as host arrays."""
+        x, k, s, w, pid = super().particles(with_pids)
+        t = self.torch.empty(max(len(x), 1), dtype=self.torch.int32, device=self.x.device)
+        wbrw_particle_instances(self.ctx, t.data_ptr())
+        return x, k, s, w, pid, t[: len(x)].cpu().numpy().view(np.uint32)

@@ -56,3 +56,39 @@ COLLISION_2D = dict(
     precision="fp64", strategy="sp1", seed=0, hbar=1.0, mass=1.0,
     gamma0=0.0,
 )
+
+
+# Batched 2D: 256 independent Gaussian-barrier problems in the same launches,
+# FP32, 600 x 256 cells each over x in [-60, 60), k in [-6.4, 6.4), dt = 0.05,
+# resampling every 10 intervals.  Per instance, drawn from a generator seeded
+# with `seed`: H ~ U[0.5, 2], w ~ U[0.5, 2], k0 ~ U[1, 2.5] and an initial
+# particle count (= N_alpha) log-uniform in [1e4, 4e6]; the packet is the one
+# of the 2D workloads (x0 = -15, sigma_x = 2.5).
+BATCH_2D_FP32_256 = dict(
+    name="batch2d_fp32_256x600x256",
+    instances=256, H_range=(0.5, 2.0), w_range=(0.5, 2.0), k0_range=(1.0, 2.5),
+    n_range=(1e4, 4e6), x0=-15.0, sigma_x=2.5, xc=0.0,
+    dt=0.05, resample_every=10,
+    nx=600, nk=256, xmin=-60.0, xmax=60.0, kmin=-6.4, kmax=6.4,
+    precision="fp32", strategy="sp1", seed=0, hbar=1.0, mass=1.0,
+    gamma0=0.0, n_alpha=1, H=1.0, w=1.0, k0=1.5,
+)
+
+
+def batch_instances(spec: dict, n_scale: float = 1.0) -> list:
+    """The seeded instance parameters of a batched workload (inputs only).
+    n_scale shrinks every particle count (small test and profiling cases)."""
+    import numpy as np
+    rng = np.random.default_rng(spec["seed"])
+    m = spec["instances"]
+    H = rng.uniform(*spec["H_range"], m)
+    w = rng.uniform(*spec["w_range"], m)
+    k0 = rng.uniform(*spec["k0_range"], m)
+    lo, hi = np.log(spec["n_range"][0]), np.log(spec["n_range"][1])
+    n = np.exp(rng.uniform(lo, hi, m))
+    out = []
+    for i in range(m):
+        cnt = max(1, int(round(n[i] * n_scale)))
+        out.append(dict(H=float(H[i]), w=float(w[i]), xc=spec["xc"], x0=spec["x0"],
+                        sigma_x=spec["sigma_x"], k0=float(k0[i]), n_init=cnt, n_alpha=cnt))
+    return out
