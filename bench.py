@@ -54,6 +54,8 @@ def parse():
                     help="override the particle count (profiling small cases)")
     ap.add_argument("--capacity-factor", type=float, default=4.0,
                     help="particle capacity as a multiple of the particle count")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="launch every period kernel by kernel instead of replaying a CUDA graph")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -188,6 +190,7 @@ def config_of(wl, args):
             "intervals_per_step": wl["resample_every"], "strategy": wl["strategy"],
             "precision": wl["precision"], "potential": "gaussian H=%g w=%g" % (wl["H"], wl["w"]),
             "l2": "flushed (512 MiB write) between timed steps",
+            "cuda_graphs": not args.no_graph and wl["strategy"] == "sp1",
             "parallelism": "replicas x%d" % args.gpus}
 
 
@@ -210,8 +213,11 @@ def ours(args, wl):
     wl = workloads.scaled(wl, seed=wl["seed"] + rank)
     n = int(wl["n_alpha"])
     cap = int(args.capacity_factor * n) + (1 << 20)
-    sim = Simulation(wl, capacity=cap)
+    sim = Simulation(wl, capacity=cap, stream=torch.cuda.Stream())
     stream = sim.stream
+    graphs = not args.no_graph and wl["strategy"] == "sp1"
+    if graphs:
+        sim.graph(True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
     def barrier():
@@ -326,8 +332,11 @@ def ours_batch(args, spec):
     insts = workloads.batch_instances(wl, args.n_scale)
     n_total = sum(v["n_init"] for v in insts)
     cap = int(args.capacity_factor * n_total) + (1 << 20)
-    sim = Batch(wl, insts, capacity=cap)
+    sim = Batch(wl, insts, capacity=cap, stream=torch.cuda.Stream())
     stream = sim.stream
+    graphs = not args.no_graph
+    if graphs:
+        sim.graph(True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
     def barrier():
@@ -396,7 +405,7 @@ def ours_batch(args, spec):
         base = workloads.scaled(wl, n_alpha=nmax)
         host = Simulation.__new__(Simulation)
         host.ninst = 1
-        host._buffers(base, int(args.capacity_factor * nmax) + (1 << 20), 0, None)
+        host._buffers(base, int(args.capacity_factor * nmax) + (1 << 20), 0, torch.cuda.Stream())
         t_plain, ps_plain = 0.0, 0
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         for v in insts:
@@ -406,6 +415,8 @@ def ours_batch(args, spec):
             pot = wbrw.Potential(wbrw.POT_GAUSSIAN, v["H"], v["w"], v["xc"])
             ctx = wbrw.wbrw_init(cfg, pot, host.bufs, int(v["n_init"]), v["x0"], v["sigma_x"],
                                  v["k0"], host.stream.cuda_stream)
+            if graphs:
+                wbrw.wbrw_graph(ctx, True)
             for _ in range(args.warmup):
                 wbrw.wbrw_run(ctx, P)
             p0 = wbrw.wbrw_counters(ctx)["particle_steps"]
@@ -420,7 +431,8 @@ def ours_batch(args, spec):
             wbrw.wbrw_destroy(ctx)
         plain = {"value": ps_plain / (t_plain / 1e3), "unit": UNIT,
                  "ms_per_step": t_plain / args.steps, "particle_steps": ps_plain,
-                 "path": "one context per instance, instances one after the other"}
+                 "path": "one context per instance, instances one after the other",
+                 "cuda_graphs": graphs}
 
     t_max, ps_all, e2e_sum = reduce_over_ranks(ws, t_ms, psteps, e2e["value"] if e2e else 0.0,
                                                "cuda")
@@ -444,6 +456,7 @@ def ours_batch(args, spec):
                            "particles": int(n_total), "particles_min_max": [min(ns), max(ns)],
                            "grid_per_instance": [wl["nx"], wl["nk"]], "dt": wl["dt"],
                            "intervals_per_step": P, "strategy": "sp1", "precision": "fp32",
+                           "cuda_graphs": graphs,
                            "l2": "flushed (512 MiB write) between timed steps",
                            "parallelism": "replicas x%d" % ws},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,

@@ -223,6 +223,19 @@ wbrw_status wbrw_profile(wbrw_ctx* ctx, int enable);
 wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
                               long long* launches);
 
+/* CUDA graphs for wbrw_run.  With enable = 1, each sp1 resampling period that
+ * regenerates its particles from the histogram (every period but one that
+ * starts from the initial particles or from wbrw_step) is captured into a
+ * CUDA graph the first time a period of its length runs, and replayed after
+ * that: one launch per period instead of one per kernel.  Results are bit
+ * for bit those of enable = 0 (the kernels read the period's first interval
+ * and id base from device memory, and the graph advances them).  The context
+ * stream must be a created stream (not the legacy or per-thread default
+ * stream) and must not be capturing; otherwise WBRW_ERR_ARG.  enable = 0
+ * synchronises the stream and releases the graphs.  sp2 periods always
+ * launch kernel by kernel. */
+wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
+
 /* Observables of a signed histogram without any allocation and without a
  * context.  The paper has no counterpart: this is an interface for callers
  * that cannot call cudaMalloc, such as code running inside a fixed device

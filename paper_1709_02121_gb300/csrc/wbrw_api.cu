@@ -209,6 +209,120 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
   return WBRW_OK;
 }
 
+// One fused period of wbrw_run: zero the histogram (sp1) or the bootstrap
+// tallies (sp2), fly [l0, L) from src into the sink, bootstrap (sp2), and
+// build the regeneration plan.  The source's ids are those of regen_epoch;
+// the histogram made here is epoch regen_epoch + 1, which c->epoch holds on
+// return.
+wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_epoch) {
+  const Driver* d = drv(c);
+  c->epoch = regen_epoch + 1;
+  if (c->cfg.strategy == WBRW_SP1_PAIR) {
+    WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
+  } else {
+    WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
+    WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
+    for (int s = 0; s < 2; ++s) {
+      WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
+      WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
+    }
+  }
+  // the regeneration of the previous histogram uses its own epoch's ids
+  const long long keep_epoch = c->epoch;
+  c->epoch = regen_epoch;
+  cudaError_t e = d->chunk(c, l0, L, src,
+                           c->cfg.strategy == WBRW_SP1_PAIR ? DST_BIN1 : DST_BIN2);
+  c->epoch = keep_epoch;
+  WBRW_TRY(c, e, "period");
+  if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c), "bootstrap");
+  WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+  return WBRW_OK;
+}
+
+void drop_graphs(wbrw_ctx* c) {
+  for (int i = 0; i < c->ngraphs; ++i) {
+    if (c->graphs[i].exec) cudaGraphExecDestroy(c->graphs[i].exec);
+    if (c->graphs[i].graph) cudaGraphDestroy(c->graphs[i].graph);
+  }
+  c->ngraphs = 0;
+}
+
+// Capture one sp1 period of length len that regenerates from the histogram.
+// Its kernels take the first interval and the id base from the device
+// period state, which the graph advances at its end.
+wbrw_status capture_period(wbrw_ctx* c, int len, PeriodGraph* g) {
+  memset(g, 0, sizeof(*g));
+  g->len = len;
+  const long long launches0 = c->launches;
+  const long long epoch0 = c->epoch;
+  WBRW_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal),
+           "begin capture");
+  c->capturing = 1;
+  wbrw_status st = enqueue_period(c, SRC_REGEN, (int)c->step, (int)c->step + len, c->epoch);
+  if (st == WBRW_OK)
+    st = cuda_check(c, launch_setup(c, SETUP_ADVANCE, (unsigned long long)len, 0), "advance");
+  c->capturing = 0;
+  c->epoch = epoch0;
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+  g->launches = c->launches - launches0;
+  c->launches = launches0;
+  if (st != WBRW_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  WBRW_TRY(c, e, "end capture");
+  g->graph = graph;
+  size_t n = 0;
+  WBRW_TRY(c, cudaGraphGetNodes(graph, nullptr, &n), "graph nodes");
+  cudaGraphNode_t* nodes = (cudaGraphNode_t*)calloc(n ? n : 1, sizeof(cudaGraphNode_t));
+  if (!nodes) return seterr(c, WBRW_ERR_ARG, "out of host memory");
+  cudaError_t ge = cudaGraphGetNodes(graph, nodes, &n);
+  for (size_t i = 0; ge == cudaSuccess && i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord)
+      continue;
+    cudaEvent_t ev;
+    if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
+    if (ev == c->gev[0]) g->ev_begin = nodes[i];
+    if (ev == c->gev[1]) g->ev_end = nodes[i];
+  }
+  free(nodes);
+  WBRW_TRY(c, ge, "graph nodes");
+  WBRW_TRY(c, cudaGraphInstantiate(&g->exec, graph, 0), "instantiate graph");
+  return WBRW_OK;
+}
+
+// Replay (capturing first if needed) one regenerating sp1 period.
+wbrw_status graph_period(wbrw_ctx* c, int len) {
+  PeriodGraph* g = nullptr;
+  for (int i = 0; i < c->ngraphs; ++i)
+    if (c->graphs[i].len == len) g = &c->graphs[i];
+  if (!g) {
+    if (c->ngraphs == kMaxGraphs) drop_graphs(c);
+    g = &c->graphs[c->ngraphs];
+    wbrw_status st = capture_period(c, len, g);
+    if (st != WBRW_OK) return st;
+    c->ngraphs += 1;
+  }
+  if (!c->dev_period_ok)
+    WBRW_TRY(c, launch_setup(c, SETUP_PERIOD, (unsigned long long)c->step,
+                             (unsigned long long)c->epoch << 40), "period state");
+  if (g->ev_begin && g->ev_end) {
+    const bool on = c->prof_on && c->prof_n < 4096;
+    WBRW_TRY(c, cudaGraphExecEventRecordNodeSetEvent(
+                    g->exec, g->ev_begin, on ? c->prof_ev[2 * c->prof_n] : c->gev[0]),
+             "profile event");
+    WBRW_TRY(c, cudaGraphExecEventRecordNodeSetEvent(
+                    g->exec, g->ev_end, on ? c->prof_ev[2 * c->prof_n + 1] : c->gev[1]),
+             "profile event");
+    if (on) c->prof_n += 1;
+  }
+  WBRW_TRY(c, cudaGraphLaunch(g->exec, c->stream), "graph launch");
+  c->launches += g->launches;
+  return WBRW_OK;
+}
+
 wbrw_status ensure_particles(wbrw_ctx* c) {
   if (c->state == ST_PARTICLES) return WBRW_OK;
   WBRW_TRY(c, drv(c)->materialize(c), "regenerate");
@@ -232,11 +346,21 @@ wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
 }  // namespace
 
 namespace wbrw {
+// While a period is captured the pair becomes two event-record nodes on
+// placeholder events; each replay points them at the profiling events.
 void prof_begin(Ctx* c) {
+  if (c->capturing) {
+    cudaEventRecordWithFlags(c->gev[0], c->stream, cudaEventRecordExternal);
+    return;
+  }
   if (!c->prof_on || c->prof_n >= 4096) return;
   cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
 }
 void prof_end(Ctx* c) {
+  if (c->capturing) {
+    cudaEventRecordWithFlags(c->gev[1], c->stream, cudaEventRecordExternal);
+    return;
+  }
   if (!c->prof_on || c->prof_n >= 4096) return;
   cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
   c->prof_n += 1;
@@ -458,30 +582,16 @@ wbrw_status wbrw_run(wbrw_ctx* c, int nsteps) {
       continue;
     }
     // one fused period: (regenerate) + fly to the boundary + histogram
-    const Driver* d = drv(c);
     const int src = c->state == ST_HISTOGRAM ? SRC_REGEN : SRC_ARRAY;
     const int l0 = (int)c->step, L = l0 + to_boundary;
     const long long regen_epoch = c->epoch;
-    c->epoch += 1;  // the histogram this period produces
-    if (c->cfg.strategy == WBRW_SP1_PAIR) {
-      WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
-    } else {
-      WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
-      WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
-      for (int s = 0; s < 2; ++s) {
-        WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
-        WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
-      }
-    }
-    // the regeneration of the previous histogram uses its own epoch's ids
-    const long long keep_epoch = c->epoch;
-    c->epoch = regen_epoch;
-    cudaError_t e = d->chunk(c, l0, L, src,
-                             c->cfg.strategy == WBRW_SP1_PAIR ? DST_BIN1 : DST_BIN2);
-    c->epoch = keep_epoch;
-    WBRW_TRY(c, e, "period");
-    if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c), "bootstrap");
-    WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+    wbrw_status st;
+    if (c->graph_on && src == SRC_REGEN && c->cfg.strategy == WBRW_SP1_PAIR)
+      st = graph_period(c, to_boundary);
+    else
+      st = enqueue_period(c, src, l0, L, regen_epoch);
+    if (st != WBRW_OK) return st;
+    c->epoch = regen_epoch + 1;  // the histogram this period produced
     c->step = L;
     c->state = ST_HISTOGRAM;
     c->fresh = 1;
@@ -647,6 +757,29 @@ wbrw_status wbrw_restore(wbrw_ctx* c, const int* grid, long long step, long long
   c->epoch = epoch;
   c->state = ST_HISTOGRAM;
   c->fresh = 1;
+  c->dev_period_ok = 0;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_graph(wbrw_ctx* c, int enable) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (enable && !c->gev_created) {
+    for (int i = 0; i < 2; ++i)
+      WBRW_TRY(c, cudaEventCreateWithFlags(&c->gev[i], cudaEventDefault), "create events");
+    c->gev_created = 1;
+  }
+  if (enable) {
+    cudaStreamCaptureStatus cs;
+    WBRW_TRY(c, cudaStreamIsCapturing(c->stream, &cs), "stream");
+    if (c->stream == nullptr || c->stream == cudaStreamLegacy ||
+        c->stream == cudaStreamPerThread || cs != cudaStreamCaptureStatusNone)
+      return seterr(c, WBRW_ERR_ARG, "graph capture needs a created, non-capturing stream");
+  } else {
+    WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+    drop_graphs(c);
+  }
+  c->graph_on = enable ? 1 : 0;
   return WBRW_OK;
 }
 
@@ -679,6 +812,10 @@ wbrw_status wbrw_profile_read(wbrw_ctx* c, double* total_ms, long long* launches
 
 void wbrw_destroy(wbrw_ctx* c) {
   if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->gev_created)
+    for (int i = 0; i < 2; ++i) cudaEventDestroy(c->gev[i]);
   if (c->prof_created)
     for (int i = 0; i < 2 * 4096; ++i) cudaEventDestroy(c->prof_ev[i]);
   free_ctx(c);

@@ -45,16 +45,30 @@ constexpr uint32_t kStepRound = 0xFFFFFFFCu;
 // ---------------------------------------------------------------------------
 __global__ void k_setup(Counters* c, int op, unsigned long long a,
                         unsigned long long b) {
-  (void)b;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   switch (op) {
     case SETUP_CHUNK:
       c->n_src = c->n;
+      c->per_l0 = (int)a;
+      c->per_regen_base = b;
+      break;
+    case SETUP_CHUNK_DEV:
+      c->n_src = c->n;
+      break;
+    case SETUP_PERIOD:
+      c->per_l0 = (int)a;
+      c->per_regen_base = b;
+      break;
+    case SETUP_ADVANCE:
+      c->per_l0 += (int)a;
+      c->per_regen_base += 1ull << 40;
       break;
     case SETUP_AFTER_REGEN:
       c->n = c->regen_total;
       c->n_base = c->regen_total;
       c->base_pid = a;
+      c->per_regen_base = a;
+      c->per_l0 = (int)b;
       break;
     case SETUP_INIT:
       c->n = a;
@@ -449,6 +463,8 @@ int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
 }  // namespace
 
 cudaError_t launch_setup(Ctx* c, int op, unsigned long long a, unsigned long long b) {
+  if (op == SETUP_CHUNK || op == SETUP_AFTER_REGEN) c->dev_period_ok = 0;
+  if (op == SETUP_PERIOD) c->dev_period_ok = 1;
   k_setup<<<1, 32, 0, c->stream>>>(c->cnt, op, a, b);
   c->launches++;
   return cudaGetLastError();

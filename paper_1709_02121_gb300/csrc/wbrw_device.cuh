@@ -167,7 +167,8 @@ struct KP {
   unsigned* cinst;                        // instance of offspring appended to the arrays
   KeySched ks;      // Philox key schedule of the run seed
   int strategy;     // 1 = sp1, 2 = sp2
-  int l0, L, round;
+  int l0, L;        // the intervals [l0, L) of the chunk (read at kernel entry)
+  int len;          // L - l0
   unsigned long long regen_base;  // epoch << 40 of the histogram's particles
   T* x;
   T* k;
@@ -202,6 +203,19 @@ struct KP {
   long long log_cap;
   int count_ledger;
 };
+
+// The chunk's first interval and the regeneration's id base are
+// device-resident (Counters::per_*): the chunk set-up writes them, and a
+// captured period advances them in place, so that one captured period replays
+// correctly.  Each kernel takes them into its own copy of the parameters.
+template <class P>
+__device__ __forceinline__ KP<P> with_period(const KP<P>& q) {
+  KP<P> p = q;
+  p.l0 = q.cnt->per_l0;
+  p.L = p.l0 + q.len;
+  p.regen_base = q.cnt->per_regen_base;
+  return p;
+}
 
 constexpr int kWarps = kBlock / 32;
 constexpr int kStack = 32;    // pending offspring frames per thread (drain)
@@ -503,7 +517,7 @@ __device__ __forceinline__ void defer(const KP<P>& p, WarpCounts& wc, int level,
   const unsigned long long g = global_warp();
   const unsigned q = atomicAdd(&wc.d, 1u);
   if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.dseg)
-    p.dq[level & 1][(long long)g * p.dseg + (long long)q] = s;
+    ((level & 1) ? p.dq[1] : p.dq[0])[(long long)g * p.dseg + (long long)q] = s;
   else
     set_err(p.cnt, ERR_CAP_EQUEUE);
 }
@@ -793,7 +807,8 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
 }
 
 template <class P, int SRC, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> p_) {
+  const KP<P> p = with_period(p_);
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -928,7 +943,8 @@ __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, co
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p_) {
+  const KP<P> p = with_period(p_);
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -973,7 +989,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p, int level) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_, int level) {
+  const KP<P> p = with_period(p_);
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -984,7 +1001,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p,
   load_counts(p, wc, level + 1);
   const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
-  const SEntry<P>* in = p.dq[level & 1];
+  const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, level + 1, ch); };
   for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
@@ -1013,7 +1030,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p,
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p_) {
+  const KP<P> p = with_period(p_);
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
   const int lane = threadIdx.x & 31;
@@ -1024,7 +1042,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p
   const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   const int level = kLevels - 1;
-  const SEntry<P>* in = p.dq[level & 1];
+  const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
   for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
     const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
@@ -1129,7 +1147,7 @@ KP<P> make_kp(const Ctx* c) {
   }
   p.strategy = g.strategy;
   p.l0 = p.L = (int)c->step;
-  p.round = 0;
+  p.len = 0;
   p.regen_base = (unsigned long long)c->epoch << 40;
   p.x = (T*)c->buf.x;
   p.k = (T*)c->buf.k;
@@ -1295,15 +1313,16 @@ struct DriverImpl {
   // or later; offspring start one interval after their birth, so L - l0
   // rounds drain every wave.
   static cudaError_t chunk(Ctx* c, int l0, int L, int src, int dst) {
-    cudaError_t e = launch_setup(c, SETUP_CHUNK, 0, 0);
+    cudaError_t e = launch_setup(c, c->capturing ? SETUP_CHUNK_DEV : SETUP_CHUNK,
+                                 (unsigned long long)l0, (unsigned long long)c->epoch << 40);
     if (e != cudaSuccess) return e;
     KP<P> p = make_kp<P>(c);
     p.l0 = l0;
     p.L = L;
+    p.len = L - l0;
     const int rounds = L > l0 ? L - l0 : 1;
     const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
     for (int r = 0; r < rounds; ++r) {
-      p.round = r;
       p.fq_in = (FEntry<typename P::T>*)c->fq[r & 1];
       p.fcnt_in = c->fcnt[r & 1];
       p.fq_out = (FEntry<typename P::T>*)c->fq[(r + 1) & 1];
@@ -1324,7 +1343,8 @@ struct DriverImpl {
   }
 
   static cudaError_t bin(Ctx* c, int dst, int* grid, int count_ledger) {
-    cudaError_t e = launch_setup(c, SETUP_CHUNK, 0, 0);
+    cudaError_t e = launch_setup(c, SETUP_CHUNK, (unsigned long long)c->step,
+                                 (unsigned long long)c->epoch << 40);
     if (e != cudaSuccess) return e;
     KP<P> p = make_kp<P>(c);
     p.grid = grid;
@@ -1333,8 +1353,8 @@ struct DriverImpl {
   }
 
   static cudaError_t materialize(Ctx* c) {
-    cudaError_t e = launch_setup(c, SETUP_AFTER_REGEN,
-                                 (unsigned long long)c->epoch << 40, 0);
+    cudaError_t e = launch_setup(c, SETUP_AFTER_REGEN, (unsigned long long)c->epoch << 40,
+                                 (unsigned long long)c->step);
     if (e != cudaSuccess) return e;
     KP<P> p = make_kp<P>(c);
     return flight<P, SRC_REGEN, DST_ARRAY>(c, p);

@@ -55,9 +55,22 @@ struct Counters {
   unsigned long long boot_n[2], boot_w[2], boot_keep[2], boot_nr[2];
   unsigned long long boot_R[2];    // total residual (Q0.32) per side
   long long obs_total;             // observables: transmission numerator
+  unsigned long long per_regen_base;  // the chunk's regeneration id base (epoch << 40)
+  int per_l0;                         // the chunk's first interval
   int err;
-  int pad[3];
+  int pad[2];
 };
+
+// A resampling period of wbrw_run captured into a CUDA graph (sp1, source =
+// the regeneration of the previous histogram), keyed by its length.
+struct PeriodGraph {
+  int len;
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  cudaGraphNode_t ev_begin, ev_end;  // event records around the first wave
+  long long launches;                // kernels in the graph
+};
+constexpr int kMaxGraphs = 4;
 
 // One instance of a batch, host FP64 (Sec. 4.2 / Remark 3 / Sec. 3.2).
 struct InstHost {
@@ -129,6 +142,13 @@ struct Ctx {
   long long epoch;
   int fresh;
   int failed;
+  int capturing;      // a period is being captured into a CUDA graph
+  int graph_on;       // wbrw_graph: replay periods from CUDA graphs
+  int dev_period_ok;  // the device period state equals (step, epoch)
+  int ngraphs;
+  PeriodGraph graphs[kMaxGraphs];
+  cudaEvent_t gev[2];  // placeholders of the captured event records
+  int gev_created;
   long long launches;
   // CUDA-event timing of the first flight wave of each chunk
   int prof_on;
@@ -139,6 +159,7 @@ struct Ctx {
 };
 
 enum { ST_PARTICLES = 0, ST_HISTOGRAM = 1 };
+
 
 // Per-precision drivers (wbrw_fp64.cu / wbrw_fp32.cu).
 // Event pair around a profiled launch (no-ops while profiling is off).
@@ -175,7 +196,13 @@ cudaError_t launch_zero(Ctx*, void* p, size_t bytes);
 // to *out (device).
 cudaError_t launch_live_instance(Ctx*, int inst, unsigned long long* out);
 
+// k_setup operations.  SETUP_PERIOD: set the device period state only.
+// SETUP_CHUNK: snapshot n, set the chunk's first
+// interval (a) and id base (b).  SETUP_CHUNK_DEV: snapshot n only (a captured
+// period takes both from the device).  SETUP_ADVANCE: move the device period
+// state on by a intervals and one resampling.  SETUP_AFTER_REGEN: the arrays
+// hold the regeneration of id base a at interval b.
 enum { SETUP_CHUNK = 0, SETUP_AFTER_REGEN = 1, SETUP_INIT = 2,
-       SETUP_BOOT = 3 };
+       SETUP_BOOT = 3, SETUP_CHUNK_DEV = 4, SETUP_ADVANCE = 5, SETUP_PERIOD = 6 };
 
 }  // namespace wbrw

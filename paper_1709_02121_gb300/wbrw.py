@@ -34,7 +34,8 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_restore", "wbrw_profile", "wbrw_profile_read", "wbrw_counters",
            "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
-           "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances")
+           "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
+           "wbrw_graph")
 MAX_INSTANCES = 256
 
 
@@ -114,8 +115,9 @@ def load(path: str = LIB_PATH):
                  "wbrw_restore", "wbrw_profile", "wbrw_profile_read",
                  "wbrw_counters", "wbrw_sync_status", "wbrw_batch_init",
                  "wbrw_instance_density", "wbrw_transmissions",
-                 "wbrw_particle_instances"):
+                 "wbrw_particle_instances", "wbrw_graph"):
         getattr(L, name).restype = I
+    L.wbrw_graph.argtypes = [P, I]
     L.wbrw_checkpoint.argtypes = [P, P, P, P]
     L.wbrw_restore.argtypes = [P, P, LL, LL]
     L.wbrw_profile.argtypes = [P, I]
@@ -234,6 +236,10 @@ def wbrw_restore(ctx, grid_ptr, step, epoch):
     _check(ctx, load().wbrw_restore(ctx, ctypes.c_void_p(grid_ptr), step, epoch))
 
 
+def wbrw_graph(ctx, enable=True):
+    _check(ctx, load().wbrw_graph(ctx, 1 if enable else 0))
+
+
 def wbrw_profile(ctx, enable=True):
     _check(ctx, load().wbrw_profile(ctx, 1 if enable else 0))
 
@@ -323,6 +329,9 @@ class Simulation:
                             self.log.data_ptr() if self.log is not None else None,
                             event_log)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        # the buffers were made on torch's current stream: the context's
+        # stream must see them finished
+        self.stream.wait_stream(torch.cuda.current_stream())
 
     def step(self, n=1):
         wbrw_step(self.ctx, n)
@@ -332,6 +341,10 @@ class Simulation:
 
     def run(self, n):
         wbrw_run(self.ctx, n)
+
+    def graph(self, enable=True):
+        """Replay resampling periods from CUDA graphs (needs a created stream)."""
+        wbrw_graph(self.ctx, enable)
 
     def density(self):
         return wbrw_density(self.ctx, self.nx, self.nk)
@@ -356,6 +369,7 @@ class Simulation:
             ptr = grid.ctypes.data
         else:
             ptr = grid.data_ptr()
+            self.stream.wait_stream(self.torch.cuda.current_stream())
         wbrw_restore(self.ctx, ptr, step, epoch)
 
     def particles(self, with_pids=True):
@@ -374,6 +388,7 @@ class Simulation:
         return x, k, s, w, pid
 
     def grid_counts(self):
+        self.stream.synchronize()
         if self.ninst > 1:
             return self.grid.view(self.ninst, self.nx, self.nk).cpu().numpy()
         return self.grid.view(self.nx, self.nk).cpu().numpy()
