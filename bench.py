@@ -56,6 +56,8 @@ def parse():
                     help="particle capacity as a multiple of the particle count")
     ap.add_argument("--no-graph", action="store_true",
                     help="launch every period kernel by kernel instead of replaying a CUDA graph")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shape instead of autotuning it after warm-up")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -228,6 +230,7 @@ def ours(args, wl):
     P = wl["resample_every"]
     for _ in range(args.warmup):
         sim.run(P)
+    tuning = autotune(sim, args)
     barrier()
 
     c0 = sim.counters()
@@ -238,6 +241,7 @@ def ours(args, wl):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for i in range(args.steps):
         flush.fill_(i)  # evict the histogram and plan from L2
+        stream.wait_stream(torch.cuda.current_stream())  # the flush ends before the timing starts
         starts[i].record(stream)
         sim.run(P)
         ends[i].record(stream)
@@ -295,7 +299,7 @@ def ours(args, wl):
                 "dtype": "f32" if wl["precision"] == "fp32" else "f64",
                 "data": "synthetic", "config": config_of(wl, args),
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "clocks": clk,
+                "clocks": clk, "tuning": tuning,
                 "live_particles_end": c1["live"],
                 "particle_steps": psteps}
         if not args.no_cpu_baseline and ws == 1:
@@ -347,6 +351,7 @@ def ours_batch(args, spec):
     P = wl["resample_every"]
     for _ in range(args.warmup):
         sim.run(P)
+    tuning = autotune(sim, args)
     barrier()
     c0 = sim.counters()
     wbrw.wbrw_profile(sim.ctx, True)
@@ -356,6 +361,7 @@ def ours_batch(args, spec):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for i in range(args.steps):
         flush.fill_(i)
+        stream.wait_stream(torch.cuda.current_stream())  # the flush ends before the timing starts
         starts[i].record(stream)
         sim.run(P)
         ends[i].record(stream)
@@ -421,6 +427,7 @@ def ours_batch(args, spec):
                 wbrw.wbrw_run(ctx, P)
             p0 = wbrw.wbrw_counters(ctx)["particle_steps"]
             flush.fill_(0)
+            host.stream.wait_stream(torch.cuda.current_stream())
             ev[0].record(host.stream)
             for _ in range(args.steps):
                 wbrw.wbrw_run(ctx, P)
@@ -460,6 +467,7 @@ def ours_batch(args, spec):
                            "l2": "flushed (512 MiB write) between timed steps",
                            "parallelism": "replicas x%d" % ws},
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
+                "tuning": tuning,
                 "live_particles_end": c1["live"], "particle_steps": psteps,
                 "transmission_mean": float(np.mean(T_batch))}
         if plain is not None:
@@ -479,6 +487,17 @@ def ours_batch(args, spec):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def autotune(sim, args):
+    """Pick the launch shape by timing one period under each (results do not
+    depend on it); the run continues from where it was."""
+    if args.no_autotune:
+        b, p = sim.tuning()
+        return {"blocks_per_sm": b, "event_passes": p, "autotuned": False}
+    (b, p), table = sim.autotune(trials=2)
+    return {"blocks_per_sm": b, "event_passes": p, "autotuned": True,
+            "period_ms": [[round(float(v), 4) for v in row] for row in table]}
 
 
 def reduce_over_ranks(ws, t_ms, psteps, e2e_value, device):

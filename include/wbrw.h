@@ -236,6 +236,41 @@ wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
  * launch kernel by kernel. */
 wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
 
+/* Launch shape.  Neither knob changes any result (random numbers are keyed
+ * by particle and interval, and every count is an integer sum), only speed:
+ *   blocks_per_sm : resident 256-thread blocks per SM of the particle
+ *                   kernels, 1..WBRW_TUNE_BLOCKS_PER_SM_MAX (default the
+ *                   maximum).  Each warp owns one segment of every queue, so
+ *                   this also sets the queue segmentation.
+ *   event_passes  : offspring with further events in their interval are
+ *                   processed one event per lockstep pass for this many
+ *                   passes (0..WBRW_TUNE_PASSES_MAX, default 3); what remains
+ *                   is finished by one recursive pass.
+ * wbrw_set_tuning takes effect from the next call and releases captured
+ * graphs; out-of-range values give WBRW_ERR_ARG. */
+#define WBRW_TUNE_BLOCKS_PER_SM_MAX 3
+#define WBRW_TUNE_PASSES_MAX 6
+typedef struct {
+  int blocks_per_sm;
+  int event_passes;
+} wbrw_tuning;
+
+wbrw_status wbrw_get_tuning(wbrw_ctx* ctx, wbrw_tuning* out);
+wbrw_status wbrw_set_tuning(wbrw_ctx* ctx, const wbrw_tuning* tuning);
+
+/* Autotuner: time one resampling period of wbrw_run (the period that starts
+ * now) under every setting, `trials` times each (>= 1), keep the fastest
+ * setting and report it in *best (may be NULL).  ms_table (may be NULL)
+ * receives WBRW_TUNE_BLOCKS_PER_SM_MAX x (WBRW_TUNE_PASSES_MAX + 1) times in
+ * milliseconds, entry (b - 1) * (WBRW_TUNE_PASSES_MAX + 1) + p for
+ * blocks_per_sm = b and event_passes = p, each the fastest of its trials
+ * (negative if that setting hit a capacity limit).  Every trial starts from
+ * the same histogram, and the context is put back afterwards: state, counters
+ * and interval index are as before the call.  Needs the state right after a
+ * resampling (as wbrw_checkpoint) and resample_every > 0; the event log is
+ * not written while tuning.  Synchronises the stream. */
+wbrw_status wbrw_autotune(wbrw_ctx* ctx, int trials, wbrw_tuning* best, double* ms_table);
+
 /* Observables of a signed histogram without any allocation and without a
  * context.  The paper has no counterpart: this is an interface for callers
  * that cannot call cudaMalloc, such as code running inside a fixed device

@@ -20,7 +20,6 @@ struct wbrw_ctx : public Ctx {};
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kLevelsHost = 5;  // deferred-segment levels (kLevels of the device code)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
@@ -28,7 +27,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
   size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, seg_counts, tabs, cinst, total;
+      rec_a, keep0, keep1, res0, res1, seg_counts, cnt_save, tabs, cinst, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
@@ -78,7 +77,8 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
     return at;
   };
   L.counters = take(sizeof(Counters));
-  L.seg_counts = take((size_t)(1 + 2 + kLevelsHost + 1) * kMaxSeg * sizeof(unsigned));
+  L.seg_counts = take((size_t)(1 + 2 + kMaxLevels + 1) * kMaxSeg * sizeof(unsigned));
+  L.cnt_save = take(sizeof(Counters));
   L.cpid = take((size_t)capacity * 8);
   L.fq0 = take((size_t)L.qcap * fentry_size(c->precision));
   L.fq1 = take((size_t)L.qcap * fentry_size(c->precision));
@@ -383,6 +383,18 @@ size_t wbrw_batch_scratch_bytes(const wbrw_config* config, int ninst, long long 
 
 namespace {
 
+// Resident blocks per SM of the queue kernels, and with it the queue
+// segmentation: one segment per warp of the grid.
+void set_shape(wbrw_ctx* c, int bps) {
+  c->bps = bps;
+  c->nseg = bps * c->num_sms * (kBlock / 32);
+  if (c->nseg > kMaxSeg) c->nseg = kMaxSeg;
+  c->qseg = c->qcap / c->nseg;
+  c->eseg = c->ecap / c->nseg;
+  c->dseg = c->dcap / c->nseg;
+  c->rseg = c->rec_cap / c->nseg;
+}
+
 // Create a context for ninst instances (records q, starts filled in here)
 // and enqueue the initial sampling.  Takes ownership of q.
 wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw_buffers* b,
@@ -441,27 +453,24 @@ wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw
   char* base = (char*)b->scratch;
   c->cnt = (Counters*)(base + L.counters);
   c->cpid = (unsigned long long*)(base + L.cpid);
-  // one queue segment per producer warp: at most kMaxBlocksPerSm blocks per SM
-  c->nseg = kMaxBlocksPerSm * c->num_sms * (kBlock / 32);
-  if (c->nseg > kMaxSeg) c->nseg = kMaxSeg;
   unsigned* counts = (unsigned*)(base + L.seg_counts);
   c->ecnt = counts;
   c->fcnt[0] = counts + kMaxSeg;
   c->fcnt[1] = counts + 2 * kMaxSeg;
   c->dcnt = counts + 3 * kMaxSeg;
-  c->rcnt = counts + (3 + kLevelsHost) * kMaxSeg;
+  c->rcnt = counts + (3 + kMaxLevels) * kMaxSeg;
+  c->cnt_save = (Counters*)(base + L.cnt_save);
   c->fq[0] = base + L.fq0;
   c->fq[1] = base + L.fq1;
   c->qcap = L.qcap;
-  c->qseg = L.qcap / c->nseg;
   c->eq = base + L.eq;
   c->ecap = L.ecap;
-  c->eseg = L.ecap / c->nseg;
   c->dq[0] = base + L.dq0;
   c->dq[1] = base + L.dq1;
   c->dcap = L.dcap;
-  c->dseg = L.dcap / c->nseg;
-  c->rseg = L.rec_cap / c->nseg;
+  c->rec_cap = L.rec_cap;
+  c->passes = 3;
+  set_shape(c, kMaxBlocksPerSm);
   c->nz_cell = (uint32_t*)(base + L.nz_cell);
   c->nz_start = (unsigned long long*)(base + L.nz_start);
   c->tile_nz = (uint32_t*)(base + L.tile_nz);
@@ -477,7 +486,6 @@ wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw
   c->obs_scalar = (double*)(base + L.obs_scalar);
   c->rec_cell = (uint32_t*)(base + L.rec_cell);
   c->rec_a = (uint32_t*)(base + L.rec_a);
-  c->rec_cap = L.rec_cap;
   c->boot_keep[0] = (int*)(base + L.keep0);
   c->boot_keep[1] = (int*)(base + L.keep1);
   c->boot_res[0] = (unsigned long long*)(base + L.res0);
@@ -781,6 +789,122 @@ wbrw_status wbrw_graph(wbrw_ctx* c, int enable) {
   }
   c->graph_on = enable ? 1 : 0;
   return WBRW_OK;
+}
+
+wbrw_status wbrw_get_tuning(wbrw_ctx* c, wbrw_tuning* out) {
+  if (!c || !out) return WBRW_ERR_ARG;
+  out->blocks_per_sm = c->bps;
+  out->event_passes = c->passes;
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_set_tuning(wbrw_ctx* c, const wbrw_tuning* t) {
+  if (!c || !t) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (t->blocks_per_sm < 1 || t->blocks_per_sm > kMaxBlocksPerSm || t->event_passes < 0 ||
+      t->event_passes > kMaxPasses)
+    return seterr(c, WBRW_ERR_ARG, "tuning out of range");
+  if (t->blocks_per_sm != c->bps || t->event_passes != c->passes) {
+    WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+    drop_graphs(c);
+    set_shape(c, t->blocks_per_sm);
+    c->passes = t->event_passes;
+  }
+  return WBRW_OK;
+}
+
+wbrw_status wbrw_autotune(wbrw_ctx* c, int trials, wbrw_tuning* best, double* ms_table) {
+  if (!c || trials < 1) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (!c->fresh || c->state != ST_HISTOGRAM || c->cfg.resample_every <= 0)
+    return seterr(c, WBRW_ERR_STATE, "autotune needs the state right after a resampling");
+  const int T = c->cfg.resample_every;
+  const int len = T - (int)(c->step % T);
+  if (len > c->max_chunk)
+    return seterr(c, WBRW_ERR_STATE, "the period is longer than one flight");
+  // what the trials disturb, to be put back
+  const long long step0 = c->step, epoch0 = c->epoch, launches0 = c->launches;
+  const int prof0 = c->prof_on, graph0 = c->graph_on, bps0 = c->bps, passes0 = c->passes;
+  void* log0 = c->buf.event_log;
+  WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  drop_graphs(c);
+  c->prof_on = 0;
+  c->graph_on = 0;
+  c->buf.event_log = nullptr;
+  WBRW_TRY(c, cudaMemcpyAsync(c->cnt_save, c->cnt, sizeof(Counters), cudaMemcpyDeviceToDevice,
+                              c->stream), "save counters");
+  WBRW_TRY(c, cudaMemcpyAsync(c->tmp_grid, c->buf.grid, (size_t)c->nh * 4,
+                              cudaMemcpyDeviceToDevice, c->stream), "save grid");
+  cudaEvent_t ev[2];
+  WBRW_TRY(c, cudaEventCreate(&ev[0]), "event");
+  if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+    cudaEventDestroy(ev[0]);
+    return seterr(c, WBRW_ERR_CUDA, "event");
+  }
+  auto put_back = [&]() -> wbrw_status {
+    WBRW_TRY(c, cudaMemcpyAsync(c->buf.grid, c->tmp_grid, (size_t)c->nh * 4,
+                                cudaMemcpyDeviceToDevice, c->stream), "restore grid");
+    WBRW_TRY(c, cudaMemcpyAsync(c->cnt, c->cnt_save, sizeof(Counters),
+                                cudaMemcpyDeviceToDevice, c->stream), "restore counters");
+    WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+    c->step = step0;
+    c->epoch = epoch0;
+    c->state = ST_HISTOGRAM;
+    c->fresh = 1;
+    c->dev_period_ok = 0;
+    return WBRW_OK;
+  };
+  double best_ms = -1;
+  int best_b = bps0, best_p = passes0;
+  wbrw_status st = WBRW_OK;
+  for (int b = 1; b <= kMaxBlocksPerSm && st == WBRW_OK; ++b) {
+    for (int pz = 0; pz <= kMaxPasses && st == WBRW_OK; ++pz) {
+      set_shape(c, b);
+      c->passes = pz;
+      double t_min = -1;
+      for (int t = 0; t < trials && st == WBRW_OK; ++t) {
+        if ((st = put_back()) != WBRW_OK) break;
+        if ((st = cuda_check(c, cudaEventRecord(ev[0], c->stream), "record")) != WBRW_OK) break;
+        if ((st = enqueue_period(c, SRC_REGEN, (int)step0, (int)step0 + len, epoch0)) != WBRW_OK)
+          break;
+        if ((st = cuda_check(c, cudaEventRecord(ev[1], c->stream), "record")) != WBRW_OK) break;
+        int err = 0;
+        if ((st = cuda_check(c, cudaMemcpyAsync(&err, &c->cnt->err, sizeof(int),
+                                                cudaMemcpyDeviceToHost, c->stream),
+                             "read error word")) != WBRW_OK)
+          break;
+        if ((st = cuda_check(c, cudaStreamSynchronize(c->stream), "synchronise")) != WBRW_OK)
+          break;
+        float ms = 0;
+        if ((st = cuda_check(c, cudaEventElapsedTime(&ms, ev[0], ev[1]), "elapsed")) != WBRW_OK)
+          break;
+        if (err) { t_min = -1; break; }  // a capacity limit under this shape
+        if (t_min < 0 || ms < t_min) t_min = ms;
+      }
+      if (ms_table) ms_table[(b - 1) * (kMaxPasses + 1) + pz] = t_min;
+      if (t_min >= 0 && (best_ms < 0 || t_min < best_ms)) {
+        best_ms = t_min;
+        best_b = b;
+        best_p = pz;
+      }
+    }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (st != WBRW_OK) return st;
+  set_shape(c, best_b);
+  c->passes = best_p;
+  st = put_back();
+  if (st != WBRW_OK) return st;
+  c->launches = launches0;
+  c->prof_on = prof0;
+  c->graph_on = graph0;
+  c->buf.event_log = log0;
+  if (best) {
+    best->blocks_per_sm = best_b;
+    best->event_passes = best_p;
+  }
+  return device_status(c);
 }
 
 wbrw_status wbrw_profile(wbrw_ctx* c, int enable) {

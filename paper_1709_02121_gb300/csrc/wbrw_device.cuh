@@ -118,7 +118,6 @@ static_assert(sizeof(FEntry<double>) == 40 && sizeof(FEntry<float>) == 24, "FEnt
 template <class P>
 struct SEntry;
 
-constexpr int kLevels = 5;  // deferred segments: levels 1..3 in passes, 4 drained
 
 // Physics of one instance of a batch (a single run is a batch of one).
 template <class T>
@@ -186,7 +185,7 @@ struct KP {
   unsigned* ecnt;
   long long eseg;
   SEntry<P>* dq[2];          // deferred segments; level L lives in dq[L & 1]
-  unsigned* dcnt;            // kLevels x nseg counts
+  unsigned* dcnt;            // kMaxLevels x nseg counts
   long long dseg;
   uint32_t* rec_cell;        // sp2 records (cell | side << 31, |w| in Q1.31)
   uint32_t* rec_a;
@@ -1030,7 +1029,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p_) {
+__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p_, int level) {
   const KP<P> p = with_period(p_);
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -1041,7 +1040,6 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p
   load_counts(p, wc, 0);
   const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
-  const int level = kLevels - 1;
   const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
   for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
@@ -1187,16 +1185,21 @@ KP<P> make_kp(const Ctx* c) {
   return p;
 }
 
-// Every queue kernel runs exactly kMaxBlocksPerSm resident blocks per SM:
-// producer warp g owns queue segment g and consumer warp g reads it, so equal
-// grids keep the segments matched one to one (nseg of them).
+// Every queue kernel runs the same number of resident blocks per SM (the
+// context's tuning, at most kMaxBlocksPerSm): producer warp g owns queue
+// segment g and consumer warp g reads it, so equal grids keep the segments
+// matched one to one (nseg of them).
 template <class K>
-int grid_for(Ctx* c, K kern) {
+int occupancy(K kern) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  if (per_sm > kMaxBlocksPerSm) per_sm = kMaxBlocksPerSm;
+  return per_sm;
+}
+
+inline int grid_of(const Ctx* c, int occ) {
+  const int per_sm = occ < c->bps ? occ : c->bps;
   int g = per_sm * c->num_sms;
   if (g * kWarps > c->nseg) g = c->nseg / kWarps;
   return g;
@@ -1204,26 +1207,22 @@ int grid_for(Ctx* c, K kern) {
 
 template <class P, int SRC, int DST>
 cudaError_t flight(Ctx* c, const KP<P>& p) {
-  static int grid = 0;
-  if (!grid) grid = grid_for(c, k_flight<P, SRC, DST>);
-  k_flight<P, SRC, DST><<<grid, kBlock, 0, c->stream>>>(p);
+  static const int occ = occupancy(k_flight<P, SRC, DST>);
+  k_flight<P, SRC, DST><<<grid_of(c, occ), kBlock, 0, c->stream>>>(p);
   c->launches++;
   return cudaGetLastError();
 }
 
 template <class P, int DST>
 cudaError_t events(Ctx* c, const KP<P>& p) {
-  static int g_ev = 0, g_cont = 0, g_drain = 0;
-  if (!g_ev) {
-    g_ev = grid_for(c, k_event<P, DST>);
-    g_cont = grid_for(c, k_cont<P, DST>);
-    g_drain = grid_for(c, k_drain<P, DST>);
-  }
-  k_event<P, DST><<<g_ev, kBlock, 0, c->stream>>>(p);
-  for (int level = 1; level < kLevels - 1; ++level)
-    k_cont<P, DST><<<g_cont, kBlock, 0, c->stream>>>(p, level);
-  k_drain<P, DST><<<g_drain, kBlock, 0, c->stream>>>(p);
-  c->launches += kLevels;
+  static const int o_ev = occupancy(k_event<P, DST>);
+  static const int o_cont = occupancy(k_cont<P, DST>);
+  static const int o_drain = occupancy(k_drain<P, DST>);
+  k_event<P, DST><<<grid_of(c, o_ev), kBlock, 0, c->stream>>>(p);
+  for (int level = 1; level <= c->passes; ++level)
+    k_cont<P, DST><<<grid_of(c, o_cont), kBlock, 0, c->stream>>>(p, level);
+  k_drain<P, DST><<<grid_of(c, o_drain), kBlock, 0, c->stream>>>(p, c->passes + 1);
+  c->launches += c->passes + 2;
   return cudaGetLastError();
 }
 
@@ -1301,9 +1300,8 @@ struct DriverImpl {
     if (e != cudaSuccess) return e;
     if ((e = launch_setup(c, SETUP_INIT, (unsigned long long)n, 0)) != cudaSuccess) return e;
     KP<P> p = make_kp<P>(c);
-    static int grid = 0;
-    if (!grid) grid = grid_for(c, k_init<P>);
-    k_init<P><<<grid, kBlock, 0, c->stream>>>(p, (const InitInst*)((char*)c->inst_tab + kInstTabBytes),
+    static const int occ = occupancy(k_init<P>);
+    k_init<P><<<occ * c->num_sms, kBlock, 0, c->stream>>>(p, (const InitInst*)((char*)c->inst_tab + kInstTabBytes),
                                               (unsigned long long)n);
     c->launches++;
     return cudaGetLastError();
@@ -1334,7 +1332,8 @@ struct DriverImpl {
       if (e != cudaSuccess) return e;
       if (L > l0) {
         if ((e = launch_zero(c, p.fcnt_out, cnt_bytes)) != cudaSuccess) return e;
-        if ((e = launch_zero(c, c->dcnt, kLevels * cnt_bytes)) != cudaSuccess) return e;
+        if ((e = launch_zero(c, c->dcnt, (size_t)(c->passes + 2) * cnt_bytes)) != cudaSuccess)
+          return e;
         e = events_any<P>(c, p, dst);
         if (e != cudaSuccess) return e;
       }
@@ -1362,9 +1361,8 @@ struct DriverImpl {
 
   static cudaError_t pids(Ctx* c, unsigned long long* out, unsigned* inst_out) {
     KP<P> p = make_kp<P>(c);
-    static int grid = 0;
-    if (!grid) grid = grid_for(c, k_pids<P>);
-    k_pids<P><<<grid, kBlock, 0, c->stream>>>(p, out, inst_out);
+    static const int occ = occupancy(k_pids<P>);
+    k_pids<P><<<occ * c->num_sms, kBlock, 0, c->stream>>>(p, out, inst_out);
     c->launches++;
     return cudaGetLastError();
   }

@@ -14,7 +14,12 @@ constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
 constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
-constexpr int kMaxBlocksPerSm = 3;  // resident blocks per SM of every queue kernel
+constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // launch bound of the queue kernels
+// Deferred-segment levels of the event kernels: level 1 is fed by the first
+// event of each candidate interval, levels 1..passes are finished one event
+// per lockstep pass, level passes + 1 by the recursive drain.
+constexpr int kMaxPasses = WBRW_TUNE_PASSES_MAX;
+constexpr int kMaxLevels = kMaxPasses + 2;
 constexpr int kMaxInst = WBRW_MAX_INSTANCES;  // instances of a batch (8 id bits)
 constexpr int kInstBytes = 64;                // one per-instance record on the device
 constexpr size_t kInstTabBytes = (size_t)kMaxInst * kInstBytes;
@@ -113,11 +118,14 @@ struct Ctx {
   unsigned* ecnt;
   long long ecap, eseg;
   void* dq[2];        // deferred segments, levels alternating
-  unsigned* dcnt;     // kLevels x nseg
+  unsigned* dcnt;     // kMaxLevels x kMaxSeg
   long long dcap, dseg;
   unsigned* rcnt;     // sp2 records per segment
   long long rseg;
   int max_chunk;      // steps per flight: about one candidate per particle
+  Counters* cnt_save; // autotuner: the counters to put back
+  int bps;            // tuning: resident blocks per SM of the queue kernels
+  int passes;         // tuning: lockstep event passes before the drain
   uint32_t* nz_cell;
   unsigned long long* nz_start;
   uint32_t* tile_nz;  // first nonzero cell of each 32-slot tile of the plan

@@ -35,7 +35,8 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
-           "wbrw_graph")
+           "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune")
+TUNE_BPS_MAX, TUNE_PASSES_MAX = 3, 6
 MAX_INSTANCES = 256
 
 
@@ -61,6 +62,10 @@ class Instance(ctypes.Structure):
     _fields_ = [("pot", Potential), ("x0", ctypes.c_double), ("sigma_x", ctypes.c_double),
                 ("k0", ctypes.c_double), ("n_init", ctypes.c_longlong),
                 ("n_alpha", ctypes.c_longlong), ("gamma0", ctypes.c_double)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int), ("event_passes", ctypes.c_int)]
 
 
 class Buffers(ctypes.Structure):
@@ -115,8 +120,12 @@ def load(path: str = LIB_PATH):
                  "wbrw_restore", "wbrw_profile", "wbrw_profile_read",
                  "wbrw_counters", "wbrw_sync_status", "wbrw_batch_init",
                  "wbrw_instance_density", "wbrw_transmissions",
-                 "wbrw_particle_instances", "wbrw_graph"):
+                 "wbrw_particle_instances", "wbrw_graph", "wbrw_get_tuning",
+                 "wbrw_set_tuning", "wbrw_autotune"):
         getattr(L, name).restype = I
+    L.wbrw_get_tuning.argtypes = [P, P]
+    L.wbrw_set_tuning.argtypes = [P, P]
+    L.wbrw_autotune.argtypes = [P, I, P, P]
     L.wbrw_graph.argtypes = [P, I]
     L.wbrw_checkpoint.argtypes = [P, P, P, P]
     L.wbrw_restore.argtypes = [P, P, LL, LL]
@@ -240,6 +249,26 @@ def wbrw_graph(ctx, enable=True):
     _check(ctx, load().wbrw_graph(ctx, 1 if enable else 0))
 
 
+def wbrw_get_tuning(ctx):
+    t = Tuning()
+    _check(ctx, load().wbrw_get_tuning(ctx, ctypes.byref(t)))
+    return t.blocks_per_sm, t.event_passes
+
+
+def wbrw_set_tuning(ctx, blocks_per_sm, event_passes):
+    t = Tuning(blocks_per_sm, event_passes)
+    _check(ctx, load().wbrw_set_tuning(ctx, ctypes.byref(t)))
+
+
+def wbrw_autotune(ctx, trials=2):
+    """Returns ((blocks_per_sm, event_passes), table) with table[b-1, p] the
+    fastest period time in ms of that setting (negative: capacity limit)."""
+    t = Tuning()
+    table = np.zeros((TUNE_BPS_MAX, TUNE_PASSES_MAX + 1), np.float64)
+    _check(ctx, load().wbrw_autotune(ctx, trials, ctypes.byref(t), table.ctypes.data))
+    return (t.blocks_per_sm, t.event_passes), table
+
+
 def wbrw_profile(ctx, enable=True):
     _check(ctx, load().wbrw_profile(ctx, 1 if enable else 0))
 
@@ -341,6 +370,19 @@ class Simulation:
 
     def run(self, n):
         wbrw_run(self.ctx, n)
+
+    def autotune(self, trials=2):
+        """Time the next resampling period under every launch shape and keep
+        the fastest (results do not depend on it)."""
+        return wbrw_autotune(self.ctx, trials)
+
+    def tuning(self, blocks_per_sm=None, event_passes=None):
+        b, p = wbrw_get_tuning(self.ctx)
+        if blocks_per_sm is not None or event_passes is not None:
+            wbrw_set_tuning(self.ctx, b if blocks_per_sm is None else blocks_per_sm,
+                            p if event_passes is None else event_passes)
+            b, p = wbrw_get_tuning(self.ctx)
+        return b, p
 
     def graph(self, enable=True):
         """Replay resampling periods from CUDA graphs (needs a created stream)."""
