@@ -7,6 +7,9 @@ package imports nothing from it.
 
 Contents
 --------
+* ``wbrw4_oracle.c`` -- the same for the 4D Helium-like system of Example 1
+  (two electrons, soft-Coulomb kernels tabulated from Eq. 2, M = 3
+  components); ``Oracle4`` below.
 * ``wbrw_oracle.c`` -- plain FP64 C implementation of Alg. 1 (per interval),
   the signed histogram (Eq. signed_histogram), Alg. 3 and the signed residual
   bootstrap (Alg. 2 with Eq. lambda / double_bootstrap / boostrap_histogram),
@@ -26,6 +29,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "wbrw_oracle.c")
+_SRC4 = os.path.join(_HERE, "wbrw4_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libwbrw_oracle.so")
 
@@ -46,11 +50,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, no FMA contraction, no fast-math)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(_SRC4))):
         return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared", "-o", tmp, _SRC, _SRC4, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -75,6 +79,25 @@ EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"),
                         ("t", "<f8"), ("xe", "<f8"), ("kappa", "<f8"),
                         ("factor", "<f8"), ("kill_plus", "<i4"),
                         ("kill_minus", "<i4")])
+
+EVENT4_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"),
+                         ("pid_minus", "<u8"), ("step", "<u4"), ("j", "<u4"),
+                         ("t", "<f8"), ("xe", "<f8"), ("kappa", "<f8"),
+                         ("factor", "<f8"), ("kill_plus", "<i4"),
+                         ("kill_minus", "<i4"), ("xe2", "<f8"), ("comp", "<i4"),
+                         ("pad", "<i4")])
+
+
+class _Config4(ctypes.Structure):
+    _fields_ = [("hbar", ctypes.c_double), ("mass", ctypes.c_double),
+                ("dt", ctypes.c_double), ("Z", ctypes.c_double),
+                ("a", ctypes.c_double), ("xc", ctypes.c_double),
+                ("lam", ctypes.c_double), ("nx", ctypes.c_int), ("nk", ctypes.c_int),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
+                ("ny", ctypes.c_int), ("nkap", ctypes.c_int),
+                ("n_alpha", ctypes.c_longlong), ("seed", ctypes.c_ulonglong)]
+
 
 _lib = None
 
@@ -128,6 +151,35 @@ def lib():
         L.orc_event_outcome.argtypes = [P, ctypes.c_uint64, U32, U32, D,
                                         P, P, P]
         assert L.orc_event_size() == EVENT_DTYPE.itemsize
+        L.orc4_k0.argtypes = [D]
+        L.orc4_k0.restype = D
+        L.orc4_create.argtypes = [ctypes.POINTER(_Config4)]
+        L.orc4_create.restype = P
+        L.orc4_destroy.argtypes = [P]
+        for name in ("orc4_gamma",):
+            getattr(L, name).argtypes = [P, ctypes.c_int]
+            getattr(L, name).restype = D
+        L.orc4_Gamma.argtypes = [P]
+        L.orc4_Gamma.restype = D
+        L.orc4_enable_log.argtypes = [P, ctypes.c_int]
+        L.orc4_get_table.argtypes = [P, ctypes.c_int, P, P, P]
+        L.orc4_init_gauss.argtypes = [P, LL, D, D, D, D, D]
+        L.orc4_event_outcome.argtypes = [P, ctypes.c_uint64, U32, U32, D, D, P, P, P, P]
+        L.orc4_step.argtypes = [P, ctypes.c_int]
+        L.orc4_annihilate.argtypes = [P]
+        L.orc4_count.argtypes = [P]
+        L.orc4_count.restype = LL
+        L.orc4_epoch.argtypes = [P]
+        L.orc4_epoch.restype = LL
+        L.orc4_get_particles.argtypes = [P, P, P, P, P, P, P]
+        L.orc4_get_grid.argtypes = [P, P]
+        L.orc4_get_ledger.argtypes = [P, P]
+        L.orc4_log_count.argtypes = [P]
+        L.orc4_log_count.restype = LL
+        L.orc4_get_log.argtypes = [P, P]
+        L.orc4_event_size.restype = LL
+        L.orc4_observables.argtypes = [P, P, P, P, P]
+        assert L.orc4_event_size() == EVENT4_DTYPE.itemsize
         _lib = L
     return _lib
 
@@ -298,3 +350,105 @@ class Oracle:
                                        ctypes.byref(kap), ctypes.byref(f),
                                        ctypes.byref(gap))
         return bool(emit), kap.value, f.value, gap.value
+
+
+def k0(z):
+    """K0 of the 4D oracle (its integral representation, trapezoid rule)."""
+    return lib().orc4_k0(float(z))
+
+
+class Oracle4:
+    """One run of the 4D Helium-like oracle (two electrons, M = 3 kernels)."""
+
+    def __init__(self, *, hbar=1.0, mass=1.0, dt=0.02, Z=2.0, a=1.0, xc=0.0, lam=1.0,
+                 nx=64, nk=64, xmin=-10.0, xmax=10.0, kmin=-6.4, kmax=6.4, ny=4096,
+                 nkap=2048, n_alpha=100000, seed=0):
+        self.cfg = _Config4(hbar, mass, dt, Z, a, xc, lam, nx, nk, xmin, xmax, kmin, kmax,
+                            ny, nkap, n_alpha, seed)
+        self.nx, self.nk, self.ny, self.nkap = nx, nk, ny, nkap
+        self._s = lib().orc4_create(ctypes.byref(self.cfg))
+        if not self._s:
+            raise ValueError("oracle rejected the configuration")
+
+    def __del__(self):
+        s = getattr(self, "_s", None)
+        if s and _lib is not None:
+            _lib.orc4_destroy(s)
+            self._s = None
+
+    def gamma(self, t):
+        return lib().orc4_gamma(self._s, t)
+
+    @property
+    def Gamma(self):
+        return lib().orc4_Gamma(self._s)
+
+    def table(self, t, with_S=False):
+        A = np.empty(self.nkap)
+        xi = np.empty(self.ny)
+        S = np.empty((self.ny, self.nkap)) if with_S else None
+        lib().orc4_get_table(self._s, t, _ptr(A), _ptr(xi), _ptr(S))
+        return (A, xi, S) if with_S else (A, xi)
+
+    def enable_log(self, on=True):
+        lib().orc4_enable_log(self._s, 1 if on else 0)
+
+    def init_gauss(self, n, x0, sigma_x, k0):
+        if lib().orc4_init_gauss(self._s, n, x0[0], x0[1], sigma_x, k0[0], k0[1]):
+            raise MemoryError
+
+    def event_outcome(self, pid, step, j, x1e, x2e):
+        comp = ctypes.c_int()
+        kap, prob, gap = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        e = lib().orc4_event_outcome(self._s, pid, step, j, x1e, x2e, ctypes.byref(comp),
+                                     ctypes.byref(kap), ctypes.byref(prob), ctypes.byref(gap))
+        return bool(e), comp.value, kap.value, prob.value, gap.value
+
+    def step(self, n=1):
+        if lib().orc4_step(self._s, n):
+            raise MemoryError
+
+    def annihilate(self):
+        if lib().orc4_annihilate(self._s):
+            raise MemoryError
+
+    @property
+    def n(self):
+        return lib().orc4_count(self._s)
+
+    @property
+    def epoch(self):
+        return lib().orc4_epoch(self._s)
+
+    def particles(self):
+        n = self.n
+        out = [np.empty(n) for _ in range(5)]
+        pid = np.empty(n, np.uint64)
+        lib().orc4_get_particles(self._s, *[_ptr(a) for a in out], _ptr(pid))
+        x1, x2, k1, k2, w = out
+        return x1, x2, k1, k2, w, pid
+
+    def grid(self):
+        g = np.empty(self.nx * self.nx * self.nk * self.nk, np.int32)
+        lib().orc4_get_grid(self._s, _ptr(g))
+        return g.reshape(self.nx, self.nx, self.nk, self.nk)
+
+    def ledger(self):
+        out = np.zeros(8, np.int64)
+        lib().orc4_get_ledger(self._s, _ptr(out))
+        return dict(zip(LEDGER, out.tolist()))
+
+    def event_log(self):
+        n = lib().orc4_log_count(self._s)
+        out = np.zeros(n, EVENT4_DTYPE)
+        if n:
+            lib().orc4_get_log(self._s, _ptr(out))
+        return out
+
+    def observables(self, counts):
+        c = np.ascontiguousarray(counts, np.int32).reshape(-1)
+        f1 = np.empty(self.nx * self.nk)
+        marg = np.empty(self.nx)
+        right = np.zeros(1)
+        lib().orc4_observables(self._s, _ptr(c), _ptr(f1), _ptr(marg), _ptr(right))
+        return f1.reshape(self.nx, self.nk), marg, float(right[0])

@@ -141,3 +141,37 @@ def gauss_vw_closed(H, w, xc, hbar):
 def wigner_gauss_f0(x, k, x0, sigma, k0):
     return (1.0 / np.pi) * np.exp(-((x - x0) ** 2) / (2 * sigma ** 2)
                                   - 2 * sigma ** 2 * (k - k0) ** 2)
+
+
+def soft_coulomb_2e(Z, a, lam, xc=0.0):
+    """V(x1, x2) of two electrons in 1D: -Z/sqrt((x_i-xc)^2+a^2) for each,
+    plus lam/sqrt((x1-x2)^2+a^2)."""
+    def V(x1, x2):
+        return (-Z / np.sqrt((x1 - xc) ** 2 + a * a) - Z / np.sqrt((x2 - xc) ** 2 + a * a)
+                + lam / np.sqrt((x1 - x2) ** 2 + a * a))
+    return V
+
+
+def tdse2_marginals(V, x0, sigma, k0, t, *, L=40.0, n=256, dt=2e-3, hbar=1.0, mass=1.0):
+    """Two distinguishable particles in 1D: Strang split-step Fourier on an
+    n x n periodic grid over [-L/2, L/2)^2 from the product of Gaussian
+    wavepackets (x0[e], sigma, k0[e]).  Returns x and the position densities
+    of particle 1 and particle 2 at time t."""
+    x = (np.arange(n) - n // 2) * (L / n)
+    kx = 2 * np.pi * np.fft.fftfreq(n, d=L / n)
+    X1, X2 = np.meshgrid(x, x, indexing="ij")
+    K1, K2 = np.meshgrid(kx, kx, indexing="ij")
+    psi = np.outer(gaussian_psi0(x, x0[0], sigma, k0[0]),
+                   gaussian_psi0(x, x0[1], sigma, k0[1])).astype(np.complex128)
+    v = V(X1, X2)
+    nsteps = int(round(t / dt))
+    h = t / nsteps if nsteps else 0.0
+    half_v = np.exp(-0.5j * v * h / hbar)
+    kin = np.exp(-0.5j * hbar * (K1 ** 2 + K2 ** 2) * h / mass)
+    for _ in range(nsteps):
+        psi = half_v * psi
+        psi = np.fft.ifft2(kin * np.fft.fft2(psi))
+        psi = half_v * psi
+    dens = np.abs(psi) ** 2
+    dx = L / n
+    return x, dens.sum(1) * dx, dens.sum(0) * dx

@@ -18,3 +18,13 @@ def make_oracle(wl, **over):
 
 def net_sign(w):
     return int(np.sum(np.sign(w)))
+
+
+def make_oracle4(wl, **over):
+    """The 4D Helium-like oracle for a workload dict (workloads.HE_4D_*)."""
+    w = dict(wl)
+    w.update(over)
+    return oracle.Oracle4(hbar=w["hbar"], mass=w["mass"], dt=w["dt"], Z=w["Z"], a=w["a"],
+                          xc=w["xc"], lam=w["lam"], nx=w["nx"], nk=w["nk"], xmin=w["xmin"],
+                          xmax=w["xmax"], kmin=w["kmin"], kmax=w["kmax"], ny=w["ny"],
+                          nkap=w["nkap"], n_alpha=w["n_alpha"], seed=w["seed"])

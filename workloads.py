@@ -92,3 +92,21 @@ def batch_instances(spec: dict, n_scale: float = 1.0) -> list:
         out.append(dict(H=float(H[i]), w=float(w[i]), xc=spec["xc"], x0=spec["x0"],
                         sigma_x=spec["sigma_x"], k0=float(k0[i]), n_init=cnt, n_alpha=cnt))
     return out
+
+
+# 4D Helium-like system (two 1D electrons, Example 1 of the paper with
+# soft-Coulomb terms): V = -Z/sqrt(x1^2+a^2) - Z/sqrt(x2^2+a^2)
+# + 1/sqrt((x1-x2)^2+a^2), Z = 2, a = 1; kernels tabulated on 4096 y nodes x
+# 2048 kappa cells; initial product of Gaussian packets with sigma = 1 at
+# x0 = (-1, 1), k0 = (0.5, -0.5); 5e7 particles; 64^4 cells over
+# x in [-10, 10)^2, k in [-6.4, 6.4)^2; dt = 0.02, 250 steps, resampling every
+# 10 steps; FP32.
+HE_4D_FP32_5E7 = dict(
+    name="he4d_fp32_n5e7_64x64x64x64",
+    dim=4, Z=2.0, a=1.0, lam=1.0, xc=0.0, ny=4096, nkap=2048,
+    x0=(-1.0, 1.0), sigma_x=1.0, k0=(0.5, -0.5),
+    n_alpha=50_000_000, dt=0.02, steps=250, resample_every=10,
+    nx=64, nk=64, xmin=-10.0, xmax=10.0, kmin=-6.4, kmax=6.4,
+    precision="fp32", strategy="sp1", seed=0, hbar=1.0, mass=1.0,
+    gamma0=0.0, H=2.0, w=1.0,
+)
