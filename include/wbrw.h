@@ -51,14 +51,27 @@ typedef enum {
 
 typedef enum { WBRW_SP1_PAIR = 1, WBRW_SP2_BOOTSTRAP = 2 } wbrw_strategy;
 typedef enum { WBRW_FP64 = 0, WBRW_FP32 = 1 } wbrw_precision;
-typedef enum { WBRW_POT_GAUSSIAN = 0 } wbrw_potential_kind;
+typedef enum { WBRW_POT_GAUSSIAN = 0, WBRW_POT_SOFT_COULOMB_2E = 1 } wbrw_potential_kind;
 
-/* Potential (Sec. 4.2, symmetric about xc): V(x) = H exp(-(x-xc)^2/(2 w^2)).
- * Its Wigner kernel (Eq. 2) is V_W(x,k) = (2/(pi hbar)) Vhat(2k)
- * sin(2 (x-xc) k) with Vhat(q) = H w sqrt(2 pi) exp(-q^2 w^2/2). */
+/* Potential.
+ * WBRW_POT_GAUSSIAN (dim 2; Sec. 4.2, symmetric about xc):
+ *   V(x) = H exp(-(x-xc)^2/(2 w^2)).  Its Wigner kernel (Eq. 2) is
+ *   V_W(x,k) = (2/(pi hbar)) Vhat(2k) sin(2 (x-xc) k) with
+ *   Vhat(q) = H w sqrt(2 pi) exp(-q^2 w^2/2).
+ * WBRW_POT_SOFT_COULOMB_2E (dim 4; the Helium-like system of Example 1 with
+ *   soft-Coulomb terms): two electrons at x1, x2 and a nucleus at xc,
+ *   V = -H/sqrt((x1-xc)^2 + w^2) - H/sqrt((x2-xc)^2 + w^2)
+ *       + ee/sqrt((x1-x2)^2 + w^2),
+ *   i.e. H = Z the nuclear charge, w = a the softening length, ee the
+ *   interaction strength.  Each term's kernel is
+ *   (2/(pi hbar)) q Uhat(2 kappa) sin(2 y kappa), Uhat(q) = 2 K0(w |q|), with
+ *   y = x1 - xc, x2 - xc or x1 - x2 and q = -H, -H or ee (Eq. M); the first
+ *   two kick k1 or k2, the interaction kicks k1 by +kappa and k2 by -kappa. */
 typedef struct {
-  int kind;        /* WBRW_POT_GAUSSIAN                                     */
-  double H, w, xc; /* height (any sign), width (> 0), centre                */
+  int kind;        /* wbrw_potential_kind                                   */
+  double H, w, xc; /* Gaussian: height (any sign), width (> 0), centre;    */
+                   /* soft-Coulomb: Z, softening a (> 0), nucleus          */
+  double ee;       /* soft-Coulomb: interaction strength (Gaussian: unused) */
 } wbrw_potential;
 
 /* Problem statement (Sec. 2 and Sec. 4): hbar, mass, interval dt of the
@@ -68,19 +81,23 @@ typedef struct {
  * cells, x-major with k contiguous), the resampling period T_A in steps, and
  * the sample size N_alpha of the estimator (Eq. estimator). */
 typedef struct {
-  int dim;                  /* 2: one position and one wavevector            */
+  int dim;                  /* 2: (x, k); 4: (x1, x2, k1, k2), two electrons */
   int precision;            /* wbrw_precision: particle state and arithmetic */
   int strategy;             /* wbrw_strategy                                 */
   double hbar, mass, dt, gamma0;
-  int nx, nk;               /* cells; nx * nk < 2^30                          */
+  int nx, nk;               /* cells per coordinate: nx * nk (dim 2) or      */
+                            /* nx^2 nk^2 (dim 4) cells, < 2^30               */
   double xmin, xmax, kmin, kmax;
   int resample_every;       /* steps per T_A for wbrw_run; 0 = never          */
   long long n_alpha;        /* N_alpha (> 0)                                 */
   unsigned long long seed;  /* Philox key                                    */
+  int table_ny, table_nkappa; /* dim 4: kernel tables of table_ny y nodes x  */
+                            /* table_nkappa kappa cells (0: 4096 x 2048)     */
 } wbrw_config;
 
 /* Caller-owned device buffers, structure of arrays, `capacity` elements each:
- *   x, k : positions and wavevectors, double (WBRW_FP64) or float (WBRW_FP32)
+ *   x, k : positions and wavevectors, double (WBRW_FP64) or float (WBRW_FP32);
+ *          dim 4: 2*capacity elements each (see wbrw_init4d)
  *   s    : signs +1 / -1 (int8)
  *   w    : signed weights (sp2 only; same type as x; NULL for sp1)
  *   grid : nx*nk int32 signed counts c_nu (grid_cells >= nx*nk), valid after
@@ -107,12 +124,17 @@ typedef struct {
 
 /* One accepted branching event (Alg. 1 item 3), as logged for parity tests.
  * kappa is the oriented kick: the + child is at k + kappa, the - child at
- * k - kappa.  factor = cacc |sin(2 (xe - xc) kappa)|. */
+ * k - kappa (dim 4: k +/- kappa e_comp with e_0 = (1,0), e_1 = (0,1),
+ * e_2 = (1,-1)).  factor: dim 2, cacc |sin(2 (xe - xc) kappa)|; dim 4, the
+ * probability xi_h(y)/gamma_comp that the death made a pair.  xe2 is the
+ * second electron's position (dim 4; dim 2 repeats xe). */
 typedef struct {
   unsigned long long pid, pid_plus, pid_minus;
   unsigned int step, j;
   double t, xe, kappa, factor;
   int kill_plus, kill_minus;
+  double xe2;
+  int comp, pad;
 } wbrw_event;
 
 /* Counter slots returned by wbrw_counters. */
@@ -158,6 +180,29 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
                       double x0, double sigma_x, double k0, void* cuda_stream,
                       wbrw_ctx** out);
 
+/* The 4D Helium-like system (config->dim = 4, pot->kind =
+ * WBRW_POT_SOFT_COULOMB_2E, sp1): draw n_init particles from the product of
+ * two Gaussian-wavepacket Wigner functions (electron e: x0[e], sigma_x,
+ * k0[e]), sign +1.  The kernel tables are built on the device from the
+ * definition above: rows at y_i = -Y + i 2Y/(table_ny - 1) with Y = xmax - xmin
+ * (one-body) or 2 (xmax - xmin) (interaction), cells
+ * kappa_j = -K + (j + 1/2) 2K/table_nkappa with K = kmax - kmin, values
+ * max(V_W(y_i, kappa_j), 0) and their running sums along each row,
+ * xi_i = (row sum) dkappa.  Each component's rate is the smallest multiple
+ * of 2^-10 at or above its largest xi_i; deaths come at the total rate
+ * Gamma = 2 gamma_onebody + gamma_interaction (Sec. 3.2), pick a component
+ * in proportion to its rate, and make a pair with probability
+ * xi_h(y)/gamma (xi_h linear between rows, clamped outside them), the kick
+ * drawn by inverse CDF of the interpolated row (Eq. def.xi_m and Sec. 4.2).
+ * Buffers: x and k hold 2*capacity elements each (electron 1 in
+ * [0, capacity), electron 2 in [capacity, 2 capacity)); grid holds
+ * nx^2 nk^2 cells, cell ((ix1 nx + ix2) nk + ik1) nk + ik2.  Synchronises
+ * the stream once (the tables' maxima).  Otherwise as wbrw_init. */
+wbrw_status wbrw_init4d(const wbrw_config* config, const wbrw_potential* pot,
+                        const wbrw_buffers* buffers, long long n_init, const double x0[2],
+                        double sigma_x, const double k0[2], void* cuda_stream,
+                        wbrw_ctx** out);
+
 /* Advance nsteps intervals [t_l, t_{l+1}] (Alg. 1) without resampling and
  * leave the particles in the caller's arrays (offspring appended).  Async. */
 wbrw_status wbrw_step(wbrw_ctx* ctx, int nsteps);
@@ -181,6 +226,9 @@ wbrw_status wbrw_run(wbrw_ctx* ctx, int nsteps);
  *   marginal_x_host [nx]: sum_k c_nu / (N_alpha dx) (or NULL)
  *   transmission: sum over cells with centre x > 0 of c_nu / N_alpha
  *   live_particles: particles now (or NULL)
+ * For dim 4 these are electron 1's: the counts summed over (x2, k2) give
+ * the reduced Wigner function f1(x1, k1), its x1-marginal, and the
+ * probability of x1 > 0.
  * After a resampling c_nu is the grid.  Otherwise the current particles are
  * histogrammed on the fly (sp2: signed weights in Q1.31) without changing
  * the state.  Synchronises the stream. */

@@ -8,6 +8,6 @@ bootstrap filter (sp2).  All of it runs in hand-written CUDA kernels behind
 the C ABI of include/wbrw.h; ``wbrw`` is its ctypes binding.
 """
 from . import wbrw  # noqa: F401
-from .wbrw import Batch, Simulation, WbrwError, load  # noqa: F401
+from .wbrw import Batch, Simulation, Simulation4, WbrwError, load  # noqa: F401
 
-__all__ = ["wbrw", "Batch", "Simulation", "WbrwError", "load"]
+__all__ = ["wbrw", "Batch", "Simulation", "Simulation4", "WbrwError", "load"]

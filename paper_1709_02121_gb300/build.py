@@ -1,6 +1,8 @@
 """Build the CUDA library libwbrw.so for sm_103a (GB300), in tree.
 
-Four translation units are compiled in parallel with nvcc and linked into
+Six translation units (the kernels of each precision and phase-space model,
+the resampling kernels and the C ABI) are compiled in parallel with nvcc and
+linked into
 ``paper_1709_02121_gb300/_build/libwbrw.so`` against the shared CUDA runtime
 (the process shares one runtime with PyTorch).  No CMake, one -gencode.
 """
@@ -16,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwbrw.so")
-SOURCES = ["wbrw_fp32.cu", "wbrw_fp64.cu", "wbrw_common.cu", "wbrw_api.cu"]
+SOURCES = ["wbrw_fp32.cu", "wbrw_fp64.cu", "wbrw_fp32_4d.cu", "wbrw_fp64_4d.cu",
+           "wbrw_common.cu", "wbrw_api.cu"]
 HEADERS = ["wbrw_device.cuh", "wbrw_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -40,7 +43,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    # host code: no contraction into fused multiply-adds, so that host-side
+    # constants round as written on either host architecture
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                    "-Xcompiler", "-ffp-contract=off",
                     "-I", INCLUDE, "-I", CSRC, "-Xptxas", "-v" if verbose else "-O3"]
     procs, objs = [], []
     for src in SOURCES:

@@ -8,7 +8,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <new>
+#include <vector>
 
 #include "wbrw.h"
 #include "wbrw_internal.h"
@@ -27,7 +29,8 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
   size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, seg_counts, cnt_save, tabs, cinst, total;
+      rec_a, keep0, keep1, res0, res1, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
+      tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
@@ -38,13 +41,21 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
     return false;
   };
   if (!c) return fail("NULL config");
-  if (c->dim != 2) return fail("dim must be 2");
+  if (c->dim != 2 && c->dim != 4) return fail("dim must be 2 or 4");
+  if (c->dim == 4 && c->strategy != WBRW_SP1_PAIR) return fail("dim 4 uses sp1 only");
+  if (c->dim == 4 && ninst > 1) return fail("dim 4 runs one instance");
+  if (c->table_ny < 0 || c->table_ny == 1 || c->table_nkappa < 0 || c->table_ny > (1 << 20) ||
+      c->table_nkappa > (1 << 20))
+    return fail("table sizes");
   if (c->precision != WBRW_FP64 && c->precision != WBRW_FP32) return fail("precision");
   if (c->strategy != WBRW_SP1_PAIR && c->strategy != WBRW_SP2_BOOTSTRAP) return fail("strategy");
   if (!(c->hbar > 0) || !(c->mass > 0) || !(c->dt > 0)) return fail("hbar, mass and dt must be > 0");
   if (c->nx <= 0 || c->nk <= 0) return fail("nx and nk must be > 0");
   if (ninst < 0 || ninst > kMaxInst) return fail("instances must be 1..WBRW_MAX_INSTANCES");
-  if ((long long)c->nx * (long long)c->nk * (ninst > 0 ? ninst : 1) >= (1ll << 30))
+  const long long cells = c->dim == 4 ? (long long)c->nx * c->nx * c->nk * c->nk
+                                      : (long long)c->nx * c->nk;
+  if (c->dim == 4 && (c->nx > 4096 || c->nk > 4096)) return fail("nx, nk <= 4096 for dim 4");
+  if (cells * (ninst > 0 ? ninst : 1) >= (1ll << 30))
     return fail("cells of all instances must be < 2^30");
   if (ninst > 1 && c->strategy != WBRW_SP1_PAIR) return fail("batches use sp1 only");
   if (!(c->xmax > c->xmin) || !(c->kmax > c->kmin)) return fail("empty domain");
@@ -58,11 +69,20 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
 // into one segment per producer warp (at most kMaxSeg); each segment gets at
 // least kMinSeg entries so that small runs cannot starve a warp.
 constexpr long long kMinSeg = 64;
-size_t fentry_size(int precision) { return precision == WBRW_FP64 ? 40 : 24; }
+const Driver* drv_for(int precision, int dim) {
+  if (dim == 4) return precision == WBRW_FP64 ? driver_fp64_4d() : driver_fp32_4d();
+  return precision == WBRW_FP64 ? driver_fp64() : driver_fp32();
+}
+
+int table_ny(const wbrw_config* c) { return c->table_ny > 0 ? c->table_ny : 4096; }
+int table_nkappa(const wbrw_config* c) { return c->table_nkappa > 0 ? c->table_nkappa : 2048; }
 
 Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   Layout L;
-  const long long nh = (long long)c->nx * c->nk * ninst;
+  const Driver* d = drv_for(c->precision, c->dim);
+  const long long cells = c->dim == 4 ? (long long)c->nx * c->nx * c->nk * c->nk
+                                      : (long long)c->nx * c->nk;
+  const long long nh = cells * ninst;
   const long long floor_entries = (long long)kMaxSeg * kMinSeg;
   L.qcap = capacity > floor_entries ? capacity : floor_entries;
   L.ecap = 2 * L.qcap;  // about one candidate interval per particle per flight
@@ -80,11 +100,11 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.seg_counts = take((size_t)(1 + 2 + kMaxLevels + 1) * kMaxSeg * sizeof(unsigned));
   L.cnt_save = take(sizeof(Counters));
   L.cpid = take((size_t)capacity * 8);
-  L.fq0 = take((size_t)L.qcap * fentry_size(c->precision));
-  L.fq1 = take((size_t)L.qcap * fentry_size(c->precision));
-  L.eq = take((size_t)L.ecap * fentry_size(c->precision));
-  L.dq0 = take((size_t)L.dcap * 64);
-  L.dq1 = take((size_t)L.dcap * 64);
+  L.fq0 = take((size_t)L.qcap * d->fentry_bytes);
+  L.fq1 = take((size_t)L.qcap * d->fentry_bytes);
+  L.eq = take((size_t)L.ecap * d->fentry_bytes);
+  L.dq0 = take((size_t)L.dcap * d->sentry_bytes);
+  L.dq1 = take((size_t)L.dcap * d->sentry_bytes);
   L.nz_cell = take((size_t)nh * 4);
   L.nz_start = take((size_t)nh * 8);
   L.tile_nz = take((size_t)L.tile_cap * 4);
@@ -96,6 +116,7 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.obs_marg = take((size_t)c->nx * 8);
   L.obs_col = take((size_t)c->nx * 8);
   L.obs_scalar = take(64);
+  L.obs_red = take(c->dim == 4 ? (size_t)c->nx * c->nk * 8 : 0);
   L.rec_cell = take((size_t)L.rec_cap * 4);
   L.rec_a = take((size_t)L.rec_cap * 4);
   const bool sp2 = c->strategy == WBRW_SP2_BOOTSTRAP;
@@ -105,6 +126,15 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.res1 = take(sp2 ? (size_t)nh * 8 : 0);
   L.tabs = take(kTabBytes);
   L.cinst = take(ninst > 1 ? (size_t)capacity * 4 : 0);
+  const bool d4 = c->dim == 4;
+  const size_t el = c->precision == WBRW_FP64 ? 8 : 4;
+  const size_t ny = (size_t)table_ny(c), nk = (size_t)table_nkappa(c);
+  L.tab_A = take(d4 ? 2 * nk * 8 : 0);
+  L.tab_xmax = take(d4 ? 16 : 0);
+  L.tab_xi0 = take(d4 ? ny * el : 0);
+  L.tab_xi1 = take(d4 ? ny * el : 0);
+  L.tab_cdf0 = take(d4 ? ny * nk * el : 0);
+  L.tab_cdf1 = take(d4 ? ny * nk * el : 0);
   L.total = off;
   return L;
 }
@@ -161,9 +191,7 @@ wbrw_status cuda_check(wbrw_ctx* c, cudaError_t e, const char* what) {
   return seterr(c, WBRW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-const Driver* drv(const wbrw_ctx* c) {
-  return c->cfg.precision == WBRW_FP64 ? driver_fp64() : driver_fp32();
-}
+const Driver* drv(const wbrw_ctx* c) { return drv_for(c->cfg.precision, c->cfg.dim); }
 
 #define WBRW_TRY(c, expr, what)                           \
   do {                                                    \
@@ -395,13 +423,62 @@ void set_shape(wbrw_ctx* c, int bps) {
   c->rseg = c->rec_cap / c->nseg;
 }
 
+// The 4D model's kernel tables: A_tj = (4 q_t / (pi hbar)) K0(2 a |kappa_j|)
+// on the host (the library routine for K0), rows and running sums on the
+// device; then each component's rate, the smallest multiple of 2^-10 at or
+// above its largest xi, and the total rate Gamma = 2 gamma_0 + gamma_1 of the
+// candidate clock (one-body terms on electrons 1 and 2, and the interaction).
+wbrw_status build_tables(wbrw_ctx* c, char* base, const Layout& L) {
+  const wbrw_config& g = c->cfg;
+  c->tab_ny = table_ny(&g);
+  c->tab_nkap = table_nkappa(&g);
+  c->tab_K = g.kmax - g.kmin;
+  c->tab_dkap = 2.0 * c->tab_K / (double)c->tab_nkap;
+  for (int t = 0; t < 2; ++t) {
+    c->tab_Y[t] = t == 0 ? (g.xmax - g.xmin) : 2.0 * (g.xmax - g.xmin);
+    c->tab_dy[t] = 2.0 * c->tab_Y[t] / (double)(c->tab_ny - 1);
+    c->tab_inv_dy[t] = (double)(c->tab_ny - 1) / (2.0 * c->tab_Y[t]);
+  }
+  c->tab_A = (double*)(base + L.tab_A);
+  c->tab_xmax = (unsigned long long*)(base + L.tab_xmax);
+  c->tab_xi[0] = base + L.tab_xi0;
+  c->tab_xi[1] = base + L.tab_xi1;
+  c->tab_cdf[0] = base + L.tab_cdf0;
+  c->tab_cdf[1] = base + L.tab_cdf1;
+  std::vector<double> A((size_t)2 * c->tab_nkap);
+  const double pi = 3.141592653589793238462643383280;
+  for (int t = 0; t < 2; ++t) {
+    const double q = t == 0 ? -c->pot.H : c->pot.ee;
+    const double pre = (4.0 * q) / (pi * g.hbar);
+    for (int j = 0; j < c->tab_nkap; ++j) {
+      const double kap = -c->tab_K + ((double)j + 0.5) * c->tab_dkap;
+      A[(size_t)t * c->tab_nkap + j] = pre * std::cyl_bessel_k(0.0, 2.0 * c->pot.w * fabs(kap));
+    }
+  }
+  double xmax[2] = {0, 0};
+  WBRW_TRY(c, drv(c)->tables(c, A.data(), xmax), "kernel tables");
+  for (int t = 0; t < 2; ++t) c->tab_gam[t] = ceil(1024.0 * xmax[t]) / 1024.0;
+  InstHost& q = c->ih[0];
+  double Gam = 2.0 * c->tab_gam[0] + c->tab_gam[1];
+  if (!(Gam > 0)) Gam = 1.0;  // no potential: no pair is ever made
+  q.gamma0 = Gam;
+  q.cacc = 1.0;
+  q.sig_k = 0.0;
+  q.C = 0.0;
+  q.p_any = -expm1(-Gam * g.dt);
+  return WBRW_OK;
+}
+
 // Create a context for ninst instances (records q, starts filled in here)
 // and enqueue the initial sampling.  Takes ownership of q.
-wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw_buffers* b,
-                   void* cuda_stream, wbrw_ctx** out) {
+wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int ninst, InstHost* q,
+                   const wbrw_buffers* b, void* cuda_stream, wbrw_ctx** out) {
+  const long long cells = config->dim == 4
+                              ? (long long)config->nx * config->nx * config->nk * config->nk
+                              : (long long)config->nx * config->nk;
   if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0 ||
       (config->strategy == WBRW_SP2_BOOTSTRAP && !b->w) ||
-      b->grid_cells < (long long)config->nx * config->nk * ninst ||
+      b->grid_cells < cells * ninst ||
       ((uintptr_t)b->scratch & (kAlign - 1)) != 0 ||
       (b->event_log && b->event_log_capacity <= 0)) {
     free(q);
@@ -425,10 +502,16 @@ wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw
   if (!c->host_tab) { free_ctx(c); return WBRW_ERR_ARG; }
   c->ninst = ninst;
   c->cfg = *config;
-  c->pot.kind = WBRW_POT_GAUSSIAN;
-  c->pot.H = q[0].H;
-  c->pot.w = q[0].w;
-  c->pot.xc = q[0].xc;
+  c->dim = config->dim;
+  if (pot) {
+    c->pot = *pot;
+  } else {
+    c->pot.kind = WBRW_POT_GAUSSIAN;
+    c->pot.H = q[0].H;
+    c->pot.w = q[0].w;
+    c->pot.xc = q[0].xc;
+    c->pot.ee = 0;
+  }
   c->buf = *b;
   c->stream = (cudaStream_t)cuda_stream;
   c->hm = config->hbar / config->mass;
@@ -442,7 +525,7 @@ wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw
   c->dk = (config->kmax - config->kmin) / (double)config->nk;
   c->inv_dx = (double)config->nx / (config->xmax - config->xmin);
   c->inv_dk = (double)config->nk / (config->kmax - config->kmin);
-  c->nhi = (long long)config->nx * config->nk;
+  c->nhi = cells;
   c->nh = c->nhi * ninst;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) !=
@@ -495,6 +578,18 @@ wbrw_status create(const wbrw_config* config, int ninst, InstHost* q, const wbrw
   c->inst_na = (double*)(base + L.tabs + kTabNaOff);
   c->inst_trans = (double*)(base + L.tabs + kTabTransOff);
   c->cinst = ninst > 1 ? (unsigned*)(base + L.cinst) : nullptr;
+  c->obs_red = (long long*)(base + L.obs_red);
+  if (c->dim == 4) {
+    wbrw_status st = build_tables(c, base, L);
+    if (st != WBRW_OK) {
+      free_ctx(c);
+      return st;
+    }
+    // the total rate of the three components sets the candidate clock
+    c->max_chunk = q[0].p_any > 0 ? (int)floor(1.0 / q[0].p_any) : kMaxChunk;
+    if (c->max_chunk > kMaxChunk) c->max_chunk = kMaxChunk;
+    if (c->max_chunk < 1) c->max_chunk = 1;
+  }
   c->state = ST_PARTICLES;
   c->step = 0;
   c->epoch = 0;
@@ -523,21 +618,51 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
                       wbrw_ctx** out) {
   if (!out) return WBRW_ERR_ARG;
   *out = nullptr;
-  if (!config_ok(config, nullptr, 0)) return WBRW_ERR_ARG;
+  if (!config_ok(config, nullptr, 0) || config->dim != 2) return WBRW_ERR_ARG;
   InstHost* q = (InstHost*)calloc(1, sizeof(InstHost));
   if (!q) return WBRW_ERR_ARG;
   if (!make_instance(config, pot, config->gamma0, x0, sigma_x, k0, n_init, config->n_alpha, q)) {
     free(q);
     return WBRW_ERR_ARG;
   }
-  return create(config, 1, q, b, cuda_stream, out);
+  return create(config, nullptr, 1, q, b, cuda_stream, out);
+}
+
+wbrw_status wbrw_init4d(const wbrw_config* config, const wbrw_potential* pot,
+                        const wbrw_buffers* b, long long n_init, const double x0[2],
+                        double sigma_x, const double k0[2], void* cuda_stream, wbrw_ctx** out) {
+  if (!out) return WBRW_ERR_ARG;
+  *out = nullptr;
+  if (!config_ok(config, nullptr, 0) || config->dim != 4 || !x0 || !k0) return WBRW_ERR_ARG;
+  if (!pot || pot->kind != WBRW_POT_SOFT_COULOMB_2E || !(pot->w > 0) || !isfinite(pot->w) ||
+      !isfinite(pot->H) || !isfinite(pot->xc) || !isfinite(pot->ee))
+    return WBRW_ERR_ARG;
+  if (!(sigma_x > 0) || !isfinite(sigma_x) || n_init < 0 || !isfinite(x0[0]) ||
+      !isfinite(x0[1]) || !isfinite(k0[0]) || !isfinite(k0[1]))
+    return WBRW_ERR_ARG;
+  InstHost* q = (InstHost*)calloc(1, sizeof(InstHost));
+  if (!q) return WBRW_ERR_ARG;
+  q->H = pot->H;
+  q->w = pot->w;
+  q->xc = pot->xc;
+  q->x0 = x0[0];
+  q->x0b = x0[1];
+  q->sx = sigma_x;
+  q->k0 = k0[0];
+  q->k0b = k0[1];
+  q->n_init = n_init;
+  q->n_alpha = config->n_alpha;
+  q->gamma0 = 1.0;  // set with the tables
+  q->p_any = 0.0;
+  return create(config, pot, 1, q, b, cuda_stream, out);
 }
 
 wbrw_status wbrw_batch_init(const wbrw_config* config, int ninst, const wbrw_instance* inst,
                             const wbrw_buffers* b, void* cuda_stream, wbrw_ctx** out) {
   if (!out) return WBRW_ERR_ARG;
   *out = nullptr;
-  if (ninst < 1 || !inst || !config_ok(config, nullptr, 0, ninst)) return WBRW_ERR_ARG;
+  if (ninst < 1 || !inst || !config_ok(config, nullptr, 0, ninst) || config->dim != 2)
+    return WBRW_ERR_ARG;
   InstHost* q = (InstHost*)calloc((size_t)ninst, sizeof(InstHost));
   if (!q) return WBRW_ERR_ARG;
   for (int i = 0; i < ninst; ++i) {
@@ -548,7 +673,7 @@ wbrw_status wbrw_batch_init(const wbrw_config* config, int ninst, const wbrw_ins
       return WBRW_ERR_ARG;
     }
   }
-  return create(config, ninst, q, b, cuda_stream, out);
+  return create(config, nullptr, ninst, q, b, cuda_stream, out);
 }
 
 wbrw_status wbrw_step(wbrw_ctx* c, int nsteps) {
@@ -627,7 +752,8 @@ wbrw_status wbrw_instance_density(wbrw_ctx* c, int inst, double* density_host,
     WBRW_TRY(c, launch_observables(c, inst, nullptr, c->tmp_wsum), "observables");
   }
   if (density_host)
-    WBRW_TRY(c, cudaMemcpyAsync(density_host, c->obs_density, (size_t)c->nhi * 8,
+    WBRW_TRY(c, cudaMemcpyAsync(density_host, c->obs_density,
+                                (size_t)c->cfg.nx * c->cfg.nk * 8,
                                 cudaMemcpyDeviceToHost, c->stream), "copy density");
   if (marginal_x_host)
     WBRW_TRY(c, cudaMemcpyAsync(marginal_x_host, c->obs_marg, (size_t)c->cfg.nx * 8,
@@ -669,6 +795,12 @@ wbrw_status wbrw_transmissions(wbrw_ctx* c, double* out_host) {
   if (c->failed) return WBRW_ERR_STATE;
   if (c->state != ST_HISTOGRAM)
     return seterr(c, WBRW_ERR_STATE, "transmissions need a resampling first");
+  if (c->dim == 4) {
+    WBRW_TRY(c, launch_observables(c, 0, c->buf.grid, nullptr), "observables");
+    WBRW_TRY(c, cudaMemcpyAsync(out_host, c->obs_scalar, 8, cudaMemcpyDeviceToHost, c->stream),
+             "copy");
+    return device_status(c);
+  }
   WBRW_TRY(c, launch_transmissions(c, c->buf.grid, c->inst_trans), "transmissions");
   WBRW_TRY(c, cudaMemcpyAsync(out_host, c->inst_trans, (size_t)c->ninst * 8,
                               cudaMemcpyDeviceToHost, c->stream), "copy");

@@ -375,14 +375,14 @@ __global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long
 // ---------------------------------------------------------------------------
 // Observables: one warp per x-column.
 // ---------------------------------------------------------------------------
+// counts (int) or wsum (int64, each value times scale) per cell, x-major.
 __global__ void __launch_bounds__(kBlock) k_obs_cols(const int* counts, const long long* wsum,
                                                      int nx, int nk, double na, double dx,
-                                                     double dk, double* density, double* marg,
-                                                     long long* col) {
+                                                     double dk, double scale, double* density,
+                                                     double* marg, long long* col) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * kBlock) >> 5;
-  const double scale = wsum ? 1.0 / 2147483648.0 : 1.0;
   for (long long ix = warp; ix < nx; ix += nwarps) {
     long long s = 0;
     for (int ik = lane; ik < nk; ik += 32) {
@@ -458,6 +458,27 @@ __global__ void __launch_bounds__(kBlock) k_live_inst(const Counters* c,
   if (threadIdx.x == 0 && t) atomicAdd(out, t);
 }
 
+// The 4D counts summed over electron 2: red[ix1 nk + ik1] =
+// sum over (ix2, ik2) of counts[((ix1 nx + ix2) nk + ik1) nk + ik2], one warp
+// per output.
+__global__ void __launch_bounds__(kBlock) k_reduce4(const int* counts, int nx, int nk,
+                                                    long long* red) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * kBlock) >> 5;
+  for (long long o = warp; o < (long long)nx * nk; o += nwarps) {
+    const long long ix1 = o / nk, ik1 = o % nk;
+    long long s = 0;
+    for (long long ix2 = 0; ix2 < nx; ++ix2) {
+      const int* row = counts + ((ix1 * nx + ix2) * nk + ik1) * nk;
+      for (int ik2 = lane; ik2 < nk; ik2 += 32) s += row[ik2];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, d);
+    if (lane == 0) red[o] = s;
+  }
+}
+
 int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
 
 }  // namespace
@@ -514,11 +535,20 @@ cudaError_t launch_observables(Ctx* c, int inst, const int* counts, const long l
   const double na = (double)c->ih[inst].n_alpha;
   const int g = grid_cap(c, 4);
   const long long off = (long long)inst * c->nhi;
-  k_obs_cols<<<g, kBlock, 0, c->stream>>>(counts ? counts + off : nullptr,
-                                          wsum ? wsum + off : nullptr, c->cfg.nx, c->cfg.nk, na,
-                                          c->dx, c->dk, c->obs_density, c->obs_marg, c->obs_col);
+  const int* cn = counts ? counts + off : nullptr;
+  const long long* ws = wsum ? wsum + off : nullptr;
+  double scale = wsum ? 1.0 / 2147483648.0 : 1.0;
+  if (c->dim == 4 && cn) {  // electron 1's reduced counts
+    k_reduce4<<<g, kBlock, 0, c->stream>>>(cn, c->cfg.nx, c->cfg.nk, c->obs_red);
+    c->launches++;
+    cn = nullptr;
+    ws = c->obs_red;
+    scale = 1.0;
+  }
+  k_obs_cols<<<g, kBlock, 0, c->stream>>>(cn, ws, c->cfg.nx, c->cfg.nk, na, c->dx, c->dk, scale,
+                                          c->obs_density, c->obs_marg, c->obs_col);
   k_obs_total<<<1, kBlock, 0, c->stream>>>(c->obs_col, c->cfg.nx, c->cfg.xmin, c->dx, na,
-                                           wsum ? 1.0 / 2147483648.0 : 1.0, c->obs_scalar);
+                                           scale, c->obs_scalar);
   c->launches += 2;
   return cudaGetLastError();
 }
@@ -584,7 +614,7 @@ extern "C" wbrw_status wbrw_observables_static(const int* grid, int nx, int nk, 
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return WBRW_ERR_CUDA;
-  wbrw::k_obs_cols<<<4 * sms, wbrw::kBlock, 0, s>>>(grid, nullptr, nx, nk, na, dx, dk, density,
+  wbrw::k_obs_cols<<<4 * sms, wbrw::kBlock, 0, s>>>(grid, nullptr, nx, nk, na, dx, dk, 1.0, density,
                                                     marginal_x, col);
   wbrw::k_obs_total<<<1, wbrw::kBlock, 0, s>>>(col, nx, xmin, dx, na, 1.0, transmission);
   return cudaGetLastError() == cudaSuccess ? WBRW_OK : WBRW_ERR_CUDA;

@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "wbrw_internal.h"
 
@@ -79,7 +80,7 @@ constexpr uint32_t kDrawCoins = 0xC0000000u;  // FP32 16-bit coins
 // no multiply-add is contracted: every expression rounds exactly as written,
 // which is the operation order the FP64 parity contract fixes.
 // ---------------------------------------------------------------------------
-struct P64 {
+struct F64 {
   using T = double;
   static constexpr bool is64 = true;
   __device__ static T add(T a, T b) { return __dadd_rn(a, b); }
@@ -92,7 +93,7 @@ struct P64 {
   __device__ static T next_up(T a) { return nextafter(a, CUDART_INF); }
 };
 
-struct P32 {
+struct F32 {
   using T = float;
   static constexpr bool is64 = false;
   __device__ static T add(T a, T b) { return __fadd_rn(a, b); }
@@ -105,21 +106,42 @@ struct P32 {
   __device__ static T next_up(T a) { return nextafterf(a, CUDART_INF_F); }
 };
 
-template <class T>
+// Phase-space model: precision F and D position coordinates (D = 1: the 2D
+// phase space (x, k) of one particle; D = 2: the 4D phase space
+// (x1, x2, k1, k2) of two electrons, Example 1).
+template <class F, int Dm>
+struct PD : F {
+  static constexpr int D = Dm;
+};
+using P64 = PD<F64, 1>;
+using P32 = PD<F32, 1>;
+using Q64 = PD<F64, 2>;
+using Q32 = PD<F32, 2>;
+
+// A position or a wavevector of the model.
+template <class P>
+struct PV {
+  typename P::T c[P::D];
+};
+
+template <class P>
 struct FEntry {  // a particle at the start of interval l (offspring waves),
                  // or a candidate interval l with x at its start
   unsigned long long pid;
-  T x, k, w;
+  PV<P> x, k;
+  typename P::T w;
   int l;
 };
 
-static_assert(sizeof(FEntry<double>) == 40 && sizeof(FEntry<float>) == 24, "FEntry layout");
+static_assert(sizeof(FEntry<P64>) == 40 && sizeof(FEntry<P32>) == 24, "FEntry layout");
+static_assert(sizeof(FEntry<Q32>) == 32, "FEntry layout");
 
 template <class P>
 struct SEntry;
 
 
-// Physics of one instance of a batch (a single run is a batch of one).
+// Physics of one instance of a batch (a single run is a batch of one).  In
+// the 4D model gamma0 is the total rate Gamma of the three components.
 template <class T>
 struct Inst {
   T gamma0, cacc, sig_k, xc;  // rate, acceptance factor C/(2 gamma0), kick scale, centre
@@ -129,10 +151,27 @@ struct Inst {
   int well;                   // H < 0: V_W has the sign of -sin (Eq. 2)
 };
 
-// Initial sampling of one instance: slots [start, start + n) of the arrays.
+// Initial sampling of one instance: slots [start, start + n) of the arrays
+// (x0b, k0b: the second electron of the 4D model).
 struct InitInst {
   double x0, sx, k0, sk;
   unsigned long long start;
+  double x0b, k0b;
+};
+
+// Kernel tables of the 4D model (type 0: one-body, 1: interaction).  Row i
+// of type t belongs to y_i = -Y_t + i dy_t; cell j to kappa_j =
+// -K + (j + 1/2) dkappa.  cdf rows: FP64 the prefix sums S_ij of V_W^+,
+// FP32 S_ij / S_i,last.
+template <class T>
+struct Tab4 {
+  const T* xi[2];     // ny per type
+  const T* cdf[2];    // ny x nkap per type
+  double Y[2], inv_dy[2];
+  double gam[2];      // component rates gamma_t (one-body twice, interaction once)
+  double xc;          // nucleus
+  T kap0, dkap;       // -K, dkappa
+  int ny, nkap;
 };
 
 // Queue entries carry the interval and the instance in one word.
@@ -154,6 +193,7 @@ template <class P>
 struct KP {
   using T = typename P::T;
   T dt, dtv, hm;
+  Tab4<T> tab;      // 4D model only
   T xmin, kmin, kmax, dx, dk, inv_dx, inv_dk;
   int nx, nk;
   float inv_nk;     // 1/nk, for cell -> (ix, ik)
@@ -169,19 +209,19 @@ struct KP {
   int l0, L;        // the intervals [l0, L) of the chunk (read at kernel entry)
   int len;          // L - l0
   unsigned long long regen_base;  // epoch << 40 of the histogram's particles
-  T* x;
+  T* x;             // coordinate d of slot i at x[d capacity + i]
   T* k;
   signed char* s;
   T* w;
   long long capacity;
   unsigned long long* cpid;
   int nseg;                  // segments per queue (producer warps)
-  FEntry<T>* fq_in;          // offspring of the previous wave
+  FEntry<P>* fq_in;          // offspring of the previous wave
   const unsigned* fcnt_in;
-  FEntry<T>* fq_out;         // offspring for the next wave
+  FEntry<P>* fq_out;         // offspring for the next wave
   unsigned* fcnt_out;
   long long qseg;
-  FEntry<T>* eq;             // candidate intervals
+  FEntry<P>* eq;             // candidate intervals
   unsigned* ecnt;
   long long eseg;
   SEntry<P>* dq[2];          // deferred segments; level L lives in dq[L & 1]
@@ -246,15 +286,43 @@ __device__ __forceinline__ unsigned long long global_warp() {
   return (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
 }
 
+// The histogram cell of a phase-space point (Sec. 4.3, uniform mesh):
+// ix nk + ik, or ((ix1 nx + ix2) nk + ik1) nk + ik2 in the 4D model.
 template <class P>
-__device__ __forceinline__ bool cell_of(const KP<P>& p, typename P::T x,
-                                        typename P::T k, int& cell) {
+__device__ __forceinline__ bool cell_of(const KP<P>& p, const PV<P>& x, const PV<P>& k,
+                                        int& cell) {
   using T = typename P::T;
-  const T fx = P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx));
-  const T fk = P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk));
-  if (!(fx >= (T)0 && fx < (T)p.nx && fk >= (T)0 && fk < (T)p.nk)) return false;
-  cell = (int)fx * p.nk + (int)fk;
+  int ix[P::D], ik[P::D];
+#pragma unroll
+  for (int d = 0; d < P::D; ++d) {
+    const T fx = P::flr(P::mul(P::sub(x.c[d], p.xmin), p.inv_dx));
+    const T fk = P::flr(P::mul(P::sub(k.c[d], p.kmin), p.inv_dk));
+    if (!(fx >= (T)0 && fx < (T)p.nx && fk >= (T)0 && fk < (T)p.nk)) return false;
+    ix[d] = (int)fx;
+    ik[d] = (int)fk;
+  }
+  if constexpr (P::D == 1) cell = ix[0] * p.nk + ik[0];
+  else cell = ((ix[0] * p.nx + ix[1]) * p.nk + ik[0]) * p.nk + ik[1];
   return true;
+}
+
+// Position at time t of a segment that started at (xo, to).
+template <class P>
+__device__ __forceinline__ PV<P> pos_at(const KP<P>& p, const PV<P>& xo,
+                                        typename P::T to, const PV<P>& k, typename P::T t) {
+  PV<P> x;
+  const typename P::T h = P::mul(P::sub(t, to), p.hm);
+#pragma unroll
+  for (int d = 0; d < P::D; ++d) x.c[d] = P::add(xo.c[d], P::mul(k.c[d], h));
+  return x;
+}
+
+template <class P>
+__device__ __forceinline__ bool k_inside(const KP<P>& p, const PV<P>& k) {
+  bool in = true;
+#pragma unroll
+  for (int d = 0; d < P::D; ++d) in = in && k.c[d] >= p.kmin && k.c[d] < p.kmax;
+  return in;
 }
 
 // Sum of one value over the block, added to a global counter by one thread.
@@ -306,23 +374,100 @@ __device__ __forceinline__ void store_counts(const KP<P>& p, const WarpCounts& w
 // (>= dt when there is none); Draw<P>::event gives event j's kick, sign
 // factor, acceptance uniform and next gap.
 // ---------------------------------------------------------------------------
-template <class P>
+template <class P, bool = P::is64>
 struct Draw;
+
+// The kick of the 4D model from its tables, given the event's uniforms:
+// component m (0: y = x1 - xc on k1; 1: y = x2 - xc on k2; 2: y = x1 - x2
+// on (k1, -k2)) is the first with uc Gamma < gamma_0 + ... + gamma_m; the row
+// position s = (y + Y)/dy, clamped to the mesh, splits into node i and weight
+// th; with g0 = (1 - th) xi_i and g1 = th xi_{i+1} the pair comes from row i
+// if ua gamma_m < g0, from row i+1 if ua gamma_m < g0 + g1, and is not made
+// otherwise, which thins the rate gamma_m down to the interpolant xi_h(y)
+// (Sec. 3.2, Eq. def.xi_m) and makes the kick law the interpolant of the two
+// rows' laws.  The kick is kappa_j + (uj - 1/2) dkappa for the first cell j
+// of the row's inverse CDF above uk.  prob = xi_h(y)/gamma_m.
+template <class P>
+__device__ __forceinline__ bool table_kick(const KP<P>& p, typename P::T Gam, const PV<P>& xe,
+                                           typename P::T ua, typename P::T uk,
+                                           typename P::T uc, typename P::T uj, int& comp,
+                                           typename P::T& kap, typename P::T& prob) {
+  using T = typename P::T;
+  const Tab4<T>& tb = p.tab;
+  const T g_ne = (T)tb.gam[0], g_ee = (T)tb.gam[1];
+  const T v = P::mul(uc, Gam);
+  const int m = v < g_ne ? 0 : (v < P::mul((T)2, g_ne) ? 1 : 2);
+  comp = m;
+  const int t = m == 2 ? 1 : 0;
+  const T xc = (T)tb.xc;
+  const T y = m == 0 ? P::sub(xe.c[0], xc)
+                     : (m == 1 ? P::sub(xe.c[P::D - 1], xc) : P::sub(xe.c[0], xe.c[P::D - 1]));
+  const T g = m == 2 ? g_ee : g_ne;
+  // (selects, not indexing by t: the parameters stay out of local memory)
+  const T sp = P::mul(P::add(y, (T)(t ? tb.Y[1] : tb.Y[0])), (T)(t ? tb.inv_dy[1] : tb.inv_dy[0]));
+  int i;
+  T th;
+  if (!(sp > (T)0)) {
+    i = 0;
+    th = (T)0;
+  } else if (sp >= (T)(tb.ny - 1)) {
+    i = tb.ny - 2;
+    th = (T)1;
+  } else {
+    i = (int)P::flr(sp);
+    th = P::sub(sp, (T)i);
+  }
+  const T* xi = t ? tb.xi[1] : tb.xi[0];
+  const T g0 = P::mul(P::sub((T)1, th), xi[i]);
+  const T g1 = P::mul(th, xi[i + 1]);
+  const T g01 = P::add(g0, g1);
+  prob = g > (T)0 ? P::div(g01, g) : (T)0;
+  const T va = P::mul(ua, g);
+  int r;
+  if (va < g0) r = i;
+  else if (va < g01) r = i + 1;
+  else return false;
+  const T* row = (t ? tb.cdf[1] : tb.cdf[0]) + (long long)r * tb.nkap;
+  const T target = P::is64 ? P::mul(uk, row[tb.nkap - 1]) : uk;
+  int lo = 0, hi = tb.nkap - 1;  // the first cell whose cumulative sum exceeds target
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (row[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  const T kj = P::add(tb.kap0, P::mul(P::add((T)lo, (T)0.5), tb.dkap));
+  kap = P::add(kj, P::mul(P::sub(uj, (T)0.5), tb.dkap));
+  return true;
+}
 
 // FP64: the parity contract shared with the oracle.  u0 of (pid, l, 0)
 // gives the first life-length from `to`; event j uses (pid, l, 1+2j) and
 // (pid, l, 2+2j).  Offspring draw their first life-length the same way.
-template <>
-struct Draw<P64> {
+// In the 4D model event j takes from those two calls ua = U53(a0,a1),
+// uk = U53(a2,a3), the gap from U53(b0,b1), uc = b2 2^-32, uj = b3 2^-32.
+template <class P>
+struct Draw<P, true> {
   struct State {};
-  __device__ static double first(const KP<P64>& p, const Inst<double>& ip,
+  __device__ static double first(const KP<P>& p, const Inst<double>& ip,
                                  unsigned long long pid, int l, double to, bool /*root*/,
                                  State&) {
     const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
     const double u0 = u53(r.x, r.y);
-    return P64::add(to, P64::div(-log1p(-u0), ip.gamma0));
+    return P::add(to, P::div(-log1p(-u0), ip.gamma0));
   }
-  __device__ static void event(const KP<P64>& p, const Inst<double>& ip, unsigned long long pid,
+  __device__ static bool event4(const KP<P>& p, const Inst<double>& ip, unsigned long long pid,
+                                int l, unsigned j, const PV<P>& xe, const State&, int& comp,
+                                double& kap, double& prob, double& gap) {
+    const uint32_t lo = (uint32_t)pid, hi = (uint32_t)(pid >> 32);
+    const uint4 a = philox_ks(p.ks, lo, hi, (uint32_t)l, 1u + 2u * j);
+    const uint4 b = philox_ks(p.ks, lo, hi, (uint32_t)l, 2u + 2u * j);
+    const double ua = u53(a.x, a.y), uk = u53(a.z, a.w), ug = u53(b.x, b.y);
+    const double uc = (double)b.z * (1.0 / 4294967296.0);
+    const double uj = (double)b.w * (1.0 / 4294967296.0);
+    gap = __ddiv_rn(-log1p(-ug), ip.gamma0);
+    return table_kick<P>(p, ip.gamma0, xe, ua, uk, uc, uj, comp, kap, prob);
+  }
+  __device__ static void event(const KP<P>& p, const Inst<double>& ip, unsigned long long pid,
                                int l, unsigned j, double xe, const State&, double& kap,
                                double& sg, double& u3, double& gap) {
     const uint32_t lo = (uint32_t)pid, hi = (uint32_t)(pid >> 32);
@@ -350,12 +495,24 @@ struct Draw<P64> {
 //    p_r 2^32, p_r = 1 - exp(-gamma0 (dt - tb)).  Only a hit draws the call
 //    (pid, l, 0), which then serves as for a root, with p_r for p_any.
 //  - Event j >= 1 of a segment uses the call (pid, l, 1+j): U24 of w0..w3.
-template <>
-struct Draw<P32> {
+//  - In the 4D model every event j, the first included, uses the call
+//    (pid, l, 1+j): ua = U24(w0), uk = U24(w1), the gap from U24(w2),
+//    uc = (w3 >> 16) 2^-16, uj = (w3 & 0xFFFF) 2^-16.
+template <class P>
+struct Draw<P, false> {
   struct State {
     uint4 r;
   };
-  __device__ static float first(const KP<P32>& p, const Inst<float>& ip, unsigned long long pid,
+  __device__ static bool event4(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
+                                int l, unsigned j, const PV<P>& xe, const State&, int& comp,
+                                float& kap, float& prob, float& gap) {
+    const uint4 a = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 1u + j);
+    const float uc = (float)(a.w >> 16) * (1.0f / 65536.0f);
+    const float uj = (float)(a.w & 0xFFFFu) * (1.0f / 65536.0f);
+    gap = (-log1pf(-u24(a.z))) / ip.gamma0;
+    return table_kick<P>(p, ip.gamma0, xe, u24(a.x), u24(a.y), uc, uj, comp, kap, prob);
+  }
+  __device__ static float first(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
                                 int l, float to, bool root, State& st) {
     float pr;
     if (root) {
@@ -367,7 +524,7 @@ struct Draw<P32> {
     st.r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
     return to + (-log1pf(-pr * u24(st.r.x))) / ip.gamma0;
   }
-  __device__ static void event(const KP<P32>& p, const Inst<float>& ip, unsigned long long pid,
+  __device__ static void event(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
                                int l, unsigned j, float xe, const State& st, float& kap,
                                float& sg, float& u3, float& gap) {
     float u1, u2, u4;
@@ -423,7 +580,7 @@ __device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long i
 // An end-of-chunk state produced inside the divergent event code.
 template <class P, int DST>
 __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
-                                 unsigned long long pid, typename P::T x, typename P::T k,
+                                 unsigned long long pid, const PV<P>& x, const PV<P>& k,
                                  typename P::T w) {
   using T = typename P::T;
   int cell;
@@ -448,8 +605,11 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
   } else {  // DST_ARRAY
     const unsigned long long slot = atomicAdd(&p.cnt->n, 1ull);
     if (slot >= (unsigned long long)p.capacity) { set_err(p.cnt, ERR_CAP_PARTICLES); return; }
-    p.x[slot] = x;
-    p.k[slot] = k;
+#pragma unroll
+    for (int d = 0; d < P::D; ++d) {
+      p.x[d * p.capacity + slot] = x.c[d];
+      p.k[d * p.capacity + slot] = k.c[d];
+    }
     p.s[slot] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
     if (p.w) p.w[slot] = w;
     p.cpid[slot - p.cnt->n_base] = pid;
@@ -472,13 +632,17 @@ template <class P>
 struct SEntry {  // a deferred segment, with the time and index of its next event
   using T = typename P::T;
   unsigned long long pid;
-  T xo, to, k, w, t;
+  PV<P> xo;
+  T to;
+  PV<P> k;
+  T w, t;
   int l;
   unsigned j;   // bits 0..30: index of the next event; bit 31: the root segment
   typename Draw<P>::State st;
 };
 
 static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
+static_assert(sizeof(SEntry<Q32>) == 64, "SEntry layout");
 
 constexpr unsigned kRootFlag = 0x80000000u;
 
@@ -486,13 +650,12 @@ constexpr unsigned kRootFlag = 0x80000000u;
 // the sink's in the chunk's last interval.
 template <class P, int DST>
 __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
-                                       unsigned long long pid, typename P::T xo,
-                                       typename P::T to, typename P::T k, typename P::T w,
+                                       unsigned long long pid, const PV<P>& xo,
+                                       typename P::T to, const PV<P>& k, typename P::T w,
                                        int l) {
-  using T = typename P::T;
-  const T xf = P::add(xo, P::mul(k, P::mul(P::sub(p.dt, to), p.hm)));
+  const PV<P> xf = pos_at(p, xo, to, k, p.dt);
   if (l + 1 < p.L) {
-    FEntry<T> e;
+    FEntry<P> e;
     e.pid = pid;
     e.x = xf;
     e.k = k;
@@ -521,35 +684,61 @@ __device__ __forceinline__ void defer(const KP<P>& p, WarpCounts& wc, int level,
     set_err(p.cnt, ERR_CAP_EQUEUE);
 }
 
-// Event j of a segment at time t: the kick of Remark 3, the acceptance
-// (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair.  Offspring are settled
-// or, when they have an event of their own in the interval, handed to
-// `later`.  Returns the gap to the segment's next event.
+// Event j of a segment at time t.  2D model: the kick of Remark 3, the
+// acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair.  4D model:
+// the component, thinning and tabulated kick of table_kick; the pair is
+// k +/- kappa e_m with e_0 = (1, 0), e_1 = (0, 1), e_2 = (1, -1).  Offspring
+// are settled or, when they have an event of their own in the interval,
+// handed to `later`.  Returns the gap to the segment's next event.
 template <class P, int DST, class Later>
 __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
                                                   const Inst<typename P::T>& ip, int inst,
                                                   WarpCounts& wc, Acc& acc,
-                                                  unsigned long long pid, typename P::T xo,
-                                                  typename P::T to, typename P::T k,
+                                                  unsigned long long pid, const PV<P>& xo,
+                                                  typename P::T to, const PV<P>& k,
                                                   typename P::T w,
                                                   const typename Draw<P>::State& st, int l,
                                                   unsigned j, typename P::T t, Later later) {
   using T = typename P::T;
-  const T xe = P::add(xo, P::mul(k, P::mul(P::sub(t, to), p.hm)));
-  T kap, sg, u3, gap;
-  Draw<P>::event(p, ip, pid, l, j, xe, st, kap, sg, u3, gap);
-  const T fac = P::mul(ip.cacc, (T)fabs(sg));
-  const bool emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
+  const PV<P> xe = pos_at(p, xo, to, k, t);
+  T kap, gap, fac;
+  bool emit;
+  int comp = 0;
+  PV<P> kp = k, km = k;
+  if constexpr (P::D == 1) {
+    T sg, u3;
+    Draw<P>::event(p, ip, pid, l, j, xe.c[0], st, kap, sg, u3, gap);
+    fac = P::mul(ip.cacc, (T)fabs(sg));
+    emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
+    if (emit) {
+      if (ip.well ? sg > (T)0 : sg < (T)0) kap = -kap;  // orient by sign(V_W)
+      kp.c[0] = P::add(k.c[0], kap);
+      km.c[0] = P::sub(k.c[0], kap);
+    }
+  } else {
+    emit = Draw<P>::event4(p, ip, pid, l, j, xe, st, comp, kap, fac, gap);
+    if (emit) {
+      if (comp != 1) {
+        kp.c[0] = P::add(k.c[0], kap);
+        km.c[0] = P::sub(k.c[0], kap);
+      }
+      if (comp == 1) {
+        kp.c[1] = P::add(k.c[1], kap);
+        km.c[1] = P::sub(k.c[1], kap);
+      } else if (comp == 2) {
+        kp.c[1] = P::sub(k.c[1], kap);
+        km.c[1] = P::add(k.c[1], kap);
+      }
+    }
+  }
   if (emit) {
-    if (ip.well ? sg > (T)0 : sg < (T)0) kap = -kap;  // orient by sign(V_W)
     const uint4 h = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
                               kDrawPids | j);
     const unsigned long long pid_p = (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
     const unsigned long long pid_m = (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
-    const T kp = P::add(k, kap), km = P::sub(k, kap);
-    const bool kill_p = !(kp >= p.kmin && kp < p.kmax);
-    const bool kill_m = !(km >= p.kmin && km < p.kmax);
-    const T wc_ = p.strategy == 1 ? w : P::mul(w, fac);
+    const bool kill_p = !k_inside(p, kp);
+    const bool kill_m = !k_inside(p, km);
+    const T wc_ = (P::D == 1 && p.strategy != 1) ? P::mul(w, fac) : w;
     ++acc.events;
     if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
     if (kill_m) { if (-wc_ > (T)0) ++acc.kill_p; else if (-wc_ < (T)0) ++acc.kill_m; }
@@ -563,11 +752,14 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
         ev.step = (unsigned)l;
         ev.j = j;
         ev.t = (double)t;
-        ev.xe = (double)xe;
+        ev.xe = (double)xe.c[0];
         ev.kappa = (double)kap;
         ev.factor = (double)fac;
         ev.kill_plus = kill_p;
         ev.kill_minus = kill_m;
+        ev.xe2 = (double)xe.c[P::D - 1];
+        ev.comp = comp;
+        ev.pad = 0;
         p.log[idx] = ev;
       }
     }
@@ -623,6 +815,17 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
 // interval's start, k, w, l) of the warp's segment of the candidate queue,
 // for k_event.
 // ---------------------------------------------------------------------------
+// A regenerated coordinate moved by single ulps back into its cell idx if
+// rounding left it there (Alg. 3 places every particle inside its cell).
+template <class P>
+__device__ __forceinline__ typename P::T in_cell(typename P::T v, typename P::T lo,
+                                                 typename P::T inv, int idx) {
+  using T = typename P::T;
+  for (int it = 0; it < 8 && P::flr(P::mul(P::sub(v, lo), inv)) > (T)idx; ++it) v = P::next_dn(v);
+  for (int it = 0; it < 8 && P::flr(P::mul(P::sub(v, lo), inv)) < (T)idx; ++it) v = P::next_up(v);
+  return v;
+}
+
 // Instance of a slot of the base region: the last instance whose first slot
 // is <= slot (empty instances share their start with the next one).
 template <class P>
@@ -638,9 +841,9 @@ __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long 
 
 template <class P, int SRC, int DST>
 __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
-                                            unsigned long long slot, typename P::T x,
-                                            typename P::T k, typename P::T w,
-                                            unsigned long long pid, int ls, int inst) {
+                                            unsigned long long slot, PV<P> x, const PV<P>& k,
+                                            typename P::T w, unsigned long long pid, int ls,
+                                            int inst) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   const unsigned long long g = global_warp();
@@ -649,7 +852,6 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
 
   // ---- candidate clock over [ls, L) (Sec. 3.2): which intervals hold an
   // event.  Bit b of mask is interval l0 + b.
-  const T x_start = x;
   unsigned mask = 0;
   const uint32_t plo = (uint32_t)pid, phi = (uint32_t)(pid >> 32);
   if (act) {
@@ -709,7 +911,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     for (int l = ls; l < p.L; ++l) {
       if ((mask >> (l - p.l0)) & 1u) {
         if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
-          FEntry<T> e;
+          FEntry<P> e;
           e.pid = pid;
           e.x = x;
           e.k = k;
@@ -721,10 +923,10 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         }
         ++q;
       }
-      x = P::stream(x, k, p.dtv);
+#pragma unroll
+      for (int d = 0; d < P::D; ++d) x.c[d] = P::stream(x.c[d], k.c[d], p.dtv);
     }
   }
-  (void)x_start;
   if (total) {
     __syncwarp();
     if (lane == 0) wc.e += total;
@@ -734,13 +936,19 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
   // ---- the particle's own final state ----------------------------------
   if constexpr (DST == DST_ARRAY) {
     if constexpr (SRC == SRC_ARRAY) {
-      if (act) p.x[slot] = x;
+      if (act) {
+#pragma unroll
+        for (int d = 0; d < P::D; ++d) p.x[d * p.capacity + slot] = x.c[d];
+      }
     } else if constexpr (SRC == SRC_REGEN) {
       if (act && slot >= (unsigned long long)p.capacity) {
         set_err(p.cnt, ERR_CAP_PARTICLES);
       } else if (act) {
-        p.x[slot] = x;
-        p.k[slot] = k;
+#pragma unroll
+        for (int d = 0; d < P::D; ++d) {
+          p.x[d * p.capacity + slot] = x.c[d];
+          p.k[d * p.capacity + slot] = k.c[d];
+        }
         p.s[slot] = w > (T)0 ? 1 : -1;
         if (p.w) p.w[slot] = w;
       }
@@ -753,8 +961,11 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         if (off >= (unsigned long long)p.capacity) {
           set_err(p.cnt, ERR_CAP_PARTICLES);
         } else {
-          p.x[off] = x;
-          p.k[off] = k;
+#pragma unroll
+          for (int d = 0; d < P::D; ++d) {
+            p.x[d * p.capacity + off] = x.c[d];
+            p.k[d * p.capacity + off] = k.c[d];
+          }
           p.s[off] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
           if (p.w) p.w[off] = w;
           p.cpid[off - p.cnt->n_base] = pid;
@@ -826,9 +1037,11 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       for (unsigned b = 0; b < n; b += 32) {
         const unsigned i = b + lane;
         const bool act = i < n;
-        FEntry<T> e;
+        FEntry<P> e;
         e.pid = 0;
-        e.x = e.k = e.w = (T)0;
+#pragma unroll
+        for (int d = 0; d < P::D; ++d) e.x.c[d] = e.k.c[d] = (T)0;
+        e.w = (T)0;
         e.l = p.L;
         if (act) e = p.fq_in[(long long)sg * p.qseg + i];
         flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
@@ -844,7 +1057,10 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
     for (unsigned long long base = g * 32ull; base < n; base += nwarps * 32ull) {
       const unsigned long long slot = base + lane;
       const bool act = slot < n;
-      T x = (T)0, k = (T)0, w = (T)0;
+      PV<P> x, k;
+#pragma unroll
+      for (int d = 0; d < P::D; ++d) x.c[d] = k.c[d] = (T)0;
+      T w = (T)0;
       unsigned long long pid = 0;
       int inst = 0;
       if constexpr (SRC == SRC_REGEN) {
@@ -869,29 +1085,47 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
             inst = (int)((unsigned)cell / (unsigned)p.nhi);
             cell -= inst * p.nhi;
           }
-          int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
-          if (p.nh_big) ix = cell / p.nk;
-          int ik = cell - ix * p.nk;
-          if (ik < 0) { --ix; ik += p.nk; } else if (ik >= p.nk) { ++ix; ik -= p.nk; }
           pid = p.regen_base | slot;
           if (p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | (slot - p.inst_slot[inst]);
           const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
-          T ux, uk;
-          if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
-          else { ux = (T)u24(r.x); uk = (T)u24(r.y); }
-          x = P::add(p.xmin, P::mul(P::add((T)ix, ux), p.dx));
-          k = P::add(p.kmin, P::mul(P::add((T)ik, uk), p.dk));
-          // move by single ulps back into the cell if rounding left it
-          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) > (T)ix; ++it) x = P::next_dn(x);
-          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(x, p.xmin), p.inv_dx)) < (T)ix; ++it) x = P::next_up(x);
-          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) > (T)ik; ++it) k = P::next_dn(k);
-          for (int it = 0; it < 8 && P::flr(P::mul(P::sub(k, p.kmin), p.inv_dk)) < (T)ik; ++it) k = P::next_up(k);
+          if constexpr (P::D == 1) {
+            int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
+            if (p.nh_big) ix = cell / p.nk;
+            int ik = cell - ix * p.nk;
+            if (ik < 0) { --ix; ik += p.nk; } else if (ik >= p.nk) { ++ix; ik -= p.nk; }
+            T ux, uk;
+            if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
+            else { ux = (T)u24(r.x); uk = (T)u24(r.y); }
+            x.c[0] = in_cell<P>(P::add(p.xmin, P::mul(P::add((T)ix, ux), p.dx)), p.xmin, p.inv_dx, ix);
+            k.c[0] = in_cell<P>(P::add(p.kmin, P::mul(P::add((T)ik, uk), p.dk)), p.kmin, p.inv_dk, ik);
+          } else {
+            // cell = ((ix1 nx + ix2) nk + ik1) nk + ik2; x offsets from the
+            // draw (pid, REGEN, 0), k offsets from (pid, REGEN, 1) in FP64,
+            // all four from the first draw in FP32
+            const int ik2 = cell % p.nk, c1 = cell / p.nk;
+            const int ik1 = c1 % p.nk, c2 = c1 / p.nk;
+            const int ix2 = c2 % p.nx, ix1 = c2 / p.nx;
+            T u[4];
+            if constexpr (P::is64) {
+              const uint4 r2 = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 1u);
+              u[0] = u53(r.x, r.y); u[1] = u53(r.z, r.w); u[2] = u53(r2.x, r2.y); u[3] = u53(r2.z, r2.w);
+            } else {
+              u[0] = u24(r.x); u[1] = u24(r.y); u[2] = u24(r.z); u[3] = u24(r.w);
+            }
+            x.c[0] = in_cell<P>(P::add(p.xmin, P::mul(P::add((T)ix1, u[0]), p.dx)), p.xmin, p.inv_dx, ix1);
+            x.c[P::D - 1] = in_cell<P>(P::add(p.xmin, P::mul(P::add((T)ix2, u[1]), p.dx)), p.xmin, p.inv_dx, ix2);
+            k.c[0] = in_cell<P>(P::add(p.kmin, P::mul(P::add((T)ik1, u[2]), p.dk)), p.kmin, p.inv_dk, ik1);
+            k.c[P::D - 1] = in_cell<P>(P::add(p.kmin, P::mul(P::add((T)ik2, u[3]), p.dk)), p.kmin, p.inv_dk, ik2);
+          }
           w = (cwl >> 31) ? (T)-1 : (T)1;
         }
       } else {
         if (act) {
-          x = p.x[slot];
-          k = p.k[slot];
+#pragma unroll
+          for (int d = 0; d < P::D; ++d) {
+            x.c[d] = p.x[d * p.capacity + slot];
+            k.c[d] = p.k[d * p.capacity + slot];
+          }
           w = p.w ? p.w[slot] : (T)p.s[slot];
           if (slot < n_base) {
             pid = base_pid + slot;
@@ -960,7 +1194,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
     for (unsigned b = 0; b < n; b += 32) {
       const unsigned i = b + lane;
       if (i < n) {
-        const FEntry<T> e = p.eq[(long long)sg * p.eseg + i];
+        const FEntry<P> e = p.eq[(long long)sg * p.eseg + i];
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T>& ip = p.inst[inst];
         SEntry<P> s;
@@ -1064,23 +1298,29 @@ __global__ void __launch_bounds__(kBlock) k_init(const KP<P> p, const InitInst* 
     const InitInst g = ini[inst];
     const unsigned long long pid = ((unsigned long long)inst << 32) | (i - g.start);
     const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepInit, 0u);
-    T x, k;
-    if constexpr (P::is64) {
-      const double ua = u53(r.x, r.y), ub = u53(r.z, r.w);
-      const double rad = __dsqrt_rn(__dmul_rn(-2.0, log1p(-ua)));
-      const double th = __dmul_rn(6.283185307179586476925286766559, ub);
-      x = (T)__dadd_rn(g.x0, __dmul_rn(g.sx, __dmul_rn(rad, cos(th))));
-      k = (T)__dadd_rn(g.k0, __dmul_rn(g.sk, __dmul_rn(rad, sin(th))));
-    } else {
-      const float ua = u24(r.x), ub = u24(r.y);
-      const float rad = sqrtf(-2.0f * log1pf(-ua));
-      float sn, cs;
-      sincospif(2.0f * ub, &sn, &cs);
-      x = (T)(g.x0 + g.sx * (double)(rad * cs));
-      k = (T)(g.k0 + g.sk * (double)(rad * sn));
+#pragma unroll
+    for (int e = 0; e < P::D; ++e) {  // electron e of the 4D model: its own pair of draws
+      const double x0 = e == 0 ? g.x0 : g.x0b, k0 = e == 0 ? g.k0 : g.k0b;
+      T x, k;
+      if constexpr (P::is64) {
+        const uint4 q =
+            e == 0 ? r : philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepInit, (uint32_t)e);
+        const double ua = u53(q.x, q.y), ub = u53(q.z, q.w);
+        const double rad = __dsqrt_rn(__dmul_rn(-2.0, log1p(-ua)));
+        const double th = __dmul_rn(6.283185307179586476925286766559, ub);
+        x = (T)__dadd_rn(x0, __dmul_rn(g.sx, __dmul_rn(rad, cos(th))));
+        k = (T)__dadd_rn(k0, __dmul_rn(g.sk, __dmul_rn(rad, sin(th))));
+      } else {
+        const float ua = u24(e == 0 ? r.x : r.z), ub = u24(e == 0 ? r.y : r.w);
+        const float rad = sqrtf(-2.0f * log1pf(-ua));
+        float sn, cs;
+        sincospif(2.0f * ub, &sn, &cs);
+        x = (T)(x0 + g.sx * (double)(rad * cs));
+        k = (T)(k0 + g.sk * (double)(rad * sn));
+      }
+      p.x[e * p.capacity + i] = x;
+      p.k[e * p.capacity + i] = k;
     }
-    p.x[i] = x;
-    p.k[i] = k;
     p.s[i] = 1;
     if (p.w) p.w[i] = (T)1;
   }
@@ -1146,6 +1386,18 @@ KP<P> make_kp(const Ctx* c) {
   p.strategy = g.strategy;
   p.l0 = p.L = (int)c->step;
   p.len = 0;
+  for (int t = 0; t < 2; ++t) {
+    p.tab.xi[t] = (const T*)c->tab_xi[t];
+    p.tab.cdf[t] = (const T*)c->tab_cdf[t];
+    p.tab.Y[t] = c->tab_Y[t];
+    p.tab.inv_dy[t] = c->tab_inv_dy[t];
+    p.tab.gam[t] = c->tab_gam[t];
+  }
+  p.tab.xc = c->pot.xc;
+  p.tab.kap0 = (T)(-c->tab_K);
+  p.tab.dkap = (T)c->tab_dkap;
+  p.tab.ny = c->tab_ny;
+  p.tab.nkap = c->tab_nkap;
   p.regen_base = (unsigned long long)c->epoch << 40;
   p.x = (T*)c->buf.x;
   p.k = (T*)c->buf.k;
@@ -1154,12 +1406,12 @@ KP<P> make_kp(const Ctx* c) {
   p.capacity = c->buf.capacity;
   p.cpid = c->cpid;
   p.nseg = c->nseg;
-  p.fq_in = (FEntry<T>*)c->fq[0];
+  p.fq_in = (FEntry<P>*)c->fq[0];
   p.fcnt_in = c->fcnt[0];
-  p.fq_out = (FEntry<T>*)c->fq[1];
+  p.fq_out = (FEntry<P>*)c->fq[1];
   p.fcnt_out = c->fcnt[1];
   p.qseg = c->qseg;
-  p.eq = (FEntry<T>*)c->eq;
+  p.eq = (FEntry<P>*)c->eq;
   p.ecnt = c->ecnt;
   p.eseg = c->eseg;
   p.dq[0] = (SEntry<P>*)c->dq[0];
@@ -1237,22 +1489,62 @@ cudaError_t flight_src(Ctx* c, const KP<P>& p, int src) {
 
 template <class P>
 cudaError_t flight_any(Ctx* c, const KP<P>& p, int src, int dst) {
-  switch (dst) {
-    case DST_ARRAY: return flight_src<P, DST_ARRAY>(c, p, src);
-    case DST_BIN1: return flight_src<P, DST_BIN1>(c, p, src);
-    case DST_BIN2: return flight_src<P, DST_BIN2>(c, p, src);
-    default: return flight_src<P, DST_WSUM>(c, p, src);
+  if (dst == DST_ARRAY) return flight_src<P, DST_ARRAY>(c, p, src);
+  if (dst == DST_BIN1) return flight_src<P, DST_BIN1>(c, p, src);
+  if constexpr (P::D == 1) {  // weighted sinks: sp2 and its observables (2D only)
+    if (dst == DST_BIN2) return flight_src<P, DST_BIN2>(c, p, src);
+    return flight_src<P, DST_WSUM>(c, p, src);
   }
+  return cudaErrorNotSupported;
 }
 
 template <class P>
 cudaError_t events_any(Ctx* c, const KP<P>& p, int dst) {
-  switch (dst) {
-    case DST_ARRAY: return events<P, DST_ARRAY>(c, p);
-    case DST_BIN1: return events<P, DST_BIN1>(c, p);
-    case DST_BIN2: return events<P, DST_BIN2>(c, p);
-    default: return events<P, DST_WSUM>(c, p);
+  if (dst == DST_ARRAY) return events<P, DST_ARRAY>(c, p);
+  if (dst == DST_BIN1) return events<P, DST_BIN1>(c, p);
+  if constexpr (P::D == 1) {
+    if (dst == DST_BIN2) return events<P, DST_BIN2>(c, p);
+    return events<P, DST_WSUM>(c, p);
   }
+  return cudaErrorNotSupported;
+}
+
+// The kernel tables of the 4D model, one thread per row of either type.
+// Row i of type t: v_j = max(A_tj sin(2 y_i kappa_j), 0) for the cells j in
+// order, y_i = -Y_t + i dy_t, kappa_j = kap0 + (j + 1/2) dkappa; S_j = the
+// running sum of v; xi_i = S_last dkappa.  FP64 rows hold S, FP32 rows S/S_last
+// (a second pass).  The largest xi of each type goes to xmax[t] (positive
+// doubles order like their bit patterns).
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tab4(const double* A, int ny, int nkap,
+                                                 double Y0, double dy0, double Y1, double dy1,
+                                                 double kap0, double dkap, T* cdf0, T* cdf1,
+                                                 T* xi0, T* xi1, unsigned long long* xmax) {
+  const int row = blockIdx.x * kBlock + threadIdx.x;
+  if (row >= 2 * ny) return;
+  const int t = row / ny, i = row % ny;
+  const double* At = A + (long long)t * nkap;
+  const double y = __dadd_rn(-(t ? Y1 : Y0), __dmul_rn((double)i, t ? dy1 : dy0));
+  T* out = (t ? cdf1 : cdf0) + (long long)i * nkap;
+  double acc = 0.0;
+  for (int j = 0; j < nkap; ++j) {
+    const double kap = __dadd_rn(kap0, __dmul_rn(__dadd_rn((double)j, 0.5), dkap));
+    const double v = __dmul_rn(At[j], sin(__dmul_rn(__dmul_rn(2.0, y), kap)));
+    if (v > 0.0) acc = __dadd_rn(acc, v);
+    if constexpr (sizeof(T) == 8) out[j] = (T)acc;
+  }
+  const double xi = __dmul_rn(acc, dkap);
+  if constexpr (sizeof(T) == 4) {
+    double run = 0.0;
+    for (int j = 0; j < nkap; ++j) {
+      const double kap = __dadd_rn(kap0, __dmul_rn(__dadd_rn((double)j, 0.5), dkap));
+      const double v = __dmul_rn(At[j], sin(__dmul_rn(__dmul_rn(2.0, y), kap)));
+      if (v > 0.0) run = __dadd_rn(run, v);
+      out[j] = acc > 0.0 ? (T)(run / acc) : (T)0;
+    }
+  }
+  (t ? xi1 : xi0)[i] = (T)xi;
+  atomicMax(xmax + t, (unsigned long long)__double_as_longlong(xi));
 }
 
 template <class P>
@@ -1287,6 +1579,8 @@ struct DriverImpl {
       g.k0 = q.k0;
       g.sk = 1.0 / (2.0 * q.sx);
       g.start = q.start;
+      g.x0b = q.x0b;
+      g.k0b = q.k0b;
       ii[i] = g;
       is[i] = q.start;
       na[i] = (double)q.n_alpha;
@@ -1321,9 +1615,9 @@ struct DriverImpl {
     const int rounds = L > l0 ? L - l0 : 1;
     const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
     for (int r = 0; r < rounds; ++r) {
-      p.fq_in = (FEntry<typename P::T>*)c->fq[r & 1];
+      p.fq_in = (FEntry<P>*)c->fq[r & 1];
       p.fcnt_in = c->fcnt[r & 1];
-      p.fq_out = (FEntry<typename P::T>*)c->fq[(r + 1) & 1];
+      p.fq_out = (FEntry<P>*)c->fq[(r + 1) & 1];
       p.fcnt_out = c->fcnt[(r + 1) & 1];
       if ((e = launch_zero(c, c->ecnt, cnt_bytes)) != cudaSuccess) return e;
       if (r == 0) prof_begin(c);
@@ -1359,6 +1653,43 @@ struct DriverImpl {
     return flight<P, SRC_REGEN, DST_ARRAY>(c, p);
   }
 
+  // Build the 4D model's tables from A (host, 2 x nkap) into the scratch and
+  // return the largest xi of each type.
+  static cudaError_t tables(Ctx* c, const double* A_host, double* xmax_host) {
+    using T = typename P::T;
+    if constexpr (P::D == 2) {
+      cudaError_t e = cudaMemcpyAsync(c->tab_A, A_host, (size_t)2 * c->tab_nkap * sizeof(double),
+                                      cudaMemcpyHostToDevice, c->stream);
+      if (e != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(c->tab_xmax, 0, 2 * sizeof(unsigned long long), c->stream)) !=
+          cudaSuccess)
+        return e;
+      const int nrow = 2 * c->tab_ny;
+      k_tab4<T><<<(nrow + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
+          c->tab_A, c->tab_ny, c->tab_nkap, c->tab_Y[0], c->tab_dy[0], c->tab_Y[1],
+          c->tab_dy[1], -c->tab_K, c->tab_dkap, (T*)c->tab_cdf[0], (T*)c->tab_cdf[1],
+          (T*)c->tab_xi[0], (T*)c->tab_xi[1], c->tab_xmax);
+      c->launches++;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      unsigned long long m[2];
+      if ((e = cudaMemcpyAsync(m, c->tab_xmax, sizeof(m), cudaMemcpyDeviceToHost, c->stream)) !=
+          cudaSuccess)
+        return e;
+      if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+      for (int t = 0; t < 2; ++t) {
+        double v;
+        memcpy(&v, &m[t], sizeof(v));
+        xmax_host[t] = v;
+      }
+      return cudaSuccess;
+    } else {
+      (void)c;
+      (void)A_host;
+      (void)xmax_host;
+      return cudaErrorNotSupported;
+    }
+  }
+
   static cudaError_t pids(Ctx* c, unsigned long long* out, unsigned* inst_out) {
     KP<P> p = make_kp<P>(c);
     static const int occ = occupancy(k_pids<P>);
@@ -1368,7 +1699,8 @@ struct DriverImpl {
   }
 
   static const Driver* get() {
-    static const Driver d = {&init, &chunk, &bin, &materialize, &pids};
+    static const Driver d = {&init,   &chunk, &bin, &materialize, &pids, &tables,
+                             (int)sizeof(FEntry<P>), (int)sizeof(SEntry<P>)};
     return &d;
   }
 };

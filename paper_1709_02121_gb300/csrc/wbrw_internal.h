@@ -82,6 +82,7 @@ struct InstHost {
   double H, w, xc;             // potential
   double C, sig_k, gamma0, cacc, p_any;
   double x0, sx, k0;           // initial wavepacket
+  double x0b, k0b;             // 4D model: the second electron's packet
   long long n_init, n_alpha;
   unsigned long long start;    // first slot of its initial particles
 };
@@ -105,6 +106,14 @@ struct Ctx {
   unsigned* cinst;    // instance of each appended offspring (batches only)
   double* inst_na;    // N_alpha of each instance (device)
   double* inst_trans; // transmissions read-out (device)
+  // 4D model: kernel tables in the scratch (type 0: one-body, 1: interaction)
+  int dim;            // 2 or 4
+  int tab_ny, tab_nkap;
+  double tab_Y[2], tab_dy[2], tab_inv_dy[2], tab_gam[2], tab_K, tab_dkap;
+  double* tab_A;                  // staging of A_tj (2 x nkap)
+  void* tab_xi[2];                // ny values of type T
+  void* tab_cdf[2];               // ny x nkap values of type T
+  unsigned long long* tab_xmax;   // the largest xi of each type
   // scratch carve-up
   Counters* cnt;
   unsigned long long* cpid;
@@ -136,6 +145,7 @@ struct Ctx {
   int* tmp_grid;
   long long* tmp_wsum;
   double* obs_density;
+  long long* obs_red;   // dim 4: counts summed over (x2, k2), nx x nk
   double* obs_marg;
   long long* obs_col;
   double* obs_scalar;
@@ -184,10 +194,16 @@ struct Driver {
   // Regenerate the histogram into the arrays (Alg. 3).
   cudaError_t (*materialize)(Ctx*);
   cudaError_t (*pids)(Ctx*, unsigned long long* out, unsigned* inst_out);
+  // 4D model: build the kernel tables from A (host, 2 x nkap values) and
+  // return the largest xi of each type (synchronises).
+  cudaError_t (*tables)(Ctx*, const double* A_host, double* xmax_host);
+  int fentry_bytes, sentry_bytes;  // queue entry sizes of this model and precision
 };
 
 const Driver* driver_fp64();
 const Driver* driver_fp32();
+const Driver* driver_fp64_4d();
+const Driver* driver_fp32_4d();
 
 // Precision-independent launches (wbrw_common.cu).
 cudaError_t launch_setup(Ctx*, int op, unsigned long long a,

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libwbrw.so")
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NUMERIC = 0, -1, -2, -3, -4, -5, -6
 SP1_PAIR, SP2_BOOTSTRAP = 1, 2
 FP64, FP32 = 0, 1
-POT_GAUSSIAN = 0
+POT_GAUSSIAN, POT_SOFT_COULOMB_2E = 0, 1
 
 # counter slots (WBRW_C_*)
 COUNTERS = ("live", "events", "kill_plus", "kill_minus", "out_plus", "out_minus",
@@ -35,7 +35,8 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
-           "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune")
+           "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune",
+           "wbrw_init4d")
 TUNE_BPS_MAX, TUNE_PASSES_MAX = 3, 6
 MAX_INSTANCES = 256
 
@@ -50,12 +51,14 @@ class Config(ctypes.Structure):
                 ("kmin", ctypes.c_double), ("kmax", ctypes.c_double),
                 ("resample_every", ctypes.c_int),
                 ("n_alpha", ctypes.c_longlong),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong),
+                ("table_ny", ctypes.c_int), ("table_nkappa", ctypes.c_int)]
 
 
 class Potential(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("H", ctypes.c_double),
-                ("w", ctypes.c_double), ("xc", ctypes.c_double)]
+                ("w", ctypes.c_double), ("xc", ctypes.c_double),
+                ("ee", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):
@@ -81,7 +84,8 @@ class Buffers(ctypes.Structure):
 EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"), ("pid_minus", "<u8"),
                         ("step", "<u4"), ("j", "<u4"), ("t", "<f8"), ("xe", "<f8"),
                         ("kappa", "<f8"), ("factor", "<f8"), ("kill_plus", "<i4"),
-                        ("kill_minus", "<i4")])
+                        ("kill_minus", "<i4"), ("xe2", "<f8"), ("comp", "<i4"),
+                        ("pad", "<i4")])
 
 _lib = None
 
@@ -108,6 +112,10 @@ def load(path: str = LIB_PATH):
                             ctypes.POINTER(Buffers), LL, ctypes.c_double,
                             ctypes.c_double, ctypes.c_double, P,
                             ctypes.POINTER(P)]
+    L.wbrw_init4d.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Potential),
+                              ctypes.POINTER(Buffers), LL, P, ctypes.c_double, P, P,
+                              ctypes.POINTER(P)]
+    L.wbrw_init4d.restype = I
     L.wbrw_batch_scratch_bytes.argtypes = [ctypes.POINTER(Config), I, LL]
     L.wbrw_batch_scratch_bytes.restype = ctypes.c_size_t
     L.wbrw_batch_init.argtypes = [ctypes.POINTER(Config), I, ctypes.POINTER(Instance),
@@ -167,6 +175,17 @@ def wbrw_init(cfg, pot, bufs, n_init, x0, sigma_x, k0, stream_ptr):
                           ctypes.byref(ctx))
     if st != OK:
         raise WbrwError(st, "wbrw_init rejected its arguments")
+    return ctx
+
+
+def wbrw_init4d(cfg, pot, bufs, n_init, x0, sigma_x, k0, stream_ptr):
+    ctx = ctypes.c_void_p()
+    x0a = (ctypes.c_double * 2)(*x0)
+    k0a = (ctypes.c_double * 2)(*k0)
+    st = load().wbrw_init4d(ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(bufs), n_init,
+                            x0a, sigma_x, k0a, ctypes.c_void_p(stream_ptr), ctypes.byref(ctx))
+    if st != OK:
+        raise WbrwError(st, "wbrw_init4d rejected its arguments")
     return ctx
 
 
@@ -331,21 +350,26 @@ class Simulation:
         self.wl = dict(wl)
         prec = FP64 if wl["precision"] == "fp64" else FP32
         strat = SP1_PAIR if wl["strategy"] == "sp1" else SP2_BOOTSTRAP
-        self.cfg = Config(2, prec, strat, wl["hbar"], wl["mass"], wl["dt"], wl["gamma0"],
+        self.dim = int(wl.get("dim", 2))
+        self.cfg = Config(self.dim, prec, strat, wl["hbar"], wl["mass"], wl["dt"], wl["gamma0"],
                           wl["nx"], wl["nk"], wl["xmin"], wl["xmax"], wl["kmin"], wl["kmax"],
-                          wl["resample_every"], int(wl["n_alpha"]), int(wl["seed"]))
+                          wl["resample_every"], int(wl["n_alpha"]), int(wl["seed"]),
+                          int(wl.get("ny", 0)), int(wl.get("nkap", 0)))
         dev = torch.device("cuda", torch.cuda.current_device())
         fdt = torch.float64 if prec == FP64 else torch.float32
         self.nx, self.nk = wl["nx"], wl["nk"]
         self.capacity = int(capacity)
-        self.x = torch.empty(self.capacity, dtype=fdt, device=dev)
-        self.k = torch.empty(self.capacity, dtype=fdt, device=dev)
+        nd = 2 if self.dim == 4 else 1   # coordinates per particle
+        self.x = torch.empty(nd * self.capacity, dtype=fdt, device=dev)
+        self.k = torch.empty(nd * self.capacity, dtype=fdt, device=dev)
         self.s = torch.empty(self.capacity, dtype=torch.int8, device=dev)
         self.w = torch.empty(self.capacity, dtype=fdt, device=dev) if strat == SP2_BOOTSTRAP else None
-        cells = self.ninst * self.nx * self.nk
+        self.cells = (self.nx * self.nx * self.nk * self.nk if self.dim == 4
+                      else self.nx * self.nk)
+        cells = self.ninst * self.cells
         self.grid = torch.zeros(cells, dtype=torch.int32, device=dev)
-        nbytes = (wbrw_scratch_bytes(self.cfg, self.capacity) if type(self) is Simulation
-                  else wbrw_batch_scratch_bytes(self.cfg, self.ninst, self.capacity))
+        nbytes = (wbrw_batch_scratch_bytes(self.cfg, self.ninst, self.capacity)
+                  if isinstance(self, Batch) else wbrw_scratch_bytes(self.cfg, self.capacity))
         if nbytes == 0:
             raise ValueError("invalid configuration")
         self.scratch = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -484,3 +508,41 @@ class Batch(Simulation):
         t = self.torch.empty(max(len(x), 1), dtype=self.torch.int32, device=self.x.device)
         wbrw_particle_instances(self.ctx, t.data_ptr())
         return x, k, s, w, pid, t[: len(x)].cpu().numpy().view(np.uint32)
+
+
+class Simulation4(Simulation):
+    """The 4D Helium-like system: two electrons (x1, x2, k1, k2) around a
+    nucleus, soft-Coulomb one-body terms of charge Z and an interaction of
+    strength ee, softening a (workloads.HE_4D_*)."""
+
+    def __init__(self, wl: dict, capacity: int, *, event_log: int = 0, stream=None):
+        wl = dict(wl, dim=4)
+        self._buffers(wl, capacity, event_log, stream)
+        self.pot = Potential(POT_SOFT_COULOMB_2E, wl["Z"], wl["a"], wl["xc"], wl["lam"])
+        self.ctx = wbrw_init4d(self.cfg, self.pot, self.bufs, int(wl["n_alpha"]),
+                               tuple(wl["x0"]), wl["sigma_x"], tuple(wl["k0"]),
+                               self.stream.cuda_stream)
+
+    def particles(self, with_pids=True):
+        """(x1, x2, k1, k2, s, pid) of the current particles as host arrays."""
+        torch = self.torch
+        n = wbrw_particles(self.ctx)
+        pid = None
+        if with_pids:
+            pid_t = torch.empty(max(n, 1), dtype=torch.int64, device=self.x.device)
+            wbrw_particles(self.ctx, pid_t.data_ptr())
+            pid = pid_t[:n].cpu().numpy().view(np.uint64)
+        c = self.capacity
+        x1, x2 = self.x[:n].cpu().numpy(), self.x[c:c + n].cpu().numpy()
+        k1, k2 = self.k[:n].cpu().numpy(), self.k[c:c + n].cpu().numpy()
+        s = self.s[:n].cpu().numpy()
+        return x1, x2, k1, k2, s, pid
+
+    def grid_counts(self):
+        self.stream.synchronize()
+        return self.grid.view(self.nx, self.nx, self.nk, self.nk).cpu().numpy()
+
+    def checkpoint(self, grid_out=None):
+        if grid_out is None:
+            grid_out = np.empty((self.nx, self.nx, self.nk, self.nk), np.int32)
+        return super().checkpoint(grid_out)

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "wbrw.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(wbrw_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(wbrw_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +60,10 @@ def test_scratch_bytes_and_argument_checks(lib):
     assert wbrw.wbrw_scratch_bytes(_cfg(dt=-1.0), 10) == 0
     assert wbrw.wbrw_scratch_bytes(_cfg(xmax=-60.0), 10) == 0
     bad = _cfg()
-    bad.dim = 4
+    bad.dim = 3
+    assert wbrw.wbrw_scratch_bytes(bad, 10) == 0
+    bad = _cfg(nx=300)
+    bad.dim = 4                                   # 300^2 128^2 cells >= 2^30
     assert wbrw.wbrw_scratch_bytes(bad, 10) == 0
 
 
@@ -89,3 +92,18 @@ def test_product_path_has_no_fallback(tmp_path):
             wbrw.load(str(tmp_path / "missing.so"))
         finally:
             wbrw._lib = saved
+
+
+def test_dim4_scratch_holds_the_kernel_tables(lib):
+    from paper_1709_02121_gb300 import wbrw
+    c = _cfg(precision="fp32", nx=16, nk=16)
+    c.dim = 4
+    n = wbrw.wbrw_scratch_bytes(c, 100000)
+    c.table_ny, c.table_nkappa = 1024, 512
+    m = wbrw.wbrw_scratch_bytes(c, 100000)
+    # default tables 4096 x 2048 of float, two types
+    assert n - m >= 2 * 4 * (4096 * 2048 - 1024 * 512)
+    c.strategy = 2
+    assert wbrw.wbrw_scratch_bytes(c, 100000) == 0     # dim 4 is sp1 only
+    c.strategy, c.table_ny = 1, 1
+    assert wbrw.wbrw_scratch_bytes(c, 100000) == 0     # a table needs two rows

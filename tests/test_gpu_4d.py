@@ -1,0 +1,160 @@
+"""GPU parity of the 4D Helium-like system (two electrons, M = 3 kernels).
+
+FP64: the same counter-based streams and the same operation order as the 4D
+oracle, on kernel tables each side builds from the definition (Eq. 2 with
+Uhat = 2 K0(a|q|); K0 from a library routine here, from its integral
+representation in the oracle).  Ids, event logs (component, kill flags),
+ledgers and integer cell counts agree exactly; positions, kicks, times and
+acceptance probabilities to 1e-12 relative.  FP32: the production streams,
+checked in law against the two-electron Schroedinger equation.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from helpers import make_oracle4
+from oracle import refs
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+# 16^4 cells: 32 full scan tiles of 2048; 3100 particles: a ragged last warp
+WL = workloads.scaled(workloads.HE_4D_FP32_5E7, precision="fp64", n_alpha=3100, nx=16, nk=16,
+                      resample_every=5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_02121_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def sim_of(wl, capacity=600_000, event_log=0, stream=None):
+    from paper_1709_02121_gb300 import Simulation4
+    return Simulation4(wl, capacity, event_log=event_log, stream=stream)
+
+
+def oracle_of(wl, log=False):
+    o = make_oracle4(wl)
+    o.init_gauss(wl["n_alpha"], wl["x0"], wl["sigma_x"], wl["k0"])
+    if log:
+        o.enable_log()
+    return o
+
+
+def close(a, b):
+    return np.all(np.abs(a - b) <= REL * np.maximum(1.0, np.abs(b)))
+
+
+def assert_same_particles(sim, o):
+    x1, x2, k1, k2, s, pid = sim.particles()
+    ox1, ox2, ok1, ok2, ow, opid = o.particles()
+    assert len(pid) == len(opid)
+    a, b = np.argsort(pid, kind="stable"), np.argsort(opid, kind="stable")
+    assert np.array_equal(pid[a], opid[b])
+    for g, r in ((x1, ox1), (x2, ox2), (k1, ok1), (k2, ok2)):
+        assert close(g[a], r[b])
+    assert np.array_equal(s[a].astype(np.float64), ow[b])
+
+
+def assert_same_log(glog, olog):
+    assert len(glog) == len(olog)
+    kg = np.lexsort((glog["j"], glog["pid"], glog["step"]))
+    ko = np.lexsort((olog["j"], olog["pid"], olog["step"]))
+    g, o = glog[kg], olog[ko]
+    for f in ("pid", "pid_plus", "pid_minus", "step", "j", "kill_plus", "kill_minus", "comp"):
+        assert np.array_equal(g[f], o[f]), f
+    for f in ("t", "xe", "xe2", "kappa", "factor"):
+        assert close(g[f], o[f]), f
+
+
+def assert_same_ledger(sim, o):
+    c, led = sim.counters(), o.ledger()
+    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps"):
+        assert c[key] == led[key], (key, c[key], led[key])
+
+
+def test_initial_sampling_matches_oracle():
+    sim, o = sim_of(WL), oracle_of(WL)
+    x1, x2, k1, k2, s, pid = sim.particles()
+    ox1, ox2, ok1, ok2, ow, opid = o.particles()
+    assert np.array_equal(pid, opid) and np.all(s == 1)
+    for g, r in ((x1, ox1), (x2, ox2), (k1, ok1), (k2, ok2)):
+        assert np.max(np.abs(g - r)) <= 1e-13
+
+
+@pytest.mark.parametrize("steps", [1, 6])
+def test_steps_match_oracle(steps):
+    wl = workloads.scaled(WL, kmin=-1.6, kmax=1.6)   # a narrow K: offspring get killed
+    sim, o = sim_of(wl, event_log=400_000), oracle_of(wl, log=True)
+    sim.step(steps)
+    o.step(steps)
+    assert_same_particles(sim, o)
+    glog, olog = sim.event_log(), o.event_log()
+    assert_same_log(glog, olog)
+    assert set(np.unique(glog["comp"])) == {0, 1, 2}
+    assert_same_ledger(sim, o)
+    c = sim.counters()
+    assert c["kill_plus"] + c["kill_minus"] > 0
+
+
+def test_fused_schedule_and_observables_match_oracle():
+    sim, o = sim_of(WL), oracle_of(WL)
+    for period in range(3):
+        sim.run(5)
+        o.step(5)
+        o.annihilate()
+        assert np.array_equal(sim.grid_counts(), o.grid()), period
+    assert_same_ledger(sim, o)
+    dens, marg, T, live = sim.density()
+    of1, omarg, oT = o.observables(o.grid())
+    assert np.array_equal(dens, of1) and np.array_equal(marg, omarg) and T == oT
+    assert live == o.n
+    # the regenerated particles themselves, after two more steps
+    sim.run(2)
+    o.step(2)
+    assert_same_particles(sim, o)
+
+
+def test_replays_and_launch_shapes_do_not_change_results(gpu):
+    wl = workloads.scaled(WL, precision="fp32", n_alpha=20000)
+    ref = sim_of(wl)
+    ref.run(15)
+    g = sim_of(wl, stream=gpu.cuda.Stream())
+    g.graph(True)
+    g.tuning(2, 0)
+    g.run(15)
+    assert np.array_equal(ref.grid_counts(), g.grid_counts())
+    assert ref.counters()["events"] == g.counters()["events"]
+
+
+def test_fp32_matches_the_two_electron_schroedinger_equation():
+    # pure branching to t = 0.4 (20 steps, no resampling) in FP32: electron
+    # 1's position density against the split-step TDSE, within the Monte
+    # Carlo error of 8 independent runs
+    edges = np.linspace(-5.0, 3.0, 9)
+    V = refs.soft_coulomb_2e(2.0, 1.0, 1.0)
+    x, r1, r2 = refs.tdse2_marginals(V, WL["x0"], WL["sigma_x"], WL["k0"], 0.4)
+    ref1 = refs.bin_density(x, r1, edges)
+    ref2 = refs.bin_density(x, r2, edges)
+    n = 200_000
+    c1, c2 = [], []
+    for seed in range(8):
+        wl = workloads.scaled(WL, precision="fp32", n_alpha=n, seed=seed, nx=64, nk=64,
+                              resample_every=0)
+        sim = sim_of(wl, capacity=8 * n)
+        sim.step(20)
+        x1, x2, k1, k2, s, _ = sim.particles(with_pids=False)
+        w = s.astype(np.float64)   # (int8 weights would overflow in the histogram)
+        c1.append(np.histogram(x1, bins=edges, weights=w)[0] / n)
+        c2.append(np.histogram(x2, bins=edges, weights=w)[0] / n)
+    for cells, ref in ((np.array(c1), ref1), (np.array(c2), ref2)):
+        m, se = cells.mean(0), cells.std(0, ddof=1) / np.sqrt(len(cells))
+        z = (m - ref) / np.sqrt(se ** 2 + 1e-8)
+        assert np.max(np.abs(z)) < 4.5, np.round(z, 2)
+        assert np.mean(z ** 2) < 3.0, np.round(z, 2)
