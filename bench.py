@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2"])
     ap.add_argument("--workload", default="gauss2d_fp32_n1e8",
-                    choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5", "batch2d_fp32_256"])
+                    choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5", "batch2d_fp32_256",
+                             "he4d_fp32_n5e7"])
     ap.add_argument("--n-scale", type=float, default=1.0,
                     help="batched workload: scale every instance's particle count")
     ap.add_argument("--no-plain", action="store_true",
@@ -66,6 +67,11 @@ def parse():
 def workload(args):
     if args.workload == "batch2d_fp32_256":
         return workloads.scaled(workloads.BATCH_2D_FP32_256)
+    if args.workload == "he4d_fp32_n5e7":
+        wl = workloads.scaled(workloads.HE_4D_FP32_5E7)
+        if args.particles:
+            wl["n_alpha"] = int(args.particles)
+        return wl
     base = (workloads.GAUSS_2D_FP32_1E8 if args.workload == "gauss2d_fp32_n1e8"
             else workloads.GAUSS_2D_FP64_2E5)
     wl = workloads.scaled(base, strategy=args.strategy)
@@ -141,11 +147,17 @@ def oracle_period_rate(wl, n_sample, budget_s, max_periods=None):
     n_sample initial particles, full periods until budget_s has elapsed."""
     import oracle
     oracle.build()
-    o = oracle.Oracle(hbar=wl["hbar"], mass=wl["mass"], dt=wl["dt"], gamma0=wl["gamma0"],
-                      H=wl["H"], w=wl["w"], xc=wl["xc"], nx=wl["nx"], nk=wl["nk"],
-                      xmin=wl["xmin"], xmax=wl["xmax"], kmin=wl["kmin"], kmax=wl["kmax"],
-                      strategy=oracle.SP1 if wl["strategy"] == "sp1" else oracle.SP2,
-                      n_alpha=n_sample, seed=wl["seed"])
+    if wl.get("dim", 2) == 4:
+        o = oracle.Oracle4(hbar=wl["hbar"], mass=wl["mass"], dt=wl["dt"], Z=wl["Z"], a=wl["a"],
+                           xc=wl["xc"], lam=wl["lam"], nx=wl["nx"], nk=wl["nk"],
+                           xmin=wl["xmin"], xmax=wl["xmax"], kmin=wl["kmin"], kmax=wl["kmax"],
+                           ny=wl["ny"], nkap=wl["nkap"], n_alpha=n_sample, seed=wl["seed"])
+    else:
+        o = oracle.Oracle(hbar=wl["hbar"], mass=wl["mass"], dt=wl["dt"], gamma0=wl["gamma0"],
+                          H=wl["H"], w=wl["w"], xc=wl["xc"], nx=wl["nx"], nk=wl["nk"],
+                          xmin=wl["xmin"], xmax=wl["xmax"], kmin=wl["kmin"], kmax=wl["kmax"],
+                          strategy=oracle.SP1 if wl["strategy"] == "sp1" else oracle.SP2,
+                          n_alpha=n_sample, seed=wl["seed"])
     o.init_gauss(n_sample, wl["x0"], wl["sigma_x"], wl["k0"])
     times, psteps = [], []
     t_all = time.perf_counter()
@@ -187,10 +199,15 @@ def reference_arm(args, wl):
 
 
 def config_of(wl, args):
-    return {"workload": wl["name"], "particles": int(wl["n_alpha"]),
-            "grid": [wl["nx"], wl["nk"]], "dt": wl["dt"],
+    d4 = wl.get("dim", 2) == 4
+    pot = ("soft-Coulomb Z=%g a=%g ee=%g, tables %dx%d" % (wl["Z"], wl["a"], wl["lam"], wl["ny"],
+                                                          wl["nkap"])
+           if d4 else "gaussian H=%g w=%g" % (wl["H"], wl["w"]))
+    return {"workload": wl["name"], "dim": 4 if d4 else 2, "particles": int(wl["n_alpha"]),
+            "grid": [wl["nx"]] * (2 if d4 else 1) + [wl["nk"]] * (2 if d4 else 1),
+            "dt": wl["dt"],
             "intervals_per_step": wl["resample_every"], "strategy": wl["strategy"],
-            "precision": wl["precision"], "potential": "gaussian H=%g w=%g" % (wl["H"], wl["w"]),
+            "precision": wl["precision"], "potential": pot,
             "l2": "flushed (512 MiB write) between timed steps",
             "cuda_graphs": not args.no_graph and wl["strategy"] == "sp1",
             "parallelism": "replicas x%d" % args.gpus}
@@ -210,12 +227,13 @@ def ours(args, wl):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1709_02121_gb300 import build
     build.build()
-    from paper_1709_02121_gb300 import Simulation, wbrw
+    from paper_1709_02121_gb300 import Simulation, Simulation4, wbrw
 
     wl = workloads.scaled(wl, seed=wl["seed"] + rank)
     n = int(wl["n_alpha"])
     cap = int(args.capacity_factor * n) + (1 << 20)
-    sim = Simulation(wl, capacity=cap, stream=torch.cuda.Stream())
+    model = Simulation4 if wl.get("dim", 2) == 4 else Simulation
+    sim = model(wl, capacity=cap, stream=torch.cuda.Stream())
     stream = sim.stream
     graphs = not args.no_graph and wl["strategy"] == "sp1"
     if graphs:
@@ -258,7 +276,7 @@ def ours(args, wl):
     # ---- end to end: host checkpoint in, one period, checkpoint + observables out
     e2e = None
     if not args.no_e2e:
-        grid_h = torch.empty((wl["nx"], wl["nk"]), dtype=torch.int32).pin_memory()
+        grid_h = torch.empty(sim.grid_counts().shape, dtype=torch.int32).pin_memory()
         g0, step0, epoch0 = sim.checkpoint(grid_h.numpy())
         e2e_steps = min(args.steps, 10)
         barrier()
@@ -273,8 +291,8 @@ def ours(args, wl):
         te = time.perf_counter() - t0
         pe = sim.counters()["particle_steps"] - pe0
         e2e = {"value": pe / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(wl["nx"] * wl["nk"] * 4),
-               "d2h_bytes_per_step": int(wl["nx"] * wl["nk"] * 4 + wl["nx"] * wl["nk"] * 8
+               "h2d_bytes_per_step": int(sim.cells * 4),
+               "d2h_bytes_per_step": int(sim.cells * 4 + wl["nx"] * wl["nk"] * 8
                                          + wl["nx"] * 8 + 16),
                "steps": e2e_steps, "transmission_last": T_last}
 
@@ -528,15 +546,17 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
     timed region (one integer operation per lane per cycle)."""
     if not kern_n or kern_ms <= 0:
         return None
-    ops = INT_OPS_PER_PSTEP[wl["precision"]]
+    key = wl["precision"] + ("_4d" if wl.get("dim", 2) == 4 else "")
+    ops = INT_OPS_PER_PSTEP[wl["precision"] + ("_4d" if wl.get("dim", 2) == 4 else "")]
     per_launch_ms = kern_ms / kern_n
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak = 152 * 64 * sm_mhz * 1e6 / 1e9
     ach = ops * (psteps_first / kern_n) / (per_launch_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
-            "frac": ach / peak, "traffic": TRAFFIC_PER_PSTEP.get(wl["precision"]) and
-            TRAFFIC_PER_PSTEP[wl["precision"]] * psteps_first / kern_n,
-            "kernel": "k_flight<%s,regen,bin>" % wl["precision"],
+            "frac": ach / peak, "traffic": TRAFFIC_PER_PSTEP.get(key) and
+            TRAFFIC_PER_PSTEP[key] * psteps_first / kern_n,
+            "kernel": "k_flight<%s%s,regen,bin>" % (wl["precision"],
+                                                     ",4d" if wl.get("dim", 2) == 4 else ""),
             "launch_ms": per_launch_ms, "launches": kern_n,
             "first_wave_particle_steps_per_launch": psteps_first / kern_n,
             "int_ops_per_particle_step": ops,
@@ -548,9 +568,9 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
 # ("Roofline of the first wave"): three Philox4x32-10 calls per
 # particle per period at 100 operations each, the coin tests, the cell decode
 # of the regeneration and the histogram index.
-INT_OPS_PER_PSTEP = {"fp32": 33.6, "fp64": 63.0}
+INT_OPS_PER_PSTEP = {"fp32": 33.6, "fp64": 63.0, "fp32_4d": 36.0, "fp64_4d": 73.0}
 # DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
-TRAFFIC_PER_PSTEP = {"fp32": 0.83, "fp64": None}
+TRAFFIC_PER_PSTEP = {"fp32": 0.83, "fp64": None, "fp32_4d": 1.57, "fp64_4d": None}
 
 
 def main():
