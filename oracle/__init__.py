@@ -71,7 +71,8 @@ class _Config(ctypes.Structure):
                 ("strategy", ctypes.c_int),
                 ("n_alpha", ctypes.c_longlong),
                 ("seed", ctypes.c_ulonglong),
-                ("instance", ctypes.c_int)]
+                ("instance", ctypes.c_int),
+                ("tangent", ctypes.c_int), ("tquantum", ctypes.c_longlong)]
 
 
 EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"),
@@ -150,6 +151,10 @@ def lib():
         L.orc_event_size.restype = LL
         L.orc_event_outcome.argtypes = [P, ctypes.c_uint64, U32, U32, D,
                                         P, P, P]
+        L.orc_get_tangent.argtypes = [P, P, P]
+        L.orc_get_dgrid.argtypes = [P, P, P]
+        L.orc_get_tkill.argtypes = [P, P]
+        L.orc_tangent_transmission.argtypes = [P, P]
         assert L.orc_event_size() == EVENT_DTYPE.itemsize
         L.orc4_k0.argtypes = [D]
         L.orc4_k0.restype = D
@@ -215,9 +220,10 @@ class Oracle:
     def __init__(self, *, hbar=1.0, mass=1.0, dt=0.1, gamma0=0.0, H=1.0,
                  w=1.0, xc=0.0, nx=240, nk=128, xmin=-60.0, xmax=60.0,
                  kmin=-6.4, kmax=6.4, strategy=SP1, n_alpha=200000, seed=0,
-                 instance=0):
+                 instance=0, tangent=False, tquantum=1.0):
         self.cfg = _Config(hbar, mass, dt, gamma0, H, w, xc, nx, nk, xmin,
-                           xmax, kmin, kmax, strategy, n_alpha, seed, instance)
+                           xmax, kmin, kmax, strategy, n_alpha, seed, instance,
+                           1 if tangent else 0, int(round(tquantum * 2.0 ** 32)))
         self.nx, self.nk = nx, nk
         self.n_alpha = n_alpha
         self._s = lib().orc_create(ctypes.byref(self.cfg))
@@ -294,6 +300,32 @@ class Oracle:
         g = np.empty(self.nx * self.nk, np.int32)
         lib().orc_get_grid(self._s, _ptr(g))
         return g.reshape(self.nx, self.nk)
+
+    # ---- tangent mode (likelihood-ratio derivatives in H and w) -----------
+    def tangent(self):
+        """(tau_H, tau_w) of the current particles."""
+        n = self.n
+        tH, tw = np.empty(n), np.empty(n)
+        lib().orc_get_tangent(self._s, _ptr(tH), _ptr(tw))
+        return tH, tw
+
+    def dgrid(self):
+        """The tangent histogram (D_H, D_w) of the last resampling, 2^-32 units."""
+        dH = np.empty(self.nx * self.nk, np.int64)
+        dw = np.empty(self.nx * self.nk, np.int64)
+        lib().orc_get_dgrid(self._s, _ptr(dH), _ptr(dw))
+        return dH.reshape(self.nx, self.nk), dw.reshape(self.nx, self.nk)
+
+    def tangent_killed(self):
+        out = np.zeros(2)
+        lib().orc_get_tkill(self._s, _ptr(out))
+        return out
+
+    def transmission_gradient(self):
+        """(dT/dH, dT/dw) from the tangent histogram of the last resampling."""
+        out = np.zeros(2)
+        lib().orc_tangent_transmission(self._s, _ptr(out))
+        return out
 
     def histogram(self):
         """Signed counts and FP64 weight sums of the current particles."""

@@ -135,11 +135,15 @@ typedef struct {
   long long n_alpha;             /* sample size N_alpha of the estimator     */
   unsigned long long seed;
   int instance;                  /* id salt 0..255: a run as instance i of a batch */
+  int tangent;                   /* sp1: carry the tangent weights (H, w)   */
+  long long tquantum;            /* tangent particles: |tau| <= this / 2^32 */
 } orc_config;
 
 typedef struct {
-  double x, k, w; /* position, wavevector, signed weight (sp1: +-1)          */
+  double x, k, w; /* position, wavevector, signed weight (sp1: +-1, 0 for a  */
+                  /* particle that only carries tangent weight)              */
   uint64_t pid;   /* counter-stream id                                       */
+  double tH, tw;  /* tangent weights d/dH and d/dw (tangent mode)            */
 } orc_particle;
 
 typedef struct {
@@ -180,6 +184,8 @@ typedef struct {
   long long boot_n[2], boot_keep[2], boot_nr[2];
   unsigned long long boot_wfix[2];
   long long* boot_cnt[2]; /* n~_nu^+ and n~_nu^- of the last filter        */
+  long long* dgrid[2];    /* tangent histogram D_nu (H, w) in units of 2^-32 */
+  double tkill[2];        /* tangent weight of killed offspring, (H, w)      */
 } orc_state;
 
 static void draw4(const orc_state* s, uint64_t pid, uint32_t c2, uint32_t c3,
@@ -206,6 +212,7 @@ orc_state* orc_create(const orc_config* c) {
       !(c->kmax > c->kmin) || c->dt <= 0 || c->hbar <= 0 || c->mass <= 0 ||
       (c->strategy != 1 && c->strategy != 2) || c->n_alpha <= 0 || c->w <= 0)
     return NULL;
+  if (c->tangent && (c->strategy != 1 || c->H == 0.0 || c->tquantum <= 0)) return NULL;
   orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
   s->c = *c;
   s->C = 2.0 * fabs(c->H) / c->hbar;          /* int |Vhat(2k)| (2/(pi hbar)) dk */
@@ -222,6 +229,9 @@ orc_state* orc_create(const orc_config* c) {
   s->key[0] = (uint32_t)c->seed;
   s->key[1] = (uint32_t)(c->seed >> 32);
   s->grid = (int*)calloc((size_t)c->nx * (size_t)c->nk, sizeof(int));
+  if (c->tangent)
+    for (int d = 0; d < 2; ++d)
+      s->dgrid[d] = (long long*)calloc((size_t)c->nx * (size_t)c->nk, sizeof(long long));
   return s;
 }
 
@@ -233,6 +243,8 @@ void orc_destroy(orc_state* s) {
   free(s->log);
   free(s->boot_cnt[0]);
   free(s->boot_cnt[1]);
+  free(s->dgrid[0]);
+  free(s->dgrid[1]);
   free(s);
 }
 
@@ -265,6 +277,7 @@ int orc_init_gauss(orc_state* s, long long n, double x0, double sx,
     p.k = k0 + sk * (rad * sin(th));
     p.w = 1.0;
     p.pid = pid0;
+    p.tH = p.tw = 0.0;
     if (push(&s->p, &s->n, &s->cap, p)) return -1;
   }
   s->step = 0;
@@ -279,7 +292,7 @@ int orc_set_particles(orc_state* s, long long n, const double* x,
                       long long step) {
   s->n = 0;
   for (long long i = 0; i < n; ++i) {
-    orc_particle p = {x[i], k[i], w[i], pid[i]};
+    orc_particle p = {x[i], k[i], w[i], pid[i], 0.0, 0.0};
     if (push(&s->p, &s->n, &s->cap, p)) return -1;
   }
   s->step = step;
@@ -310,8 +323,19 @@ int orc_set_particles(orc_state* s, long long n, const double* x,
 /* Surviving offspring continue the same interval from their birth time.     */
 /* ------------------------------------------------------------------------ */
 
+/* Tangent mode (sp1, theta = (H, w)): each particle also carries a tangent
+ * weight tau = s S, its sign s times the likelihood-ratio score S of its
+ * lineage.  The expected particle measure is a sum over lineages of products
+ * of the birth intensities V_W^+(x_b, kappa_b) (the parent survives every
+ * birth, so no survival factor enters), hence the score of a lineage is the
+ * sum over its births of g = d/dtheta log V_W^+(x_b, kappa_b; theta) =
+ * (1/H, 1/w - 4 w kappa^2) for the Gaussian barrier (Eq. 2 with
+ * Vhat(2 kappa) = H w sqrt(2 pi) exp(-2 w^2 kappa^2)).  A birth from (s, tau)
+ * gives the + child (s, tau + s g) and the - child (-s, -(tau + s g)); the
+ * parent keeps (s, tau).  Then d/dtheta E[sum_i s_i A(x_i, k_i)] =
+ * E[sum_i tau_i A(x_i, k_i)] for any observable A. */
 static int segment(orc_state* s, double xo, double to, double k, double w,
-                   uint64_t pid, uint32_t l, int is_root) {
+                   uint64_t pid, uint32_t l, int is_root, double tH, double tw) {
   const orc_config* c = &s->c;
   uint32_t r[4];
   draw4(s, pid, l, 0u, r);
@@ -353,6 +377,8 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
       int kill_m = !(km >= c->kmin && km < c->kmax);
       s->ledger[ORC_L_EVENTS] += 1;
       double wp = wc, wm = -wc; /* + child carries +wc, - child -wc */
+      double gH = 1.0 / c->H, gw = 1.0 / c->w - 4.0 * c->w * kap * kap;
+      double tpH = tH + w * gH, tpw = tw + w * gw; /* + child's tangent    */
       if (kill_p) {
         if (wp > 0) s->ledger[ORC_L_KILL_P] += 1; else if (wp < 0) s->ledger[ORC_L_KILL_M] += 1;
         if (wp > 0) s->wkill[0] += wp; else s->wkill[1] += -wp;
@@ -360,6 +386,10 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
       if (kill_m) {
         if (wm > 0) s->ledger[ORC_L_KILL_P] += 1; else if (wm < 0) s->ledger[ORC_L_KILL_M] += 1;
         if (wm > 0) s->wkill[0] += wm; else s->wkill[1] += -wm;
+      }
+      if (c->tangent) {
+        if (kill_p) { s->tkill[0] += tpH; s->tkill[1] += tpw; }
+        if (kill_m) { s->tkill[0] -= tpH; s->tkill[1] -= tpw; }
       }
       if (s->log_on) {
         if (s->nlog == s->logcap) {
@@ -383,8 +413,8 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
         e.kill_minus = kill_m;
         s->log[s->nlog++] = e;
       }
-      if (!kill_p && segment(s, xe, t, kp, wp, pid_p, l, 0)) return -1;
-      if (!kill_m && segment(s, xe, t, km, wm, pid_m, l, 0)) return -1;
+      if (!kill_p && segment(s, xe, t, kp, wp, pid_p, l, 0, tpH, tpw)) return -1;
+      if (!kill_m && segment(s, xe, t, km, wm, pid_m, l, 0, -tpH, -tpw)) return -1;
     }
     t += -log1p(-u4) / s->gamma0;
     ++j;
@@ -394,6 +424,8 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
   out.k = k;
   out.w = w;
   out.pid = pid;
+  out.tH = tH;
+  out.tw = tw;
   return push(&s->q, &s->nq, &s->capq, out);
 }
 
@@ -405,7 +437,7 @@ int orc_step(orc_state* s, int nsteps) {
     s->ledger[ORC_L_PSTEPS] += s->n;
     for (long long i = 0; i < s->n; ++i) {
       orc_particle p = s->p[i];
-      if (segment(s, p.x, 0.0, p.k, p.w, p.pid, l, 1)) return -1;
+      if (segment(s, p.x, 0.0, p.k, p.w, p.pid, l, 1, p.tH, p.tw)) return -1;
     }
     orc_particle* t = s->p;
     s->p = s->q;
@@ -469,7 +501,37 @@ static int regenerate(orc_state* s) {
       while (bin_x(s, x) < (double)ix) x = nextafter(x, INFINITY);
       while (bin_k(s, k) > (double)ik) k = nextafter(k, -INFINITY);
       while (bin_k(s, k) < (double)ik) k = nextafter(k, INFINITY);
-      orc_particle p = {x, k, sign, pid};
+      orc_particle p = {x, k, sign, pid, 0.0, 0.0};
+      if (push(&s->p, &s->n, &s->cap, p)) return -1;
+    }
+  }
+  if (!s->c.tangent) return 0;
+  /* Tangent mode: the tangent histogram D_nu is carried by particles of
+   * sign 0, n_t = ceil(max(|D_H|, |D_w|) / quantum) of them per cell with
+   * tau = D_nu / n_t each, uniform in D_nu (Alg. 3's offsets); their ids
+   * are (epoch << 40) | (instance << 32) | 2^31 | j, j counting them in cell
+   * order.  The signed particles carry tau = 0. */
+  uint64_t jt = 0;
+  for (long long nu = 0; nu < nh; ++nu) {
+    long long dH = s->dgrid[0][nu], dw = s->dgrid[1][nu];
+    long long m = llabs(dH) > llabs(dw) ? llabs(dH) : llabs(dw);
+    if (m == 0) continue;
+    long long nt = (m + s->c.tquantum - 1) / s->c.tquantum;
+    long long ix = nu / s->c.nk, ik = nu % s->c.nk;
+    double tH = (double)dH * (1.0 / 4294967296.0) / (double)nt;
+    double tw = (double)dw * (1.0 / 4294967296.0) / (double)nt;
+    for (long long r = 0; r < nt; ++r, ++jt) {
+      uint64_t pid = ((uint64_t)s->epoch << 40) | ((uint64_t)s->c.instance << 32) |
+                     0x80000000ull | jt;
+      uint32_t h[4];
+      draw4(s, pid, ORC_STEP_REGEN, 0u, h);
+      double x = s->c.xmin + ((double)ix + orc_u53(h[0], h[1])) * s->dx;
+      double k = s->c.kmin + ((double)ik + orc_u53(h[2], h[3])) * s->dk;
+      while (bin_x(s, x) > (double)ix) x = nextafter(x, -INFINITY);
+      while (bin_x(s, x) < (double)ix) x = nextafter(x, INFINITY);
+      while (bin_k(s, k) > (double)ik) k = nextafter(k, -INFINITY);
+      while (bin_k(s, k) < (double)ik) k = nextafter(k, INFINITY);
+      orc_particle p = {x, k, 0.0, pid, tH, tw};
       if (push(&s->p, &s->n, &s->cap, p)) return -1;
     }
   }
@@ -477,15 +539,25 @@ static int regenerate(orc_state* s) {
 }
 
 /* sp1: signed histogram c_nu = n_nu^+ - n_nu^- (Eq. signed_histogram). */
+/* In tangent mode also D_nu = sum of tau over the particles in D_nu, each
+ * tau rounded to a multiple of 2^-32 (so the sum is exact and independent
+ * of order); sign-0 particles enter D only. */
 static void bin_signed(orc_state* s) {
   long long nh = (long long)s->c.nx * s->c.nk;
   memset(s->grid, 0, (size_t)nh * sizeof(int));
+  if (s->c.tangent)
+    for (int d = 0; d < 2; ++d) memset(s->dgrid[d], 0, (size_t)nh * sizeof(long long));
   for (long long i = 0; i < s->n; ++i) {
     long long nu;
-    if (cell_of(s, s->p[i].x, s->p[i].k, &nu)) {
-      s->grid[nu] += s->p[i].w > 0 ? 1 : -1;
+    const orc_particle* p = &s->p[i];
+    if (cell_of(s, p->x, p->k, &nu)) {
+      if (p->w != 0.0) s->grid[nu] += p->w > 0 ? 1 : -1;
+      if (s->c.tangent) {
+        s->dgrid[0][nu] += llrint(p->tH * 4294967296.0);
+        s->dgrid[1][nu] += llrint(p->tw * 4294967296.0);
+      }
     } else {
-      if (s->p[i].w > 0) s->ledger[ORC_L_OUT_P] += 1; else s->ledger[ORC_L_OUT_M] += 1;
+      if (p->w > 0) s->ledger[ORC_L_OUT_P] += 1; else if (p->w < 0) s->ledger[ORC_L_OUT_M] += 1;
     }
   }
 }
@@ -695,6 +767,39 @@ int orc_regenerate(orc_state* s) {
 
 void orc_get_ledger(const orc_state* s, long long* out) {
   for (int i = 0; i < ORC_L_N; ++i) out[i] = s->ledger[i];
+}
+
+void orc_get_tangent(const orc_state* s, double* tH, double* tw) {
+  for (long long i = 0; i < s->n; ++i) {
+    if (tH) tH[i] = s->p[i].tH;
+    if (tw) tw[i] = s->p[i].tw;
+  }
+}
+
+void orc_get_dgrid(const orc_state* s, long long* dH, long long* dw) {
+  size_t nh = (size_t)s->c.nx * (size_t)s->c.nk;
+  if (dH && s->dgrid[0]) memcpy(dH, s->dgrid[0], nh * sizeof(long long));
+  if (dw && s->dgrid[1]) memcpy(dw, s->dgrid[1], nh * sizeof(long long));
+}
+
+void orc_get_tkill(const orc_state* s, double* out) {
+  out[0] = s->tkill[0];
+  out[1] = s->tkill[1];
+}
+
+/* d/dtheta of the transmission estimate from the tangent histogram: the sum
+ * of D_nu over cells with centre x > 0, divided by N_alpha. */
+void orc_tangent_transmission(const orc_state* s, double* out) {
+  const orc_config* c = &s->c;
+  long long acc[2] = {0, 0};
+  for (int ix = 0; ix < c->nx; ++ix) {
+    double centre = c->xmin + ((double)ix + 0.5) * s->dx;
+    if (!(centre > 0.0)) continue;
+    for (int ik = 0; ik < c->nk; ++ik)
+      for (int d = 0; d < 2; ++d) acc[d] += s->dgrid[d][(long long)ix * c->nk + ik];
+  }
+  for (int d = 0; d < 2; ++d)
+    out[d] = (double)acc[d] * (1.0 / 4294967296.0) / (double)c->n_alpha;
 }
 
 void orc_get_wkill(const orc_state* s, double* out) {

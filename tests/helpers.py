@@ -13,7 +13,9 @@ def make_oracle(wl, **over):
                          nx=w["nx"], nk=w["nk"], xmin=w["xmin"],
                          xmax=w["xmax"], kmin=w["kmin"], kmax=w["kmax"],
                          strategy=strat, n_alpha=w["n_alpha"], seed=w["seed"],
-                         instance=w.get("instance", 0))
+                         instance=w.get("instance", 0),
+                         tangent=w.get("tangent", False),
+                         tquantum=w.get("tquantum", 1.0))
 
 
 def net_sign(w):
