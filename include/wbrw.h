@@ -93,6 +93,10 @@ typedef struct {
   unsigned long long seed;  /* Philox key                                    */
   int table_ny, table_nkappa; /* dim 4: kernel tables of table_ny y nodes x  */
                             /* table_nkappa kappa cells (0: 4096 x 2048)     */
+  int tangent;              /* 1: carry likelihood-ratio tangents d/dH, d/dw */
+                            /* (dim 2, sp1, Gaussian kind; see               */
+                            /* wbrw_transmission_gradients)                  */
+  double tangent_quantum;   /* largest |tau| of a tangent particle (<= 0: 1) */
 } wbrw_config;
 
 /* Caller-owned device buffers, structure of arrays, `capacity` elements each:
@@ -120,6 +124,8 @@ typedef struct {
   size_t scratch_bytes;
   void* event_log;
   long long event_log_capacity;
+  void* tangent;   /* tangent mode: 2*capacity doubles, tau_H of slot i at  */
+                   /* [i] and tau_w at [capacity + i] (else NULL)           */
 } wbrw_buffers;
 
 /* One accepted branching event (Alg. 1 item 3), as logged for parity tests.
@@ -405,6 +411,31 @@ wbrw_status wbrw_transmissions(wbrw_ctx* ctx, double* out_host);
 /* After wbrw_particles: the instance of every materialised particle,
  * inst_dev[0..n) (device memory).  Synchronises the stream. */
 wbrw_status wbrw_particle_instances(wbrw_ctx* ctx, unsigned int* inst_dev);
+
+/* ------------------------------------------------------------------------
+ * Likelihood-ratio derivatives (config->tangent = 1).  The paper has no
+ * differentiation; this is an extension.  The expected particle measure of
+ * the branching walk is a sum over lineages of products of the birth
+ * intensities V_W^+(x_b, kappa_b; theta) (a parent outlives its births, so no
+ * survival factor enters).  Each particle therefore carries a tangent weight
+ * tau = s S: its sign times the sum, over the births of its lineage, of
+ * g = d/dtheta log V_W^+ = (1/H, 1/w - 4 w kappa^2), theta = (H, w).  A birth
+ * from (s, tau) gives the + child (s, tau + s g) and the - child
+ * (-s, -(tau + s g)).  Then d/dtheta E[sum_i s_i A(x_i, k_i)] =
+ * E[sum_i tau_i A(x_i, k_i)].  Annihilation also sums the tangent histogram
+ * D_nu (tau rounded to multiples of 2^-32, exact and order-free) and
+ * regeneration carries it on particles of sign 0: ceil(max(|D_H|, |D_w|) /
+ * tangent_quantum) per cell with tau = D_nu / count, ids
+ * (epoch << 40) | (instance << 32) | 2^31 | j.  The signed particles, their
+ * ids and every count are exactly those of the run without tangents.
+ * Batches differentiate each instance in its own (H, w).  wbrw_restore loads
+ * no tangent (the restored run has D = 0).
+ * ------------------------------------------------------------------------ */
+
+/* (dT/dH, dT/dw) of every instance's transmission estimate
+ * (sum over cells with centre x > 0 of D_nu / N_alpha), right after a
+ * resampling: out_host[2 i], out_host[2 i + 1].  Synchronises the stream. */
+wbrw_status wbrw_transmission_gradients(wbrw_ctx* ctx, double* out_host);
 
 /* Copy the counters (WBRW_C_*) to out[0..WBRW_C_COUNT).  Synchronises. */
 wbrw_status wbrw_counters(wbrw_ctx* ctx, long long* out);

@@ -1,6 +1,6 @@
 """Build the CUDA library libwbrw.so for sm_103a (GB300), in tree.
 
-Six translation units (the kernels of each precision and phase-space model,
+Eight translation units (the kernels of each precision and phase-space model,
 the resampling kernels and the C ABI) are compiled in parallel with nvcc and
 linked into
 ``paper_1709_02121_gb300/_build/libwbrw.so`` against the shared CUDA runtime
@@ -19,6 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwbrw.so")
 SOURCES = ["wbrw_fp32.cu", "wbrw_fp64.cu", "wbrw_fp32_4d.cu", "wbrw_fp64_4d.cu",
+           "wbrw_fp32_grad.cu", "wbrw_fp64_grad.cu",
            "wbrw_common.cu", "wbrw_api.cu"]
 HEADERS = ["wbrw_device.cuh", "wbrw_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -30,7 +30,8 @@ struct Layout {
   size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
       rec_a, keep0, keep1, res0, res1, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
-      tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, total;
+      tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, dgrid0, dgrid1, tnz_cell, tnz_start,
+      tnz_tau, ttile_nz, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
@@ -43,6 +44,10 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
   if (!c) return fail("NULL config");
   if (c->dim != 2 && c->dim != 4) return fail("dim must be 2 or 4");
   if (c->dim == 4 && c->strategy != WBRW_SP1_PAIR) return fail("dim 4 uses sp1 only");
+  if (c->tangent != 0 && c->tangent != 1) return fail("tangent must be 0 or 1");
+  if (c->tangent && (c->dim != 2 || c->strategy != WBRW_SP1_PAIR))
+    return fail("tangents need dim 2 and sp1");
+  if (c->tangent && !(c->tangent_quantum < 1e9)) return fail("tangent quantum");
   if (c->dim == 4 && ninst > 1) return fail("dim 4 runs one instance");
   if (c->table_ny < 0 || c->table_ny == 1 || c->table_nkappa < 0 || c->table_ny > (1 << 20) ||
       c->table_nkappa > (1 << 20))
@@ -69,9 +74,17 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
 // into one segment per producer warp (at most kMaxSeg); each segment gets at
 // least kMinSeg entries so that small runs cannot starve a warp.
 constexpr long long kMinSeg = 64;
-const Driver* drv_for(int precision, int dim) {
+const Driver* drv_for(int precision, int dim, int tangent) {
   if (dim == 4) return precision == WBRW_FP64 ? driver_fp64_4d() : driver_fp32_4d();
+  if (tangent) return precision == WBRW_FP64 ? driver_fp64_grad() : driver_fp32_grad();
   return precision == WBRW_FP64 ? driver_fp64() : driver_fp32();
+}
+
+// The tangent quantum in units of 2^-32 (at least one unit).
+long long tquantum_of(const wbrw_config* c) {
+  const double q = c->tangent_quantum > 0 ? c->tangent_quantum : 1.0;
+  const double u = std::ldexp(q, 32);
+  return u < 1.0 ? 1 : (long long)std::llround(u);
 }
 
 int table_ny(const wbrw_config* c) { return c->table_ny > 0 ? c->table_ny : 4096; }
@@ -79,7 +92,7 @@ int table_nkappa(const wbrw_config* c) { return c->table_nkappa > 0 ? c->table_n
 
 Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   Layout L;
-  const Driver* d = drv_for(c->precision, c->dim);
+  const Driver* d = drv_for(c->precision, c->dim, c->tangent);
   const long long cells = c->dim == 4 ? (long long)c->nx * c->nx * c->nk * c->nk
                                       : (long long)c->nx * c->nk;
   const long long nh = cells * ninst;
@@ -135,6 +148,13 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.tab_xi1 = take(d4 ? ny * el : 0);
   L.tab_cdf0 = take(d4 ? ny * nk * el : 0);
   L.tab_cdf1 = take(d4 ? ny * nk * el : 0);
+  const bool tg = c->tangent != 0;
+  L.dgrid0 = take(tg ? (size_t)nh * 8 : 0);
+  L.dgrid1 = take(tg ? (size_t)nh * 8 : 0);
+  L.tnz_cell = take(tg ? (size_t)nh * 4 : 0);
+  L.tnz_start = take(tg ? (size_t)nh * 8 : 0);
+  L.tnz_tau = take(tg ? (size_t)nh * 16 : 0);
+  L.ttile_nz = take(tg ? (size_t)L.tile_cap * 4 : 0);
   L.total = off;
   return L;
 }
@@ -191,7 +211,9 @@ wbrw_status cuda_check(wbrw_ctx* c, cudaError_t e, const char* what) {
   return seterr(c, WBRW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-const Driver* drv(const wbrw_ctx* c) { return drv_for(c->cfg.precision, c->cfg.dim); }
+const Driver* drv(const wbrw_ctx* c) {
+  return drv_for(c->cfg.precision, c->cfg.dim, c->cfg.tangent);
+}
 
 #define WBRW_TRY(c, expr, what)                           \
   do {                                                    \
@@ -215,6 +237,11 @@ wbrw_status device_status(wbrw_ctx* c) {
                 (err & ERR_CAP_RECORDS) ? " bootstrap record capacity exceeded;" : "");
 }
 
+cudaError_t zero_tangent(wbrw_ctx* c) {
+  cudaError_t e = launch_zero(c, c->dgrid[0], (size_t)c->nh * 8);
+  return e == cudaSuccess ? launch_zero(c, c->dgrid[1], (size_t)c->nh * 8) : e;
+}
+
 // Histogram the particles of the arrays into c->buf.grid (sp1) or run the
 // signed bootstrap (sp2), then build the regeneration plan.  c->epoch has
 // already been advanced.
@@ -222,6 +249,7 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
   const Driver* d = drv(c);
   if (c->cfg.strategy == WBRW_SP1_PAIR) {
     WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
+    if (c->tangent) WBRW_TRY(c, zero_tangent(c), "zero tangent");
     WBRW_TRY(c, d->bin(c, DST_BIN1, c->buf.grid, 1), "bin");
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
@@ -234,6 +262,7 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
     WBRW_TRY(c, launch_boot(c), "bootstrap");
   }
   WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+  if (c->tangent) WBRW_TRY(c, launch_scan_tangent(c), "tangent plan");
   return WBRW_OK;
 }
 
@@ -247,6 +276,7 @@ wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_
   c->epoch = regen_epoch + 1;
   if (c->cfg.strategy == WBRW_SP1_PAIR) {
     WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
+    if (c->tangent) WBRW_TRY(c, zero_tangent(c), "zero tangent");
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
     WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
@@ -264,6 +294,7 @@ wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_
   WBRW_TRY(c, e, "period");
   if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c), "bootstrap");
   WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+  if (c->tangent) WBRW_TRY(c, launch_scan_tangent(c), "tangent plan");
   return WBRW_OK;
 }
 
@@ -478,7 +509,7 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
                               : (long long)config->nx * config->nk;
   if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0 ||
       (config->strategy == WBRW_SP2_BOOTSTRAP && !b->w) ||
-      b->grid_cells < cells * ninst ||
+      b->grid_cells < cells * ninst || (config->tangent && !b->tangent) ||
       ((uintptr_t)b->scratch & (kAlign - 1)) != 0 ||
       (b->event_log && b->event_log_capacity <= 0)) {
     free(q);
@@ -579,6 +610,24 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->inst_trans = (double*)(base + L.tabs + kTabTransOff);
   c->cinst = ninst > 1 ? (unsigned*)(base + L.cinst) : nullptr;
   c->obs_red = (long long*)(base + L.obs_red);
+  c->tangent = config->tangent;
+  c->inst_grad = (double*)(base + L.tabs + kTabGradOff);
+  c->tinst_slot = (unsigned long long*)(base + L.tabs + kTabTSlotOff);
+  if (c->tangent) {
+    c->tquantum = tquantum_of(config);
+    c->dgrid[0] = (long long*)(base + L.dgrid0);
+    c->dgrid[1] = (long long*)(base + L.dgrid1);
+    c->tnz_cell = (uint32_t*)(base + L.tnz_cell);
+    c->tnz_start = (unsigned long long*)(base + L.tnz_start);
+    c->tnz_tau = (double*)(base + L.tnz_tau);
+    c->ttile_nz = (uint32_t*)(base + L.ttile_nz);
+    if (cudaMemsetAsync(c->dgrid[0], 0, (size_t)c->nh * 8, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->dgrid[1], 0, (size_t)c->nh * 8, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->tinst_slot, 0, (size_t)(kMaxInst + 1) * 8, c->stream) != cudaSuccess) {
+      free_ctx(c);
+      return WBRW_ERR_CUDA;
+    }
+  }
   if (c->dim == 4) {
     wbrw_status st = build_tables(c, base, L);
     if (st != WBRW_OK) {
@@ -807,6 +856,18 @@ wbrw_status wbrw_transmissions(wbrw_ctx* c, double* out_host) {
   return device_status(c);
 }
 
+wbrw_status wbrw_transmission_gradients(wbrw_ctx* c, double* out_host) {
+  if (!c || !out_host) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if (!c->tangent) return seterr(c, WBRW_ERR_STATE, "the context carries no tangents");
+  if (c->state != ST_HISTOGRAM)
+    return seterr(c, WBRW_ERR_STATE, "gradients need a resampling first");
+  WBRW_TRY(c, launch_transmission_gradients(c), "gradients");
+  WBRW_TRY(c, cudaMemcpyAsync(out_host, c->inst_grad, (size_t)c->ninst * 16,
+                              cudaMemcpyDeviceToHost, c->stream), "copy");
+  return device_status(c);
+}
+
 wbrw_status wbrw_particle_instances(wbrw_ctx* c, unsigned int* inst_dev) {
   if (!c || !inst_dev) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
@@ -893,6 +954,10 @@ wbrw_status wbrw_restore(wbrw_ctx* c, const int* grid, long long step, long long
   WBRW_TRY(c, cudaMemcpyAsync(c->buf.grid, grid, (size_t)c->nh * 4, cudaMemcpyDefault,
                               c->stream), "copy grid");
   WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
+  if (c->tangent) {
+    WBRW_TRY(c, zero_tangent(c), "zero tangent");
+    WBRW_TRY(c, launch_scan_tangent(c), "tangent plan");
+  }
   c->step = step;
   c->epoch = epoch;
   c->state = ST_HISTOGRAM;
@@ -950,6 +1015,8 @@ wbrw_status wbrw_autotune(wbrw_ctx* c, int trials, wbrw_tuning* best, double* ms
   if (c->failed) return WBRW_ERR_STATE;
   if (!c->fresh || c->state != ST_HISTOGRAM || c->cfg.resample_every <= 0)
     return seterr(c, WBRW_ERR_STATE, "autotune needs the state right after a resampling");
+  if (c->tangent)
+    return seterr(c, WBRW_ERR_STATE, "autotune a context without tangents (same shapes)");
   const int T = c->cfg.resample_every;
   const int len = T - (int)(c->step % T);
   if (len > c->max_chunk)

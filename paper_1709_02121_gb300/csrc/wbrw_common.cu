@@ -144,11 +144,12 @@ __global__ void __launch_bounds__(kBlock) k_cells_a(const int* grid, long long n
   }
 }
 
+// which = 0: the plan of the signed particles; 1: the tangent plan.
 __global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
                                                     unsigned int* bnz,
                                                     long long nb, Counters* c,
                                                     long long tile_cap,
-                                                    unsigned long long* inst_end) {
+                                                    unsigned long long* inst_end, int which) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   unsigned long long carry_s = 0, carry_z = 0;
   for (long long b0 = 0; b0 < nb; b0 += kBlock) {
@@ -165,8 +166,13 @@ __global__ void __launch_bounds__(kBlock) k_cells_b(unsigned long long* bsum,
     carry_z += tz;
   }
   if (threadIdx.x == 0) {
-    c->regen_total = carry_s;
-    c->nz_count = carry_z;
+    if (which) {
+      c->tan_total = carry_s;
+      c->tan_nz = carry_z;
+    } else {
+      c->regen_total = carry_s;
+      c->nz_count = carry_z;
+    }
     *inst_end = carry_s;
     if (carry_s > (unsigned long long)tile_cap * 32ull) atomicOr(&c->err, ERR_CAP_PARTICLES);
   }
@@ -479,6 +485,109 @@ __global__ void __launch_bounds__(kBlock) k_reduce4(const int* counts, int nx, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tangent plan (tangent mode): cell nu carries n_nu = ceil(max(|D_H|, |D_w|)
+// / quantum) tangent particles with tau = D_nu / n_nu each.  The same three
+// passes as the plan of the signed particles.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long tan_count(const long long* dH, const long long* dw,
+                                                       long long c, long long q) {
+  const long long a = dH[c] < 0 ? -dH[c] : dH[c], b = dw[c] < 0 ? -dw[c] : dw[c];
+  const long long m = a > b ? a : b;
+  return m ? (unsigned long long)((m + q - 1) / q) : 0ull;
+}
+
+__global__ void __launch_bounds__(kBlock) k_tcells_a(const long long* dH, const long long* dw,
+                                                     long long nh, long long q,
+                                                     unsigned long long* bsum, unsigned int* bnz) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned long long s = 0, z = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    const long long c = base + i;
+    if (c < nh) {
+      const unsigned long long n = tan_count(dH, dw, c, q);
+      s += n;
+      z += n != 0;
+    }
+  }
+  unsigned long long ts, tz;
+  block_exscan(s, red, ts);
+  block_exscan(z, red, tz);
+  if (threadIdx.x == 0) {
+    bsum[blockIdx.x] = ts;
+    bnz[blockIdx.x] = (unsigned int)tz;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_tcells_c(const long long* dH, const long long* dw,
+                                                     long long nh, long long q,
+                                                     const unsigned long long* bsum,
+                                                     const unsigned int* bnz, uint32_t* nz_cell,
+                                                     unsigned long long* nz_start, double* nz_tau,
+                                                     uint32_t* tile_nz, long long tile_cap,
+                                                     long long nhi, unsigned long long* inst_slot) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
+  unsigned long long n[kScanItems];
+  unsigned long long s = 0, z = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    const long long c = base + i;
+    n[i] = c < nh ? tan_count(dH, dw, c, q) : 0ull;
+    s += n[i];
+    z += n[i] != 0;
+  }
+  unsigned long long ts, tz;
+  unsigned long long os = block_exscan(s, red, ts) + bsum[blockIdx.x];
+  unsigned long long oz = block_exscan(z, red, tz) + bnz[blockIdx.x];
+  long long next_inst = (base + nhi - 1) / nhi * nhi;
+  for (int i = 0; i < kScanItems; ++i) {
+    const long long c = base + i;
+    if (c == next_inst && next_inst < nh) {
+      inst_slot[next_inst / nhi] = os;
+      next_inst += nhi;
+    }
+    if (n[i]) {
+      nz_cell[oz] = (uint32_t)c;
+      nz_start[oz] = os;
+      nz_tau[2 * oz] = __ddiv_rn(__dmul_rn((double)dH[c], 1.0 / 4294967296.0), (double)n[i]);
+      nz_tau[2 * oz + 1] = __ddiv_rn(__dmul_rn((double)dw[c], 1.0 / 4294967296.0), (double)n[i]);
+      const unsigned long long t_end = min((os + n[i] + 31) >> 5, (unsigned long long)tile_cap);
+      for (unsigned long long t = (os + 31) >> 5; t < t_end; ++t) tile_nz[t] = (uint32_t)oz;
+      ++oz;
+      os += n[i];
+    }
+  }
+}
+
+// (dT/dH, dT/dw) of each instance (one block each): the tangent histogram
+// summed over the cells with centre x > 0, times 2^-32, over N_alpha.
+__global__ void __launch_bounds__(kBlock) k_obs_tgrad(const long long* dH, const long long* dw,
+                                                      int nx, int nk, double xmin, double dx,
+                                                      const double* na, double* out) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  __shared__ int s_ix0;
+  if (threadIdx.x == 0) {
+    int ix0 = nx;
+    for (int ix = 0; ix < nx; ++ix)
+      if (__dadd_rn(xmin, __dmul_rn(__dadd_rn((double)ix, 0.5), dx)) > 0.0) { ix0 = ix; break; }
+    s_ix0 = ix0;
+  }
+  __syncthreads();
+  const long long nhi = (long long)nx * nk;
+  for (int d = 0; d < 2; ++d) {
+    const long long* g = (d ? dw : dH) + (long long)blockIdx.x * nhi;
+    long long acc = 0;
+    for (long long nu = (long long)s_ix0 * nk + threadIdx.x; nu < nhi; nu += kBlock) acc += g[nu];
+    unsigned long long t;
+    block_exscan((unsigned long long)acc, red, t);
+    if (threadIdx.x == 0)
+      out[2 * blockIdx.x + d] =
+          __ddiv_rn(__dmul_rn((double)(long long)t, 1.0 / 4294967296.0), na[blockIdx.x]);
+    __syncthreads();
+  }
+}
+
 int grid_cap(Ctx* c, int per_sm) { return c->num_sms * per_sm; }
 
 }  // namespace
@@ -499,7 +608,7 @@ cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
   const long long nb = c->scan_blocks;
   k_cells_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz);
   k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt, c->tile_cap,
-                                         c->inst_slot + c->ninst);
+                                         c->inst_slot + c->ninst, 0);
   k_cells_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(grid, c->nh, c->scan_bsum, c->scan_bnz,
                                                    c->nz_cell, c->nz_start, c->tile_nz,
                                                    c->tile_cap, c->nhi, c->inst_slot);
@@ -556,6 +665,27 @@ cudaError_t launch_observables(Ctx* c, int inst, const int* counts, const long l
 cudaError_t launch_transmissions(Ctx* c, const int* counts, double* out) {
   k_obs_trans<<<c->ninst, kBlock, 0, c->stream>>>(counts, c->cfg.nx, c->cfg.nk, c->cfg.xmin,
                                                   c->dx, c->inst_na, out);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_tangent(Ctx* c) {
+  const long long nb = c->scan_blocks;
+  k_tcells_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->dgrid[0], c->dgrid[1], c->nh, c->tquantum,
+                                                    c->scan_bsum, c->scan_bnz);
+  k_cells_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, c->scan_bnz, nb, c->cnt, c->tile_cap,
+                                         c->tinst_slot + c->ninst, 1);
+  k_tcells_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->dgrid[0], c->dgrid[1], c->nh, c->tquantum,
+                                                    c->scan_bsum, c->scan_bnz, c->tnz_cell,
+                                                    c->tnz_start, c->tnz_tau, c->ttile_nz,
+                                                    c->tile_cap, c->nhi, c->tinst_slot);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transmission_gradients(Ctx* c) {
+  k_obs_tgrad<<<c->ninst, kBlock, 0, c->stream>>>(c->dgrid[0], c->dgrid[1], c->cfg.nx, c->cfg.nk,
+                                                  c->cfg.xmin, c->dx, c->inst_na, c->inst_grad);
   c->launches++;
   return cudaGetLastError();
 }

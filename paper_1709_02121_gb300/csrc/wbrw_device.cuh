@@ -109,14 +109,29 @@ struct F32 {
 // Phase-space model: precision F and D position coordinates (D = 1: the 2D
 // phase space (x, k) of one particle; D = 2: the 4D phase space
 // (x1, x2, k1, k2) of two electrons, Example 1).
-template <class F, int Dm>
+//
+// TGm: the tangent mode of the 2D model: every particle also carries its
+// likelihood-ratio tangent weight (d/dH, d/dw), see do_event.
+template <class F, int Dm, bool TGm = false>
 struct PD : F {
   static constexpr int D = Dm;
+  static constexpr bool TG = TGm;
 };
 using P64 = PD<F64, 1>;
 using P32 = PD<F32, 1>;
 using Q64 = PD<F64, 2>;
 using Q32 = PD<F32, 2>;
+using P64G = PD<F64, 1, true>;
+using P32G = PD<F32, 1, true>;
+
+// The tangent weight tau = s S (sign times lineage score) of a particle, in
+// FP64 whatever the precision; an empty base outside the tangent mode.
+template <bool TG>
+struct TanField {};
+template <>
+struct TanField<true> {
+  double th, tw;
+};
 
 // A position or a wavevector of the model.
 template <class P>
@@ -125,8 +140,8 @@ struct PV {
 };
 
 template <class P>
-struct FEntry {  // a particle at the start of interval l (offspring waves),
-                 // or a candidate interval l with x at its start
+struct FEntry : TanField<P::TG> {  // a particle at the start of interval l (offspring
+                                   // waves), or a candidate interval l with x at its start
   unsigned long long pid;
   PV<P> x, k;
   typename P::T w;
@@ -135,6 +150,7 @@ struct FEntry {  // a particle at the start of interval l (offspring waves),
 
 static_assert(sizeof(FEntry<P64>) == 40 && sizeof(FEntry<P32>) == 24, "FEntry layout");
 static_assert(sizeof(FEntry<Q32>) == 32, "FEntry layout");
+static_assert(sizeof(FEntry<P32G>) == 40 && sizeof(FEntry<P64G>) == 56, "FEntry layout");
 
 template <class P>
 struct SEntry;
@@ -149,6 +165,7 @@ struct Inst {
   float p_any_f;              // FP32: P(candidate) per interval
   unsigned p16, p16_frac8;    // FP32 coin threshold and tie refinement
   int well;                   // H < 0: V_W has the sign of -sin (Eq. 2)
+  double gH, gw0, gw1;        // tangent mode: 1/H, 1/w, 4w (the score of a birth)
 };
 
 // Initial sampling of one instance: slots [start, start + n) of the arrays
@@ -237,6 +254,16 @@ struct KP {
   const unsigned long long* nz_start;
   const uint32_t* tile_nz;   // first nonzero cell of each 32-slot tile
   long long tile_cap;
+  // tangent mode: the tangent histogram D (2^-32 units) and tangent arrays
+  // (slot i: tan[i] = tau_H, tan[capacity + i] = tau_w); the tangent
+  // particles' plan: nonzero cells, first slots, tau per particle, tiles
+  long long* dgrid[2];
+  double* tan;
+  const uint32_t* tnz_cell;
+  const unsigned long long* tnz_start;
+  const double* tnz_tau;     // (tau_H, tau_w) of each plan entry
+  const uint32_t* ttile_nz;
+  const unsigned long long* tinst_slot;
   Counters* cnt;
   wbrw_event* log;
   long long log_cap;
@@ -568,6 +595,20 @@ __device__ __forceinline__ void tally_out(const KP<P>& p, Acc& acc, typename P::
   }
 }
 
+// Tangent mode: tau into the tangent histogram, rounded to a multiple of
+// 2^-32 so that the sums are exact and independent of order.
+template <class P>
+__device__ __forceinline__ void add_tangent(const KP<P>& p, long long gcell,
+                                            const TanField<P::TG>& tau) {
+  if constexpr (P::TG) {
+    if (!p.dgrid[0]) return;
+    const long long a = __double2ll_rn(tau.th * 4294967296.0);
+    const long long b = __double2ll_rn(tau.tw * 4294967296.0);
+    if (a) atomicAdd((unsigned long long*)(p.dgrid[0] + gcell), (unsigned long long)a);
+    if (b) atomicAdd((unsigned long long*)(p.dgrid[1] + gcell), (unsigned long long)b);
+  }
+}
+
 template <class P>
 __device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long idx, int cell,
                                            typename P::T w) {
@@ -581,13 +622,17 @@ __device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long i
 template <class P, int DST>
 __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                  unsigned long long pid, const PV<P>& x, const PV<P>& k,
-                                 typename P::T w) {
+                                 typename P::T w, const TanField<P::TG>& tau) {
   using T = typename P::T;
   int cell;
   const int cbase = inst * p.nhi;
   if constexpr (DST == DST_BIN1) {
-    if (cell_of<P>(p, x, k, cell)) atomicAdd(p.grid + cbase + cell, w > (T)0 ? 1 : -1);
-    else tally_out<P>(p, acc, w);
+    if (cell_of<P>(p, x, k, cell)) {
+      if (!P::TG || w != (T)0) atomicAdd(p.grid + cbase + cell, w > (T)0 ? 1 : -1);
+      add_tangent<P>(p, (long long)cbase + cell, tau);
+    } else {
+      tally_out<P>(p, acc, w);
+    }
   } else if constexpr (DST == DST_WSUM) {
     if (cell_of<P>(p, x, k, cell))
       atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
@@ -612,6 +657,10 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
     }
     p.s[slot] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
     if (p.w) p.w[slot] = w;
+    if constexpr (P::TG) {
+      p.tan[slot] = tau.th;
+      p.tan[p.capacity + slot] = tau.tw;
+    }
     p.cpid[slot - p.cnt->n_base] = pid;
     if (p.ninst > 1) p.cinst[slot - p.cnt->n_base] = (unsigned)inst;
   }
@@ -629,7 +678,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
 // pass a drain kernel finishes whatever remains with a full recursion.
 // ---------------------------------------------------------------------------
 template <class P>
-struct SEntry {  // a deferred segment, with the time and index of its next event
+struct SEntry : TanField<P::TG> {  // a deferred segment, with the time and index of its next event
   using T = typename P::T;
   unsigned long long pid;
   PV<P> xo;
@@ -643,6 +692,7 @@ struct SEntry {  // a deferred segment, with the time and index of its next even
 
 static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<Q32>) == 64, "SEntry layout");
+static_assert(sizeof(SEntry<P32G>) == 80, "SEntry layout");
 
 constexpr unsigned kRootFlag = 0x80000000u;
 
@@ -652,10 +702,11 @@ template <class P, int DST>
 __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                        unsigned long long pid, const PV<P>& xo,
                                        typename P::T to, const PV<P>& k, typename P::T w,
-                                       int l) {
+                                       int l, const TanField<P::TG>& tau) {
   const PV<P> xf = pos_at(p, xo, to, k, p.dt);
   if (l + 1 < p.L) {
     FEntry<P> e;
+    static_cast<TanField<P::TG>&>(e) = tau;
     e.pid = pid;
     e.x = xf;
     e.k = k;
@@ -668,7 +719,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
     else
       set_err(p.cnt, ERR_CAP_QUEUE);
   } else {
-    emit_child_final<P, DST>(p, wc, acc, inst, pid, xf, k, w);
+    emit_child_final<P, DST>(p, wc, acc, inst, pid, xf, k, w, tau);
   }
 }
 
@@ -698,7 +749,8 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
                                                   typename P::T to, const PV<P>& k,
                                                   typename P::T w,
                                                   const typename Draw<P>::State& st, int l,
-                                                  unsigned j, typename P::T t, Later later) {
+                                                  unsigned j, typename P::T t, Later later,
+                                                  const TanField<P::TG>& tau) {
   using T = typename P::T;
   const PV<P> xe = pos_at(p, xo, to, k, t);
   T kap, gap, fac;
@@ -739,6 +791,16 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
     const bool kill_p = !k_inside(p, kp);
     const bool kill_m = !k_inside(p, km);
     const T wc_ = (P::D == 1 && p.strategy != 1) ? P::mul(w, fac) : w;
+    // tangent mode: the birth's score g = (1/H, 1/w - 4 w kappa^2), the
+    // derivative of log V_W^+(x_e, kappa) (Eq. 2); the + child gets
+    // tau + s g, the - child its negative
+    TanField<P::TG> tp;
+    if constexpr (P::TG) {
+      const double kd = (double)kap;
+      const double gw = __dsub_rn(ip.gw0, __dmul_rn(__dmul_rn(ip.gw1, kd), kd));
+      tp.th = __dadd_rn(tau.th, __dmul_rn((double)w, ip.gH));
+      tp.tw = __dadd_rn(tau.tw, __dmul_rn((double)w, gw));
+    }
     ++acc.events;
     if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
     if (kill_m) { if (-wc_ > (T)0) ++acc.kill_p; else if (-wc_ < (T)0) ++acc.kill_m; }
@@ -767,6 +829,10 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
     for (int c = 0; c < 2; ++c) {
       if (c == 0 ? kill_p : kill_m) continue;
       SEntry<P> ch;
+      if constexpr (P::TG) {
+        ch.th = c == 0 ? tp.th : -tp.th;
+        ch.tw = c == 0 ? tp.tw : -tp.tw;
+      }
       ch.pid = c == 0 ? pid_p : pid_m;
       ch.xo = xe;
       ch.to = t;
@@ -776,7 +842,7 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
       ch.j = 0;
       ch.t = Draw<P>::first(p, ip, ch.pid, l, t, false, ch.st);
       if (ch.t < p.dt) later(ch);
-      else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l);
+      else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l, ch);
     }
   }
   return gap;
@@ -799,11 +865,11 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
     };
     while (s.t < p.dt) {
       const typename P::T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k,
-                                                 s.w, s.st, l, j, s.t, later);
+                                                 s.w, s.st, l, j, s.t, later, s);
       s.t = P::add(s.t, gap);
       ++j;
     }
-    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l);
+    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s);
   }
 }
 
@@ -843,7 +909,7 @@ template <class P, int SRC, int DST>
 __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
                                             unsigned long long slot, PV<P> x, const PV<P>& k,
                                             typename P::T w, unsigned long long pid, int ls,
-                                            int inst) {
+                                            int inst, const TanField<P::TG>& tau) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   const unsigned long long g = global_warp();
@@ -912,6 +978,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if ((mask >> (l - p.l0)) & 1u) {
         if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
           FEntry<P> e;
+          static_cast<TanField<P::TG>&>(e) = tau;
           e.pid = pid;
           e.x = x;
           e.k = k;
@@ -939,6 +1006,17 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if (act) {
 #pragma unroll
         for (int d = 0; d < P::D; ++d) p.x[d * p.capacity + slot] = x.c[d];
+      }
+    } else if constexpr (SRC == SRC_REGEN && P::TG) {
+      // the base region: the signed particles, with tau = 0
+      if (act && slot >= (unsigned long long)p.capacity) {
+        set_err(p.cnt, ERR_CAP_PARTICLES);
+      } else if (act) {
+        p.x[slot] = x.c[0];
+        p.k[slot] = k.c[0];
+        p.s[slot] = w > (T)0 ? 1 : -1;
+        p.tan[slot] = 0.0;
+        p.tan[p.capacity + slot] = 0.0;
       }
     } else if constexpr (SRC == SRC_REGEN) {
       if (act && slot >= (unsigned long long)p.capacity) {
@@ -968,6 +1046,10 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
           }
           p.s[off] = w > (T)0 ? 1 : (w < (T)0 ? -1 : 0);
           if (p.w) p.w[off] = w;
+          if constexpr (P::TG) {
+            p.tan[off] = tau.th;
+            p.tan[p.capacity + off] = tau.tw;
+          }
           p.cpid[off - p.cnt->n_base] = pid;
           if (p.ninst > 1) p.cinst[off - p.cnt->n_base] = (unsigned)inst;
         }
@@ -977,15 +1059,21 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     // lanes that hit the same cell with the same sign add once (the key is
     // 2 cell + sign, or ~0 for none; 2 nx nk < 2^32 is checked on the host)
     unsigned key = ~0u;
+    int cell = -1;
     if (act) {
-      int cell;
-      if (cell_of<P>(p, x, k, cell))
-        key = 2u * (unsigned)(cbase + cell) + (w > (T)0 ? 1u : 0u);
-      else tally_out<P>(p, acc, w);
+      if (cell_of<P>(p, x, k, cell)) {
+        if (!P::TG || w != (T)0) key = 2u * (unsigned)(cbase + cell) + (w > (T)0 ? 1u : 0u);
+      } else {
+        cell = -1;
+        tally_out<P>(p, acc, w);
+      }
     }
     const unsigned grp = __match_any_sync(kFull, key);
     if (key != ~0u && lane == __ffs(grp) - 1)
       atomicAdd(p.grid + (key >> 1), (key & 1u) ? __popc(grp) : -__popc(grp));
+    if constexpr (P::TG) {
+      if (act && cell >= 0) add_tangent<P>(p, (long long)cbase + cell, tau);
+    }
   } else if constexpr (DST == DST_WSUM) {
     if (act) {
       int cell;
@@ -1043,17 +1131,26 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         for (int d = 0; d < P::D; ++d) e.x.c[d] = e.k.c[d] = (T)0;
         e.w = (T)0;
         e.l = p.L;
+        if constexpr (P::TG) e.th = e.tw = 0.0;
         if (act) e = p.fq_in[(long long)sg * p.qseg + i];
         flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
-                                 ent_inst(e.l));
+                                 ent_inst(e.l), e);
       }
     }
   } else {
+    // SRC_TREGEN walks the tangent plan exactly as SRC_REGEN walks the plan
+    // of the signed particles
+    constexpr bool TR = SRC == SRC_TREGEN;
+    constexpr bool RG = SRC == SRC_REGEN || TR;
+    const uint32_t* tile_nz = TR ? p.ttile_nz : p.tile_nz;
+    const uint32_t* nz_cell = TR ? p.tnz_cell : p.nz_cell;
+    const unsigned long long* nz_start = TR ? p.tnz_start : p.nz_start;
+    const unsigned long long* islot = TR ? p.tinst_slot : p.inst_slot;
     unsigned long long n;
     if constexpr (SRC == SRC_ARRAY) n = p.cnt->n_src;
-    else n = min(p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
+    else n = min(TR ? p.cnt->tan_total : p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
     const unsigned long long n_base = p.cnt->n_base, base_pid = p.cnt->base_pid;
-    const unsigned long long nz = (SRC == SRC_REGEN) ? p.cnt->nz_count : 0ull;
+    const unsigned long long nz = RG ? (TR ? p.cnt->tan_nz : p.cnt->nz_count) : 0ull;
     for (unsigned long long base = g * 32ull; base < n; base += nwarps * 32ull) {
       const unsigned long long slot = base + lane;
       const bool act = slot < n;
@@ -1063,14 +1160,16 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       T w = (T)0;
       unsigned long long pid = 0;
       int inst = 0;
-      if constexpr (SRC == SRC_REGEN) {
+      TanField<P::TG> tau;
+      if constexpr (P::TG) tau.th = tau.tw = 0.0;
+      if constexpr (RG) {
         // Alg. 3: the cell of each slot.  The tile's first nonzero cell comes
         // from the plan; the 32 slots of a tile lie in at most 32 nonzero
         // cells, searched with shuffles.
-        const unsigned long long a0 = p.tile_nz[base >> 5];
+        const unsigned long long a0 = tile_nz[base >> 5];
         const unsigned long long idx = a0 + lane;
-        const unsigned long long st = idx < nz ? p.nz_start[idx] : ~0ull;
-        const uint32_t cw = idx < nz ? p.nz_cell[idx] : 0u;
+        const unsigned long long st = idx < nz ? nz_start[idx] : ~0ull;
+        const uint32_t cw = idx < nz ? nz_cell[idx] : 0u;
         int lo = 0, hi = 31;  // last i with start_i <= slot
 #pragma unroll
         for (int it = 0; it < 5; ++it) {
@@ -1079,14 +1178,22 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
           if (sv <= slot) lo = mid; else hi = mid - 1;
         }
         const uint32_t cwl = __shfl_sync(kFull, cw, lo);
+        if constexpr (TR) {  // the tangent particles of a cell share its tau
+          const double th = idx < nz ? p.tnz_tau[2 * idx] : 0.0;
+          const double tw = idx < nz ? p.tnz_tau[2 * idx + 1] : 0.0;
+          tau.th = __shfl_sync(kFull, th, lo);
+          tau.tw = __shfl_sync(kFull, tw, lo);
+        }
         if (act) {
           int cell = (int)(cwl & 0x7FFFFFFFu);
           if (p.ninst > 1) {
             inst = (int)((unsigned)cell / (unsigned)p.nhi);
             cell -= inst * p.nhi;
           }
-          pid = p.regen_base | slot;
-          if (p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | (slot - p.inst_slot[inst]);
+          // tangent particles: ids (epoch << 40) | (instance << 32) | 2^31 | j
+          const unsigned long long tag = TR ? 0x80000000ull : 0ull;
+          pid = p.regen_base | tag | slot;
+          if (p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | tag | (slot - islot[inst]);
           const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
           if constexpr (P::D == 1) {
             int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
@@ -1117,10 +1224,14 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
             k.c[0] = in_cell<P>(P::add(p.kmin, P::mul(P::add((T)ik1, u[2]), p.dk)), p.kmin, p.inv_dk, ik1);
             k.c[P::D - 1] = in_cell<P>(P::add(p.kmin, P::mul(P::add((T)ik2, u[3]), p.dk)), p.kmin, p.inv_dk, ik2);
           }
-          w = (cwl >> 31) ? (T)-1 : (T)1;
+          w = TR ? (T)0 : ((cwl >> 31) ? (T)-1 : (T)1);
         }
       } else {
         if (act) {
+          if constexpr (P::TG) {
+            tau.th = p.tan[slot];
+            tau.tw = p.tan[p.capacity + slot];
+          }
 #pragma unroll
           for (int d = 0; d < P::D; ++d) {
             x.c[d] = p.x[d * p.capacity + slot];
@@ -1139,7 +1250,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
           }
         }
       }
-      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst);
+      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst, tau);
     }
   }
 
@@ -1198,6 +1309,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T>& ip = p.inst[inst];
         SEntry<P> s;
+        static_cast<TanField<P::TG>&>(s) = static_cast<const TanField<P::TG>&>(e);
         s.pid = e.pid;
         s.xo = e.x;
         s.to = (T)0;
@@ -1207,7 +1319,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         s.t = Draw<P>::first(p, ip, e.pid, l, (T)0, true, s.st);
         if (s.t < p.dt) {
           const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w,
-                                         s.st, l, 0u, s.t, later);
+                                         s.st, l, 0u, s.t, later, s);
           s.t = P::add(s.t, gap);
           if (s.t < p.dt) {
             s.j = 1u | kRootFlag;
@@ -1247,13 +1359,13 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
         const int l = ent_l(s.l), inst = ent_inst(s.l);
         const Inst<T>& ip = p.inst[inst];
         const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
-                                       l, j, s.t, later);
+                                       l, j, s.t, later, s);
         s.t = P::add(s.t, gap);
         if (s.t < p.dt) {
           s.j = (j + 1) | (s.j & kRootFlag);
           defer<P>(p, wc, level + 1, s);
         } else if (!(s.j & kRootFlag)) {
-          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l);
+          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s);
         }
       }
     }
@@ -1398,6 +1510,14 @@ KP<P> make_kp(const Ctx* c) {
   p.tab.dkap = (T)c->tab_dkap;
   p.tab.ny = c->tab_ny;
   p.tab.nkap = c->tab_nkap;
+  p.dgrid[0] = c->dgrid[0];
+  p.dgrid[1] = c->dgrid[1];
+  p.tan = (double*)c->buf.tangent;
+  p.tnz_cell = c->tnz_cell;
+  p.tnz_start = c->tnz_start;
+  p.tnz_tau = c->tnz_tau;
+  p.ttile_nz = c->ttile_nz;
+  p.tinst_slot = c->tinst_slot;
   p.regen_base = (unsigned long long)c->epoch << 40;
   p.x = (T*)c->buf.x;
   p.k = (T*)c->buf.k;
@@ -1480,6 +1600,9 @@ cudaError_t events(Ctx* c, const KP<P>& p) {
 
 template <class P, int DST>
 cudaError_t flight_src(Ctx* c, const KP<P>& p, int src) {
+  if constexpr (P::TG) {
+    if (src == SRC_TREGEN) return flight<P, SRC_TREGEN, DST>(c, p);
+  }
   switch (src) {
     case SRC_ARRAY: return flight<P, SRC_ARRAY, DST>(c, p);
     case SRC_REGEN: return flight<P, SRC_REGEN, DST>(c, p);
@@ -1491,7 +1614,7 @@ template <class P>
 cudaError_t flight_any(Ctx* c, const KP<P>& p, int src, int dst) {
   if (dst == DST_ARRAY) return flight_src<P, DST_ARRAY>(c, p, src);
   if (dst == DST_BIN1) return flight_src<P, DST_BIN1>(c, p, src);
-  if constexpr (P::D == 1) {  // weighted sinks: sp2 and its observables (2D only)
+  if constexpr (P::D == 1 && !P::TG) {  // weighted sinks: sp2 and its observables (2D only)
     if (dst == DST_BIN2) return flight_src<P, DST_BIN2>(c, p, src);
     return flight_src<P, DST_WSUM>(c, p, src);
   }
@@ -1502,7 +1625,7 @@ template <class P>
 cudaError_t events_any(Ctx* c, const KP<P>& p, int dst) {
   if (dst == DST_ARRAY) return events<P, DST_ARRAY>(c, p);
   if (dst == DST_BIN1) return events<P, DST_BIN1>(c, p);
-  if constexpr (P::D == 1) {
+  if constexpr (P::D == 1 && !P::TG) {
     if (dst == DST_BIN2) return events<P, DST_BIN2>(c, p);
     return events<P, DST_WSUM>(c, p);
   }
@@ -1566,6 +1689,9 @@ struct DriverImpl {
       v.sig_k = (T)q.sig_k;
       v.xc = (T)q.xc;
       v.well = q.H < 0.0;
+      v.gH = q.H != 0.0 ? 1.0 / q.H : 0.0;
+      v.gw0 = 1.0 / q.w;
+      v.gw1 = 4.0 * q.w;
       v.p_hi = q.p_any * (1.0 + 1e-9) + 1e-300;
       v.p_any_f = (float)q.p_any;
       const double sc = q.p_any * 65536.0;
@@ -1624,6 +1750,11 @@ struct DriverImpl {
       e = flight_any<P>(c, p, r == 0 ? src : (int)SRC_QUEUE, dst);
       if (r == 0) prof_end(c);
       if (e != cudaSuccess) return e;
+      if (P::TG && r == 0 && src == SRC_REGEN) {
+        // the tangent particles of the same histogram join the first wave
+        // (the same round: they continue the round's queue counts)
+        if ((e = flight_any<P>(c, p, SRC_TREGEN, dst)) != cudaSuccess) return e;
+      }
       if (L > l0) {
         if ((e = launch_zero(c, p.fcnt_out, cnt_bytes)) != cudaSuccess) return e;
         if ((e = launch_zero(c, c->dcnt, (size_t)(c->passes + 2) * cnt_bytes)) != cudaSuccess)
@@ -1642,6 +1773,7 @@ struct DriverImpl {
     KP<P> p = make_kp<P>(c);
     p.grid = grid;
     p.count_ledger = count_ledger;
+    if (!count_ledger) p.dgrid[0] = p.dgrid[1] = nullptr;  // observables only
     return flight_any<P>(c, p, SRC_ARRAY, dst);
   }
 
@@ -1650,7 +1782,11 @@ struct DriverImpl {
                                  (unsigned long long)c->step);
     if (e != cudaSuccess) return e;
     KP<P> p = make_kp<P>(c);
-    return flight<P, SRC_REGEN, DST_ARRAY>(c, p);
+    e = flight<P, SRC_REGEN, DST_ARRAY>(c, p);
+    if constexpr (P::TG) {  // the tangent particles, appended
+      if (e == cudaSuccess) e = flight<P, SRC_TREGEN, DST_ARRAY>(c, p);
+    }
+    return e;
   }
 
   // Build the 4D model's tables from A (host, 2 x nkap) into the scratch and

@@ -21,7 +21,7 @@ constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // launch bound of
 constexpr int kMaxPasses = WBRW_TUNE_PASSES_MAX;
 constexpr int kMaxLevels = kMaxPasses + 2;
 constexpr int kMaxInst = WBRW_MAX_INSTANCES;  // instances of a batch (8 id bits)
-constexpr int kInstBytes = 64;                // one per-instance record on the device
+constexpr int kInstBytes = 128;               // one per-instance record on the device
 constexpr size_t kInstTabBytes = (size_t)kMaxInst * kInstBytes;
 // device tables: physics records, initial-sampling records, first slots,
 // N_alpha (double) and the transmissions read-out, in this order; the host
@@ -29,9 +29,15 @@ constexpr size_t kInstTabBytes = (size_t)kMaxInst * kInstBytes;
 constexpr size_t kTabSlotOff = 2 * kInstTabBytes;
 constexpr size_t kTabNaOff = kTabSlotOff + (size_t)(kMaxInst + 1) * 8;
 constexpr size_t kTabTransOff = kTabNaOff + (size_t)kMaxInst * 8;
-constexpr size_t kTabBytes = kTabTransOff + (size_t)kMaxInst * 8;
+// tangent mode: the first slot of each instance's tangent particles, and the
+// read-out of (dT/dH, dT/dw) per instance
+constexpr size_t kTabTSlotOff = kTabTransOff + (size_t)kMaxInst * 8;
+constexpr size_t kTabGradOff = kTabTSlotOff + (size_t)(kMaxInst + 1) * 8;
+constexpr size_t kTabBytes = kTabGradOff + (size_t)kMaxInst * 16;
 
-enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2 };
+// SRC_TREGEN: the tangent mode's sign-0 particles regenerated from the
+// tangent histogram (a second plan).
+enum Src { SRC_ARRAY = 0, SRC_REGEN = 1, SRC_QUEUE = 2, SRC_TREGEN = 3 };
 enum Dst { DST_ARRAY = 0, DST_BIN1 = 1, DST_BIN2 = 2, DST_WSUM = 3 };
 
 // device error bits (Counters::err)
@@ -61,6 +67,8 @@ struct Counters {
   unsigned long long boot_R[2];    // total residual (Q0.32) per side
   long long obs_total;             // observables: transmission numerator
   unsigned long long per_regen_base;  // the chunk's regeneration id base (epoch << 40)
+  unsigned long long tan_total;       // tangent particles implied by the tangent histogram
+  unsigned long long tan_nz;          // cells carrying tangent weight
   int per_l0;                         // the chunk's first interval
   int err;
   int pad[2];
@@ -114,6 +122,16 @@ struct Ctx {
   void* tab_xi[2];                // ny values of type T
   void* tab_cdf[2];               // ny x nkap values of type T
   unsigned long long* tab_xmax;   // the largest xi of each type
+  // tangent mode (likelihood-ratio d/dH, d/dw; sp1, 2D)
+  int tangent;
+  long long tquantum;             // tangent particles carry |tau| <= tquantum 2^-32
+  long long* dgrid[2];            // tangent histogram (H, w) of all instances, 2^-32 units
+  uint32_t* tnz_cell;             // the tangent plan: cells with tangent weight,
+  unsigned long long* tnz_start;  //   their first tangent slot,
+  double* tnz_tau;                //   (tau_H, tau_w) of each of their particles,
+  uint32_t* ttile_nz;             //   and the first plan entry of each 32-slot tile
+  unsigned long long* tinst_slot; // first tangent slot of each instance (+ total)
+  double* inst_grad;              // read-out (dT/dH, dT/dw) per instance (device)
   // scratch carve-up
   Counters* cnt;
   unsigned long long* cpid;
@@ -204,11 +222,18 @@ const Driver* driver_fp64();
 const Driver* driver_fp32();
 const Driver* driver_fp64_4d();
 const Driver* driver_fp32_4d();
+const Driver* driver_fp64_grad();
+const Driver* driver_fp32_grad();
 
 // Precision-independent launches (wbrw_common.cu).
 cudaError_t launch_setup(Ctx*, int op, unsigned long long a,
                          unsigned long long b);
 cudaError_t launch_scan_cells(Ctx*, const int* grid);
+// The tangent plan from the tangent histogram (tangent mode).
+cudaError_t launch_scan_tangent(Ctx*);
+// (dT/dH, dT/dw) of every instance from the tangent histogram, into
+// c->inst_grad.
+cudaError_t launch_transmission_gradients(Ctx*);
 cudaError_t launch_boot(Ctx*);
 // Observables of instance `inst` from the counts / Q1.31 weight sums of all
 // instances (one of the two is NULL).

@@ -36,7 +36,7 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
            "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune",
-           "wbrw_init4d")
+           "wbrw_init4d", "wbrw_transmission_gradients")
 TUNE_BPS_MAX, TUNE_PASSES_MAX = 3, 6
 MAX_INSTANCES = 256
 
@@ -52,7 +52,8 @@ class Config(ctypes.Structure):
                 ("resample_every", ctypes.c_int),
                 ("n_alpha", ctypes.c_longlong),
                 ("seed", ctypes.c_ulonglong),
-                ("table_ny", ctypes.c_int), ("table_nkappa", ctypes.c_int)]
+                ("table_ny", ctypes.c_int), ("table_nkappa", ctypes.c_int),
+                ("tangent", ctypes.c_int), ("tangent_quantum", ctypes.c_double)]
 
 
 class Potential(ctypes.Structure):
@@ -78,7 +79,8 @@ class Buffers(ctypes.Structure):
                 ("grid", ctypes.c_void_p), ("grid_cells", ctypes.c_longlong),
                 ("scratch", ctypes.c_void_p), ("scratch_bytes", ctypes.c_size_t),
                 ("event_log", ctypes.c_void_p),
-                ("event_log_capacity", ctypes.c_longlong)]
+                ("event_log_capacity", ctypes.c_longlong),
+                ("tangent", ctypes.c_void_p)]
 
 
 EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"), ("pid_minus", "<u8"),
@@ -116,6 +118,8 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(Buffers), LL, P, ctypes.c_double, P, P,
                               ctypes.POINTER(P)]
     L.wbrw_init4d.restype = I
+    L.wbrw_transmission_gradients.argtypes = [P, P]
+    L.wbrw_transmission_gradients.restype = I
     L.wbrw_batch_scratch_bytes.argtypes = [ctypes.POINTER(Config), I, LL]
     L.wbrw_batch_scratch_bytes.restype = ctypes.c_size_t
     L.wbrw_batch_init.argtypes = [ctypes.POINTER(Config), I, ctypes.POINTER(Instance),
@@ -221,6 +225,13 @@ def wbrw_transmissions(ctx, ninst):
 
 def wbrw_particle_instances(ctx, inst_dev_ptr):
     _check(ctx, load().wbrw_particle_instances(ctx, ctypes.c_void_p(inst_dev_ptr)))
+
+
+def wbrw_transmission_gradients(ctx, ninst):
+    """(dT/dH, dT/dw) per instance, shape (ninst, 2)."""
+    out = np.empty(2 * ninst, np.float64)
+    _check(ctx, load().wbrw_transmission_gradients(ctx, out.ctypes.data))
+    return out.reshape(ninst, 2)
 
 
 def wbrw_step(ctx, nsteps):
@@ -354,7 +365,8 @@ class Simulation:
         self.cfg = Config(self.dim, prec, strat, wl["hbar"], wl["mass"], wl["dt"], wl["gamma0"],
                           wl["nx"], wl["nk"], wl["xmin"], wl["xmax"], wl["kmin"], wl["kmax"],
                           wl["resample_every"], int(wl["n_alpha"]), int(wl["seed"]),
-                          int(wl.get("ny", 0)), int(wl.get("nkap", 0)))
+                          int(wl.get("ny", 0)), int(wl.get("nkap", 0)),
+                          1 if wl.get("tangent") else 0, float(wl.get("tquantum", 1.0)))
         dev = torch.device("cuda", torch.cuda.current_device())
         fdt = torch.float64 if prec == FP64 else torch.float32
         self.nx, self.nk = wl["nx"], wl["nk"]
@@ -364,6 +376,8 @@ class Simulation:
         self.k = torch.empty(nd * self.capacity, dtype=fdt, device=dev)
         self.s = torch.empty(self.capacity, dtype=torch.int8, device=dev)
         self.w = torch.empty(self.capacity, dtype=fdt, device=dev) if strat == SP2_BOOTSTRAP else None
+        self.tan = (torch.zeros(2 * self.capacity, dtype=torch.float64, device=dev)
+                    if wl.get("tangent") else None)
         self.cells = (self.nx * self.nx * self.nk * self.nk if self.dim == 4
                       else self.nx * self.nk)
         cells = self.ninst * self.cells
@@ -380,7 +394,7 @@ class Simulation:
                             self.capacity, self.grid.data_ptr(), cells,
                             self.scratch.data_ptr(), nbytes,
                             self.log.data_ptr() if self.log is not None else None,
-                            event_log)
+                            event_log, self.tan.data_ptr() if self.tan is not None else None)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         # the buffers were made on torch's current stream: the context's
         # stream must see them finished
@@ -452,6 +466,17 @@ class Simulation:
         s = self.s[:n].cpu().numpy()
         w = self.w[:n].cpu().numpy() if self.w is not None else s.astype(x.dtype)
         return x, k, s, w, pid
+
+    def transmission_gradients(self):
+        """(dT/dH, dT/dw) per instance after a resampling (tangent mode)."""
+        g = wbrw_transmission_gradients(self.ctx, self.ninst)
+        return g if self.ninst > 1 else g[0]
+
+    def tangents(self):
+        """(tau_H, tau_w) of the materialised particles (tangent mode)."""
+        n = wbrw_particles(self.ctx)
+        c = self.capacity
+        return self.tan[:n].cpu().numpy(), self.tan[c:c + n].cpu().numpy()
 
     def grid_counts(self):
         self.stream.synchronize()

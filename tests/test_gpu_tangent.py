@@ -1,0 +1,142 @@
+"""GPU parity of the tangent mode (likelihood-ratio dT/dH, dT/dw).
+
+FP64: the same tangent rules and the same operation order as the oracle's
+tangent mode, so tangent weights agree to 1e-12 relative, the fixed-point
+tangent histogram and therefore the gradients exactly, and the signed
+particles are bit for bit those of the run without tangents.  FP32: the
+gradient of the transmission against finite differences of the TDSE, with
+the instances of a batch as independent replicas.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from helpers import make_oracle
+from oracle import refs
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-12
+WL = workloads.scaled(workloads.COLLISION_2D, n_alpha=4100, gamma0=2.0, nx=100, nk=64,
+                      xmin=-25.0, xmax=25.0, kmin=-3.2, kmax=3.2, resample_every=5,
+                      tangent=True, tquantum=0.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_02121_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    return torch
+
+
+def sim_of(wl, capacity=800_000, **kw):
+    from paper_1709_02121_gb300 import Simulation
+    return Simulation(wl, capacity, **kw)
+
+
+def oracle_of(wl):
+    o = make_oracle(wl)
+    o.init_gauss(wl["n_alpha"], wl["x0"], wl["sigma_x"], wl["k0"])
+    return o
+
+
+def close(a, b):
+    return np.all(np.abs(a - b) <= REL * np.maximum(1.0, np.abs(b)))
+
+
+def assert_same(sim, o):
+    x, k, s, w, pid = sim.particles()
+    tH, tw = sim.tangents()
+    ox, ok_, ow, opid = o.particles()
+    oH, ow_ = o.tangent()
+    assert len(pid) == len(opid)
+    a, b = np.argsort(pid, kind="stable"), np.argsort(opid, kind="stable")
+    assert np.array_equal(pid[a], opid[b])
+    assert close(x[a], ox[b]) and close(k[a], ok_[b])
+    assert np.array_equal(s[a].astype(np.float64), ow[b])
+    assert close(tH[a], oH[b]) and close(tw[a], ow_[b])
+    return np.abs(tH).max()
+
+
+def test_steps_carry_the_oracles_tangents():
+    sim, o = sim_of(WL), oracle_of(WL)
+    sim.step(7)
+    o.step(7)
+    assert assert_same(sim, o) > 1.0
+
+
+def test_fused_schedule_gradients_match_the_oracle():
+    sim, o = sim_of(WL), oracle_of(WL)
+    for period in range(3):
+        sim.run(5)
+        o.step(5)
+        o.annihilate()
+        assert np.array_equal(sim.grid_counts(), o.grid()), period
+        g = sim.transmission_gradients()
+        assert np.array_equal(g, o.transmission_gradient()), (period, g, o.transmission_gradient())
+    # the regenerated set, tangent particles included, then two more steps
+    assert_same(sim, o)
+    sim.run(2)
+    o.step(2)
+    assert_same(sim, o)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_signed_particles_are_those_of_the_plain_run(gpu, precision):
+    a = sim_of(workloads.scaled(WL, precision=precision, tangent=False))
+    b = sim_of(workloads.scaled(WL, precision=precision), stream=gpu.cuda.Stream())
+    b.graph(True)
+    for _ in range(4):
+        a.run(5)
+        b.run(5)
+        assert np.array_equal(a.grid_counts(), b.grid_counts())
+    assert a.counters()["events"] < b.counters()["events"]   # tangent particles branch too
+
+
+def test_batch_instances_match_the_oracle():
+    from paper_1709_02121_gb300 import Batch
+    insts = [dict(H=1.0, w=1.0, x0=-3.0, sigma_x=1.0, k0=1.5, n_init=3000, n_alpha=3000,
+                  gamma0=2.0),
+             dict(H=1.6, w=0.6, x0=-4.0, sigma_x=1.2, k0=1.8, n_init=1200, n_alpha=1200,
+                  gamma0=2.0)]
+    b = Batch(WL, insts, 400_000)
+    b.run(10)
+    g = b.transmission_gradients()
+    for i, v in enumerate(insts):
+        o = make_oracle(WL, H=v["H"], w=v["w"], n_alpha=v["n_alpha"], instance=i)
+        o.init_gauss(v["n_init"], v["x0"], v["sigma_x"], v["k0"])
+        for _ in range(2):
+            o.step(5)
+            o.annihilate()
+        assert np.array_equal(b.grid_counts()[i], o.grid())
+        assert np.array_equal(g[i], o.transmission_gradient()), i
+
+
+def test_fp32_gradient_matches_the_schroedinger_equation():
+    # 24 instances of the same problem as independent replicas; t = 2 with
+    # one resampling; dT/dH and dT/dw against central differences of the TDSE
+    from paper_1709_02121_gb300 import Batch
+    wl = workloads.scaled(workloads.COLLISION_2D, precision="fp32", gamma0=2.0, w=0.5,
+                          resample_every=10, tangent=True)
+    n = 40_000
+    insts = [dict(H=1.0, w=0.5, x0=wl["x0"], sigma_x=wl["sigma_x"], k0=wl["k0"], n_init=n,
+                  n_alpha=n, gamma0=2.0)] * 24
+    b = Batch(wl, insts, 24 * n * 6)
+    b.run(20)
+    g = b.transmission_gradients()
+
+    def T_tdse(H, w):
+        V = refs.gauss_potential(H, w, 0.0)
+        x, rho = refs.tdse_density(V, wl["x0"], wl["sigma_x"], wl["k0"], 2.0, L=80.0, n=4096,
+                                   dt=2e-3)
+        return refs.bin_density(x, rho, np.array([0.0, 40.0 - 1e-9]))[0]
+    d = 1e-3
+    ref = [(T_tdse(1.0 + d, 0.5) - T_tdse(1.0 - d, 0.5)) / (2 * d),
+           (T_tdse(1.0, 0.5 + d) - T_tdse(1.0, 0.5 - d)) / (2 * d)]
+    for c in range(2):
+        m, se = g[:, c].mean(), g[:, c].std(ddof=1) / np.sqrt(len(g))
+        assert abs(m - ref[c]) < 4.0 * se + 0.02 * abs(ref[c]), (c, m, se, ref[c])
