@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2"])
     ap.add_argument("--workload", default="gauss2d_fp32_n1e8",
                     choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5", "batch2d_fp32_256",
-                             "he4d_fp32_n5e7"])
+                             "he4d_fp32_n5e7", "grad2d_fp32_64"])
+    ap.add_argument("--group", type=int, default=4,
+                    help="differentiation workload: parameter points per batch")
     ap.add_argument("--n-scale", type=float, default=1.0,
                     help="batched workload: scale every instance's particle count")
     ap.add_argument("--no-plain", action="store_true",
@@ -65,6 +67,8 @@ def parse():
 
 
 def workload(args):
+    if args.workload == "grad2d_fp32_64":
+        return workloads.scaled(workloads.GRAD_2D_FP32_64)
     if args.workload == "batch2d_fp32_256":
         return workloads.scaled(workloads.BATCH_2D_FP32_256)
     if args.workload == "he4d_fp32_n5e7":
@@ -518,6 +522,111 @@ def autotune(sim, args):
             "period_ms": [[round(float(v), 4) for v in row] for row in table]}
 
 
+def ours_grad(args, spec):
+    """The differentiation workload: T(H, w) and its likelihood-ratio
+    derivatives for a batch of parameter points.  Times the forward batch
+    (no tangents) and the gradient batch (tangent mode, the replay that
+    autograd's backward runs) on the same points and periods, and reports
+    the cost of the gradient against central finite differences, which need
+    four forward runs per point for two parameters."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1709_02121_gb300 import build
+    build.build()
+    from paper_1709_02121_gb300 import Batch, wbrw
+
+    wl = workloads.scaled(spec, seed=spec["seed"] + rank)
+    pts = workloads.grad_points(wl)
+    # a group spread over the parameter square (the sweep runs 64 / group
+    # such batches one after another)
+    idx = np.linspace(0, len(pts) - 1, args.group).round().astype(int)
+    pts = [pts[i] for i in idx]
+    n = max(1, int(round(wl["n_per_point"] * args.n_scale)))
+    insts = [dict(H=h, w=v, xc=wl["xc"], x0=wl["x0"], sigma_x=wl["sigma_x"], k0=wl["k0"],
+                  n_init=n, n_alpha=n) for h, v in pts]
+    cap = int(args.capacity_factor * n * len(insts)) + (1 << 20)
+    P = wl["resample_every"]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def arm(tangent):
+        b = Batch(dict(wl, tangent=tangent), insts, cap, stream=torch.cuda.Stream())
+        stream = b.stream
+        if not args.no_graph:
+            b.graph(True)
+        for _ in range(args.warmup):
+            b.run(P)
+        barrier()
+        c0 = b.counters()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        clocks = Clocks(local)
+        clocks.start()
+        for i in range(args.steps):
+            flush.fill_(i)
+            stream.wait_stream(torch.cuda.current_stream())
+            ev[2 * i].record(stream)
+            b.run(P)
+            ev[2 * i + 1].record(stream)
+        barrier()
+        clk = clocks.stop()
+        c1 = b.counters()
+        t_ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps))
+        T = b.transmissions()
+        g = b.transmission_gradients() if tangent else None
+        res = {"t_ms": t_ms, "psteps": c1["particle_steps"] - c0["particle_steps"],
+               "launches": c1["launches"] - c0["launches"], "live": c1["live"], "T": T,
+               "grad": g, "clk": clk}
+        b.close()
+        del b
+        torch.cuda.empty_cache()
+        return res
+
+    fwd = arm(False)
+    bwd = arm(True)
+    if not np.array_equal(fwd["T"], bwd["T"]):
+        raise RuntimeError("the tangent run did not reproduce the forward run")
+    t_max, ps_all, _ = reduce_over_ranks(ws, bwd["t_ms"], bwd["psteps"], 0.0, "cuda")
+    if rank == 0:
+        value = ps_all / (t_max / 1e3)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 tangents",
+                "data": "synthetic",
+                "config": {"workload": wl["name"], "points_in_batch": len(insts),
+                           "points": [[round(h, 4), round(v, 4)] for h, v in pts],
+                           "particles_per_point": n, "grid": [wl["nx"], wl["nk"]],
+                           "dt": wl["dt"], "intervals_per_step": P, "strategy": "sp1",
+                           "precision": "fp32 state, fp64 tangent weights",
+                           "cuda_graphs": not args.no_graph,
+                           "l2": "flushed (512 MiB write) between timed steps",
+                           "parallelism": "replicas x%d" % ws},
+                "e2e": None, "gpu_launches": bwd["launches"], "clocks": bwd["clk"],
+                "particle_steps": bwd["psteps"],
+                "note": "value: the gradient run (tangent mode), whose particle-steps include "
+                        "the sign-0 tangent particles",
+                "forward": {"value": fwd["psteps"] / (fwd["t_ms"] / 1e3), "unit": UNIT,
+                            "ms_per_step": fwd["t_ms"] / args.steps},
+                "gradient_cost_vs_forward": bwd["t_ms"] / fwd["t_ms"],
+                "lr_speedup_vs_central_differences": 4.0 * fwd["t_ms"] / bwd["t_ms"],
+                "T": [round(float(x), 6) for x in bwd["T"]],
+                "dT_dH": [round(float(x), 6) for x in bwd["grad"][:, 0]],
+                "dT_dw": [round(float(x), 6) for x in bwd["grad"][:, 1]]}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def reduce_over_ranks(ws, t_ms, psteps, e2e_value, device):
     """Whole-job numbers of the replicas: the slowest rank's time, and the
     particle-steps and end-to-end rates of all ranks summed."""
@@ -580,6 +689,8 @@ def main():
         reference_arm(args, wl)
     elif args.workload == "batch2d_fp32_256":
         ours_batch(args, wl)
+    elif args.workload == "grad2d_fp32_64":
+        ours_grad(args, wl)
     else:
         ours(args, wl)
 

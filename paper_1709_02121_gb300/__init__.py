@@ -7,7 +7,7 @@ offspring compaction, and resampling by annihilation (sp1) or by the signed
 bootstrap filter (sp2).  All of it runs in hand-written CUDA kernels behind
 the C ABI of include/wbrw.h; ``wbrw`` is its ctypes binding.
 """
-from . import wbrw  # noqa: F401
+from . import grad, wbrw  # noqa: F401
 from .wbrw import Batch, Simulation, Simulation4, WbrwError, load  # noqa: F401
 
-__all__ = ["wbrw", "Batch", "Simulation", "Simulation4", "WbrwError", "load"]
+__all__ = ["grad", "wbrw", "Batch", "Simulation", "Simulation4", "WbrwError", "load"]

@@ -110,3 +110,29 @@ HE_4D_FP32_5E7 = dict(
     precision="fp32", strategy="sp1", seed=0, hbar=1.0, mass=1.0,
     gamma0=0.0, H=2.0, w=1.0,
 )
+
+
+# Differentiation, batched: the transmission T(H, w) of the 2D Gaussian
+# barrier at t = 20 and its likelihood-ratio derivatives, at 64 parameter
+# points (an 8 x 8 grid over H in [0.5, 2], w in [0.5, 2]) with 1e7
+# particles each; FP32 particles with FP64 tangent weights; resampling (and
+# the checkpoint of the state) every 16 intervals of 0.025 (0.05 would let
+# the particle count grow about 8-fold between resamplings at H = 2); the
+# packet and the 240 x 128 grid of the 2D workloads.
+GRAD_2D_FP32_64 = dict(
+    name="grad2d_fp32_64x1e7_240x128",
+    H_points=(0.5, 2.0, 8), w_points=(0.5, 2.0, 8), n_per_point=10_000_000,
+    H=1.0, w=1.0, xc=0.0, x0=-15.0, sigma_x=2.5, k0=1.5,
+    n_alpha=10_000_000, dt=0.025, steps=800, resample_every=16,
+    nx=240, nk=128, xmin=-60.0, xmax=60.0, kmin=-6.4, kmax=6.4,
+    precision="fp32", strategy="sp1", seed=0, hbar=1.0, mass=1.0,
+    gamma0=0.0, tangent=True, tquantum=1.0,
+)
+
+
+def grad_points(spec: dict) -> list:
+    """The (H, w) parameter points of a differentiation workload, H-major."""
+    import numpy as np
+    Hs = np.linspace(*spec["H_points"])
+    ws = np.linspace(*spec["w_points"])
+    return [(float(h), float(v)) for h in Hs for v in ws]
