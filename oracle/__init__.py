@@ -60,6 +60,11 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Comp(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("om", ctypes.c_double),
+                ("ph", ctypes.c_double), ("w", ctypes.c_double), ("xc", ctypes.c_double)]
+
+
 class _Config(ctypes.Structure):
     _fields_ = [("hbar", ctypes.c_double), ("mass", ctypes.c_double),
                 ("dt", ctypes.c_double), ("gamma0", ctypes.c_double),
@@ -72,7 +77,8 @@ class _Config(ctypes.Structure):
                 ("n_alpha", ctypes.c_longlong),
                 ("seed", ctypes.c_ulonglong),
                 ("instance", ctypes.c_int),
-                ("tangent", ctypes.c_int), ("tquantum", ctypes.c_longlong)]
+                ("tangent", ctypes.c_int), ("tquantum", ctypes.c_longlong),
+                ("ncomp", ctypes.c_int), ("comp", _Comp * 4)]
 
 
 EVENT_DTYPE = np.dtype([("pid", "<u8"), ("pid_plus", "<u8"),
@@ -220,10 +226,16 @@ class Oracle:
     def __init__(self, *, hbar=1.0, mass=1.0, dt=0.1, gamma0=0.0, H=1.0,
                  w=1.0, xc=0.0, nx=240, nk=128, xmin=-60.0, xmax=60.0,
                  kmin=-6.4, kmax=6.4, strategy=SP1, n_alpha=200000, seed=0,
-                 instance=0, tangent=False, tquantum=1.0):
+                 instance=0, tangent=False, tquantum=1.0, comps=()):
+        """comps: up to 4 dicts (a, b, om, ph, w, xc) of a time-dependent
+        potential sum_m (a + b cos(om t + ph)) exp(-(x-xc)^2/(2 w^2)); when
+        given, H, w, xc and gamma0 are not used."""
+        cs = (_Comp * 4)(*[_Comp(c["a"], c["b"], c["om"], c["ph"], c["w"], c["xc"])
+                           for c in comps])
         self.cfg = _Config(hbar, mass, dt, gamma0, H, w, xc, nx, nk, xmin,
                            xmax, kmin, kmax, strategy, n_alpha, seed, instance,
-                           1 if tangent else 0, int(round(tquantum * 2.0 ** 32)))
+                           1 if tangent else 0, int(round(tquantum * 2.0 ** 32)),
+                           len(comps), cs)
         self.nx, self.nk = nx, nk
         self.n_alpha = n_alpha
         self._s = lib().orc_create(ctypes.byref(self.cfg))

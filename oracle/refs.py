@@ -175,3 +175,32 @@ def tdse2_marginals(V, x0, sigma, k0, t, *, L=40.0, n=256, dt=2e-3, hbar=1.0, ma
     dens = np.abs(psi) ** 2
     dx = L / n
     return x, dens.sum(1) * dx, dens.sum(0) * dx
+
+
+def gauss_components(comps):
+    """V(x, t) = sum_m (a + b cos(om t + ph)) exp(-(x-xc)^2/(2 w^2))."""
+    def V(x, t):
+        x = np.asarray(x)
+        out = np.zeros_like(x, dtype=np.float64)
+        for c in comps:
+            out = out + (c["a"] + c["b"] * np.cos(c["om"] * t + c["ph"])) * np.exp(
+                -((x - c["xc"]) ** 2) / (2.0 * c["w"] ** 2))
+        return out
+    return V
+
+
+def tdse_density_t(Vt, x0, sigma, k0, t, *, L=200.0, n=1 << 14, dt=1e-3, hbar=1.0, mass=1.0):
+    """|psi(x,t)|^2 for a time-dependent potential Vt(x, t): Strang
+    split-step Fourier with the potential of each step taken at its midpoint."""
+    x = (np.arange(n) - n // 2) * (L / n)
+    kx = 2 * np.pi * np.fft.fftfreq(n, d=L / n)
+    psi = gaussian_psi0(x, x0, sigma, k0).astype(np.complex128)
+    nsteps = int(round(t / dt))
+    h = t / nsteps if nsteps else 0.0
+    kin = np.exp(-0.5j * hbar * kx ** 2 * h / mass)
+    for i in range(nsteps):
+        half_v = np.exp(-0.5j * Vt(x, (i + 0.5) * h) * h / hbar)
+        psi = half_v * psi
+        psi = np.fft.ifft(kin * np.fft.fft(psi))
+        psi = half_v * psi
+    return x, np.abs(psi) ** 2

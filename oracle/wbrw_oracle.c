@@ -45,6 +45,8 @@
 #define ORC_STEP_BOOT 0xFFFFFFFDu  /* residual draws of Alg. 2               */
 #define ORC_STEP_ROUND 0xFFFFFFFCu /* rounding step of Alg. 3 (sp2 only)     */
 #define ORC_DRAW_PIDS 0x80000000u  /* counter word 3 flag: offspring ids     */
+#define ORC_DRAW_COMP 0x40000000u  /* counter word 3 flag: component choice  */
+#define ORC_MAXC 4                 /* components of a time-dependent V       */
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10                                                             */
@@ -126,6 +128,12 @@ double orc_xi_gauss(double H, double w, double xc, double hbar, double x) {
 /* Configuration and state                                                   */
 /* ------------------------------------------------------------------------ */
 
+/* One Gaussian component of a time-dependent potential (Remark 1):
+ * V_m(x, t) = (a + b cos(om t + ph)) exp(-(x - xc)^2 / (2 w^2)). */
+typedef struct {
+  double a, b, om, ph, w, xc;
+} orc_comp;
+
 typedef struct {
   double hbar, mass, dt, gamma0; /* gamma0 <= 0 selects C/2                  */
   double H, w, xc;               /* Gaussian barrier                         */
@@ -137,6 +145,8 @@ typedef struct {
   int instance;                  /* id salt 0..255: a run as instance i of a batch */
   int tangent;                   /* sp1: carry the tangent weights (H, w)   */
   long long tquantum;            /* tangent particles: |tau| <= this / 2^32 */
+  int ncomp;                     /* > 0: V is the sum of comp[0..ncomp), and */
+  orc_comp comp[ORC_MAXC];       /* H, w, xc, gamma0 are not used           */
 } orc_config;
 
 typedef struct {
@@ -166,6 +176,7 @@ enum {
 typedef struct {
   orc_config c;
   double C, sig_k, gamma0, cacc, hm, dtv, dx, dk, inv_dx, inv_dk;
+  double gam_c[ORC_MAXC];  /* component rates (time-dependent potential)      */
   uint32_t key[2];
   orc_particle* p;
   long long n, cap;
@@ -213,6 +224,9 @@ orc_state* orc_create(const orc_config* c) {
       (c->strategy != 1 && c->strategy != 2) || c->n_alpha <= 0 || c->w <= 0)
     return NULL;
   if (c->tangent && (c->strategy != 1 || c->H == 0.0 || c->tquantum <= 0)) return NULL;
+  if (c->ncomp < 0 || c->ncomp > ORC_MAXC || (c->ncomp > 0 && c->tangent)) return NULL;
+  for (int m = 0; m < c->ncomp; ++m)
+    if (!(c->comp[m].w > 0)) return NULL;
   orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
   s->c = *c;
   s->C = 2.0 * fabs(c->H) / c->hbar;          /* int |Vhat(2k)| (2/(pi hbar)) dk */
@@ -220,6 +234,17 @@ orc_state* orc_create(const orc_config* c) {
   s->gamma0 = c->gamma0 > 0 ? c->gamma0 : 0.5 * s->C;
   if (s->gamma0 <= 0) s->gamma0 = 1.0;        /* H = 0: any clock works          */
   s->cacc = s->C / (2.0 * s->gamma0);         /* xi_hat/gamma0 of Remark 3       */
+  if (c->ncomp > 0) {
+    /* Remark 1: a rate at or above every component's xi at every time; the
+     * majorant C_m(t)/2 = |a + b cos(.)|/hbar <= (|a| + |b|)/hbar of each
+     * component, summed for the clock. */
+    double G = 0.0;
+    for (int m = 0; m < c->ncomp; ++m) {
+      s->gam_c[m] = (fabs(c->comp[m].a) + fabs(c->comp[m].b)) / c->hbar;
+      G += s->gam_c[m];
+    }
+    s->gamma0 = G > 0.0 ? G : 1.0;
+  }
   s->hm = c->hbar / c->mass;
   s->dtv = c->dt * s->hm;
   s->dx = (c->xmax - c->xmin) / (double)c->nx;
@@ -352,9 +377,33 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
     double u3 = orc_u53(b[0], b[1]);
     double u4 = orc_u53(b[2], b[3]);
     double z = sqrt(-2.0 * log1p(-u1)) * cos(ORC_TWO_PI * u2);
-    double kap = s->sig_k * z;
-    double sg = sin(2.0 * (xe - c->xc) * kap);
-    double f = s->cacc * fabs(sg);
+    double kap, sg, f;
+    int flip;
+    if (c->ncomp == 0) {
+      kap = s->sig_k * z;
+      sg = sin(2.0 * (xe - c->xc) * kap);
+      f = s->cacc * fabs(sg);
+      flip = c->H < 0.0 ? sg > 0.0 : sg < 0.0;
+    } else {
+      /* time-dependent V (Remark 1): component m with probability
+       * gamma_m/gamma0 (uniform uc of the draw (pid, l, COMP | j)), its
+       * height H_m(t) at the absolute time t_l + t of the event, the kick
+       * N(0, (1/(2 w_m))^2) and the acceptance |H_m(t)|/(hbar gamma_m)
+       * |sin(2 (xe - xc_m) kappa)| (the component's majorant ratio) */
+      uint32_t cc[4];
+      draw4(s, pid, l, ORC_DRAW_COMP | j, cc);
+      double v = orc_u53(cc[0], cc[1]) * s->gamma0;
+      int m = 0;
+      double acc = s->gam_c[0];
+      while (m + 1 < c->ncomp && !(v < acc)) acc += s->gam_c[++m];
+      const orc_comp* q = &c->comp[m];
+      double ta = (double)l * c->dt + t;
+      double Hm = q->a + q->b * cos(q->om * ta + q->ph);
+      kap = (1.0 / (2.0 * q->w)) * z;
+      sg = sin(2.0 * (xe - q->xc) * kap);
+      f = s->gam_c[m] > 0.0 ? fabs(Hm) / (c->hbar * s->gam_c[m]) * fabs(sg) : 0.0;
+      flip = Hm < 0.0 ? sg > 0.0 : sg < 0.0;
+    }
     int emit;
     double wc;
     if (c->strategy == 1) {
@@ -365,7 +414,7 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
       wc = w * f;
     }
     if (emit) {
-      if (c->H < 0.0 ? sg > 0.0 : sg < 0.0) kap = -kap;
+      if (flip) kap = -kap;
       uint32_t h[4];
       draw4(s, pid, l, ORC_DRAW_PIDS | j, h);
       uint64_t pid_p =

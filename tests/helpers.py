@@ -15,7 +15,8 @@ def make_oracle(wl, **over):
                          strategy=strat, n_alpha=w["n_alpha"], seed=w["seed"],
                          instance=w.get("instance", 0),
                          tangent=w.get("tangent", False),
-                         tquantum=w.get("tquantum", 1.0))
+                         tquantum=w.get("tquantum", 1.0),
+                         comps=tuple(w.get("comps", ())))
 
 
 def net_sign(w):
