@@ -209,6 +209,26 @@ wbrw_status wbrw_init4d(const wbrw_config* config, const wbrw_potential* pot,
                         double sigma_x, const double k0[2], void* cuda_stream,
                         wbrw_ctx** out);
 
+/* A time-dependent potential (Remark 1; dim 2): the sum of ncomp
+ * (1..WBRW_MAX_COMPONENTS) Gaussian components
+ *   V_m(x, t) = (a + b cos(omega t + phase)) exp(-(x - xc)^2 / (2 w^2)),
+ * t the absolute time t_l + tau of an event.  Each component's kernel is that
+ * of the Gaussian barrier with height H_m(t) (Eq. 2).  Its majorant rate is
+ * gamma_m = (|a| + |b|)/hbar >= C_m(t)/2 for every t; the life-length clock
+ * runs at Gamma = sum gamma_m (config->gamma0 is ignored).  A death picks
+ * component m with probability gamma_m/Gamma and makes a pair with
+ * probability |H_m(t)|/(hbar gamma_m) |sin(2 (x - xc) kappa)|, the kick
+ * kappa ~ N(0, (1/(2w))^2) oriented by the sign of H_m(t) sin (sp2/wp: the
+ * pair's weights carry that factor instead).  Otherwise as wbrw_init. */
+#define WBRW_MAX_COMPONENTS 4
+typedef struct {
+  double a, b, omega, phase, w, xc;
+} wbrw_component;
+
+wbrw_status wbrw_init_td(const wbrw_config* config, int ncomp, const wbrw_component* comps,
+                         const wbrw_buffers* buffers, long long n_init, double x0,
+                         double sigma_x, double k0, void* cuda_stream, wbrw_ctx** out);
+
 /* Advance nsteps intervals [t_l, t_{l+1}] (Alg. 1) without resampling and
  * leave the particles in the caller's arrays (offspring appended).  Async. */
 wbrw_status wbrw_step(wbrw_ctx* ctx, int nsteps);

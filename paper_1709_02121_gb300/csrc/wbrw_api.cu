@@ -503,7 +503,8 @@ wbrw_status build_tables(wbrw_ctx* c, char* base, const Layout& L) {
 // Create a context for ninst instances (records q, starts filled in here)
 // and enqueue the initial sampling.  Takes ownership of q.
 wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int ninst, InstHost* q,
-                   const wbrw_buffers* b, void* cuda_stream, wbrw_ctx** out) {
+                   const wbrw_buffers* b, void* cuda_stream, wbrw_ctx** out, int ncomp = 0,
+                   const Comp* comps = nullptr) {
   const long long cells = config->dim == 4
                               ? (long long)config->nx * config->nx * config->nk * config->nk
                               : (long long)config->nx * config->nk;
@@ -610,6 +611,13 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->inst_trans = (double*)(base + L.tabs + kTabTransOff);
   c->cinst = ninst > 1 ? (unsigned*)(base + L.cinst) : nullptr;
   c->obs_red = (long long*)(base + L.obs_red);
+  c->ncomp = ncomp;
+  c->comp_tab = base + L.tabs + kTabCompOff;
+  if (ncomp > 0 && cudaMemcpyAsync(c->comp_tab, comps, (size_t)ncomp * sizeof(Comp),
+                                   cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+    free_ctx(c);
+    return WBRW_ERR_CUDA;
+  }
   c->tangent = config->tangent;
   c->inst_grad = (double*)(base + L.tabs + kTabGradOff);
   c->tinst_slot = (unsigned long long*)(base + L.tabs + kTabTSlotOff);
@@ -675,6 +683,47 @@ wbrw_status wbrw_init(const wbrw_config* config, const wbrw_potential* pot,
     return WBRW_ERR_ARG;
   }
   return create(config, nullptr, 1, q, b, cuda_stream, out);
+}
+
+wbrw_status wbrw_init_td(const wbrw_config* config, int ncomp, const wbrw_component* comps,
+                         const wbrw_buffers* b, long long n_init, double x0, double sigma_x,
+                         double k0, void* cuda_stream, wbrw_ctx** out) {
+  if (!out) return WBRW_ERR_ARG;
+  *out = nullptr;
+  if (!config_ok(config, nullptr, 0) || config->dim != 2 || config->tangent) return WBRW_ERR_ARG;
+  if (ncomp < 1 || ncomp > kMaxComp || !comps) return WBRW_ERR_ARG;
+  if (!(sigma_x > 0) || !isfinite(sigma_x) || !isfinite(x0) || !isfinite(k0) || n_init < 0)
+    return WBRW_ERR_ARG;
+  Comp tab[kMaxComp];
+  memset(tab, 0, sizeof(tab));
+  double G = 0.0;
+  for (int m = 0; m < ncomp; ++m) {
+    const wbrw_component& v = comps[m];
+    if (!(v.w > 0) || !isfinite(v.w) || !isfinite(v.a) || !isfinite(v.b) || !isfinite(v.omega) ||
+        !isfinite(v.phase) || !isfinite(v.xc))
+      return WBRW_ERR_ARG;
+    tab[m].a = v.a;
+    tab[m].b = v.b;
+    tab[m].om = v.omega;
+    tab[m].ph = v.phase;
+    tab[m].sig_k = 1.0 / (2.0 * v.w);
+    tab[m].xc = v.xc;
+    tab[m].gam = (fabs(v.a) + fabs(v.b)) / config->hbar;
+    tab[m].hg = config->hbar * tab[m].gam;
+    G += tab[m].gam;
+  }
+  InstHost* q = (InstHost*)calloc(1, sizeof(InstHost));
+  if (!q) return WBRW_ERR_ARG;
+  q->w = 1.0;
+  q->x0 = x0;
+  q->sx = sigma_x;
+  q->k0 = k0;
+  q->n_init = n_init;
+  q->n_alpha = config->n_alpha;
+  q->gamma0 = G > 0.0 ? G : 1.0;  // no potential: no pair is ever made
+  q->cacc = 1.0;
+  q->p_any = -expm1(-q->gamma0 * config->dt);
+  return create(config, nullptr, 1, q, b, cuda_stream, out, ncomp, tab);
 }
 
 wbrw_status wbrw_init4d(const wbrw_config* config, const wbrw_potential* pot,

@@ -74,6 +74,7 @@ constexpr uint32_t kStepBoot = 0xFFFFFFFDu;
 constexpr uint32_t kStepRound = 0xFFFFFFFCu;
 constexpr uint32_t kDrawPids = 0x80000000u;
 constexpr uint32_t kDrawCoins = 0xC0000000u;  // FP32 16-bit coins
+constexpr uint32_t kDrawComp = 0x40000000u;   // component choice (time-dependent V)
 
 // ---------------------------------------------------------------------------
 // Precision traits.  FP64 arithmetic goes through the _rn intrinsics so that
@@ -91,6 +92,8 @@ struct F64 {
   __device__ static T flr(T a) { return floor(a); }
   __device__ static T next_dn(T a) { return nextafter(a, -CUDART_INF); }
   __device__ static T next_up(T a) { return nextafter(a, CUDART_INF); }
+  __device__ static T sn(T a) { return sin(a); }
+  __device__ static T cs(T a) { return cos(a); }
 };
 
 struct F32 {
@@ -104,6 +107,8 @@ struct F32 {
   __device__ static T flr(T a) { return floorf(a); }
   __device__ static T next_dn(T a) { return nextafterf(a, -CUDART_INF_F); }
   __device__ static T next_up(T a) { return nextafterf(a, CUDART_INF_F); }
+  __device__ static T sn(T a) { return sinf(a); }
+  __device__ static T cs(T a) { return cosf(a); }
 };
 
 // Phase-space model: precision F and D position coordinates (D = 1: the 2D
@@ -211,6 +216,8 @@ struct KP {
   using T = typename P::T;
   T dt, dtv, hm;
   Tab4<T> tab;      // 4D model only
+  const Comp* comp; // time-dependent potential: ncomp components (0: static)
+  int ncomp;
   T xmin, kmin, kmax, dx, dk, inv_dx, inv_dk;
   int nx, nk;
   float inv_nk;     // 1/nk, for cell -> (ix, ik)
@@ -494,19 +501,19 @@ struct Draw<P, true> {
     gap = __ddiv_rn(-log1p(-ug), ip.gamma0);
     return table_kick<P>(p, ip.gamma0, xe, ua, uk, uc, uj, comp, kap, prob);
   }
+  // event j of the 2D model: the standard normal z of the kick, the
+  // acceptance uniform u3 and the gap to the next event
   __device__ static void event(const KP<P>& p, const Inst<double>& ip, unsigned long long pid,
-                               int l, unsigned j, double xe, const State&, double& kap,
-                               double& sg, double& u3, double& gap) {
+                               int l, unsigned j, const State&, double& z, double& u3,
+                               double& gap) {
     const uint32_t lo = (uint32_t)pid, hi = (uint32_t)(pid >> 32);
     const uint4 a = philox_ks(p.ks, lo, hi, (uint32_t)l, 1u + 2u * j);
     const uint4 b = philox_ks(p.ks, lo, hi, (uint32_t)l, 2u + 2u * j);
     const double u1 = u53(a.x, a.y), u2 = u53(a.z, a.w);
     u3 = u53(b.x, b.y);
     const double u4 = u53(b.z, b.w);
-    const double z = __dmul_rn(__dsqrt_rn(__dmul_rn(-2.0, log1p(-u1))),
-                               cos(__dmul_rn(6.283185307179586476925286766559, u2)));
-    kap = __dmul_rn(ip.sig_k, z);
-    sg = sin(__dmul_rn(__dmul_rn(2.0, __dsub_rn(xe, ip.xc)), kap));
+    z = __dmul_rn(__dsqrt_rn(__dmul_rn(-2.0, log1p(-u1))),
+                  cos(__dmul_rn(6.283185307179586476925286766559, u2)));
     gap = __ddiv_rn(-log1p(-u4), ip.gamma0);
   }
 };
@@ -552,8 +559,8 @@ struct Draw<P, false> {
     return to + (-log1pf(-pr * u24(st.r.x))) / ip.gamma0;
   }
   __device__ static void event(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
-                               int l, unsigned j, float xe, const State& st, float& kap,
-                               float& sg, float& u3, float& gap) {
+                               int l, unsigned j, const State& st, float& z, float& u3,
+                               float& gap) {
     float u1, u2, u4;
     if (j == 0) {
       const uint4 r = st.r;
@@ -569,9 +576,7 @@ struct Draw<P, false> {
       u3 = u24(a.z);
       u4 = u24(a.w);
     }
-    const float z = sqrtf(-2.0f * log1pf(-u1)) * cospif(2.0f * u2);
-    kap = ip.sig_k * z;
-    sg = sinf(2.0f * (xe - ip.xc) * kap);
+    z = sqrtf(-2.0f * log1pf(-u1)) * cospif(2.0f * u2);
     gap = (-log1pf(-u4)) / ip.gamma0;
   }
 };
@@ -735,6 +740,38 @@ __device__ __forceinline__ void defer(const KP<P>& p, WarpCounts& wc, int level,
     set_err(p.cnt, ERR_CAP_EQUEUE);
 }
 
+// A time-dependent potential (Remark 1): component m with probability
+// gam_m/Gamma (uniform of the draw (pid, l, COMP | j)), its height
+// H_m(t_l + t) at the event's absolute time, the kick sig_k,m z and the
+// acceptance |H_m|/(hbar gam_m) |sin(2 (xe - xc_m) kappa)|, oriented by the
+// sign of H_m sin.
+template <class P>
+__device__ __forceinline__ void comp_kick(const KP<P>& p, const Inst<typename P::T>& ip,
+                                          unsigned long long pid, int l, unsigned j,
+                                          typename P::T xe, typename P::T t, typename P::T z,
+                                          typename P::T& kap, typename P::T& sg,
+                                          typename P::T& fac, bool& flip) {
+  using T = typename P::T;
+  const uint4 c = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, kDrawComp | j);
+  T uc;
+  if constexpr (P::is64) uc = u53(c.x, c.y);
+  else uc = u24(c.x);
+  const T v = P::mul(uc, ip.gamma0);
+  int m = 0;
+  T acc = (T)p.comp[0].gam;
+  while (m + 1 < p.ncomp && !(v < acc)) {
+    ++m;
+    acc = P::add(acc, (T)p.comp[m].gam);
+  }
+  const Comp& q = p.comp[m];
+  const T ta = P::add(P::mul((T)l, p.dt), t);
+  const T Hm = P::add((T)q.a, P::mul((T)q.b, P::cs(P::add(P::mul((T)q.om, ta), (T)q.ph))));
+  kap = P::mul((T)q.sig_k, z);
+  sg = P::sn(P::mul(P::mul((T)2, P::sub(xe, (T)q.xc)), kap));
+  fac = q.gam > 0.0 ? P::mul(P::div((T)fabs(Hm), (T)q.hg), (T)fabs(sg)) : (T)0;
+  flip = Hm < (T)0 ? sg > (T)0 : sg < (T)0;
+}
+
 // Event j of a segment at time t.  2D model: the kick of Remark 3, the
 // acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair.  4D model:
 // the component, thinning and tabulated kick of table_kick; the pair is
@@ -758,12 +795,20 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
   int comp = 0;
   PV<P> kp = k, km = k;
   if constexpr (P::D == 1) {
-    T sg, u3;
-    Draw<P>::event(p, ip, pid, l, j, xe.c[0], st, kap, sg, u3, gap);
-    fac = P::mul(ip.cacc, (T)fabs(sg));
+    T z, sg, u3;
+    bool flip;
+    Draw<P>::event(p, ip, pid, l, j, st, z, u3, gap);
+    if (p.ncomp == 0) {  // the static barrier: kick, |sin| ratio, orientation
+      kap = P::mul(ip.sig_k, z);
+      sg = P::sn(P::mul(P::mul((T)2, P::sub(xe.c[0], ip.xc)), kap));
+      fac = P::mul(ip.cacc, (T)fabs(sg));
+      flip = ip.well ? sg > (T)0 : sg < (T)0;
+    } else {
+      comp_kick<P>(p, ip, pid, l, j, xe.c[0], t, z, kap, sg, fac, flip);
+    }
     emit = p.strategy == 1 ? (u3 < fac) : (fac > (T)0);
     if (emit) {
-      if (ip.well ? sg > (T)0 : sg < (T)0) kap = -kap;  // orient by sign(V_W)
+      if (flip) kap = -kap;  // orient by sign(V_W)
       kp.c[0] = P::add(k.c[0], kap);
       km.c[0] = P::sub(k.c[0], kap);
     }
@@ -1510,6 +1555,8 @@ KP<P> make_kp(const Ctx* c) {
   p.tab.dkap = (T)c->tab_dkap;
   p.tab.ny = c->tab_ny;
   p.tab.nkap = c->tab_nkap;
+  p.comp = (const Comp*)c->comp_tab;
+  p.ncomp = c->ncomp;
   p.dgrid[0] = c->dgrid[0];
   p.dgrid[1] = c->dgrid[1];
   p.tan = (double*)c->buf.tangent;

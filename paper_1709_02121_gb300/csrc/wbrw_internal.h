@@ -33,7 +33,9 @@ constexpr size_t kTabTransOff = kTabNaOff + (size_t)kMaxInst * 8;
 // read-out of (dT/dH, dT/dw) per instance
 constexpr size_t kTabTSlotOff = kTabTransOff + (size_t)kMaxInst * 8;
 constexpr size_t kTabGradOff = kTabTSlotOff + (size_t)(kMaxInst + 1) * 8;
-constexpr size_t kTabBytes = kTabGradOff + (size_t)kMaxInst * 16;
+constexpr size_t kTabCompOff = kTabGradOff + (size_t)kMaxInst * 16;
+constexpr int kMaxComp = WBRW_MAX_COMPONENTS;  // components of a time-dependent V
+constexpr size_t kTabBytes = kTabCompOff + (size_t)kMaxComp * 64;
 
 // SRC_TREGEN: the tangent mode's sign-0 particles regenerated from the
 // tangent histogram (a second plan).
@@ -85,6 +87,13 @@ struct PeriodGraph {
 };
 constexpr int kMaxGraphs = 4;
 
+// One Gaussian component of a time-dependent potential, as the kernels read
+// it: V_m(x, t) = (a + b cos(om t + ph)) exp(-(x - xc)^2/(2 w^2)),
+// sig_k = 1/(2w), gam = (|a| + |b|)/hbar (its majorant rate), hg = hbar gam.
+struct Comp {
+  double a, b, om, ph, sig_k, xc, gam, hg;
+};
+
 // One instance of a batch, host FP64 (Sec. 4.2 / Remark 3 / Sec. 3.2).
 struct InstHost {
   double H, w, xc;             // potential
@@ -132,6 +141,9 @@ struct Ctx {
   uint32_t* ttile_nz;             //   and the first plan entry of each 32-slot tile
   unsigned long long* tinst_slot; // first tangent slot of each instance (+ total)
   double* inst_grad;              // read-out (dT/dH, dT/dw) per instance (device)
+  // time-dependent potential (wbrw_init_td): components on the device
+  int ncomp;
+  void* comp_tab;
   // scratch carve-up
   Counters* cnt;
   unsigned long long* cpid;

@@ -36,7 +36,7 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
            "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune",
-           "wbrw_init4d", "wbrw_transmission_gradients")
+           "wbrw_init4d", "wbrw_transmission_gradients", "wbrw_init_td")
 TUNE_BPS_MAX, TUNE_PASSES_MAX = 3, 6
 MAX_INSTANCES = 256
 
@@ -66,6 +66,11 @@ class Instance(ctypes.Structure):
     _fields_ = [("pot", Potential), ("x0", ctypes.c_double), ("sigma_x", ctypes.c_double),
                 ("k0", ctypes.c_double), ("n_init", ctypes.c_longlong),
                 ("n_alpha", ctypes.c_longlong), ("gamma0", ctypes.c_double)]
+
+
+class Component(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("omega", ctypes.c_double),
+                ("phase", ctypes.c_double), ("w", ctypes.c_double), ("xc", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -118,6 +123,10 @@ def load(path: str = LIB_PATH):
                               ctypes.POINTER(Buffers), LL, P, ctypes.c_double, P, P,
                               ctypes.POINTER(P)]
     L.wbrw_init4d.restype = I
+    L.wbrw_init_td.argtypes = [ctypes.POINTER(Config), I, P, ctypes.POINTER(Buffers), LL,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
+                               ctypes.POINTER(P)]
+    L.wbrw_init_td.restype = I
     L.wbrw_transmission_gradients.argtypes = [P, P]
     L.wbrw_transmission_gradients.restype = I
     L.wbrw_batch_scratch_bytes.argtypes = [ctypes.POINTER(Config), I, LL]
@@ -190,6 +199,18 @@ def wbrw_init4d(cfg, pot, bufs, n_init, x0, sigma_x, k0, stream_ptr):
                             x0a, sigma_x, k0a, ctypes.c_void_p(stream_ptr), ctypes.byref(ctx))
     if st != OK:
         raise WbrwError(st, "wbrw_init4d rejected its arguments")
+    return ctx
+
+
+def wbrw_init_td(cfg, comps, bufs, n_init, x0, sigma_x, k0, stream_ptr):
+    """comps: dicts with a, b, om, ph, w, xc (see include/wbrw.h)."""
+    arr = (Component * len(comps))(*[Component(c["a"], c["b"], c["om"], c["ph"], c["w"],
+                                               c["xc"]) for c in comps])
+    ctx = ctypes.c_void_p()
+    st = load().wbrw_init_td(ctypes.byref(cfg), len(comps), arr, ctypes.byref(bufs), n_init,
+                             x0, sigma_x, k0, ctypes.c_void_p(stream_ptr), ctypes.byref(ctx))
+    if st != OK:
+        raise WbrwError(st, "wbrw_init_td rejected its arguments")
     return ctx
 
 
@@ -352,8 +373,12 @@ class Simulation:
     def __init__(self, wl: dict, capacity: int, *, event_log: int = 0, stream=None):
         self._buffers(wl, capacity, event_log, stream)
         self.pot = Potential(POT_GAUSSIAN, wl["H"], wl["w"], wl["xc"])
-        self.ctx = wbrw_init(self.cfg, self.pot, self.bufs, int(wl["n_alpha"]),
-                             wl["x0"], wl["sigma_x"], wl["k0"], self.stream.cuda_stream)
+        if wl.get("comps"):   # a time-dependent potential (sum of components)
+            self.ctx = wbrw_init_td(self.cfg, list(wl["comps"]), self.bufs, int(wl["n_alpha"]),
+                                    wl["x0"], wl["sigma_x"], wl["k0"], self.stream.cuda_stream)
+        else:
+            self.ctx = wbrw_init(self.cfg, self.pot, self.bufs, int(wl["n_alpha"]),
+                                 wl["x0"], wl["sigma_x"], wl["k0"], self.stream.cuda_stream)
 
     def _buffers(self, wl, capacity, event_log, stream):
         import torch

@@ -136,3 +136,16 @@ def grad_points(spec: dict) -> list:
     Hs = np.linspace(*spec["H_points"])
     ws = np.linspace(*spec["w_points"])
     return [(float(h), float(v)) for h in Hs for v in ws]
+
+
+# 2D scattering on the time-dependent double barrier of the paper's Sec. 5
+# (Eq. tDV) with the switch on the left, as its text describes:
+# V(x, t) = 0.8 (0.5 + 0.5 cos(pi + 0.1 t)) exp(-(x+10)^2/8)
+#         + 0.8 exp(-(x-10)^2/8);
+# the packet, grid and sizes of the 1e8 2D workload, 1200 intervals of 0.05
+# (t = 60), resampling every 10.
+TDV_2D_FP32_1E8 = dict(
+    GAUSS_2D_FP32_1E8, name="tdv2d_fp32_n1e8_1200x512", steps=1200,
+    comps=(dict(a=0.4, b=0.4, om=0.1, ph=3.141592653589793, w=2.0, xc=-10.0),
+           dict(a=0.8, b=0.0, om=0.0, ph=0.0, w=2.0, xc=10.0)),
+)
