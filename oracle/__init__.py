@@ -35,6 +35,7 @@ _LIB = os.path.join(_BUILD, "libwbrw_oracle.so")
 
 SP1 = 1
 SP2 = 2
+WP = 3
 
 # counter word 2 of the reserved streams (documented in wbrw_oracle.c)
 STEP_INIT = 0xFFFFFFFF

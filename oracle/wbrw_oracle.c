@@ -139,7 +139,8 @@ typedef struct {
   double H, w, xc;               /* Gaussian barrier                         */
   int nx, nk;                    /* histogram cells in x and k               */
   double xmin, xmax, kmin, kmax; /* histogram domain = truncation domain K   */
-  int strategy;                  /* 1 = sp1 (pair generation), 2 = sp2       */
+  int strategy;                  /* 1 = sp1 (pair generation), 2 = sp2,     */
+                                 /* 3 = wp (weighted histogram)             */
   long long n_alpha;             /* sample size N_alpha of the estimator     */
   unsigned long long seed;
   int instance;                  /* id salt 0..255: a run as instance i of a batch */
@@ -221,7 +222,7 @@ static int push(orc_particle** a, long long* n, long long* cap,
 orc_state* orc_create(const orc_config* c) {
   if (c->instance < 0 || c->instance >= 256 || c->nx <= 0 || c->nk <= 0 || !(c->xmax > c->xmin) ||
       !(c->kmax > c->kmin) || c->dt <= 0 || c->hbar <= 0 || c->mass <= 0 ||
-      (c->strategy != 1 && c->strategy != 2) || c->n_alpha <= 0 || c->w <= 0)
+      (c->strategy < 1 || c->strategy > 3) || c->n_alpha <= 0 || c->w <= 0)
     return NULL;
   if (c->tangent && (c->strategy != 1 || c->H == 0.0 || c->tquantum <= 0)) return NULL;
   if (c->ncomp < 0 || c->ncomp > ORC_MAXC || (c->ncomp > 0 && c->tangent)) return NULL;
@@ -733,11 +734,45 @@ static int bootstrap(orc_state* s) {
 
 /* Resampling (Sec. 4.3): histogram, then Alg. 3.  A second call with no step
  * in between changes nothing. */
+/* wp: the weighted histogram of Eq. piecewise_constant_function, sum_i w_i
+ * over D_nu (each w in fixed point, llrint(w 2^31), so the sum is exact),
+ * then Alg. 3 with its rounding step: floor(|m|) particles plus one with
+ * probability |m| - floor(|m|), of sign sign(m), from the uniform of the
+ * draw (nu, ROUND, epoch) as for sp2. */
+static int wp_histogram(orc_state* s) {
+  long long nh = (long long)s->c.nx * s->c.nk;
+  long long* ws = (long long*)calloc((size_t)nh, sizeof(long long));
+  if (!ws) return -1;
+  for (long long i = 0; i < s->n; ++i) {
+    long long nu;
+    const orc_particle* p = &s->p[i];
+    if (cell_of(s, p->x, p->k, &nu)) {
+      ws[nu] += llrint(p->w * 2147483648.0);
+    } else {
+      if (p->w > 0) s->ledger[ORC_L_OUT_P] += 1; else if (p->w < 0) s->ledger[ORC_L_OUT_M] += 1;
+    }
+  }
+  for (long long nu = 0; nu < nh; ++nu) {
+    double m = (double)ws[nu] * (1.0 / 2147483648.0);
+    double am = fabs(m);
+    double fl = floor(am);
+    uint32_t h[4];
+    draw4(s, (uint64_t)nu, ORC_STEP_ROUND, (uint32_t)s->epoch, h);
+    double u = orc_u53(h[0], h[1]);
+    long long cnt = (long long)fl + (u < am - fl ? 1 : 0);
+    s->grid[nu] = (int)(m < 0 ? -cnt : cnt);
+  }
+  free(ws);
+  return 0;
+}
+
 int orc_annihilate(orc_state* s) {
   if (s->fresh) return 0;
   s->epoch += 1;
   if (s->c.strategy == 1) {
     bin_signed(s);
+  } else if (s->c.strategy == 3) {
+    if (wp_histogram(s)) return -1;
   } else {
     if (bootstrap(s)) return -1;
   }

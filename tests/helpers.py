@@ -7,7 +7,7 @@ import oracle
 def make_oracle(wl, **over):
     w = dict(wl)
     w.update(over)
-    strat = {"sp1": oracle.SP1, "sp2": oracle.SP2}[w["strategy"]]
+    strat = {"sp1": oracle.SP1, "sp2": oracle.SP2, "wp": oracle.WP}[w["strategy"]]
     return oracle.Oracle(hbar=w["hbar"], mass=w["mass"], dt=w["dt"],
                          gamma0=w["gamma0"], H=w["H"], w=w["w"], xc=w["xc"],
                          nx=w["nx"], nk=w["nk"], xmin=w["xmin"],
