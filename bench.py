@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2"])
     ap.add_argument("--workload", default="gauss2d_fp32_n1e8",
                     choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5", "batch2d_fp32_256",
-                             "he4d_fp32_n5e7", "grad2d_fp32_64"])
+                             "he4d_fp32_n5e7", "grad2d_fp32_64", "tdv2d_fp32_n1e8"])
     ap.add_argument("--group", type=int, default=4,
                     help="differentiation workload: parameter points per batch")
     ap.add_argument("--n-scale", type=float, default=1.0,
@@ -69,6 +69,11 @@ def parse():
 def workload(args):
     if args.workload == "grad2d_fp32_64":
         return workloads.scaled(workloads.GRAD_2D_FP32_64)
+    if args.workload == "tdv2d_fp32_n1e8":
+        wl = workloads.scaled(workloads.TDV_2D_FP32_1E8, strategy=args.strategy)
+        if args.particles:
+            wl["n_alpha"] = int(args.particles)
+        return wl
     if args.workload == "batch2d_fp32_256":
         return workloads.scaled(workloads.BATCH_2D_FP32_256)
     if args.workload == "he4d_fp32_n5e7":
@@ -161,7 +166,7 @@ def oracle_period_rate(wl, n_sample, budget_s, max_periods=None):
                           H=wl["H"], w=wl["w"], xc=wl["xc"], nx=wl["nx"], nk=wl["nk"],
                           xmin=wl["xmin"], xmax=wl["xmax"], kmin=wl["kmin"], kmax=wl["kmax"],
                           strategy=oracle.SP1 if wl["strategy"] == "sp1" else oracle.SP2,
-                          n_alpha=n_sample, seed=wl["seed"])
+                          n_alpha=n_sample, seed=wl["seed"], comps=tuple(wl.get("comps", ())))
     o.init_gauss(n_sample, wl["x0"], wl["sigma_x"], wl["k0"])
     times, psteps = [], []
     t_all = time.perf_counter()
@@ -207,6 +212,10 @@ def config_of(wl, args):
     pot = ("soft-Coulomb Z=%g a=%g ee=%g, tables %dx%d" % (wl["Z"], wl["a"], wl["lam"], wl["ny"],
                                                           wl["nkap"])
            if d4 else "gaussian H=%g w=%g" % (wl["H"], wl["w"]))
+    if wl.get("comps"):
+        pot = "time-dependent: " + " + ".join(
+            "(%g%+g cos(%g t%+.4g)) gauss(w=%g, xc=%g)" % (c["a"], c["b"], c["om"], c["ph"], c["w"],
+                                                         c["xc"]) for c in wl["comps"])
     return {"workload": wl["name"], "dim": 4 if d4 else 2, "particles": int(wl["n_alpha"]),
             "grid": [wl["nx"]] * (2 if d4 else 1) + [wl["nk"]] * (2 if d4 else 1),
             "dt": wl["dt"],

@@ -49,7 +49,11 @@ typedef enum {
   WBRW_ERR_NUMERIC = -6   /* reserved: non-finite state detected           */
 } wbrw_status;
 
-typedef enum { WBRW_SP1_PAIR = 1, WBRW_SP2_BOOTSTRAP = 2 } wbrw_strategy;
+/* WBRW_WP: weighted particles (pairs always made with weights
+ * +/- w cacc |sin|, as sp2 between its filters), resampled by the weighted
+ * histogram of Eq. piecewise_constant_function (weights summed in fixed
+ * point 2^-31) and Alg. 3 with its rounding step (sp2's rounding stream). */
+typedef enum { WBRW_SP1_PAIR = 1, WBRW_SP2_BOOTSTRAP = 2, WBRW_WP = 3 } wbrw_strategy;
 typedef enum { WBRW_FP64 = 0, WBRW_FP32 = 1 } wbrw_precision;
 typedef enum { WBRW_POT_GAUSSIAN = 0, WBRW_POT_SOFT_COULOMB_2E = 1 } wbrw_potential_kind;
 
@@ -103,7 +107,7 @@ typedef struct {
  *   x, k : positions and wavevectors, double (WBRW_FP64) or float (WBRW_FP32);
  *          dim 4: 2*capacity elements each (see wbrw_init4d)
  *   s    : signs +1 / -1 (int8)
- *   w    : signed weights (sp2 only; same type as x; NULL for sp1)
+ *   w    : signed weights (sp2 and wp; same type as x; NULL for sp1)
  *   grid : nx*nk int32 signed counts c_nu (grid_cells >= nx*nk), valid after
  *          a resampling
  *   scratch : >= wbrw_scratch_bytes(config, capacity) bytes, 256-byte aligned

@@ -53,7 +53,9 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
       c->table_nkappa > (1 << 20))
     return fail("table sizes");
   if (c->precision != WBRW_FP64 && c->precision != WBRW_FP32) return fail("precision");
-  if (c->strategy != WBRW_SP1_PAIR && c->strategy != WBRW_SP2_BOOTSTRAP) return fail("strategy");
+  if (c->strategy != WBRW_SP1_PAIR && c->strategy != WBRW_SP2_BOOTSTRAP &&
+      c->strategy != WBRW_WP)
+    return fail("strategy");
   if (!(c->hbar > 0) || !(c->mass > 0) || !(c->dt > 0)) return fail("hbar, mass and dt must be > 0");
   if (c->nx <= 0 || c->nk <= 0) return fail("nx and nk must be > 0");
   if (ninst < 0 || ninst > kMaxInst) return fail("instances must be 1..WBRW_MAX_INSTANCES");
@@ -251,6 +253,10 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
     WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
     if (c->tangent) WBRW_TRY(c, zero_tangent(c), "zero tangent");
     WBRW_TRY(c, d->bin(c, DST_BIN1, c->buf.grid, 1), "bin");
+  } else if (c->cfg.strategy == WBRW_WP) {
+    WBRW_TRY(c, launch_zero(c, c->tmp_wsum, (size_t)c->nh * 8), "zero");
+    WBRW_TRY(c, d->bin(c, DST_WSUM, c->buf.grid, 1), "weights");
+    WBRW_TRY(c, launch_wp_round(c), "rounding");
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
     WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
@@ -277,6 +283,8 @@ wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_
   if (c->cfg.strategy == WBRW_SP1_PAIR) {
     WBRW_TRY(c, launch_zero(c, c->buf.grid, (size_t)c->nh * 4), "zero grid");
     if (c->tangent) WBRW_TRY(c, zero_tangent(c), "zero tangent");
+  } else if (c->cfg.strategy == WBRW_WP) {
+    WBRW_TRY(c, launch_zero(c, c->tmp_wsum, (size_t)c->nh * 8), "zero");
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
     WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
@@ -288,11 +296,13 @@ wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_
   // the regeneration of the previous histogram uses its own epoch's ids
   const long long keep_epoch = c->epoch;
   c->epoch = regen_epoch;
-  cudaError_t e = d->chunk(c, l0, L, src,
-                           c->cfg.strategy == WBRW_SP1_PAIR ? DST_BIN1 : DST_BIN2);
+  const int dst = c->cfg.strategy == WBRW_SP1_PAIR ? DST_BIN1
+                  : (c->cfg.strategy == WBRW_WP ? DST_WSUM : DST_BIN2);
+  cudaError_t e = d->chunk(c, l0, L, src, dst);
   c->epoch = keep_epoch;
   WBRW_TRY(c, e, "period");
   if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c), "bootstrap");
+  if (c->cfg.strategy == WBRW_WP) WBRW_TRY(c, launch_wp_round(c), "rounding");
   WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
   if (c->tangent) WBRW_TRY(c, launch_scan_tangent(c), "tangent plan");
   return WBRW_OK;
@@ -509,7 +519,7 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
                               ? (long long)config->nx * config->nx * config->nk * config->nk
                               : (long long)config->nx * config->nk;
   if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0 ||
-      (config->strategy == WBRW_SP2_BOOTSTRAP && !b->w) ||
+      (config->strategy != WBRW_SP1_PAIR && !b->w) ||
       b->grid_cells < cells * ninst || (config->tangent && !b->tangent) ||
       ((uintptr_t)b->scratch & (kAlign - 1)) != 0 ||
       (b->event_log && b->event_log_capacity <= 0)) {

@@ -378,6 +378,26 @@ __global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long
   }
 }
 
+// wp: the weighted histogram (Eq. piecewise_constant_function, weights in
+// fixed point 2^-31) rounded by Alg. 3: floor(|m|) particles plus one with
+// probability |m| - floor(|m|), sign of m, the uniform of the draw
+// (nu, ROUND, epoch) as for sp2.
+__global__ void __launch_bounds__(kBlock) k_wp_round(long long nh, const long long* wsum,
+                                                     int* grid, uint32_t key0, uint32_t key1,
+                                                     unsigned long long epoch) {
+  for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
+       nu += (long long)gridDim.x * kBlock) {
+    const double m = __dmul_rn((double)wsum[nu], 1.0 / 2147483648.0);
+    const double am = fabs(m);
+    const double fl = floor(am);
+    const uint4 r = philox((uint32_t)nu, (uint32_t)((unsigned long long)nu >> 32), kStepRound,
+                           (uint32_t)epoch, key0, key1);
+    const double u = u53(r.x, r.y);
+    const long long cnt = (long long)fl + (u < __dsub_rn(am, fl) ? 1 : 0);
+    grid[nu] = (int)(m < 0 ? -cnt : cnt);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Observables: one warp per x-column.
 // ---------------------------------------------------------------------------
@@ -637,6 +657,14 @@ cudaError_t launch_boot(Ctx* c) {
   k_boot_combine<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_keep[0], c->boot_keep[1],
                                               c->buf.grid, key0, key1, epoch);
   c->launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wp_round(Ctx* c) {
+  const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
+  k_wp_round<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->nh, c->tmp_wsum, c->buf.grid, key0,
+                                                       key1, (unsigned long long)c->epoch);
+  c->launches++;
   return cudaGetLastError();
 }
 

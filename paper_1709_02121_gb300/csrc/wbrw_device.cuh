@@ -642,6 +642,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
     if (cell_of<P>(p, x, k, cell))
       atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
                 (unsigned long long)llrint((double)w * 2147483648.0));
+    else tally_out<P>(p, acc, w);
   } else if constexpr (DST == DST_BIN2) {
     if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
     if (w == (T)0) return;
@@ -1125,6 +1126,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if (cell_of<P>(p, x, k, cell))
         atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
                   (unsigned long long)llrint((double)w * 2147483648.0));
+      else tally_out<P>(p, acc, w);
     }
   } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
     int cell = -1;
@@ -1569,7 +1571,7 @@ KP<P> make_kp(const Ctx* c) {
   p.x = (T*)c->buf.x;
   p.k = (T*)c->buf.k;
   p.s = c->buf.s;
-  p.w = g.strategy == WBRW_SP2_BOOTSTRAP ? (T*)c->buf.w : nullptr;
+  p.w = g.strategy != WBRW_SP1_PAIR ? (T*)c->buf.w : nullptr;  // sp2 and wp
   p.capacity = c->buf.capacity;
   p.cpid = c->cpid;
   p.nseg = c->nseg;

@@ -247,6 +247,8 @@ cudaError_t launch_scan_tangent(Ctx*);
 // c->inst_grad.
 cudaError_t launch_transmission_gradients(Ctx*);
 cudaError_t launch_boot(Ctx*);
+// wp: Alg. 3's rounding of the weighted histogram tmp_wsum into the grid.
+cudaError_t launch_wp_round(Ctx*);
 // Observables of instance `inst` from the counts / Q1.31 weight sums of all
 // instances (one of the two is NULL).
 cudaError_t launch_observables(Ctx*, int inst, const int* counts, const long long* wsum);

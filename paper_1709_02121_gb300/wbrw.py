@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libwbrw.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_CUDA, ERR_STATE, ERR_TIMEOUT, ERR_NUMERIC = 0, -1, -2, -3, -4, -5, -6
-SP1_PAIR, SP2_BOOTSTRAP = 1, 2
+SP1_PAIR, SP2_BOOTSTRAP, WP = 1, 2, 3
 FP64, FP32 = 0, 1
 POT_GAUSSIAN, POT_SOFT_COULOMB_2E = 0, 1
 
@@ -385,7 +385,7 @@ class Simulation:
         self.torch = torch
         self.wl = dict(wl)
         prec = FP64 if wl["precision"] == "fp64" else FP32
-        strat = SP1_PAIR if wl["strategy"] == "sp1" else SP2_BOOTSTRAP
+        strat = {"sp1": SP1_PAIR, "sp2": SP2_BOOTSTRAP, "wp": WP}[wl["strategy"]]
         self.dim = int(wl.get("dim", 2))
         self.cfg = Config(self.dim, prec, strat, wl["hbar"], wl["mass"], wl["dt"], wl["gamma0"],
                           wl["nx"], wl["nk"], wl["xmin"], wl["xmax"], wl["kmin"], wl["kmax"],
@@ -400,7 +400,7 @@ class Simulation:
         self.x = torch.empty(nd * self.capacity, dtype=fdt, device=dev)
         self.k = torch.empty(nd * self.capacity, dtype=fdt, device=dev)
         self.s = torch.empty(self.capacity, dtype=torch.int8, device=dev)
-        self.w = torch.empty(self.capacity, dtype=fdt, device=dev) if strat == SP2_BOOTSTRAP else None
+        self.w = torch.empty(self.capacity, dtype=fdt, device=dev) if strat != SP1_PAIR else None
         self.tan = (torch.zeros(2 * self.capacity, dtype=torch.float64, device=dev)
                     if wl.get("tangent") else None)
         self.cells = (self.nx * self.nx * self.nk * self.nk if self.dim == 4

@@ -144,7 +144,7 @@ def test_annihilation_and_regeneration_match_oracle():
     assert_same_particles(sim, o)
 
 
-@pytest.mark.parametrize("strategy", ["sp1", "sp2"])
+@pytest.mark.parametrize("strategy", ["sp1", "sp2", "wp"])
 def test_fused_schedule_matches_oracle(strategy):
     wl = small(strategy=strategy, resample_every=6, n_alpha=3000)
     sim, o = sim_of(wl), oracle_of(wl)
