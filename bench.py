@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2"])
+    ap.add_argument("--strategy", default="sp1", choices=["sp1", "sp2", "wp"])
     ap.add_argument("--workload", default="gauss2d_fp32_n1e8",
                     choices=["gauss2d_fp32_n1e8", "gauss2d_fp64_n2e5", "batch2d_fp32_256",
                              "he4d_fp32_n5e7", "grad2d_fp32_64", "tdv2d_fp32_n1e8"])
