@@ -688,7 +688,7 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
 # of the regeneration and the histogram index.
 INT_OPS_PER_PSTEP = {"fp32": 33.6, "fp64": 63.0, "fp32_4d": 36.0, "fp64_4d": 73.0}
 # DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
-TRAFFIC_PER_PSTEP = {"fp32": 0.83, "fp64": None, "fp32_4d": 1.57, "fp64_4d": None}
+TRAFFIC_PER_PSTEP = {"fp32": None, "fp64": None, "fp32_4d": None, "fp64_4d": None}
 
 
 def main():

@@ -951,6 +951,29 @@ __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long 
   return lo;
 }
 
+// Bit i of the result: half i of the four 16x2 SIMD masks (0 or 0xFFFF per
+// half; half 2j + h is half h of word j).  Bytes 0 and 2 of each word carry
+// its halves; each selected byte keeps one distinct bit, and the multiply
+// sums the four bytes into the top byte without carries.
+__device__ __forceinline__ unsigned coin_bits(unsigned c0, unsigned c1, unsigned c2, unsigned c3) {
+  const unsigned lo = __byte_perm(c0, c1, 0x6420u), hi = __byte_perm(c2, c3, 0x6420u);
+  return (((lo & 0x08040201u) | (hi & 0x80402010u)) * 0x01010101u) >> 24;
+}
+
+// Position after n free-flight intervals of length dt (dtv = dt hbar/m).
+// FP64 rounds once per interval, in the oracle's order; FP32 takes the
+// n intervals in one fused step, x + k (n dtv).
+template <class P>
+__device__ __forceinline__ typename P::T stream_n(typename P::T x, typename P::T k,
+                                                  typename P::T dtv, int n) {
+  if constexpr (P::is64) {
+    for (int i = 0; i < n; ++i) x = P::stream(x, k, dtv);
+    return x;
+  } else {
+    return n > 0 ? __fmaf_rn(k, __fmul_rn((float)n, dtv), x) : x;
+  }
+}
+
 template <class P, int SRC, int DST>
 __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
                                             unsigned long long slot, PV<P> x, const PV<P>& k,
@@ -979,17 +1002,12 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       const unsigned thr = p16 | (p16 << 16);
       for (int b = ls >> 3; (b << 3) < p.L; ++b) {
         const uint4 q = philox_ks(p.ks, plo, phi, (uint32_t)b, kDrawCoins);
-        const unsigned c0 = __vcmpltu2(q.x, thr), c1 = __vcmpltu2(q.y, thr);
-        const unsigned c2 = __vcmpltu2(q.z, thr), c3 = __vcmpltu2(q.w, thr);
-        unsigned hit = (c0 & 1u) | ((c0 >> 15) & 2u) | ((c1 & 1u) << 2) | ((c1 >> 13) & 8u) |
-                       ((c2 & 1u) << 4) | ((c2 >> 11) & 32u) | ((c3 & 1u) << 6) |
-                       ((c3 >> 9) & 128u);
+        unsigned hit = coin_bits(__vcmpltu2(q.x, thr), __vcmpltu2(q.y, thr),
+                                 __vcmpltu2(q.z, thr), __vcmpltu2(q.w, thr));
         const unsigned e0 = __vcmpeq2(q.x, thr), e1 = __vcmpeq2(q.y, thr);
         const unsigned e2 = __vcmpeq2(q.z, thr), e3 = __vcmpeq2(q.w, thr);
         if ((e0 | e1 | e2 | e3) != 0u) {  // a tie: refine with 8 more bits
-          const unsigned tie = (e0 & 1u) | ((e0 >> 15) & 2u) | ((e1 & 1u) << 2) |
-                               ((e1 >> 13) & 8u) | ((e2 & 1u) << 4) | ((e2 >> 11) & 32u) |
-                               ((e3 & 1u) << 6) | ((e3 >> 9) & 128u);
+          const unsigned tie = coin_bits(e0, e1, e2, e3);
           for (unsigned t = tie; t; t &= t - 1) {
             const int jj = __ffs(t) - 1;
             const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)((b << 3) + jj), 0u);
@@ -1006,7 +1024,10 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     acc.psteps += (unsigned long long)(p.L - ls);
   }
 
-  // ---- offsets of this warp's candidate entries --------------------------
+  // ---- the warp's candidate entries.  Entry j of the warp (lanes in
+  // order, intervals in order within a lane) goes to queue slot wc.e + j and
+  // is written by lane j mod 32, which fetches its owner's state with
+  // shuffles: every lane stores, and consecutive entries are adjacent.
   const unsigned cnt = __popc(mask);
   unsigned inc = cnt;
 #pragma unroll
@@ -1015,35 +1036,62 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     if (lane >= o) inc += t;
   }
   const unsigned total = __shfl_sync(kFull, inc, 31);
-  unsigned q = wc.e + (inc - cnt);
-
-  // ---- free streaming x <- x + (hbar/m) k dt, one rounding per interval;
-  // a candidate interval is entered with x at its start ------------------
-  if (act) {
-    for (int l = ls; l < p.L; ++l) {
-      if ((mask >> (l - p.l0)) & 1u) {
+  if (total) {
+    const unsigned excl = inc - cnt;
+    for (unsigned j0 = 0; j0 < total; j0 += 32) {
+      const unsigned j = j0 + lane;
+      int o = 0;  // the owner: the number of lanes whose inclusive count is <= j
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        const unsigned v = __shfl_sync(kFull, inc, o + s - 1);
+        if (v <= j) o += s;
+      }
+      o = min(o, 31);
+      unsigned mo = __shfl_sync(kFull, mask, o);
+      const unsigned eo = __shfl_sync(kFull, excl, o);
+      const int lo_s = __shfl_sync(kFull, ls, o);
+      const int io = __shfl_sync(kFull, inst, o);
+      const unsigned long long po = __shfl_sync(kFull, pid, o);
+      const T wo = __shfl_sync(kFull, w, o);
+      PV<P> xo, ko;
+#pragma unroll
+      for (int d = 0; d < P::D; ++d) {
+        xo.c[d] = __shfl_sync(kFull, x.c[d], o);
+        ko.c[d] = __shfl_sync(kFull, k.c[d], o);
+      }
+      TanField<P::TG> to;
+      if constexpr (P::TG) {
+        to.th = __shfl_sync(kFull, tau.th, o);
+        to.tw = __shfl_sync(kFull, tau.tw, o);
+      }
+      if (j < total) {
+        for (unsigned t = j - eo; t; --t) mo &= mo - 1;  // the (j - eo)-th set bit
+        const int l = p.l0 + __ffs(mo) - 1;
+        const unsigned long long q = (unsigned long long)wc.e + j;
         if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
           FEntry<P> e;
-          static_cast<TanField<P::TG>&>(e) = tau;
-          e.pid = pid;
-          e.x = x;
-          e.k = k;
-          e.w = w;
-          e.l = ent_pack(l, inst);
+          static_cast<TanField<P::TG>&>(e) = to;
+          e.pid = po;
+#pragma unroll
+          for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(xo.c[d], ko.c[d], p.dtv, l - lo_s);
+          e.k = ko;
+          e.w = wo;
+          e.l = ent_pack(l, io);
           p.eq[(long long)g * p.eseg + (long long)q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
         }
-        ++q;
       }
-#pragma unroll
-      for (int d = 0; d < P::D; ++d) x.c[d] = P::stream(x.c[d], k.c[d], p.dtv);
     }
-  }
-  if (total) {
     __syncwarp();
     if (lane == 0) wc.e += total;
     __syncwarp();
+  }
+
+  // ---- free streaming x <- x + (hbar/m) k dt to the end of the period
+  if (act) {
+#pragma unroll
+    for (int d = 0; d < P::D; ++d) x.c[d] = stream_n<P>(x.c[d], k.c[d], p.dtv, p.L - ls);
   }
 
   // ---- the particle's own final state ----------------------------------
@@ -1210,20 +1258,19 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       TanField<P::TG> tau;
       if constexpr (P::TG) tau.th = tau.tw = 0.0;
       if constexpr (RG) {
-        // Alg. 3: the cell of each slot.  The tile's first nonzero cell comes
-        // from the plan; the 32 slots of a tile lie in at most 32 nonzero
-        // cells, searched with shuffles.
+        // Alg. 3: the cell of each slot.  The tile's first nonzero cell a0
+        // comes from the plan and holds slot base; the 32 slots of a tile lie
+        // in at most 32 nonzero cells, whose starts strictly increase.  Lane i
+        // marks bit (start of a0 + i) - base when that start falls inside the
+        // tile, and slot base + lane lies in cell a0 + (marks at or below lane).
         const unsigned long long a0 = tile_nz[base >> 5];
         const unsigned long long idx = a0 + lane;
         const unsigned long long st = idx < nz ? nz_start[idx] : ~0ull;
         const uint32_t cw = idx < nz ? nz_cell[idx] : 0u;
-        int lo = 0, hi = 31;  // last i with start_i <= slot
-#pragma unroll
-        for (int it = 0; it < 5; ++it) {
-          const int mid = (lo + hi + 1) >> 1;
-          const unsigned long long sv = __shfl_sync(kFull, st, mid);
-          if (sv <= slot) lo = mid; else hi = mid - 1;
-        }
+        const unsigned mark =
+            (lane > 0 && st > base && st - base < 32ull) ? 1u << (unsigned)(st - base) : 0u;
+        const unsigned marks = __reduce_or_sync(kFull, mark);
+        const int lo = __popc(marks & ((2u << lane) - 1u));
         const uint32_t cwl = __shfl_sync(kFull, cw, lo);
         if constexpr (TR) {  // the tangent particles of a cell share its tau
           const double th = idx < nz ? p.tnz_tau[2 * idx] : 0.0;
