@@ -27,7 +27,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
 
 struct Layout {
-  size_t counters, cpid, fq0, fq1, eq, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
+  size_t counters, cpid, fq0, fq1, eq0, eq1, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
       rec_a, keep0, keep1, res0, res1, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
       tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, dgrid0, dgrid1, tnz_cell, tnz_start,
@@ -100,7 +100,9 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   const long long nh = cells * ninst;
   const long long floor_entries = (long long)kMaxSeg * kMinSeg;
   L.qcap = capacity > floor_entries ? capacity : floor_entries;
-  L.ecap = 2 * L.qcap;  // about one candidate interval per particle per flight
+  // per round buffer: FP32 flights queue at most one candidate interval per
+  // particle, FP64 flights all of them (about one per particle per flight)
+  L.ecap = c->precision == WBRW_FP32 ? L.qcap : 2 * L.qcap;
   L.dcap = L.ecap / 4;  // deferred segments: a few per cent of the events
   L.tile_cap = capacity / 32 + 2;
   L.rec_cap = c->strategy == WBRW_SP2_BOOTSTRAP ? 4 * L.qcap : 0;
@@ -112,12 +114,13 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
     return at;
   };
   L.counters = take(sizeof(Counters));
-  L.seg_counts = take((size_t)(1 + 2 + kMaxLevels + 1) * kMaxSeg * sizeof(unsigned));
+  L.seg_counts = take((size_t)(2 + 2 + kMaxLevels + 1) * kMaxSeg * sizeof(unsigned));
   L.cnt_save = take(sizeof(Counters));
   L.cpid = take((size_t)capacity * 8);
   L.fq0 = take((size_t)L.qcap * d->fentry_bytes);
   L.fq1 = take((size_t)L.qcap * d->fentry_bytes);
-  L.eq = take((size_t)L.ecap * d->fentry_bytes);
+  L.eq0 = take((size_t)L.ecap * d->fentry_bytes);
+  L.eq1 = take((size_t)L.ecap * d->fentry_bytes);
   L.dq0 = take((size_t)L.dcap * d->sentry_bytes);
   L.dq1 = take((size_t)L.dcap * d->sentry_bytes);
   L.nz_cell = take((size_t)nh * 4);
@@ -579,7 +582,8 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->cnt = (Counters*)(base + L.counters);
   c->cpid = (unsigned long long*)(base + L.cpid);
   unsigned* counts = (unsigned*)(base + L.seg_counts);
-  c->ecnt = counts;
+  c->ecnt[0] = counts;
+  c->ecnt[1] = counts + (4 + kMaxLevels) * kMaxSeg;
   c->fcnt[0] = counts + kMaxSeg;
   c->fcnt[1] = counts + 2 * kMaxSeg;
   c->dcnt = counts + 3 * kMaxSeg;
@@ -588,7 +592,8 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->fq[0] = base + L.fq0;
   c->fq[1] = base + L.fq1;
   c->qcap = L.qcap;
-  c->eq = base + L.eq;
+  c->eq[0] = base + L.eq0;
+  c->eq[1] = base + L.eq1;
   c->ecap = L.ecap;
   c->dq[0] = base + L.dq0;
   c->dq[1] = base + L.dq1;

@@ -73,7 +73,7 @@ constexpr uint32_t kStepRegen = 0xFFFFFFFEu;
 constexpr uint32_t kStepBoot = 0xFFFFFFFDu;
 constexpr uint32_t kStepRound = 0xFFFFFFFCu;
 constexpr uint32_t kDrawPids = 0x80000000u;
-constexpr uint32_t kDrawCoins = 0xC0000000u;  // FP32 16-bit coins
+constexpr uint32_t kDrawGap = 0xC0000000u;    // FP32 gap to the next candidate interval
 constexpr uint32_t kDrawComp = 0x40000000u;   // component choice (time-dependent V)
 
 // ---------------------------------------------------------------------------
@@ -168,7 +168,7 @@ struct Inst {
   T gamma0, cacc, sig_k, xc;  // rate, acceptance factor C/(2 gamma0), kick scale, centre
   double p_hi;                // FP64: u0 < p_hi may start an event in an interval
   float p_any_f;              // FP32: P(candidate) per interval
-  unsigned p16, p16_frac8;    // FP32 coin threshold and tie refinement
+  float ilq;                  // FP32: 1 / ln(1 - p_any), the geometric gap's scale
   int well;                   // H < 0: V_W has the sign of -sin (Eq. 2)
   double gH, gw0, gw1;        // tangent mode: 1/H, 1/w, 4w (the score of a birth)
 };
@@ -245,8 +245,10 @@ struct KP {
   FEntry<P>* fq_out;         // offspring for the next wave
   unsigned* fcnt_out;
   long long qseg;
-  FEntry<P>* eq;             // candidate intervals
+  FEntry<P>* eq;             // candidate intervals: the queue appended to
   unsigned* ecnt;
+  const FEntry<P>* eq_in;    // the candidate intervals k_event takes
+  const unsigned* ecnt_in;
   long long eseg;
   SEntry<P>* dq[2];          // deferred segments; level L lives in dq[L & 1]
   unsigned* dcnt;            // kMaxLevels x nseg counts
@@ -951,15 +953,6 @@ __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long 
   return lo;
 }
 
-// Bit i of the result: half i of the four 16x2 SIMD masks (0 or 0xFFFF per
-// half; half 2j + h is half h of word j).  Bytes 0 and 2 of each word carry
-// its halves; each selected byte keeps one distinct bit, and the multiply
-// sums the four bytes into the top byte without carries.
-__device__ __forceinline__ unsigned coin_bits(unsigned c0, unsigned c1, unsigned c2, unsigned c3) {
-  const unsigned lo = __byte_perm(c0, c1, 0x6420u), hi = __byte_perm(c2, c3, 0x6420u);
-  return (((lo & 0x08040201u) | (hi & 0x80402010u)) * 0x01010101u) >> 24;
-}
-
 // Position after n free-flight intervals of length dt (dtv = dt hbar/m).
 // FP64 rounds once per interval, in the oracle's order; FP32 takes the
 // n intervals in one fused step, x + k (n dtv).
@@ -974,11 +967,55 @@ __device__ __forceinline__ typename P::T stream_n(typename P::T x, typename P::T
   }
 }
 
+// FP32 candidate clock.  Whether an interval holds a candidate is a
+// Bernoulli(p_any) trial, independent across intervals (the constant-rate
+// clock of Sec. 3.2), so the number of whole intervals before the next
+// candidate is geometric: G = floor(ln U / ln(1 - p_any)), U = (2 m + 1)
+// 2^-24 from 23 random bits m.  Returns min(G, nmax).
+__device__ __forceinline__ int geo_gap(uint32_t m, float ilq, int nmax) {
+  const float u = (float)(2u * m + 1u) * (1.0f / 16777216.0f);
+  const float g = __fmul_rn(logf(u), ilq);
+  return g < (float)nmax ? (int)g : nmax;
+}
+
+// Append one candidate entry per flagged lane (interval c, the position
+// streamed from the lane's interval ls to c) to the warp's segment of the
+// candidate queue p.eq.  Every lane of the warp calls it.
+template <class P>
+__device__ __forceinline__ void append_candidate(const KP<P>& p, WarpCounts& wc, bool has,
+                                                 unsigned long long pid, const PV<P>& x,
+                                                 const PV<P>& k, typename P::T w, int ls, int c,
+                                                 int inst, const TanField<P::TG>& tau) {
+  const int lane = threadIdx.x & 31;
+  const unsigned bal = __ballot_sync(kFull, has);
+  if (has) {
+    const unsigned long long g = global_warp();
+    const unsigned long long q = (unsigned long long)wc.e + __popc(bal & ((1u << lane) - 1u));
+    if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
+      FEntry<P> e;
+      static_cast<TanField<P::TG>&>(e) = tau;
+      e.pid = pid;
+#pragma unroll
+      for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(x.c[d], k.c[d], p.dtv, c - ls);
+      e.k = k;
+      e.w = w;
+      e.l = ent_pack(c, inst);
+      p.eq[(long long)g * p.eseg + (long long)q] = e;
+    } else {
+      set_err(p.cnt, ERR_CAP_EQUEUE);
+    }
+  }
+  __syncwarp();
+  if (lane == 0) wc.e += __popc(bal);
+  __syncwarp();
+}
+
 template <class P, int SRC, int DST>
 __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
                                             unsigned long long slot, PV<P> x, const PV<P>& k,
                                             typename P::T w, unsigned long long pid, int ls,
-                                            int inst, const TanField<P::TG>& tau) {
+                                            int inst, const TanField<P::TG>& tau,
+                                            uint32_t gbits) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   const unsigned long long g = global_warp();
@@ -995,31 +1032,16 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)l, 0u);
         if (u53(r.x, r.y) < ip.p_hi) mask |= 1u << (l - p.l0);
       }
-    } else {
-      // eight 16-bit coins per Philox call for the intervals 8b .. 8b+7,
-      // compared two at a time against floor(65536 p_any)
-      const unsigned p16 = ip.p16;
-      const unsigned thr = p16 | (p16 << 16);
-      for (int b = ls >> 3; (b << 3) < p.L; ++b) {
-        const uint4 q = philox_ks(p.ks, plo, phi, (uint32_t)b, kDrawCoins);
-        unsigned hit = coin_bits(__vcmpltu2(q.x, thr), __vcmpltu2(q.y, thr),
-                                 __vcmpltu2(q.z, thr), __vcmpltu2(q.w, thr));
-        const unsigned e0 = __vcmpeq2(q.x, thr), e1 = __vcmpeq2(q.y, thr);
-        const unsigned e2 = __vcmpeq2(q.z, thr), e3 = __vcmpeq2(q.w, thr);
-        if ((e0 | e1 | e2 | e3) != 0u) {  // a tie: refine with 8 more bits
-          const unsigned tie = coin_bits(e0, e1, e2, e3);
-          for (unsigned t = tie; t; t &= t - 1) {
-            const int jj = __ffs(t) - 1;
-            const uint4 r = philox_ks(p.ks, plo, phi, (uint32_t)((b << 3) + jj), 0u);
-            if ((r.w & 0xFFu) < ip.p16_frac8) hit |= 1u << jj;
-          }
-        }
-        const int sh = (b << 3) - p.l0;
-        mask |= sh >= 0 ? (hit << sh) : (hit >> (-sh));
-      }
-      if (p16 >= 65536u) mask = ~0u;  // p_any rounds to one: every interval
-      const int lo = ls - p.l0, hi = p.L - p.l0;
-      mask &= (hi >= 32 ? ~0u : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+    } else if (ls < p.L) {
+      // FP32: the first candidate interval from ls on, a geometric gap from
+      // 23 random bits: the regeneration draw's (gbits), bits 32..54 of an
+      // offspring's random id, or the draw (pid, ls, GAP) otherwise
+      uint32_t m;
+      if constexpr (SRC == SRC_QUEUE) m = (uint32_t)(pid >> 32) & 0x7FFFFFu;
+      else if constexpr (SRC == SRC_ARRAY) m = philox_ks(p.ks, plo, phi, (uint32_t)ls, kDrawGap).x >> 9;
+      else m = gbits;
+      const int c = ls + geo_gap(m, ip.ilq, p.L - ls);
+      if (c < p.L) mask = 1u << (c - p.l0);
     }
     acc.psteps += (unsigned long long)(p.L - ls);
   }
@@ -1028,6 +1050,11 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
   // order, intervals in order within a lane) goes to queue slot wc.e + j and
   // is written by lane j mod 32, which fetches its owner's state with
   // shuffles: every lane stores, and consecutive entries are adjacent.
+  if constexpr (!P::is64) {
+    // FP32: at most one entry per lane (the first candidate interval)
+    if (__ballot_sync(kFull, mask != 0u))
+      append_candidate<P>(p, wc, mask != 0u, pid, x, k, w, ls, p.l0 + __ffs(mask) - 1, inst, tau);
+  } else {
   const unsigned cnt = __popc(mask);
   unsigned inc = cnt;
 #pragma unroll
@@ -1086,6 +1113,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     __syncwarp();
     if (lane == 0) wc.e += total;
     __syncwarp();
+  }
   }
 
   // ---- free streaming x <- x + (hbar/m) k dt to the end of the period
@@ -1229,7 +1257,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         if constexpr (P::TG) e.th = e.tw = 0.0;
         if (act) e = p.fq_in[(long long)sg * p.qseg + i];
         flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
-                                 ent_inst(e.l), e);
+                                 ent_inst(e.l), e, 0u);
       }
     }
   } else {
@@ -1255,6 +1283,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       T w = (T)0;
       unsigned long long pid = 0;
       int inst = 0;
+      uint32_t gbits = 0;  // FP32: the first gap's random bits (regeneration)
       TanField<P::TG> tau;
       if constexpr (P::TG) tau.th = tau.tw = 0.0;
       if constexpr (RG) {
@@ -1296,7 +1325,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
             if (ik < 0) { --ix; ik += p.nk; } else if (ik >= p.nk) { ++ix; ik -= p.nk; }
             T ux, uk;
             if constexpr (P::is64) { ux = (T)u53(r.x, r.y); uk = (T)u53(r.z, r.w); }
-            else { ux = (T)u24(r.x); uk = (T)u24(r.y); }
+            else { ux = (T)u24(r.x); uk = (T)u24(r.y); gbits = r.z >> 9; }
             x.c[0] = in_cell<P>(P::add(p.xmin, P::mul(P::add((T)ix, ux), p.dx)), p.xmin, p.inv_dx, ix);
             k.c[0] = in_cell<P>(P::add(p.kmin, P::mul(P::add((T)ik, uk), p.dk)), p.kmin, p.inv_dk, ik);
           } else {
@@ -1312,6 +1341,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
               u[0] = u53(r.x, r.y); u[1] = u53(r.z, r.w); u[2] = u53(r2.x, r2.y); u[3] = u53(r2.z, r2.w);
             } else {
               u[0] = u24(r.x); u[1] = u24(r.y); u[2] = u24(r.z); u[3] = u24(r.w);
+              gbits = ((r.x & 0xFFu) << 15) | ((r.y & 0xFFu) << 7) | ((r.z & 0xFFu) >> 1);
             }
             x.c[0] = in_cell<P>(P::add(p.xmin, P::mul(P::add((T)ix1, u[0]), p.dx)), p.xmin, p.inv_dx, ix1);
             x.c[P::D - 1] = in_cell<P>(P::add(p.xmin, P::mul(P::add((T)ix2, u[1]), p.dx)), p.xmin, p.inv_dx, ix2);
@@ -1344,7 +1374,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
           }
         }
       }
-      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst, tau);
+      flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst, tau,
+                               gbits);
     }
   }
 
@@ -1395,11 +1426,26 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
   for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
-    const unsigned n = min(p.ecnt[sg], (unsigned)p.eseg);
+    const unsigned n = min(p.ecnt_in[sg], (unsigned)p.eseg);
     for (unsigned b = 0; b < n; b += 32) {
       const unsigned i = b + lane;
+      FEntry<P> e{};
+      if (i < n) e = p.eq_in[(long long)sg * p.eseg + i];
+      if constexpr (!P::is64) {
+        // FP32: the particle's next candidate interval after this one, a
+        // geometric gap from the draw (pid, l + 1, GAP), queued for the
+        // next round
+        const int l = ent_l(e.l), inst = ent_inst(e.l);
+        int c = p.L;
+        if (i < n && l + 1 < p.L) {
+          const uint4 r = philox_ks(p.ks, (uint32_t)e.pid, (uint32_t)(e.pid >> 32),
+                                    (uint32_t)(l + 1), kDrawGap);
+          c = l + 1 + geo_gap(r.x >> 9, p.inst[inst].ilq, p.L - l - 1);
+        }
+        if (__ballot_sync(kFull, c < p.L))
+          append_candidate<P>(p, wc, c < p.L, e.pid, e.x, e.k, e.w, l, c, inst, e);
+      }
       if (i < n) {
-        const FEntry<P> e = p.eq[(long long)sg * p.eseg + i];
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T>& ip = p.inst[inst];
         SEntry<P> s;
@@ -1423,7 +1469,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
       }
     }
   }
-  store_counts(p, wc, 1, true, false, DST == DST_BIN2);
+  store_counts(p, wc, 1, true, true, DST == DST_BIN2);
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
@@ -1627,8 +1673,10 @@ KP<P> make_kp(const Ctx* c) {
   p.fq_out = (FEntry<P>*)c->fq[1];
   p.fcnt_out = c->fcnt[1];
   p.qseg = c->qseg;
-  p.eq = (FEntry<P>*)c->eq;
-  p.ecnt = c->ecnt;
+  p.eq = (FEntry<P>*)c->eq[0];
+  p.ecnt = c->ecnt[0];
+  p.eq_in = (const FEntry<P>*)c->eq[1];
+  p.ecnt_in = c->ecnt[1];
   p.eseg = c->eseg;
   p.dq[0] = (SEntry<P>*)c->dq[0];
   p.dq[1] = (SEntry<P>*)c->dq[1];
@@ -1790,10 +1838,7 @@ struct DriverImpl {
       v.gw1 = 4.0 * q.w;
       v.p_hi = q.p_any * (1.0 + 1e-9) + 1e-300;
       v.p_any_f = (float)q.p_any;
-      const double sc = q.p_any * 65536.0;
-      const double fl = floor(sc);
-      v.p16 = (unsigned)fl;
-      v.p16_frac8 = (unsigned)floor((sc - fl) * 256.0);
+      v.ilq = (float)(1.0 / log1p(-q.p_any));  // -inf for p_any = 0, -0 for p_any = 1
       it[i] = v;
       InitInst g;
       g.x0 = q.x0;
@@ -1841,7 +1886,11 @@ struct DriverImpl {
       p.fcnt_in = c->fcnt[r & 1];
       p.fq_out = (FEntry<P>*)c->fq[(r + 1) & 1];
       p.fcnt_out = c->fcnt[(r + 1) & 1];
-      if ((e = launch_zero(c, c->ecnt, cnt_bytes)) != cudaSuccess) return e;
+      // round r's candidates: those k_event of round r - 1 chained (FP32),
+      // then those of the round's flight
+      p.eq = (FEntry<P>*)c->eq[r & 1];
+      p.ecnt = c->ecnt[r & 1];
+      if (r == 0 && (e = launch_zero(c, p.ecnt, cnt_bytes)) != cudaSuccess) return e;
       if (r == 0) prof_begin(c);
       e = flight_any<P>(c, p, r == 0 ? src : (int)SRC_QUEUE, dst);
       if (r == 0) prof_end(c);
@@ -1852,6 +1901,11 @@ struct DriverImpl {
         if ((e = flight_any<P>(c, p, SRC_TREGEN, dst)) != cudaSuccess) return e;
       }
       if (L > l0) {
+        p.eq_in = p.eq;
+        p.ecnt_in = p.ecnt;
+        p.eq = (FEntry<P>*)c->eq[(r + 1) & 1];
+        p.ecnt = c->ecnt[(r + 1) & 1];
+        if ((e = launch_zero(c, p.ecnt, cnt_bytes)) != cudaSuccess) return e;
         if ((e = launch_zero(c, p.fcnt_out, cnt_bytes)) != cudaSuccess) return e;
         if ((e = launch_zero(c, c->dcnt, (size_t)(c->passes + 2) * cnt_bytes)) != cudaSuccess)
           return e;

@@ -153,8 +153,8 @@ struct Ctx {
   void* fq[2];        // offspring waves (double buffered)
   unsigned* fcnt[2];
   long long qcap, qseg;
-  void* eq;           // candidate intervals
-  unsigned* ecnt;
+  void* eq[2];        // candidate intervals of the even and odd rounds
+  unsigned* ecnt[2];
   long long ecap, eseg;
   void* dq[2];        // deferred segments, levels alternating
   unsigned* dcnt;     // kMaxLevels x kMaxSeg

@@ -1,7 +1,7 @@
-"""FP32 production path, checked in law: it draws its clock from 16-bit coins
-(eight intervals per Philox call), so it is compared with the Schroedinger
-equation and with the FP64 path (bit-identical to the oracle) through
-estimates and their Monte Carlo standard errors."""
+"""FP32 production path, checked in law: it draws its candidate clock as
+geometric gaps between candidate intervals, so it is compared with the
+Schroedinger equation and with the FP64 path (bit-identical to the oracle)
+through estimates and their Monte Carlo standard errors."""
 import numpy as np
 import pytest
 

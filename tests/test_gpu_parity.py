@@ -4,7 +4,7 @@ FP64: the same counter-based streams and the same operation order on both
 sides, so ids, event logs and integer cell counts must agree bit for bit and
 positions to 1e-12 relative (the only differences allowed are the last-ulp
 differences of log1p/sin/cos between CUDA and the host C library).
-FP32: a different stream layout by design (16-bit coins), checked in law.
+FP32: a different stream layout by design (geometric candidate gaps), checked in law.
 """
 import numpy as np
 import pytest
