@@ -107,8 +107,17 @@ struct F32 {
   __device__ static T flr(T a) { return floorf(a); }
   __device__ static T next_dn(T a) { return nextafterf(a, -CUDART_INF_F); }
   __device__ static T next_up(T a) { return nextafterf(a, CUDART_INF_F); }
-  __device__ static T sn(T a) { return sinf(a); }
-  __device__ static T cs(T a) { return cosf(a); }
+  // sin and cos: the argument reduced to [-pi, pi] by Cody and Waite's
+  // method (2 pi split into a head with 8 significant bits, so that n times
+  // it is exact for |n| < 2^16, and a tail), then the hardware
+  // approximation, whose absolute error on [-pi, pi] is below 2^-21.4; the
+  // rounding of a phase argument of a few units already exceeds that
+  __device__ static T reduce(T a) {
+    const float n = rintf(a * 0.15915494f);
+    return __fmaf_rn(-n, 0.0019353071795862320f, __fmaf_rn(-n, 6.28125f, a));
+  }
+  __device__ static T sn(T a) { return __sinf(reduce(a)); }
+  __device__ static T cs(T a) { return __cosf(reduce(a)); }
 };
 
 // Phase-space model: precision F and D position coordinates (D = 1: the 2D
@@ -169,6 +178,7 @@ struct Inst {
   double p_hi;                // FP64: u0 < p_hi may start an event in an interval
   float p_any_f;              // FP32: P(candidate) per interval
   float ilq;                  // FP32: 1 / ln(1 - p_any), the geometric gap's scale
+  float ig0;                  // FP32: 1 / gamma0
   int well;                   // H < 0: V_W has the sign of -sin (Eq. 2)
   double gH, gw0, gw1;        // tangent mode: 1/H, 1/w, 4w (the score of a birth)
 };
@@ -506,8 +516,8 @@ struct Draw<P, true> {
   // event j of the 2D model: the standard normal z of the kick, the
   // acceptance uniform u3 and the gap to the next event
   __device__ static void event(const KP<P>& p, const Inst<double>& ip, unsigned long long pid,
-                               int l, unsigned j, const State&, double& z, double& u3,
-                               double& gap) {
+                               int l, unsigned j, bool /*root*/, const State&, double& z,
+                               double& u3, double& gap) {
     const uint32_t lo = (uint32_t)pid, hi = (uint32_t)(pid >> 32);
     const uint4 a = philox_ks(p.ks, lo, hi, (uint32_t)l, 1u + 2u * j);
     const uint4 b = philox_ks(p.ks, lo, hi, (uint32_t)l, 2u + 2u * j);
@@ -525,12 +535,12 @@ struct Draw<P, true> {
 //    serves both the first life-length, drawn from the exponential truncated
 //    to the interval, tau = -log1p(-p_any U24(w0))/gamma0, and event 0
 //    (u1..u3 = U24(w1..w3), u4 from the low bytes of w0..w2).
-//  - Offspring segments (from their birth time tb): whether an event falls in
-//    the rest of the interval is decided by the offspring's own random id,
-//    whose low 32 bits are a uniform: hit iff they are below
-//    p_r 2^32, p_r = 1 - exp(-gamma0 (dt - tb)).  Only a hit draws the call
-//    (pid, l, 0), which then serves as for a root, with p_r for p_any.
-//  - Event j >= 1 of a segment uses the call (pid, l, 1+j): U24 of w0..w3.
+//  - Offspring segments (from their birth time tb): the first event comes at
+//    tb + E/gamma0, E = -ln U exponential (memorylessness), U = (2m + 1)
+//    2^-24 from bits 9..31 of the offspring's own random id; no event in the
+//    interval when that time is >= dt.
+//  - Event j of a segment, except event 0 of a root, uses the call
+//    (pid, l, 1+j): u1..u4 = U24 of w0..w3.
 //  - In the 4D model every event j, the first included, uses the call
 //    (pid, l, 1+j): ua = U24(w0), uk = U24(w1), the gap from U24(w2),
 //    uc = (w3 >> 16) 2^-16, uj = (w3 & 0xFFFF) 2^-16.
@@ -545,26 +555,23 @@ struct Draw<P, false> {
     const uint4 a = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 1u + j);
     const float uc = (float)(a.w >> 16) * (1.0f / 65536.0f);
     const float uj = (float)(a.w & 0xFFFFu) * (1.0f / 65536.0f);
-    gap = (-log1pf(-u24(a.z))) / ip.gamma0;
+    gap = (-log1pf(-u24(a.z))) * ip.ig0;
     return table_kick<P>(p, ip.gamma0, xe, u24(a.x), u24(a.y), uc, uj, comp, kap, prob);
   }
   __device__ static float first(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
                                 int l, float to, bool root, State& st) {
-    float pr;
-    if (root) {
-      pr = ip.p_any_f;
-    } else {
-      pr = -expm1f(-ip.gamma0 * (p.dt - to));
-      if (!((float)(uint32_t)pid < pr * 4294967296.0f)) return p.dt;  // no event
+    if (!root) {
+      const float u = (float)(2u * ((uint32_t)pid >> 9) + 1u) * (1.0f / 16777216.0f);
+      return to + (-logf(u)) * ip.ig0;
     }
     st.r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
-    return to + (-log1pf(-pr * u24(st.r.x))) / ip.gamma0;
+    return to + (-log1pf(-ip.p_any_f * u24(st.r.x))) * ip.ig0;
   }
   __device__ static void event(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
-                               int l, unsigned j, const State& st, float& z, float& u3,
-                               float& gap) {
+                               int l, unsigned j, bool root, const State& st, float& z,
+                               float& u3, float& gap) {
     float u1, u2, u4;
-    if (j == 0) {
+    if (j == 0 && root) {
       const uint4 r = st.r;
       u1 = u24(r.y);
       u2 = u24(r.z);
@@ -578,8 +585,9 @@ struct Draw<P, false> {
       u3 = u24(a.z);
       u4 = u24(a.w);
     }
-    z = sqrtf(-2.0f * log1pf(-u1)) * cospif(2.0f * u2);
-    gap = (-log1pf(-u4)) / ip.gamma0;
+    // Box-Muller with the angle 2 pi (u2 - 1/2) in [-pi, pi) (law unchanged)
+    z = sqrtf(-2.0f * log1pf(-u1)) * __cosf(6.2831855f * (u2 - 0.5f));
+    gap = (-log1pf(-u4)) * ip.ig0;
   }
 };
 
@@ -789,8 +797,8 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
                                                   typename P::T to, const PV<P>& k,
                                                   typename P::T w,
                                                   const typename Draw<P>::State& st, int l,
-                                                  unsigned j, typename P::T t, Later later,
-                                                  const TanField<P::TG>& tau) {
+                                                  unsigned j, bool root, typename P::T t,
+                                                  Later later, const TanField<P::TG>& tau) {
   using T = typename P::T;
   const PV<P> xe = pos_at(p, xo, to, k, t);
   T kap, gap, fac;
@@ -800,7 +808,7 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
   if constexpr (P::D == 1) {
     T z, sg, u3;
     bool flip;
-    Draw<P>::event(p, ip, pid, l, j, st, z, u3, gap);
+    Draw<P>::event(p, ip, pid, l, j, root, st, z, u3, gap);
     if (p.ncomp == 0) {  // the static barrier: kick, |sin| ratio, orientation
       kap = P::mul(ip.sig_k, z);
       sg = P::sn(P::mul(P::mul((T)2, P::sub(xe.c[0], ip.xc)), kap));
@@ -913,7 +921,8 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
     };
     while (s.t < p.dt) {
       const typename P::T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k,
-                                                 s.w, s.st, l, j, s.t, later, s);
+                                                 s.w, s.st, l, j, (s.j & kRootFlag) != 0u, s.t,
+                                                 later, s);
       s.t = P::add(s.t, gap);
       ++j;
     }
@@ -1243,19 +1252,18 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
 
   if constexpr (SRC == SRC_QUEUE) {
     // the previous wave's offspring, one producer segment at a time
+    // (the next tile's entries load while the current tile is processed)
+    FEntry<P> none{};
+    none.l = p.L;
     for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
       const unsigned n = min(p.fcnt_in[sg], (unsigned)p.qseg);
+      const FEntry<P>* seg = p.fq_in + (long long)sg * p.qseg;
+      FEntry<P> nx = (unsigned)lane < n ? seg[lane] : none;
       for (unsigned b = 0; b < n; b += 32) {
         const unsigned i = b + lane;
         const bool act = i < n;
-        FEntry<P> e;
-        e.pid = 0;
-#pragma unroll
-        for (int d = 0; d < P::D; ++d) e.x.c[d] = e.k.c[d] = (T)0;
-        e.w = (T)0;
-        e.l = p.L;
-        if constexpr (P::TG) e.th = e.tw = 0.0;
-        if (act) e = p.fq_in[(long long)sg * p.qseg + i];
+        const FEntry<P> e = nx;
+        nx = i + 32 < n ? seg[i + 32] : none;
         flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
                                  ent_inst(e.l), e, 0u);
       }
@@ -1459,7 +1467,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         s.t = Draw<P>::first(p, ip, e.pid, l, (T)0, true, s.st);
         if (s.t < p.dt) {
           const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w,
-                                         s.st, l, 0u, s.t, later, s);
+                                         s.st, l, 0u, true, s.t, later, s);
           s.t = P::add(s.t, gap);
           if (s.t < p.dt) {
             s.j = 1u | kRootFlag;
@@ -1499,7 +1507,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
         const int l = ent_l(s.l), inst = ent_inst(s.l);
         const Inst<T>& ip = p.inst[inst];
         const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
-                                       l, j, s.t, later, s);
+                                       l, j, (s.j & kRootFlag) != 0u, s.t, later, s);
         s.t = P::add(s.t, gap);
         if (s.t < p.dt) {
           s.j = (j + 1) | (s.j & kRootFlag);
@@ -1839,6 +1847,7 @@ struct DriverImpl {
       v.p_hi = q.p_any * (1.0 + 1e-9) + 1e-300;
       v.p_any_f = (float)q.p_any;
       v.ilq = (float)(1.0 / log1p(-q.p_any));  // -inf for p_any = 0, -0 for p_any = 1
+      v.ig0 = q.gamma0 > 0.0 ? (float)(1.0 / q.gamma0) : 0.0f;
       it[i] = v;
       InitInst g;
       g.x0 = q.x0;
