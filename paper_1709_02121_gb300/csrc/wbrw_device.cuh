@@ -1259,11 +1259,13 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       const unsigned n = min(p.fcnt_in[sg], (unsigned)p.qseg);
       const FEntry<P>* seg = p.fq_in + (long long)sg * p.qseg;
       FEntry<P> nx = (unsigned)lane < n ? seg[lane] : none;
+      FEntry<P> nx2 = (unsigned)lane + 32u < n ? seg[lane + 32] : none;
       for (unsigned b = 0; b < n; b += 32) {
         const unsigned i = b + lane;
         const bool act = i < n;
         const FEntry<P> e = nx;
-        nx = i + 32 < n ? seg[i + 32] : none;
+        nx = nx2;
+        nx2 = i + 64 < n ? seg[i + 64] : none;
         flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
                                  ent_inst(e.l), e, 0u);
       }
@@ -1282,7 +1284,21 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
     else n = min(TR ? p.cnt->tan_total : p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
     const unsigned long long n_base = p.cnt->n_base, base_pid = p.cnt->base_pid;
     const unsigned long long nz = RG ? (TR ? p.cnt->tan_nz : p.cnt->nz_count) : 0ull;
-    for (unsigned long long base = g * 32ull; base < n; base += nwarps * 32ull) {
+    // regeneration plan entries, loaded ahead: the first nonzero cell a0 two
+    // tiles ahead, the starts and cells one tile ahead
+    const unsigned long long stride = nwarps * 32ull;
+    unsigned long long a0_next = 0, idx_n = 0, st_n = ~0ull;
+    uint32_t cw_n = 0u;
+    if constexpr (RG) {
+      const unsigned long long b0 = g * 32ull;
+      if (b0 < n) {
+        idx_n = tile_nz[b0 >> 5] + lane;
+        st_n = idx_n < nz ? nz_start[idx_n] : ~0ull;
+        cw_n = idx_n < nz ? nz_cell[idx_n] : 0u;
+      }
+      if (b0 + stride < n) a0_next = tile_nz[(b0 + stride) >> 5];
+    }
+    for (unsigned long long base = g * 32ull; base < n; base += stride) {
       const unsigned long long slot = base + lane;
       const bool act = slot < n;
       PV<P> x, k;
@@ -1300,10 +1316,14 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         // in at most 32 nonzero cells, whose starts strictly increase.  Lane i
         // marks bit (start of a0 + i) - base when that start falls inside the
         // tile, and slot base + lane lies in cell a0 + (marks at or below lane).
-        const unsigned long long a0 = tile_nz[base >> 5];
-        const unsigned long long idx = a0 + lane;
-        const unsigned long long st = idx < nz ? nz_start[idx] : ~0ull;
-        const uint32_t cw = idx < nz ? nz_cell[idx] : 0u;
+        const unsigned long long idx = idx_n, st = st_n;
+        const uint32_t cw = cw_n;
+        if (base + stride < n) {
+          idx_n = a0_next + lane;
+          st_n = idx_n < nz ? nz_start[idx_n] : ~0ull;
+          cw_n = idx_n < nz ? nz_cell[idx_n] : 0u;
+        }
+        if (base + 2 * stride < n) a0_next = tile_nz[(base + 2 * stride) >> 5];
         const unsigned mark =
             (lane > 0 && st > base && st - base < 32ull) ? 1u << (unsigned)(st - base) : 0u;
         const unsigned marks = __reduce_or_sync(kFull, mark);
