@@ -225,6 +225,7 @@ template <class P>
 struct KP {
   using T = typename P::T;
   T dt, dtv, hm;
+  T inv_dt;         // 1/dt
   Tab4<T> tab;      // 4D model only
   const Comp* comp; // time-dependent potential: ncomp components (0: static)
   int ncomp;
@@ -565,7 +566,8 @@ struct Draw<P, false> {
       return to + (-logf(u)) * ip.ig0;
     }
     st.r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
-    return to + (-log1pf(-ip.p_any_f * u24(st.r.x))) * ip.ig0;
+    // below dt in exact arithmetic; kept below it after rounding
+    return fminf(to + (-log1pf(-ip.p_any_f * u24(st.r.x))) * ip.ig0, P::next_dn(p.dt));
   }
   __device__ static void event(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
                                int l, unsigned j, bool root, const State& st, float& z,
@@ -711,6 +713,53 @@ static_assert(sizeof(SEntry<Q32>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<P32G>) == 80, "SEntry layout");
 
 constexpr unsigned kRootFlag = 0x80000000u;
+
+// Position after n free-flight intervals of length dt (dtv = dt hbar/m).
+// FP64 rounds once per interval, in the oracle's order; FP32 takes the
+// n intervals in one fused step, x + k (n dtv).
+template <class P>
+__device__ __forceinline__ typename P::T stream_n(typename P::T x, typename P::T k,
+                                                  typename P::T dtv, int n) {
+  if constexpr (P::is64) {
+    for (int i = 0; i < n; ++i) x = P::stream(x, k, dtv);
+    return x;
+  } else {
+    return n > 0 ? __fmaf_rn(k, __fmul_rn((float)n, dtv), x) : x;
+  }
+}
+
+// FP32 candidate clock, continued by a root segment (a particle in one of
+// its candidate intervals l) whose next event time t falls at or beyond dt:
+// under the constant rate that event lies in interval l + floor(t/dt), the
+// particle's next candidate interval, queued for the next round when it is
+// inside the chunk.  Its own first event there is drawn afresh when that
+// entry is taken (the interval's truncated exponential; memorylessness).
+template <class P>
+__device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
+                                           const SEntry<P>& s) {
+  if constexpr (!P::is64) {
+    const int l = ent_l(s.l);
+    const float q = floorf(s.t * p.inv_dt);
+    if (q < (float)(p.L - l)) {
+      const int c = l + (int)q;
+      const unsigned long long g = global_warp();
+      const unsigned slot = atomicAdd(&wc.e, 1u);
+      if (g < (unsigned long long)p.nseg && slot < (unsigned long long)p.eseg) {
+        FEntry<P> e;
+        static_cast<TanField<P::TG>&>(e) = static_cast<const TanField<P::TG>&>(s);
+        e.pid = s.pid;
+#pragma unroll
+        for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(s.xo.c[d], s.k.c[d], p.dtv, c - l);
+        e.k = s.k;
+        e.w = s.w;
+        e.l = ent_pack(c, ent_inst(s.l));
+        p.eq[(long long)g * p.eseg + (long long)slot] = e;
+      } else {
+        set_err(p.cnt, ERR_CAP_EQUEUE);
+      }
+    }
+  }
+}
 
 // An offspring's state at the end of interval l: the next wave's input, or
 // the sink's in the chunk's last interval.
@@ -927,6 +976,7 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
       ++j;
     }
     if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s);
+    else chain_next<P>(p, wc, s);
   }
 }
 
@@ -960,20 +1010,6 @@ __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long 
     if (p.inst_slot[mid] <= slot) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-// Position after n free-flight intervals of length dt (dtv = dt hbar/m).
-// FP64 rounds once per interval, in the oracle's order; FP32 takes the
-// n intervals in one fused step, x + k (n dtv).
-template <class P>
-__device__ __forceinline__ typename P::T stream_n(typename P::T x, typename P::T k,
-                                                  typename P::T dtv, int n) {
-  if constexpr (P::is64) {
-    for (int i = 0; i < n; ++i) x = P::stream(x, k, dtv);
-    return x;
-  } else {
-    return n > 0 ? __fmaf_rn(k, __fmul_rn((float)n, dtv), x) : x;
-  }
 }
 
 // FP32 candidate clock.  Whether an interval holds a candidate is a
@@ -1459,20 +1495,6 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
       const unsigned i = b + lane;
       FEntry<P> e{};
       if (i < n) e = p.eq_in[(long long)sg * p.eseg + i];
-      if constexpr (!P::is64) {
-        // FP32: the particle's next candidate interval after this one, a
-        // geometric gap from the draw (pid, l + 1, GAP), queued for the
-        // next round
-        const int l = ent_l(e.l), inst = ent_inst(e.l);
-        int c = p.L;
-        if (i < n && l + 1 < p.L) {
-          const uint4 r = philox_ks(p.ks, (uint32_t)e.pid, (uint32_t)(e.pid >> 32),
-                                    (uint32_t)(l + 1), kDrawGap);
-          c = l + 1 + geo_gap(r.x >> 9, p.inst[inst].ilq, p.L - l - 1);
-        }
-        if (__ballot_sync(kFull, c < p.L))
-          append_candidate<P>(p, wc, c < p.L, e.pid, e.x, e.k, e.w, l, c, inst, e);
-      }
       if (i < n) {
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T>& ip = p.inst[inst];
@@ -1492,6 +1514,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
           if (s.t < p.dt) {
             s.j = 1u | kRootFlag;
             defer<P>(p, wc, 1, s);
+          } else {
+            chain_next<P>(p, wc, s);
           }
         }
       }
@@ -1534,11 +1558,13 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
           defer<P>(p, wc, level + 1, s);
         } else if (!(s.j & kRootFlag)) {
           settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s);
+        } else {
+          chain_next<P>(p, wc, s);
         }
       }
     }
   }
-  store_counts(p, wc, level + 1, true, false, DST == DST_BIN2);
+  store_counts(p, wc, level + 1, true, true, DST == DST_BIN2);
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
@@ -1561,7 +1587,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p
     for (unsigned i = lane; i < n; i += 32)
       finish_segment<P, DST>(p, wc, acc, in[(long long)sg * p.dseg + i]);
   }
-  store_counts(p, wc, 0, true, false, DST == DST_BIN2);
+  store_counts(p, wc, 0, true, true, DST == DST_BIN2);
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
@@ -1641,6 +1667,7 @@ KP<P> make_kp(const Ctx* c) {
   KP<P> p;
   const wbrw_config& g = c->cfg;
   p.dt = (T)g.dt;
+  p.inv_dt = (T)(1.0 / g.dt);
   p.dtv = (T)c->dtv;
   p.hm = (T)c->hm;
   p.xmin = (T)g.xmin;
