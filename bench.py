@@ -657,15 +657,18 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
     HBM sees only the candidate queue, so the pass is bound by the integer
     pipe (Philox4x32-10 is 32-bit multiplies and XORs).
 
-    achieved = INT_OPS_PER_PSTEP (the algorithm's integer operations per
-    first-wave particle-step, derived in the design doc) x the first-wave
-    particle-steps of one launch / the launch's average CUDA-event time.
+    achieved = the algorithm's integer operations per first-wave particle
+    and period (INT_OPS_PER_PARTICLE, derived in the design doc) / the period's
+    intervals x the first-wave particle-steps of one launch / the launch's
+    average CUDA-event time.
     peak = 152 SMs x 64 INT32 lanes x the median SM clock sampled during the
     timed region (one integer operation per lane per cycle)."""
     if not kern_n or kern_ms <= 0:
         return None
     key = wl["precision"] + ("_4d" if wl.get("dim", 2) == 4 else "")
-    ops = INT_OPS_PER_PSTEP[wl["precision"] + ("_4d" if wl.get("dim", 2) == 4 else "")]
+    R = wl["resample_every"]
+    base, per_interval = INT_OPS_PER_PARTICLE[key]
+    ops = (base + per_interval * R) / R
     per_launch_ms = kern_ms / kern_n
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak = 152 * 64 * sm_mhz * 1e6 / 1e9
@@ -682,11 +685,15 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
                           "timed region)" % sm_mhz}
 
 
-# Integer operations per first-wave particle-step of a 10-interval period
-# ("Roofline of the first wave"): three Philox4x32-10 calls per
-# particle per period at 100 operations each, the coin tests, the cell decode
-# of the regeneration and the histogram index.
-INT_OPS_PER_PSTEP = {"fp32": 33.6, "fp64": 63.0, "fp32_4d": 36.0, "fp64_4d": 73.0}
+# Integer operations per first-wave particle and period of R intervals
+# ("Roofline of the first wave"): (per particle, per interval).
+# A Philox4x32-10 call counts 100 (10 rounds of two 32x32->64 multiplies as
+# lo and hi, four XORs, two key additions).  FP32: one call per particle
+# (regeneration offsets and the first candidate gap) plus the cell decode,
+# in-cell coordinates, gap bits and histogram index.  FP64: the
+# regeneration call(s) plus one call per interval for the candidate test.
+INT_OPS_PER_PARTICLE = {"fp32": (120, 0), "fp32_4d": (135, 0),
+                        "fp64": (116, 100), "fp64_4d": (230, 100)}
 # DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
 TRAFFIC_PER_PSTEP = {"fp32": None, "fp64": None, "fp32_4d": None, "fp64_4d": None}
 

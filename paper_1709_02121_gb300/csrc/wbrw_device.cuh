@@ -236,6 +236,7 @@ struct KP {
   int ninst;        // instances in the batch (1 for a single run)
   int nhi;          // cells per instance (nx nk); instance i owns [i nhi, (i+1) nhi)
   const Inst<T>* inst;                    // per-instance physics
+  Inst<T> inst0;                          // instance 0's record, in the parameters
   const unsigned long long* inst_slot;    // first array slot of each base instance
   const unsigned long long* regen_start;  // first regenerated slot of each instance
   unsigned* cinst;                        // instance of offspring appended to the arrays
@@ -301,6 +302,14 @@ __device__ __forceinline__ KP<P> with_period(const KP<P>& q) {
   p.L = p.l0 + q.len;
   p.regen_base = q.cnt->per_regen_base;
   return p;
+}
+
+// The physics record of instance i: a single run reads it from the kernel
+// parameters (constant bank), a batch from its table in global memory.
+template <class P>
+__device__ __forceinline__ Inst<typename P::T> inst_of(const KP<P>& p, int i) {
+  if (p.ninst > 1) return p.inst[i];
+  return p.inst0;
 }
 
 constexpr int kWarps = kBlock / 32;
@@ -963,7 +972,7 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
     SEntry<P> s = stack[--sp];
     unsigned j = s.j & ~kRootFlag;
     const int inst = ent_inst(s.l), l = ent_l(s.l);
-    const Inst<typename P::T>& ip = p.inst[inst];
+    const Inst<typename P::T> ip = inst_of(p, inst);
     auto later = [&](const SEntry<P>& ch) {
       if (sp < kStack) stack[sp++] = ch;
       else set_err(p.cnt, ERR_NESTING);
@@ -1064,7 +1073,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   const unsigned long long g = global_warp();
-  const Inst<T>& ip = p.inst[inst];
+  const Inst<T> ip = inst_of(p, inst);
   const int cbase = inst * p.nhi;
 
   // ---- candidate clock over [ls, L) (Sec. 3.2): which intervals hold an
@@ -1497,7 +1506,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
       if (i < n) e = p.eq_in[(long long)sg * p.eseg + i];
       if (i < n) {
         const int l = ent_l(e.l), inst = ent_inst(e.l);
-        const Inst<T>& ip = p.inst[inst];
+        const Inst<T> ip = inst_of(p, inst);
         SEntry<P> s;
         static_cast<TanField<P::TG>&>(s) = static_cast<const TanField<P::TG>&>(e);
         s.pid = e.pid;
@@ -1549,7 +1558,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
         SEntry<P> s = in[(long long)sg * p.dseg + i];
         const unsigned j = s.j & ~kRootFlag;
         const int l = ent_l(s.l), inst = ent_inst(s.l);
-        const Inst<T>& ip = p.inst[inst];
+        const Inst<T> ip = inst_of(p, inst);
         const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
                                        l, j, (s.j & kRootFlag) != 0u, s.t, later, s);
         s.t = P::add(s.t, gap);
@@ -1684,6 +1693,7 @@ KP<P> make_kp(const Ctx* c) {
   p.ninst = c->ninst;
   p.nhi = (int)c->nhi;
   p.inst = (const Inst<T>*)c->inst_tab;
+  p.inst0 = *(const Inst<T>*)c->host_tab;
   p.inst_slot = c->inst_slot;
   p.cinst = c->cinst;
   for (int r = 0; r < 10; ++r) {
