@@ -723,6 +723,17 @@ static_assert(sizeof(SEntry<P32G>) == 80, "SEntry layout");
 
 constexpr unsigned kRootFlag = 0x80000000u;
 
+// FP32 candidate clock.  Whether an interval holds a candidate is a
+// Bernoulli(p_any) trial, independent across intervals (the constant-rate
+// clock of Sec. 3.2), so the number of whole intervals before the next
+// candidate is geometric: G = floor(ln U / ln(1 - p_any)), U = (2 m + 1)
+// 2^-24 from 23 random bits m.  Returns min(G, nmax).
+__device__ __forceinline__ int geo_gap(uint32_t m, float ilq, int nmax) {
+  const float u = (float)(2u * m + 1u) * (1.0f / 16777216.0f);
+  const float g = __fmul_rn(logf(u), ilq);
+  return g < (float)nmax ? (int)g : nmax;
+}
+
 // Position after n free-flight intervals of length dt (dtv = dt hbar/m).
 // FP64 rounds once per interval, in the oracle's order; FP32 takes the
 // n intervals in one fused step, x + k (n dtv).
@@ -778,6 +789,41 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
                                        typename P::T to, const PV<P>& k, typename P::T w,
                                        int l, const TanField<P::TG>& tau) {
   const PV<P> xf = pos_at(p, xo, to, k, p.dt);
+  if constexpr (!P::is64) {
+    // FP32: the offspring's flight through [l + 1, L) right here, as the
+    // flight kernel would carry it: its first candidate interval (the
+    // geometric gap from bits 32..54 of its random id) queued for the next
+    // round, then the sink at the end of the chunk
+    const int n = p.L - l - 1;
+    if (n > 0) {
+      acc.psteps += (unsigned long long)n;
+      const int c = l + 1 + geo_gap((uint32_t)(pid >> 32) & 0x7FFFFFu, inst_of(p, inst).ilq, n);
+      if (c < p.L) {
+        const unsigned long long g = global_warp();
+        const unsigned q = atomicAdd(&wc.e, 1u);
+        if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
+          FEntry<P> e;
+          static_cast<TanField<P::TG>&>(e) = tau;
+          e.pid = pid;
+#pragma unroll
+          for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(xf.c[d], k.c[d], p.dtv, c - l - 1);
+          e.k = k;
+          e.w = w;
+          e.l = ent_pack(c, inst);
+          p.eq[(long long)g * p.eseg + (long long)q] = e;
+        } else {
+          set_err(p.cnt, ERR_CAP_EQUEUE);
+        }
+      }
+      PV<P> xl;
+#pragma unroll
+      for (int d = 0; d < P::D; ++d) xl.c[d] = stream_n<P>(xf.c[d], k.c[d], p.dtv, n);
+      emit_child_final<P, DST>(p, wc, acc, inst, pid, xl, k, w, tau);
+    } else {
+      emit_child_final<P, DST>(p, wc, acc, inst, pid, xf, k, w, tau);
+    }
+    return;
+  }
   if (l + 1 < p.L) {
     FEntry<P> e;
     static_cast<TanField<P::TG>&>(e) = tau;
@@ -1019,17 +1065,6 @@ __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long 
     if (p.inst_slot[mid] <= slot) lo = mid; else hi = mid - 1;
   }
   return lo;
-}
-
-// FP32 candidate clock.  Whether an interval holds a candidate is a
-// Bernoulli(p_any) trial, independent across intervals (the constant-rate
-// clock of Sec. 3.2), so the number of whole intervals before the next
-// candidate is geometric: G = floor(ln U / ln(1 - p_any)), U = (2 m + 1)
-// 2^-24 from 23 random bits m.  Returns min(G, nmax).
-__device__ __forceinline__ int geo_gap(uint32_t m, float ilq, int nmax) {
-  const float u = (float)(2u * m + 1u) * (1.0f / 16777216.0f);
-  const float g = __fmul_rn(logf(u), ilq);
-  return g < (float)nmax ? (int)g : nmax;
 }
 
 // Append one candidate entry per flagged lane (interval c, the position
@@ -1471,6 +1506,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, const Acc& acc,
                                                      Counters* c, bool bin2) {
+  block_reduce_add(red, acc.psteps, &c->ledger[LG_PSTEPS]);  // FP32 offspring flights
   block_reduce_add(red, acc.events, &c->ledger[LG_EVENTS]);
   block_reduce_add(red, acc.kill_p, &c->ledger[LG_KILL_P]);
   block_reduce_add(red, acc.kill_m, &c->ledger[LG_KILL_M]);
@@ -1958,7 +1994,9 @@ struct DriverImpl {
       p.ecnt = c->ecnt[r & 1];
       if (r == 0 && (e = launch_zero(c, p.ecnt, cnt_bytes)) != cudaSuccess) return e;
       if (r == 0) prof_begin(c);
-      e = flight_any<P>(c, p, r == 0 ? src : (int)SRC_QUEUE, dst);
+      // FP32 offspring fly inside the event kernels that settle them; FP64
+      // offspring fly in a wave of their own (the per-interval draws)
+      if (r == 0 || P::is64) e = flight_any<P>(c, p, r == 0 ? src : (int)SRC_QUEUE, dst);
       if (r == 0) prof_end(c);
       if (e != cudaSuccess) return e;
       if (P::TG && r == 0 && src == SRC_REGEN) {
