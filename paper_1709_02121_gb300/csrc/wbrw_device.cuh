@@ -1520,6 +1520,21 @@ __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, co
   }
 }
 
+// Prefetch entries [b, min(b + 32, n)) of a queue segment into L1: lane j
+// touches the tile's j-th 128-byte line when that line starts inside the
+// valid entries (so no address past them is touched).  No register holds
+// the data; the tile's loads one iteration later hit L1.
+template <class P>
+__device__ __forceinline__ void prefetch_tile(const FEntry<P>* seg, unsigned n, unsigned b,
+                                              int lane) {
+  if (b >= n) return;
+  const unsigned bytes = (min(32u, n - b)) * (unsigned)sizeof(FEntry<P>);
+  if ((unsigned)lane * 128u < bytes) {
+    const char* a = (const char*)(seg + b) + 128u * (unsigned)lane;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+  }
+}
+
 template <class P, int DST>
 __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p_) {
   const KP<P> p = with_period(p_);
@@ -1536,10 +1551,12 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
   for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
     const unsigned n = min(p.ecnt_in[sg], (unsigned)p.eseg);
+    const FEntry<P>* seg = p.eq_in + (long long)sg * p.eseg;
     for (unsigned b = 0; b < n; b += 32) {
       const unsigned i = b + lane;
+      prefetch_tile<P>(seg, n, b + 32, lane);  // the next tile, into L1
       FEntry<P> e{};
-      if (i < n) e = p.eq_in[(long long)sg * p.eseg + i];
+      if (i < n) e = seg[i];
       if (i < n) {
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T> ip = inst_of(p, inst);
