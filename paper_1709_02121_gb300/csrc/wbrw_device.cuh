@@ -887,25 +887,37 @@ __device__ __forceinline__ void comp_kick(const KP<P>& p, const Inst<typename P:
   flip = Hm < (T)0 ? sg > (T)0 : sg < (T)0;
 }
 
-// Event j of a segment at time t.  2D model: the kick of Remark 3, the
-// acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair.  4D model:
-// the component, thinning and tabulated kick of table_kick; the pair is
-// k +/- kappa e_m with e_0 = (1, 0), e_1 = (0, 1), e_2 = (1, -1).  Offspring
-// are settled or, when they have an event of their own in the interval,
-// handed to `later`.  Returns the gap to the segment's next event.
-template <class P, int DST, class Later>
-__device__ __forceinline__ typename P::T do_event(const KP<P>& p,
-                                                  const Inst<typename P::T>& ip, int inst,
-                                                  WarpCounts& wc, Acc& acc,
-                                                  unsigned long long pid, const PV<P>& xo,
-                                                  typename P::T to, const PV<P>& k,
-                                                  typename P::T w,
-                                                  const typename Draw<P>::State& st, int l,
-                                                  unsigned j, bool root, typename P::T t,
-                                                  Later later, const TanField<P::TG>& tau) {
+// An accepted event: what its +/- pair needs (the parent's id, tangent
+// weight and weight, the event's position and time, the two wavevectors).
+template <class P>
+struct Birth : TanField<P::TG> {
+  using T = typename P::T;
+  unsigned long long pid;
+  PV<P> xe, kp, km;
+  T t, w, fac, kap;
+  int l;       // interval | instance << kLBits
+  unsigned j;  // the event's index in its segment
+  int comp;    // 4D: the component
+};
+
+// Event j of a segment at time t, up to the decision.  2D model: the kick
+// of Remark 3, the acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/-
+// wavevectors.  4D model: the component, thinning and tabulated kick of
+// table_kick; the pair is k +/- kappa e_m with e_0 = (1, 0), e_1 = (0, 1),
+// e_2 = (1, -1).  Returns whether a pair is made (its data in b) and sets
+// the gap to the segment's next event.
+template <class P>
+__device__ __forceinline__ bool event_decide(const KP<P>& p, const Inst<typename P::T>& ip,
+                                             int inst, unsigned long long pid,
+                                             const PV<P>& xo, typename P::T to,
+                                             const PV<P>& k, typename P::T w,
+                                             const typename Draw<P>::State& st, int l,
+                                             unsigned j, bool root, typename P::T t,
+                                             const TanField<P::TG>& tau, Birth<P>& b,
+                                             typename P::T& gap) {
   using T = typename P::T;
   const PV<P> xe = pos_at(p, xo, to, k, t);
-  T kap, gap, fac;
+  T kap, fac;
   bool emit;
   int comp = 0;
   PV<P> kp = k, km = k;
@@ -944,67 +956,109 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
     }
   }
   if (emit) {
-    const uint4 h = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l,
-                              kDrawPids | j);
-    const unsigned long long pid_p = (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
-    const unsigned long long pid_m = (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
-    const bool kill_p = !k_inside(p, kp);
-    const bool kill_m = !k_inside(p, km);
-    const T wc_ = (P::D == 1 && p.strategy != 1) ? P::mul(w, fac) : w;
-    // tangent mode: the birth's score g = (1/H, 1/w - 4 w kappa^2), the
-    // derivative of log V_W^+(x_e, kappa) (Eq. 2); the + child gets
-    // tau + s g, the - child its negative
-    TanField<P::TG> tp;
-    if constexpr (P::TG) {
-      const double kd = (double)kap;
-      const double gw = __dsub_rn(ip.gw0, __dmul_rn(__dmul_rn(ip.gw1, kd), kd));
-      tp.th = __dadd_rn(tau.th, __dmul_rn((double)w, ip.gH));
-      tp.tw = __dadd_rn(tau.tw, __dmul_rn((double)w, gw));
-    }
-    ++acc.events;
-    if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
-    if (kill_m) { if (-wc_ > (T)0) ++acc.kill_p; else if (-wc_ < (T)0) ++acc.kill_m; }
-    if (p.log) {
-      const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
-      if (idx < (unsigned long long)p.log_cap) {
-        wbrw_event ev;
-        ev.pid = pid;
-        ev.pid_plus = pid_p;
-        ev.pid_minus = pid_m;
-        ev.step = (unsigned)l;
-        ev.j = j;
-        ev.t = (double)t;
-        ev.xe = (double)xe.c[0];
-        ev.kappa = (double)kap;
-        ev.factor = (double)fac;
-        ev.kill_plus = kill_p;
-        ev.kill_minus = kill_m;
-        ev.xe2 = (double)xe.c[P::D - 1];
-        ev.comp = comp;
-        ev.pad = 0;
-        p.log[idx] = ev;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      if (c == 0 ? kill_p : kill_m) continue;
-      SEntry<P> ch;
-      if constexpr (P::TG) {
-        ch.th = c == 0 ? tp.th : -tp.th;
-        ch.tw = c == 0 ? tp.tw : -tp.tw;
-      }
-      ch.pid = c == 0 ? pid_p : pid_m;
-      ch.xo = xe;
-      ch.to = t;
-      ch.k = c == 0 ? kp : km;
-      ch.w = c == 0 ? wc_ : -wc_;
-      ch.l = ent_pack(l, inst);
-      ch.j = 0;
-      ch.t = Draw<P>::first(p, ip, ch.pid, l, t, false, ch.st);
-      if (ch.t < p.dt) later(ch);
-      else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l, ch);
+    static_cast<TanField<P::TG>&>(b) = tau;
+    b.pid = pid;
+    b.xe = xe;
+    b.kp = kp;
+    b.km = km;
+    b.t = t;
+    b.w = w;
+    b.fac = fac;
+    b.kap = kap;
+    b.l = ent_pack(l, inst);
+    b.j = j;
+    b.comp = comp;
+  }
+  return emit;
+}
+
+// The pair of an accepted event (Alg. 1 item 3): ids, kills outside the
+// k-range, tallies, the event log, then each offspring settled or, when it
+// has an event of its own in the interval, handed to `later`.
+template <class P, int DST, class Later>
+__device__ __forceinline__ void event_pair(const KP<P>& p, const Inst<typename P::T>& ip,
+                                           WarpCounts& wc, Acc& acc, const Birth<P>& b,
+                                           Later later) {
+  using T = typename P::T;
+  const int l = ent_l(b.l), inst = ent_inst(b.l);
+  const uint4 h = philox_ks(p.ks, (uint32_t)b.pid, (uint32_t)(b.pid >> 32), (uint32_t)l,
+                            kDrawPids | b.j);
+  const unsigned long long pid_p = (1ull << 63) | ((((unsigned long long)h.y << 32) | h.x) >> 1);
+  const unsigned long long pid_m = (1ull << 63) | ((((unsigned long long)h.w << 32) | h.z) >> 1);
+  const bool kill_p = !k_inside(p, b.kp);
+  const bool kill_m = !k_inside(p, b.km);
+  const T wc_ = (P::D == 1 && p.strategy != 1) ? P::mul(b.w, b.fac) : b.w;
+  // tangent mode: the birth's score g = (1/H, 1/w - 4 w kappa^2), the
+  // derivative of log V_W^+(x_e, kappa) (Eq. 2); the + child gets
+  // tau + s g, the - child its negative
+  TanField<P::TG> tp;
+  if constexpr (P::TG) {
+    const double kd = (double)b.kap;
+    const double gw = __dsub_rn(ip.gw0, __dmul_rn(__dmul_rn(ip.gw1, kd), kd));
+    tp.th = __dadd_rn(b.th, __dmul_rn((double)b.w, ip.gH));
+    tp.tw = __dadd_rn(b.tw, __dmul_rn((double)b.w, gw));
+  }
+  ++acc.events;
+  if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
+  if (kill_m) { if (-wc_ > (T)0) ++acc.kill_p; else if (-wc_ < (T)0) ++acc.kill_m; }
+  if (p.log) {
+    const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
+    if (idx < (unsigned long long)p.log_cap) {
+      wbrw_event ev;
+      ev.pid = b.pid;
+      ev.pid_plus = pid_p;
+      ev.pid_minus = pid_m;
+      ev.step = (unsigned)l;
+      ev.j = b.j;
+      ev.t = (double)b.t;
+      ev.xe = (double)b.xe.c[0];
+      ev.kappa = (double)b.kap;
+      ev.factor = (double)b.fac;
+      ev.kill_plus = kill_p;
+      ev.kill_minus = kill_m;
+      ev.xe2 = (double)b.xe.c[P::D - 1];
+      ev.comp = b.comp;
+      ev.pad = 0;
+      p.log[idx] = ev;
     }
   }
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    if (c == 0 ? kill_p : kill_m) continue;
+    SEntry<P> ch;
+    if constexpr (P::TG) {
+      ch.th = c == 0 ? tp.th : -tp.th;
+      ch.tw = c == 0 ? tp.tw : -tp.tw;
+    }
+    ch.pid = c == 0 ? pid_p : pid_m;
+    ch.xo = b.xe;
+    ch.to = b.t;
+    ch.k = c == 0 ? b.kp : b.km;
+    ch.w = c == 0 ? wc_ : -wc_;
+    ch.l = b.l;
+    ch.j = 0;
+    ch.t = Draw<P>::first(p, ip, ch.pid, l, b.t, false, ch.st);
+    if (ch.t < p.dt) later(ch);
+    else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l, ch);
+  }
+}
+
+// Event j of a segment at time t: the decision and, when a pair is made,
+// the pair.  Returns the gap to the segment's next event.
+template <class P, int DST, class Later>
+__device__ __forceinline__ typename P::T do_event(const KP<P>& p,
+                                                  const Inst<typename P::T>& ip, int inst,
+                                                  WarpCounts& wc, Acc& acc,
+                                                  unsigned long long pid, const PV<P>& xo,
+                                                  typename P::T to, const PV<P>& k,
+                                                  typename P::T w,
+                                                  const typename Draw<P>::State& st, int l,
+                                                  unsigned j, bool root, typename P::T t,
+                                                  Later later, const TanField<P::TG>& tau) {
+  typename P::T gap;
+  Birth<P> b;
+  if (event_decide<P>(p, ip, inst, pid, xo, to, k, w, st, l, j, root, t, tau, b, gap))
+    event_pair<P, DST>(p, ip, wc, acc, b, later);
   return gap;
 }
 
@@ -1286,7 +1340,22 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if (act && cell >= 0) add_tangent<P>(p, (long long)cbase + cell, tau);
     }
   } else if constexpr (DST == DST_WSUM) {
-    if (act) {
+    if constexpr (SRC == SRC_REGEN) {
+      // regenerated weights are +-1: lanes with the same cell and sign add
+      // once, +-(their count) 2^31 (the same fixed-point sum, exactly)
+      unsigned key = ~0u;
+      if (act) {
+        int cell;
+        if (cell_of<P>(p, x, k, cell)) key = 2u * (unsigned)(cbase + cell) + (w > (T)0 ? 1u : 0u);
+        else tally_out<P>(p, acc, w);
+      }
+      const unsigned grp = __match_any_sync(kFull, key);
+      if (key != ~0u && lane == __ffs(grp) - 1) {
+        const long long v = (long long)__popc(grp) * 2147483648ll;
+        atomicAdd((unsigned long long*)(p.wsum + (key >> 1)),
+                  (unsigned long long)((key & 1u) ? v : -v));
+      }
+    } else if (act) {
       int cell;
       if (cell_of<P>(p, x, k, cell))
         atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
@@ -1520,19 +1589,26 @@ __device__ __forceinline__ void reduce_event_tallies(unsigned long long* red, co
   }
 }
 
-// Prefetch entries [b, min(b + 32, n)) of a queue segment into L1: lane j
-// touches the tile's j-th 128-byte line when that line starts inside the
-// valid entries (so no address past them is touched).  No register holds
-// the data; the tile's loads one iteration later hit L1.
+// Asynchronous global -> shared copies (cp.async.ca, 8 bytes each), in
+// groups: a thread's wait_group N returns once at most its N most recent
+// groups are pending; each thread reads only what it copied itself.
+__device__ __forceinline__ void cp_async8(void* dst_smem, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 template <class P>
-__device__ __forceinline__ void prefetch_tile(const FEntry<P>* seg, unsigned n, unsigned b,
-                                              int lane) {
-  if (b >= n) return;
-  const unsigned bytes = (min(32u, n - b)) * (unsigned)sizeof(FEntry<P>);
-  if ((unsigned)lane * 128u < bytes) {
-    const char* a = (const char*)(seg + b) + 128u * (unsigned)lane;
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-  }
+__device__ __forceinline__ void copy_entry_async(FEntry<P>* dst, const FEntry<P>* src) {
+  static_assert(sizeof(FEntry<P>) % 8 == 0 && alignof(FEntry<P>) >= 8, "entry words");
+#pragma unroll
+  for (unsigned w = 0; w < sizeof(FEntry<P>) / 8; ++w)
+    cp_async8((char*)dst + 8 * w, (const char*)src + 8 * w);
 }
 
 template <class P, int DST>
@@ -1549,14 +1625,46 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
   const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
+  // FP32 2D: the accepted events of the warp's tiles wait in a per-warp
+  // buffer and their pairs are made 32 at a time, so that every lane has one
+  // (the acceptance would otherwise leave a third of the lanes idle there);
+  // the 4D events, with larger records and more registers, measured slower so
+  constexpr bool CMP = !P::is64 && P::D == 1;
+  constexpr unsigned kBirths = 64;
+  __shared__ Birth<P> s_birth[CMP ? kWarps : 1][CMP ? kBirths : 1];
+  Birth<P>* buf = s_birth[CMP ? (threadIdx.x >> 5) : 0];
+  unsigned nb = 0;  // births in the buffer (the same in every lane)
+  __shared__ __align__(16) FEntry<P> s_stage[kWarps][2][32];
+  FEntry<P>(*stage)[32] = s_stage[threadIdx.x >> 5];
+  auto make_pairs = [&](unsigned lim) {
+    while (nb >= lim) {
+      const unsigned take = min(nb, 32u);
+      __syncwarp();
+      if ((unsigned)lane < take) {
+        const Birth<P> bb = buf[nb - take + lane];
+        event_pair<P, DST>(p, inst_of(p, ent_inst(bb.l)), wc, acc, bb, later);
+      }
+      __syncwarp();
+      nb -= take;
+    }
+  };
   for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
     const unsigned n = min(p.ecnt_in[sg], (unsigned)p.eseg);
     const FEntry<P>* seg = p.eq_in + (long long)sg * p.eseg;
-    for (unsigned b = 0; b < n; b += 32) {
+    // each lane copies its entry of the next tile into shared memory
+    // asynchronously while the current tile is processed
+    if ((unsigned)lane < n) copy_entry_async<P>(&stage[0][lane], seg + lane);
+    cp_async_commit();
+    unsigned t = 0;
+    for (unsigned b = 0; b < n; b += 32, ++t) {
       const unsigned i = b + lane;
-      prefetch_tile<P>(seg, n, b + 32, lane);  // the next tile, into L1
+      if (i + 32 < n) copy_entry_async<P>(&stage[(t + 1) & 1][lane], seg + i + 32);
+      cp_async_commit();
+      cp_async_wait<1>();
       FEntry<P> e{};
-      if (i < n) e = seg[i];
+      if (i < n) e = stage[t & 1][lane];
+      bool made = false;
+      Birth<P> bb;
       if (i < n) {
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T> ip = inst_of(p, inst);
@@ -1570,8 +1678,14 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         s.l = e.l;
         s.t = Draw<P>::first(p, ip, e.pid, l, (T)0, true, s.st);
         if (s.t < p.dt) {
-          const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w,
-                                         s.st, l, 0u, true, s.t, later, s);
+          T gap;
+          if constexpr (CMP) {
+            made = event_decide<P>(p, ip, inst, s.pid, s.xo, s.to, s.k, s.w, s.st, l, 0u, true,
+                                   s.t, s, bb, gap);
+          } else {
+            gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, l,
+                                   0u, true, s.t, later, s);
+          }
           s.t = P::add(s.t, gap);
           if (s.t < p.dt) {
             s.j = 1u | kRootFlag;
@@ -1581,8 +1695,16 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
           }
         }
       }
+      if constexpr (CMP) {
+        const unsigned bal = __ballot_sync(kFull, made);
+        if (made) buf[nb + __popc(bal & ((1u << lane) - 1u))] = bb;
+        nb += __popc(bal);
+        make_pairs(32u);
+      }
     }
+    cp_async_wait<0>();
   }
+  if constexpr (CMP) make_pairs(1u);
   store_counts(p, wc, 1, true, true, DST == DST_BIN2);
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
