@@ -759,7 +759,7 @@ __device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
                                            const SEntry<P>& s) {
   if constexpr (!P::is64) {
     const int l = ent_l(s.l);
-    const float q = floorf(s.t * p.inv_dt);
+    const float q = fmaxf(floorf(s.t * p.inv_dt), 1.0f);  // s.t >= dt
     if (q < (float)(p.L - l)) {
       const int c = l + (int)q;
       const unsigned long long g = global_warp();
@@ -782,22 +782,25 @@ __device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
 }
 
 // An offspring's state at the end of interval l: the next wave's input, or
-// the sink's in the chunk's last interval.
+// the sink's in the chunk's last interval.  t_next (>= dt) is the time of
+// its next event under the constant-rate clock.
 template <class P, int DST>
 __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                        unsigned long long pid, const PV<P>& xo,
                                        typename P::T to, const PV<P>& k, typename P::T w,
-                                       int l, const TanField<P::TG>& tau) {
+                                       int l, const TanField<P::TG>& tau,
+                                       typename P::T t_next) {
   const PV<P> xf = pos_at(p, xo, to, k, p.dt);
   if constexpr (!P::is64) {
-    // FP32: the offspring's flight through [l + 1, L) right here, as the
-    // flight kernel would carry it: its first candidate interval (the
-    // geometric gap from bits 32..54 of its random id) queued for the next
-    // round, then the sink at the end of the chunk
+    // FP32: the offspring's flight through [l + 1, L) right here.  Its
+    // next event lies in interval l + floor(t_next/dt), its first candidate
+    // interval (as for a root, chain_next), queued for the next round when
+    // inside the chunk; then the sink at the end of the chunk
     const int n = p.L - l - 1;
     if (n > 0) {
       acc.psteps += (unsigned long long)n;
-      const int c = l + 1 + geo_gap((uint32_t)(pid >> 32) & 0x7FFFFFu, inst_of(p, inst).ilq, n);
+      const float q = fmaxf(floorf(t_next * p.inv_dt), 1.0f);
+      const int c = q < (float)(n + 1) ? l + (int)q : p.L;
       if (c < p.L) {
         const unsigned long long g = global_warp();
         const unsigned q = atomicAdd(&wc.e, 1u);
@@ -1039,7 +1042,7 @@ __device__ __forceinline__ void event_pair(const KP<P>& p, const Inst<typename P
     ch.j = 0;
     ch.t = Draw<P>::first(p, ip, ch.pid, l, b.t, false, ch.st);
     if (ch.t < p.dt) later(ch);
-    else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l, ch);
+    else settle<P, DST>(p, wc, acc, inst, ch.pid, ch.xo, ch.to, ch.k, ch.w, l, ch, ch.t);
   }
 }
 
@@ -1084,7 +1087,7 @@ __device__ void finish_segment(const KP<P>& p, WarpCounts& wc, Acc& acc, const S
       s.t = P::add(s.t, gap);
       ++j;
     }
-    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s);
+    if (!(s.j & kRootFlag)) settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s, s.t);
     else chain_next<P>(p, wc, s);
   }
 }
@@ -1103,6 +1106,7 @@ template <class P>
 __device__ __forceinline__ typename P::T in_cell(typename P::T v, typename P::T lo,
                                                  typename P::T inv, int idx) {
   using T = typename P::T;
+  if (P::flr(P::mul(P::sub(v, lo), inv)) == (T)idx) return v;  // the common case
   for (int it = 0; it < 8 && P::flr(P::mul(P::sub(v, lo), inv)) > (T)idx; ++it) v = P::next_dn(v);
   for (int it = 0; it < 8 && P::flr(P::mul(P::sub(v, lo), inv)) < (T)idx; ++it) v = P::next_up(v);
   return v;
@@ -1177,8 +1181,11 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       }
     } else if (ls < p.L) {
       // FP32: the first candidate interval from ls on, a geometric gap from
-      // 23 random bits: the regeneration draw's (gbits), bits 32..54 of an
-      // offspring's random id, or the draw (pid, ls, GAP) otherwise
+      // 23 random bits: the regeneration draw's (gbits), or the draw (pid,
+      // ls, GAP) otherwise.  (FP32 launches no offspring wave: its offspring
+      // take their first candidate interval from their next event time, in
+      // settle; an entry of an offspring queue would use bits 32..54 of its
+      // random id.)
       uint32_t m;
       if constexpr (SRC == SRC_QUEUE) m = (uint32_t)(pid >> 32) & 0x7FFFFFu;
       else if constexpr (SRC == SRC_ARRAY) m = philox_ks(p.ks, plo, phi, (uint32_t)ls, kDrawGap).x >> 9;
@@ -1741,7 +1748,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
           s.j = (j + 1) | (s.j & kRootFlag);
           defer<P>(p, wc, level + 1, s);
         } else if (!(s.j & kRootFlag)) {
-          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s);
+          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s, s.t);
         } else {
           chain_next<P>(p, wc, s);
         }
