@@ -24,6 +24,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <math_constants.h>
 #include <stdint.h>
 #include <string.h>
@@ -226,6 +227,7 @@ struct KP {
   using T = typename P::T;
   T dt, dtv, hm;
   T inv_dt;         // 1/dt
+  T dt_lo;          // the largest value below dt
   Tab4<T> tab;      // 4D model only
   const Comp* comp; // time-dependent potential: ncomp components (0: static)
   int ncomp;
@@ -565,7 +567,7 @@ struct Draw<P, false> {
     const uint4 a = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 1u + j);
     const float uc = (float)(a.w >> 16) * (1.0f / 65536.0f);
     const float uj = (float)(a.w & 0xFFFFu) * (1.0f / 65536.0f);
-    gap = (-log1pf(-u24(a.z))) * ip.ig0;
+    gap = (-logf(1.0f - u24(a.z))) * ip.ig0;  // 1 - u exact on the 2^-24 grid
     return table_kick<P>(p, ip.gamma0, xe, u24(a.x), u24(a.y), uc, uj, comp, kap, prob);
   }
   __device__ static float first(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
@@ -576,7 +578,7 @@ struct Draw<P, false> {
     }
     st.r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), (uint32_t)l, 0u);
     // below dt in exact arithmetic; kept below it after rounding
-    return fminf(to + (-log1pf(-ip.p_any_f * u24(st.r.x))) * ip.ig0, P::next_dn(p.dt));
+    return fminf(to + (-log1pf(-ip.p_any_f * u24(st.r.x))) * ip.ig0, p.dt_lo);
   }
   __device__ static void event(const KP<P>& p, const Inst<float>& ip, unsigned long long pid,
                                int l, unsigned j, bool root, const State& st, float& z,
@@ -597,8 +599,10 @@ struct Draw<P, false> {
       u4 = u24(a.w);
     }
     // Box-Muller with the angle 2 pi (u2 - 1/2) in [-pi, pi) (law unchanged)
-    z = sqrtf(-2.0f * log1pf(-u1)) * __cosf(6.2831855f * (u2 - 0.5f));
-    gap = (-log1pf(-u4)) * ip.ig0;
+    // (u1, u4 lie on the 2^-24 grid of [0, 1): 1 - u is exact, so log(1 - u)
+    // is as accurate as log1p(-u))
+    z = sqrtf(-2.0f * logf(1.0f - u1)) * __cosf(6.2831855f * (u2 - 0.5f));
+    gap = (-logf(1.0f - u4)) * ip.ig0;
   }
 };
 
@@ -1859,6 +1863,7 @@ KP<P> make_kp(const Ctx* c) {
   const wbrw_config& g = c->cfg;
   p.dt = (T)g.dt;
   p.inv_dt = (T)(1.0 / g.dt);
+  p.dt_lo = std::nextafter((T)g.dt, (T)-1e30);
   p.dtv = (T)c->dtv;
   p.hm = (T)c->hm;
   p.xmin = (T)g.xmin;
