@@ -1130,19 +1130,21 @@ __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long 
 }
 
 // Append one candidate entry per flagged lane (interval c, the position
-// streamed from the lane's interval ls to c) to the warp's segment of the
-// candidate queue p.eq.  Every lane of the warp calls it.
+// streamed from the lane's interval ls to c) to the warp's segment eq_seg
+// of the candidate queue (null when the warp owns none); ecount is the
+// segment's count, held in a register by every lane.  Every lane of the
+// warp calls it.
 template <class P>
-__device__ __forceinline__ void append_candidate(const KP<P>& p, WarpCounts& wc, bool has,
+__device__ __forceinline__ void append_candidate(const KP<P>& p, unsigned& ecount,
+                                                 FEntry<P>* eq_seg, bool has,
                                                  unsigned long long pid, const PV<P>& x,
                                                  const PV<P>& k, typename P::T w, int ls, int c,
                                                  int inst, const TanField<P::TG>& tau) {
   const int lane = threadIdx.x & 31;
   const unsigned bal = __ballot_sync(kFull, has);
   if (has) {
-    const unsigned long long g = global_warp();
-    const unsigned long long q = (unsigned long long)wc.e + __popc(bal & ((1u << lane) - 1u));
-    if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
+    const unsigned q = ecount + __popc(bal & ((1u << lane) - 1u));
+    if (eq_seg && (long long)q < p.eseg) {
       FEntry<P> e;
       static_cast<TanField<P::TG>&>(e) = tau;
       e.pid = pid;
@@ -1151,14 +1153,12 @@ __device__ __forceinline__ void append_candidate(const KP<P>& p, WarpCounts& wc,
       e.k = k;
       e.w = w;
       e.l = ent_pack(c, inst);
-      p.eq[(long long)g * p.eseg + (long long)q] = e;
+      eq_seg[q] = e;
     } else {
       set_err(p.cnt, ERR_CAP_EQUEUE);
     }
   }
-  __syncwarp();
-  if (lane == 0) wc.e += __popc(bal);
-  __syncwarp();
+  ecount += __popc(bal);
 }
 
 template <class P, int SRC, int DST>
@@ -1166,7 +1166,8 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
                                             unsigned long long slot, PV<P> x, const PV<P>& k,
                                             typename P::T w, unsigned long long pid, int ls,
                                             int inst, const TanField<P::TG>& tau,
-                                            uint32_t gbits) {
+                                            uint32_t gbits, unsigned& ecount,
+                                            FEntry<P>* eq_seg) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
   const unsigned long long g = global_warp();
@@ -1201,13 +1202,14 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
   }
 
   // ---- the warp's candidate entries.  Entry j of the warp (lanes in
-  // order, intervals in order within a lane) goes to queue slot wc.e + j and
+  // order, intervals in order within a lane) goes to queue slot ecount + j and
   // is written by lane j mod 32, which fetches its owner's state with
   // shuffles: every lane stores, and consecutive entries are adjacent.
   if constexpr (!P::is64) {
     // FP32: at most one entry per lane (the first candidate interval)
     if (__ballot_sync(kFull, mask != 0u))
-      append_candidate<P>(p, wc, mask != 0u, pid, x, k, w, ls, p.l0 + __ffs(mask) - 1, inst, tau);
+      append_candidate<P>(p, ecount, eq_seg, mask != 0u, pid, x, k, w, ls,
+                          p.l0 + __ffs(mask) - 1, inst, tau);
   } else {
   const unsigned cnt = __popc(mask);
   unsigned inc = cnt;
@@ -1248,8 +1250,8 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if (j < total) {
         for (unsigned t = j - eo; t; --t) mo &= mo - 1;  // the (j - eo)-th set bit
         const int l = p.l0 + __ffs(mo) - 1;
-        const unsigned long long q = (unsigned long long)wc.e + j;
-        if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
+        const unsigned long long q = (unsigned long long)ecount + j;
+        if (eq_seg && q < (unsigned long long)p.eseg) {
           FEntry<P> e;
           static_cast<TanField<P::TG>&>(e) = to;
           e.pid = po;
@@ -1258,15 +1260,13 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
           e.k = ko;
           e.w = wo;
           e.l = ent_pack(l, io);
-          p.eq[(long long)g * p.eseg + (long long)q] = e;
+          eq_seg[q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
         }
       }
     }
-    __syncwarp();
-    if (lane == 0) wc.e += total;
-    __syncwarp();
+    ecount += total;
   }
   }
 
@@ -1409,6 +1409,9 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
   load_counts(p, wc, 0);
   const unsigned long long g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  // the warp's candidate segment and its count, in registers
+  unsigned ecount = wc.e;
+  FEntry<P>* const eq_seg = g < (unsigned long long)p.nseg ? p.eq + (long long)g * p.eseg : nullptr;
 
   if constexpr (SRC == SRC_QUEUE) {
     // the previous wave's offspring, one producer segment at a time
@@ -1427,7 +1430,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         nx = nx2;
         nx2 = i + 64 < n ? seg[i + 64] : none;
         flight_tile<P, SRC, DST>(p, wc, acc, act, 0, e.x, e.k, e.w, e.pid, ent_l(e.l),
-                                 ent_inst(e.l), e, 0u);
+                                 ent_inst(e.l), e, 0u, ecount, eq_seg);
       }
     }
   } else {
@@ -1563,10 +1566,11 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         }
       }
       flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst, tau,
-                               gbits);
+                               gbits, ecount, eq_seg);
     }
   }
 
+  if (lane == 0) wc.e = ecount;
   store_counts(p, wc, 0, false, true, DST == DST_BIN2);
   block_reduce_add(red, acc.psteps, &p.cnt->ledger[SRC == SRC_QUEUE ? LG_PSTEPS : LG_PSTEPS0]);
   block_reduce_add(red, acc.out_p, &p.cnt->ledger[LG_OUT_P]);
