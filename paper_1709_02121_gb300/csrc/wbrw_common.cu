@@ -282,31 +282,81 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
                                                      int nseg, long long rseg,
                                                      int* keep0, int* keep1,
                                                      unsigned long long* res0,
-                                                     unsigned long long* res1) {
+                                                     unsigned long long* res1, int fx) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   double ratio[2];
-  for (int s = 0; s < 2; ++s)
+  // fx (FP32 runs): q_i in fixed point, a_i M / 2^64 with M = floor(N 2^64 / W)
+  // from one FP64 division, so that no record needs FP64 arithmetic (slow on
+  // this GPU); the integer part and the Q0.32 residual agree with the FP64
+  // form to about one unit of 2^-32 (the FP32 contract is in law).  FP64 runs
+  // keep the FP64 form, which the oracle follows.
+  unsigned long long mx[2] = {0, 0};
+  bool use_fx[2] = {false, false};
+  for (int s = 0; s < 2; ++s) {
     ratio[s] = c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
+    if (fx && c->boot_n[s] < c->boot_w[s]) {
+      const double m = ratio[s] * 18446744073709551616.0;
+      if (m < 18446744073709551616.0) {
+        mx[s] = (unsigned long long)m;
+        use_fx[s] = true;
+      }
+    }
+  }
   unsigned long long ks[2] = {0, 0};
   // records sit in one segment per producer warp; a warp takes a segment
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * kBlock) >> 5;
+  // Records of one producer segment are mostly in cell order (the first
+  // wave writes a regenerated tile's particles in order), so the warp sums
+  // runs of equal (cell, side) keys in consecutive lanes and only a run's
+  // first lane adds to the grids: far fewer contended atomics, the same
+  // integer sums.
   for (long long sg = gw; sg < nseg; sg += nw) {
     const unsigned n = min(rcnt[sg], (unsigned)rseg);
-    for (unsigned i = lane; i < n; i += 32) {
-      const long long ri = sg * rseg + i;
-      const uint32_t rc = rec_cell[ri];
-      const int side = rc >> 31;
-      const uint32_t cell = rc & 0x7FFFFFFFu;
-      const double q = __dmul_rn((double)rec_a[ri], ratio[side]);
-      const double fl = floor(q);
-      const unsigned long long res =
-          (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
-      const int kf = (int)fl;
-      if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
-      if (res) atomicAdd((side ? res1 : res0) + cell, res);
-      ks[side] += (unsigned long long)kf;
+    for (unsigned b = 0; b < n; b += 32) {
+      const unsigned i = b + lane;
+      unsigned key = ~0u;  // 2 cell + side, or none
+      int kf = 0;
+      unsigned long long res = 0;
+      if (i < n) {
+        const long long ri = sg * rseg + i;
+        const uint32_t rc = rec_cell[ri];
+        const int side = rc >> 31;
+        const uint32_t cell = rc & 0x7FFFFFFFu;
+        if (use_fx[side]) {
+          const unsigned long long a = rec_a[ri], m = mx[side];
+          kf = (int)__umul64hi(a, m);  // bits 64..95 of the 96-bit a m
+          res = (a * m) >> 32;         // bits 32..63: the Q0.32 residual
+        } else {
+          const double q = __dmul_rn((double)rec_a[ri], ratio[side]);
+          const double fl = floor(q);
+          res = (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
+          kf = (int)fl;
+        }
+        key = 2u * cell + (unsigned)side;
+      }
+      const unsigned prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+      const bool head = lane == 0 || prev != key;
+      const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+      const unsigned later = heads & ~((2u << lane) - 1u);
+      const int end = later ? __ffs(later) - 1 : 32;  // the next run's first lane
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int kf2 = __shfl_down_sync(0xFFFFFFFFu, kf, off);
+        const unsigned long long res2 = __shfl_down_sync(0xFFFFFFFFu, res, off);
+        if (lane + off < end) {
+          kf += kf2;
+          res += res2;
+        }
+      }
+      if (head && key != ~0u) {
+        const int side = key & 1u;
+        const uint32_t cell = key >> 1;
+        if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
+        if (res) atomicAdd((side ? res1 : res0) + cell, res);
+        ks[side] += (unsigned long long)kf;
+      }
     }
   }
   for (int s = 0; s < 2; ++s) {
@@ -316,14 +366,43 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
   }
 }
 
+// Guide table of the draws (the indexed search of Chen and Asau): for each
+// side and bucket j of the top kGuideBits bits of r, G_j = the first cell
+// whose inclusive residual prefix exceeds floor(j R / 2^kGuideBits), and
+// G_{2^kGuideBits} = nh - 1.  A draw with r in bucket j has its cell in
+// [G_j, G_{j+1}].
+__global__ void __launch_bounds__(kBlock) k_boot_guide(const Counters* c, long long nh,
+                                                       const unsigned long long* pre0,
+                                                       const unsigned long long* pre1,
+                                                       int* guide) {
+  const int per = kGuide + 1;
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < 2 * per; i += gridDim.x * kBlock) {
+    const int side = i / per, j = i - side * per;
+    const unsigned long long* pre = side ? pre1 : pre0;
+    long long lo = 0, hi = nh - 1;
+    if (j < kGuide) {
+      const unsigned long long R = c->boot_R[side];
+      const unsigned long long t = __umul64hi((unsigned long long)j << (64 - kGuideBits), R);
+      while (lo < hi) {
+        const long long mid = lo + (hi - lo) / 2;
+        if (pre[mid] > t) hi = mid; else lo = mid + 1;
+      }
+    } else {
+      lo = nh - 1;
+    }
+    guide[i] = (int)lo;
+  }
+}
+
 // N_r^s = N^s - sum floor(q_i) draws per side, each an upper-bound search of
-// U = floor(r R / 2^64) in the inclusive residual prefix.
+// U = floor(r R / 2^64) in the inclusive residual prefix, within the range
+// the guide table gives.
 __global__ void __launch_bounds__(kBlock) k_boot_draw(Counters* c, long long nh,
                                                       const unsigned long long* pre0,
                                                       const unsigned long long* pre1,
                                                       int* keep0, int* keep1,
-                                                      uint32_t key0, uint32_t key1,
-                                                      unsigned long long epoch) {
+                                                      const int* guide, uint32_t key0,
+                                                      uint32_t key1, unsigned long long epoch) {
   unsigned long long nr[2];
   for (int s = 0; s < 2; ++s) {
     const long long d = (long long)c->boot_n[s] - (long long)c->boot_keep[s];
@@ -344,7 +423,9 @@ __global__ void __launch_bounds__(kBlock) k_boot_draw(Counters* c, long long nh,
     const unsigned long long r64 = ((unsigned long long)r.y << 32) | r.x;
     const unsigned long long U = __umul64hi(r64, c->boot_R[side]);
     const unsigned long long* pre = side ? pre1 : pre0;
-    long long lo = 0, hi = nh - 1;  // first cell with pre > U
+    const int* gs = guide + side * (kGuide + 1);
+    const int j = (int)(r64 >> (64 - kGuideBits));
+    long long lo = gs[j], hi = gs[j + 1];  // first cell with pre > U
     while (lo < hi) {
       const long long mid = lo + (hi - lo) / 2;
       if (pre[mid] > U) hi = mid; else lo = mid + 1;
@@ -644,7 +725,7 @@ cudaError_t launch_boot(Ctx* c) {
   const int g = grid_cap(c, 8);
   k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg,
                                           c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
-                                          c->boot_res[1]);
+                                          c->boot_res[1], c->cfg.precision == WBRW_FP32);
   c->launches++;
   for (int s = 0; s < 2; ++s) {
     k_u64_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
@@ -652,11 +733,14 @@ cudaError_t launch_boot(Ctx* c) {
     k_u64_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
     c->launches += 3;
   }
+  k_boot_guide<<<(2 * (kGuide + 1) + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
+      c->cnt, nh, c->boot_res[0], c->boot_res[1], c->boot_guide);
   k_boot_draw<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_res[0], c->boot_res[1],
-                                           c->boot_keep[0], c->boot_keep[1], key0, key1, epoch);
+                                           c->boot_keep[0], c->boot_keep[1], c->boot_guide, key0,
+                                           key1, epoch);
   k_boot_combine<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_keep[0], c->boot_keep[1],
                                               c->buf.grid, key0, key1, epoch);
-  c->launches += 2;
+  c->launches += 3;
   return cudaGetLastError();
 }
 

@@ -617,6 +617,15 @@ __device__ __forceinline__ uint32_t q131(typename P::T w) {
   else return (uint32_t)(fabsf(w) * 2147483648.0f);
 }
 
+// A weight in the fixed-point units 2^-31 of the wp histogram, rounded to
+// nearest.  The scaling by 2^31 is exact in either precision, so the FP32
+// form (no FP64 arithmetic) gives the same integer as the FP64 one.
+template <class P>
+__device__ __forceinline__ long long wsum_units(typename P::T w) {
+  if constexpr (P::is64) return llrint(w * 2147483648.0);
+  else return __float2ll_rn(w * 2147483648.0f);
+}
+
 template <class P>
 __device__ __forceinline__ void tally_out(const KP<P>& p, Acc& acc, typename P::T w) {
   if (p.count_ledger) {
@@ -666,7 +675,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
   } else if constexpr (DST == DST_WSUM) {
     if (cell_of<P>(p, x, k, cell))
       atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
-                (unsigned long long)llrint((double)w * 2147483648.0));
+                (unsigned long long)wsum_units<P>(w));
     else tally_out<P>(p, acc, w);
   } else if constexpr (DST == DST_BIN2) {
     if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
@@ -1370,7 +1379,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       int cell;
       if (cell_of<P>(p, x, k, cell))
         atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
-                  (unsigned long long)llrint((double)w * 2147483648.0));
+                  (unsigned long long)wsum_units<P>(w));
       else tally_out<P>(p, acc, w);
     }
   } else {  // DST_BIN2: one record per in-grid particle of nonzero weight

@@ -13,6 +13,8 @@ constexpr int kBlock = 256;      // threads per block of every particle kernel
 constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
 constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
+constexpr int kGuideBits = 16;  // sp2 draws: guide table of 2^16 buckets per side
+constexpr int kGuide = 1 << kGuideBits;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
 constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // launch bound of the queue kernels
 // Deferred-segment levels of the event kernels: level 1 is fed by the first
@@ -184,6 +186,7 @@ struct Ctx {
   long long rec_cap;
   int* boot_keep[2];
   unsigned long long* boot_res[2];
+  int* boot_guide;    // sp2: 2 x (kGuide + 1) guide-table entries of the draws
   // state
   int state;  // 0 = particles in the arrays, 1 = histogram (grid + nz lists)
   long long step;
