@@ -277,6 +277,8 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 // sp2 bootstrap (Alg. 2 per side).  Records hold (cell | side << 31, a) with
 // a = floor(|w| 2^31); N^s and W^s = sum a were tallied with the records.
 // ---------------------------------------------------------------------------
+constexpr int kBootChunk = 1024;  // records per work item of k_boot_bin
+
 __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t* rec_cell,
                                                      const uint32_t* rec_a, const unsigned* rcnt,
                                                      int nseg, long long rseg,
@@ -312,9 +314,15 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
   // runs of equal (cell, side) keys in consecutive lanes and only a run's
   // first lane adds to the grids: far fewer contended atomics, the same
   // integer sums.
-  for (long long sg = gw; sg < nseg; sg += nw) {
-    const unsigned n = min(rcnt[sg], (unsigned)rseg);
-    for (unsigned b = 0; b < n; b += 32) {
+  // Work items: chunks of kBootChunk records of a segment, spread over all
+  // warps (a segment holds up to rseg records; most chunks of the last
+  // segments are empty)
+  const long long cps = (rseg + kBootChunk - 1) / kBootChunk;
+  for (long long it = gw; it < (long long)nseg * cps; it += nw) {
+    const long long sg = it / cps;
+    const unsigned b0 = (unsigned)((it - sg * cps) * kBootChunk);
+    const unsigned n = min(min(rcnt[sg], (unsigned)rseg), b0 + (unsigned)kBootChunk);
+    for (unsigned b = b0; b < n; b += 32) {
       const unsigned i = b + lane;
       unsigned key = ~0u;  // 2 cell + side, or none
       int kf = 0;
