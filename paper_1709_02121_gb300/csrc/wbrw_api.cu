@@ -30,7 +30,7 @@ struct Layout {
   size_t counters, cpid, fq0, fq1, eq0, eq1, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
       rec_a, keep0, keep1, res0, res1, guide, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
-      tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, dgrid0, dgrid1, tnz_cell, tnz_start,
+      tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, tab_guide0, tab_guide1, dgrid0, dgrid1, tnz_cell, tnz_start,
       tnz_tau, ttile_nz, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
@@ -154,6 +154,9 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.tab_xi1 = take(d4 ? ny * el : 0);
   L.tab_cdf0 = take(d4 ? ny * nk * el : 0);
   L.tab_cdf1 = take(d4 ? ny * nk * el : 0);
+  const size_t ng = d4 && el == 4 ? ny * (kTabGuide + 1) * 4 : 0;
+  L.tab_guide0 = take(ng);
+  L.tab_guide1 = take(ng);
   const bool tg = c->tangent != 0;
   L.dgrid0 = take(tg ? (size_t)nh * 8 : 0);
   L.dgrid1 = take(tg ? (size_t)nh * 8 : 0);
@@ -490,6 +493,8 @@ wbrw_status build_tables(wbrw_ctx* c, char* base, const Layout& L) {
   c->tab_xi[1] = base + L.tab_xi1;
   c->tab_cdf[0] = base + L.tab_cdf0;
   c->tab_cdf[1] = base + L.tab_cdf1;
+  c->tab_guide[0] = (int*)(base + L.tab_guide0);
+  c->tab_guide[1] = (int*)(base + L.tab_guide1);
   std::vector<double> A((size_t)2 * c->tab_nkap);
   const double pi = 3.141592653589793238462643383280;
   for (int t = 0; t < 2; ++t) {

@@ -200,6 +200,7 @@ template <class T>
 struct Tab4 {
   const T* xi[2];     // ny per type
   const T* cdf[2];    // ny x nkap per type
+  const int* guide[2];  // FP32: ny x (kTabGuide + 1) per type (see k_tab4_guide)
   double Y[2], inv_dy[2];
   double gam[2];      // component rates gamma_t (one-body twice, interaction once)
   double xc;          // nucleus
@@ -488,6 +489,15 @@ __device__ __forceinline__ bool table_kick(const KP<P>& p, typename P::T Gam, co
   const T* row = (t ? tb.cdf[1] : tb.cdf[0]) + (long long)r * tb.nkap;
   const T target = P::is64 ? P::mul(uk, row[tb.nkap - 1]) : uk;
   int lo = 0, hi = tb.nkap - 1;  // the first cell whose cumulative sum exceeds target
+  if constexpr (!P::is64) {
+    // FP32 rows are normalised: uk (on the 2^-24 grid) lies in bucket
+    // b = floor(uk 2^kTabGuideBits) exactly, and the answer in
+    // [G_b, G_(b+1)] of the row's guide table: the same cell as the full search
+    const int b = (int)(uk * (float)kTabGuide);
+    const int* gd = (t ? tb.guide[1] : tb.guide[0]) + (long long)r * (kTabGuide + 1);
+    lo = gd[b];
+    hi = gd[b + 1];
+  }
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
     if (row[mid] > target) hi = mid;
@@ -1906,6 +1916,7 @@ KP<P> make_kp(const Ctx* c) {
   for (int t = 0; t < 2; ++t) {
     p.tab.xi[t] = (const T*)c->tab_xi[t];
     p.tab.cdf[t] = (const T*)c->tab_cdf[t];
+    p.tab.guide[t] = c->tab_guide[t];
     p.tab.Y[t] = c->tab_Y[t];
     p.tab.inv_dy[t] = c->tab_inv_dy[t];
     p.tab.gam[t] = c->tab_gam[t];
@@ -2079,6 +2090,35 @@ __global__ void __launch_bounds__(kBlock) k_tab4(const double* A, int ny, int nk
   atomicMax(xmax + t, (unsigned long long)__double_as_longlong(xi));
 }
 
+// Guide tables of the FP32 4D kick rows (the indexed search of Chen and
+// Asau): entry b < 2^kTabGuideBits of row i is the first cell whose
+// normalised cumulative sum exceeds b 2^-kTabGuideBits (nkap - 1 if none),
+// entry 2^kTabGuideBits is nkap - 1.  A target u in [b, b + 1) 2^-kTabGuideBits
+// has its cell in [G_b, G_(b+1)].
+template <class T>
+__global__ void __launch_bounds__(kBlock) k_tab4_guide(const T* cdf0, const T* cdf1, int ny,
+                                                       int nkap, int* guide0, int* guide1) {
+  const long long per = (long long)ny * (kTabGuide + 1);
+  for (long long i = (long long)blockIdx.x * kBlock + threadIdx.x; i < 2 * per;
+       i += (long long)gridDim.x * kBlock) {
+    const int t = i < per ? 0 : 1;
+    const long long k = i - t * per;
+    const int row = (int)(k / (kTabGuide + 1)), b = (int)(k - (long long)row * (kTabGuide + 1));
+    const T* r = (t ? cdf1 : cdf0) + (long long)row * nkap;
+    int lo = 0, hi = nkap - 1;
+    if (b < kTabGuide) {
+      const T thr = (T)b * ((T)1 / (T)kTabGuide);
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (r[mid] > thr) hi = mid; else lo = mid + 1;
+      }
+    } else {
+      lo = nkap - 1;
+    }
+    (t ? guide1 : guide0)[k] = lo;
+  }
+}
+
 template <class P>
 struct DriverImpl {
   // The per-instance tables (physics, initial sampling, first slots) are
@@ -2225,6 +2265,14 @@ struct DriverImpl {
           (T*)c->tab_xi[0], (T*)c->tab_xi[1], c->tab_xmax);
       c->launches++;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if constexpr (!P::is64) {
+        const long long ng = 2ll * c->tab_ny * (kTabGuide + 1);
+        k_tab4_guide<T><<<(unsigned)((ng + kBlock - 1) / kBlock), kBlock, 0, c->stream>>>(
+            (const T*)c->tab_cdf[0], (const T*)c->tab_cdf[1], c->tab_ny, c->tab_nkap,
+            c->tab_guide[0], c->tab_guide[1]);
+        c->launches++;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
       unsigned long long m[2];
       if ((e = cudaMemcpyAsync(m, c->tab_xmax, sizeof(m), cudaMemcpyDeviceToHost, c->stream)) !=
           cudaSuccess)

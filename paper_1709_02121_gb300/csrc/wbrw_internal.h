@@ -13,6 +13,8 @@ constexpr int kBlock = 256;      // threads per block of every particle kernel
 constexpr int kMaxChunk = 32;    // steps fused in one flight (bits of a mask)
 constexpr int kScanItems = 8;    // cells per thread in the cell scans
 constexpr int kScanTile = kBlock * kScanItems;
+constexpr int kTabGuideBits = 8;  // 4D kick rows (FP32): guide table of 2^8 buckets per row
+constexpr int kTabGuide = 1 << kTabGuideBits;
 constexpr int kGuideBits = 16;  // sp2 draws: guide table of 2^16 buckets per side
 constexpr int kGuide = 1 << kGuideBits;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
@@ -132,6 +134,7 @@ struct Ctx {
   double* tab_A;                  // staging of A_tj (2 x nkap)
   void* tab_xi[2];                // ny values of type T
   void* tab_cdf[2];               // ny x nkap values of type T
+  int* tab_guide[2];              // FP32: ny x (kTabGuide + 1) guide-table entries
   unsigned long long* tab_xmax;   // the largest xi of each type
   // tangent mode (likelihood-ratio d/dH, d/dw; sp1, 2D)
   int tangent;
