@@ -610,13 +610,13 @@ def ours_grad(args, spec):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 tangents",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f32 tangent weights)",
                 "data": "synthetic",
                 "config": {"workload": wl["name"], "points_in_batch": len(insts),
                            "points": [[round(h, 4), round(v, 4)] for h, v in pts],
                            "particles_per_point": n, "grid": [wl["nx"], wl["nk"]],
                            "dt": wl["dt"], "intervals_per_step": P, "strategy": "sp1",
-                           "precision": "fp32 state, fp64 tangent weights",
+                           "precision": "fp32 state and tangent weights",
                            "cuda_graphs": not args.no_graph,
                            "l2": "flushed (512 MiB write) between timed steps",
                            "parallelism": "replicas x%d" % ws},

@@ -140,13 +140,17 @@ using P64G = PD<F64, 1, true>;
 using P32G = PD<F32, 1, true>;
 
 // The tangent weight tau = s S (sign times lineage score) of a particle, in
-// FP64 whatever the precision; an empty base outside the tangent mode.
-template <bool TG>
+// the run's precision (FP64 for the parity path; FP32 runs keep it in FP32,
+// since FP64 arithmetic is slow on this GPU); an empty base outside the
+// tangent mode.
+template <bool TG, class U = double>
 struct TanField {};
-template <>
-struct TanField<true> {
-  double th, tw;
+template <class U>
+struct TanField<true, U> {
+  U th, tw;
 };
+template <class P>
+using TanOf = TanField<P::TG, typename P::T>;
 
 // A position or a wavevector of the model.
 template <class P>
@@ -155,7 +159,7 @@ struct PV {
 };
 
 template <class P>
-struct FEntry : TanField<P::TG> {  // a particle at the start of interval l (offspring
+struct FEntry : TanOf<P> {  // a particle at the start of interval l (offspring
                                    // waves), or a candidate interval l with x at its start
   unsigned long long pid;
   PV<P> x, k;
@@ -165,7 +169,7 @@ struct FEntry : TanField<P::TG> {  // a particle at the start of interval l (off
 
 static_assert(sizeof(FEntry<P64>) == 40 && sizeof(FEntry<P32>) == 24, "FEntry layout");
 static_assert(sizeof(FEntry<Q32>) == 32, "FEntry layout");
-static_assert(sizeof(FEntry<P32G>) == 40 && sizeof(FEntry<P64G>) == 56, "FEntry layout");
+static_assert(sizeof(FEntry<P32G>) == 32 && sizeof(FEntry<P64G>) == 56, "FEntry layout");
 
 template <class P>
 struct SEntry;
@@ -181,7 +185,7 @@ struct Inst {
   float ilq;                  // FP32: 1 / ln(1 - p_any), the geometric gap's scale
   float ig0;                  // FP32: 1 / gamma0
   int well;                   // H < 0: V_W has the sign of -sin (Eq. 2)
-  double gH, gw0, gw1;        // tangent mode: 1/H, 1/w, 4w (the score of a birth)
+  T gH, gw0, gw1;             // tangent mode: 1/H, 1/w, 4w (the score of a birth)
 };
 
 // Initial sampling of one instance: slots [start, start + n) of the arrays
@@ -648,11 +652,18 @@ __device__ __forceinline__ void tally_out(const KP<P>& p, Acc& acc, typename P::
 // 2^-32 so that the sums are exact and independent of order.
 template <class P>
 __device__ __forceinline__ void add_tangent(const KP<P>& p, long long gcell,
-                                            const TanField<P::TG>& tau) {
+                                            const TanOf<P>& tau) {
   if constexpr (P::TG) {
     if (!p.dgrid[0]) return;
-    const long long a = __double2ll_rn(tau.th * 4294967296.0);
-    const long long b = __double2ll_rn(tau.tw * 4294967296.0);
+    // (scaling by 2^32 is exact in either precision)
+    long long a, b;
+    if constexpr (P::is64) {
+      a = __double2ll_rn(tau.th * 4294967296.0);
+      b = __double2ll_rn(tau.tw * 4294967296.0);
+    } else {
+      a = __float2ll_rn(tau.th * 4294967296.0f);
+      b = __float2ll_rn(tau.tw * 4294967296.0f);
+    }
     if (a) atomicAdd((unsigned long long*)(p.dgrid[0] + gcell), (unsigned long long)a);
     if (b) atomicAdd((unsigned long long*)(p.dgrid[1] + gcell), (unsigned long long)b);
   }
@@ -671,7 +682,7 @@ __device__ __forceinline__ void put_record(const KP<P>& p, Acc& acc, long long i
 template <class P, int DST>
 __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                  unsigned long long pid, const PV<P>& x, const PV<P>& k,
-                                 typename P::T w, const TanField<P::TG>& tau) {
+                                 typename P::T w, const TanOf<P>& tau) {
   using T = typename P::T;
   int cell;
   const int cbase = inst * p.nhi;
@@ -728,7 +739,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
 // pass a drain kernel finishes whatever remains with a full recursion.
 // ---------------------------------------------------------------------------
 template <class P>
-struct SEntry : TanField<P::TG> {  // a deferred segment, with the time and index of its next event
+struct SEntry : TanOf<P> {  // a deferred segment, with the time and index of its next event
   using T = typename P::T;
   unsigned long long pid;
   PV<P> xo;
@@ -742,7 +753,7 @@ struct SEntry : TanField<P::TG> {  // a deferred segment, with the time and inde
 
 static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<Q32>) == 64, "SEntry layout");
-static_assert(sizeof(SEntry<P32G>) == 80, "SEntry layout");
+static_assert(sizeof(SEntry<P32G>) == 64, "SEntry layout");
 
 constexpr unsigned kRootFlag = 0x80000000u;
 
@@ -789,7 +800,7 @@ __device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
       const unsigned slot = atomicAdd(&wc.e, 1u);
       if (g < (unsigned long long)p.nseg && slot < (unsigned long long)p.eseg) {
         FEntry<P> e;
-        static_cast<TanField<P::TG>&>(e) = static_cast<const TanField<P::TG>&>(s);
+        static_cast<TanOf<P>&>(e) = static_cast<const TanOf<P>&>(s);
         e.pid = s.pid;
 #pragma unroll
         for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(s.xo.c[d], s.k.c[d], p.dtv, c - l);
@@ -811,7 +822,7 @@ template <class P, int DST>
 __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc, int inst,
                                        unsigned long long pid, const PV<P>& xo,
                                        typename P::T to, const PV<P>& k, typename P::T w,
-                                       int l, const TanField<P::TG>& tau,
+                                       int l, const TanOf<P>& tau,
                                        typename P::T t_next) {
   const PV<P> xf = pos_at(p, xo, to, k, p.dt);
   if constexpr (!P::is64) {
@@ -829,7 +840,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
         const unsigned q = atomicAdd(&wc.e, 1u);
         if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
           FEntry<P> e;
-          static_cast<TanField<P::TG>&>(e) = tau;
+          static_cast<TanOf<P>&>(e) = tau;
           e.pid = pid;
 #pragma unroll
           for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(xf.c[d], k.c[d], p.dtv, c - l - 1);
@@ -852,7 +863,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
   }
   if (l + 1 < p.L) {
     FEntry<P> e;
-    static_cast<TanField<P::TG>&>(e) = tau;
+    static_cast<TanOf<P>&>(e) = tau;
     e.pid = pid;
     e.x = xf;
     e.k = k;
@@ -916,7 +927,7 @@ __device__ __forceinline__ void comp_kick(const KP<P>& p, const Inst<typename P:
 // An accepted event: what its +/- pair needs (the parent's id, tangent
 // weight and weight, the event's position and time, the two wavevectors).
 template <class P>
-struct Birth : TanField<P::TG> {
+struct Birth : TanOf<P> {
   using T = typename P::T;
   unsigned long long pid;
   PV<P> xe, kp, km;
@@ -939,7 +950,7 @@ __device__ __forceinline__ bool event_decide(const KP<P>& p, const Inst<typename
                                              const PV<P>& k, typename P::T w,
                                              const typename Draw<P>::State& st, int l,
                                              unsigned j, bool root, typename P::T t,
-                                             const TanField<P::TG>& tau, Birth<P>& b,
+                                             const TanOf<P>& tau, Birth<P>& b,
                                              typename P::T& gap) {
   using T = typename P::T;
   const PV<P> xe = pos_at(p, xo, to, k, t);
@@ -982,7 +993,7 @@ __device__ __forceinline__ bool event_decide(const KP<P>& p, const Inst<typename
     }
   }
   if (emit) {
-    static_cast<TanField<P::TG>&>(b) = tau;
+    static_cast<TanOf<P>&>(b) = tau;
     b.pid = pid;
     b.xe = xe;
     b.kp = kp;
@@ -1017,12 +1028,11 @@ __device__ __forceinline__ void event_pair(const KP<P>& p, const Inst<typename P
   // tangent mode: the birth's score g = (1/H, 1/w - 4 w kappa^2), the
   // derivative of log V_W^+(x_e, kappa) (Eq. 2); the + child gets
   // tau + s g, the - child its negative
-  TanField<P::TG> tp;
+  TanOf<P> tp;
   if constexpr (P::TG) {
-    const double kd = (double)b.kap;
-    const double gw = __dsub_rn(ip.gw0, __dmul_rn(__dmul_rn(ip.gw1, kd), kd));
-    tp.th = __dadd_rn(b.th, __dmul_rn((double)b.w, ip.gH));
-    tp.tw = __dadd_rn(b.tw, __dmul_rn((double)b.w, gw));
+    const T gw = P::sub(ip.gw0, P::mul(P::mul(ip.gw1, b.kap), b.kap));
+    tp.th = P::add(b.th, P::mul(b.w, ip.gH));
+    tp.tw = P::add(b.tw, P::mul(b.w, gw));
   }
   ++acc.events;
   if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
@@ -1080,7 +1090,7 @@ __device__ __forceinline__ typename P::T do_event(const KP<P>& p,
                                                   typename P::T w,
                                                   const typename Draw<P>::State& st, int l,
                                                   unsigned j, bool root, typename P::T t,
-                                                  Later later, const TanField<P::TG>& tau) {
+                                                  Later later, const TanOf<P>& tau) {
   typename P::T gap;
   Birth<P> b;
   if (event_decide<P>(p, ip, inst, pid, xo, to, k, w, st, l, j, root, t, tau, b, gap))
@@ -1158,14 +1168,14 @@ __device__ __forceinline__ void append_candidate(const KP<P>& p, unsigned& ecoun
                                                  FEntry<P>* eq_seg, bool has,
                                                  unsigned long long pid, const PV<P>& x,
                                                  const PV<P>& k, typename P::T w, int ls, int c,
-                                                 int inst, const TanField<P::TG>& tau) {
+                                                 int inst, const TanOf<P>& tau) {
   const int lane = threadIdx.x & 31;
   const unsigned bal = __ballot_sync(kFull, has);
   if (has) {
     const unsigned q = ecount + __popc(bal & ((1u << lane) - 1u));
     if (eq_seg && (long long)q < p.eseg) {
       FEntry<P> e;
-      static_cast<TanField<P::TG>&>(e) = tau;
+      static_cast<TanOf<P>&>(e) = tau;
       e.pid = pid;
 #pragma unroll
       for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(x.c[d], k.c[d], p.dtv, c - ls);
@@ -1184,7 +1194,7 @@ template <class P, int SRC, int DST>
 __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc& acc, bool act,
                                             unsigned long long slot, PV<P> x, const PV<P>& k,
                                             typename P::T w, unsigned long long pid, int ls,
-                                            int inst, const TanField<P::TG>& tau,
+                                            int inst, const TanOf<P>& tau,
                                             uint32_t gbits, unsigned& ecount,
                                             FEntry<P>* eq_seg) {
   using T = typename P::T;
@@ -1261,7 +1271,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         xo.c[d] = __shfl_sync(kFull, x.c[d], o);
         ko.c[d] = __shfl_sync(kFull, k.c[d], o);
       }
-      TanField<P::TG> to;
+      TanOf<P> to;
       if constexpr (P::TG) {
         to.th = __shfl_sync(kFull, tau.th, o);
         to.tw = __shfl_sync(kFull, tau.tw, o);
@@ -1272,7 +1282,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         const unsigned long long q = (unsigned long long)ecount + j;
         if (eq_seg && q < (unsigned long long)p.eseg) {
           FEntry<P> e;
-          static_cast<TanField<P::TG>&>(e) = to;
+          static_cast<TanOf<P>&>(e) = to;
           e.pid = po;
 #pragma unroll
           for (int d = 0; d < P::D; ++d) e.x.c[d] = stream_n<P>(xo.c[d], ko.c[d], p.dtv, l - lo_s);
@@ -1490,7 +1500,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
       unsigned long long pid = 0;
       int inst = 0;
       uint32_t gbits = 0;  // FP32: the first gap's random bits (regeneration)
-      TanField<P::TG> tau;
+      TanOf<P> tau;
       if constexpr (P::TG) tau.th = tau.tw = 0.0;
       if constexpr (RG) {
         // Alg. 3: the cell of each slot.  The tile's first nonzero cell a0
@@ -1512,8 +1522,8 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         const int lo = __popc(marks & ((2u << lane) - 1u));
         const uint32_t cwl = __shfl_sync(kFull, cw, lo);
         if constexpr (TR) {  // the tangent particles of a cell share its tau
-          const double th = idx < nz ? p.tnz_tau[2 * idx] : 0.0;
-          const double tw = idx < nz ? p.tnz_tau[2 * idx + 1] : 0.0;
+          const T th = idx < nz ? (T)p.tnz_tau[2 * idx] : (T)0;
+          const T tw = idx < nz ? (T)p.tnz_tau[2 * idx + 1] : (T)0;
           tau.th = __shfl_sync(kFull, th, lo);
           tau.tw = __shfl_sync(kFull, tw, lo);
         }
@@ -1703,7 +1713,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         const int l = ent_l(e.l), inst = ent_inst(e.l);
         const Inst<T> ip = inst_of(p, inst);
         SEntry<P> s;
-        static_cast<TanField<P::TG>&>(s) = static_cast<const TanField<P::TG>&>(e);
+        static_cast<TanOf<P>&>(s) = static_cast<const TanOf<P>&>(e);
         s.pid = e.pid;
         s.xo = e.x;
         s.to = (T)0;
