@@ -71,8 +71,9 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
   return true;
 }
 
-// Queue entries: {u64 pid; T x, k, w; int l;} for offspring waves and
-// candidate intervals; deferred segments take 64 bytes.  Every queue is cut
+// Queue entries: {u64 pid; T x, k, w; int l;} (plus the tangent weights in
+// the tangent mode) for offspring waves (FP64) and candidate intervals;
+// deferred segments take 64 bytes (FP64 tangent mode: 80).  Every queue is cut
 // into one segment per producer warp (at most kMaxSeg); each segment gets at
 // least kMinSeg entries so that small runs cannot starve a warp.
 constexpr long long kMinSeg = 64;

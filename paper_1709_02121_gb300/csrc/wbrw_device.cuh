@@ -5,22 +5,24 @@
 // Shao, arXiv:1709.02121) for a chunk of intervals [l0, L):
 //   source  SRC_ARRAY  particles in the caller's SoA arrays
 //           SRC_REGEN  Alg. 3 regeneration from the histogram, in registers
-//           SRC_QUEUE  offspring waiting at the start of a later interval
-//   flight  free streaming x <- x + (hbar/m) k dt per interval (Eq. 1) and
-//           the candidate clock of constant rate gamma0 (Sec. 3.2)
-//   events  candidate intervals are queued per warp in shared memory and
-//           processed warp-cooperatively: the kick of Remark 3, the
-//           acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair of
-//           Alg. 1 item 3 and the offspring's own events in the same interval
+//           SRC_QUEUE  (FP64) offspring waiting at the start of a later interval
+//   flight  free streaming x <- x + (hbar/m) k dt (Eq. 1) and the candidate
+//           clock of constant rate gamma0 (Sec. 3.2): which intervals hold a
+//           candidate event
 //   sink    DST_ARRAY  back to the arrays (offspring appended)
 //           DST_BIN1   signed histogram c_nu (Eq. signed_histogram)
 //           DST_BIN2   (cell, |w| in Q1.31) records for the sp2 bootstrap
-//           DST_WSUM   signed weights per cell in Q1.31 (observables)
-// Candidate intervals go to k_event and its follow-up passes (one event per
-// lane per pass).  Offspring that live into a later interval are appended to
-// the next wave, a launch of k_flight with SRC_QUEUE.  Every queue has one
-// private segment per producer warp, so appending takes no global atomic,
-// and no barrier is taken inside any main loop.
+//           DST_WSUM   signed weights per cell in fixed point (wp, observables)
+// Candidate intervals go to per-warp queue segments and round by round to
+// k_event and its follow-up passes (one event per lane per pass): the kick of
+// Remark 3, the acceptance (sp1) or weight (sp2/wp) cacc |sin|, the +/- pair
+// of Alg. 1 item 3 and the offspring's own events in the same interval.  An
+// FP32 offspring then flies on to the sink inside the event kernel, its
+// candidate intervals queued for the next round; an FP64 offspring joins the
+// next wave, a launch of k_flight with SRC_QUEUE (the FP64 clock draws per
+// interval).  Every queue has one private segment per producer warp, so
+// appending takes no global atomic, and no barrier is taken inside any main
+// loop.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -261,7 +263,7 @@ struct KP {
   int nseg;                  // segments per queue (producer warps)
   FEntry<P>* fq_in;          // offspring of the previous wave
   const unsigned* fcnt_in;
-  FEntry<P>* fq_out;         // offspring for the next wave
+  FEntry<P>* fq_out;         // offspring for the next wave (FP64)
   unsigned* fcnt_out;
   long long qseg;
   FEntry<P>* eq;             // candidate intervals: the queue appended to
