@@ -103,7 +103,8 @@ typedef struct {
   double tangent_quantum;   /* largest |tau| of a tangent particle (<= 0: 1) */
 } wbrw_config;
 
-/* Caller-owned device buffers, structure of arrays, `capacity` elements each:
+/* Caller-owned device buffers, structure of arrays, `capacity` elements each
+ * (1 <= capacity <= WBRW_MAX_CAPACITY, else WBRW_ERR_ARG at init):
  *   x, k : positions and wavevectors, double (WBRW_FP64) or float (WBRW_FP32);
  *          dim 4: 2*capacity elements each (see wbrw_init4d)
  *   s    : signs +1 / -1 (int8)
@@ -116,6 +117,7 @@ typedef struct {
  * The arrays stay owned by the caller.  Between calls they hold the current
  * particles only after wbrw_step or wbrw_particles; wbrw_run keeps the
  * particle state implicit in the histogram. */
+#define WBRW_MAX_CAPACITY 4293918720LL /* 2^32 - 2^20: slots index in 32 bits */
 typedef struct {
   void* x;
   void* k;

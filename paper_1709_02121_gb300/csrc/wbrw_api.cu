@@ -529,6 +529,7 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
                               ? (long long)config->nx * config->nx * config->nk * config->nk
                               : (long long)config->nx * config->nk;
   if (!b || !b->x || !b->k || !b->s || !b->grid || !b->scratch || b->capacity <= 0 ||
+      b->capacity > WBRW_MAX_CAPACITY ||
       (config->strategy != WBRW_SP1_PAIR && !b->w) ||
       b->grid_cells < cells * ninst || (config->tangent && !b->tangent) ||
       ((uintptr_t)b->scratch & (kAlign - 1)) != 0 ||

@@ -27,6 +27,7 @@
 
 #include <cuda_runtime.h>
 #include <cmath>
+#include <type_traits>
 #include <math_constants.h>
 #include <stdint.h>
 #include <string.h>
@@ -1477,24 +1478,28 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
     if constexpr (SRC == SRC_ARRAY) n = p.cnt->n_src;
     else n = min(TR ? p.cnt->tan_total : p.cnt->regen_total, (unsigned long long)p.tile_cap * 32ull);
     const unsigned long long n_base = p.cnt->n_base, base_pid = p.cnt->base_pid;
-    const unsigned long long nz = RG ? (TR ? p.cnt->tan_nz : p.cnt->nz_count) : 0ull;
+    // slots and plan positions of a regeneration index in 32 bits (the
+    // capacity is below 2^32 - 2^20, so no sum below overflows)
+    using IX = std::conditional_t<RG, unsigned, unsigned long long>;
+    const IX nn = (IX)n;
+    const IX nz = RG ? (IX)(TR ? p.cnt->tan_nz : p.cnt->nz_count) : (IX)0;
     // regeneration plan entries, loaded ahead: the first nonzero cell a0 two
     // tiles ahead, the starts and cells one tile ahead
-    const unsigned long long stride = nwarps * 32ull;
-    unsigned long long a0_next = 0, idx_n = 0, st_n = ~0ull;
+    const IX stride = (IX)(nwarps * 32ull);
+    IX a0_next = 0, idx_n = 0, st_n = (IX)~0ull;
     uint32_t cw_n = 0u;
     if constexpr (RG) {
-      const unsigned long long b0 = g * 32ull;
-      if (b0 < n) {
+      const IX b0 = (IX)(g * 32ull);
+      if (b0 < nn) {
         idx_n = tile_nz[b0 >> 5] + lane;
-        st_n = idx_n < nz ? nz_start[idx_n] : ~0ull;
+        st_n = idx_n < nz ? (IX)nz_start[idx_n] : (IX)~0ull;
         cw_n = idx_n < nz ? nz_cell[idx_n] : 0u;
       }
-      if (b0 + stride < n) a0_next = tile_nz[(b0 + stride) >> 5];
+      if (b0 + stride < nn) a0_next = tile_nz[(b0 + stride) >> 5];
     }
-    for (unsigned long long base = g * 32ull; base < n; base += stride) {
-      const unsigned long long slot = base + lane;
-      const bool act = slot < n;
+    for (IX base = (IX)(g * 32ull); base < nn; base += stride) {
+      const IX slot = base + lane;
+      const bool act = slot < nn;
       PV<P> x, k;
 #pragma unroll
       for (int d = 0; d < P::D; ++d) x.c[d] = k.c[d] = (T)0;
@@ -1510,16 +1515,16 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         // in at most 32 nonzero cells, whose starts strictly increase.  Lane i
         // marks bit (start of a0 + i) - base when that start falls inside the
         // tile, and slot base + lane lies in cell a0 + (marks at or below lane).
-        const unsigned long long idx = idx_n, st = st_n;
+        const IX idx = idx_n, st = st_n;
         const uint32_t cw = cw_n;
-        if (base + stride < n) {
+        if (base + stride < nn) {
           idx_n = a0_next + lane;
-          st_n = idx_n < nz ? nz_start[idx_n] : ~0ull;
+          st_n = idx_n < nz ? (IX)nz_start[idx_n] : (IX)~0ull;
           cw_n = idx_n < nz ? nz_cell[idx_n] : 0u;
         }
-        if (base + 2 * stride < n) a0_next = tile_nz[(base + 2 * stride) >> 5];
+        if (base + 2 * stride < nn) a0_next = tile_nz[(base + 2 * stride) >> 5];
         const unsigned mark =
-            (lane > 0 && st > base && st - base < 32ull) ? 1u << (unsigned)(st - base) : 0u;
+            (lane > 0 && st > base && st - base < (IX)32) ? 1u << (unsigned)(st - base) : 0u;
         const unsigned marks = __reduce_or_sync(kFull, mark);
         const int lo = __popc(marks & ((2u << lane) - 1u));
         const uint32_t cwl = __shfl_sync(kFull, cw, lo);
