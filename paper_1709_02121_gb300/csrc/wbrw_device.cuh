@@ -266,19 +266,19 @@ struct KP {
   const unsigned* fcnt_in;
   FEntry<P>* fq_out;         // offspring for the next wave (FP64)
   unsigned* fcnt_out;
-  long long qseg;
+  unsigned qseg;
   FEntry<P>* eq;             // candidate intervals: the queue appended to
   unsigned* ecnt;
   const FEntry<P>* eq_in;    // the candidate intervals k_event takes
   const unsigned* ecnt_in;
-  long long eseg;
+  unsigned eseg;
   SEntry<P>* dq[2];          // deferred segments; level L lives in dq[L & 1]
   unsigned* dcnt;            // kMaxLevels x nseg counts
-  long long dseg;
+  unsigned dseg;
   uint32_t* rec_cell;        // sp2 records (cell | side << 31, |w| in Q1.31)
   uint32_t* rec_a;
   unsigned* rcnt;
-  long long rseg;
+  unsigned rseg;
   int* grid;
   long long* wsum;
   const uint32_t* nz_cell;
@@ -348,8 +348,8 @@ __device__ __forceinline__ void set_err(Counters* c, int bit) {
   atomicOr(&c->err, bit);
 }
 
-__device__ __forceinline__ unsigned long long global_warp() {
-  return (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+__device__ __forceinline__ unsigned global_warp() {
+  return blockIdx.x * kWarps + (threadIdx.x >> 5);
 }
 
 // The histogram cell of a phase-space point (Sec. 4.3, uniform mesh):
@@ -409,9 +409,9 @@ __device__ __forceinline__ void block_reduce_add(unsigned long long* red, unsign
 
 template <class P>
 __device__ __forceinline__ void load_counts(const KP<P>& p, WarpCounts& wc, int level_out) {
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   if ((threadIdx.x & 31) == 0) {
-    const bool own = g < (unsigned long long)p.nseg;
+    const bool own = g < (unsigned)p.nseg;
     wc.f = own && p.fcnt_out ? p.fcnt_out[g] : 0u;
     wc.e = own && p.ecnt ? p.ecnt[g] : 0u;
     wc.d = own && level_out > 0 ? p.dcnt[(long long)level_out * p.nseg + g] : 0u;
@@ -424,8 +424,8 @@ template <class P>
 __device__ __forceinline__ void store_counts(const KP<P>& p, const WarpCounts& wc, int level_out,
                                              bool f, bool e, bool r) {
   __syncwarp();
-  const unsigned long long g = global_warp();
-  if ((threadIdx.x & 31) == 0 && g < (unsigned long long)p.nseg) {
+  const unsigned g = global_warp();
+  if ((threadIdx.x & 31) == 0 && g < (unsigned)p.nseg) {
     if (f && p.fcnt_out) p.fcnt_out[g] = wc.f;
     if (e && p.ecnt) p.ecnt[g] = wc.e;
     if (level_out > 0) p.dcnt[(long long)level_out * p.nseg + g] = wc.d;
@@ -704,13 +704,13 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
   } else if constexpr (DST == DST_BIN2) {
     if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
     if (w == (T)0) return;
-    const unsigned long long g = global_warp();
+    const unsigned g = global_warp();
     const unsigned r = atomicAdd(&wc.r, 1u);
-    if (g >= (unsigned long long)p.nseg || r >= (unsigned long long)p.rseg) {
+    if (g >= (unsigned)p.nseg || r >= p.rseg) {
       set_err(p.cnt, ERR_CAP_RECORDS);
       return;
     }
-    put_record<P>(p, acc, (long long)g * p.rseg + (long long)r, cell, w);
+    put_record<P>(p, acc, (size_t)g * p.rseg + r, cell, w);
   } else {  // DST_ARRAY
     const unsigned long long slot = atomicAdd(&p.cnt->n, 1ull);
     if (slot >= (unsigned long long)p.capacity) { set_err(p.cnt, ERR_CAP_PARTICLES); return; }
@@ -799,9 +799,9 @@ __device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
     const float q = fmaxf(floorf(s.t * p.inv_dt), 1.0f);  // s.t >= dt
     if (q < (float)(p.L - l)) {
       const int c = l + (int)q;
-      const unsigned long long g = global_warp();
+      const unsigned g = global_warp();
       const unsigned slot = atomicAdd(&wc.e, 1u);
-      if (g < (unsigned long long)p.nseg && slot < (unsigned long long)p.eseg) {
+      if (g < (unsigned)p.nseg && slot < p.eseg) {
         FEntry<P> e;
         static_cast<TanOf<P>&>(e) = static_cast<const TanOf<P>&>(s);
         e.pid = s.pid;
@@ -810,7 +810,7 @@ __device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
         e.k = s.k;
         e.w = s.w;
         e.l = ent_pack(c, ent_inst(s.l));
-        p.eq[(long long)g * p.eseg + (long long)slot] = e;
+        p.eq[(size_t)g * p.eseg + slot] = e;
       } else {
         set_err(p.cnt, ERR_CAP_EQUEUE);
       }
@@ -839,9 +839,9 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
       const float q = fmaxf(floorf(t_next * p.inv_dt), 1.0f);
       const int c = q < (float)(n + 1) ? l + (int)q : p.L;
       if (c < p.L) {
-        const unsigned long long g = global_warp();
+        const unsigned g = global_warp();
         const unsigned q = atomicAdd(&wc.e, 1u);
-        if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.eseg) {
+        if (g < (unsigned)p.nseg && q < p.eseg) {
           FEntry<P> e;
           static_cast<TanOf<P>&>(e) = tau;
           e.pid = pid;
@@ -850,7 +850,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
           e.k = k;
           e.w = w;
           e.l = ent_pack(c, inst);
-          p.eq[(long long)g * p.eseg + (long long)q] = e;
+          p.eq[(size_t)g * p.eseg + q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
         }
@@ -872,10 +872,10 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
     e.k = k;
     e.w = w;
     e.l = ent_pack(l + 1, inst);
-    const unsigned long long g = global_warp();
+    const unsigned g = global_warp();
     const unsigned q = atomicAdd(&wc.f, 1u);
-    if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.qseg)
-      p.fq_out[(long long)g * p.qseg + (long long)q] = e;
+    if (g < (unsigned)p.nseg && q < p.qseg)
+      p.fq_out[(size_t)g * p.qseg + q] = e;
     else
       set_err(p.cnt, ERR_CAP_QUEUE);
   } else {
@@ -887,10 +887,10 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
 template <class P>
 __device__ __forceinline__ void defer(const KP<P>& p, WarpCounts& wc, int level,
                                       const SEntry<P>& s) {
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   const unsigned q = atomicAdd(&wc.d, 1u);
-  if (g < (unsigned long long)p.nseg && q < (unsigned long long)p.dseg)
-    ((level & 1) ? p.dq[1] : p.dq[0])[(long long)g * p.dseg + (long long)q] = s;
+  if (g < (unsigned)p.nseg && q < p.dseg)
+    ((level & 1) ? p.dq[1] : p.dq[0])[(size_t)g * p.dseg + q] = s;
   else
     set_err(p.cnt, ERR_CAP_EQUEUE);
 }
@@ -1176,7 +1176,7 @@ __device__ __forceinline__ void append_candidate(const KP<P>& p, unsigned& ecoun
   const unsigned bal = __ballot_sync(kFull, has);
   if (has) {
     const unsigned q = ecount + __popc(bal & ((1u << lane) - 1u));
-    if (eq_seg && (long long)q < p.eseg) {
+    if (eq_seg && q < p.eseg) {
       FEntry<P> e;
       static_cast<TanOf<P>&>(e) = tau;
       e.pid = pid;
@@ -1202,7 +1202,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
                                             FEntry<P>* eq_seg) {
   using T = typename P::T;
   const int lane = threadIdx.x & 31;
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   const Inst<T> ip = inst_of(p, inst);
   const int cbase = inst * p.nhi;
 
@@ -1283,7 +1283,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         for (unsigned t = j - eo; t; --t) mo &= mo - 1;  // the (j - eo)-th set bit
         const int l = p.l0 + __ffs(mo) - 1;
         const unsigned long long q = (unsigned long long)ecount + j;
-        if (eq_seg && q < (unsigned long long)p.eseg) {
+        if (eq_seg && q < p.eseg) {
           FEntry<P> e;
           static_cast<TanOf<P>&>(e) = to;
           e.pid = po;
@@ -1415,7 +1415,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     if (bal) {
       const unsigned off = wc.r + __popc(bal & ((1u << lane) - 1u));
       if (cell >= 0) {
-        if (g >= (unsigned long long)p.nseg || off >= (unsigned long long)p.rseg)
+        if (g >= (unsigned)p.nseg || off >= p.rseg)
           set_err(p.cnt, ERR_CAP_RECORDS);
         else
           put_record<P>(p, acc, (long long)g * p.rseg + (long long)off, cell, w);
@@ -1439,18 +1439,18 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
   Acc acc;
   acc.zero();
   load_counts(p, wc, 0);
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   // the warp's candidate segment and its count, in registers
   unsigned ecount = wc.e;
-  FEntry<P>* const eq_seg = g < (unsigned long long)p.nseg ? p.eq + (long long)g * p.eseg : nullptr;
+  FEntry<P>* const eq_seg = g < (unsigned)p.nseg ? p.eq + (long long)g * p.eseg : nullptr;
 
   if constexpr (SRC == SRC_QUEUE) {
     // the previous wave's offspring, one producer segment at a time
     // (the next tile's entries load while the current tile is processed)
     FEntry<P> none{};
     none.l = p.L;
-    for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+    for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) {
       const unsigned n = min(p.fcnt_in[sg], (unsigned)p.qseg);
       const FEntry<P>* seg = p.fq_in + (long long)sg * p.qseg;
       FEntry<P> nx = (unsigned)lane < n ? seg[lane] : none;
@@ -1673,7 +1673,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
   Acc acc;
   acc.zero();
   load_counts(p, wc, 1);
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
   // FP32 2D: the accepted events of the warp's tiles wait in a per-warp
@@ -1699,7 +1699,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
       nb -= take;
     }
   };
-  for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+  for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) {
     const unsigned n = min(p.ecnt_in[sg], (unsigned)p.eseg);
     const FEntry<P>* seg = p.eq_in + (long long)sg * p.eseg;
     // each lane copies its entry of the next tile into shared memory
@@ -1771,12 +1771,12 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
   Acc acc;
   acc.zero();
   load_counts(p, wc, level + 1);
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, level + 1, ch); };
-  for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+  for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) {
     const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
     for (unsigned b = 0; b < n; b += 32) {
       const unsigned i = b + lane;
@@ -1813,11 +1813,11 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p
   Acc acc;
   acc.zero();
   load_counts(p, wc, 0);
-  const unsigned long long g = global_warp();
+  const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
-  for (unsigned long long sg = g; sg < (unsigned long long)p.nseg; sg += nwarps) {
+  for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) {
     const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
     for (unsigned i = lane; i < n; i += 32)
       finish_segment<P, DST>(p, wc, acc, in[(long long)sg * p.dseg + i]);
@@ -1965,20 +1965,20 @@ KP<P> make_kp(const Ctx* c) {
   p.fcnt_in = c->fcnt[0];
   p.fq_out = (FEntry<P>*)c->fq[1];
   p.fcnt_out = c->fcnt[1];
-  p.qseg = c->qseg;
+  p.qseg = (unsigned)c->qseg;
   p.eq = (FEntry<P>*)c->eq[0];
   p.ecnt = c->ecnt[0];
   p.eq_in = (const FEntry<P>*)c->eq[1];
   p.ecnt_in = c->ecnt[1];
-  p.eseg = c->eseg;
+  p.eseg = (unsigned)c->eseg;
   p.dq[0] = (SEntry<P>*)c->dq[0];
   p.dq[1] = (SEntry<P>*)c->dq[1];
   p.dcnt = c->dcnt;
-  p.dseg = c->dseg;
+  p.dseg = (unsigned)c->dseg;
   p.rec_cell = c->rec_cell;
   p.rec_a = c->rec_a;
   p.rcnt = c->cfg.strategy == WBRW_SP2_BOOTSTRAP ? c->rcnt : nullptr;
-  p.rseg = c->rseg;
+  p.rseg = (unsigned)c->rseg;
   p.grid = c->buf.grid;
   p.wsum = c->tmp_wsum;
   p.rec_cell = c->rec_cell;
