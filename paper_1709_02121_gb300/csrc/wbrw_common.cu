@@ -322,22 +322,23 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
     const long long sg = it / cps;
     const unsigned b0 = (unsigned)((it - sg * cps) * kBootChunk);
     const unsigned n = min(min(rcnt[sg], (unsigned)rseg), b0 + (unsigned)kBootChunk);
+    const uint32_t* rcs = rec_cell + sg * rseg;  // the segment's records
+    const uint32_t* ras = rec_a + sg * rseg;
     for (unsigned b = b0; b < n; b += 32) {
       const unsigned i = b + lane;
       unsigned key = ~0u;  // 2 cell + side, or none
       int kf = 0;
       unsigned long long res = 0;
       if (i < n) {
-        const long long ri = sg * rseg + i;
-        const uint32_t rc = rec_cell[ri];
+        const uint32_t rc = rcs[i];
         const int side = rc >> 31;
         const uint32_t cell = rc & 0x7FFFFFFFu;
         if (use_fx[side]) {
-          const unsigned long long a = rec_a[ri], m = mx[side];
+          const unsigned long long a = ras[i], m = mx[side];
           kf = (int)__umul64hi(a, m);  // bits 64..95 of the 96-bit a m
           res = (a * m) >> 32;         // bits 32..63: the Q0.32 residual
         } else {
-          const double q = __dmul_rn((double)rec_a[ri], ratio[side]);
+          const double q = __dmul_rn((double)ras[i], ratio[side]);
           const double fl = floor(q);
           res = (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
           kf = (int)fl;
@@ -433,9 +434,9 @@ __global__ void __launch_bounds__(kBlock) k_boot_draw(Counters* c, long long nh,
     const unsigned long long* pre = side ? pre1 : pre0;
     const int* gs = guide + side * (kGuide + 1);
     const int j = (int)(r64 >> (64 - kGuideBits));
-    long long lo = gs[j], hi = gs[j + 1];  // first cell with pre > U
+    int lo = gs[j], hi = gs[j + 1];  // first cell with pre > U (nh < 2^31)
     while (lo < hi) {
-      const long long mid = lo + (hi - lo) / 2;
+      const int mid = lo + ((hi - lo) >> 1);
       if (pre[mid] > U) hi = mid; else lo = mid + 1;
     }
     atomicAdd((side ? keep1 : keep0) + lo, 1);
