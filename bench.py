@@ -695,7 +695,7 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
 INT_OPS_PER_PARTICLE = {"fp32": (120, 0), "fp32_4d": (135, 0),
                         "fp64": (116, 100), "fp64_4d": (230, 100)}
 # DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
-TRAFFIC_PER_PSTEP = {"fp32": 0.573, "fp64": None, "fp32_4d": 1.18, "fp64_4d": None}
+TRAFFIC_PER_PSTEP = {"fp32": 0.579, "fp64": None, "fp32_4d": 1.19, "fp64_4d": None}
 
 
 def main():
