@@ -203,21 +203,33 @@ __global__ void __launch_bounds__(kBlock) k_cells_c(const int* grid, long long n
   unsigned long long os = block_exscan(s, red, ts) + bsum[blockIdx.x];
   unsigned long long oz = block_exscan(z, red, tz) + bnz[blockIdx.x];
   long long next_inst = (base + nhi - 1) / nhi * nhi;  // first instance boundary >= base
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     if (base + i == next_inst && next_inst < nh) {
       inst_slot[next_inst / nhi] = os;
       next_inst += nhi;
     }
+    // every 32-slot tile whose first slot falls in this cell starts here:
+    // tiles [t0, t1) (tile indices fit 32 bits: tile_cap <= capacity / 32 + 2)
+    unsigned t0 = 0, t1 = 0;
+    const uint32_t val = (uint32_t)oz;
     if (v[i] != 0) {
       const unsigned long long m = (unsigned long long)(v[i] < 0 ? -(long long)v[i] : (long long)v[i]);
       nz_cell[oz] = (uint32_t)(base + i) | (v[i] < 0 ? 0x80000000u : 0u);
       nz_start[oz] = os;
-      // every 32-slot tile whose first slot falls in this cell starts here
-      const unsigned long long t_end = min((os + m + 31) >> 5, (unsigned long long)tile_cap);
-      for (unsigned long long t = (os + 31) >> 5; t < t_end; ++t) tile_nz[t] = (uint32_t)oz;
+      t0 = (unsigned)min((os + 31) >> 5, (unsigned long long)tile_cap);
+      t1 = (unsigned)min((os + m + 31) >> 5, (unsigned long long)tile_cap);
       ++oz;
       os += m;
+    }
+    // the warp writes each lane's tile range in turn, 32 consecutive
+    // entries per store (a dense cell spans many tiles)
+    for (unsigned pend = __ballot_sync(0xFFFFFFFFu, t1 > t0); pend; pend &= pend - 1) {
+      const int src = __ffs(pend) - 1;
+      const unsigned a = __shfl_sync(0xFFFFFFFFu, t0, src), b = __shfl_sync(0xFFFFFFFFu, t1, src);
+      const uint32_t w = __shfl_sync(0xFFFFFFFFu, val, src);
+      for (unsigned t = a + lane; t < b; t += 32) tile_nz[t] = w;
     }
   }
 }
