@@ -82,6 +82,15 @@ def test_init_rejects_bad_arguments_without_touching_a_gpu(lib):
     assert lib.wbrw_step(None, 1) == wbrw.ERR_ARG
     assert lib.wbrw_last_error(None) == b"NULL context"
     lib.wbrw_destroy(None)
+    # a capacity beyond the 32-bit slot limit is refused before any buffer
+    # (here placeholders that are never dereferenced) is touched
+    fake = wbrw.Buffers(256, 256, 256, None, wbrw.MAX_CAPACITY + 1, 256, 1 << 20, 256, 1 << 40,
+                        None, 0, None)
+    st = lib.wbrw_init(ctypes.byref(cfg), ctypes.byref(pot), ctypes.byref(fake), 10,
+                       -15.0, 2.5, 1.5, None, ctypes.byref(ctx))
+    assert st == wbrw.ERR_ARG and not ctx.value
+    hdr = open(os.path.join(ROOT, "include", "wbrw.h")).read()
+    assert "#define WBRW_MAX_CAPACITY %dLL" % wbrw.MAX_CAPACITY in hdr
 
 
 def test_product_path_has_no_fallback(tmp_path):
