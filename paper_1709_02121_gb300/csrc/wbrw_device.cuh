@@ -930,7 +930,7 @@ __device__ __forceinline__ void comp_kick(const KP<P>& p, const Inst<typename P:
 // An accepted event: what its +/- pair needs (the parent's id, tangent
 // weight and weight, the event's position and time, the two wavevectors).
 template <class P>
-struct Birth : TanOf<P> {
+struct __align__(16) Birth : TanOf<P> {
   using T = typename P::T;
   unsigned long long pid;
   PV<P> xe, kp, km;
