@@ -23,6 +23,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -107,7 +108,8 @@ class Clocks:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % gpu_index)
+        self.path = os.path.join(tempfile.gettempdir(), "wbrw_clocks_%d_%d.csv" % (gpu_index,
+                                                                               os.getpid()))
 
     def start(self):
         try:
@@ -658,7 +660,7 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
     pipe (Philox4x32-10 is 32-bit multiplies and XORs).
 
     achieved = the algorithm's integer operations per first-wave particle
-    and period (INT_OPS_PER_PARTICLE, derived in the design doc) / the period's
+    and period (INT_OPS_PER_PARTICLE, counted below) / the period's
     intervals x the first-wave particle-steps of one launch / the launch's
     average CUDA-event time.
     peak = 152 SMs x 64 INT32 lanes x the median SM clock sampled during the
@@ -686,7 +688,7 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
 
 
 # Integer operations per first-wave particle and period of R intervals
-# ("Roofline of the first wave"): (per particle, per interval).
+# (per particle, per interval).
 # A Philox4x32-10 call counts 100 (10 rounds of two 32x32->64 multiplies as
 # lo and hi, four XORs, two key additions).  FP32: one call per particle
 # (regeneration offsets and the first candidate gap) plus the cell decode,
