@@ -44,7 +44,7 @@ STEP_BOOT = 0xFFFFFFFD
 STEP_ROUND = 0xFFFFFFFC
 
 LEDGER = ("events", "kill_plus", "kill_minus", "out_plus", "out_minus",
-          "particle_steps", "_6", "_7")
+          "particle_steps", "candidates", "first_pairs")
 
 
 def build(force: bool = False) -> str:

@@ -98,7 +98,10 @@ typedef struct {
   double gam; /* ceil(1024 max_i xi_i)/1024 */
 } orc4_table;
 
-enum { O4_EVENTS = 0, O4_KILL_P, O4_KILL_M, O4_OUT_P, O4_OUT_M, O4_PSTEPS, O4_LN = 8 };
+/* O4_CAND: intervals in which a particle alive at their start has its first
+ * event; O4_PAIRS0: those whose first event emits a pair. */
+enum { O4_EVENTS = 0, O4_KILL_P, O4_KILL_M, O4_OUT_P, O4_OUT_M, O4_PSTEPS, O4_CAND, O4_PAIRS0,
+       O4_LN = 8 };
 
 typedef struct {
   orc4_config c;
@@ -354,6 +357,7 @@ static int segment4(orc4_state* s, double x1o, double x2o, double to, double k1,
   double u0 = orc_u53(r[0], r[1]);
   double t = to + (-log1p(-u0) / s->Gam);
   uint32_t j = 0;
+  if (is_root && t < c->dt) s->ledger[O4_CAND] += 1;
   while (t < c->dt) {
     double x1e = x1o + k1 * ((t - to) * s->hm);
     double x2e = x2o + k2 * ((t - to) * s->hm);
@@ -382,6 +386,7 @@ static int segment4(orc4_state* s, double x1o, double x2o, double to, double k1,
       int kill_p = !(kin(s, kp1) && kin(s, kp2));
       int kill_m = !(kin(s, km1) && kin(s, km2));
       s->ledger[O4_EVENTS] += 1;
+      if (is_root && j == 0) s->ledger[O4_PAIRS0] += 1;
       double wp = w, wm = -w;
       if (kill_p) { if (wp > 0) s->ledger[O4_KILL_P] += 1; else s->ledger[O4_KILL_M] += 1; }
       if (kill_m) { if (wm > 0) s->ledger[O4_KILL_P] += 1; else s->ledger[O4_KILL_M] += 1; }

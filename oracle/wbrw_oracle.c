@@ -171,6 +171,9 @@ enum {
   ORC_L_OUT_P = 3,   /* + particles outside the histogram at binning    */
   ORC_L_OUT_M = 4,   /* - particles outside the histogram at binning    */
   ORC_L_PSTEPS = 5,  /* sum over steps of particles alive at step start */
+  ORC_L_CAND = 6,    /* candidate intervals: a particle alive at the start
+                        of an interval has its first event inside it     */
+  ORC_L_PAIRS0 = 7,  /* the candidate intervals whose first event emits  */
   ORC_L_N = 8
 };
 
@@ -368,6 +371,7 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
   double u0 = orc_u53(r[0], r[1]);
   double t = to + (-log1p(-u0) / s->gamma0);
   uint32_t j = 0;
+  if (is_root && t < c->dt) s->ledger[ORC_L_CAND] += 1;
   while (t < c->dt) {
     double xe = xo + k * ((t - to) * s->hm);
     uint32_t a[4], b[4];
@@ -426,6 +430,7 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
       int kill_p = !(kp >= c->kmin && kp < c->kmax);
       int kill_m = !(km >= c->kmin && km < c->kmax);
       s->ledger[ORC_L_EVENTS] += 1;
+      if (is_root && j == 0) s->ledger[ORC_L_PAIRS0] += 1;
       double wp = wc, wm = -wc; /* + child carries +wc, - child -wc */
       double gH = 1.0 / c->H, gw = 1.0 / c->w - 4.0 * c->w * kap * kap;
       double tpH = tH + w * gH, tpw = tw + w * gw; /* + child's tangent    */
