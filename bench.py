@@ -281,6 +281,7 @@ def ours(args, wl):
     barrier()
     clk = clocks.stop()
     kern_ms, kern_n = wbrw.wbrw_profile_read(sim.ctx)
+    ev_ms, ev_n = wbrw.wbrw_profile_read_events(sim.ctx)
     wbrw.wbrw_profile(sim.ctx, False)
     c1 = sim.counters()
     t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
@@ -324,7 +325,10 @@ def ours(args, wl):
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except Exception:
             pass
-        roof = roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk)
+        roof, roof2 = dominant(
+            roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk),
+            roofline_event(wl, ev_ms, ev_n, c1["candidates"] - c0["candidates"],
+                           c1["first_pairs"] - c0["first_pairs"], peaks, clk))
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -332,7 +336,7 @@ def ours(args, wl):
                 "dtype": "f32" if wl["precision"] == "fp32" else "f64",
                 "data": "synthetic", "config": config_of(wl, args),
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-                "clocks": clk, "tuning": tuning,
+                "roofline_secondary": roof2, "clocks": clk, "tuning": tuning,
                 "live_particles_end": c1["live"],
                 "particle_steps": psteps}
         if not args.no_cpu_baseline and ws == 1:
@@ -401,6 +405,7 @@ def ours_batch(args, spec):
     barrier()
     clk = clocks.stop()
     kern_ms, kern_n = wbrw.wbrw_profile_read(sim.ctx)
+    ev_ms, ev_n = wbrw.wbrw_profile_read_events(sim.ctx)
     wbrw.wbrw_profile(sim.ctx, False)
     c1 = sim.counters()
     t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
@@ -485,7 +490,10 @@ def ours_batch(args, spec):
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
         except Exception:
             pass
-        roof = roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk)
+        roof, roof2 = dominant(
+            roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk),
+            roofline_event(wl, ev_ms, ev_n, c1["candidates"] - c0["candidates"],
+                           c1["first_pairs"] - c0["first_pairs"], peaks, clk))
         ns = [v["n_init"] for v in insts]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup,
@@ -499,8 +507,8 @@ def ours_batch(args, spec):
                            "cuda_graphs": graphs,
                            "l2": "flushed (512 MiB write) between timed steps",
                            "parallelism": "replicas x%d" % ws},
-                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk,
-                "tuning": tuning,
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+                "roofline_secondary": roof2, "clocks": clk, "tuning": tuning,
                 "live_particles_end": c1["live"], "particle_steps": psteps,
                 "transmission_mean": float(np.mean(T_batch))}
         if plain is not None:
@@ -652,12 +660,56 @@ def reduce_over_ranks(ws, t_ms, psteps, e2e_value, device):
     return float(tt.item()), float(sums[0].item()), float(sums[1].item())
 
 
+def dominant(*roofs):
+    """The rooflines ordered by the kernel's total time in the timed region:
+    (the dominant kernel's, the other's)."""
+    r = sorted((x for x in roofs if x), key=lambda x: -x["total_ms"])
+    return (r[0] if r else None), (r[1] if len(r) > 1 else None)
+
+
+def _int_peak(peaks, clk):
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    return 152 * 64 * sm_mhz * 1e6 / 1e9, sm_mhz
+
+
+def roofline_event(wl, ev_ms, ev_n, cand, pairs, peaks, clk):
+    """Roofline of the event kernel (k_event), which performs the first event
+    of every candidate interval: the kick, the acceptance and, for an
+    accepted event, the pair; in FP32 the offspring then fly to the end of
+    the period into the histogram inside the same kernel.  Its work is
+    Philox calls, the entry decode and the histogram index arithmetic on the
+    integer pipe, with a few transcendental functions per event.
+
+    achieved = (INT_OPS_EVENT per candidate x candidates + per pair x
+    first-event pairs) of the timed region / the kernel's summed CUDA-event
+    time; both counts are device counters.
+    peak = 152 SMs x 64 INT32 lanes x the median SM clock sampled during the
+    timed region."""
+    if not ev_n or ev_ms <= 0 or cand <= 0:
+        return None
+    key = wl["precision"] + ("_4d" if wl.get("dim", 2) == 4 else "")
+    per_cand, per_pair = INT_OPS_EVENT[key]
+    peak, sm_mhz = _int_peak(peaks, clk)
+    ops = per_cand * cand + per_pair * pairs
+    ach = ops / (ev_ms / 1e3) / 1e9
+    tpc = TRAFFIC_PER_CANDIDATE.get(key)
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
+            "frac": ach / peak, "traffic": tpc and tpc * cand / ev_n,
+            "kernel": "k_event<%s%s,bin>" % (wl["precision"],
+                                             ",4d" if wl.get("dim", 2) == 4 else ""),
+            "launch_ms": ev_ms / ev_n, "launches": ev_n, "total_ms": ev_ms,
+            "candidates_per_launch": cand / ev_n, "first_pairs_per_candidate": pairs / cand,
+            "int_ops_per_candidate": ops / cand,
+            "peak_basis": "152 SM x 64 INT32 lanes x %.0f MHz (median SM clock sampled in the "
+                          "timed region)" % sm_mhz}
+
+
 def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
-    """Roofline of the dominant kernel: the fused regenerate + flight +
-    histogram pass that carries the particles present at the start of each
-    period (the first wave).  The particle state never leaves registers and
-    HBM sees only the candidate queue, so the pass is bound by the integer
-    pipe (Philox4x32-10 is 32-bit multiplies and XORs).
+    """Roofline of the first wave: the fused regenerate + flight + histogram
+    pass that carries the particles present at the start of each period.
+    The particle state never leaves registers and HBM sees only the
+    candidate queue, so the pass is bound by the integer pipe
+    (Philox4x32-10 is 32-bit multiplies and XORs).
 
     achieved = the algorithm's integer operations per first-wave particle
     and period (INT_OPS_PER_PARTICLE, counted below) / the period's
@@ -672,15 +724,14 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
     base, per_interval = INT_OPS_PER_PARTICLE[key]
     ops = (base + per_interval * R) / R
     per_launch_ms = kern_ms / kern_n
-    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak = 152 * 64 * sm_mhz * 1e6 / 1e9
+    peak, sm_mhz = _int_peak(peaks, clk)
     ach = ops * (psteps_first / kern_n) / (per_launch_ms / 1e3) / 1e9
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gop/s",
             "frac": ach / peak, "traffic": TRAFFIC_PER_PSTEP.get(key) and
             TRAFFIC_PER_PSTEP[key] * psteps_first / kern_n,
             "kernel": "k_flight<%s%s,regen,bin>" % (wl["precision"],
                                                      ",4d" if wl.get("dim", 2) == 4 else ""),
-            "launch_ms": per_launch_ms, "launches": kern_n,
+            "launch_ms": per_launch_ms, "launches": kern_n, "total_ms": kern_ms,
             "first_wave_particle_steps_per_launch": psteps_first / kern_n,
             "int_ops_per_particle_step": ops,
             "peak_basis": "152 SM x 64 INT32 lanes x %.0f MHz (median SM clock sampled in the "
@@ -698,6 +749,21 @@ INT_OPS_PER_PARTICLE = {"fp32": (120, 0), "fp32_4d": (135, 0),
                         "fp64": (116, 100), "fp64_4d": (230, 100)}
 # DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
 TRAFFIC_PER_PSTEP = {"fp32": 0.579, "fp64": None, "fp32_4d": 1.19, "fp64_4d": None}
+
+# Integer operations of the event kernel (per candidate interval, per pair
+# of its first event).  A candidate: the Philox calls of its first event (one
+# in FP32 2D, where it also gives the life-length; the life-length call and
+# the event's call in FP32 4D; one plus the event's two in FP64) and about 20
+# for the entry decode, the uniforms and the next candidate interval, plus
+# the guided table search of the 4D kick.  A pair: the Philox call of the
+# offspring ids and, per offspring, about 20 for the first-event bits, the
+# kill test, the cell index and the histogram index (30 with the four 4D
+# indices).
+INT_OPS_EVENT = {"fp32": (120, 140), "fp32_4d": (240, 160),
+                 "fp64": (320, 140), "fp64_4d": (340, 160)}
+# DRAM bytes per candidate interval of the event kernel measured by ncu
+# (profiles/), or None
+TRAFFIC_PER_CANDIDATE = {"fp32": None, "fp64": None, "fp32_4d": None, "fp64_4d": None}
 
 
 def main():

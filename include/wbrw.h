@@ -172,6 +172,10 @@ enum {
   WBRW_C_ERROR = 18,      /* device error word                               */
   WBRW_C_PARTICLE_STEPS_FIRST = 19, /* the part carried by the first wave of  */
                                     /* each chunk (particles present at its start) */
+  WBRW_C_CANDIDATES = 20, /* candidate intervals, cumulative: a particle alive */
+                          /* at the start of an interval has its first event   */
+                          /* inside it (probability 1 - exp(-gamma0 dt), Sec. 3.2) */
+  WBRW_C_FIRST_PAIRS = 21, /* of those, the first events that emitted a pair  */
   WBRW_C_COUNT = 24
 };
 
@@ -302,6 +306,16 @@ wbrw_status wbrw_restore(wbrw_ctx* ctx, const int* grid, long long step,
 wbrw_status wbrw_profile(wbrw_ctx* ctx, int enable);
 wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
                               long long* launches);
+
+/* The same for the event kernel, which performs the first event of every
+ * candidate interval (WBRW_C_CANDIDATES counts them): while wbrw_profile is
+ * enabled each of its launches is bracketed by CUDA events on the context's
+ * stream (at most 4096 launches are kept; in a CUDA-graph replay, those of
+ * the period's first 64 rounds).  wbrw_profile_read_events synchronises and
+ * returns the summed milliseconds and the launch count since the last read
+ * or enable. */
+wbrw_status wbrw_profile_read_events(wbrw_ctx* ctx, double* total_ms,
+                                     long long* launches);
 
 /* CUDA graphs for wbrw_run.  With enable = 1, each sp1 resampling period that
  * regenerates its particles from the histogram (every period but one that

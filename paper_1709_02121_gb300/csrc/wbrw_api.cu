@@ -363,8 +363,13 @@ wbrw_status capture_period(wbrw_ctx* c, int len, PeriodGraph* g) {
     if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) continue;
     if (ev == c->gev[0]) g->ev_begin = nodes[i];
     if (ev == c->gev[1]) g->ev_end = nodes[i];
+    for (int r = 0; r < kProfRounds; ++r) {
+      if (ev == c->gev[2 + 2 * r]) g->evk_begin[r] = nodes[i];
+      if (ev == c->gev[3 + 2 * r]) g->evk_end[r] = nodes[i];
+    }
   }
   free(nodes);
+  while (g->nevk < kProfRounds && g->evk_begin[g->nevk] && g->evk_end[g->nevk]) g->nevk += 1;
   WBRW_TRY(c, ge, "graph nodes");
   WBRW_TRY(c, cudaGraphInstantiate(&g->exec, graph, 0), "instantiate graph");
   return WBRW_OK;
@@ -386,7 +391,7 @@ wbrw_status graph_period(wbrw_ctx* c, int len) {
     WBRW_TRY(c, launch_setup(c, SETUP_PERIOD, (unsigned long long)c->step,
                              (unsigned long long)c->epoch << 40), "period state");
   if (g->ev_begin && g->ev_end) {
-    const bool on = c->prof_on && c->prof_n < 4096;
+    const bool on = c->prof_on && c->prof_n < kProfLaunches;
     WBRW_TRY(c, cudaGraphExecEventRecordNodeSetEvent(
                     g->exec, g->ev_begin, on ? c->prof_ev[2 * c->prof_n] : c->gev[0]),
              "profile event");
@@ -394,6 +399,23 @@ wbrw_status graph_period(wbrw_ctx* c, int len) {
                     g->exec, g->ev_end, on ? c->prof_ev[2 * c->prof_n + 1] : c->gev[1]),
              "profile event");
     if (on) c->prof_n += 1;
+  }
+  // the event kernel's records: on profiling events while profiling, else
+  // back on the placeholders (once)
+  const bool on_k = c->prof_on && c->prof_nk + g->nevk <= kProfLaunches;
+  if (on_k || g->evk_live) {
+    for (int r = 0; r < g->nevk; ++r) {
+      WBRW_TRY(c, cudaGraphExecEventRecordNodeSetEvent(
+                      g->exec, g->evk_begin[r],
+                      on_k ? c->prof_evk[2 * (c->prof_nk + r)] : c->gev[2 + 2 * r]),
+               "profile event");
+      WBRW_TRY(c, cudaGraphExecEventRecordNodeSetEvent(
+                      g->exec, g->evk_end[r],
+                      on_k ? c->prof_evk[2 * (c->prof_nk + r) + 1] : c->gev[3 + 2 * r]),
+               "profile event");
+    }
+    if (on_k) c->prof_nk += g->nevk;
+    g->evk_live = on_k ? 1 : 0;
   }
   WBRW_TRY(c, cudaGraphLaunch(g->exec, c->stream), "graph launch");
   c->launches += g->launches;
@@ -424,23 +446,39 @@ wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
 
 namespace wbrw {
 // While a period is captured the pair becomes two event-record nodes on
-// placeholder events; each replay points them at the profiling events.
-void prof_begin(Ctx* c) {
+// placeholder events (one pair per round for the event kernel); each replay
+// points them at the profiling events.
+void prof_begin(Ctx* c, int kind, int r) {
   if (c->capturing) {
-    cudaEventRecordWithFlags(c->gev[0], c->stream, cudaEventRecordExternal);
+    if (kind == PROF_FIRST_WAVE)
+      cudaEventRecordWithFlags(c->gev[0], c->stream, cudaEventRecordExternal);
+    else if (r < kProfRounds)
+      cudaEventRecordWithFlags(c->gev[2 + 2 * r], c->stream, cudaEventRecordExternal);
     return;
   }
-  if (!c->prof_on || c->prof_n >= 4096) return;
-  cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+  if (!c->prof_on) return;
+  if (kind == PROF_FIRST_WAVE) {
+    if (c->prof_n < kProfLaunches) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+  } else if (c->prof_nk < kProfLaunches) {
+    cudaEventRecord(c->prof_evk[2 * c->prof_nk], c->stream);
+  }
 }
-void prof_end(Ctx* c) {
+void prof_end(Ctx* c, int kind, int r) {
   if (c->capturing) {
-    cudaEventRecordWithFlags(c->gev[1], c->stream, cudaEventRecordExternal);
+    if (kind == PROF_FIRST_WAVE)
+      cudaEventRecordWithFlags(c->gev[1], c->stream, cudaEventRecordExternal);
+    else if (r < kProfRounds)
+      cudaEventRecordWithFlags(c->gev[3 + 2 * r], c->stream, cudaEventRecordExternal);
     return;
   }
-  if (!c->prof_on || c->prof_n >= 4096) return;
-  cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
-  c->prof_n += 1;
+  if (!c->prof_on) return;
+  if (kind == PROF_FIRST_WAVE) {
+    if (c->prof_n < kProfLaunches) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+    c->prof_n += c->prof_n < kProfLaunches;
+  } else if (c->prof_nk < kProfLaunches) {
+    cudaEventRecord(c->prof_evk[2 * c->prof_nk + 1], c->stream);
+    c->prof_nk += 1;
+  }
 }
 }  // namespace wbrw
 
@@ -979,6 +1017,8 @@ wbrw_status wbrw_counters(wbrw_ctx* c, long long* out) {
   out[WBRW_C_OUT_MINUS] = (long long)h.ledger[LG_OUT_M];
   out[WBRW_C_PARTICLE_STEPS] = (long long)(h.ledger[LG_PSTEPS] + h.ledger[LG_PSTEPS0]);
   out[WBRW_C_PARTICLE_STEPS_FIRST] = (long long)h.ledger[LG_PSTEPS0];
+  out[WBRW_C_CANDIDATES] = (long long)h.ledger[LG_CAND];
+  out[WBRW_C_FIRST_PAIRS] = (long long)h.ledger[LG_PAIRS0];
   out[WBRW_C_LOG_LEN] = (long long)h.log_len;
   out[WBRW_C_STEP] = c->step;
   out[WBRW_C_EPOCH] = c->epoch;
@@ -1043,7 +1083,7 @@ wbrw_status wbrw_graph(wbrw_ctx* c, int enable) {
   if (!c) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
   if (enable && !c->gev_created) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2 + 2 * kProfRounds; ++i)
       WBRW_TRY(c, cudaEventCreateWithFlags(&c->gev[i], cudaEventDefault), "create events");
     c->gev_created = 1;
   }
@@ -1182,12 +1222,15 @@ wbrw_status wbrw_autotune(wbrw_ctx* c, int trials, wbrw_tuning* best, double* ms
 wbrw_status wbrw_profile(wbrw_ctx* c, int enable) {
   if (!c) return WBRW_ERR_ARG;
   if (enable && !c->prof_created) {
-    for (int i = 0; i < 2 * 4096; ++i)
+    for (int i = 0; i < 2 * kProfLaunches; ++i) {
       WBRW_TRY(c, cudaEventCreate(&c->prof_ev[i]), "create events");
+      WBRW_TRY(c, cudaEventCreate(&c->prof_evk[i]), "create events");
+    }
     c->prof_created = 1;
   }
   c->prof_on = enable ? 1 : 0;
   c->prof_n = 0;
+  c->prof_nk = 0;
   return WBRW_OK;
 }
 
@@ -1206,14 +1249,33 @@ wbrw_status wbrw_profile_read(wbrw_ctx* c, double* total_ms, long long* launches
   return WBRW_OK;
 }
 
+wbrw_status wbrw_profile_read_events(wbrw_ctx* c, double* total_ms, long long* launches) {
+  if (!c) return WBRW_ERR_ARG;
+  WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  double t = 0;
+  for (int i = 0; i < c->prof_nk; ++i) {
+    float ms = 0;
+    WBRW_TRY(c, cudaEventElapsedTime(&ms, c->prof_evk[2 * i], c->prof_evk[2 * i + 1]),
+             "elapsed");
+    t += ms;
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = c->prof_nk;
+  c->prof_nk = 0;
+  return WBRW_OK;
+}
+
 void wbrw_destroy(wbrw_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   if (c->gev_created)
-    for (int i = 0; i < 2; ++i) cudaEventDestroy(c->gev[i]);
+    for (int i = 0; i < 2 + 2 * kProfRounds; ++i) cudaEventDestroy(c->gev[i]);
   if (c->prof_created)
-    for (int i = 0; i < 2 * 4096; ++i) cudaEventDestroy(c->prof_ev[i]);
+    for (int i = 0; i < 2 * kProfLaunches; ++i) {
+      cudaEventDestroy(c->prof_ev[i]);
+      cudaEventDestroy(c->prof_evk[i]);
+    }
   free_ctx(c);
 }
 

@@ -330,9 +330,11 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 struct Acc {
   unsigned long long psteps, events, kill_p, kill_m, out_p, out_m;
   unsigned long long n_plus, n_minus, w_plus, w_minus;
+  unsigned long long cand;  // first events of candidate intervals (k_event)
   __device__ void zero() {
     psteps = events = kill_p = kill_m = out_p = out_m = 0;
     n_plus = n_minus = w_plus = w_minus = 0;
+    cand = 0;
   }
 };
 
@@ -1729,6 +1731,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
         s.l = e.l;
         s.t = Draw<P>::first(p, ip, e.pid, l, (T)0, true, s.st);
         if (s.t < p.dt) {
+          ++acc.cand;
           T gap;
           if constexpr (CMP) {
             made = event_decide<P>(p, ip, inst, s.pid, s.xo, s.to, s.k, s.w, s.st, l, 0u, true,
@@ -1757,6 +1760,11 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
   }
   if constexpr (CMP) make_pairs(1u);
   store_counts(p, wc, 1, true, true, DST == DST_BIN2);
+  // this kernel performs only the first event of each candidate interval
+  // (later events and the offspring's own go to the deferred segments), so
+  // its pairs are the first events' pairs
+  block_reduce_add(red, acc.cand, &p.cnt->ledger[LG_CAND]);
+  block_reduce_add(red, acc.events, &p.cnt->ledger[LG_PAIRS0]);
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
@@ -2023,11 +2031,13 @@ cudaError_t flight(Ctx* c, const KP<P>& p) {
 }
 
 template <class P, int DST>
-cudaError_t events(Ctx* c, const KP<P>& p) {
+cudaError_t events(Ctx* c, const KP<P>& p, int r) {
   static const int o_ev = occupancy(k_event<P, DST>);
   static const int o_cont = occupancy(k_cont<P, DST>);
   static const int o_drain = occupancy(k_drain<P, DST>);
+  prof_begin(c, PROF_EVENT, r);
   k_event<P, DST><<<grid_of(c, o_ev), kBlock, 0, c->stream>>>(p);
+  prof_end(c, PROF_EVENT, r);
   for (int level = 1; level <= c->passes; ++level)
     k_cont<P, DST><<<grid_of(c, o_cont), kBlock, 0, c->stream>>>(p, level);
   k_drain<P, DST><<<grid_of(c, o_drain), kBlock, 0, c->stream>>>(p, c->passes + 1);
@@ -2059,12 +2069,12 @@ cudaError_t flight_any(Ctx* c, const KP<P>& p, int src, int dst) {
 }
 
 template <class P>
-cudaError_t events_any(Ctx* c, const KP<P>& p, int dst) {
-  if (dst == DST_ARRAY) return events<P, DST_ARRAY>(c, p);
-  if (dst == DST_BIN1) return events<P, DST_BIN1>(c, p);
+cudaError_t events_any(Ctx* c, const KP<P>& p, int dst, int r) {
+  if (dst == DST_ARRAY) return events<P, DST_ARRAY>(c, p, r);
+  if (dst == DST_BIN1) return events<P, DST_BIN1>(c, p, r);
   if constexpr (P::D == 1 && !P::TG) {
-    if (dst == DST_BIN2) return events<P, DST_BIN2>(c, p);
-    return events<P, DST_WSUM>(c, p);
+    if (dst == DST_BIN2) return events<P, DST_BIN2>(c, p, r);
+    return events<P, DST_WSUM>(c, p, r);
   }
   return cudaErrorNotSupported;
 }
@@ -2234,7 +2244,7 @@ struct DriverImpl {
         if ((e = launch_zero(c, p.fcnt_out, cnt_bytes)) != cudaSuccess) return e;
         if ((e = launch_zero(c, c->dcnt, (size_t)(c->passes + 2) * cnt_bytes)) != cudaSuccess)
           return e;
-        e = events_any<P>(c, p, dst);
+        e = events_any<P>(c, p, dst, r);
         if (e != cudaSuccess) return e;
       }
     }

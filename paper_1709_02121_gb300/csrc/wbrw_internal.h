@@ -56,7 +56,12 @@ enum : int {
 };
 
 // ledger slots (Counters::ledger)
-enum { LG_EVENTS = 0, LG_KILL_P, LG_KILL_M, LG_OUT_P, LG_OUT_M, LG_PSTEPS, LG_PSTEPS0, LG_N = 8 };
+// LG_CAND: candidate intervals whose first event the event kernel performed;
+// LG_PAIRS0: those of them that emitted a pair.
+enum {
+  LG_EVENTS = 0, LG_KILL_P, LG_KILL_M, LG_OUT_P, LG_OUT_M, LG_PSTEPS, LG_PSTEPS0, LG_CAND,
+  LG_PAIRS0, LG_N = 10
+};
 
 // Device-resident counters: every count the host would otherwise need lives
 // here, so no launch waits for the host.
@@ -80,6 +85,11 @@ struct Counters {
   int pad[2];
 };
 
+// Rounds of a captured period whose event kernel a graph replay can time,
+// and launches each profiling buffer keeps.
+constexpr int kProfRounds = 64;
+constexpr int kProfLaunches = 4096;
+
 // A resampling period of wbrw_run captured into a CUDA graph (sp1, source =
 // the regeneration of the previous histogram), keyed by its length.
 struct PeriodGraph {
@@ -87,6 +97,10 @@ struct PeriodGraph {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   cudaGraphNode_t ev_begin, ev_end;  // event records around the first wave
+  // event records around the event kernel of round r < kProfRounds
+  cudaGraphNode_t evk_begin[kProfRounds], evk_end[kProfRounds];
+  int nevk;                          // rounds with both records
+  int evk_live;                      // they point at profiling events
   long long launches;                // kernels in the graph
 };
 constexpr int kMaxGraphs = 4;
@@ -201,13 +215,17 @@ struct Ctx {
   int dev_period_ok;  // the device period state equals (step, epoch)
   int ngraphs;
   PeriodGraph graphs[kMaxGraphs];
-  cudaEvent_t gev[2];  // placeholders of the captured event records
+  // placeholders of the captured event records: the first wave, then the
+  // event kernel of each round
+  cudaEvent_t gev[2 + 2 * kProfRounds];
   int gev_created;
   long long launches;
-  // CUDA-event timing of the first flight wave of each chunk
+  // CUDA-event timing of the first flight wave of each chunk (prof_ev) and
+  // of each event-kernel launch (prof_evk)
   int prof_on;
-  int prof_n;
-  cudaEvent_t prof_ev[2 * 4096];
+  int prof_n, prof_nk;
+  cudaEvent_t prof_ev[2 * kProfLaunches];
+  cudaEvent_t prof_evk[2 * kProfLaunches];
   int prof_created;
   char err[512];
 };
@@ -216,9 +234,11 @@ enum { ST_PARTICLES = 0, ST_HISTOGRAM = 1 };
 
 
 // Per-precision drivers (wbrw_fp64.cu / wbrw_fp32.cu).
-// Event pair around a profiled launch (no-ops while profiling is off).
-void prof_begin(Ctx*);
-void prof_end(Ctx*);
+// Event pair around a profiled launch (no-ops while profiling is off):
+// kind PROF_FIRST_WAVE, or PROF_EVENT with the launch's round r.
+enum { PROF_FIRST_WAVE = 0, PROF_EVENT = 1 };
+void prof_begin(Ctx*, int kind = PROF_FIRST_WAVE, int r = 0);
+void prof_end(Ctx*, int kind = PROF_FIRST_WAVE, int r = 0);
 
 struct Driver {
   cudaError_t (*init)(Ctx*, long long n);

@@ -26,12 +26,14 @@ POT_GAUSSIAN, POT_SOFT_COULOMB_2E = 0, 1
 COUNTERS = ("live", "events", "kill_plus", "kill_minus", "out_plus", "out_minus",
             "particle_steps", "log_len", "step", "epoch", "launches",
             "boot_nplus", "boot_nminus", "boot_nrplus", "boot_nrminus",
-            "boot_wplus", "boot_wminus", "nonzero_cells", "error", "particle_steps_first")
+            "boot_wplus", "boot_wminus", "nonzero_cells", "error", "particle_steps_first",
+            "candidates", "first_pairs")
 C_COUNT = 24
 
 SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_run", "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
-           "wbrw_restore", "wbrw_profile", "wbrw_profile_read", "wbrw_counters",
+           "wbrw_restore", "wbrw_profile", "wbrw_profile_read", "wbrw_profile_read_events",
+           "wbrw_counters",
            "wbrw_sync_status", "wbrw_last_error", "wbrw_destroy",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
@@ -140,7 +142,7 @@ def load(path: str = LIB_PATH):
     for name in ("wbrw_init", "wbrw_step", "wbrw_annihilate", "wbrw_run",
                  "wbrw_density", "wbrw_particles", "wbrw_checkpoint",
                  "wbrw_restore", "wbrw_profile", "wbrw_profile_read",
-                 "wbrw_counters", "wbrw_sync_status", "wbrw_batch_init",
+                 "wbrw_profile_read_events", "wbrw_counters", "wbrw_sync_status", "wbrw_batch_init",
                  "wbrw_instance_density", "wbrw_transmissions",
                  "wbrw_particle_instances", "wbrw_graph", "wbrw_get_tuning",
                  "wbrw_set_tuning", "wbrw_autotune"):
@@ -153,6 +155,7 @@ def load(path: str = LIB_PATH):
     L.wbrw_restore.argtypes = [P, P, LL, LL]
     L.wbrw_profile.argtypes = [P, I]
     L.wbrw_profile_read.argtypes = [P, P, P]
+    L.wbrw_profile_read_events.argtypes = [P, P, P]
     L.wbrw_step.argtypes = [P, I]
     L.wbrw_annihilate.argtypes = [P]
     L.wbrw_run.argtypes = [P, I]
@@ -329,6 +332,14 @@ def wbrw_profile_read(ctx):
     ms = ctypes.c_double()
     n = ctypes.c_longlong()
     _check(ctx, load().wbrw_profile_read(ctx, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def wbrw_profile_read_events(ctx):
+    """(summed ms, launches) of the event kernel since the last read."""
+    ms = ctypes.c_double()
+    n = ctypes.c_longlong()
+    _check(ctx, load().wbrw_profile_read_events(ctx, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
 
 

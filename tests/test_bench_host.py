@@ -57,3 +57,29 @@ def test_workload_selection(bench):
     assert bench.workload(A)["n_alpha"] == 15_000_000
     A.workload, A.particles = "he4d_fp32_n5e7", 0
     assert bench.workload(A)["dim"] == 4
+
+
+def test_event_roofline_counts_candidates_and_pairs(bench):
+    wl = {"precision": "fp32", "resample_every": 10}
+    r = bench.roofline_event(wl, ev_ms=3.0, ev_n=10, cand=2e8, pairs=1.2e8, peaks={},
+                             clk={"sm_mhz": 2000.0})
+    # 120 operations per candidate and 140 per pair over the summed 3 ms
+    assert r["achieved"] == pytest.approx((120 * 2e8 + 140 * 1.2e8) / 3e-3 / 1e9)
+    assert r["peak"] == pytest.approx(152 * 64 * 2000e6 / 1e9)
+    assert r["launch_ms"] == pytest.approx(0.3) and r["total_ms"] == pytest.approx(3.0)
+    assert r["candidates_per_launch"] == pytest.approx(2e7)
+    assert r["first_pairs_per_candidate"] == pytest.approx(0.6)
+    assert r["kernel"] == "k_event<fp32,bin>" and r["bound"] == "alu"
+    tpc = bench.TRAFFIC_PER_CANDIDATE["fp32"]
+    assert r["traffic"] == (None if tpc is None else pytest.approx(tpc * 2e7))
+    assert bench.roofline_event(wl, 0.0, 0, 0, 0, {}, {}) is None
+
+
+def test_the_dominant_kernel_is_the_one_with_more_time(bench):
+    wl = {"precision": "fp32", "resample_every": 10}
+    first = bench.roofline(wl, kern_ms=2.0, kern_n=2, psteps_first=3.2e9, peaks={},
+                           clk={"sm_mhz": 2070.0})
+    ev = bench.roofline_event(wl, 3.0, 20, 2e8, 1.2e8, {}, {"sm_mhz": 2070.0})
+    assert bench.dominant(first, ev) == (ev, first)
+    assert bench.dominant(ev, None) == (ev, None)
+    assert bench.dominant(None, None) == (None, None)

@@ -75,7 +75,8 @@ def assert_same_log(glog, olog):
 
 def assert_same_ledger(sim, o):
     c, led = sim.counters(), o.ledger()
-    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps"):
+    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps",
+                "candidates", "first_pairs"):
         assert c[key] == led[key], (key, c[key], led[key])
 
 

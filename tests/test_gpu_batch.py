@@ -108,7 +108,8 @@ def test_fused_schedule_matches_oracle_per_instance():
     # ledgers are sums over instances
     c = b.counters()
     leds = [o.ledger() for o in ors]
-    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps"):
+    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps",
+                "candidates", "first_pairs"):
         assert c[key] == sum(led[key] for led in leds), key
     # observables per instance, and all transmissions at once
     T_all = b.transmissions()

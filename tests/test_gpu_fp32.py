@@ -2,6 +2,8 @@
 geometric gaps between candidate intervals, so it is compared with the
 Schroedinger equation and with the FP64 path (bit-identical to the oracle)
 through estimates and their Monte Carlo standard errors."""
+import math
+
 import numpy as np
 import pytest
 
@@ -69,3 +71,28 @@ def test_fp32_matches_fp64_path():
     z = (m32 - m64) / np.sqrt(se32 ** 2 + se64 ** 2 + 1e-12)
     assert np.max(np.abs(z)) < 4.5, np.round(z, 2)
     assert abs(T32 - T64) < 2e-3 + 3 * np.hypot(Tse32, Tse64)
+
+
+@pytest.mark.parametrize("resample", [0, 5])
+def test_fp32_candidate_tallies_follow_the_clock(resample):
+    """A particle alive at the start of an interval has its first event in it
+    with probability p = 1 - exp(-gamma0 dt) (Sec. 3.2), so the candidate
+    intervals are Binomial(particle-steps, p) given the population.  Far from
+    the barrier the acceptance |sin(2 x kappa)| averages 2/pi (Remark 3 with
+    gamma0 = C/2), so the first events' pairs are Binomial(candidates, 2/pi).
+    The packet at x0 = -15 stays beyond |x| = 5 for these 6 intervals."""
+    from paper_1709_02121_gb300 import Simulation
+    wl = workloads.scaled(workloads.GAUSS_2D_FP64_2E5, precision="fp32", n_alpha=400_000,
+                          resample_every=resample)
+    sim = Simulation(wl, capacity=4_000_000)
+    sim.run(6)
+    c = sim.counters()
+    sim.close()
+    p = 1.0 - math.exp(-1.0 * wl["dt"])  # gamma0 = |H|/hbar = 1
+    n = c["particle_steps"]
+    z = (c["candidates"] - n * p) / math.sqrt(n * p * (1 - p))
+    assert abs(z) < 4.5, (c["candidates"], n, z)
+    q = 2.0 / math.pi
+    z = (c["first_pairs"] - c["candidates"] * q) / math.sqrt(c["candidates"] * q * (1 - q))
+    assert abs(z) < 4.5, (c["first_pairs"], c["candidates"], z)
+    assert c["first_pairs"] <= c["events"]

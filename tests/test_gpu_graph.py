@@ -43,7 +43,7 @@ def sim(wl, graph, gpu, capacity=400_000):
 
 
 KEYS = ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps",
-        "particle_steps_first", "live", "step", "epoch")
+        "particle_steps_first", "live", "step", "epoch", "candidates", "first_pairs")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -120,6 +120,27 @@ def test_profiling_sees_every_replayed_first_wave(gpu):
     s.run(20)
     ms, n = wbrw.wbrw_profile_read(s.ctx)
     assert n == 4 and ms > 0
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_profiling_sees_every_event_kernel(gpu, graphs):
+    from paper_1709_02121_gb300 import wbrw
+    s = sim(small(precision="fp32", n_alpha=50_000), graphs, gpu, capacity=1_000_000)
+    s.run(10)
+    wbrw.wbrw_profile(s.ctx, True)
+    s.run(20)
+    ms_f, n_f = wbrw.wbrw_profile_read(s.ctx)
+    ms_e, n_e = wbrw.wbrw_profile_read_events(s.ctx)
+    # one event-kernel launch per round: 4 periods of 5 rounds
+    assert n_f == 4 and n_e == 20 and ms_e > 0
+    assert wbrw.wbrw_profile_read_events(s.ctx) == (0.0, 0)
+    # off again: replays point the records back at their placeholders
+    wbrw.wbrw_profile(s.ctx, False)
+    s.run(10)
+    assert wbrw.wbrw_profile_read_events(s.ctx)[1] == 0
+    wbrw.wbrw_profile(s.ctx, True)
+    s.run(5)
+    assert wbrw.wbrw_profile_read_events(s.ctx)[1] == 5
 
 
 def test_graphs_need_a_created_stream(gpu):

@@ -79,7 +79,8 @@ def assert_same_ledger(sim, o):
     led = o.ledger()
     for a, b in (("events", "events"), ("kill_plus", "kill_plus"), ("kill_minus", "kill_minus"),
                  ("out_plus", "out_plus"), ("out_minus", "out_minus"),
-                 ("particle_steps", "particle_steps")):
+                 ("particle_steps", "particle_steps"), ("candidates", "candidates"),
+                 ("first_pairs", "first_pairs")):
         assert c[a] == led[b], (a, c[a], led[b])
 
 

@@ -73,7 +73,8 @@ def test_steps_and_events_match_oracle():
     for f in ("t", "xe", "kappa", "factor"):
         assert close(g[kg][f], r[ko][f]), f
     c, led = sim.counters(), o.ledger()
-    for key in ("events", "kill_plus", "kill_minus", "particle_steps"):
+    for key in ("events", "kill_plus", "kill_minus", "particle_steps", "candidates",
+                "first_pairs"):
         assert c[key] == led[key], key
 
 
