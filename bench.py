@@ -261,13 +261,11 @@ def ours(args, wl):
         torch.cuda.synchronize()
 
     P = wl["resample_every"]
-    for _ in range(args.warmup):
-        sim.run(P)
-    tuning = autotune(sim, args)
+    tuning = warm_up(sim, args, P)
     barrier()
 
     c0 = sim.counters()
-    wbrw.wbrw_profile(sim.ctx, True)
+    wbrw.wbrw_profile(sim.ctx, True)  # clears what the last warm-up period recorded
     clocks = Clocks(local)
     clocks.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -282,7 +280,6 @@ def ours(args, wl):
     clk = clocks.stop()
     kern_ms, kern_n = wbrw.wbrw_profile_read(sim.ctx)
     ev_ms, ev_n = wbrw.wbrw_profile_read_events(sim.ctx)
-    wbrw.wbrw_profile(sim.ctx, False)
     c1 = sim.counters()
     t_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     psteps = c1["particle_steps"] - c0["particle_steps"]
@@ -386,12 +383,10 @@ def ours_batch(args, spec):
         torch.cuda.synchronize()
 
     P = wl["resample_every"]
-    for _ in range(args.warmup):
-        sim.run(P)
-    tuning = autotune(sim, args)
+    tuning = warm_up(sim, args, P)
     barrier()
     c0 = sim.counters()
-    wbrw.wbrw_profile(sim.ctx, True)
+    wbrw.wbrw_profile(sim.ctx, True)  # clears what the last warm-up period recorded
     clocks = Clocks(local)
     clocks.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -406,7 +401,6 @@ def ours_batch(args, spec):
     clk = clocks.stop()
     kern_ms, kern_n = wbrw.wbrw_profile_read(sim.ctx)
     ev_ms, ev_n = wbrw.wbrw_profile_read_events(sim.ctx)
-    wbrw.wbrw_profile(sim.ctx, False)
     c1 = sim.counters()
     t_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     psteps = c1["particle_steps"] - c0["particle_steps"]
@@ -528,6 +522,21 @@ def ours_batch(args, spec):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def warm_up(sim, args, P):
+    """W untimed periods: W - 1, the launch-shape autotuning (which releases
+    the period graphs), then profiling on and the last one, which captures
+    the period graph again with the profiling events, so that no capture
+    falls in the timed region.  Profiling stays on until the end (switching
+    it captures the graphs again)."""
+    from paper_1709_02121_gb300 import wbrw
+    for _ in range(max(args.warmup - 1, 0)):
+        sim.run(P)
+    tuning = autotune(sim, args)
+    wbrw.wbrw_profile(sim.ctx, True)
+    sim.run(P)
+    return tuning
 
 
 def autotune(sim, args):
@@ -763,7 +772,7 @@ INT_OPS_EVENT = {"fp32": (120, 140), "fp32_4d": (240, 160),
                  "fp64": (320, 140), "fp64_4d": (340, 160)}
 # DRAM bytes per candidate interval of the event kernel measured by ncu
 # (profiles/), or None
-TRAFFIC_PER_CANDIDATE = {"fp32": None, "fp64": None, "fp32_4d": None, "fp64_4d": None}
+TRAFFIC_PER_CANDIDATE = {"fp32": 31.1, "fp64": None, "fp32_4d": None, "fp64_4d": None}
 
 
 def main():

@@ -327,7 +327,10 @@ wbrw_status wbrw_profile_read_events(wbrw_ctx* ctx, double* total_ms,
  * stream must be a created stream (not the legacy or per-thread default
  * stream) and must not be capturing; otherwise WBRW_ERR_ARG.  enable = 0
  * synchronises the stream and releases the graphs.  sp2 periods always
- * launch kernel by kernel. */
+ * launch kernel by kernel.  The CUDA events of wbrw_profile are part of a
+ * graph only if profiling was on when it was captured (each event costs a
+ * few microseconds per replay), so the first replay after wbrw_profile
+ * switches profiling on or off captures its period again. */
 wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
 
 /* Launch shape.  Neither knob changes any result (random numbers are keyed

@@ -330,6 +330,7 @@ void drop_graphs(wbrw_ctx* c) {
 wbrw_status capture_period(wbrw_ctx* c, int len, PeriodGraph* g) {
   memset(g, 0, sizeof(*g));
   g->len = len;
+  g->prof = c->prof_on;
   const long long launches0 = c->launches;
   const long long epoch0 = c->epoch;
   WBRW_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal),
@@ -380,6 +381,18 @@ wbrw_status graph_period(wbrw_ctx* c, int len) {
   PeriodGraph* g = nullptr;
   for (int i = 0; i < c->ngraphs; ++i)
     if (c->graphs[i].len == len) g = &c->graphs[i];
+  if (g && g->prof != c->prof_on) {  // profiling switched: capture again
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    wbrw_status st = capture_period(c, len, g);
+    if (st != WBRW_OK) {
+      if (g->exec) cudaGraphExecDestroy(g->exec);
+      if (g->graph) cudaGraphDestroy(g->graph);
+      *g = c->graphs[c->ngraphs - 1];
+      c->ngraphs -= 1;
+      return st;
+    }
+  }
   if (!g) {
     if (c->ngraphs == kMaxGraphs) drop_graphs(c);
     g = &c->graphs[c->ngraphs];
@@ -450,6 +463,7 @@ namespace wbrw {
 // points them at the profiling events.
 void prof_begin(Ctx* c, int kind, int r) {
   if (c->capturing) {
+    if (!c->prof_on) return;
     if (kind == PROF_FIRST_WAVE)
       cudaEventRecordWithFlags(c->gev[0], c->stream, cudaEventRecordExternal);
     else if (r < kProfRounds)
@@ -465,6 +479,7 @@ void prof_begin(Ctx* c, int kind, int r) {
 }
 void prof_end(Ctx* c, int kind, int r) {
   if (c->capturing) {
+    if (!c->prof_on) return;
     if (kind == PROF_FIRST_WAVE)
       cudaEventRecordWithFlags(c->gev[1], c->stream, cudaEventRecordExternal);
     else if (r < kProfRounds)

@@ -91,7 +91,10 @@ constexpr int kProfRounds = 64;
 constexpr int kProfLaunches = 4096;
 
 // A resampling period of wbrw_run captured into a CUDA graph (sp1, source =
-// the regeneration of the previous histogram), keyed by its length.
+// the regeneration of the previous histogram), keyed by its length.  The
+// event records of the profiling are captured only while profiling is on
+// (each costs a few microseconds per replay); a replay in the other state
+// captures the period again.
 struct PeriodGraph {
   int len;
   cudaGraph_t graph;
@@ -101,6 +104,7 @@ struct PeriodGraph {
   cudaGraphNode_t evk_begin[kProfRounds], evk_end[kProfRounds];
   int nevk;                          // rounds with both records
   int evk_live;                      // they point at profiling events
+  int prof;                          // captured while profiling: the records exist
   long long launches;                // kernels in the graph
 };
 constexpr int kMaxGraphs = 4;
