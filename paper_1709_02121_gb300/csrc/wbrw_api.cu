@@ -339,6 +339,11 @@ wbrw_status capture_period(wbrw_ctx* c, int len, PeriodGraph* g) {
   wbrw_status st = enqueue_period(c, SRC_REGEN, (int)c->step, (int)c->step + len, c->epoch);
   if (st == WBRW_OK)
     st = cuda_check(c, launch_setup(c, SETUP_ADVANCE, (unsigned long long)len, 0), "advance");
+  if (c->prof_side_used) {  // join the profiling branch before the capture ends
+    cudaEventRecord(c->prof_join, c->prof_side);
+    cudaStreamWaitEvent(c->stream, c->prof_join, 0);
+    c->prof_side_used = 0;
+  }
   c->capturing = 0;
   c->epoch = epoch0;
   cudaGraph_t graph = nullptr;
@@ -460,14 +465,23 @@ wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
 namespace wbrw {
 // While a period is captured the pair becomes two event-record nodes on
 // placeholder events (one pair per round for the event kernel); each replay
-// points them at the profiling events.
+// points them at the profiling events.  The records sit on a side branch
+// that follows the stream's work so far: an event-record node in the
+// stream's own chain delays the next kernel by several microseconds.
+static void side_record(Ctx* c, cudaEvent_t ev) {
+  cudaEventRecord(c->prof_fork, c->stream);
+  cudaStreamWaitEvent(c->prof_side, c->prof_fork, 0);
+  cudaEventRecordWithFlags(ev, c->prof_side, cudaEventRecordExternal);
+  c->prof_side_used = 1;
+}
+
 void prof_begin(Ctx* c, int kind, int r) {
   if (c->capturing) {
     if (!c->prof_on) return;
     if (kind == PROF_FIRST_WAVE)
-      cudaEventRecordWithFlags(c->gev[0], c->stream, cudaEventRecordExternal);
+      side_record(c, c->gev[0]);
     else if (r < kProfRounds)
-      cudaEventRecordWithFlags(c->gev[2 + 2 * r], c->stream, cudaEventRecordExternal);
+      side_record(c, c->gev[2 + 2 * r]);
     return;
   }
   if (!c->prof_on) return;
@@ -481,9 +495,9 @@ void prof_end(Ctx* c, int kind, int r) {
   if (c->capturing) {
     if (!c->prof_on) return;
     if (kind == PROF_FIRST_WAVE)
-      cudaEventRecordWithFlags(c->gev[1], c->stream, cudaEventRecordExternal);
+      side_record(c, c->gev[1]);
     else if (r < kProfRounds)
-      cudaEventRecordWithFlags(c->gev[3 + 2 * r], c->stream, cudaEventRecordExternal);
+      side_record(c, c->gev[3 + 2 * r]);
     return;
   }
   if (!c->prof_on) return;
@@ -1100,6 +1114,9 @@ wbrw_status wbrw_graph(wbrw_ctx* c, int enable) {
   if (enable && !c->gev_created) {
     for (int i = 0; i < 2 + 2 * kProfRounds; ++i)
       WBRW_TRY(c, cudaEventCreateWithFlags(&c->gev[i], cudaEventDefault), "create events");
+    WBRW_TRY(c, cudaEventCreateWithFlags(&c->prof_fork, cudaEventDisableTiming), "create events");
+    WBRW_TRY(c, cudaEventCreateWithFlags(&c->prof_join, cudaEventDisableTiming), "create events");
+    WBRW_TRY(c, cudaStreamCreateWithFlags(&c->prof_side, cudaStreamNonBlocking), "create stream");
     c->gev_created = 1;
   }
   if (enable) {
@@ -1284,8 +1301,12 @@ void wbrw_destroy(wbrw_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
-  if (c->gev_created)
+  if (c->gev_created) {
     for (int i = 0; i < 2 + 2 * kProfRounds; ++i) cudaEventDestroy(c->gev[i]);
+    cudaEventDestroy(c->prof_fork);
+    cudaEventDestroy(c->prof_join);
+    cudaStreamDestroy(c->prof_side);
+  }
   if (c->prof_created)
     for (int i = 0; i < 2 * kProfLaunches; ++i) {
       cudaEventDestroy(c->prof_ev[i]);

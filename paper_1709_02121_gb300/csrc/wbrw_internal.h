@@ -223,6 +223,12 @@ struct Ctx {
   // event kernel of each round
   cudaEvent_t gev[2 + 2 * kProfRounds];
   int gev_created;
+  // a captured period records its profiling events on a side branch (fork
+  // from the stream before each record, joined at the end), so that the
+  // kernels do not wait for the records
+  cudaStream_t prof_side;
+  cudaEvent_t prof_fork, prof_join;
+  int prof_side_used;
   long long launches;
   // CUDA-event timing of the first flight wave of each chunk (prof_ev) and
   // of each event-kernel launch (prof_evk)
