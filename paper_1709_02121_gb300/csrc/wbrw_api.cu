@@ -465,14 +465,18 @@ wbrw_status step_impl(wbrw_ctx* c, int nsteps) {
 namespace wbrw {
 // While a period is captured the pair becomes two event-record nodes on
 // placeholder events (one pair per round for the event kernel); each replay
-// points them at the profiling events.  The records sit on a side branch
-// that follows the stream's work so far: an event-record node in the
-// stream's own chain delays the next kernel by several microseconds.
+// points them at the profiling events.  Captured or not, the records sit on
+// a side stream that waits for the stream's work so far: a record in the
+// stream's own order delays the next kernel by several microseconds.
 static void side_record(Ctx* c, cudaEvent_t ev) {
   cudaEventRecord(c->prof_fork, c->stream);
   cudaStreamWaitEvent(c->prof_side, c->prof_fork, 0);
-  cudaEventRecordWithFlags(ev, c->prof_side, cudaEventRecordExternal);
-  c->prof_side_used = 1;
+  if (c->capturing) {
+    cudaEventRecordWithFlags(ev, c->prof_side, cudaEventRecordExternal);
+    c->prof_side_used = 1;
+  } else {
+    cudaEventRecord(ev, c->prof_side);
+  }
 }
 
 void prof_begin(Ctx* c, int kind, int r) {
@@ -486,9 +490,9 @@ void prof_begin(Ctx* c, int kind, int r) {
   }
   if (!c->prof_on) return;
   if (kind == PROF_FIRST_WAVE) {
-    if (c->prof_n < kProfLaunches) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+    if (c->prof_n < kProfLaunches) side_record(c, c->prof_ev[2 * c->prof_n]);
   } else if (c->prof_nk < kProfLaunches) {
-    cudaEventRecord(c->prof_evk[2 * c->prof_nk], c->stream);
+    side_record(c, c->prof_evk[2 * c->prof_nk]);
   }
 }
 void prof_end(Ctx* c, int kind, int r) {
@@ -502,10 +506,10 @@ void prof_end(Ctx* c, int kind, int r) {
   }
   if (!c->prof_on) return;
   if (kind == PROF_FIRST_WAVE) {
-    if (c->prof_n < kProfLaunches) cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+    if (c->prof_n < kProfLaunches) side_record(c, c->prof_ev[2 * c->prof_n + 1]);
     c->prof_n += c->prof_n < kProfLaunches;
   } else if (c->prof_nk < kProfLaunches) {
-    cudaEventRecord(c->prof_evk[2 * c->prof_nk + 1], c->stream);
+    side_record(c, c->prof_evk[2 * c->prof_nk + 1]);
     c->prof_nk += 1;
   }
 }
@@ -1108,16 +1112,27 @@ wbrw_status wbrw_restore(wbrw_ctx* c, const int* grid, long long step, long long
   return WBRW_OK;
 }
 
+// The side stream and fork/join events of the profiling records.
+static wbrw_status ensure_side(wbrw_ctx* c) {
+  if (c->prof_side_created) return WBRW_OK;
+  WBRW_TRY(c, cudaEventCreateWithFlags(&c->prof_fork, cudaEventDisableTiming), "create events");
+  WBRW_TRY(c, cudaEventCreateWithFlags(&c->prof_join, cudaEventDisableTiming), "create events");
+  WBRW_TRY(c, cudaStreamCreateWithFlags(&c->prof_side, cudaStreamNonBlocking), "create stream");
+  c->prof_side_created = 1;
+  return WBRW_OK;
+}
+
 wbrw_status wbrw_graph(wbrw_ctx* c, int enable) {
   if (!c) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
   if (enable && !c->gev_created) {
     for (int i = 0; i < 2 + 2 * kProfRounds; ++i)
       WBRW_TRY(c, cudaEventCreateWithFlags(&c->gev[i], cudaEventDefault), "create events");
-    WBRW_TRY(c, cudaEventCreateWithFlags(&c->prof_fork, cudaEventDisableTiming), "create events");
-    WBRW_TRY(c, cudaEventCreateWithFlags(&c->prof_join, cudaEventDisableTiming), "create events");
-    WBRW_TRY(c, cudaStreamCreateWithFlags(&c->prof_side, cudaStreamNonBlocking), "create stream");
     c->gev_created = 1;
+  }
+  if (enable) {
+    const wbrw_status st = ensure_side(c);
+    if (st != WBRW_OK) return st;
   }
   if (enable) {
     cudaStreamCaptureStatus cs;
@@ -1253,6 +1268,10 @@ wbrw_status wbrw_autotune(wbrw_ctx* c, int trials, wbrw_tuning* best, double* ms
 
 wbrw_status wbrw_profile(wbrw_ctx* c, int enable) {
   if (!c) return WBRW_ERR_ARG;
+  if (enable) {
+    const wbrw_status st = ensure_side(c);
+    if (st != WBRW_OK) return st;
+  }
   if (enable && !c->prof_created) {
     for (int i = 0; i < 2 * kProfLaunches; ++i) {
       WBRW_TRY(c, cudaEventCreate(&c->prof_ev[i]), "create events");
@@ -1269,6 +1288,8 @@ wbrw_status wbrw_profile(wbrw_ctx* c, int enable) {
 wbrw_status wbrw_profile_read(wbrw_ctx* c, double* total_ms, long long* launches) {
   if (!c) return WBRW_ERR_ARG;
   WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (c->prof_side_created)
+    WBRW_TRY(c, cudaStreamSynchronize(c->prof_side), "synchronise");
   double t = 0;
   for (int i = 0; i < c->prof_n; ++i) {
     float ms = 0;
@@ -1284,6 +1305,8 @@ wbrw_status wbrw_profile_read(wbrw_ctx* c, double* total_ms, long long* launches
 wbrw_status wbrw_profile_read_events(wbrw_ctx* c, double* total_ms, long long* launches) {
   if (!c) return WBRW_ERR_ARG;
   WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (c->prof_side_created)
+    WBRW_TRY(c, cudaStreamSynchronize(c->prof_side), "synchronise");
   double t = 0;
   for (int i = 0; i < c->prof_nk; ++i) {
     float ms = 0;
@@ -1301,8 +1324,10 @@ void wbrw_destroy(wbrw_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
-  if (c->gev_created) {
+  if (c->gev_created)
     for (int i = 0; i < 2 + 2 * kProfRounds; ++i) cudaEventDestroy(c->gev[i]);
+  if (c->prof_side_created) {
+    cudaStreamSynchronize(c->prof_side);
     cudaEventDestroy(c->prof_fork);
     cudaEventDestroy(c->prof_join);
     cudaStreamDestroy(c->prof_side);

@@ -223,12 +223,14 @@ struct Ctx {
   // event kernel of each round
   cudaEvent_t gev[2 + 2 * kProfRounds];
   int gev_created;
-  // a captured period records its profiling events on a side branch (fork
-  // from the stream before each record, joined at the end), so that the
-  // kernels do not wait for the records
+  // the profiling events are recorded on a side stream that waits for the
+  // context stream's work so far (in a captured period: a side branch,
+  // joined before the capture ends), so that the kernels do not wait for
+  // the records
   cudaStream_t prof_side;
   cudaEvent_t prof_fork, prof_join;
-  int prof_side_used;
+  int prof_side_used;     // the capture in progress forked the side stream
+  int prof_side_created;
   long long launches;
   // CUDA-event timing of the first flight wave of each chunk (prof_ev) and
   // of each event-kernel launch (prof_evk)
