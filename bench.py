@@ -757,7 +757,7 @@ def roofline(wl, kern_ms, kern_n, psteps_first, peaks, clk):
 INT_OPS_PER_PARTICLE = {"fp32": (120, 0), "fp32_4d": (135, 0),
                         "fp64": (116, 100), "fp64_4d": (230, 100)}
 # DRAM bytes per first-wave particle-step measured by ncu (profiles/), or None
-TRAFFIC_PER_PSTEP = {"fp32": 0.577, "fp64": None, "fp32_4d": None, "fp64_4d": None}
+TRAFFIC_PER_PSTEP = {"fp32": 0.577, "fp64": None, "fp32_4d": 1.11, "fp64_4d": None}
 
 # Integer operations of the event kernel (per candidate interval, per pair
 # of its first event).  A candidate: the Philox calls of its first event (one
@@ -772,7 +772,7 @@ INT_OPS_EVENT = {"fp32": (120, 140), "fp32_4d": (240, 160),
                  "fp64": (320, 140), "fp64_4d": (340, 160)}
 # DRAM bytes per candidate interval of the event kernel measured by ncu
 # (profiles/), or None
-TRAFFIC_PER_CANDIDATE = {"fp32": 31.2, "fp64": None, "fp32_4d": None, "fp64_4d": None}
+TRAFFIC_PER_CANDIDATE = {"fp32": 31.2, "fp64": None, "fp32_4d": 48.6, "fp64_4d": None}
 
 
 def main():
