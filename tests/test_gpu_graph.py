@@ -149,3 +149,23 @@ def test_graphs_need_a_created_stream(gpu):
     with pytest.raises(WbrwError) as ei:
         s.graph(True)
     assert ei.value.status == wbrw.ERR_ARG
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_profiling_changes_no_result(gpu, graphs):
+    """The profiling records sit on a side stream (a side branch of a
+    captured period): switching them on and off, which captures the period
+    again, leaves every count and cell bit-identical."""
+    from paper_1709_02121_gb300 import wbrw
+    wl = small(precision="fp32", n_alpha=50_000)
+    a = sim(wl, graphs, gpu, capacity=1_000_000)
+    b = sim(wl, graphs, gpu, capacity=1_000_000)
+    for i in range(6):
+        wbrw.wbrw_profile(b.ctx, i % 2 == 1)
+        a.run(5)
+        b.run(5)
+    ca, cb = a.counters(), b.counters()
+    for key in KEYS:
+        assert ca[key] == cb[key], key
+    assert np.array_equal(a.grid_counts(), b.grid_counts())
+
