@@ -291,32 +291,38 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 // ---------------------------------------------------------------------------
 constexpr int kBootChunk = 1024;  // records per work item of k_boot_bin
 
-__global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t* rec_cell,
+__global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint32_t* rec_cell,
                                                      const uint32_t* rec_a, const unsigned* rcnt,
                                                      int nseg, long long rseg,
                                                      int* keep0, int* keep1,
                                                      unsigned long long* res0,
                                                      unsigned long long* res1, int fx) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
-  double ratio[2];
   // fx (FP32 runs): q_i in fixed point, a_i M / 2^64 with M = floor(N 2^64 / W)
   // from one FP64 division, so that no record needs FP64 arithmetic (slow on
   // this GPU); the integer part and the Q0.32 residual agree with the FP64
   // form to about one unit of 2^-32 (the FP32 contract is in law).  FP64 runs
-  // keep the FP64 form, which the oracle follows.
-  unsigned long long mx[2] = {0, 0};
-  bool use_fx[2] = {false, false};
+  // keep the FP64 form, which the oracle follows.  The two sides' constants
+  // are separate scalars, chosen per record by a select: an array indexed by
+  // the record's side would live in local memory.
+  double ratio0 = 0.0, ratio1 = 0.0;
+  unsigned long long mx0 = 0, mx1 = 0;
+  bool fx0 = false, fx1 = false;
   for (int s = 0; s < 2; ++s) {
-    ratio[s] = c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
+    const double r =
+        c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
+    unsigned long long m_s = 0;
+    bool f_s = false;
     if (fx && c->boot_n[s] < c->boot_w[s]) {
-      const double m = ratio[s] * 18446744073709551616.0;
+      const double m = r * 18446744073709551616.0;
       if (m < 18446744073709551616.0) {
-        mx[s] = (unsigned long long)m;
-        use_fx[s] = true;
+        m_s = (unsigned long long)m;
+        f_s = true;
       }
     }
+    if (s == 0) { ratio0 = r; mx0 = m_s; fx0 = f_s; } else { ratio1 = r; mx1 = m_s; fx1 = f_s; }
   }
-  unsigned long long ks[2] = {0, 0};
+  unsigned long long ks0 = 0, ks1 = 0;
   // records sit in one segment per producer warp; a warp takes a segment
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
@@ -345,12 +351,12 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
         const uint32_t rc = rcs[i];
         const int side = rc >> 31;
         const uint32_t cell = rc & 0x7FFFFFFFu;
-        if (use_fx[side]) {
-          const unsigned long long a = ras[i], m = mx[side];
+        if (side ? fx1 : fx0) {
+          const unsigned long long a = ras[i], m = side ? mx1 : mx0;
           kf = (int)__umul64hi(a, m);  // bits 64..95 of the 96-bit a m
           res = (a * m) >> 32;         // bits 32..63: the Q0.32 residual
         } else {
-          const double q = __dmul_rn((double)ras[i], ratio[side]);
+          const double q = __dmul_rn((double)ras[i], side ? ratio1 : ratio0);
           const double fl = floor(q);
           res = (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
           kf = (int)fl;
@@ -362,13 +368,15 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
       const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
       const unsigned later = heads & ~((2u << lane) - 1u);
       const int end = later ? __ffs(later) - 1 : 32;  // the next run's first lane
+      if (heads != 0xFFFFFFFFu) {  // some run is longer than one record
 #pragma unroll
-      for (int off = 1; off < 32; off <<= 1) {
-        const int kf2 = __shfl_down_sync(0xFFFFFFFFu, kf, off);
-        const unsigned long long res2 = __shfl_down_sync(0xFFFFFFFFu, res, off);
-        if (lane + off < end) {
-          kf += kf2;
-          res += res2;
+        for (int off = 1; off < 32; off <<= 1) {
+          const int kf2 = __shfl_down_sync(0xFFFFFFFFu, kf, off);
+          const unsigned long long res2 = __shfl_down_sync(0xFFFFFFFFu, res, off);
+          if (lane + off < end) {
+            kf += kf2;
+            res += res2;
+          }
         }
       }
       if (head && key != ~0u) {
@@ -376,13 +384,13 @@ __global__ void __launch_bounds__(kBlock) k_boot_bin(Counters* c, const uint32_t
         const uint32_t cell = key >> 1;
         if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
         if (res) atomicAdd((side ? res1 : res0) + cell, res);
-        ks[side] += (unsigned long long)kf;
+        if (side) ks1 += (unsigned long long)kf; else ks0 += (unsigned long long)kf;
       }
     }
   }
   for (int s = 0; s < 2; ++s) {
     unsigned long long t;
-    block_exscan(ks[s], red, t);
+    block_exscan(s ? ks1 : ks0, red, t);
     if (threadIdx.x == 0 && t) atomicAdd(&c->boot_keep[s], t);
   }
 }
@@ -651,8 +659,9 @@ __global__ void __launch_bounds__(kBlock) k_tcells_c(const long long* dH, const 
                                                      long long nhi, unsigned long long* inst_slot) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-  unsigned long long n[kScanItems];
+  unsigned long long n[kScanItems];  // unrolled loops keep it in registers
   unsigned long long s = 0, z = 0;
+#pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const long long c = base + i;
     n[i] = c < nh ? tan_count(dH, dw, c, q) : 0ull;
@@ -663,6 +672,7 @@ __global__ void __launch_bounds__(kBlock) k_tcells_c(const long long* dH, const 
   unsigned long long os = block_exscan(s, red, ts) + bsum[blockIdx.x];
   unsigned long long oz = block_exscan(z, red, tz) + bnz[blockIdx.x];
   long long next_inst = (base + nhi - 1) / nhi * nhi;
+#pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
     const long long c = base + i;
     if (c == next_inst && next_inst < nh) {
