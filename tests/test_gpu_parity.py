@@ -167,6 +167,27 @@ def test_fused_schedule_matches_oracle(strategy):
     assert_same_particles(sim, o)
 
 
+@pytest.mark.parametrize("n_alpha,nx,nk", [
+    (20_000, 100, 64),   # about 1e5 records a period, many per cell and per warp
+    (3000, 4096, 520),   # 2.1e6 cells: sparse records, runs of one
+])
+def test_bootstrap_binning_matches_oracle(n_alpha, nx, nk):
+    """The signed bootstrap's per-cell floor counts and residual sums are
+    integer sums, so the warp's run sums and atomics give the oracle's
+    histogram bit for bit, with dense cells and on a grid large enough that
+    every record stands alone."""
+    wl = small(strategy="sp2", resample_every=6, n_alpha=n_alpha, nx=nx, nk=nk)
+    sim, o = sim_of(wl), oracle_of(wl)
+    for period in range(2):
+        sim.run(6)
+        o.step(6)
+        o.annihilate()
+        assert np.array_equal(sim.grid_counts(), o.grid()), period
+    c = sim.counters()
+    bs = o.boot_stats()
+    assert [c["boot_nrplus"], c["boot_nrminus"]] == bs["nr"].tolist()
+
+
 def test_fused_equals_step_plus_annihilate():
     wl = small(resample_every=5)
     a, b = sim_of(wl), sim_of(wl)
