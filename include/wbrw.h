@@ -299,10 +299,13 @@ wbrw_status wbrw_restore(wbrw_ctx* ctx, const int* grid, long long step,
 /* Timing of the flight kernel that carries the particles present at the
  * start of each chunk of intervals.  This is the first wave of every chunk,
  * and in wbrw_run it is the fused regeneration + flight + histogram pass.
- * While enabled, each such launch is bracketed by CUDA events on the
- * context's stream (at most 4096 launches are kept).  wbrw_profile_read
- * synchronises and returns the summed milliseconds and the launch count since
- * the last read or enable. */
+ * While enabled, each such launch is bracketed by CUDA events recorded on a
+ * side stream of the context that waits for the context stream's work so far
+ * (a record in the stream's own order would delay the next kernel by several
+ * microseconds); at most 4096 launches are kept.  wbrw_profile_read
+ * synchronises both streams and returns the summed milliseconds and the launch
+ * count since the last read or enable.  Errors: WBRW_ERR_ARG for a null
+ * context, WBRW_ERR_CUDA if an event or the side stream cannot be created. */
 wbrw_status wbrw_profile(wbrw_ctx* ctx, int enable);
 wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
                               long long* launches);
