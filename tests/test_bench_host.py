@@ -83,3 +83,25 @@ def test_the_dominant_kernel_is_the_one_with_more_time(bench):
     assert bench.dominant(first, ev) == (ev, first)
     assert bench.dominant(ev, None) == (ev, None)
     assert bench.dominant(None, None) == (None, None)
+
+
+def test_warm_up_switches_profiling_on_before_its_last_period(bench, monkeypatch):
+    """The period graph is captured again when profiling is switched on, so
+    the switch happens before the last warm-up period: no capture falls in
+    the timed region."""
+    from paper_1709_02121_gb300 import wbrw
+    calls = []
+
+    class Sim:
+        ctx = object()
+
+        def run(self, n):
+            calls.append(("run", n))
+
+    monkeypatch.setattr(wbrw, "wbrw_profile", lambda ctx, on=True: calls.append(("profile", on)))
+    monkeypatch.setattr(bench, "autotune", lambda sim, args: calls.append(("autotune",)) or {})
+
+    class A:
+        warmup = 4
+    bench.warm_up(Sim(), A, 10)
+    assert calls == [("run", 10)] * 3 + [("autotune",), ("profile", True), ("run", 10)]
