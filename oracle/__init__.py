@@ -56,9 +56,18 @@ def build(force: bool = False) -> str:
     tmp = _LIB + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
            "-fPIC", "-shared", "-o", tmp, _SRC, _SRC4, "-lm"]
-    subprocess.run(cmd, check=True)
+    # with OpenMP where the compiler has it (threads never change a result);
+    # without it the oracle runs its chunks one after the other
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if r.returncode:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def max_threads() -> int:
+    """Threads the oracle can use (1 if it was built without OpenMP)."""
+    return int(lib().orc_max_threads())
 
 
 class _Comp(ctypes.Structure):
@@ -132,6 +141,9 @@ def lib():
         L.orc_gamma0.argtypes = [P]
         L.orc_gamma0.restype = D
         L.orc_enable_log.argtypes = [P, ctypes.c_int]
+        L.orc_max_threads.argtypes = []
+        L.orc_set_threads.argtypes = [P, ctypes.c_int]
+        L.orc_threads.argtypes = [P]
         L.orc_init_gauss.argtypes = [P, LL, D, D, D]
         L.orc_set_particles.argtypes = [P, LL, P, P, P, P, LL]
         L.orc_step.argtypes = [P, ctypes.c_int]
@@ -227,10 +239,12 @@ class Oracle:
     def __init__(self, *, hbar=1.0, mass=1.0, dt=0.1, gamma0=0.0, H=1.0,
                  w=1.0, xc=0.0, nx=240, nk=128, xmin=-60.0, xmax=60.0,
                  kmin=-6.4, kmax=6.4, strategy=SP1, n_alpha=200000, seed=0,
-                 instance=0, tangent=False, tquantum=1.0, comps=()):
+                 instance=0, tangent=False, tquantum=1.0, comps=(), threads=1):
         """comps: up to 4 dicts (a, b, om, ph, w, xc) of a time-dependent
         potential sum_m (a + b cos(om t + ph)) exp(-(x-xc)^2/(2 w^2)); when
-        given, H, w, xc and gamma0 are not used."""
+        given, H, w, xc and gamma0 are not used.  threads: chunks of each
+        interval, binning and regeneration run in parallel (results do not
+        depend on it)."""
         cs = (_Comp * 4)(*[_Comp(c["a"], c["b"], c["om"], c["ph"], c["w"], c["xc"])
                            for c in comps])
         self.cfg = _Config(hbar, mass, dt, gamma0, H, w, xc, nx, nk, xmin,
@@ -242,12 +256,18 @@ class Oracle:
         self._s = lib().orc_create(ctypes.byref(self.cfg))
         if not self._s:
             raise ValueError("oracle rejected the configuration")
+        if threads != 1 and lib().orc_set_threads(self._s, int(threads)):
+            raise ValueError("threads must be >= 1")
 
     def __del__(self):
         s = getattr(self, "_s", None)
         if s and _lib is not None:
             _lib.orc_destroy(s)
             self._s = None
+
+    @property
+    def threads(self):
+        return lib().orc_threads(self._s)
 
     # ---- set-up ---------------------------------------------------------
     @property

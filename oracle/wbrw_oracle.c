@@ -18,6 +18,12 @@
  *     Eq. lambda / double_bootstrap / boostrap_histogram) followed by Alg. 3
  *     with stochastic rounding.
  *
+ * Threads (optional, OpenMP): an interval's particle list is cut into as
+ * many contiguous chunks as threads, each chunk's outputs go to its own list,
+ * and the lists are joined in chunk order, so the result is the serial one
+ * bit for bit; binning adds integers and regeneration writes each cell's
+ * particles at their place in cell order.  The default is one thread.
+ *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror and Shaw, "Parallel
  * random numbers: as easy as 1, 2, 3", SC'11), implemented here from that
  * definition, keyed by the run seed and indexed by counters (particle id,
@@ -35,6 +41,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_TWO_PI 6.283185307179586476925286766559
 #define ORC_PI 3.141592653589793238462643383280
@@ -177,15 +186,26 @@ enum {
   ORC_L_N = 8
 };
 
+/* What the particles of one chunk produce in an interval: the next list,
+ * ledger counts, the killed weights and the event log. */
+typedef struct {
+  orc_particle* q;
+  long long nq, capq;
+  long long ledger[ORC_L_N];
+  double wkill[2], tkill[2];
+  orc_event* log;
+  long long nlog, logcap;
+} orc_sink;
+
 typedef struct {
   orc_config c;
+  int threads;        /* chunks (and OpenMP threads) of an interval        */
+  orc_sink* sink;     /* one per chunk                                     */
   double C, sig_k, gamma0, cacc, hm, dtv, dx, dk, inv_dx, inv_dk;
   double gam_c[ORC_MAXC];  /* component rates (time-dependent potential)      */
   uint32_t key[2];
   orc_particle* p;
   long long n, cap;
-  orc_particle* q; /* next list */
-  long long nq, capq;
   int* grid;          /* signed int32 counts c_nu, nx*nk, x-major          */
   long long step;     /* index l of the next interval                      */
   long long epoch;    /* number of annihilations so far                    */
@@ -233,6 +253,8 @@ orc_state* orc_create(const orc_config* c) {
     if (!(c->comp[m].w > 0)) return NULL;
   orc_state* s = (orc_state*)calloc(1, sizeof(orc_state));
   s->c = *c;
+  s->threads = 1;
+  s->sink = (orc_sink*)calloc(1, sizeof(orc_sink));
   s->C = 2.0 * fabs(c->H) / c->hbar;          /* int |Vhat(2k)| (2/(pi hbar)) dk */
   s->sig_k = 1.0 / (2.0 * c->w);              /* proposal N(0, sig_k^2)          */
   s->gamma0 = c->gamma0 > 0 ? c->gamma0 : 0.5 * s->C;
@@ -264,10 +286,18 @@ orc_state* orc_create(const orc_config* c) {
   return s;
 }
 
+static void free_sinks(orc_state* s) {
+  for (int t = 0; t < s->threads; ++t) {
+    free(s->sink[t].q);
+    free(s->sink[t].log);
+  }
+  free(s->sink);
+}
+
 void orc_destroy(orc_state* s) {
   if (!s) return;
+  free_sinks(s);
   free(s->p);
-  free(s->q);
   free(s->grid);
   free(s->log);
   free(s->boot_cnt[0]);
@@ -281,6 +311,29 @@ int orc_cacc_ok(const orc_state* s) { return s->cacc <= 1.0; }
 double orc_gamma0(const orc_state* s) { return s->gamma0; }
 
 void orc_enable_log(orc_state* s, int on) { s->log_on = on; }
+
+/* Threads the library was built for (1 without OpenMP). */
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Cut each interval (and binning and regeneration) into n chunks, run by n
+ * threads where OpenMP is available.  Results do not depend on n. */
+int orc_set_threads(orc_state* s, int n) {
+  if (n < 1) return -1;
+  orc_sink* k = (orc_sink*)calloc((size_t)n, sizeof(orc_sink));
+  if (!k) return -1;
+  free_sinks(s);
+  s->sink = k;
+  s->threads = n;
+  return 0;
+}
+
+int orc_threads(const orc_state* s) { return s->threads; }
 
 /* ------------------------------------------------------------------------ */
 /* Initial data: N particles from the Gaussian-wavepacket Wigner function     */
@@ -363,15 +416,15 @@ int orc_set_particles(orc_state* s, long long n, const double* x,
  * gives the + child (s, tau + s g) and the - child (-s, -(tau + s g)); the
  * parent keeps (s, tau).  Then d/dtheta E[sum_i s_i A(x_i, k_i)] =
  * E[sum_i tau_i A(x_i, k_i)] for any observable A. */
-static int segment(orc_state* s, double xo, double to, double k, double w,
-                   uint64_t pid, uint32_t l, int is_root, double tH, double tw) {
+static int segment(const orc_state* s, orc_sink* o, double xo, double to, double k,
+                   double w, uint64_t pid, uint32_t l, int is_root, double tH, double tw) {
   const orc_config* c = &s->c;
   uint32_t r[4];
   draw4(s, pid, l, 0u, r);
   double u0 = orc_u53(r[0], r[1]);
   double t = to + (-log1p(-u0) / s->gamma0);
   uint32_t j = 0;
-  if (is_root && t < c->dt) s->ledger[ORC_L_CAND] += 1;
+  if (is_root && t < c->dt) o->ledger[ORC_L_CAND] += 1;
   while (t < c->dt) {
     double xe = xo + k * ((t - to) * s->hm);
     uint32_t a[4], b[4];
@@ -429,30 +482,30 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
       double kp = k + kap, km = k - kap;
       int kill_p = !(kp >= c->kmin && kp < c->kmax);
       int kill_m = !(km >= c->kmin && km < c->kmax);
-      s->ledger[ORC_L_EVENTS] += 1;
-      if (is_root && j == 0) s->ledger[ORC_L_PAIRS0] += 1;
+      o->ledger[ORC_L_EVENTS] += 1;
+      if (is_root && j == 0) o->ledger[ORC_L_PAIRS0] += 1;
       double wp = wc, wm = -wc; /* + child carries +wc, - child -wc */
       double gH = 1.0 / c->H, gw = 1.0 / c->w - 4.0 * c->w * kap * kap;
       double tpH = tH + w * gH, tpw = tw + w * gw; /* + child's tangent    */
       if (kill_p) {
-        if (wp > 0) s->ledger[ORC_L_KILL_P] += 1; else if (wp < 0) s->ledger[ORC_L_KILL_M] += 1;
-        if (wp > 0) s->wkill[0] += wp; else s->wkill[1] += -wp;
+        if (wp > 0) o->ledger[ORC_L_KILL_P] += 1; else if (wp < 0) o->ledger[ORC_L_KILL_M] += 1;
+        if (wp > 0) o->wkill[0] += wp; else o->wkill[1] += -wp;
       }
       if (kill_m) {
-        if (wm > 0) s->ledger[ORC_L_KILL_P] += 1; else if (wm < 0) s->ledger[ORC_L_KILL_M] += 1;
-        if (wm > 0) s->wkill[0] += wm; else s->wkill[1] += -wm;
+        if (wm > 0) o->ledger[ORC_L_KILL_P] += 1; else if (wm < 0) o->ledger[ORC_L_KILL_M] += 1;
+        if (wm > 0) o->wkill[0] += wm; else o->wkill[1] += -wm;
       }
       if (c->tangent) {
-        if (kill_p) { s->tkill[0] += tpH; s->tkill[1] += tpw; }
-        if (kill_m) { s->tkill[0] -= tpH; s->tkill[1] -= tpw; }
+        if (kill_p) { o->tkill[0] += tpH; o->tkill[1] += tpw; }
+        if (kill_m) { o->tkill[0] -= tpH; o->tkill[1] -= tpw; }
       }
       if (s->log_on) {
-        if (s->nlog == s->logcap) {
-          long long nc = s->logcap ? s->logcap * 2 : 1024;
-          orc_event* b2 = (orc_event*)realloc(s->log, (size_t)nc * sizeof(orc_event));
+        if (o->nlog == o->logcap) {
+          long long nc = o->logcap ? o->logcap * 2 : 1024;
+          orc_event* b2 = (orc_event*)realloc(o->log, (size_t)nc * sizeof(orc_event));
           if (!b2) return -1;
-          s->log = b2;
-          s->logcap = nc;
+          o->log = b2;
+          o->logcap = nc;
         }
         orc_event e;
         e.pid = pid;
@@ -466,10 +519,10 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
         e.factor = f;
         e.kill_plus = kill_p;
         e.kill_minus = kill_m;
-        s->log[s->nlog++] = e;
+        o->log[o->nlog++] = e;
       }
-      if (!kill_p && segment(s, xe, t, kp, wp, pid_p, l, 0, tpH, tpw)) return -1;
-      if (!kill_m && segment(s, xe, t, km, wm, pid_m, l, 0, -tpH, -tpw)) return -1;
+      if (!kill_p && segment(s, o, xe, t, kp, wp, pid_p, l, 0, tpH, tpw)) return -1;
+      if (!kill_m && segment(s, o, xe, t, km, wm, pid_m, l, 0, -tpH, -tpw)) return -1;
     }
     t += -log1p(-u4) / s->gamma0;
     ++j;
@@ -481,26 +534,82 @@ static int segment(orc_state* s, double xo, double to, double k, double w,
   out.pid = pid;
   out.tH = tH;
   out.tw = tw;
-  return push(&s->q, &s->nq, &s->capq, out);
+  return push(&o->q, &o->nq, &o->capq, out);
 }
 
-/* Advance nsteps intervals (Alg. 1 applied interval by interval). */
+/* Advance nsteps intervals (Alg. 1 applied interval by interval).  Chunk t
+ * of the particle list is [t n / T, (t + 1) n / T); the chunks' next lists,
+ * joined in chunk order, are the next list of a serial pass. */
+static int join_sinks(orc_state* s) {
+  const int T = s->threads;
+  long long total = 0;
+  for (int t = 0; t < T; ++t) total += s->sink[t].nq;
+  if (T == 1) {  /* the chunk's list becomes the particle list */
+    orc_sink* o = &s->sink[0];
+    orc_particle* tp = s->p;
+    long long tc = s->cap;
+    s->p = o->q;
+    s->cap = o->capq;
+    o->q = tp;
+    o->capq = tc;
+  } else {
+    if (total > s->cap) {
+      orc_particle* b = (orc_particle*)realloc(s->p, (size_t)total * sizeof(orc_particle));
+      if (!b) return -1;
+      s->p = b;
+      s->cap = total;
+    }
+    long long off[T + 1];
+    off[0] = 0;
+    for (int t = 0; t < T; ++t) off[t + 1] = off[t] + s->sink[t].nq;
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+    for (int t = 0; t < T; ++t)
+      if (s->sink[t].nq)
+        memcpy(s->p + off[t], s->sink[t].q, (size_t)s->sink[t].nq * sizeof(orc_particle));
+  }
+  s->n = total;
+  for (int t = 0; t < T; ++t) {
+    orc_sink* o = &s->sink[t];
+    for (int i = 0; i < ORC_L_N; ++i) s->ledger[i] += o->ledger[i];
+    for (int d = 0; d < 2; ++d) {
+      s->wkill[d] += o->wkill[d];
+      s->tkill[d] += o->tkill[d];
+    }
+    if (o->nlog) {
+      if (s->nlog + o->nlog > s->logcap) {
+        long long nc = s->nlog + o->nlog + 1024;
+        orc_event* b2 = (orc_event*)realloc(s->log, (size_t)nc * sizeof(orc_event));
+        if (!b2) return -1;
+        s->log = b2;
+        s->logcap = nc;
+      }
+      memcpy(s->log + s->nlog, o->log, (size_t)o->nlog * sizeof(orc_event));
+      s->nlog += o->nlog;
+    }
+  }
+  return 0;
+}
+
 int orc_step(orc_state* s, int nsteps) {
+  const int T = s->threads;
   for (int it = 0; it < nsteps; ++it) {
     uint32_t l = (uint32_t)s->step;
-    s->nq = 0;
     s->ledger[ORC_L_PSTEPS] += s->n;
-    for (long long i = 0; i < s->n; ++i) {
-      orc_particle p = s->p[i];
-      if (segment(s, p.x, 0.0, p.k, p.w, p.pid, l, 1, p.tH, p.tw)) return -1;
+    int fail = 0;
+#pragma omp parallel for num_threads(T) schedule(static, 1) reduction(| : fail)
+    for (int t = 0; t < T; ++t) {
+      orc_sink* o = &s->sink[t];
+      o->nq = 0;
+      o->nlog = 0;
+      memset(o->ledger, 0, sizeof(o->ledger));
+      o->wkill[0] = o->wkill[1] = o->tkill[0] = o->tkill[1] = 0.0;
+      const long long i0 = s->n * t / T, i1 = s->n * (t + 1) / T;
+      for (long long i = i0; i < i1 && !fail; ++i) {
+        const orc_particle p = s->p[i];
+        if (segment(s, o, p.x, 0.0, p.k, p.w, p.pid, l, 1, p.tH, p.tw)) fail = 1;
+      }
     }
-    orc_particle* t = s->p;
-    s->p = s->q;
-    s->q = t;
-    long long tc = s->cap;
-    s->cap = s->capq;
-    s->capq = tc;
-    s->n = s->nq;
+    if (fail || join_sinks(s)) return -1;
     s->step += 1;
     s->fresh = 0;
   }
@@ -534,32 +643,55 @@ static double bin_k(const orc_state* s, double k) {
  * offsets from its own stream.  A coordinate that rounds onto a neighbouring cell is moved by
  * single ulps back into D_nu, so that binning the regenerated set gives the
  * same counts. */
+/* One regenerated particle of cell (ix, ik): offsets from its own stream. */
+static orc_particle regen_one(const orc_state* s, uint64_t pid, long long ix, long long ik,
+                              double w, double tH, double tw) {
+  uint32_t h[4];
+  draw4(s, pid, ORC_STEP_REGEN, 0u, h);
+  double x = s->c.xmin + ((double)ix + orc_u53(h[0], h[1])) * s->dx;
+  double k = s->c.kmin + ((double)ik + orc_u53(h[2], h[3])) * s->dk;
+  while (bin_x(s, x) > (double)ix) x = nextafter(x, -INFINITY);
+  while (bin_x(s, x) < (double)ix) x = nextafter(x, INFINITY);
+  while (bin_k(s, k) > (double)ik) k = nextafter(k, -INFINITY);
+  while (bin_k(s, k) < (double)ik) k = nextafter(k, INFINITY);
+  orc_particle p = {x, k, w, pid, tH, tw};
+  return p;
+}
+
 static int regenerate(orc_state* s) {
-  long long nh = (long long)s->c.nx * s->c.nk;
-  s->n = 0;
-  uint64_t j = 0;
-  for (long long nu = 0; nu < nh; ++nu) {
-    int cnt = s->grid[nu];
-    if (cnt == 0) continue;
-    long long ix = nu / s->c.nk, ik = nu % s->c.nk;
-    long long m = cnt > 0 ? cnt : -(long long)cnt;
-    double sign = cnt > 0 ? 1.0 : -1.0;
-    for (long long r = 0; r < m; ++r, ++j) {
-      uint64_t pid = ((uint64_t)s->epoch << 40) | ((uint64_t)s->c.instance << 32) | j;
-      uint32_t h[4];
-      draw4(s, pid, ORC_STEP_REGEN, 0u, h);
-      double ux = orc_u53(h[0], h[1]);
-      double uk = orc_u53(h[2], h[3]);
-      double x = s->c.xmin + ((double)ix + ux) * s->dx;
-      double k = s->c.kmin + ((double)ik + uk) * s->dk;
-      while (bin_x(s, x) > (double)ix) x = nextafter(x, -INFINITY);
-      while (bin_x(s, x) < (double)ix) x = nextafter(x, INFINITY);
-      while (bin_k(s, k) > (double)ik) k = nextafter(k, -INFINITY);
-      while (bin_k(s, k) < (double)ik) k = nextafter(k, INFINITY);
-      orc_particle p = {x, k, sign, pid, 0.0, 0.0};
-      if (push(&s->p, &s->n, &s->cap, p)) return -1;
+  const long long nh = (long long)s->c.nx * s->c.nk;
+  const int T = s->threads;
+  /* chunk t holds cells [t nh / T, (t + 1) nh / T); its particles start
+   * after those of the chunks before it */
+  long long off[T + 1];
+  off[0] = 0;
+  for (int t = 0; t < T; ++t) {
+    long long m = 0;
+    for (long long nu = nh * t / T; nu < nh * (t + 1) / T; ++nu) m += llabs((long long)s->grid[nu]);
+    off[t + 1] = off[t] + m;
+  }
+  if (off[T] > s->cap) {
+    orc_particle* b = (orc_particle*)realloc(s->p, (size_t)off[T] * sizeof(orc_particle));
+    if (!b) return -1;
+    s->p = b;
+    s->cap = off[T];
+  }
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+  for (int t = 0; t < T; ++t) {
+    uint64_t j = (uint64_t)off[t];
+    for (long long nu = nh * t / T; nu < nh * (t + 1) / T; ++nu) {
+      int cnt = s->grid[nu];
+      if (cnt == 0) continue;
+      long long ix = nu / s->c.nk, ik = nu % s->c.nk;
+      long long m = cnt > 0 ? cnt : -(long long)cnt;
+      double sign = cnt > 0 ? 1.0 : -1.0;
+      for (long long r = 0; r < m; ++r, ++j) {
+        uint64_t pid = ((uint64_t)s->epoch << 40) | ((uint64_t)s->c.instance << 32) | j;
+        s->p[j] = regen_one(s, pid, ix, ik, sign, 0.0, 0.0);
+      }
     }
   }
+  s->n = off[T];
   if (!s->c.tangent) return 0;
   /* Tangent mode: the tangent histogram D_nu is carried by particles of
    * sign 0, n_t = ceil(max(|D_H|, |D_w|) / quantum) of them per cell with
@@ -578,16 +710,7 @@ static int regenerate(orc_state* s) {
     for (long long r = 0; r < nt; ++r, ++jt) {
       uint64_t pid = ((uint64_t)s->epoch << 40) | ((uint64_t)s->c.instance << 32) |
                      0x80000000ull | jt;
-      uint32_t h[4];
-      draw4(s, pid, ORC_STEP_REGEN, 0u, h);
-      double x = s->c.xmin + ((double)ix + orc_u53(h[0], h[1])) * s->dx;
-      double k = s->c.kmin + ((double)ik + orc_u53(h[2], h[3])) * s->dk;
-      while (bin_x(s, x) > (double)ix) x = nextafter(x, -INFINITY);
-      while (bin_x(s, x) < (double)ix) x = nextafter(x, INFINITY);
-      while (bin_k(s, k) > (double)ik) k = nextafter(k, -INFINITY);
-      while (bin_k(s, k) < (double)ik) k = nextafter(k, INFINITY);
-      orc_particle p = {x, k, 0.0, pid, tH, tw};
-      if (push(&s->p, &s->n, &s->cap, p)) return -1;
+      if (push(&s->p, &s->n, &s->cap, regen_one(s, pid, ix, ik, 0.0, tH, tw))) return -1;
     }
   }
   return 0;
@@ -602,19 +725,30 @@ static void bin_signed(orc_state* s) {
   memset(s->grid, 0, (size_t)nh * sizeof(int));
   if (s->c.tangent)
     for (int d = 0; d < 2; ++d) memset(s->dgrid[d], 0, (size_t)nh * sizeof(long long));
+  long long out_p = 0, out_m = 0;
+  /* integer sums: the same in any order */
+#pragma omp parallel for num_threads(s->threads) reduction(+ : out_p, out_m)
   for (long long i = 0; i < s->n; ++i) {
     long long nu;
     const orc_particle* p = &s->p[i];
     if (cell_of(s, p->x, p->k, &nu)) {
-      if (p->w != 0.0) s->grid[nu] += p->w > 0 ? 1 : -1;
+      if (p->w != 0.0) {
+#pragma omp atomic
+        s->grid[nu] += p->w > 0 ? 1 : -1;
+      }
       if (s->c.tangent) {
-        s->dgrid[0][nu] += llrint(p->tH * 4294967296.0);
-        s->dgrid[1][nu] += llrint(p->tw * 4294967296.0);
+        const long long a = llrint(p->tH * 4294967296.0), b = llrint(p->tw * 4294967296.0);
+#pragma omp atomic
+        s->dgrid[0][nu] += a;
+#pragma omp atomic
+        s->dgrid[1][nu] += b;
       }
     } else {
-      if (p->w > 0) s->ledger[ORC_L_OUT_P] += 1; else if (p->w < 0) s->ledger[ORC_L_OUT_M] += 1;
+      if (p->w > 0) out_p += 1; else if (p->w < 0) out_m += 1;
     }
   }
+  s->ledger[ORC_L_OUT_P] += out_p;
+  s->ledger[ORC_L_OUT_M] += out_m;
 }
 
 static uint64_t mulhi64(uint64_t a, uint64_t b) {

@@ -16,7 +16,8 @@ def make_oracle(wl, **over):
                          instance=w.get("instance", 0),
                          tangent=w.get("tangent", False),
                          tquantum=w.get("tquantum", 1.0),
-                         comps=tuple(w.get("comps", ())))
+                         comps=tuple(w.get("comps", ())),
+                         threads=w.get("threads", 1))
 
 
 def net_sign(w):
