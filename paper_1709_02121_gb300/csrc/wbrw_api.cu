@@ -238,8 +238,9 @@ wbrw_status device_status(wbrw_ctx* c) {
            "read device error word");
   WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
   if (err == 0) return WBRW_OK;
-  return seterr(c, WBRW_ERR_CAPACITY,
-                "device error 0x%x:%s%s%s%s%s", err,
+  return seterr(c, (err & ERR_NUMERIC) ? WBRW_ERR_NUMERIC : WBRW_ERR_CAPACITY,
+                "device error 0x%x:%s%s%s%s%s%s", err,
+                (err & ERR_NUMERIC) ? " non-finite position or wavevector at binning;" : "",
                 (err & ERR_CAP_PARTICLES) ? " particle capacity exceeded;" : "",
                 (err & ERR_CAP_QUEUE) ? " offspring queue capacity exceeded;" : "",
                 (err & ERR_CAP_EQUEUE) ? " candidate queue capacity exceeded;" : "",

@@ -653,8 +653,17 @@ __device__ __forceinline__ long long wsum_units(typename P::T w) {
   else return __float2ll_rn(w * 2147483648.0f);
 }
 
+// A particle outside the grid at binning: dropped and tallied by sign.  A
+// non-finite coordinate also lands here (every comparison of the cell test
+// fails for NaN or infinity), so this rare branch is where the numeric
+// error is latched; the in-grid path pays nothing for the check.
 template <class P>
-__device__ __forceinline__ void tally_out(const KP<P>& p, Acc& acc, typename P::T w) {
+__device__ __forceinline__ void tally_out(const KP<P>& p, Acc& acc, typename P::T w,
+                                          const PV<P>& x, const PV<P>& k) {
+  bool finite = true;
+#pragma unroll
+  for (int d = 0; d < P::D; ++d) finite = finite && isfinite(x.c[d]) && isfinite(k.c[d]);
+  if (!finite) set_err(p.cnt, ERR_NUMERIC);
   if (p.count_ledger) {
     if (w > (typename P::T)0) ++acc.out_p;
     else if (w < (typename P::T)0) ++acc.out_m;
@@ -704,15 +713,15 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
       if (!P::TG || w != (T)0) atomicAdd(p.grid + cbase + cell, w > (T)0 ? 1 : -1);
       add_tangent<P>(p, (long long)cbase + cell, tau);
     } else {
-      tally_out<P>(p, acc, w);
+      tally_out<P>(p, acc, w, x, k);
     }
   } else if constexpr (DST == DST_WSUM) {
     if (cell_of<P>(p, x, k, cell))
       atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
                 (unsigned long long)wsum_units<P>(w));
-    else tally_out<P>(p, acc, w);
+    else tally_out<P>(p, acc, w, x, k);
   } else if constexpr (DST == DST_BIN2) {
-    if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w); return; }
+    if (!cell_of<P>(p, x, k, cell)) { tally_out<P>(p, acc, w, x, k); return; }
     if (w == (T)0) return;
     const unsigned g = global_warp();
     const unsigned r = atomicAdd(&wc.r, 1u);
@@ -1383,7 +1392,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         if (!P::TG || w != (T)0) key = 2u * (unsigned)(cbase + cell) + (w > (T)0 ? 1u : 0u);
       } else {
         cell = -1;
-        tally_out<P>(p, acc, w);
+        tally_out<P>(p, acc, w, x, k);
       }
     }
     const unsigned grp = __match_any_sync(kFull, key);
@@ -1400,7 +1409,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if (act) {
         int cell;
         if (cell_of<P>(p, x, k, cell)) key = 2u * (unsigned)(cbase + cell) + (w > (T)0 ? 1u : 0u);
-        else tally_out<P>(p, acc, w);
+        else tally_out<P>(p, acc, w, x, k);
       }
       const unsigned grp = __match_any_sync(kFull, key);
       if (key != ~0u && lane == __ffs(grp) - 1) {
@@ -1413,12 +1422,12 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       if (cell_of<P>(p, x, k, cell))
         atomicAdd((unsigned long long*)(p.wsum + cbase + cell),
                   (unsigned long long)wsum_units<P>(w));
-      else tally_out<P>(p, acc, w);
+      else tally_out<P>(p, acc, w, x, k);
     }
   } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
     int cell = -1;
     if (act) {
-      if (!cell_of<P>(p, x, k, cell)) { cell = -1; tally_out<P>(p, acc, w); }
+      if (!cell_of<P>(p, x, k, cell)) { cell = -1; tally_out<P>(p, acc, w, x, k); }
       else if (w == (T)0) cell = -1;
     }
     const unsigned bal = __ballot_sync(kFull, cell >= 0);

@@ -53,6 +53,7 @@ enum : int {
   ERR_CAP_EQUEUE = 4,
   ERR_NESTING = 8,
   ERR_CAP_RECORDS = 16,
+  ERR_NUMERIC = 32,  // a non-finite position or wavevector reached binning
 };
 
 // ledger slots (Counters::ledger)
