@@ -21,9 +21,11 @@
  *    wbrw_annihilate and wbrw_run do not wait for the GPU.  wbrw_density,
  *    wbrw_particles, wbrw_counters and wbrw_sync_status synchronise the stream.
  *  - Device-side faults are latched in a device error word: particle or queue
- *    capacity exceeded, or offspring nesting too deep.  The next synchronising
- *    call reports them.  After any error the context refuses further work
- *    with WBRW_ERR_STATE; only wbrw_last_error and wbrw_destroy remain valid.
+ *    capacity exceeded, offspring nesting too deep (WBRW_ERR_CAPACITY), or a
+ *    non-finite coordinate at binning (WBRW_ERR_NUMERIC).  The next
+ *    synchronising call reports them.  After any error the context refuses
+ *    further work with WBRW_ERR_STATE; only wbrw_last_error and wbrw_destroy
+ *    remain valid.
  *  - Random numbers are Philox4x32-10 keyed by config.seed and indexed by
  *    (particle id, step, draw).  Results therefore do not depend on the order
  *    in which the GPU processes particles.
@@ -46,7 +48,9 @@ typedef enum {
   WBRW_ERR_CUDA = -3,     /* a CUDA runtime call failed                    */
   WBRW_ERR_STATE = -4,    /* context already failed, or call out of order  */
   WBRW_ERR_TIMEOUT = -5,  /* reserved: a bounded device wait gave up       */
-  WBRW_ERR_NUMERIC = -6   /* reserved: non-finite state detected           */
+  WBRW_ERR_NUMERIC = -6   /* a non-finite position or wavevector reached   */
+                          /* binning (latched by the device, reported by   */
+                          /* the next synchronising call)                  */
 } wbrw_status;
 
 /* WBRW_WP: weighted particles (pairs always made with weights
@@ -386,12 +390,18 @@ wbrw_status wbrw_autotune(wbrw_ctx* ctx, int trials, wbrw_tuning* best, double* 
  * Its only scratch, the per-column sums, lives in a static device array of
  * WBRW_STATIC_MAX_NX int64 entries (512 KiB) that every GPU loading the
  * library keeps until the process exits.  nx above that maximum is refused
- * with WBRW_ERR_CAPACITY; invalid arguments give WBRW_ERR_ARG.  The first
- * call on each device looks up the array's device address on that device
- * (make that first call before any stream capture).  All calls share the
- * array: calls whose GPU work overlaps (other streams, other threads) race
- * and must be serialised by the caller.  Each call overwrites every entry it
- * reads, so nothing needs clearing between calls. */
+ * with WBRW_ERR_CAPACITY.  Invalid arguments give WBRW_ERR_ARG, and so does
+ * any non-NULL buffer that is not device (or managed) memory of the current
+ * device: host memory or another GPU's buffer is refused before any launch.
+ * The first call on each device looks up the array's device address on that
+ * device and keeps it (make that first call before any stream capture).
+ * The address is not looked up again, so calls after a cudaDeviceReset in
+ * the same process are not supported.  All calls share the array: calls
+ * whose GPU work overlaps (other streams, other threads) race and must be
+ * serialised by the caller.  Each call overwrites every entry it reads, so
+ * nothing needs clearing between calls.  A launch failure gives
+ * WBRW_ERR_CUDA; the check also consumes, and reports, an error that an
+ * earlier runtime call of the caller left pending. */
 #define WBRW_STATIC_MAX_NX 65536
 wbrw_status wbrw_observables_static(const int* grid, int nx, int nk,
                                     double xmin, double xmax, double kmin,

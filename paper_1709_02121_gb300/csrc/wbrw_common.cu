@@ -856,6 +856,20 @@ constexpr int kStaticMaxDevices = 64;
 static __device__ __align__(256) long long g_obs_col_static[WBRW_STATIC_MAX_NX];
 std::mutex g_static_mu;
 long long* g_static_col[kStaticMaxDevices];  // device address, per device
+
+// A caller's buffer must be device (or managed) memory of the current
+// device: the kernels below run there, and a buffer of another GPU or of the
+// host would be read across the interconnect at best and fault at worst.
+bool on_device(const void* ptr, int dev) {
+  if (!ptr) return true;  // optional outputs
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();  // unregistered host memory: clear the query's error
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+
 }  // namespace
 
 extern "C" wbrw_status wbrw_observables_static(const int* grid, int nx, int nk, double xmin,
@@ -870,6 +884,9 @@ extern "C" wbrw_status wbrw_observables_static(const int* grid, int nx, int nk, 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices)
     return WBRW_ERR_CUDA;
+  if (!on_device(grid, dev) || !on_device(density, dev) || !on_device(marginal_x, dev) ||
+      !on_device(transmission, dev))
+    return WBRW_ERR_ARG;
   long long* col = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mu);
@@ -887,8 +904,13 @@ extern "C" wbrw_status wbrw_observables_static(const int* grid, int nx, int nk, 
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return WBRW_ERR_CUDA;
+  // Each launch is checked on its own.  cudaGetLastError also returns (and
+  // clears) an error that an earlier runtime call of the caller left
+  // pending; such an error is reported here as WBRW_ERR_CUDA.
   wbrw::k_obs_cols<<<4 * sms, wbrw::kBlock, 0, s>>>(grid, nullptr, nx, nk, na, dx, dk, 1.0, density,
                                                     marginal_x, col);
+  if (cudaGetLastError() != cudaSuccess) return WBRW_ERR_CUDA;
   wbrw::k_obs_total<<<1, wbrw::kBlock, 0, s>>>(col, nx, xmin, dx, na, 1.0, transmission);
-  return cudaGetLastError() == cudaSuccess ? WBRW_OK : WBRW_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return WBRW_ERR_CUDA;
+  return WBRW_OK;
 }
