@@ -409,6 +409,18 @@ wbrw_status wbrw_observables_static(const int* grid, int nx, int nk,
                                     double* density, double* marginal_x,
                                     double* transmission, void* cuda_stream);
 
+/* Measurement aid: the Philox4x32-10 call of the flight and event kernels
+ * (Salmon et al., SC'11; keyed by `seed`), run in a dependent chain of
+ * `iters` calls by each of `nthreads` threads (each call's output is the
+ * next call's counter), with nothing else around it.  Its call rate,
+ * nthreads * iters / (the kernel's time on cuda_stream), is the integer-pipe
+ * ceiling of the hot path's random numbers: the peak that the integer-bound
+ * kernels are compared against.  out: nthreads uint32 in device memory of
+ * the current device (the XOR of each thread's last output), else
+ * WBRW_ERR_ARG.  Async; no context.  The paper has no counterpart. */
+wbrw_status wbrw_philox_chain(unsigned long long seed, int iters, long long nthreads,
+                              unsigned int* out, void* cuda_stream);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent problems in the same launches.
  *

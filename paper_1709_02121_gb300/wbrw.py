@@ -38,7 +38,8 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_observables_static", "wbrw_batch_scratch_bytes", "wbrw_batch_init",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
            "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune",
-           "wbrw_init4d", "wbrw_transmission_gradients", "wbrw_init_td")
+           "wbrw_init4d", "wbrw_transmission_gradients", "wbrw_init_td",
+           "wbrw_philox_chain")
 TUNE_BPS_MAX, TUNE_PASSES_MAX = 3, 6
 MAX_CAPACITY = 4293918720  # WBRW_MAX_CAPACITY: slots index in 32 bits
 MAX_INSTANCES = 256
@@ -170,6 +171,8 @@ def load(path: str = LIB_PATH):
     D = ctypes.c_double
     L.wbrw_observables_static.argtypes = [P, I, I, D, D, D, D, LL, P, P, P, P]
     L.wbrw_observables_static.restype = I
+    L.wbrw_philox_chain.argtypes = [ctypes.c_ulonglong, I, LL, P, P]
+    L.wbrw_philox_chain.restype = I
     _lib = L
     return L
 
@@ -365,6 +368,12 @@ def wbrw_observables_static(grid_ptr, nx, nk, xmin, xmax, kmin, kmax, n_alpha,
         ctypes.c_void_p(density_ptr) if density_ptr else None,
         ctypes.c_void_p(marginal_ptr), ctypes.c_void_p(transmission_ptr),
         ctypes.c_void_p(stream_ptr))
+
+
+def wbrw_philox_chain(seed, iters, nthreads, out_ptr, stream_ptr):
+    """Launch the chained Philox rate probe (device output, async)."""
+    return load().wbrw_philox_chain(seed, iters, nthreads, ctypes.c_void_p(out_ptr),
+                                    ctypes.c_void_p(stream_ptr))
 
 
 def wbrw_destroy(ctx):

@@ -131,6 +131,10 @@ def test_fp32_density_within_3_standard_errors_of_fp64(runs, ti):
     e = nul_c / (nul_c - 2)
     v = 2 * nul_c ** 2 * (nul_c - 1) / ((nul_c - 2) ** 2 * (nul_c - 4))
     z = ((tl ** 2).sum() - e.sum()) / math.sqrt(v.sum())
+    print("\ndensity t=%g: %d cells, %d beyond 3 SE (expected %.1f), max |t| %.2f "
+          "(bound %.2f), mean t^2 %.3f (null %.3f, z %.2f)"
+          % (TIMES[ti] * WL["dt"], K, beyond, mean_p, np.abs(tl).max(), bound.min(),
+             (tl ** 2).mean(), e.mean(), z))
     assert z < 5.0, z
 
 
@@ -138,6 +142,8 @@ def test_fp32_density_within_3_standard_errors_of_fp64(runs, ti):
 def test_fp32_transmission_within_2e_3_of_fp64(runs, ti):
     T32, T64 = runs["fp32"][1][:, ti], runs["fp64"][1][:, ti]
     se = math.hypot(T32.std(ddof=1), T64.std(ddof=1)) / math.sqrt(SEEDS)
+    print("\ntransmission t=%g: fp32 %.6f fp64 %.6f difference %.2e (combined SE %.2e)"
+          % (TIMES[ti] * WL["dt"], T32.mean(), T64.mean(), T32.mean() - T64.mean(), se))
     assert se < 5e-4, se                   # resolution well inside the bound
     assert abs(T32.mean() - T64.mean()) <= 2e-3, (T32.mean(), T64.mean(), se)
 
@@ -156,6 +162,10 @@ def test_the_benchmark_size_matches_fp64(torch, runs):
         live_c = se > 0
         z = (d[ti] - d64[:, ti].mean(0))[live_c] / se[live_c]
         K = int(live_c.sum())
+        print("\n1e8 run t=%g: T %.6f (fp64 %.6f), %d cells, %d beyond 3 SE, max |z| %.2f, "
+              "mean z^2 %.3f, live %d" % (TIMES[ti] * WL["dt"], T[ti], T64[:, ti].mean(), K,
+                                          (np.abs(z) > 3).sum(), np.abs(z).max(),
+                                          np.mean(z ** 2), live[ti]))
         assert (np.abs(z) > 3.0).sum() <= 0.01 * K + 5, ((np.abs(z) > 3).sum(), K)
         assert np.abs(z).max() < 7.0, np.abs(z).max()
         assert np.mean(z ** 2) < 1.5, np.mean(z ** 2)
