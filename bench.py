@@ -274,7 +274,7 @@ def config_of(wl, args):
             "intervals_per_step": wl["resample_every"], "strategy": wl["strategy"],
             "precision": wl["precision"], "potential": pot,
             "l2": "flushed (512 MiB write) between timed steps",
-            "cuda_graphs": not args.no_graph and wl["strategy"] == "sp1",
+            "cuda_graphs": not args.no_graph,
             "parallelism": "replicas x%d" % args.gpus}
 
 
@@ -619,7 +619,7 @@ def ours(args, wl):
     cap = int(args.capacity_factor * n) + (1 << 20)
     model = Simulation4 if wl.get("dim", 2) == 4 else Simulation
     sim = model(wl, capacity=cap, stream=torch.cuda.Stream())
-    if not args.no_graph and wl["strategy"] == "sp1":
+    if not args.no_graph:
         sim.graph(True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     cells = sim.cells
@@ -684,10 +684,10 @@ def secondaries(args, local, flush, ceiling, peaks):
     jobs = [
         # sp2: the 1e8 workload with the signed bootstrap filter
         ("sp2", lambda: plain_like(workloads.scaled(workloads.GAUSS_2D_FP32_1E8, strategy="sp2"),
-                                   Simulation, False)),
+                                   Simulation, not args.no_graph)),
         # the 4D Helium-like system
         ("he4d", lambda: plain_like(workloads.scaled(workloads.HE_4D_FP32_5E7), Simulation4,
-                                    True)),
+                                    not args.no_graph)),
         # the batch of 256 against the plain per-instance path
         ("batch", lambda: _strip(batch_measure(args, workloads.BATCH_2D_FP32_256, K, W, local,
                                                flush, ceiling, peaks, plain=True))),

@@ -324,17 +324,18 @@ wbrw_status wbrw_profile_read(wbrw_ctx* ctx, double* total_ms,
 wbrw_status wbrw_profile_read_events(wbrw_ctx* ctx, double* total_ms,
                                      long long* launches);
 
-/* CUDA graphs for wbrw_run.  With enable = 1, each sp1 resampling period that
+/* CUDA graphs for wbrw_run.  With enable = 1, each resampling period that
  * regenerates its particles from the histogram (every period but one that
  * starts from the initial particles or from wbrw_step) is captured into a
  * CUDA graph the first time a period of its length runs, and replayed after
- * that: one launch per period instead of one per kernel.  Results are bit
- * for bit those of enable = 0 (the kernels read the period's first interval
- * and id base from device memory, and the graph advances them).  The context
- * stream must be a created stream (not the legacy or per-thread default
- * stream) and must not be capturing; otherwise WBRW_ERR_ARG.  enable = 0
- * synchronises the stream and releases the graphs.  sp2 periods always
- * launch kernel by kernel.  The CUDA events of wbrw_profile are part of a
+ * that: one launch per period instead of one per kernel.  This holds for
+ * every strategy (sp1, sp2, wp).  Results are bit for bit those of
+ * enable = 0 (the kernels read the period's first interval and id base from
+ * device memory, the resampling kernels the epoch of the histogram they make,
+ * and the graph advances them).  The context stream must be a created stream
+ * (not the legacy or per-thread default stream) and must not be capturing;
+ * otherwise WBRW_ERR_ARG.  enable = 0 synchronises the stream and releases
+ * the graphs.  The CUDA events of wbrw_profile are part of a
  * graph only if profiling was on when it was captured (each event costs a
  * few microseconds per replay), so the first replay after wbrw_profile
  * switches profiling on or off captures its period again. */

@@ -265,7 +265,7 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
   } else if (c->cfg.strategy == WBRW_WP) {
     WBRW_TRY(c, launch_zero(c, c->tmp_wsum, (size_t)c->nh * 8), "zero");
     WBRW_TRY(c, d->bin(c, DST_WSUM, c->buf.grid, 1), "weights");
-    WBRW_TRY(c, launch_wp_round(c), "rounding");
+    WBRW_TRY(c, launch_wp_round(c, 0), "rounding");  // binning set the new epoch's id base
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
     WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
@@ -274,7 +274,7 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
       WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
     }
     WBRW_TRY(c, d->bin(c, DST_BIN2, c->buf.grid, 1), "records");
-    WBRW_TRY(c, launch_boot(c), "bootstrap");
+    WBRW_TRY(c, launch_boot(c, 0), "bootstrap");
   }
   WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
   if (c->tangent) WBRW_TRY(c, launch_scan_tangent(c), "tangent plan");
@@ -310,8 +310,9 @@ wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_
   cudaError_t e = d->chunk(c, l0, L, src, dst);
   c->epoch = keep_epoch;
   WBRW_TRY(c, e, "period");
-  if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c), "bootstrap");
-  if (c->cfg.strategy == WBRW_WP) WBRW_TRY(c, launch_wp_round(c), "rounding");
+  // the device id base is still the source's epoch: the histogram is the next
+  if (c->cfg.strategy == WBRW_SP2_BOOTSTRAP) WBRW_TRY(c, launch_boot(c, 1), "bootstrap");
+  if (c->cfg.strategy == WBRW_WP) WBRW_TRY(c, launch_wp_round(c, 1), "rounding");
   WBRW_TRY(c, launch_scan_cells(c, c->buf.grid), "scan");
   if (c->tangent) WBRW_TRY(c, launch_scan_tangent(c), "tangent plan");
   return WBRW_OK;
@@ -325,7 +326,7 @@ void drop_graphs(wbrw_ctx* c) {
   c->ngraphs = 0;
 }
 
-// Capture one sp1 period of length len that regenerates from the histogram.
+// Capture one period of length len that regenerates from the histogram.
 // Its kernels take the first interval and the id base from the device
 // period state, which the graph advances at its end.
 wbrw_status capture_period(wbrw_ctx* c, int len, PeriodGraph* g) {
@@ -382,7 +383,7 @@ wbrw_status capture_period(wbrw_ctx* c, int len, PeriodGraph* g) {
   return WBRW_OK;
 }
 
-// Replay (capturing first if needed) one regenerating sp1 period.
+// Replay (capturing first if needed) one regenerating period.
 wbrw_status graph_period(wbrw_ctx* c, int len) {
   PeriodGraph* g = nullptr;
   for (int i = 0; i < c->ngraphs; ++i)
@@ -913,7 +914,7 @@ wbrw_status wbrw_run(wbrw_ctx* c, int nsteps) {
     const int l0 = (int)c->step, L = l0 + to_boundary;
     const long long regen_epoch = c->epoch;
     wbrw_status st;
-    if (c->graph_on && src == SRC_REGEN && c->cfg.strategy == WBRW_SP1_PAIR)
+    if (c->graph_on && src == SRC_REGEN)
       st = graph_period(c, to_boundary);
     else
       st = enqueue_period(c, src, l0, L, regen_epoch);

@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(kBlock) k_boot_draw(Counters* c, long long nh,
                                                       const unsigned long long* pre1,
                                                       int* keep0, int* keep1,
                                                       const int* guide, uint32_t key0,
-                                                      uint32_t key1, unsigned long long epoch) {
+                                                      uint32_t key1, int epoch_delta) {
+  const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
   unsigned long long nr[2];
   for (int s = 0; s < 2; ++s) {
     const long long d = (long long)c->boot_n[s] - (long long)c->boot_keep[s];
@@ -467,7 +468,8 @@ __global__ void __launch_bounds__(kBlock) k_boot_draw(Counters* c, long long nh,
 __global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long long nh,
                                                          const int* keep0, const int* keep1,
                                                          int* grid, uint32_t key0,
-                                                         uint32_t key1, unsigned long long epoch) {
+                                                         uint32_t key1, int epoch_delta) {
+  const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
   double amp[2];
   for (int s = 0; s < 2; ++s)
     amp[s] = c->boot_n[s] > 0
@@ -492,9 +494,11 @@ __global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long
 // fixed point 2^-31) rounded by Alg. 3: floor(|m|) particles plus one with
 // probability |m| - floor(|m|), sign of m, the uniform of the draw
 // (nu, ROUND, epoch) as for sp2.
-__global__ void __launch_bounds__(kBlock) k_wp_round(long long nh, const long long* wsum,
-                                                     int* grid, uint32_t key0, uint32_t key1,
-                                                     unsigned long long epoch) {
+__global__ void __launch_bounds__(kBlock) k_wp_round(const Counters* c, long long nh,
+                                                     const long long* wsum, int* grid,
+                                                     uint32_t key0, uint32_t key1,
+                                                     int epoch_delta) {
+  const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
   for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
        nu += (long long)gridDim.x * kBlock) {
     const double m = __dmul_rn((double)wsum[nu], 1.0 / 2147483648.0);
@@ -749,10 +753,12 @@ cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
 }
 
 // Called after the records of the period are written and tallied.
-cudaError_t launch_boot(Ctx* c) {
+// The resampling kernels read the epoch of the histogram they make from the
+// device period state (the id base of the particles just binned, plus
+// epoch_delta), so that a captured period replays with the right streams.
+cudaError_t launch_boot(Ctx* c, int epoch_delta) {
   const long long nh = c->nh, nb = c->scan_blocks;
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
-  const unsigned long long epoch = (unsigned long long)c->epoch;
   const int g = grid_cap(c, 8);
   k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg,
                                           c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
@@ -768,17 +774,17 @@ cudaError_t launch_boot(Ctx* c) {
       c->cnt, nh, c->boot_res[0], c->boot_res[1], c->boot_guide);
   k_boot_draw<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_res[0], c->boot_res[1],
                                            c->boot_keep[0], c->boot_keep[1], c->boot_guide, key0,
-                                           key1, epoch);
+                                           key1, epoch_delta);
   k_boot_combine<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_keep[0], c->boot_keep[1],
-                                              c->buf.grid, key0, key1, epoch);
+                                              c->buf.grid, key0, key1, epoch_delta);
   c->launches += 3;
   return cudaGetLastError();
 }
 
-cudaError_t launch_wp_round(Ctx* c) {
+cudaError_t launch_wp_round(Ctx* c, int epoch_delta) {
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
-  k_wp_round<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->nh, c->tmp_wsum, c->buf.grid, key0,
-                                                       key1, (unsigned long long)c->epoch);
+  k_wp_round<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->cnt, c->nh, c->tmp_wsum, c->buf.grid,
+                                                       key0, key1, epoch_delta);
   c->launches++;
   return cudaGetLastError();
 }

@@ -285,9 +285,9 @@ cudaError_t launch_scan_tangent(Ctx*);
 // (dT/dH, dT/dw) of every instance from the tangent histogram, into
 // c->inst_grad.
 cudaError_t launch_transmission_gradients(Ctx*);
-cudaError_t launch_boot(Ctx*);
+cudaError_t launch_boot(Ctx*, int epoch_delta);
 // wp: Alg. 3's rounding of the weighted histogram tmp_wsum into the grid.
-cudaError_t launch_wp_round(Ctx*);
+cudaError_t launch_wp_round(Ctx*, int epoch_delta);
 // Observables of instance `inst` from the counts / Q1.31 weight sums of all
 // instances (one of the two is NULL).
 cudaError_t launch_observables(Ctx*, int inst, const int* counts, const long long* wsum);

@@ -46,24 +46,28 @@ KEYS = ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_
         "particle_steps_first", "live", "step", "epoch", "candidates", "first_pairs")
 
 
+@pytest.mark.parametrize("strategy", ["sp1", "sp2", "wp"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_replayed_periods_equal_eager_periods(gpu, precision):
-    wl = small(precision=precision)
+def test_replayed_periods_equal_eager_periods(gpu, precision, strategy):
+    wl = small(precision=precision, strategy=strategy)
     a, b = sim(wl, False, gpu), sim(wl, True, gpu)
     for period in range(6):
         a.run(5)
         b.run(5)
         assert np.array_equal(a.grid_counts(), b.grid_counts()), period
     ca, cb = a.counters(), b.counters()
-    for k in KEYS:
+    keys = KEYS + (("boot_nplus", "boot_nminus", "boot_nrplus", "boot_nrminus", "boot_wplus",
+                    "boot_wminus") if strategy == "sp2" else ())
+    for k in keys:
         assert ca[k] == cb[k], k
     # the same kernels, plus one period-state advance per replay (periods 2-6)
     # and one initial period-state write
     assert cb["launches"] - ca["launches"] == 5 + 1
 
 
-def test_replays_match_the_oracle_fp64(gpu):
-    wl = small(n_alpha=3000)
+@pytest.mark.parametrize("strategy", ["sp1", "sp2", "wp"])
+def test_replays_match_the_oracle_fp64(gpu, strategy):
+    wl = small(n_alpha=3000, strategy=strategy)
     s = sim(wl, True, gpu)
     o = make_oracle(wl)
     o.init_gauss(wl["n_alpha"], wl["x0"], wl["sigma_x"], wl["k0"])
