@@ -29,7 +29,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
   size_t counters, cpid, fq0, fq1, eq0, eq1, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, guide, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
+      rec_a, keep0, keep1, res0, res1, ucnt, guide, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
       tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, tab_guide0, tab_guide1, dgrid0, dgrid1, tnz_cell, tnz_start,
       tnz_tau, ttile_nz, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
@@ -143,6 +143,7 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.keep1 = take(sp2 ? (size_t)nh * 4 : 0);
   L.res0 = take(sp2 ? (size_t)nh * 8 : 0);
   L.res1 = take(sp2 ? (size_t)nh * 8 : 0);
+  L.ucnt = take(sp2 ? (size_t)2 * nh * 4 : 0);
   L.guide = take(sp2 ? (size_t)2 * (kGuide + 1) * 4 : 0);
   L.tabs = take(kTabBytes);
   L.cinst = take(ninst > 1 ? (size_t)capacity * 4 : 0);
@@ -269,10 +270,7 @@ wbrw_status resample_from_arrays(wbrw_ctx* c) {
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
     WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
-    for (int s = 0; s < 2; ++s) {
-      WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
-      WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
-    }
+    WBRW_TRY(c, launch_zero(c, c->boot_ucnt, (size_t)2 * c->nh * 4), "zero");
     WBRW_TRY(c, d->bin(c, DST_BIN2, c->buf.grid, 1), "records");
     WBRW_TRY(c, launch_boot(c, 0), "bootstrap");
   }
@@ -297,10 +295,7 @@ wbrw_status enqueue_period(wbrw_ctx* c, int src, int l0, int L, long long regen_
   } else {
     WBRW_TRY(c, launch_setup(c, SETUP_BOOT, 0, 0), "setup");
     WBRW_TRY(c, launch_zero(c, c->rcnt, (size_t)c->nseg * sizeof(unsigned)), "zero");
-    for (int s = 0; s < 2; ++s) {
-      WBRW_TRY(c, launch_zero(c, c->boot_keep[s], (size_t)c->nh * 4), "zero");
-      WBRW_TRY(c, launch_zero(c, c->boot_res[s], (size_t)c->nh * 8), "zero");
-    }
+    WBRW_TRY(c, launch_zero(c, c->boot_ucnt, (size_t)2 * c->nh * 4), "zero");
   }
   // the regeneration of the previous histogram uses its own epoch's ids
   const long long keep_epoch = c->epoch;
@@ -701,6 +696,7 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->boot_keep[1] = (int*)(base + L.keep1);
   c->boot_res[0] = (unsigned long long*)(base + L.res0);
   c->boot_res[1] = (unsigned long long*)(base + L.res1);
+  c->boot_ucnt = (int*)(base + L.ucnt);
   c->boot_guide = (int*)(base + L.guide);
   c->inst_tab = base + L.tabs;
   c->inst_slot = (unsigned long long*)(base + L.tabs + kTabSlotOff);

@@ -291,6 +291,85 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 // ---------------------------------------------------------------------------
 constexpr int kBootChunk = 1024;  // records per work item of k_boot_bin
 
+// The share q_i = a_i N^s / W^s of a record of side s (Alg. 2 on S^s), split
+// into its integer part and its Q0.32 residual.  fx (FP32 runs): in fixed
+// point, a_i M / 2^64 with M = floor(N 2^64 / W) from one FP64 division, so
+// that no record needs FP64 arithmetic (slow on this GPU); the integer part
+// and the residual agree with the FP64 form to about one unit of 2^-32 (the
+// FP32 contract is in law).  FP64 runs keep the FP64 form, which the oracle
+// follows.  The two sides' constants are separate scalars, chosen by a
+// select: an array indexed by the side would live in local memory.
+struct BootShare {
+  double ratio0, ratio1;
+  unsigned long long mx0, mx1;
+  bool fx0, fx1;
+
+  __device__ void init(const Counters* c, int fx) {
+    ratio0 = ratio1 = 0.0;
+    mx0 = mx1 = 0;
+    fx0 = fx1 = false;
+    for (int s = 0; s < 2; ++s) {
+      const double r =
+          c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
+      unsigned long long m_s = 0;
+      bool f_s = false;
+      if (fx && c->boot_n[s] < c->boot_w[s]) {
+        const double m = r * 18446744073709551616.0;
+        if (m < 18446744073709551616.0) {
+          m_s = (unsigned long long)m;
+          f_s = true;
+        }
+      }
+      if (s == 0) { ratio0 = r; mx0 = m_s; fx0 = f_s; } else { ratio1 = r; mx1 = m_s; fx1 = f_s; }
+    }
+  }
+  __device__ __forceinline__ void of(uint32_t a, int side, int& kf,
+                                     unsigned long long& res) const {
+    if (side ? fx1 : fx0) {
+      const unsigned long long m = side ? mx1 : mx0;
+      kf = (int)__umul64hi((unsigned long long)a, m);  // bits 64..95 of the 96-bit a m
+      res = ((unsigned long long)a * m) >> 32;         // bits 32..63: the Q0.32 residual
+    } else {
+      const double q = __dmul_rn((double)a, side ? ratio1 : ratio0);
+      const double fl = floor(q);
+      res = (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
+      kf = (int)fl;
+    }
+  }
+};
+
+// The regenerated particles' part (weight +-1, a = 2^31, all of a side with
+// the same share): count x (integer part, residual) per side and cell,
+// written into the tallies that k_boot_bin then adds the records to.
+__global__ void __launch_bounds__(kBlock) k_boot_unit(Counters* c, const int* ucnt, long long nh,
+                                                      int* keep0, int* keep1,
+                                                      unsigned long long* res0,
+                                                      unsigned long long* res1, int fx) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  BootShare sh;
+  sh.init(c, fx);
+  int kf[2];
+  unsigned long long rs[2];
+  sh.of(2147483648u, 0, kf[0], rs[0]);
+  sh.of(2147483648u, 1, kf[1], rs[1]);
+  unsigned long long ks0 = 0, ks1 = 0;
+  for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
+       nu += (long long)gridDim.x * kBlock) {
+    const int u0 = ucnt[nu], u1 = ucnt[nh + nu];
+    keep0[nu] = u0 * kf[0];
+    keep1[nu] = u1 * kf[1];
+    res0[nu] = (unsigned long long)u0 * rs[0];
+    res1[nu] = (unsigned long long)u1 * rs[1];
+    ks0 += (unsigned long long)u0 * (unsigned long long)kf[0];
+    ks1 += (unsigned long long)u1 * (unsigned long long)kf[1];
+  }
+  for (int s = 0; s < 2; ++s) {
+    unsigned long long t;
+    block_exscan(s ? ks1 : ks0, red, t);
+    if (threadIdx.x == 0 && t) atomicAdd(&c->boot_keep[s], t);
+  }
+}
+
 __global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint32_t* rec_cell,
                                                      const uint32_t* rec_a, const unsigned* rcnt,
                                                      int nseg, long long rseg,
@@ -298,30 +377,8 @@ __global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint3
                                                      unsigned long long* res0,
                                                      unsigned long long* res1, int fx) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
-  // fx (FP32 runs): q_i in fixed point, a_i M / 2^64 with M = floor(N 2^64 / W)
-  // from one FP64 division, so that no record needs FP64 arithmetic (slow on
-  // this GPU); the integer part and the Q0.32 residual agree with the FP64
-  // form to about one unit of 2^-32 (the FP32 contract is in law).  FP64 runs
-  // keep the FP64 form, which the oracle follows.  The two sides' constants
-  // are separate scalars, chosen per record by a select: an array indexed by
-  // the record's side would live in local memory.
-  double ratio0 = 0.0, ratio1 = 0.0;
-  unsigned long long mx0 = 0, mx1 = 0;
-  bool fx0 = false, fx1 = false;
-  for (int s = 0; s < 2; ++s) {
-    const double r =
-        c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
-    unsigned long long m_s = 0;
-    bool f_s = false;
-    if (fx && c->boot_n[s] < c->boot_w[s]) {
-      const double m = r * 18446744073709551616.0;
-      if (m < 18446744073709551616.0) {
-        m_s = (unsigned long long)m;
-        f_s = true;
-      }
-    }
-    if (s == 0) { ratio0 = r; mx0 = m_s; fx0 = f_s; } else { ratio1 = r; mx1 = m_s; fx1 = f_s; }
-  }
+  BootShare sh;
+  sh.init(c, fx);
   unsigned long long ks0 = 0, ks1 = 0;
   // records sit in one segment per producer warp; a warp takes a segment
   const int lane = threadIdx.x & 31;
@@ -351,16 +408,7 @@ __global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint3
         const uint32_t rc = rcs[i];
         const int side = rc >> 31;
         const uint32_t cell = rc & 0x7FFFFFFFu;
-        if (side ? fx1 : fx0) {
-          const unsigned long long a = ras[i], m = side ? mx1 : mx0;
-          kf = (int)__umul64hi(a, m);  // bits 64..95 of the 96-bit a m
-          res = (a * m) >> 32;         // bits 32..63: the Q0.32 residual
-        } else {
-          const double q = __dmul_rn((double)ras[i], side ? ratio1 : ratio0);
-          const double fl = floor(q);
-          res = (unsigned long long)floor(__dmul_rn(__dsub_rn(q, fl), 4294967296.0));
-          kf = (int)fl;
-        }
+        sh.of(ras[i], side, kf, res);
         key = 2u * cell + (unsigned)side;
       }
       const unsigned prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
@@ -760,6 +808,11 @@ cudaError_t launch_boot(Ctx* c, int epoch_delta) {
   const long long nh = c->nh, nb = c->scan_blocks;
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
   const int g = grid_cap(c, 8);
+  const int fx = c->cfg.precision == WBRW_FP32;
+  k_boot_unit<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->cnt, c->boot_ucnt, nh, c->boot_keep[0],
+                                                        c->boot_keep[1], c->boot_res[0],
+                                                        c->boot_res[1], fx);
+  c->launches++;
   k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg,
                                           c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
                                           c->boot_res[1], c->cfg.precision == WBRW_FP32);

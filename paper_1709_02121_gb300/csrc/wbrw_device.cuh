@@ -287,6 +287,7 @@ struct KP {
   uint32_t* rec_a;
   unsigned* rcnt;
   unsigned rseg;
+  int* ucnt;                 // sp2: unit-weight particles per (side, cell), side-major
   int* grid;
   long long* wsum;
   const uint32_t* nz_cell;
@@ -334,11 +335,16 @@ constexpr int kWarps = kBlock / 32;
 constexpr int kStack = 32;    // pending offspring frames per thread (drain)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Per-thread tallies, reduced once per block at the end of a kernel.
+// Per-thread tallies, reduced once per block at the end of a kernel.  The
+// counts are 32-bit: a thread touches at most (its share of the capacity) x
+// (the intervals of one flight, <= kMaxChunk) particle-steps in a launch,
+// below 2^32 for every capacity the library accepts; the Q1.31 weight sums
+// need 64 bits.
 struct Acc {
-  unsigned long long psteps, events, kill_p, kill_m, out_p, out_m;
-  unsigned long long n_plus, n_minus, w_plus, w_minus;
-  unsigned long long cand;  // first events of candidate intervals (k_event)
+  unsigned psteps, events, kill_p, kill_m, out_p, out_m;
+  unsigned n_plus, n_minus;
+  unsigned long long w_plus, w_minus;
+  unsigned cand;  // first events of candidate intervals (k_event)
   __device__ void zero() {
     psteps = events = kill_p = kill_m = out_p = out_m = 0;
     n_plus = n_minus = w_plus = w_minus = 0;
@@ -854,7 +860,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
     // inside the chunk; then the sink at the end of the chunk
     const int n = p.L - l - 1;
     if (n > 0) {
-      acc.psteps += (unsigned long long)n;
+      acc.psteps += (unsigned)n;
       const float q = fmaxf(floorf(t_next * p.inv_dt), 1.0f);
       const int c = q < (float)(n + 1) ? l + (int)q : p.L;
       if (c < p.L) {
@@ -1249,7 +1255,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
       const int c = ls + geo_gap(m, ip.ilq, p.L - ls);
       if (c < p.L) mask = 1u << (c - p.l0);
     }
-    acc.psteps += (unsigned long long)(p.L - ls);
+    acc.psteps += (unsigned)(p.L - ls);
   }
 
   // ---- the warp's candidate entries.  Entry j of the warp (lanes in
@@ -1424,6 +1430,27 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
                   (unsigned long long)wsum_units<P>(w));
       else tally_out<P>(p, acc, w, x, k);
     }
+  } else if constexpr (SRC == SRC_REGEN) {
+    // DST_BIN2, regenerated particles: weight +-1, so every one has the same
+    // share q = 2^31 N/W of its side (Alg. 2); they are counted per side and
+    // cell instead of recorded (lanes with the same cell and side add once),
+    // and the bootstrap adds count x (that share's floor and residual) to
+    // the cell, the same integer sums as one record each
+    unsigned key = ~0u;
+    if (act) {
+      int cell;
+      if (cell_of<P>(p, x, k, cell)) {
+        const bool neg = w < (T)0;
+        key = 2u * (unsigned)(cbase + cell) + (neg ? 1u : 0u);
+        if (!neg) { ++acc.n_plus; acc.w_plus += 2147483648ull; }
+        else { ++acc.n_minus; acc.w_minus += 2147483648ull; }
+      } else {
+        tally_out<P>(p, acc, w, x, k);
+      }
+    }
+    const unsigned grp = __match_any_sync(kFull, key);
+    if (key != ~0u && lane == __ffs(grp) - 1)
+      atomicAdd(p.ucnt + (size_t)(key & 1u) * (size_t)p.nhi + (key >> 1), __popc(grp));
   } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
     int cell = -1;
     if (act) {
@@ -1691,9 +1718,15 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
   WarpCounts& wc = s_wc[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  load_counts(p, wc, 1);
   const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  // a block with no candidate in any of its warps' segments leaves at once
+  // (the late rounds of a period hold few): it would append nothing, and its
+  // tallies and queue counts would stay as they are
+  bool any = false;
+  for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) any |= p.ecnt_in[sg] != 0u;
+  if (!__syncthreads_or(any)) return;
+  load_counts(p, wc, 1);
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
   // FP32 2D: the accepted events of the warp's tiles wait in a per-warp
   // buffer and their pairs are made 32 at a time, so that every lane has one
@@ -1795,11 +1828,14 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
   WarpCounts& wc = s_wc[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  load_counts(p, wc, level + 1);
   const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
+  bool any = false;  // a block with nothing to do leaves at once
+  for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) any |= in_cnt[sg] != 0u;
+  if (!__syncthreads_or(any)) return;
+  load_counts(p, wc, level + 1);
   auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, level + 1, ch); };
   for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) {
     const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
@@ -1837,11 +1873,14 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p
   WarpCounts& wc = s_wc[threadIdx.x >> 5];
   Acc acc;
   acc.zero();
-  load_counts(p, wc, 0);
   const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   const SEntry<P>* in = ((level & 1) ? p.dq[1] : p.dq[0]);
   const unsigned* in_cnt = p.dcnt + (long long)level * p.nseg;
+  bool any = false;  // a block with nothing to do leaves at once
+  for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) any |= in_cnt[sg] != 0u;
+  if (!__syncthreads_or(any)) return;
+  load_counts(p, wc, 0);
   for (unsigned long long sg = g; sg < (unsigned)p.nseg; sg += nwarps) {
     const unsigned n = min(in_cnt[sg], (unsigned)p.dseg);
     for (unsigned i = lane; i < n; i += 32)
@@ -2004,6 +2043,7 @@ KP<P> make_kp(const Ctx* c) {
   p.rec_a = c->rec_a;
   p.rcnt = c->cfg.strategy == WBRW_SP2_BOOTSTRAP ? c->rcnt : nullptr;
   p.rseg = (unsigned)c->rseg;
+  p.ucnt = c->boot_ucnt;
   p.grid = c->buf.grid;
   p.wsum = c->tmp_wsum;
   p.rec_cell = c->rec_cell;

@@ -208,6 +208,7 @@ struct Ctx {
   long long rec_cap;
   int* boot_keep[2];
   unsigned long long* boot_res[2];
+  int* boot_ucnt;     // sp2: regenerated (unit-weight) particles per side and cell, 2 x nh
   int* boot_guide;    // sp2: 2 x (kGuide + 1) guide-table entries of the draws
   // state
   int state;  // 0 = particles in the arrays, 1 = histogram (grid + nz lists)

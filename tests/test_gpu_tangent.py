@@ -155,3 +155,55 @@ def test_autograd_function_backward_is_the_tangent_replay():
     assert np.array_equal(T.detach().numpy(), T2)
     assert np.array_equal(H.grad.numpy(), np.array([1.0, 2.0]) * g[:, 0])
     assert np.array_equal(w.grad.numpy(), np.array([1.0, 2.0]) * g[:, 1])
+
+
+@pytest.mark.parametrize("param, theta, reps", [("H", (1.0, 1.0), 48), ("w", (1.0, 0.5), 192)])
+def test_lr_gradient_agrees_with_crn_central_differences(param, theta, reps):
+    """FP64, central differences with delta = 1e-3 and common random numbers.
+
+    Instance i of a batch draws from the streams of instance salt i whatever
+    its parameters, so replica i at theta - delta, theta and theta + delta
+    shares every random number (gamma0 is held at 2, so the candidate clock
+    does not move either).  Per replica, FD_i = (T(theta + delta) -
+    T(theta - delta)) / (2 delta) and the likelihood-ratio estimate LR_i of
+    the same replica are both unbiased for dT/dtheta (FD up to delta^2), and
+    their paired difference must average to zero within its standard error.
+    A change of theta flips an acceptance decision with probability of order
+    delta per event, so Var(FD_i) grows like 1/delta; resampling would re-key
+    the particles of every cell after the first changed count (ids are
+    slots in cell order) and break the common numbers, so the runs go to
+    t = 2 without resampling and are binned once at the end.  A change of w
+    moves every kick and so flips more decisions than a change of H: its
+    differences are noisier per replica, and 192 replicas resolve them."""
+    from paper_1709_02121_gb300 import Batch
+    H, w = theta
+    delta = 1e-3
+    n = 40_000
+    wl = workloads.scaled(workloads.COLLISION_2D, precision="fp64", gamma0=2.0, H=H, w=w,
+                          resample_every=0, tangent=False)
+
+    def batch(h, v, tangent):
+        insts = [dict(H=h, w=v, x0=wl["x0"], sigma_x=wl["sigma_x"], k0=wl["k0"], n_init=n,
+                      n_alpha=n, gamma0=2.0)] * reps
+        b = Batch(dict(wl, tangent=tangent, tquantum=1.0), insts, reps * n * 16)
+        b.run(20)
+        b.annihilate()
+        T = b.transmissions()
+        g = b.transmission_gradients() if tangent else None
+        b.close()
+        return T, g
+
+    sh = {"H": (delta, 0.0), "w": (0.0, delta)}[param]
+    Tp, _ = batch(H + sh[0], w + sh[1], False)
+    Tm, _ = batch(H - sh[0], w - sh[1], False)
+    T0, g = batch(H, w, True)
+    lr = g[:, 0 if param == "H" else 1]
+    fd = (Tp - Tm) / (2 * delta)
+    d = fd - lr
+    se_d = d.std(ddof=1) / np.sqrt(reps)
+    se_lr = lr.std(ddof=1) / np.sqrt(reps)
+    print("\nd T/d%s: LR %.4f (SE %.4f), FD %.4f (SE %.4f), paired difference %.4f (SE %.4f)"
+          % (param, lr.mean(), se_lr, fd.mean(), fd.std(ddof=1) / np.sqrt(reps), d.mean(),
+             se_d))
+    assert abs(lr.mean()) > 5 * se_lr                  # a derivative well above the noise
+    assert abs(d.mean()) < 4.0 * se_d + 0.01 * abs(lr.mean()), (lr.mean(), fd.mean(), se_d)
