@@ -223,6 +223,7 @@ wbrw_status cuda_check(wbrw_ctx* c, cudaError_t e, const char* what) {
 }
 
 const Driver* drv(const wbrw_ctx* c) {
+  if (c->lean) return driver_fp32_lean();
   return drv_for(c->cfg.precision, c->cfg.dim, c->cfg.tangent);
 }
 
@@ -705,6 +706,8 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->cinst = ninst > 1 ? (unsigned*)(base + L.cinst) : nullptr;
   c->obs_red = (long long*)(base + L.obs_red);
   c->ncomp = ncomp;
+  c->lean = c->cfg.precision == WBRW_FP32 && c->cfg.dim == 2 && !c->cfg.tangent &&
+            c->ninst == 1 && ncomp == 0 && !c->buf.event_log;
   c->comp_tab = base + L.tabs + kTabCompOff;
   if (ncomp > 0 && cudaMemcpyAsync(c->comp_tab, comps, (size_t)ncomp * sizeof(Comp),
                                    cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {

@@ -138,10 +138,16 @@ struct F32 {
 //
 // TGm: the tangent mode of the 2D model: every particle also carries its
 // likelihood-ratio tangent weight (d/dH, d/dw), see do_event.
-template <class F, int Dm, bool TGm = false>
+//
+// LEANm: a run with one instance, the static potential and no event log.
+// The kernels then leave out the batch decode, the time-dependent
+// components and the log writes, and their registers (the results are
+// those of the general kernels, which serve every other run).
+template <class F, int Dm, bool TGm = false, bool LEANm = false>
 struct PD : F {
   static constexpr int D = Dm;
   static constexpr bool TG = TGm;
+  static constexpr bool LEAN = LEANm;
 };
 using P64 = PD<F64, 1>;
 using P32 = PD<F32, 1>;
@@ -149,6 +155,7 @@ using Q64 = PD<F64, 2>;
 using Q32 = PD<F32, 2>;
 using P64G = PD<F64, 1, true>;
 using P32G = PD<F32, 1, true>;
+using P32L = PD<F32, 1, false, true>;
 
 // The tangent weight tau = s S (sign times lineage score) of a particle, in
 // the run's precision (FP64 for the parity path; FP32 runs keep it in FP32,
@@ -179,6 +186,7 @@ struct FEntry : TanOf<P> {  // a particle at the start of interval l (offspring
 };
 
 static_assert(sizeof(FEntry<P64>) == 40 && sizeof(FEntry<P32>) == 24, "FEntry layout");
+static_assert(sizeof(FEntry<P32L>) == sizeof(FEntry<P32>), "FEntry layout");
 static_assert(sizeof(FEntry<Q32>) == 32, "FEntry layout");
 static_assert(sizeof(FEntry<P32G>) == 32 && sizeof(FEntry<P64G>) == 56, "FEntry layout");
 
@@ -327,7 +335,7 @@ __device__ __forceinline__ KP<P> with_period(const KP<P>& q) {
 // parameters (constant bank), a batch from its table in global memory.
 template <class P>
 __device__ __forceinline__ Inst<typename P::T> inst_of(const KP<P>& p, int i) {
-  if (p.ninst > 1) return p.inst[i];
+  if (!P::LEAN && p.ninst > 1) return p.inst[i];
   return p.inst0;
 }
 
@@ -751,7 +759,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
       p.tan[p.capacity + slot] = tau.tw;
     }
     p.cpid[slot - p.cnt->n_base] = pid;
-    if (p.ninst > 1) p.cinst[slot - p.cnt->n_base] = (unsigned)inst;
+    if (!P::LEAN && p.ninst > 1) p.cinst[slot - p.cnt->n_base] = (unsigned)inst;
   }
 }
 
@@ -780,6 +788,7 @@ struct SEntry : TanOf<P> {  // a deferred segment, with the time and index of it
 };
 
 static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
+static_assert(sizeof(SEntry<P32L>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<Q32>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<P32G>) == 64, "SEntry layout");
 
@@ -990,7 +999,7 @@ __device__ __forceinline__ bool event_decide(const KP<P>& p, const Inst<typename
     T z, sg, u3;
     bool flip;
     Draw<P>::event(p, ip, pid, l, j, root, st, z, u3, gap);
-    if (p.ncomp == 0) {  // the static barrier: kick, |sin| ratio, orientation
+    if (P::LEAN || p.ncomp == 0) {  // the static barrier: kick, |sin| ratio, orientation
       kap = P::mul(ip.sig_k, z);
       sg = P::sn(P::mul(P::mul((T)2, P::sub(xe.c[0], ip.xc)), kap));
       fac = P::mul(ip.cacc, (T)fabs(sg));
@@ -1065,7 +1074,7 @@ __device__ __forceinline__ void event_pair(const KP<P>& p, const Inst<typename P
   ++acc.events;
   if (kill_p) { if (wc_ > (T)0) ++acc.kill_p; else if (wc_ < (T)0) ++acc.kill_m; }
   if (kill_m) { if (-wc_ > (T)0) ++acc.kill_p; else if (-wc_ < (T)0) ++acc.kill_m; }
-  if (p.log) {
+  if (!P::LEAN && p.log) {
     const unsigned long long idx = atomicAdd(&p.cnt->log_len, 1ull);
     if (idx < (unsigned long long)p.log_cap) {
       wbrw_event ev;
@@ -1177,7 +1186,7 @@ __device__ __forceinline__ typename P::T in_cell(typename P::T v, typename P::T 
 // is <= slot (empty instances share their start with the next one).
 template <class P>
 __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long slot) {
-  if (p.ninst <= 1) return 0;
+  if (P::LEAN || p.ninst <= 1) return 0;
   int lo = 0, hi = p.ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -1384,7 +1393,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
             p.tan[p.capacity + off] = tau.tw;
           }
           p.cpid[off - p.cnt->n_base] = pid;
-          if (p.ninst > 1) p.cinst[off - p.cnt->n_base] = (unsigned)inst;
+          if (!P::LEAN && p.ninst > 1) p.cinst[off - p.cnt->n_base] = (unsigned)inst;
         }
       }
     }
@@ -1582,14 +1591,14 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
         }
         if (act) {
           int cell = (int)(cwl & 0x7FFFFFFFu);
-          if (p.ninst > 1) {
+          if (!P::LEAN && p.ninst > 1) {
             inst = (int)((unsigned)cell / (unsigned)p.nhi);
             cell -= inst * p.nhi;
           }
           // tangent particles: ids (epoch << 40) | (instance << 32) | 2^31 | j
           const unsigned long long tag = TR ? 0x80000000ull : 0ull;
           pid = p.regen_base | tag | slot;
-          if (p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | tag | (slot - islot[inst]);
+          if (!P::LEAN && p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | tag | (slot - islot[inst]);
           const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
           if constexpr (P::D == 1) {
             int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
@@ -1637,13 +1646,13 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> 
           w = p.w ? p.w[slot] : (T)p.s[slot];
           if (slot < n_base) {
             pid = base_pid + slot;
-            if (p.ninst > 1) {
+            if (!P::LEAN && p.ninst > 1) {
               inst = base_instance(p, slot);
               pid = base_pid + ((unsigned long long)inst << 32) + (slot - p.inst_slot[inst]);
             }
           } else {
             pid = p.cpid[slot - n_base];
-            if (p.ninst > 1) inst = (int)p.cinst[slot - n_base];
+            if (!P::LEAN && p.ninst > 1) inst = (int)p.cinst[slot - n_base];
           }
         }
       }
@@ -1946,7 +1955,7 @@ __global__ void __launch_bounds__(kBlock) k_pids(const KP<P> p, unsigned long lo
       pid = bp + ((unsigned long long)inst << 32) + (i - p.inst_slot[inst]);
     } else {
       pid = p.cpid[i - nb];
-      if (p.ninst > 1) inst = (int)p.cinst[i - nb];
+      if (!P::LEAN && p.ninst > 1) inst = (int)p.cinst[i - nb];
     }
     if (out) out[i] = pid;
     if (inst_out) inst_out[i] = (unsigned)inst;

@@ -1,0 +1,7 @@
+// FP32 instantiation for runs with one instance, the static potential and no
+// event log: the production path of the 2D workloads.
+#include "wbrw_device.cuh"
+
+namespace wbrw {
+const Driver* driver_fp32_lean() { return DriverImpl<P32L>::get(); }
+}  // namespace wbrw
