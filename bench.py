@@ -70,6 +70,8 @@ def parse(argv=None):
                     help="launch every period kernel by kernel instead of replaying a CUDA graph")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape instead of autotuning it after warm-up")
+    ap.add_argument("--tuning", default="",
+                    help="BLOCKS_PER_SM,EVENT_PASSES: this launch shape instead of autotuning")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
@@ -319,9 +321,17 @@ PHILOX_FIRST = {"fp32": (1, 0), "fp32_4d": (1, 0), "fp64": (1, 1), "fp64_4d": (2
 # (smsp__thread_inst_executed.sum / calls; profiles/k_philox_chain_311296x4096.md).
 INST_PER_PHILOX = 42.0
 SMS, INT32_LANES = 152, 64
-# DRAM bytes per unit measured by ncu (profiles/), or None
-TRAFFIC_PER_PSTEP = {"fp32": 0.577, "fp64": None, "fp32_4d": 1.11, "fp64_4d": None}
-TRAFFIC_PER_CANDIDATE = {"fp32": 31.2, "fp64": None, "fp32_4d": 48.6, "fp64_4d": None}
+# DRAM bytes per unit measured by ncu for the plain sp1 workloads
+# (profiles/); None where no capture of the current kernels exists (other
+# strategies, batches, FP64)
+TRAFFIC_PER_PSTEP = {"fp32": 0.562, "fp64": None, "fp32_4d": 1.18, "fp64_4d": None}
+TRAFFIC_PER_CANDIDATE = {"fp32": 31.0, "fp64": None, "fp32_4d": 49.7, "fp64_4d": None}
+
+
+def _traffic(table, wl):
+    if wl.get("strategy", "sp1") != "sp1" or "instances" in wl:
+        return None
+    return table.get(_key(wl))
 # Algorithmic HBM bytes per particle-step of the whole step if every interval
 # moved the particle state through HBM (x, k read and x written, the
 # offspring's share and the resampling amortised over the period): FP32 2D
@@ -358,7 +368,7 @@ def roofline_event(wl, ev_ms, ev_n, cand, pairs, ceiling, clk, peaks):
     peak, derived, sm_mhz = _peak(ceiling, clk, peaks)
     calls = a * cand + b * pairs
     ach = calls / (ev_ms / 1e3) / 1e9
-    tpc = TRAFFIC_PER_CANDIDATE.get(_key(wl))
+    tpc = _traffic(TRAFFIC_PER_CANDIDATE, wl)
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gcalls/s",
             "frac": ach / peak, "traffic": tpc and tpc * cand / ev_n,
             "kernel": "k_event<%s%s,bin>" % (wl["precision"],
@@ -390,7 +400,7 @@ def roofline(wl, kern_ms, kern_n, psteps_first, ceiling, clk, peaks):
     per_launch_ms = kern_ms / kern_n
     peak, derived, sm_mhz = _peak(ceiling, clk, peaks)
     ach = per_pstep * (psteps_first / kern_n) / (per_launch_ms / 1e3) / 1e9
-    tpp = TRAFFIC_PER_PSTEP.get(_key(wl))
+    tpp = _traffic(TRAFFIC_PER_PSTEP, wl)
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gcalls/s",
             "frac": ach / peak, "traffic": tpp and tpp * psteps_first / kern_n,
             "kernel": "k_flight<%s%s,regen,bin>" % (wl["precision"],
@@ -460,6 +470,10 @@ def warm_up(sim, args, P, warmup):
 def autotune(sim, args):
     """Pick the launch shape by timing one period under each (results do not
     depend on it); the run continues from where it was."""
+    if getattr(args, "tuning", ""):
+        b, p = (int(v) for v in args.tuning.split(","))
+        b, p = sim.tuning(b, p)
+        return {"blocks_per_sm": b, "event_passes": p, "autotuned": False}
     if args.no_autotune:
         b, p = sim.tuning()
         return {"blocks_per_sm": b, "event_passes": p, "autotuned": False}

@@ -344,16 +344,25 @@ wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
 /* Launch shape.  Neither knob changes any result (random numbers are keyed
  * by particle and interval, and every count is an integer sum), only speed:
  *   blocks_per_sm : resident 256-thread blocks per SM of the particle
- *                   kernels, 1..WBRW_TUNE_BLOCKS_PER_SM_MAX (default the
- *                   maximum).  Each warp owns one segment of every queue, so
- *                   this also sets the queue segmentation.
+ *                   kernels, from 1 to the context's maximum (default that
+ *                   maximum): 4 for FP32 contexts with one instance, the
+ *                   static potential and no event log, and for the FP32 4D
+ *                   model, whose kernels are built for 64 registers; 3 for
+ *                   the others (WBRW_TUNE_BLOCKS_PER_SM_MAX is the largest).
+ *                   Each warp owns one segment of every queue, so this also
+ *                   sets the queue segmentation.
  *   event_passes  : offspring with further events in their interval are
  *                   processed one event per lockstep pass for this many
  *                   passes (0..WBRW_TUNE_PASSES_MAX, default 3); what remains
- *                   is finished by one recursive pass.
+ *                   is finished by one recursive pass.  The contexts with
+ *                   four blocks per SM in 2D (FP32, one instance, static
+ *                   potential, no event log) finish every such segment in
+ *                   lockstep passes inside the event kernel itself, so there
+ *                   event_passes changes nothing.
  * wbrw_set_tuning takes effect from the next call and releases captured
- * graphs; out-of-range values give WBRW_ERR_ARG. */
-#define WBRW_TUNE_BLOCKS_PER_SM_MAX 3
+ * graphs; out-of-range values (including blocks_per_sm above the context's
+ * maximum) give WBRW_ERR_ARG. */
+#define WBRW_TUNE_BLOCKS_PER_SM_MAX 4
 #define WBRW_TUNE_PASSES_MAX 6
 typedef struct {
   int blocks_per_sm;
@@ -369,7 +378,9 @@ wbrw_status wbrw_set_tuning(wbrw_ctx* ctx, const wbrw_tuning* tuning);
  * receives WBRW_TUNE_BLOCKS_PER_SM_MAX x (WBRW_TUNE_PASSES_MAX + 1) times in
  * milliseconds, entry (b - 1) * (WBRW_TUNE_PASSES_MAX + 1) + p for
  * blocks_per_sm = b and event_passes = p, each the fastest of its trials
- * (negative if that setting hit a capacity limit).  Every trial starts from
+ * (negative if that setting hit a capacity limit, lies above the
+ * context's maximum blocks_per_sm, or has event_passes > 0 in a context
+ * where event_passes changes nothing, which is timed only at 0).  Every trial starts from
  * the same histogram, and the context is put back afterwards: state, counters
  * and interval index are as before the call.  Needs the state right after a
  * resampling (as wbrw_checkpoint) and resample_every > 0; the event log is

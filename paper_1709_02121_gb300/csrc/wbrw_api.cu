@@ -677,7 +677,10 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->dcap = L.dcap;
   c->rec_cap = L.rec_cap;
   c->passes = 3;
-  set_shape(c, kMaxBlocksPerSm);
+  c->lean = c->cfg.precision == WBRW_FP32 && c->cfg.dim == 2 && !c->cfg.tangent &&
+            c->ninst == 1 && ncomp == 0 && !c->buf.event_log;
+  c->max_bps = drv(c)->max_bps;
+  set_shape(c, c->max_bps);
   c->nz_cell = (uint32_t*)(base + L.nz_cell);
   c->nz_start = (unsigned long long*)(base + L.nz_start);
   c->tile_nz = (uint32_t*)(base + L.tile_nz);
@@ -706,8 +709,6 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->cinst = ninst > 1 ? (unsigned*)(base + L.cinst) : nullptr;
   c->obs_red = (long long*)(base + L.obs_red);
   c->ncomp = ncomp;
-  c->lean = c->cfg.precision == WBRW_FP32 && c->cfg.dim == 2 && !c->cfg.tangent &&
-            c->ninst == 1 && ncomp == 0 && !c->buf.event_log;
   c->comp_tab = base + L.tabs + kTabCompOff;
   if (ncomp > 0 && cudaMemcpyAsync(c->comp_tab, comps, (size_t)ncomp * sizeof(Comp),
                                    cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
@@ -1159,7 +1160,7 @@ wbrw_status wbrw_get_tuning(wbrw_ctx* c, wbrw_tuning* out) {
 wbrw_status wbrw_set_tuning(wbrw_ctx* c, const wbrw_tuning* t) {
   if (!c || !t) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
-  if (t->blocks_per_sm < 1 || t->blocks_per_sm > kMaxBlocksPerSm || t->event_passes < 0 ||
+  if (t->blocks_per_sm < 1 || t->blocks_per_sm > c->max_bps || t->event_passes < 0 ||
       t->event_passes > kMaxPasses)
     return seterr(c, WBRW_ERR_ARG, "tuning out of range");
   if (t->blocks_per_sm != c->bps || t->event_passes != c->passes) {
@@ -1217,8 +1218,13 @@ wbrw_status wbrw_autotune(wbrw_ctx* c, int trials, wbrw_tuning* best, double* ms
   double best_ms = -1;
   int best_b = bps0, best_p = passes0;
   wbrw_status st = WBRW_OK;
-  for (int b = 1; b <= kMaxBlocksPerSm && st == WBRW_OK; ++b) {
-    for (int pz = 0; pz <= kMaxPasses && st == WBRW_OK; ++pz) {
+  if (ms_table)  // shapes beyond what this context's kernels are built for
+    for (int i = 0; i < kMaxBlocksPerSm * (kMaxPasses + 1); ++i) ms_table[i] = -1.0;
+  // the lean kernels finish deferred segments inside the event kernel:
+  // event_passes changes nothing there, and only 0 is timed
+  const int max_pz = c->lean ? 0 : kMaxPasses;
+  for (int b = 1; b <= c->max_bps && st == WBRW_OK; ++b) {
+    for (int pz = 0; pz <= max_pz && st == WBRW_OK; ++pz) {
       set_shape(c, b);
       c->passes = pz;
       double t_min = -1;

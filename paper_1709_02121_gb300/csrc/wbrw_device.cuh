@@ -157,6 +157,21 @@ using P64G = PD<F64, 1, true>;
 using P32G = PD<F32, 1, true>;
 using P32L = PD<F32, 1, false, true>;
 
+// Resident 256-thread blocks per SM a queue kernel is built for (its launch
+// bound).  The lean FP32 kernels and the FP32 4D kernels fit 64 registers,
+// i.e. four blocks, without spilling or with little; the sp2 sink, the FP64,
+// tangent and general FP32 kernels keep 80 registers and three blocks, which
+// measured faster for them than four with spills.
+template <class P, int DST>
+constexpr int max_blocks() {
+  return (!P::is64 && !P::TG && (P::LEAN || P::D == 2) && DST != DST_BIN2) ? 4 : 3;
+}
+template <class P>
+constexpr int max_blocks_model() {
+  return (!P::is64 && !P::TG && (P::LEAN || P::D == 2)) ? 4 : 3;
+}
+static_assert(max_blocks_model<P32L>() <= kMaxBlocksPerSm, "tuning range");
+
 // The tangent weight tau = s S (sign times lineage score) of a particle, in
 // the run's precision (FP64 for the parity path; FP32 runs keep it in FP32,
 // since FP64 arithmetic is slow on this GPU); an empty base outside the
@@ -1484,7 +1499,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
 }
 
 template <class P, int SRC, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_flight(const KP<P> p_) {
+__global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_flight(const KP<P> p_) {
   const KP<P> p = with_period(p_);
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
@@ -1718,7 +1733,7 @@ __device__ __forceinline__ void copy_entry_async(FEntry<P>* dst, const FEntry<P>
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p_) {
+__global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_event(const KP<P> p_) {
   const KP<P> p = with_period(p_);
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
@@ -1818,17 +1833,55 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_event(const KP<P> p
     cp_async_wait<0>();
   }
   if constexpr (CMP) make_pairs(1u);
+  // so far the warp has made only first events' pairs
+  const unsigned first_pairs = acc.events;
+  if constexpr (P::LEAN) {
+    // The lean kernels finish their warp's deferred segments here instead of
+    // in launches of their own: one event per lane per pass (Alg. 1 item 3,
+    // offspring born inside the interval included), a segment with another
+    // event in its interval appended again to the same list, until the list
+    // is used up.  Its count is then zero for the launches that follow.
+    const SEntry<P>* dl = p.dq[1] + (size_t)g * p.dseg;
+    unsigned rd = 0;
+    for (;;) {
+      __syncwarp();
+      const unsigned end = min(wc.d, p.dseg);
+      if (rd >= end || g >= (unsigned)p.nseg) break;
+      const unsigned i = rd + lane;
+      if (i < end) {
+        SEntry<P> s = dl[i];
+        const unsigned j = s.j & ~kRootFlag;
+        const int l = ent_l(s.l), inst = ent_inst(s.l);
+        const Inst<T> ip = inst_of(p, inst);
+        const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
+                                       l, j, (s.j & kRootFlag) != 0u, s.t, later, s);
+        s.t = P::add(s.t, gap);
+        if (s.t < p.dt) {
+          s.j = (j + 1) | (s.j & kRootFlag);
+          defer<P>(p, wc, 1, s);
+        } else if (!(s.j & kRootFlag)) {
+          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s, s.t);
+        } else {
+          chain_next<P>(p, wc, s);
+        }
+      }
+      rd = min(rd + 32u, end);
+    }
+    __syncwarp();
+    if (lane == 0) wc.d = 0;
+    __syncwarp();
+  }
   store_counts(p, wc, 1, true, true, DST == DST_BIN2);
-  // this kernel performs only the first event of each candidate interval
-  // (later events and the offspring's own go to the deferred segments), so
-  // its pairs are the first events' pairs
+  // the first event of each candidate interval comes before the deferred
+  // segments (later events and the offspring's own), so the pairs made up to
+  // there are the first events' pairs
   block_reduce_add(red, acc.cand, &p.cnt->ledger[LG_CAND]);
-  block_reduce_add(red, acc.events, &p.cnt->ledger[LG_PAIRS0]);
+  block_reduce_add(red, first_pairs, &p.cnt->ledger[LG_PAIRS0]);
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_, int level) {
+__global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_cont(const KP<P> p_, int level) {
   const KP<P> p = with_period(p_);
   using T = typename P::T;
   __shared__ unsigned long long red[kWarps];
@@ -1874,7 +1927,7 @@ __global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_cont(const KP<P> p_
 }
 
 template <class P, int DST>
-__global__ void __launch_bounds__(kBlock, kMaxBlocksPerSm) k_drain(const KP<P> p_, int level) {
+__global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_drain(const KP<P> p_, int level) {
   const KP<P> p = with_period(p_);
   __shared__ unsigned long long red[kWarps];
   __shared__ WarpCounts s_wc[kWarps];
@@ -2069,7 +2122,7 @@ KP<P> make_kp(const Ctx* c) {
 }
 
 // Every queue kernel runs the same number of resident blocks per SM (the
-// context's tuning, at most kMaxBlocksPerSm): producer warp g owns queue
+// context's tuning, at most its model's max_blocks): producer warp g owns queue
 // segment g and consumer warp g reads it, so equal grids keep the segments
 // matched one to one (nseg of them).
 template <class K>
@@ -2104,10 +2157,13 @@ cudaError_t events(Ctx* c, const KP<P>& p, int r) {
   prof_begin(c, PROF_EVENT, r);
   k_event<P, DST><<<grid_of(c, o_ev), kBlock, 0, c->stream>>>(p);
   prof_end(c, PROF_EVENT, r);
-  for (int level = 1; level <= c->passes; ++level)
-    k_cont<P, DST><<<grid_of(c, o_cont), kBlock, 0, c->stream>>>(p, level);
-  k_drain<P, DST><<<grid_of(c, o_drain), kBlock, 0, c->stream>>>(p, c->passes + 1);
-  c->launches += c->passes + 2;
+  c->launches += 1;
+  if constexpr (!P::LEAN) {  // the lean event kernel finishes every segment itself
+    for (int level = 1; level <= c->passes; ++level)
+      k_cont<P, DST><<<grid_of(c, o_cont), kBlock, 0, c->stream>>>(p, level);
+    k_drain<P, DST><<<grid_of(c, o_drain), kBlock, 0, c->stream>>>(p, c->passes + 1);
+    c->launches += c->passes + 1;
+  }
   return cudaGetLastError();
 }
 
@@ -2395,7 +2451,8 @@ struct DriverImpl {
 
   static const Driver* get() {
     static const Driver d = {&init,   &chunk, &bin, &materialize, &pids, &tables,
-                             (int)sizeof(FEntry<P>), (int)sizeof(SEntry<P>)};
+                             (int)sizeof(FEntry<P>), (int)sizeof(SEntry<P>),
+                             max_blocks_model<P>()};
     return &d;
   }
 };

@@ -18,7 +18,8 @@ constexpr int kTabGuide = 1 << kTabGuideBits;
 constexpr int kGuideBits = 16;  // sp2 draws: guide table of 2^16 buckets per side
 constexpr int kGuide = 1 << kGuideBits;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
-constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // launch bound of the queue kernels
+constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // the largest launch bound of the
+                                                             // queue kernels (see max_blocks)
 // Deferred-segment levels of the event kernels: level 1 is fed by the first
 // event of each candidate interval, levels 1..passes are finished one event
 // per lockstep pass, level passes + 1 by the recursive drain.
@@ -189,6 +190,7 @@ struct Ctx {
   int max_chunk;      // steps per flight: about one candidate per particle
   Counters* cnt_save; // autotuner: the counters to put back
   int bps;            // tuning: resident blocks per SM of the queue kernels
+  int max_bps;        // the most the context's kernels are built for (3 or 4)
   int passes;         // tuning: lockstep event passes before the drain
   uint32_t* nz_cell;
   unsigned long long* nz_start;
@@ -269,6 +271,7 @@ struct Driver {
   // return the largest xi of each type (synchronises).
   cudaError_t (*tables)(Ctx*, const double* A_host, double* xmax_host);
   int fentry_bytes, sentry_bytes;  // queue entry sizes of this model and precision
+  int max_bps;                     // resident blocks per SM its queue kernels are built for
 };
 
 const Driver* driver_fp64();

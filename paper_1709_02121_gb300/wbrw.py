@@ -40,7 +40,7 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune",
            "wbrw_init4d", "wbrw_transmission_gradients", "wbrw_init_td",
            "wbrw_philox_chain")
-TUNE_BPS_MAX, TUNE_PASSES_MAX = 3, 6
+TUNE_BPS_MAX, TUNE_PASSES_MAX = 4, 6
 MAX_CAPACITY = 4293918720  # WBRW_MAX_CAPACITY: slots index in 32 bits
 MAX_INSTANCES = 256
 

@@ -40,6 +40,9 @@ def sim(wl, event_log=0):
 
 
 SHAPES = [(1, 0), (2, 1), (3, 3), (1, 6), (3, 6), (2, 0)]
+# FP32 runs with one instance, the static potential and no event log run
+# kernels built for four blocks per SM
+SHAPES_LEAN = SHAPES + [(4, 0), (4, 3)]
 KEYS = ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps", "live")
 
 
@@ -51,7 +54,7 @@ def test_results_do_not_depend_on_the_shape(precision):
     ref.step(4)
     xr, kr, _, _, pr = ref.particles()
     order = np.argsort(pr)
-    for b, p in SHAPES:
+    for b, p in (SHAPES_LEAN if precision == "fp32" else SHAPES):
         s = sim(wl)
         assert s.tuning(b, p) == (b, p)
         s.run(15)
@@ -73,8 +76,9 @@ def test_autotune_leaves_the_run_unchanged():
     b.run(5)
     log_len = b.counters()["log_len"]
     (bps, passes), table = b.autotune(trials=1)
-    assert table.shape == (3, 7) and np.all(table > 0)
-    assert table[bps - 1, passes] == table.min()
+    # the event log selects the general kernels: three blocks per SM at most
+    assert table.shape == (4, 7) and np.all(table[:3] > 0) and np.all(table[3] < 0)
+    assert table[bps - 1, passes] == table[:3].min()
     assert b.tuning() == (bps, passes)
     assert b.counters()["log_len"] == log_len
     a.run(10)
@@ -82,6 +86,25 @@ def test_autotune_leaves_the_run_unchanged():
     assert np.array_equal(a.grid_counts(), b.grid_counts())
     ca, cb = a.counters(), b.counters()
     for key in KEYS + ("step", "epoch", "log_len"):
+        assert ca[key] == cb[key], key
+
+
+def test_autotune_of_the_lean_kernels_leaves_the_run_unchanged():
+    wl = small(precision="fp32", n_alpha=20000)
+    a, b = sim(wl), sim(wl)
+    a.run(5)
+    b.run(5)
+    (bps, passes), table = b.autotune(trials=1)
+    # deferred segments are finished inside the event kernel: only
+    # event_passes = 0 is timed
+    assert table.shape == (4, 7) and np.all(table[:, 0] > 0) and np.all(table[:, 1:] < 0)
+    assert passes == 0 and table[bps - 1, 0] == table[:, 0].min()
+    assert b.tuning() == (bps, passes)
+    a.run(10)
+    b.run(10)
+    assert np.array_equal(a.grid_counts(), b.grid_counts())
+    ca, cb = a.counters(), b.counters()
+    for key in KEYS + ("step", "epoch"):
         assert ca[key] == cb[key], key
 
 
@@ -96,3 +119,10 @@ def test_tuning_arguments_are_checked():
     with pytest.raises(WbrwError) as ei:     # not right after a resampling
         s.autotune()
     assert ei.value.status == wbrw.ERR_STATE
+    lean = sim(small(precision="fp32"))       # built for four blocks per SM
+    assert lean.tuning() == (4, 3)
+    assert lean.tuning(4, 0) == (4, 0)
+    for bad in ((5, 0), (0, 0)):
+        with pytest.raises(WbrwError) as ei:
+            lean.tuning(*bad)
+        assert ei.value.status == wbrw.ERR_ARG
