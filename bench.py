@@ -522,11 +522,42 @@ def timed_periods(sim, P, steps, flush, local):
 
 
 def rooflines(wl, c0, c1, kern, ev, ceiling, clk, peaks):
+    d = {k: c1[k] - c0[k] for k in ("particle_steps_first", "candidates", "first_pairs")}
+    if not ev[1] and kern[1]:  # one launch per period: the first wave and the rounds fused
+        return roofline_period(wl, kern[0], kern[1], d["particle_steps_first"], d["candidates"],
+                               d["first_pairs"], ceiling, clk, peaks), None
     return dominant(
-        roofline(wl, kern[0], kern[1], c1["particle_steps_first"] - c0["particle_steps_first"],
-                 ceiling, clk, peaks),
-        roofline_event(wl, ev[0], ev[1], c1["candidates"] - c0["candidates"],
-                       c1["first_pairs"] - c0["first_pairs"], ceiling, clk, peaks))
+        roofline(wl, kern[0], kern[1], d["particle_steps_first"], ceiling, clk, peaks),
+        roofline_event(wl, ev[0], ev[1], d["candidates"], d["first_pairs"], ceiling, clk, peaks))
+
+
+def roofline_period(wl, ms, n, psteps_first, cand, pairs, ceiling, clk, peaks):
+    """Roofline of the one-launch period (k_period): the first wave and every
+    event round in one kernel.  achieved = the first wave's Philox calls
+    (PHILOX_FIRST per first-wave particle-step) + the event calls
+    (PHILOX_EVENT per candidate and per first-event pair) / the launches'
+    summed CUDA-event time; peak = the chained-Philox ceiling."""
+    if not n or ms <= 0:
+        return None
+    key = _key(wl)
+    R = wl["resample_every"]
+    base, per_interval = PHILOX_FIRST[key]
+    a, b = PHILOX_EVENT[key]
+    calls = (base + per_interval * R) / R * psteps_first + a * cand + b * pairs
+    peak, derived, sm_mhz = _peak(ceiling, clk, peaks)
+    ach = calls / (ms / 1e3) / 1e9
+    t1, t2 = _traffic(TRAFFIC_PER_PSTEP, wl), _traffic(TRAFFIC_PER_CANDIDATE, wl)
+    traffic = (t1 * psteps_first + t2 * cand) / n if (t1 is not None and t2 is not None) else None
+    return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gcalls/s",
+            "frac": ach / peak, "traffic": traffic,
+            "kernel": "k_period<%s%s>" % (wl["precision"], ",4d" if wl.get("dim", 2) == 4 else ""),
+            "launch_ms": ms / n, "launches": n, "total_ms": ms,
+            "first_wave_particle_steps_per_launch": psteps_first / n,
+            "candidates_per_launch": cand / n, "first_pairs_per_candidate": pairs / max(cand, 1),
+            "philox_calls_per_launch": calls / n, "peak_derived": derived,
+            "peak_basis": "Philox4x32-10 calls/s of the chained probe measured in this run "
+                          "(derived: %d SM x %d INT32 lanes x %.0f MHz / %.1f lane instructions "
+                          "per call)" % (SMS, INT32_LANES, sm_mhz, INST_PER_PHILOX)}
 
 
 def e2e_same_periods(sim, wl, P, steps, ckpt):

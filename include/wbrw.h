@@ -345,20 +345,22 @@ wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
  * by particle and interval, and every count is an integer sum), only speed:
  *   blocks_per_sm : resident 256-thread blocks per SM of the particle
  *                   kernels, from 1 to the context's maximum (default that
- *                   maximum): 4 for FP32 contexts with one instance, the
- *                   static potential and no event log, and for the FP32 4D
- *                   model, whose kernels are built for 64 registers; 3 for
- *                   the others (WBRW_TUNE_BLOCKS_PER_SM_MAX is the largest).
+ *                   maximum): 4 for 2D FP32 contexts (plain or batched)
+ *                   with the static potential, no event log and no
+ *                   tangents, and for the FP32 4D model, whose kernels are
+ *                   built for 64 registers; 3 for the others
+ *                   (WBRW_TUNE_BLOCKS_PER_SM_MAX is the largest).
  *                   Each warp owns one segment of every queue, so this also
  *                   sets the queue segmentation.
  *   event_passes  : offspring with further events in their interval are
  *                   processed one event per lockstep pass for this many
  *                   passes (0..WBRW_TUNE_PASSES_MAX, default 3); what remains
- *                   is finished by one recursive pass.  The contexts with
- *                   four blocks per SM in 2D (FP32, one instance, static
- *                   potential, no event log) finish every such segment in
- *                   lockstep passes inside the event kernel itself, so there
- *                   event_passes changes nothing.
+ *                   is finished by one recursive pass.  The 2D FP32
+ *                   contexts with four blocks per SM (above) finish every
+ *                   such segment in lockstep passes inside the event kernel
+ *                   itself, so there event_passes changes nothing; their sp1
+ *                   periods run in one launch (first wave and event rounds
+ *                   together), at most three blocks per SM.
  * wbrw_set_tuning takes effect from the next call and releases captured
  * graphs; out-of-range values (including blocks_per_sm above the context's
  * maximum) give WBRW_ERR_ARG. */

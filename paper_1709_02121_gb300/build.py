@@ -1,6 +1,6 @@
 """Build the CUDA library libwbrw.so for sm_103a (GB300), in tree.
 
-Ten translation units (the kernels of each precision and phase-space model,
+Eleven translation units (the kernels of each precision and phase-space model,
 the resampling kernels, the C ABI and the Philox rate probe) are compiled in parallel with nvcc and
 linked into
 ``paper_1709_02121_gb300/_build/libwbrw.so`` against the shared CUDA runtime
@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwbrw.so")
-SOURCES = ["wbrw_fp32.cu", "wbrw_fp32_lean.cu", "wbrw_fp64.cu", "wbrw_fp32_4d.cu",
+SOURCES = ["wbrw_fp32.cu", "wbrw_fp32_lean.cu", "wbrw_fp32_lean_batch.cu", "wbrw_fp64.cu",
+           "wbrw_fp32_4d.cu",
            "wbrw_fp64_4d.cu",
            "wbrw_fp32_grad.cu", "wbrw_fp64_grad.cu",
            "wbrw_common.cu", "wbrw_api.cu", "wbrw_probe.cu"]

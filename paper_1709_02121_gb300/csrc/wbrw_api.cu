@@ -223,7 +223,7 @@ wbrw_status cuda_check(wbrw_ctx* c, cudaError_t e, const char* what) {
 }
 
 const Driver* drv(const wbrw_ctx* c) {
-  if (c->lean) return driver_fp32_lean();
+  if (c->lean) return c->ninst > 1 ? driver_fp32_lean_batch() : driver_fp32_lean();
   return drv_for(c->cfg.precision, c->cfg.dim, c->cfg.tangent);
 }
 
@@ -678,7 +678,7 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->rec_cap = L.rec_cap;
   c->passes = 3;
   c->lean = c->cfg.precision == WBRW_FP32 && c->cfg.dim == 2 && !c->cfg.tangent &&
-            c->ninst == 1 && ncomp == 0 && !c->buf.event_log;
+            ncomp == 0 && !c->buf.event_log;
   c->max_bps = drv(c)->max_bps;
   set_shape(c, c->max_bps);
   c->nz_cell = (uint32_t*)(base + L.nz_cell);

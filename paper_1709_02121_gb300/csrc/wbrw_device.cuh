@@ -139,15 +139,17 @@ struct F32 {
 // TGm: the tangent mode of the 2D model: every particle also carries its
 // likelihood-ratio tangent weight (d/dH, d/dw), see do_event.
 //
-// LEANm: a run with one instance, the static potential and no event log.
-// The kernels then leave out the batch decode, the time-dependent
-// components and the log writes, and their registers (the results are
-// those of the general kernels, which serve every other run).
-template <class F, int Dm, bool TGm = false, bool LEANm = false>
+// LEANm: a run with the static potential and no event log: 1 for one
+// instance, 2 for a batch.  The kernels then leave out the time-dependent
+// components and the log writes, and for one instance the batch decode, and
+// their registers (the results are those of the general kernels, which serve
+// every other run).
+template <class F, int Dm, bool TGm = false, int LEANm = 0>
 struct PD : F {
   static constexpr int D = Dm;
   static constexpr bool TG = TGm;
-  static constexpr bool LEAN = LEANm;
+  static constexpr bool LEAN = LEANm != 0;
+  static constexpr bool SINGLE = LEANm == 1;  // one instance, known at compile time
 };
 using P64 = PD<F64, 1>;
 using P32 = PD<F32, 1>;
@@ -155,7 +157,8 @@ using Q64 = PD<F64, 2>;
 using Q32 = PD<F32, 2>;
 using P64G = PD<F64, 1, true>;
 using P32G = PD<F32, 1, true>;
-using P32L = PD<F32, 1, false, true>;
+using P32L = PD<F32, 1, false, 1>;
+using P32LB = PD<F32, 1, false, 2>;
 
 // Resident 256-thread blocks per SM a queue kernel is built for (its launch
 // bound).  The lean FP32 kernels and the FP32 4D kernels fit 64 registers,
@@ -163,12 +166,19 @@ using P32L = PD<F32, 1, false, true>;
 // tangent and general FP32 kernels keep 80 registers and three blocks, which
 // measured faster for them than four with spills.
 template <class P, int DST>
-constexpr int max_blocks() {
+__host__ __device__ constexpr int max_blocks() {
   return (!P::is64 && !P::TG && (P::LEAN || P::D == 2) && DST != DST_BIN2) ? 4 : 3;
 }
 template <class P>
-constexpr int max_blocks_model() {
+__host__ __device__ constexpr int max_blocks_model() {
   return (!P::is64 && !P::TG && (P::LEAN || P::D == 2)) ? 4 : 3;
+}
+// The lean kernels finish their deferred segments inside the event kernel
+// (k_event below) instead of in k_cont and k_drain launches (the 4D kernels
+// measured no gain from it).
+template <class P>
+__host__ __device__ constexpr bool inline_drain() {
+  return !P::is64 && !P::TG && P::LEAN;
 }
 static_assert(max_blocks_model<P32L>() <= kMaxBlocksPerSm, "tuning range");
 
@@ -202,6 +212,7 @@ struct FEntry : TanOf<P> {  // a particle at the start of interval l (offspring
 
 static_assert(sizeof(FEntry<P64>) == 40 && sizeof(FEntry<P32>) == 24, "FEntry layout");
 static_assert(sizeof(FEntry<P32L>) == sizeof(FEntry<P32>), "FEntry layout");
+static_assert(sizeof(FEntry<P32LB>) == sizeof(FEntry<P32>), "FEntry layout");
 static_assert(sizeof(FEntry<Q32>) == 32, "FEntry layout");
 static_assert(sizeof(FEntry<P32G>) == 32 && sizeof(FEntry<P64G>) == 56, "FEntry layout");
 
@@ -299,6 +310,7 @@ struct KP {
   unsigned* fcnt_out;
   unsigned qseg;
   FEntry<P>* eq;             // candidate intervals: the queue appended to
+  FEntry<P>* eq_alt;         // the other candidate buffer (one-launch periods)
   unsigned* ecnt;
   const FEntry<P>* eq_in;    // the candidate intervals k_event takes
   const unsigned* ecnt_in;
@@ -350,7 +362,7 @@ __device__ __forceinline__ KP<P> with_period(const KP<P>& q) {
 // parameters (constant bank), a batch from its table in global memory.
 template <class P>
 __device__ __forceinline__ Inst<typename P::T> inst_of(const KP<P>& p, int i) {
-  if (!P::LEAN && p.ninst > 1) return p.inst[i];
+  if (!P::SINGLE && p.ninst > 1) return p.inst[i];
   return p.inst0;
 }
 
@@ -375,9 +387,11 @@ struct Acc {
   }
 };
 
-// A warp's running counts in the queues it produces into.
+// A warp's running counts in the queues it produces into; flip selects the
+// candidate buffer it appends to (p.eq, or p.eq_alt in the rounds of a
+// one-launch period).
 struct WarpCounts {
-  unsigned f, e, d, r;
+  unsigned f, e, d, r, flip;
 };
 
 // ---------------------------------------------------------------------------
@@ -455,6 +469,7 @@ __device__ __forceinline__ void load_counts(const KP<P>& p, WarpCounts& wc, int 
     wc.e = own && p.ecnt ? p.ecnt[g] : 0u;
     wc.d = own && level_out > 0 ? p.dcnt[(long long)level_out * p.nseg + g] : 0u;
     wc.r = own && p.rcnt ? p.rcnt[g] : 0u;
+    wc.flip = 0u;
   }
   __syncwarp();
 }
@@ -774,7 +789,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
       p.tan[p.capacity + slot] = tau.tw;
     }
     p.cpid[slot - p.cnt->n_base] = pid;
-    if (!P::LEAN && p.ninst > 1) p.cinst[slot - p.cnt->n_base] = (unsigned)inst;
+    if (!P::SINGLE && p.ninst > 1) p.cinst[slot - p.cnt->n_base] = (unsigned)inst;
   }
 }
 
@@ -803,7 +818,7 @@ struct SEntry : TanOf<P> {  // a deferred segment, with the time and index of it
 };
 
 static_assert(sizeof(SEntry<P64>) == 64 && sizeof(SEntry<P32>) == 64, "SEntry layout");
-static_assert(sizeof(SEntry<P32L>) == 64, "SEntry layout");
+static_assert(sizeof(SEntry<P32L>) == 64 && sizeof(SEntry<P32LB>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<Q32>) == 64, "SEntry layout");
 static_assert(sizeof(SEntry<P32G>) == 64, "SEntry layout");
 
@@ -859,7 +874,7 @@ __device__ __forceinline__ void chain_next(const KP<P>& p, WarpCounts& wc,
         e.k = s.k;
         e.w = s.w;
         e.l = ent_pack(c, ent_inst(s.l));
-        p.eq[(size_t)g * p.eseg + slot] = e;
+        (wc.flip ? p.eq_alt : p.eq)[(size_t)g * p.eseg + slot] = e;
       } else {
         set_err(p.cnt, ERR_CAP_EQUEUE);
       }
@@ -899,7 +914,7 @@ __device__ __forceinline__ void settle(const KP<P>& p, WarpCounts& wc, Acc& acc,
           e.k = k;
           e.w = w;
           e.l = ent_pack(c, inst);
-          p.eq[(size_t)g * p.eseg + q] = e;
+          (wc.flip ? p.eq_alt : p.eq)[(size_t)g * p.eseg + q] = e;
         } else {
           set_err(p.cnt, ERR_CAP_EQUEUE);
         }
@@ -1201,7 +1216,7 @@ __device__ __forceinline__ typename P::T in_cell(typename P::T v, typename P::T 
 // is <= slot (empty instances share their start with the next one).
 template <class P>
 __device__ __forceinline__ int base_instance(const KP<P>& p, unsigned long long slot) {
-  if (P::LEAN || p.ninst <= 1) return 0;
+  if (P::SINGLE || p.ninst <= 1) return 0;
   int lo = 0, hi = p.ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -1408,7 +1423,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
             p.tan[p.capacity + off] = tau.tw;
           }
           p.cpid[off - p.cnt->n_base] = pid;
-          if (!P::LEAN && p.ninst > 1) p.cinst[off - p.cnt->n_base] = (unsigned)inst;
+          if (!P::SINGLE && p.ninst > 1) p.cinst[off - p.cnt->n_base] = (unsigned)inst;
         }
       }
     }
@@ -1498,22 +1513,16 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
 
 }
 
+// The work of one flight launch for the calling warp: its share of the
+// source's particles carried through [ls, L) into the sink, their candidate
+// intervals appended to the warp's candidate segment (ecount entries so far).
 template <class P, int SRC, int DST>
-__global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_flight(const KP<P> p_) {
-  const KP<P> p = with_period(p_);
+__device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc& acc,
+                                            unsigned& ecount, FEntry<P>* const eq_seg) {
   using T = typename P::T;
-  __shared__ unsigned long long red[kWarps];
-  __shared__ WarpCounts s_wc[kWarps];
   const int lane = threadIdx.x & 31;
-  WarpCounts& wc = s_wc[threadIdx.x >> 5];
-  Acc acc;
-  acc.zero();
-  load_counts(p, wc, 0);
   const unsigned g = global_warp();
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
-  // the warp's candidate segment and its count, in registers
-  unsigned ecount = wc.e;
-  FEntry<P>* const eq_seg = g < (unsigned)p.nseg ? p.eq + (long long)g * p.eseg : nullptr;
 
   if constexpr (SRC == SRC_QUEUE) {
     // the previous wave's offspring, one producer segment at a time
@@ -1606,14 +1615,14 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_flight(const
         }
         if (act) {
           int cell = (int)(cwl & 0x7FFFFFFFu);
-          if (!P::LEAN && p.ninst > 1) {
+          if (!P::SINGLE && p.ninst > 1) {
             inst = (int)((unsigned)cell / (unsigned)p.nhi);
             cell -= inst * p.nhi;
           }
           // tangent particles: ids (epoch << 40) | (instance << 32) | 2^31 | j
           const unsigned long long tag = TR ? 0x80000000ull : 0ull;
           pid = p.regen_base | tag | slot;
-          if (!P::LEAN && p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | tag | (slot - islot[inst]);
+          if (!P::SINGLE && p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | tag | (slot - islot[inst]);
           const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
           if constexpr (P::D == 1) {
             int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
@@ -1661,13 +1670,13 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_flight(const
           w = p.w ? p.w[slot] : (T)p.s[slot];
           if (slot < n_base) {
             pid = base_pid + slot;
-            if (!P::LEAN && p.ninst > 1) {
+            if (!P::SINGLE && p.ninst > 1) {
               inst = base_instance(p, slot);
               pid = base_pid + ((unsigned long long)inst << 32) + (slot - p.inst_slot[inst]);
             }
           } else {
             pid = p.cpid[slot - n_base];
-            if (!P::LEAN && p.ninst > 1) inst = (int)p.cinst[slot - n_base];
+            if (!P::SINGLE && p.ninst > 1) inst = (int)p.cinst[slot - n_base];
           }
         }
       }
@@ -1676,6 +1685,23 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_flight(const
     }
   }
 
+}
+
+template <class P, int SRC, int DST>
+__global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_flight(const KP<P> p_) {
+  const KP<P> p = with_period(p_);
+  __shared__ unsigned long long red[kWarps];
+  __shared__ WarpCounts s_wc[kWarps];
+  const int lane = threadIdx.x & 31;
+  WarpCounts& wc = s_wc[threadIdx.x >> 5];
+  Acc acc;
+  acc.zero();
+  load_counts(p, wc, 0);
+  const unsigned g = global_warp();
+  // the warp's candidate segment and its count, in registers
+  unsigned ecount = wc.e;
+  FEntry<P>* const eq_seg = g < (unsigned)p.nseg ? p.eq + (long long)g * p.eseg : nullptr;
+  flight_body<P, SRC, DST>(p, wc, acc, ecount, eq_seg);
   if (lane == 0) wc.e = ecount;
   store_counts(p, wc, 0, false, true, DST == DST_BIN2);
   block_reduce_add(red, acc.psteps, &p.cnt->ledger[SRC == SRC_QUEUE ? LG_PSTEPS : LG_PSTEPS0]);
@@ -1730,6 +1756,133 @@ __device__ __forceinline__ void copy_entry_async(FEntry<P>* dst, const FEntry<P>
 #pragma unroll
   for (unsigned w = 0; w < sizeof(FEntry<P>) / 8; ++w)
     cp_async8((char*)dst + 8 * w, (const char*)src + 8 * w);
+}
+
+// One round of the event kernel for the calling warp: the first event of
+// each candidate interval in seg[0, n) (one per lane), the pairs, and, in the
+// kernels that finish them themselves, every deferred segment; the pairs of
+// first events are added to first_pairs.  stage and buf are the warp's
+// shared staging tiles and accepted-event buffer.
+template <class P, int DST>
+__device__ __forceinline__ void event_round(const KP<P>& p, WarpCounts& wc, Acc& acc,
+                                            const FEntry<P>* seg, unsigned n,
+                                            FEntry<P> (*stage)[32], Birth<P>* buf,
+                                            unsigned& first_pairs) {
+  using T = typename P::T;
+  const int lane = threadIdx.x & 31;
+  const unsigned g = global_warp();
+  auto later = [&](const SEntry<P>& ch) { defer<P>(p, wc, 1, ch); };
+  // FP32 2D: the accepted events of the warp's tiles wait in a per-warp
+  // buffer and their pairs are made 32 at a time, so that every lane has one
+  // (the acceptance would otherwise leave a third of the lanes idle there);
+  // the 4D events, with larger records and more registers, measured slower so
+  constexpr bool CMP = !P::is64 && P::D == 1;
+  unsigned nb = 0;  // births in the buffer (the same in every lane)
+  auto make_pairs = [&](unsigned lim) {
+    while (nb >= lim) {
+      const unsigned take = min(nb, 32u);
+      __syncwarp();
+      if ((unsigned)lane < take) {
+        const Birth<P> bb = buf[nb - take + lane];
+        event_pair<P, DST>(p, inst_of(p, ent_inst(bb.l)), wc, acc, bb, later);
+      }
+      __syncwarp();
+      nb -= take;
+    }
+  };
+  const unsigned events0 = acc.events;
+  // each lane copies its entry of the next tile into shared memory
+  // asynchronously while the current tile is processed
+  if ((unsigned)lane < n) copy_entry_async<P>(&stage[0][lane], seg + lane);
+  cp_async_commit();
+  unsigned t = 0;
+  for (unsigned b = 0; b < n; b += 32, ++t) {
+    const unsigned i = b + lane;
+    if (i + 32 < n) copy_entry_async<P>(&stage[(t + 1) & 1][lane], seg + i + 32);
+    cp_async_commit();
+    cp_async_wait<1>();
+    FEntry<P> e{};
+    if (i < n) e = stage[t & 1][lane];
+    bool made = false;
+    Birth<P> bb;
+    if (i < n) {
+      const int l = ent_l(e.l), inst = ent_inst(e.l);
+      const Inst<T> ip = inst_of(p, inst);
+      SEntry<P> s;
+      static_cast<TanOf<P>&>(s) = static_cast<const TanOf<P>&>(e);
+      s.pid = e.pid;
+      s.xo = e.x;
+      s.to = (T)0;
+      s.k = e.k;
+      s.w = e.w;
+      s.l = e.l;
+      s.t = Draw<P>::first(p, ip, e.pid, l, (T)0, true, s.st);
+      if (s.t < p.dt) {
+        ++acc.cand;
+        T gap;
+        if constexpr (CMP) {
+          made = event_decide<P>(p, ip, inst, s.pid, s.xo, s.to, s.k, s.w, s.st, l, 0u, true,
+                                 s.t, s, bb, gap);
+        } else {
+          gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st, l,
+                                 0u, true, s.t, later, s);
+        }
+        s.t = P::add(s.t, gap);
+        if (s.t < p.dt) {
+          s.j = 1u | kRootFlag;
+          defer<P>(p, wc, 1, s);
+        } else {
+          chain_next<P>(p, wc, s);
+        }
+      }
+    }
+    if constexpr (CMP) {
+      const unsigned bal = __ballot_sync(kFull, made);
+      if (made) buf[nb + __popc(bal & ((1u << lane) - 1u))] = bb;
+      nb += __popc(bal);
+      make_pairs(32u);
+    }
+  }
+  cp_async_wait<0>();
+  if constexpr (CMP) make_pairs(1u);
+  // so far the warp has made only first events' pairs
+  first_pairs += acc.events - events0;
+  if constexpr (inline_drain<P>()) {
+    // These kernels finish their warp's deferred segments here instead of
+    // in launches of their own: one event per lane per pass (Alg. 1 item 3,
+    // offspring born inside the interval included), a segment with another
+    // event in its interval appended again to the same list, until the list
+    // is used up.  Its count is then zero for the launches that follow.
+    const SEntry<P>* dl = p.dq[1] + (size_t)g * p.dseg;
+    unsigned rd = 0;
+    for (;;) {
+      __syncwarp();
+      const unsigned end = min(wc.d, p.dseg);
+      if (rd >= end || g >= (unsigned)p.nseg) break;
+      const unsigned i = rd + lane;
+      if (i < end) {
+        SEntry<P> s = dl[i];
+        const unsigned j = s.j & ~kRootFlag;
+        const int l = ent_l(s.l), inst = ent_inst(s.l);
+        const Inst<T> ip = inst_of(p, inst);
+        const T gap = do_event<P, DST>(p, ip, inst, wc, acc, s.pid, s.xo, s.to, s.k, s.w, s.st,
+                                       l, j, (s.j & kRootFlag) != 0u, s.t, later, s);
+        s.t = P::add(s.t, gap);
+        if (s.t < p.dt) {
+          s.j = (j + 1) | (s.j & kRootFlag);
+          defer<P>(p, wc, 1, s);
+        } else if (!(s.j & kRootFlag)) {
+          settle<P, DST>(p, wc, acc, inst, s.pid, s.xo, s.to, s.k, s.w, l, s, s.t);
+        } else {
+          chain_next<P>(p, wc, s);
+        }
+      }
+      rd = min(rd + 32u, end);
+    }
+    __syncwarp();
+    if (lane == 0) wc.d = 0;
+    __syncwarp();
+  }
 }
 
 template <class P, int DST>
@@ -1880,6 +2033,59 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_event(const 
   reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
 }
 
+// A whole resampling period in one launch (the lean models): each warp
+// runs its share of the first wave, then the event rounds over its own
+// candidate segments.  Warp g writes candidate segment g and only warp g
+// reads it, in this launch as in the launch-per-round schedule, so the
+// rounds need no barrier between warps: a warp starts its next round as
+// soon as it has finished the previous one, and the warps of an SM mix the
+// two phases.  Round r appends to the candidate buffer round r reads not
+// (p.eq and p.eq_alt alternate); the deferred segments are finished inside
+// each round.  Results are those of the launch-per-round schedule, bit for
+// bit (every draw is keyed by particle and interval).
+template <class P, int DST>
+__global__ void __launch_bounds__(kBlock, 3) k_period(const KP<P> p_) {
+  const KP<P> p = with_period(p_);
+  __shared__ unsigned long long red[kWarps];
+  __shared__ WarpCounts s_wc[kWarps];
+  const int lane = threadIdx.x & 31;
+  WarpCounts& wc = s_wc[threadIdx.x >> 5];
+  Acc acc;
+  acc.zero();
+  load_counts(p, wc, 1);
+  const unsigned g = global_warp();
+  const bool own = g < (unsigned)p.nseg;
+  // the first wave: candidate intervals into buffer p.eq, segment g
+  unsigned ecount = wc.e;
+  flight_body<P, SRC_REGEN, DST>(p, wc, acc, ecount, own ? p.eq + (long long)g * p.eseg : nullptr);
+  const unsigned psteps_first = acc.psteps;
+  constexpr bool CMP = !P::is64 && P::D == 1;
+  constexpr unsigned kBirths = 64;
+  __shared__ Birth<P> s_birth[CMP ? kWarps : 1][CMP ? kBirths : 1];
+  __shared__ __align__(16) FEntry<P> s_stage[kWarps][2][32];
+  unsigned first_pairs = 0;
+  unsigned n = own ? min(ecount, p.eseg) : 0u;
+  for (int r = 0; r < p.len && n > 0u; ++r) {
+    __syncwarp();
+    if (lane == 0) {
+      wc.e = 0;
+      wc.flip = (unsigned)(r + 1) & 1u;  // round r reads buffer r & 1, appends to the other
+    }
+    __syncwarp();
+    event_round<P, DST>(p, wc, acc, ((r & 1) ? p.eq_alt : p.eq) + (long long)g * p.eseg, n,
+                        s_stage[threadIdx.x >> 5], s_birth[CMP ? (threadIdx.x >> 5) : 0],
+                        first_pairs);
+    __syncwarp();
+    n = min(wc.e, p.eseg);
+  }
+  store_counts(p, wc, 1, false, false, DST == DST_BIN2);
+  block_reduce_add(red, psteps_first, &p.cnt->ledger[LG_PSTEPS0]);
+  block_reduce_add(red, acc.cand, &p.cnt->ledger[LG_CAND]);
+  block_reduce_add(red, first_pairs, &p.cnt->ledger[LG_PAIRS0]);
+  acc.psteps -= psteps_first;  // the offspring's flights
+  reduce_event_tallies(red, acc, p.cnt, DST == DST_BIN2);
+}
+
 template <class P, int DST>
 __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_cont(const KP<P> p_, int level) {
   const KP<P> p = with_period(p_);
@@ -2008,7 +2214,7 @@ __global__ void __launch_bounds__(kBlock) k_pids(const KP<P> p, unsigned long lo
       pid = bp + ((unsigned long long)inst << 32) + (i - p.inst_slot[inst]);
     } else {
       pid = p.cpid[i - nb];
-      if (!P::LEAN && p.ninst > 1) inst = (int)p.cinst[i - nb];
+      if (!P::SINGLE && p.ninst > 1) inst = (int)p.cinst[i - nb];
     }
     if (out) out[i] = pid;
     if (inst_out) inst_out[i] = (unsigned)inst;
@@ -2158,7 +2364,7 @@ cudaError_t events(Ctx* c, const KP<P>& p, int r) {
   k_event<P, DST><<<grid_of(c, o_ev), kBlock, 0, c->stream>>>(p);
   prof_end(c, PROF_EVENT, r);
   c->launches += 1;
-  if constexpr (!P::LEAN) {  // the lean event kernel finishes every segment itself
+  if constexpr (!inline_drain<P>()) {  // else the event kernel finished every segment itself
     for (int level = 1; level <= c->passes; ++level)
       k_cont<P, DST><<<grid_of(c, o_cont), kBlock, 0, c->stream>>>(p, level);
     k_drain<P, DST><<<grid_of(c, o_drain), kBlock, 0, c->stream>>>(p, c->passes + 1);
@@ -2197,6 +2403,33 @@ cudaError_t events_any(Ctx* c, const KP<P>& p, int dst, int r) {
   if constexpr (P::D == 1 && !P::TG) {
     if (dst == DST_BIN2) return events<P, DST_BIN2>(c, p, r);
     return events<P, DST_WSUM>(c, p, r);
+  }
+  return cudaErrorNotSupported;
+}
+
+// One regenerating period of a lean model in one launch (k_period): the
+// candidate and deferred counts start at zero, the first wave's candidates go
+// to buffer 0 and the rounds alternate between the two buffers.
+template <class P, int DST>
+cudaError_t period(Ctx* c, KP<P> p, size_t cnt_bytes) {
+  static const int occ = occupancy(k_period<P, DST>);
+  cudaError_t e;
+  if ((e = launch_zero(c, c->ecnt[0], cnt_bytes)) != cudaSuccess) return e;
+  if ((e = launch_zero(c, c->dcnt, (size_t)(c->passes + 2) * cnt_bytes)) != cudaSuccess) return e;
+  p.eq = (FEntry<P>*)c->eq[0];
+  p.ecnt = c->ecnt[0];
+  p.eq_alt = (FEntry<P>*)c->eq[1];
+  prof_begin(c);
+  k_period<P, DST><<<grid_of(c, occ), kBlock, 0, c->stream>>>(p);
+  prof_end(c);
+  c->launches++;
+  return cudaGetLastError();
+}
+
+template <class P>
+cudaError_t period_any(Ctx* c, const KP<P>& p, int dst, size_t cnt_bytes) {
+  if constexpr (inline_drain<P>()) {
+    if (dst == DST_BIN1) return period<P, DST_BIN1>(c, p, cnt_bytes);
   }
   return cudaErrorNotSupported;
 }
@@ -2336,6 +2569,10 @@ struct DriverImpl {
     p.len = L - l0;
     const int rounds = L > l0 ? L - l0 : 1;
     const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
+    if constexpr (inline_drain<P>()) {
+      if (src == SRC_REGEN && L > l0 && dst == DST_BIN1)
+        return period_any<P>(c, p, dst, cnt_bytes);
+    }
     for (int r = 0; r < rounds; ++r) {
       p.fq_in = (FEntry<P>*)c->fq[r & 1];
       p.fcnt_in = c->fcnt[r & 1];

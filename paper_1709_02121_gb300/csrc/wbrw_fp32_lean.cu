@@ -1,5 +1,5 @@
 // FP32 instantiation for runs with one instance, the static potential and no
-// event log: the production path of the 2D workloads.
+// event log: the production path of the plain 2D workloads.
 #include "wbrw_device.cuh"
 
 namespace wbrw {

@@ -168,7 +168,7 @@ struct Ctx {
   double* inst_grad;              // read-out (dT/dH, dT/dw) per instance (device)
   // time-dependent potential (wbrw_init_td): components on the device
   int ncomp;
-  int lean;           // FP32 2D, one instance, static potential, no event log
+  int lean;           // FP32 2D, static potential, no event log, no tangents
   void* comp_tab;
   // scratch carve-up
   Counters* cnt;
@@ -277,6 +277,7 @@ struct Driver {
 const Driver* driver_fp64();
 const Driver* driver_fp32();
 const Driver* driver_fp32_lean();
+const Driver* driver_fp32_lean_batch();
 const Driver* driver_fp64_4d();
 const Driver* driver_fp32_4d();
 const Driver* driver_fp64_grad();

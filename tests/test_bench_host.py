@@ -141,3 +141,17 @@ def test_workload_selection(bench):
     assert bench.workload(A)["dim"] == 4
     d = bench.parse([])
     assert d.workload == "gauss2d_fp32_n1e8" and d.gpus == 1 and not d.no_secondary
+
+
+def test_one_launch_period_roofline_counts_both_phases(bench):
+    wl = {"precision": "fp32", "resample_every": 10, "strategy": "sp1"}
+    r = bench.roofline_period(wl, ms=8.0, n=2, psteps_first=3.2e9, cand=2e8, pairs=1.2e8,
+                              ceiling=5e11, clk={"sm_mhz": 2070.0}, peaks={})
+    calls = 0.1 * 3.2e9 + 2e8 + 1.2e8
+    assert r["achieved"] == pytest.approx(calls / 8e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 500.0)
+    assert r["launch_ms"] == pytest.approx(4.0) and r["kernel"] == "k_period<fp32>"
+    c0 = {"particle_steps_first": 0, "candidates": 0, "first_pairs": 0}
+    c1 = {"particle_steps_first": 3.2e9, "candidates": 2e8, "first_pairs": 1.2e8}
+    roof, roof2 = bench.rooflines(wl, c0, c1, (8.0, 2), (0.0, 0), 5e11, {"sm_mhz": 2070.0}, {})
+    assert roof["kernel"] == "k_period<fp32>" and roof2 is None

@@ -34,9 +34,9 @@ def small(**over):
     return workloads.scaled(workloads.GAUSS_2D_FP64_2E5, **base)
 
 
-def sim(wl, graph, gpu, capacity=400_000):
+def sim(wl, graph, gpu, capacity=400_000, event_log=0):
     from paper_1709_02121_gb300 import Simulation
-    s = Simulation(wl, capacity, stream=gpu.cuda.Stream())
+    s = Simulation(wl, capacity, event_log=event_log, stream=gpu.cuda.Stream())
     if graph:
         s.graph(True)
     return s
@@ -128,8 +128,11 @@ def test_profiling_sees_every_replayed_first_wave(gpu):
 
 @pytest.mark.parametrize("graphs", [False, True])
 def test_profiling_sees_every_event_kernel(gpu, graphs):
+    # an event log selects the general kernels, which launch the event kernel
+    # once per round (the lean ones run a whole period in one launch)
     from paper_1709_02121_gb300 import wbrw
-    s = sim(small(precision="fp32", n_alpha=50_000), graphs, gpu, capacity=1_000_000)
+    s = sim(small(precision="fp32", n_alpha=50_000), graphs, gpu, capacity=1_000_000,
+            event_log=1 << 16)
     s.run(10)
     wbrw.wbrw_profile(s.ctx, True)
     s.run(20)
@@ -145,6 +148,20 @@ def test_profiling_sees_every_event_kernel(gpu, graphs):
     wbrw.wbrw_profile(s.ctx, True)
     s.run(5)
     assert wbrw.wbrw_profile_read_events(s.ctx)[1] == 5
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_profiling_sees_every_one_launch_period(gpu, graphs):
+    """The lean kernels run a regenerating period in one launch, which the
+    first-wave records time; no event-kernel launch is left to time."""
+    from paper_1709_02121_gb300 import wbrw
+    s = sim(small(precision="fp32", n_alpha=50_000), graphs, gpu, capacity=1_000_000)
+    s.run(10)
+    wbrw.wbrw_profile(s.ctx, True)
+    s.run(20)
+    ms_f, n_f = wbrw.wbrw_profile_read(s.ctx)
+    ms_e, n_e = wbrw.wbrw_profile_read_events(s.ctx)
+    assert n_f == 4 and ms_f > 0 and n_e == 0
 
 
 def test_graphs_need_a_created_stream(gpu):

@@ -1,8 +1,9 @@
 """The lean FP32 kernels give the general kernels' results bit for bit.
 
-An FP32 2D run with one instance, the static potential and no event log runs
-kernels compiled without the batch decode, the time-dependent components and
-the log writes.  Attaching an event log (which changes no result) selects the
+An FP32 2D run (plain or batched) with the static potential and no event log
+runs kernels compiled without the time-dependent components and the log
+writes, built for four blocks per SM, whose event kernel finishes deferred
+segments itself.  Attaching an event log (which changes no result) selects the
 general kernels for the same run, so the two can be compared on the same
 streams: histograms after every period, the counters, and the particles after
 plain steps.
@@ -56,5 +57,26 @@ def test_lean_kernels_equal_the_general_ones(torch, strategy):
     assert np.array_equal(pa[ia], pb[ib])
     for u, v in ((xa, xb), (ka, kb), (sa, sb)):
         assert np.array_equal(u[ia], v[ib])
+    lean.close()
+    gen.close()
+
+
+def test_lean_batch_equals_the_general_batch(torch):
+    from paper_1709_02121_gb300 import Batch
+    wl = workloads.scaled(workloads.BATCH_2D_FP32_256, nx=100, nk=64, xmin=-25.0, xmax=25.0,
+                          kmin=-3.2, kmax=3.2, resample_every=5)
+    insts = workloads.batch_instances(dict(wl, instances=5), 0.004)
+    lean = Batch(wl, insts, 3_000_000, stream=torch.cuda.Stream())
+    gen = Batch(wl, insts, 3_000_000, event_log=1 << 16, stream=torch.cuda.Stream())
+    lean.graph(True)
+    gen.graph(True)
+    for period in range(4):
+        lean.run(5)
+        gen.run(5)
+        assert np.array_equal(lean.grid_counts(), gen.grid_counts()), period
+        assert np.array_equal(lean.transmissions(), gen.transmissions()), period
+    a, b = lean.counters(), gen.counters()
+    for k in KEYS[:12]:
+        assert a[k] == b[k], k
     lean.close()
     gen.close()
