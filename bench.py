@@ -88,7 +88,7 @@ def workload(args):
             wl["n_alpha"] = int(args.particles)
         return wl
     if args.workload == "batch2d_fp32_256":
-        return workloads.scaled(workloads.BATCH_2D_FP32_256)
+        return workloads.scaled(workloads.BATCH_2D_FP32_256, strategy=args.strategy)
     if args.workload == "he4d_fp32_n5e7":
         wl = workloads.scaled(workloads.HE_4D_FP32_5E7)
         if args.particles:
@@ -323,9 +323,13 @@ INST_PER_PHILOX = 42.0
 SMS, INT32_LANES = 152, 64
 # DRAM bytes per unit measured by ncu for the plain sp1 workloads
 # (profiles/); None where no capture of the current kernels exists (other
-# strategies, batches, FP64)
-TRAFFIC_PER_PSTEP = {"fp32": 0.562, "fp64": None, "fp32_4d": 1.18, "fp64_4d": None}
-TRAFFIC_PER_CANDIDATE = {"fp32": 31.0, "fp64": None, "fp32_4d": 49.7, "fp64_4d": None}
+# strategies, batches, FP64, and the 2D FP32 kernels that the one-launch
+# period replaced on this workload)
+TRAFFIC_PER_PSTEP = {"fp32": None, "fp64": None, "fp32_4d": 1.19, "fp64_4d": None}
+TRAFFIC_PER_CANDIDATE = {"fp32": None, "fp64": None, "fp32_4d": 49.2, "fp64_4d": None}
+# the one-launch period: its DRAM bytes per candidate interval (the queue
+# entries written by the first wave and read back by the rounds dominate)
+TRAFFIC_PERIOD_PER_CANDIDATE = {"fp32": 45.5}
 
 
 def _traffic(table, wl):
@@ -546,8 +550,8 @@ def roofline_period(wl, ms, n, psteps_first, cand, pairs, ceiling, clk, peaks):
     calls = (base + per_interval * R) / R * psteps_first + a * cand + b * pairs
     peak, derived, sm_mhz = _peak(ceiling, clk, peaks)
     ach = calls / (ms / 1e3) / 1e9
-    t1, t2 = _traffic(TRAFFIC_PER_PSTEP, wl), _traffic(TRAFFIC_PER_CANDIDATE, wl)
-    traffic = (t1 * psteps_first + t2 * cand) / n if (t1 is not None and t2 is not None) else None
+    t = _traffic(TRAFFIC_PERIOD_PER_CANDIDATE, wl)
+    traffic = t * cand / n if t is not None else None
     return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gcalls/s",
             "frac": ach / peak, "traffic": traffic,
             "kernel": "k_period<%s%s>" % (wl["precision"], ",4d" if wl.get("dim", 2) == 4 else ""),
@@ -931,7 +935,8 @@ def ours_batch(args, spec):
                            "particles": res["particles"],
                            "particles_min_max": res["particles_min_max"],
                            "grid_per_instance": [wl["nx"], wl["nk"]], "dt": wl["dt"],
-                           "intervals_per_step": wl["resample_every"], "strategy": "sp1",
+                           "intervals_per_step": wl["resample_every"],
+                           "strategy": wl["strategy"],
                            "precision": "fp32", "cuda_graphs": res["cuda_graphs"],
                            "l2": "flushed (512 MiB write) between timed steps",
                            "parallelism": "replicas x%d" % ws},

@@ -32,8 +32,13 @@ def test_first_wave_roofline_counts_philox_calls(bench):
     assert r["peak_derived"] == pytest.approx(152 * 64 * 2070e6 / 42.0 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["bound"] == "alu" and r["launch_ms"] == pytest.approx(2.0)
-    # the traffic per launch scales the measured bytes per particle-step
-    assert r["traffic"] == pytest.approx(bench.TRAFFIC_PER_PSTEP["fp32"] * 1.6e9)
+    # the traffic per launch scales the measured bytes per particle-step;
+    # null where no capture of the kernel exists
+    tpp = bench.TRAFFIC_PER_PSTEP["fp32"]
+    assert r["traffic"] == (None if tpp is None else pytest.approx(tpp * 1.6e9))
+    r4 = bench.roofline({"precision": "fp32", "dim": 4, "resample_every": 10}, 4.0, 2, 3.2e9,
+                        None, {"sm_mhz": 2070.0}, {})
+    assert r4["traffic"] == pytest.approx(bench.TRAFFIC_PER_PSTEP["fp32_4d"] * 1.6e9)
     # without a measurement the derived ceiling is the peak
     r0 = bench.roofline(wl, 4.0, 2, 3.2e9, None, {"sm_mhz": 2070.0}, {})
     assert r0["peak"] == pytest.approx(r0["peak_derived"])
@@ -153,5 +158,9 @@ def test_one_launch_period_roofline_counts_both_phases(bench):
     assert r["launch_ms"] == pytest.approx(4.0) and r["kernel"] == "k_period<fp32>"
     c0 = {"particle_steps_first": 0, "candidates": 0, "first_pairs": 0}
     c1 = {"particle_steps_first": 3.2e9, "candidates": 2e8, "first_pairs": 1.2e8}
+    # the measured bytes per candidate interval scale to the launch's candidates
+    assert r["traffic"] == pytest.approx(bench.TRAFFIC_PERIOD_PER_CANDIDATE["fp32"] * 1e8)
+    assert bench.roofline_period(dict(wl, strategy="sp2"), 8.0, 2, 3.2e9, 2e8, 1.2e8, 5e11,
+                                 {}, {})["traffic"] is None
     roof, roof2 = bench.rooflines(wl, c0, c1, (8.0, 2), (0.0, 0), 5e11, {"sm_mhz": 2070.0}, {})
     assert roof["kernel"] == "k_period<fp32>" and roof2 is None
