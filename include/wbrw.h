@@ -451,7 +451,12 @@ wbrw_status wbrw_philox_chain(unsigned long long seed, int iters, long long nthr
  * instance i owns grid[i*nx*nk .. (i+1)*nx*nk), x-major with k contiguous;
  * buffers.grid_cells >= ninst*nx*nk, and ninst*nx*nk < 2^30.  The particle
  * arrays are shared: initial particles of instance i occupy the slots after
- * those of instances 0..i-1.  Batches use sp1 (WBRW_SP1_PAIR) only.
+ * those of instances 0..i-1.  Every strategy runs in a batch: sp2
+ * bootstraps each instance on its own (Alg. 2 per instance and side, with
+ * the shares of that instance's N^s and W^s), and the residual draws and
+ * the roundings of sp2 and wp are counted (instance << 32) | d and
+ * (instance << 32) | (cell within the instance), salt 0 being the plain
+ * run's.  The sp2 counters of wbrw_counters are then sums over instances.
  * wbrw_step, wbrw_annihilate, wbrw_run, wbrw_particles, wbrw_checkpoint
  * (all instances' counts), wbrw_restore, wbrw_counters (sums over
  * instances), wbrw_profile and wbrw_destroy work on a batch unchanged;

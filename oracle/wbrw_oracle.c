@@ -768,7 +768,10 @@ static uint64_t mulhi64(uint64_t a, uint64_t b) {
  *   R_nu / R (R_nu = residual sum of the side in nu): only the cell of a
  *   draw enters the histogram, so this has the law of drawing particles.
  * Draw d of side s: r = 64 random bits, U = floor(r R / 2^64), cell = the
- * first nu whose inclusive prefix of R exceeds U.
+ * first nu whose inclusive prefix of R exceeds U.  The draw's counter is
+ * (instance << 32) | d and the rounding of cell nu's is (instance << 32) | nu,
+ * so that the instances of a batch (salt 0 for a plain run) draw from
+ * separate streams, as their particle labels do.
  * Then m_nu = (W^+/N^+) n~_nu^+ - (W^-/N^-) n~_nu^-  (= N_alpha mu(D_nu)
  * d_nu of Alg. 3) and |m_nu| is rounded stochastically with its own u. */
 static int bootstrap(orc_state* s) {
@@ -830,7 +833,7 @@ static int bootstrap(orc_state* s) {
     if (R > 0) {
       for (long long d = 0; d < nr; ++d) {
         uint32_t h[4];
-        draw4(s, (uint64_t)d, ORC_STEP_BOOT,
+        draw4(s, ((uint64_t)s->c.instance << 32) | (uint64_t)d, ORC_STEP_BOOT,
               (uint32_t)(((uint64_t)s->epoch << 1) | (uint64_t)sd), h);
         uint64_t r64 = ((uint64_t)h[1] << 32) | (uint64_t)h[0];
         uint64_t U = mulhi64(r64, R);
@@ -856,7 +859,8 @@ static int bootstrap(orc_state* s) {
     double am = fabs(m);
     double fl = floor(am);
     uint32_t h[4];
-    draw4(s, (uint64_t)nu, ORC_STEP_ROUND, (uint32_t)s->epoch, h);
+    draw4(s, ((uint64_t)s->c.instance << 32) | (uint64_t)nu, ORC_STEP_ROUND,
+          (uint32_t)s->epoch, h);
     double u = orc_u53(h[0], h[1]);
     long long cnt = (long long)fl + (u < am - fl ? 1 : 0);
     s->grid[nu] = (int)(m < 0 ? -cnt : cnt);
@@ -877,7 +881,7 @@ static int bootstrap(orc_state* s) {
  * over D_nu (each w in fixed point, llrint(w 2^31), so the sum is exact),
  * then Alg. 3 with its rounding step: floor(|m|) particles plus one with
  * probability |m| - floor(|m|), of sign sign(m), from the uniform of the
- * draw (nu, ROUND, epoch) as for sp2. */
+ * draw ((instance << 32) | nu, ROUND, epoch) as for sp2. */
 static int wp_histogram(orc_state* s) {
   long long nh = (long long)s->c.nx * s->c.nk;
   long long* ws = (long long*)calloc((size_t)nh, sizeof(long long));
@@ -896,7 +900,8 @@ static int wp_histogram(orc_state* s) {
     double am = fabs(m);
     double fl = floor(am);
     uint32_t h[4];
-    draw4(s, (uint64_t)nu, ORC_STEP_ROUND, (uint32_t)s->epoch, h);
+    draw4(s, ((uint64_t)s->c.instance << 32) | (uint64_t)nu, ORC_STEP_ROUND,
+          (uint32_t)s->epoch, h);
     double u = orc_u53(h[0], h[1]);
     long long cnt = (long long)fl + (u < am - fl ? 1 : 0);
     s->grid[nu] = (int)(m < 0 ? -cnt : cnt);

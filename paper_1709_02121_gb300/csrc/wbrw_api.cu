@@ -29,9 +29,9 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
   size_t counters, cpid, fq0, fq1, eq0, eq1, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, ucnt, guide, seg_counts, cnt_save, tabs, cinst, obs_red, tab_A,
-      tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, tab_guide0, tab_guide1, dgrid0, dgrid1, tnz_cell, tnz_start,
-      tnz_tau, ttile_nz, total;
+      rec_a, keep0, keep1, res0, res1, ucnt, guide, binst, dpre, seg_counts, cnt_save, tabs,
+      cinst, obs_red, tab_A, tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, tab_guide0,
+      tab_guide1, dgrid0, dgrid1, tnz_cell, tnz_start, tnz_tau, ttile_nz, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
 };
 
@@ -64,7 +64,6 @@ bool config_ok(const wbrw_config* c, char* why, size_t n, int ninst = 0) {
   if (c->dim == 4 && (c->nx > 4096 || c->nk > 4096)) return fail("nx, nk <= 4096 for dim 4");
   if (cells * (ninst > 0 ? ninst : 1) >= (1ll << 30))
     return fail("cells of all instances must be < 2^30");
-  if (ninst > 1 && c->strategy != WBRW_SP1_PAIR) return fail("batches use sp1 only");
   if (!(c->xmax > c->xmin) || !(c->kmax > c->kmin)) return fail("empty domain");
   if (c->resample_every < 0) return fail("resample_every must be >= 0");
   if (ninst == 0 && c->n_alpha <= 0) return fail("n_alpha must be > 0");
@@ -145,6 +144,8 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.res1 = take(sp2 ? (size_t)nh * 8 : 0);
   L.ucnt = take(sp2 ? (size_t)2 * nh * 4 : 0);
   L.guide = take(sp2 ? (size_t)2 * (kGuide + 1) * 4 : 0);
+  L.binst = take(sp2 && ninst > 1 ? (size_t)ninst * sizeof(BootInst) : 0);
+  L.dpre = take(sp2 && ninst > 1 ? (size_t)(2 * ninst + 1) * 8 : 0);
   L.tabs = take(kTabBytes);
   L.cinst = take(ninst > 1 ? (size_t)capacity * 4 : 0);
   const bool d4 = c->dim == 4;
@@ -702,6 +703,8 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->boot_res[1] = (unsigned long long*)(base + L.res1);
   c->boot_ucnt = (int*)(base + L.ucnt);
   c->boot_guide = (int*)(base + L.guide);
+  c->boot_inst = (BootInst*)(base + L.binst);
+  c->boot_dpre = (unsigned long long*)(base + L.dpre);
   c->inst_tab = base + L.tabs;
   c->inst_slot = (unsigned long long*)(base + L.tabs + kTabSlotOff);
   c->inst_na = (double*)(base + L.tabs + kTabNaOff);

@@ -290,6 +290,8 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 // a = floor(|w| 2^31); N^s and W^s = sum a were tallied with the records.
 // ---------------------------------------------------------------------------
 constexpr int kBootChunk = 1024;  // records per work item of k_boot_bin
+constexpr int kBootBinBlocks = 8; // resident blocks per SM k_boot_bin is built and launched for
+constexpr int kBootBinBatchBlocks = 6;  // the same for its batch form (shares from a table)
 
 // The share q_i = a_i N^s / W^s of a record of side s (Alg. 2 on S^s), split
 // into its integer part and its Q0.32 residual.  fx (FP32 runs): in fixed
@@ -304,16 +306,17 @@ struct BootShare {
   unsigned long long mx0, mx1;
   bool fx0, fx1;
 
-  __device__ void init(const Counters* c, int fx) {
+  __device__ void init(const Counters* c, int fx) { init(c->boot_n, c->boot_w, fx); }
+  // from the counts N^s and the weight sums W^s (Q1.31) of the two sides
+  __device__ void init(const unsigned long long* bn, const unsigned long long* bw, int fx) {
     ratio0 = ratio1 = 0.0;
     mx0 = mx1 = 0;
     fx0 = fx1 = false;
     for (int s = 0; s < 2; ++s) {
-      const double r =
-          c->boot_w[s] > 0 ? __ddiv_rn((double)c->boot_n[s], (double)c->boot_w[s]) : 0.0;
+      const double r = bw[s] > 0 ? __ddiv_rn((double)bn[s], (double)bw[s]) : 0.0;
       unsigned long long m_s = 0;
       bool f_s = false;
-      if (fx && c->boot_n[s] < c->boot_w[s]) {
+      if (fx && bn[s] < bw[s]) {
         const double m = r * 18446744073709551616.0;
         if (m < 18446744073709551616.0) {
           m_s = (unsigned long long)m;
@@ -337,6 +340,18 @@ struct BootShare {
     }
   }
 };
+
+// An instance's shares (its record filled by k_bootb_share).
+__device__ __forceinline__ BootShare share_of(const BootInst& b) {
+  BootShare sh;
+  sh.ratio0 = b.ratio[0];
+  sh.ratio1 = b.ratio[1];
+  sh.mx0 = b.mx[0];
+  sh.mx1 = b.mx[1];
+  sh.fx0 = b.fx[0] != 0;
+  sh.fx1 = b.fx[1] != 0;
+  return sh;
+}
 
 // The regenerated particles' part (weight +-1, a = 2^31, all of a side with
 // the same share): count x (integer part, residual) per side and cell,
@@ -370,15 +385,28 @@ __global__ void __launch_bounds__(kBlock) k_boot_unit(Counters* c, const int* uc
   }
 }
 
-__global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint32_t* rec_cell,
-                                                     const uint32_t* rec_a, const unsigned* rcnt,
-                                                     int nseg, long long rseg,
-                                                     int* keep0, int* keep1,
-                                                     unsigned long long* res0,
-                                                     unsigned long long* res1, int fx) {
+// The offspring records' shares added to the cell tallies.  BATCH: the
+// records of all instances of a batch, each with its instance's share (the
+// instance of global cell nu is nu / nhi); the sums of the integer parts go
+// to the instances' records instead of the run's counters.
+template <bool BATCH>
+__global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBinBlocks)
+    k_boot_bin(Counters* c, const uint32_t* rec_cell, const uint32_t* rec_a, const unsigned* rcnt,
+               int nseg, long long rseg, int* keep0, int* keep1, unsigned long long* res0,
+               unsigned long long* res1, int fx, BootInst* bi, int ninst, int nhi) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
+  __shared__ BootShare tab[BATCH ? kMaxInst : 1];
+  __shared__ unsigned long long ksum[BATCH ? 2 * kMaxInst : 1];
   BootShare sh;
-  sh.init(c, fx);
+  if constexpr (BATCH) {
+    for (int i = threadIdx.x; i < ninst; i += kBlock) {
+      tab[i] = share_of(bi[i]);
+      ksum[2 * i] = ksum[2 * i + 1] = 0;
+    }
+    __syncthreads();
+  } else {
+    sh.init(c, fx);
+  }
   unsigned long long ks0 = 0, ks1 = 0;
   // records sit in one segment per producer warp; a warp takes a segment
   const int lane = threadIdx.x & 31;
@@ -408,7 +436,8 @@ __global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint3
         const uint32_t rc = rcs[i];
         const int side = rc >> 31;
         const uint32_t cell = rc & 0x7FFFFFFFu;
-        sh.of(ras[i], side, kf, res);
+        if constexpr (BATCH) tab[cell / (unsigned)nhi].of(ras[i], side, kf, res);
+        else sh.of(ras[i], side, kf, res);
         key = 2u * cell + (unsigned)side;
       }
       const unsigned prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
@@ -432,14 +461,24 @@ __global__ void __launch_bounds__(kBlock, 8) k_boot_bin(Counters* c, const uint3
         const uint32_t cell = key >> 1;
         if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
         if (res) atomicAdd((side ? res1 : res0) + cell, res);
-        if (side) ks1 += (unsigned long long)kf; else ks0 += (unsigned long long)kf;
+        if constexpr (BATCH) {
+          if (kf) atomicAdd(&ksum[2 * (cell / (unsigned)nhi) + side], (unsigned long long)kf);
+        } else {
+          if (side) ks1 += (unsigned long long)kf; else ks0 += (unsigned long long)kf;
+        }
       }
     }
   }
-  for (int s = 0; s < 2; ++s) {
-    unsigned long long t;
-    block_exscan(s ? ks1 : ks0, red, t);
-    if (threadIdx.x == 0 && t) atomicAdd(&c->boot_keep[s], t);
+  if constexpr (BATCH) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * ninst; i += kBlock)
+      if (ksum[i]) atomicAdd(&bi[i >> 1].keep[i & 1], ksum[i]);
+  } else {
+    for (int s = 0; s < 2; ++s) {
+      unsigned long long t;
+      block_exscan(s ? ks1 : ks0, red, t);
+      if (threadIdx.x == 0 && t) atomicAdd(&c->boot_keep[s], t);
+    }
   }
 }
 
@@ -538,11 +577,255 @@ __global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long
   }
 }
 
+// ---------------------------------------------------------------------------
+// sp2 in a batch: Alg. 2 per instance and side.  Instance b owns the global
+// cells [b nhi, (b + 1) nhi); its draws and roundings are counted by
+// (b << 32) | d and (b << 32) | (nu - b nhi), so that instance b is the run
+// of salt b (a plain run is salt 0).
+// ---------------------------------------------------------------------------
+
+// Adds v to acc[idx] (shared memory) for every lane of the warp (all lanes
+// call it; idx < 0 adds nothing).  A warp whose lanes share one index (its
+// records or cells belong to one instance, the common case) adds once.
+__device__ __forceinline__ void warp_add(unsigned long long* acc, int idx, unsigned long long v) {
+  const int idx0 = __shfl_sync(0xFFFFFFFFu, idx, 0);
+  if (__all_sync(0xFFFFFFFFu, idx == idx0 || idx < 0)) {
+    unsigned long long t = idx < 0 ? 0ull : v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+    if ((threadIdx.x & 31) == 0 && t && idx0 >= 0) atomicAdd(acc + idx0, t);
+  } else if (idx >= 0 && v) {
+    atomicAdd(acc + idx, v);
+  }
+}
+
+// N^s and W^s of every instance: its offspring records (cell | side << 31,
+// a) and its unit-weight counts (a = 2^31 each), summed per block in shared
+// memory and added to the instances' records.
+__global__ void __launch_bounds__(kBlock) k_bootb_tally(const uint32_t* rec_cell,
+                                                        const uint32_t* rec_a,
+                                                        const unsigned* rcnt, int nseg,
+                                                        long long rseg, const int* ucnt,
+                                                        long long nh, int nhi, int ninst,
+                                                        BootInst* bi) {
+  __shared__ unsigned long long sn[2 * kMaxInst], sw[2 * kMaxInst];
+  for (int i = threadIdx.x; i < 2 * ninst; i += kBlock) sn[i] = sw[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kBlock) >> 5;
+  const long long cps = (rseg + kBootChunk - 1) / kBootChunk;
+  for (long long it = gw; it < (long long)nseg * cps; it += nw) {
+    const long long sg = it / cps;
+    const unsigned b0 = (unsigned)((it - sg * cps) * kBootChunk);
+    const unsigned n = min(min(rcnt[sg], (unsigned)rseg), b0 + (unsigned)kBootChunk);
+    for (unsigned b = b0; b < n; b += 32) {
+      const unsigned i = b + lane;
+      int idx = -1;
+      unsigned long long a = 0;
+      if (i < n) {
+        const uint32_t rc = __ldcs(rec_cell + sg * rseg + i);
+        idx = 2 * (int)((rc & 0x7FFFFFFFu) / (unsigned)nhi) + (int)(rc >> 31);
+        a = __ldcs(rec_a + sg * rseg + i);
+      }
+      warp_add(sn, idx, 1ull);
+      warp_add(sw, idx, a);
+    }
+  }
+  // unit counts: warps over consecutive cells
+  for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
+    const long long nu = c0 + lane;
+    const int inst = nu < nh ? (int)(nu / nhi) : -1;
+    for (int sd = 0; sd < 2; ++sd) {
+      const unsigned long long u = nu < nh ? (unsigned long long)ucnt[sd * nh + nu] : 0ull;
+      const int idx = inst < 0 ? -1 : 2 * inst + sd;
+      warp_add(sn, idx, u);
+      warp_add(sw, idx, u << 31);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * ninst; i += kBlock) {
+    if (sn[i]) atomicAdd(&bi[i >> 1].n[i & 1], sn[i]);
+    if (sw[i]) atomicAdd(&bi[i >> 1].w[i & 1], sw[i]);
+  }
+}
+
+// Each instance's shares (BootShare from its N^s, W^s), the share of a unit
+// weight and the amplitudes of the combination step.
+__global__ void __launch_bounds__(kBlock) k_bootb_share(BootInst* bi, int ninst, int fx) {
+  for (int i = blockIdx.x * kBlock + threadIdx.x; i < ninst; i += gridDim.x * kBlock) {
+    BootInst& b = bi[i];
+    BootShare sh;
+    sh.init(b.n, b.w, fx);
+    b.ratio[0] = sh.ratio0;
+    b.ratio[1] = sh.ratio1;
+    b.mx[0] = sh.mx0;
+    b.mx[1] = sh.mx1;
+    b.fx[0] = sh.fx0;
+    b.fx[1] = sh.fx1;
+    for (int sd = 0; sd < 2; ++sd) {
+      int kf;
+      unsigned long long rs;
+      sh.of(2147483648u, sd, kf, rs);
+      b.kf_unit[sd] = kf;
+      b.res_unit[sd] = rs;
+      b.amp[sd] = b.n[sd] > 0 ? __ddiv_rn(__dmul_rn((double)b.w[sd], 1.0 / 2147483648.0),
+                                          (double)b.n[sd])
+                              : 0.0;
+    }
+  }
+}
+
+// The unit-weight part of every cell (k_boot_unit per instance), with the
+// instances' sums of the integer parts.
+__global__ void __launch_bounds__(kBlock) k_bootb_unit(BootInst* bi, const int* ucnt,
+                                                       long long nh, int nhi, int ninst,
+                                                       int* keep0, int* keep1,
+                                                       unsigned long long* res0,
+                                                       unsigned long long* res1) {
+  __shared__ unsigned long long ks[2 * kMaxInst];
+  for (int i = threadIdx.x; i < 2 * ninst; i += kBlock) ks[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long gw = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * kBlock) >> 5;
+  for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
+    const long long nu = c0 + lane;
+    const int inst = nu < nh ? (int)(nu / nhi) : -1;
+    for (int sd = 0; sd < 2; ++sd) {
+      unsigned long long kf = 0;
+      if (inst >= 0) {
+        const int u = ucnt[sd * nh + nu];
+        const BootInst& b = bi[inst];
+        kf = (unsigned long long)u * (unsigned long long)b.kf_unit[sd];
+        (sd ? keep1 : keep0)[nu] = (int)kf;
+        (sd ? res1 : res0)[nu] = (unsigned long long)u * b.res_unit[sd];
+      }
+      warp_add(ks, inst < 0 ? -1 : 2 * inst + sd, kf);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * ninst; i += kBlock)
+    if (ks[i]) atomicAdd(&bi[i >> 1].keep[i & 1], ks[i]);
+}
+
+// Per instance and side: the residual total R (from the inclusive prefix
+// over all cells), N_r = N - sum floor(q) draws (none without a residual),
+// and the exclusive prefix of the draws over (instance, side) pairs; the
+// run's counters get the totals.  One block.
+__global__ void __launch_bounds__(kBlock) k_bootb_plan(Counters* c, BootInst* bi,
+                                                       const unsigned long long* pre0,
+                                                       const unsigned long long* pre1,
+                                                       int ninst, int nhi,
+                                                       unsigned long long* dpre) {
+  __shared__ unsigned long long red[kBlock / 32 + 1];
+  const int i = threadIdx.x;  // ninst <= kBlock
+  unsigned long long nr[2] = {0, 0};
+  if (i < ninst) {
+    BootInst& b = bi[i];
+    const long long first = (long long)i * nhi, last = first + nhi - 1;
+    for (int sd = 0; sd < 2; ++sd) {
+      const unsigned long long* pre = sd ? pre1 : pre0;
+      const unsigned long long base = first > 0 ? pre[first - 1] : 0ull;
+      const unsigned long long R = pre[last] - base;
+      b.base[sd] = base;
+      b.R[sd] = R;
+      nr[sd] = (R > 0 && b.n[sd] > b.keep[sd]) ? b.n[sd] - b.keep[sd] : 0ull;
+      b.nr[sd] = nr[sd];
+    }
+  }
+  unsigned long long total;
+  const unsigned long long ex = block_exscan(nr[0] + nr[1], red, total);
+  if (i < ninst) {
+    dpre[2 * i] = ex;
+    dpre[2 * i + 1] = ex + nr[0];
+  }
+  if (i == 0) {
+    dpre[2 * ninst] = total;
+    for (int sd = 0; sd < 2; ++sd) {
+      unsigned long long k = 0, r = 0, R = 0;
+      for (int j = 0; j < ninst; ++j) {
+        k += bi[j].keep[sd];
+        r += bi[j].nr[sd];
+        R += bi[j].R[sd];
+      }
+      c->boot_keep[sd] = k;
+      c->boot_nr[sd] = r;
+      c->boot_R[sd] = R;
+    }
+  }
+}
+
+// The residual draws of all instances: draw i belongs to the (instance,
+// side) pair whose prefix range holds it and is that pair's draw d; its cell
+// is the first of the instance whose residual prefix (less base) exceeds
+// U = floor(r R / 2^64).
+__global__ void __launch_bounds__(kBlock) k_bootb_draw(
+    const Counters* c, const BootInst* bi, const unsigned long long* dpre,
+    const unsigned long long* pre0, const unsigned long long* pre1, int ninst, int nhi,
+    int* keep0, int* keep1, uint32_t key0, uint32_t key1, int epoch_delta) {
+  __shared__ unsigned long long sp[2 * kMaxInst + 1];
+  const int np = 2 * ninst;
+  for (int i = threadIdx.x; i <= np; i += kBlock) sp[i] = dpre[i];
+  __syncthreads();
+  const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
+  const unsigned long long total = sp[np];
+  for (unsigned long long i = (unsigned long long)blockIdx.x * kBlock + threadIdx.x; i < total;
+       i += (unsigned long long)gridDim.x * kBlock) {
+    int a = 0, z = np;  // the pair with sp[a] <= i < sp[a + 1]
+    while (z - a > 1) {
+      const int m = (a + z) >> 1;
+      if (sp[m] <= i) a = m; else z = m;
+    }
+    const int inst = a >> 1, side = a & 1;
+    const unsigned long long d = i - sp[a];
+    const uint4 r = philox((uint32_t)d, (uint32_t)inst, kStepBoot,
+                           (uint32_t)((epoch << 1) | (unsigned long long)side), key0, key1);
+    const unsigned long long r64 = ((unsigned long long)r.y << 32) | r.x;
+    const BootInst& b = bi[inst];
+    // U + base < the prefix at the instance's last cell, which therefore
+    // bounds the search
+    const unsigned long long U = __umul64hi(r64, b.R[side]) + b.base[side];
+    const unsigned long long* pre = side ? pre1 : pre0;
+    int lo = inst * nhi, hi = lo + nhi - 1;
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo) >> 1);
+      if (pre[mid] > U) hi = mid; else lo = mid + 1;
+    }
+    atomicAdd((side ? keep1 : keep0) + lo, 1);
+  }
+}
+
+// k_boot_combine per instance: the amplitudes of the cell's instance and the
+// rounding counted by (instance << 32) | (cell within the instance).
+__global__ void __launch_bounds__(kBlock) k_bootb_combine(const Counters* c, const BootInst* bi,
+                                                          long long nh, int nhi,
+                                                          const int* keep0, const int* keep1,
+                                                          int* grid, uint32_t key0,
+                                                          uint32_t key1, int epoch_delta) {
+  const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
+  for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
+       nu += (long long)gridDim.x * kBlock) {
+    const int inst = (int)(nu / nhi);
+    const BootInst& b = bi[inst];
+    const double m = __dsub_rn(__dmul_rn((double)keep0[nu], b.amp[0]),
+                               __dmul_rn((double)keep1[nu], b.amp[1]));
+    const double am = fabs(m);
+    const double fl = floor(am);
+    const uint4 r = philox((uint32_t)(nu - (long long)inst * nhi), (uint32_t)inst, kStepRound,
+                           (uint32_t)epoch, key0, key1);
+    const double u = u53(r.x, r.y);
+    const long long cnt = (long long)fl + (u < __dsub_rn(am, fl) ? 1 : 0);
+    grid[nu] = (int)(m < 0 ? -cnt : cnt);
+  }
+}
+
 // wp: the weighted histogram (Eq. piecewise_constant_function, weights in
 // fixed point 2^-31) rounded by Alg. 3: floor(|m|) particles plus one with
 // probability |m| - floor(|m|), sign of m, the uniform of the draw
-// (nu, ROUND, epoch) as for sp2.
-__global__ void __launch_bounds__(kBlock) k_wp_round(const Counters* c, long long nh,
+// ((b << 32) | cell within instance b, ROUND, epoch) as for sp2 (b = 0 in a
+// plain run).
+__global__ void __launch_bounds__(kBlock) k_wp_round(const Counters* c, long long nh, int nhi,
                                                      const long long* wsum, int* grid,
                                                      uint32_t key0, uint32_t key1,
                                                      int epoch_delta) {
@@ -552,7 +835,8 @@ __global__ void __launch_bounds__(kBlock) k_wp_round(const Counters* c, long lon
     const double m = __dmul_rn((double)wsum[nu], 1.0 / 2147483648.0);
     const double am = fabs(m);
     const double fl = floor(am);
-    const uint4 r = philox((uint32_t)nu, (uint32_t)((unsigned long long)nu >> 32), kStepRound,
+    const int inst = (int)(nu / nhi);
+    const uint4 r = philox((uint32_t)(nu - (long long)inst * nhi), (uint32_t)inst, kStepRound,
                            (uint32_t)epoch, key0, key1);
     const double u = u53(r.x, r.y);
     const long long cnt = (long long)fl + (u < __dsub_rn(am, fl) ? 1 : 0);
@@ -800,11 +1084,50 @@ cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
   return cudaGetLastError();
 }
 
+// sp2 in a batch: every instance bootstrapped on its own (Alg. 2 per
+// instance and side), in the same launches.
+cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
+  const long long nh = c->nh, nb = c->scan_blocks;
+  const int ni = c->ninst, nhi = (int)c->nhi;
+  const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
+  const int fx = c->cfg.precision == WBRW_FP32;
+  cudaError_t e = launch_zero(c, c->boot_inst, (size_t)ni * sizeof(BootInst));
+  if (e != cudaSuccess) return e;
+  k_bootb_tally<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->rec_cell, c->rec_a, c->rcnt,
+                                                          c->nseg, c->rseg, c->boot_ucnt, nh,
+                                                          nhi, ni, c->boot_inst);
+  k_bootb_share<<<1, kBlock, 0, c->stream>>>(c->boot_inst, ni, fx);
+  k_bootb_unit<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->boot_inst, c->boot_ucnt, nh, nhi, ni,
+                                                         c->boot_keep[0], c->boot_keep[1],
+                                                         c->boot_res[0], c->boot_res[1]);
+  k_boot_bin<true><<<grid_cap(c, kBootBinBatchBlocks), kBlock, 0, c->stream>>>(
+      c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg, c->boot_keep[0], c->boot_keep[1],
+      c->boot_res[0], c->boot_res[1], fx, c->boot_inst, ni, nhi);
+  c->launches += 4;
+  for (int s = 0; s < 2; ++s) {
+    k_u64_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
+    k_u64_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, nb, &c->cnt->boot_R[s]);
+    k_u64_c<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
+    c->launches += 3;
+  }
+  k_bootb_plan<<<1, kBlock, 0, c->stream>>>(c->cnt, c->boot_inst, c->boot_res[0], c->boot_res[1],
+                                            ni, nhi, c->boot_dpre);
+  k_bootb_draw<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(
+      c->cnt, c->boot_inst, c->boot_dpre, c->boot_res[0], c->boot_res[1], ni, nhi,
+      c->boot_keep[0], c->boot_keep[1], key0, key1, epoch_delta);
+  k_bootb_combine<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->cnt, c->boot_inst, nh, nhi,
+                                                            c->boot_keep[0], c->boot_keep[1],
+                                                            c->buf.grid, key0, key1, epoch_delta);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
 // Called after the records of the period are written and tallied.
 // The resampling kernels read the epoch of the histogram they make from the
 // device period state (the id base of the particles just binned, plus
 // epoch_delta), so that a captured period replays with the right streams.
 cudaError_t launch_boot(Ctx* c, int epoch_delta) {
+  if (c->ninst > 1) return launch_boot_batch(c, epoch_delta);
   const long long nh = c->nh, nb = c->scan_blocks;
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
   const int g = grid_cap(c, 8);
@@ -813,9 +1136,9 @@ cudaError_t launch_boot(Ctx* c, int epoch_delta) {
                                                         c->boot_keep[1], c->boot_res[0],
                                                         c->boot_res[1], fx);
   c->launches++;
-  k_boot_bin<<<g, kBlock, 0, c->stream>>>(c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg,
-                                          c->boot_keep[0], c->boot_keep[1], c->boot_res[0],
-                                          c->boot_res[1], c->cfg.precision == WBRW_FP32);
+  k_boot_bin<false><<<grid_cap(c, kBootBinBlocks), kBlock, 0, c->stream>>>(
+      c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg, c->boot_keep[0], c->boot_keep[1],
+      c->boot_res[0], c->boot_res[1], fx, nullptr, 1, (int)c->nhi);
   c->launches++;
   for (int s = 0; s < 2; ++s) {
     k_u64_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
@@ -825,9 +1148,9 @@ cudaError_t launch_boot(Ctx* c, int epoch_delta) {
   }
   k_boot_guide<<<(2 * (kGuide + 1) + kBlock - 1) / kBlock, kBlock, 0, c->stream>>>(
       c->cnt, nh, c->boot_res[0], c->boot_res[1], c->boot_guide);
-  k_boot_draw<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_res[0], c->boot_res[1],
-                                           c->boot_keep[0], c->boot_keep[1], c->boot_guide, key0,
-                                           key1, epoch_delta);
+  k_boot_draw<<<g, kBlock, 0, c->stream>>>(
+      c->cnt, nh, c->boot_res[0], c->boot_res[1], c->boot_keep[0], c->boot_keep[1], c->boot_guide,
+      key0, key1, epoch_delta);
   k_boot_combine<<<g, kBlock, 0, c->stream>>>(c->cnt, nh, c->boot_keep[0], c->boot_keep[1],
                                               c->buf.grid, key0, key1, epoch_delta);
   c->launches += 3;
@@ -836,8 +1159,8 @@ cudaError_t launch_boot(Ctx* c, int epoch_delta) {
 
 cudaError_t launch_wp_round(Ctx* c, int epoch_delta) {
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
-  k_wp_round<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->cnt, c->nh, c->tmp_wsum, c->buf.grid,
-                                                       key0, key1, epoch_delta);
+  k_wp_round<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->cnt, c->nh, (int)c->nhi, c->tmp_wsum,
+                                                       c->buf.grid, key0, key1, epoch_delta);
   c->launches++;
   return cudaGetLastError();
 }

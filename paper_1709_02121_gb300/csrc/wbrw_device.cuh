@@ -322,7 +322,8 @@ struct KP {
   uint32_t* rec_a;
   unsigned* rcnt;
   unsigned rseg;
-  int* ucnt;                 // sp2: unit-weight particles per (side, cell), side-major
+  int* ucnt;                 // sp2: unit-weight particles per (side, cell of any instance),
+                             // side-major (side stride nhi ninst)
   int* grid;
   long long* wsum;
   const uint32_t* nz_cell;
@@ -773,7 +774,7 @@ __device__ void emit_child_final(const KP<P>& p, WarpCounts& wc, Acc& acc, int i
       set_err(p.cnt, ERR_CAP_RECORDS);
       return;
     }
-    put_record<P>(p, acc, (size_t)g * p.rseg + r, cell, w);
+    put_record<P>(p, acc, (size_t)g * p.rseg + r, cbase + cell, w);
   } else {  // DST_ARRAY
     const unsigned long long slot = atomicAdd(&p.cnt->n, 1ull);
     if (slot >= (unsigned long long)p.capacity) { set_err(p.cnt, ERR_CAP_PARTICLES); return; }
@@ -1489,7 +1490,8 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
     }
     const unsigned grp = __match_any_sync(kFull, key);
     if (key != ~0u && lane == __ffs(grp) - 1)
-      atomicAdd(p.ucnt + (size_t)(key & 1u) * (size_t)p.nhi + (key >> 1), __popc(grp));
+      atomicAdd(p.ucnt + (size_t)(key & 1u) * ((size_t)p.nhi * p.ninst) + (key >> 1),
+                __popc(grp));
   } else {  // DST_BIN2: one record per in-grid particle of nonzero weight
     int cell = -1;
     if (act) {
@@ -1503,7 +1505,7 @@ __device__ __forceinline__ void flight_tile(const KP<P>& p, WarpCounts& wc, Acc&
         if (g >= (unsigned)p.nseg || off >= p.rseg)
           set_err(p.cnt, ERR_CAP_RECORDS);
         else
-          put_record<P>(p, acc, (long long)g * p.rseg + (long long)off, cell, w);
+          put_record<P>(p, acc, (long long)g * p.rseg + (long long)off, cbase + cell, w);
       }
       __syncwarp();
       if (lane == 0) wc.r += __popc(bal);

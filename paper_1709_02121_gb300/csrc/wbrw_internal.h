@@ -87,6 +87,23 @@ struct Counters {
   int pad[2];
 };
 
+// The signed bootstrap of a batch (sp2, Alg. 2 per instance and side): one
+// record per instance in device memory.  The counts and weight sums come
+// from the instance's records and unit-weight counts, the shares from them,
+// the residual prefix is taken over the cells of all instances (base: its
+// value before the instance's first cell).
+struct BootInst {
+  unsigned long long n[2], w[2];     // N^s and W^s (Q1.31)
+  unsigned long long keep[2];        // sum of floor(q_i)
+  unsigned long long base[2], R[2];  // residual prefix before the instance's cells; its total
+  unsigned long long nr[2];          // the N_r^s residual draws
+  double ratio[2], amp[2];           // N^s / W^s; (W^s 2^-31) / N^s
+  unsigned long long mx[2];          // floor(N^s 2^64 / W^s) where the fixed-point shares apply
+  int fx[2];
+  int kf_unit[2];                    // the share of a unit weight: integer part
+  unsigned long long res_unit[2];    //   and Q0.32 residual
+};
+
 // Rounds of a captured period whose event kernel a graph replay can time,
 // and launches each profiling buffer keeps.
 constexpr int kProfRounds = 64;
@@ -213,6 +230,8 @@ struct Ctx {
   unsigned long long* boot_res[2];
   int* boot_ucnt;     // sp2: regenerated (unit-weight) particles per side and cell, 2 x nh
   int* boot_guide;    // sp2: 2 x (kGuide + 1) guide-table entries of the draws
+  BootInst* boot_inst;             // sp2 batches: per-instance bootstrap records
+  unsigned long long* boot_dpre;   //   and the exclusive prefix of their draws (2 ninst + 1)
   // state
   int state;  // 0 = particles in the arrays, 1 = histogram (grid + nz lists)
   long long step;
@@ -292,6 +311,8 @@ cudaError_t launch_scan_tangent(Ctx*);
 // (dT/dH, dT/dw) of every instance from the tangent histogram, into
 // c->inst_grad.
 cudaError_t launch_transmission_gradients(Ctx*);
+// sp2: the bootstrap of the period's records and unit counts into the grid
+// (a batch bootstraps every instance on its own).
 cudaError_t launch_boot(Ctx*, int epoch_delta);
 // wp: Alg. 3's rounding of the weighted histogram tmp_wsum into the grid.
 cudaError_t launch_wp_round(Ctx*, int epoch_delta);

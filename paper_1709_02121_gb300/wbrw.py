@@ -551,7 +551,7 @@ class Simulation:
 
 
 class Batch(Simulation):
-    """Many independent problems in the same launches (sp1 only).
+    """Many independent problems in the same launches (any strategy).
 
     ``wl`` gives the shared configuration (precision, dt, grid, seed, ...);
     ``instances`` is a list of dicts with keys H, w, xc, x0, sigma_x, k0,

@@ -131,9 +131,51 @@ def test_fused_schedule_matches_oracle_per_instance():
         assert np.all(np.abs(xi[a] - ox[c2]) <= REL * np.maximum(1.0, np.abs(ox[c2]))), i
 
 
+@pytest.mark.parametrize("strategy", ["sp2", "wp"])
+def test_weighted_strategies_match_oracle_per_instance(strategy):
+    """sp2 bootstraps each instance on its own (Alg. 2 per instance and side,
+    its shares from the instance's N^s and W^s) and wp rounds each instance's
+    weighted histogram; the residual draws and the roundings carry the
+    instance salt.  FP64: every instance's histogram equals the salted
+    oracle's after each period, the sp2 filter's totals are the sums of the
+    instances' (the empty instance and the one with H < 0 included)."""
+    wl = workloads.scaled(BASE, strategy=strategy)
+    b = batch_of(wl, INSTANCES)
+    ors = [oracle_of(wl, i, v) for i, v in enumerate(INSTANCES)]
+    for period in range(3):
+        b.run(5)
+        g = b.grid_counts()
+        for i, o in enumerate(ors):
+            o.step(5)
+            o.annihilate()
+            assert np.array_equal(g[i], o.grid()), (period, i)
+        if strategy == "sp2":
+            c = b.counters()
+            st = [o.boot_stats() for o in ors]
+            for key, name, side in (("boot_nplus", "n", 0), ("boot_nminus", "n", 1),
+                                    ("boot_nrplus", "nr", 0), ("boot_nrminus", "nr", 1),
+                                    ("boot_wplus", "wfix", 0), ("boot_wminus", "wfix", 1)):
+                assert c[key] == sum(int(s_[name][side]) for s_ in st), (period, key)
+    c = b.counters()
+    leds = [o.ledger() for o in ors]
+    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps"):
+        assert c[key] == sum(led[key] for led in leds), key
+    b.run(2)
+    x, k, s, w, pid, inst = b.particles()
+    for i, o in enumerate(ors):
+        o.step(2)
+        pi, xi, wi = split((pid, x, w), inst, i)
+        ox, _, ow, opid = o.particles()
+        a, c2 = np.argsort(pi, kind="stable"), np.argsort(opid, kind="stable")
+        assert np.array_equal(pi[a], opid[c2]), i
+        assert np.all(np.abs(xi[a] - ox[c2]) <= REL * np.maximum(1.0, np.abs(ox[c2]))), i
+        assert np.all(np.abs(wi[a] - ow[c2]) <= REL * np.maximum(1.0, np.abs(ow[c2]))), i
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_instances_do_not_interact(precision):
-    wl = workloads.scaled(BASE, precision=precision)
+@pytest.mark.parametrize("strategy", ["sp1", "sp2", "wp"])
+def test_instances_do_not_interact(precision, strategy):
+    wl = workloads.scaled(BASE, precision=precision, strategy=strategy)
     full = batch_of(wl, INSTANCES)
     prefix = batch_of(wl, INSTANCES[:2])
     full.run(10)
@@ -165,8 +207,6 @@ def test_batch_arguments_are_checked():
     from paper_1709_02121_gb300 import WbrwError
     with pytest.raises(WbrwError):   # more initial particles than slots
         batch_of(BASE, INSTANCES, capacity=5000)
-    with pytest.raises((WbrwError, ValueError)):   # batches are sp1 only
-        batch_of(workloads.scaled(BASE, strategy="sp2"), INSTANCES)
     with pytest.raises(WbrwError):   # a rate below the majorant C/2
         batch_of(BASE, [dict(INSTANCES[0], gamma0=0.3)])
     with pytest.raises((WbrwError, ValueError)):   # too many instances
