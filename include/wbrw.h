@@ -341,6 +341,21 @@ wbrw_status wbrw_profile_read_events(wbrw_ctx* ctx, double* total_ms,
  * switches profiling on or off captures its period again. */
 wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
 
+/* Schedule of the periods that regenerate from the histogram (sp1), in
+ * contexts whose kernels can run a period as one launch: the 2D FP32
+ * contexts with the static potential and no event log (tangent mode
+ * included) and the FP32 4D contexts.  enable = 1 (the default): the first
+ * wave (or waves) and every event round of a period run in one kernel
+ * launch, each warp on its own candidate segments (Alg. 1 over the period,
+ * the resampling of Sec. 4.3 after it).  enable = 0: the launch-per-round
+ * schedule, a first-wave launch and one event launch per round.  The
+ * results are the same bit for bit (random numbers are keyed by particle
+ * and interval); only the launches and the time differ.  Other contexts
+ * accept the call and always run launch per round.  Takes effect from the
+ * next period; releases captured graphs (synchronises the stream).
+ * WBRW_ERR_ARG for a NULL context, WBRW_ERR_STATE after a failure. */
+wbrw_status wbrw_one_launch_periods(wbrw_ctx* ctx, int enable);
+
 /* Launch shape.  Neither knob changes any result (random numbers are keyed
  * by particle and interval, and every count is an integer sum), only speed:
  *   blocks_per_sm : resident 256-thread blocks per SM of the particle
@@ -356,10 +371,12 @@ wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
  *                   processed one event per lockstep pass for this many
  *                   passes (0..WBRW_TUNE_PASSES_MAX, default 3); what remains
  *                   is finished by one recursive pass.  The 2D FP32
- *                   contexts with four blocks per SM (above) finish every
- *                   such segment in lockstep passes inside the event kernel
+ *                   contexts with the static potential and no event log
+ *                   (those with four blocks per SM above, and the same in
+ *                   tangent mode) and the FP32 4D contexts finish every such
+ *                   segment in lockstep passes inside the event kernel
  *                   itself, so there event_passes changes nothing; their sp1
- *                   periods run in one launch (first wave and event rounds
+ *                   periods run in one launch (first waves and event rounds
  *                   together), at most three blocks per SM.
  * wbrw_set_tuning takes effect from the next call and releases captured
  * graphs; out-of-range values (including blocks_per_sm above the context's

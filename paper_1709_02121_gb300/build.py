@@ -19,9 +19,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwbrw.so")
 SOURCES = ["wbrw_fp32.cu", "wbrw_fp32_lean.cu", "wbrw_fp32_lean_batch.cu", "wbrw_fp64.cu",
-           "wbrw_fp32_4d.cu",
-           "wbrw_fp64_4d.cu",
-           "wbrw_fp32_grad.cu", "wbrw_fp64_grad.cu",
+           "wbrw_fp32_4d.cu", "wbrw_fp64_4d.cu",
+           "wbrw_fp32_grad.cu", "wbrw_fp32_grad_lean.cu", "wbrw_fp64_grad.cu",
            "wbrw_common.cu", "wbrw_api.cu", "wbrw_probe.cu"]
 HEADERS = ["wbrw_device.cuh", "wbrw_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -29,7 +29,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 struct Layout {
   size_t counters, cpid, fq0, fq1, eq0, eq1, dq0, dq1, nz_cell, nz_start, tile_nz, scan_bsum,
       scan_bnz, tmp_grid, tmp_wsum, obs_density, obs_marg, obs_col, obs_scalar, rec_cell,
-      rec_a, keep0, keep1, res0, res1, ucnt, guide, binst, dpre, seg_counts, cnt_save, tabs,
+      rec_a, keep0, keep1, res0, res1, ucnt, guide, binst, dpre, bguide, seg_counts, cnt_save, tabs,
       cinst, obs_red, tab_A, tab_xmax, tab_xi0, tab_xi1, tab_cdf0, tab_cdf1, tab_guide0,
       tab_guide1, dgrid0, dgrid1, tnz_cell, tnz_start, tnz_tau, ttile_nz, total;
   long long qcap, ecap, dcap, rec_cap, scan_blocks, tile_cap;
@@ -146,6 +146,7 @@ Layout layout(const wbrw_config* c, int ninst, long long capacity) {
   L.guide = take(sp2 ? (size_t)2 * (kGuide + 1) * 4 : 0);
   L.binst = take(sp2 && ninst > 1 ? (size_t)ninst * sizeof(BootInst) : 0);
   L.dpre = take(sp2 && ninst > 1 ? (size_t)(2 * ninst + 1) * 8 : 0);
+  L.bguide = take(sp2 && ninst > 1 ? (size_t)2 * ninst * (kGuideB + 1) * 4 : 0);
   L.tabs = take(kTabBytes);
   L.cinst = take(ninst > 1 ? (size_t)capacity * 4 : 0);
   const bool d4 = c->dim == 4;
@@ -224,7 +225,10 @@ wbrw_status cuda_check(wbrw_ctx* c, cudaError_t e, const char* what) {
 }
 
 const Driver* drv(const wbrw_ctx* c) {
-  if (c->lean) return c->ninst > 1 ? driver_fp32_lean_batch() : driver_fp32_lean();
+  if (c->lean) {
+    if (c->cfg.tangent) return driver_fp32_grad_lean();
+    return c->ninst > 1 ? driver_fp32_lean_batch() : driver_fp32_lean();
+  }
   return drv_for(c->cfg.precision, c->cfg.dim, c->cfg.tangent);
 }
 
@@ -678,8 +682,8 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->dcap = L.dcap;
   c->rec_cap = L.rec_cap;
   c->passes = 3;
-  c->lean = c->cfg.precision == WBRW_FP32 && c->cfg.dim == 2 && !c->cfg.tangent &&
-            ncomp == 0 && !c->buf.event_log;
+  c->one_launch = 1;
+  c->lean = c->cfg.precision == WBRW_FP32 && c->cfg.dim == 2 && ncomp == 0 && !c->buf.event_log;
   c->max_bps = drv(c)->max_bps;
   set_shape(c, c->max_bps);
   c->nz_cell = (uint32_t*)(base + L.nz_cell);
@@ -705,6 +709,7 @@ wbrw_status create(const wbrw_config* config, const wbrw_potential* pot, int nin
   c->boot_guide = (int*)(base + L.guide);
   c->boot_inst = (BootInst*)(base + L.binst);
   c->boot_dpre = (unsigned long long*)(base + L.dpre);
+  c->boot_bguide = (int*)(base + L.bguide);
   c->inst_tab = base + L.tabs;
   c->inst_slot = (unsigned long long*)(base + L.tabs + kTabSlotOff);
   c->inst_na = (double*)(base + L.tabs + kTabNaOff);
@@ -1160,6 +1165,17 @@ wbrw_status wbrw_get_tuning(wbrw_ctx* c, wbrw_tuning* out) {
   return WBRW_OK;
 }
 
+wbrw_status wbrw_one_launch_periods(wbrw_ctx* c, int enable) {
+  if (!c) return WBRW_ERR_ARG;
+  if (c->failed) return WBRW_ERR_STATE;
+  if ((enable ? 1 : 0) != c->one_launch) {
+    WBRW_TRY(c, cudaStreamSynchronize(c->stream), "synchronise");
+    drop_graphs(c);
+    c->one_launch = enable ? 1 : 0;
+  }
+  return WBRW_OK;
+}
+
 wbrw_status wbrw_set_tuning(wbrw_ctx* c, const wbrw_tuning* t) {
   if (!c || !t) return WBRW_ERR_ARG;
   if (c->failed) return WBRW_ERR_STATE;
@@ -1223,9 +1239,9 @@ wbrw_status wbrw_autotune(wbrw_ctx* c, int trials, wbrw_tuning* best, double* ms
   wbrw_status st = WBRW_OK;
   if (ms_table)  // shapes beyond what this context's kernels are built for
     for (int i = 0; i < kMaxBlocksPerSm * (kMaxPasses + 1); ++i) ms_table[i] = -1.0;
-  // the lean kernels finish deferred segments inside the event kernel:
-  // event_passes changes nothing there, and only 0 is timed
-  const int max_pz = c->lean ? 0 : kMaxPasses;
+  // kernels that finish deferred segments inside the event kernel: there
+  // event_passes changes nothing, and only 0 is timed
+  const int max_pz = drv(c)->inline_drain ? 0 : kMaxPasses;
   for (int b = 1; b <= c->max_bps && st == WBRW_OK; ++b) {
     for (int pz = 0; pz <= max_pz && st == WBRW_OK; ++pz) {
       set_shape(c, b);

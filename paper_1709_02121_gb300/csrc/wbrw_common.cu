@@ -385,10 +385,22 @@ __global__ void __launch_bounds__(kBlock) k_boot_unit(Counters* c, const int* uc
   }
 }
 
+// Per-key sums of a warp: every lane calls with its key (-1: none) and its
+// value v < 2^32; the first lane of each key's group adds the group's sum to
+// acc[key] (shared memory), one atomic per key and warp.  (The sum is taken
+// in 16-bit halves, so that 32 values cannot overflow it.)
+__device__ __forceinline__ void warp_add(unsigned long long* acc, int key, unsigned v) {
+  const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
+  if (key < 0) return;
+  const unsigned lo = __reduce_add_sync(grp, v & 0xFFFFu), hi = __reduce_add_sync(grp, v >> 16);
+  const unsigned long long t = ((unsigned long long)hi << 16) + lo;
+  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1 && t) atomicAdd(acc + key, t);
+}
+
 // The offspring records' shares added to the cell tallies.  BATCH: the
 // records of all instances of a batch, each with its instance's share (the
-// instance of global cell nu is nu / nhi); the sums of the integer parts go
-// to the instances' records instead of the run's counters.
+// instance of global cell nu is nu / nhi); the instances' sums of the
+// integer parts are then taken over their cells (k_bootb_keep), not here.
 template <bool BATCH>
 __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBinBlocks)
     k_boot_bin(Counters* c, const uint32_t* rec_cell, const uint32_t* rec_a, const unsigned* rcnt,
@@ -396,13 +408,9 @@ __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBin
                unsigned long long* res1, int fx, BootInst* bi, int ninst, int nhi) {
   __shared__ unsigned long long red[kBlock / 32 + 1];
   __shared__ BootShare tab[BATCH ? kMaxInst : 1];
-  __shared__ unsigned long long ksum[BATCH ? 2 * kMaxInst : 1];
   BootShare sh;
   if constexpr (BATCH) {
-    for (int i = threadIdx.x; i < ninst; i += kBlock) {
-      tab[i] = share_of(bi[i]);
-      ksum[2 * i] = ksum[2 * i + 1] = 0;
-    }
+    for (int i = threadIdx.x; i < ninst; i += kBlock) tab[i] = share_of(bi[i]);
     __syncthreads();
   } else {
     sh.init(c, fx);
@@ -461,19 +469,13 @@ __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBin
         const uint32_t cell = key >> 1;
         if (kf) atomicAdd((side ? keep1 : keep0) + cell, kf);
         if (res) atomicAdd((side ? res1 : res0) + cell, res);
-        if constexpr (BATCH) {
-          if (kf) atomicAdd(&ksum[2 * (cell / (unsigned)nhi) + side], (unsigned long long)kf);
-        } else {
+        if constexpr (!BATCH) {
           if (side) ks1 += (unsigned long long)kf; else ks0 += (unsigned long long)kf;
         }
       }
     }
   }
-  if constexpr (BATCH) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < 2 * ninst; i += kBlock)
-      if (ksum[i]) atomicAdd(&bi[i >> 1].keep[i & 1], ksum[i]);
-  } else {
+  if constexpr (!BATCH) {
     for (int s = 0; s < 2; ++s) {
       unsigned long long t;
       block_exscan(s ? ks1 : ks0, red, t);
@@ -584,19 +586,13 @@ __global__ void __launch_bounds__(kBlock) k_boot_combine(const Counters* c, long
 // of salt b (a plain run is salt 0).
 // ---------------------------------------------------------------------------
 
-// Adds v to acc[idx] (shared memory) for every lane of the warp (all lanes
-// call it; idx < 0 adds nothing).  A warp whose lanes share one index (its
-// records or cells belong to one instance, the common case) adds once.
-__device__ __forceinline__ void warp_add(unsigned long long* acc, int idx, unsigned long long v) {
-  const int idx0 = __shfl_sync(0xFFFFFFFFu, idx, 0);
-  if (__all_sync(0xFFFFFFFFu, idx == idx0 || idx < 0)) {
-    unsigned long long t = idx < 0 ? 0ull : v;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
-    if ((threadIdx.x & 31) == 0 && t && idx0 >= 0) atomicAdd(acc + idx0, t);
-  } else if (idx >= 0 && v) {
-    atomicAdd(acc + idx, v);
-  }
+// Adds one run's counts and weight sums of instance i (both sides) to the
+// shared per-instance sums.
+__device__ __forceinline__ void flush_tally(unsigned long long* sn, unsigned long long* sw, int i,
+                                            unsigned long long c0, unsigned long long c1,
+                                            unsigned long long w0, unsigned long long w1) {
+  if (c0) { atomicAdd(sn + 2 * i, c0); atomicAdd(sw + 2 * i, w0); }
+  if (c1) { atomicAdd(sn + 2 * i + 1, c1); atomicAdd(sw + 2 * i + 1, w1); }
 }
 
 // N^s and W^s of every instance: its offspring records (cell | side << 31,
@@ -619,28 +615,62 @@ __global__ void __launch_bounds__(kBlock) k_bootb_tally(const uint32_t* rec_cell
     const long long sg = it / cps;
     const unsigned b0 = (unsigned)((it - sg * cps) * kBootChunk);
     const unsigned n = min(min(rcnt[sg], (unsigned)rseg), b0 + (unsigned)kBootChunk);
+    // a segment holds runs of one instance's records (of both signs, the
+    // pairs interleaved): runs of equal instances in consecutive lanes sum
+    // their counts and weights per side by shuffles, and a run's first lane
+    // adds them to the shared sums
+    const uint32_t* rcs = rec_cell + sg * rseg;
+    const uint32_t* ras = rec_a + sg * rseg;
     for (unsigned b = b0; b < n; b += 32) {
       const unsigned i = b + lane;
-      int idx = -1;
-      unsigned long long a = 0;
+      int inst = -1;
+      unsigned c0 = 0, c1 = 0;
+      unsigned long long w0 = 0, w1 = 0;
       if (i < n) {
-        const uint32_t rc = __ldcs(rec_cell + sg * rseg + i);
-        idx = 2 * (int)((rc & 0x7FFFFFFFu) / (unsigned)nhi) + (int)(rc >> 31);
-        a = __ldcs(rec_a + sg * rseg + i);
+        const uint32_t rc = __ldcs(rcs + i);
+        const uint32_t a = __ldcs(ras + i);
+        inst = (int)((rc & 0x7FFFFFFFu) / (unsigned)nhi);
+        if (rc >> 31) { c1 = 1; w1 = a; } else { c0 = 1; w0 = a; }
       }
-      warp_add(sn, idx, 1ull);
-      warp_add(sw, idx, a);
+      const int prev = __shfl_up_sync(0xFFFFFFFFu, inst, 1);
+      const bool head = lane == 0 || prev != inst;
+      const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+      if (heads != 0xFFFFFFFFu) {
+        const unsigned later = heads & ~((2u << lane) - 1u);
+        const int end = later ? __ffs(later) - 1 : 32;  // the next run's first lane
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const unsigned d0 = __shfl_down_sync(0xFFFFFFFFu, c0, off);
+          const unsigned d1 = __shfl_down_sync(0xFFFFFFFFu, c1, off);
+          const unsigned long long v0 = __shfl_down_sync(0xFFFFFFFFu, w0, off);
+          const unsigned long long v1 = __shfl_down_sync(0xFFFFFFFFu, w1, off);
+          if (lane + off < end) {
+            c0 += d0;
+            c1 += d1;
+            w0 += v0;
+            w1 += v1;
+          }
+        }
+      }
+      if (head && inst >= 0) flush_tally(sn, sw, inst, c0, c1, w0, w1);
     }
   }
   // unit counts: warps over consecutive cells
   for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
     const long long nu = c0 + lane;
-    const int inst = nu < nh ? (int)(nu / nhi) : -1;
+    const int inst = nu < nh ? (int)((unsigned)nu / (unsigned)nhi) : -1;
     for (int sd = 0; sd < 2; ++sd) {
-      const unsigned long long u = nu < nh ? (unsigned long long)ucnt[sd * nh + nu] : 0ull;
-      const int idx = inst < 0 ? -1 : 2 * inst + sd;
-      warp_add(sn, idx, u);
-      warp_add(sw, idx, u << 31);
+      const unsigned u = nu < nh ? (unsigned)ucnt[sd * nh + nu] : 0u;
+      const int key = inst < 0 || u == 0 ? -1 : 2 * inst + sd;
+      // the count once, the weight (u 2^31 each) from the count
+      const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
+      if (key >= 0) {
+        const unsigned t = __reduce_add_sync(grp, u);
+        if (lane == __ffs(grp) - 1) {
+          atomicAdd(sn + key, (unsigned long long)t);
+          atomicAdd(sw + key, (unsigned long long)t << 31);
+        }
+      }
     }
   }
   __syncthreads();
@@ -676,13 +706,26 @@ __global__ void __launch_bounds__(kBlock) k_bootb_share(BootInst* bi, int ninst,
   }
 }
 
-// The unit-weight part of every cell (k_boot_unit per instance), with the
-// instances' sums of the integer parts.
-__global__ void __launch_bounds__(kBlock) k_bootb_unit(BootInst* bi, const int* ucnt,
-                                                       long long nh, int nhi, int ninst,
-                                                       int* keep0, int* keep1,
-                                                       unsigned long long* res0,
+// The unit-weight part of every cell (k_boot_unit per instance).
+__global__ void __launch_bounds__(kBlock) k_bootb_unit(const BootInst* bi, const int* ucnt,
+                                                       long long nh, int nhi, int* keep0,
+                                                       int* keep1, unsigned long long* res0,
                                                        unsigned long long* res1) {
+  for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
+       nu += (long long)gridDim.x * kBlock) {
+    const BootInst& b = bi[(unsigned)nu / (unsigned)nhi];
+    const int u0 = ucnt[nu], u1 = ucnt[nh + nu];
+    keep0[nu] = u0 * b.kf_unit[0];
+    keep1[nu] = u1 * b.kf_unit[1];
+    res0[nu] = (unsigned long long)u0 * b.res_unit[0];
+    res1[nu] = (unsigned long long)u1 * b.res_unit[1];
+  }
+}
+
+// Each instance's sums of the kept integer parts, over its cells.
+__global__ void __launch_bounds__(kBlock) k_bootb_keep(BootInst* bi, const int* keep0,
+                                                       const int* keep1, long long nh, int nhi,
+                                                       int ninst) {
   __shared__ unsigned long long ks[2 * kMaxInst];
   for (int i = threadIdx.x; i < 2 * ninst; i += kBlock) ks[i] = 0;
   __syncthreads();
@@ -691,17 +734,10 @@ __global__ void __launch_bounds__(kBlock) k_bootb_unit(BootInst* bi, const int* 
   const long long nw = ((long long)gridDim.x * kBlock) >> 5;
   for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
     const long long nu = c0 + lane;
-    const int inst = nu < nh ? (int)(nu / nhi) : -1;
+    const int inst = nu < nh ? (int)((unsigned)nu / (unsigned)nhi) : -1;
     for (int sd = 0; sd < 2; ++sd) {
-      unsigned long long kf = 0;
-      if (inst >= 0) {
-        const int u = ucnt[sd * nh + nu];
-        const BootInst& b = bi[inst];
-        kf = (unsigned long long)u * (unsigned long long)b.kf_unit[sd];
-        (sd ? keep1 : keep0)[nu] = (int)kf;
-        (sd ? res1 : res0)[nu] = (unsigned long long)u * b.res_unit[sd];
-      }
-      warp_add(ks, inst < 0 ? -1 : 2 * inst + sd, kf);
+      const unsigned k = inst >= 0 ? (unsigned)(sd ? keep1 : keep0)[nu] : 0u;
+      warp_add(ks, inst < 0 || k == 0 ? -1 : 2 * inst + sd, k);
     }
   }
   __syncthreads();
@@ -756,6 +792,36 @@ __global__ void __launch_bounds__(kBlock) k_bootb_plan(Counters* c, BootInst* bi
   }
 }
 
+// Guide tables of the draws per instance and side (k_boot_guide's, on the
+// instance's cells and its prefix less base): G_j = the first cell of the
+// instance whose prefix exceeds floor(j R / 2^kGuideBitsB), G_last = the
+// instance's last cell.
+__global__ void __launch_bounds__(kBlock) k_bootb_guide(const BootInst* bi,
+                                                        const unsigned long long* pre0,
+                                                        const unsigned long long* pre1,
+                                                        int ninst, int nhi, int* guide) {
+  const int per = kGuideB + 1;
+  for (long long t = (long long)blockIdx.x * kBlock + threadIdx.x; t < 2ll * ninst * per;
+       t += (long long)gridDim.x * kBlock) {
+    const int pair = (int)(t / per), j = (int)(t - (long long)pair * per);
+    const int inst = pair >> 1, side = pair & 1;
+    const BootInst& b = bi[inst];
+    int lo = inst * nhi, hi = lo + nhi - 1;
+    if (j < kGuideB && b.nr[side] > 0) {
+      const unsigned long long th =
+          __umul64hi((unsigned long long)j << (64 - kGuideBitsB), b.R[side]) + b.base[side];
+      const unsigned long long* pre = side ? pre1 : pre0;
+      while (lo < hi) {
+        const int mid = lo + ((hi - lo) >> 1);
+        if (pre[mid] > th) hi = mid; else lo = mid + 1;
+      }
+    } else {
+      lo = hi;
+    }
+    guide[t] = lo;
+  }
+}
+
 // The residual draws of all instances: draw i belongs to the (instance,
 // side) pair whose prefix range holds it and is that pair's draw d; its cell
 // is the first of the instance whose residual prefix (less base) exceeds
@@ -763,7 +829,7 @@ __global__ void __launch_bounds__(kBlock) k_bootb_plan(Counters* c, BootInst* bi
 __global__ void __launch_bounds__(kBlock) k_bootb_draw(
     const Counters* c, const BootInst* bi, const unsigned long long* dpre,
     const unsigned long long* pre0, const unsigned long long* pre1, int ninst, int nhi,
-    int* keep0, int* keep1, uint32_t key0, uint32_t key1, int epoch_delta) {
+    const int* guide, int* keep0, int* keep1, uint32_t key0, uint32_t key1, int epoch_delta) {
   __shared__ unsigned long long sp[2 * kMaxInst + 1];
   const int np = 2 * ninst;
   for (int i = threadIdx.x; i <= np; i += kBlock) sp[i] = dpre[i];
@@ -783,11 +849,12 @@ __global__ void __launch_bounds__(kBlock) k_bootb_draw(
                            (uint32_t)((epoch << 1) | (unsigned long long)side), key0, key1);
     const unsigned long long r64 = ((unsigned long long)r.y << 32) | r.x;
     const BootInst& b = bi[inst];
-    // U + base < the prefix at the instance's last cell, which therefore
-    // bounds the search
+    // U + base < the prefix at the instance's last cell
     const unsigned long long U = __umul64hi(r64, b.R[side]) + b.base[side];
     const unsigned long long* pre = side ? pre1 : pre0;
-    int lo = inst * nhi, hi = lo + nhi - 1;
+    const int* gs = guide + (size_t)a * (kGuideB + 1);
+    const int j = (int)(r64 >> (64 - kGuideBitsB));
+    int lo = gs[j], hi = gs[j + 1];  // the cell lies in [G_j, G_{j+1}]
     while (lo < hi) {
       const int mid = lo + ((hi - lo) >> 1);
       if (pre[mid] > U) hi = mid; else lo = mid + 1;
@@ -806,7 +873,7 @@ __global__ void __launch_bounds__(kBlock) k_bootb_combine(const Counters* c, con
   const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
   for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
        nu += (long long)gridDim.x * kBlock) {
-    const int inst = (int)(nu / nhi);
+    const int inst = (int)((unsigned)nu / (unsigned)nhi);  // nh < 2^30
     const BootInst& b = bi[inst];
     const double m = __dsub_rn(__dmul_rn((double)keep0[nu], b.amp[0]),
                                __dmul_rn((double)keep1[nu], b.amp[1]));
@@ -835,7 +902,7 @@ __global__ void __launch_bounds__(kBlock) k_wp_round(const Counters* c, long lon
     const double m = __dmul_rn((double)wsum[nu], 1.0 / 2147483648.0);
     const double am = fabs(m);
     const double fl = floor(am);
-    const int inst = (int)(nu / nhi);
+    const int inst = (int)((unsigned)nu / (unsigned)nhi);  // nh < 2^30
     const uint4 r = philox((uint32_t)(nu - (long long)inst * nhi), (uint32_t)inst, kStepRound,
                            (uint32_t)epoch, key0, key1);
     const double u = u53(r.x, r.y);
@@ -1097,13 +1164,15 @@ cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
                                                           c->nseg, c->rseg, c->boot_ucnt, nh,
                                                           nhi, ni, c->boot_inst);
   k_bootb_share<<<1, kBlock, 0, c->stream>>>(c->boot_inst, ni, fx);
-  k_bootb_unit<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->boot_inst, c->boot_ucnt, nh, nhi, ni,
+  k_bootb_unit<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->boot_inst, c->boot_ucnt, nh, nhi,
                                                          c->boot_keep[0], c->boot_keep[1],
                                                          c->boot_res[0], c->boot_res[1]);
   k_boot_bin<true><<<grid_cap(c, kBootBinBatchBlocks), kBlock, 0, c->stream>>>(
       c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg, c->boot_keep[0], c->boot_keep[1],
       c->boot_res[0], c->boot_res[1], fx, c->boot_inst, ni, nhi);
-  c->launches += 4;
+  k_bootb_keep<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->boot_inst, c->boot_keep[0],
+                                                         c->boot_keep[1], nh, nhi, ni);
+  c->launches += 5;
   for (int s = 0; s < 2; ++s) {
     k_u64_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);
     k_u64_b<<<1, kBlock, 0, c->stream>>>(c->scan_bsum, nb, &c->cnt->boot_R[s]);
@@ -1112,9 +1181,13 @@ cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
   }
   k_bootb_plan<<<1, kBlock, 0, c->stream>>>(c->cnt, c->boot_inst, c->boot_res[0], c->boot_res[1],
                                             ni, nhi, c->boot_dpre);
+  c->launches++;
+  const long long ng = 2ll * ni * (kGuideB + 1);
+  k_bootb_guide<<<(unsigned)((ng + kBlock - 1) / kBlock), kBlock, 0, c->stream>>>(
+      c->boot_inst, c->boot_res[0], c->boot_res[1], ni, nhi, c->boot_bguide);
   k_bootb_draw<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(
       c->cnt, c->boot_inst, c->boot_dpre, c->boot_res[0], c->boot_res[1], ni, nhi,
-      c->boot_keep[0], c->boot_keep[1], key0, key1, epoch_delta);
+      c->boot_bguide, c->boot_keep[0], c->boot_keep[1], key0, key1, epoch_delta);
   k_bootb_combine<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->cnt, c->boot_inst, nh, nhi,
                                                             c->boot_keep[0], c->boot_keep[1],
                                                             c->buf.grid, key0, key1, epoch_delta);

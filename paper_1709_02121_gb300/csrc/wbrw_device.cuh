@@ -159,6 +159,7 @@ using P64G = PD<F64, 1, true>;
 using P32G = PD<F32, 1, true>;
 using P32L = PD<F32, 1, false, 1>;
 using P32LB = PD<F32, 1, false, 2>;
+using P32GL = PD<F32, 1, true, 2>;  // tangent mode, static potential, no event log
 
 // Resident 256-thread blocks per SM a queue kernel is built for (its launch
 // bound).  The lean FP32 kernels and the FP32 4D kernels fit 64 registers,
@@ -173,12 +174,17 @@ template <class P>
 __host__ __device__ constexpr int max_blocks_model() {
   return (!P::is64 && !P::TG && (P::LEAN || P::D == 2)) ? 4 : 3;
 }
-// The lean kernels finish their deferred segments inside the event kernel
-// (k_event below) instead of in k_cont and k_drain launches (the 4D kernels
-// measured no gain from it).
+// The lean kernels and the FP32 4D ones finish their deferred segments
+// inside the event kernel (k_event below) instead of in k_cont and k_drain
+// launches ...
 template <class P>
 __host__ __device__ constexpr bool inline_drain() {
-  return !P::is64 && !P::TG && P::LEAN;
+  return !P::is64 && (P::LEAN || (P::D == 2 && !P::TG));
+}
+// ... and run a regenerating period as one launch (k_period).
+template <class P>
+__host__ __device__ constexpr bool fused_period() {
+  return inline_drain<P>();
 }
 static_assert(max_blocks_model<P32L>() <= kMaxBlocksPerSm, "tuning range");
 
@@ -1990,8 +1996,8 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_event(const 
   if constexpr (CMP) make_pairs(1u);
   // so far the warp has made only first events' pairs
   const unsigned first_pairs = acc.events;
-  if constexpr (P::LEAN) {
-    // The lean kernels finish their warp's deferred segments here instead of
+  if constexpr (inline_drain<P>()) {
+    // These kernels finish their warp's deferred segments here instead of
     // in launches of their own: one event per lane per pass (Alg. 1 item 3,
     // offspring born inside the interval included), a segment with another
     // event in its interval appended again to the same list, until the list
@@ -2036,7 +2042,8 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_event(const 
 }
 
 // A whole resampling period in one launch (the lean models): each warp
-// runs its share of the first wave, then the event rounds over its own
+// runs its share of the first wave (in the tangent mode, then its share of
+// the tangent particles' first wave), then the event rounds over its own
 // candidate segments.  Warp g writes candidate segment g and only warp g
 // reads it, in this launch as in the launch-per-round schedule, so the
 // rounds need no barrier between warps: a warp starts its next round as
@@ -2060,6 +2067,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_period(const KP<P> p_) {
   // the first wave: candidate intervals into buffer p.eq, segment g
   unsigned ecount = wc.e;
   flight_body<P, SRC_REGEN, DST>(p, wc, acc, ecount, own ? p.eq + (long long)g * p.eseg : nullptr);
+  if constexpr (P::TG) {  // the tangent particles of the same histogram join the first wave
+    flight_body<P, SRC_TREGEN, DST>(p, wc, acc, ecount,
+                                    own ? p.eq + (long long)g * p.eseg : nullptr);
+  }
   const unsigned psteps_first = acc.psteps;
   constexpr bool CMP = !P::is64 && P::D == 1;
   constexpr unsigned kBirths = 64;
@@ -2430,7 +2441,7 @@ cudaError_t period(Ctx* c, KP<P> p, size_t cnt_bytes) {
 
 template <class P>
 cudaError_t period_any(Ctx* c, const KP<P>& p, int dst, size_t cnt_bytes) {
-  if constexpr (inline_drain<P>()) {
+  if constexpr (fused_period<P>()) {
     if (dst == DST_BIN1) return period<P, DST_BIN1>(c, p, cnt_bytes);
   }
   return cudaErrorNotSupported;
@@ -2571,8 +2582,8 @@ struct DriverImpl {
     p.len = L - l0;
     const int rounds = L > l0 ? L - l0 : 1;
     const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
-    if constexpr (inline_drain<P>()) {
-      if (src == SRC_REGEN && L > l0 && dst == DST_BIN1)
+    if constexpr (fused_period<P>()) {
+      if (c->one_launch && src == SRC_REGEN && L > l0 && dst == DST_BIN1)
         return period_any<P>(c, p, dst, cnt_bytes);
     }
     for (int r = 0; r < rounds; ++r) {
@@ -2691,7 +2702,7 @@ struct DriverImpl {
   static const Driver* get() {
     static const Driver d = {&init,   &chunk, &bin, &materialize, &pids, &tables,
                              (int)sizeof(FEntry<P>), (int)sizeof(SEntry<P>),
-                             max_blocks_model<P>()};
+                             max_blocks_model<P>(), inline_drain<P>() ? 1 : 0};
     return &d;
   }
 };

@@ -17,6 +17,8 @@ constexpr int kTabGuideBits = 8;  // 4D kick rows (FP32): guide table of 2^8 buc
 constexpr int kTabGuide = 1 << kTabGuideBits;
 constexpr int kGuideBits = 16;  // sp2 draws: guide table of 2^16 buckets per side
 constexpr int kGuide = 1 << kGuideBits;
+constexpr int kGuideBitsB = 12;  // sp2 draws of a batch: 2^12 buckets per instance and side
+constexpr int kGuideB = 1 << kGuideBitsB;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
 constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // the largest launch bound of the
                                                              // queue kernels (see max_blocks)
@@ -185,7 +187,7 @@ struct Ctx {
   double* inst_grad;              // read-out (dT/dH, dT/dw) per instance (device)
   // time-dependent potential (wbrw_init_td): components on the device
   int ncomp;
-  int lean;           // FP32 2D, static potential, no event log, no tangents
+  int lean;           // FP32 2D, static potential, no event log (tangents or not)
   void* comp_tab;
   // scratch carve-up
   Counters* cnt;
@@ -232,6 +234,7 @@ struct Ctx {
   int* boot_guide;    // sp2: 2 x (kGuide + 1) guide-table entries of the draws
   BootInst* boot_inst;             // sp2 batches: per-instance bootstrap records
   unsigned long long* boot_dpre;   //   and the exclusive prefix of their draws (2 ninst + 1)
+  int* boot_bguide;                //   and their guide tables, 2 ninst x (kGuideB + 1)
   // state
   int state;  // 0 = particles in the arrays, 1 = histogram (grid + nz lists)
   long long step;
@@ -240,6 +243,7 @@ struct Ctx {
   int failed;
   int capturing;      // a period is being captured into a CUDA graph
   int graph_on;       // wbrw_graph: replay periods from CUDA graphs
+  int one_launch;     // wbrw_one_launch_periods: fused periods where the kernels allow
   int dev_period_ok;  // the device period state equals (step, epoch)
   int ngraphs;
   PeriodGraph graphs[kMaxGraphs];
@@ -291,12 +295,14 @@ struct Driver {
   cudaError_t (*tables)(Ctx*, const double* A_host, double* xmax_host);
   int fentry_bytes, sentry_bytes;  // queue entry sizes of this model and precision
   int max_bps;                     // resident blocks per SM its queue kernels are built for
+  int inline_drain;                // its event kernel finishes deferred segments (no passes)
 };
 
 const Driver* driver_fp64();
 const Driver* driver_fp32();
 const Driver* driver_fp32_lean();
 const Driver* driver_fp32_lean_batch();
+const Driver* driver_fp32_grad_lean();
 const Driver* driver_fp64_4d();
 const Driver* driver_fp32_4d();
 const Driver* driver_fp64_grad();

@@ -39,7 +39,7 @@ SYMBOLS = ("wbrw_scratch_bytes", "wbrw_init", "wbrw_step", "wbrw_annihilate",
            "wbrw_instance_density", "wbrw_transmissions", "wbrw_particle_instances",
            "wbrw_graph", "wbrw_get_tuning", "wbrw_set_tuning", "wbrw_autotune",
            "wbrw_init4d", "wbrw_transmission_gradients", "wbrw_init_td",
-           "wbrw_philox_chain")
+           "wbrw_philox_chain", "wbrw_one_launch_periods")
 TUNE_BPS_MAX, TUNE_PASSES_MAX = 4, 6
 MAX_CAPACITY = 4293918720  # WBRW_MAX_CAPACITY: slots index in 32 bits
 MAX_INSTANCES = 256
@@ -152,6 +152,8 @@ def load(path: str = LIB_PATH):
     L.wbrw_set_tuning.argtypes = [P, P]
     L.wbrw_autotune.argtypes = [P, I, P, P]
     L.wbrw_graph.argtypes = [P, I]
+    L.wbrw_one_launch_periods.argtypes = [P, I]
+    L.wbrw_one_launch_periods.restype = I
     L.wbrw_checkpoint.argtypes = [P, P, P, P]
     L.wbrw_restore.argtypes = [P, P, LL, LL]
     L.wbrw_profile.argtypes = [P, I]
@@ -305,6 +307,10 @@ def wbrw_restore(ctx, grid_ptr, step, epoch):
 
 def wbrw_graph(ctx, enable=True):
     _check(ctx, load().wbrw_graph(ctx, 1 if enable else 0))
+
+
+def wbrw_one_launch_periods(ctx, enable=True):
+    _check(ctx, load().wbrw_one_launch_periods(ctx, 1 if enable else 0))
 
 
 def wbrw_get_tuning(ctx):
@@ -471,6 +477,11 @@ class Simulation:
     def graph(self, enable=True):
         """Replay resampling periods from CUDA graphs (needs a created stream)."""
         wbrw_graph(self.ctx, enable)
+
+    def one_launch_periods(self, enable=True):
+        """Run regenerating periods as one launch where the kernels allow
+        (the default), or launch per round (the same results)."""
+        wbrw_one_launch_periods(self.ctx, enable)
 
     def density(self):
         return wbrw_density(self.ctx, self.nx, self.nk)

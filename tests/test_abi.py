@@ -84,6 +84,7 @@ def test_init_rejects_bad_arguments_without_touching_a_gpu(lib):
     assert lib.wbrw_profile_read(None, None, None) == wbrw.ERR_ARG
     assert lib.wbrw_profile_read_events(None, None, None) == wbrw.ERR_ARG
     assert lib.wbrw_counters(None, None) == wbrw.ERR_ARG
+    assert lib.wbrw_one_launch_periods(None, 1) == wbrw.ERR_ARG
     assert lib.wbrw_last_error(None) == b"NULL context"
     lib.wbrw_destroy(None)
     # a capacity beyond the 32-bit slot limit is refused before any buffer

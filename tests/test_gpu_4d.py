@@ -159,3 +159,23 @@ def test_fp32_matches_the_two_electron_schroedinger_equation():
         z = (m - ref) / np.sqrt(se ** 2 + 1e-8)
         assert np.max(np.abs(z)) < 4.5, np.round(z, 2)
         assert np.mean(z ** 2) < 3.0, np.round(z, 2)
+
+
+
+def test_fp32_one_launch_periods_equal_the_launch_per_round_schedule(gpu):
+    """FP32 4D regenerating periods run as one launch (first wave and event
+    rounds, deferred segments finished in the rounds); the launch-per-round
+    schedule of the same periods gives the same histograms and counters bit
+    for bit."""
+    wl = workloads.scaled(WL, precision="fp32", n_alpha=20000)
+    a, b = sim_of(wl), sim_of(wl, stream=gpu.cuda.Stream())
+    b.one_launch_periods(False)
+    b.graph(True)
+    for period in range(3):
+        a.run(5)
+        b.run(5)
+        assert np.array_equal(a.grid_counts(), b.grid_counts()), period
+    ca, cb = a.counters(), b.counters()
+    for key in ("events", "kill_plus", "kill_minus", "out_plus", "out_minus", "particle_steps",
+                "particle_steps_first", "candidates", "first_pairs", "live"):
+        assert ca[key] == cb[key], key

@@ -142,19 +142,27 @@ def test_fp32_gradient_matches_the_schroedinger_equation():
         assert abs(m - ref[c]) < 4.0 * se + 0.02 * abs(ref[c]), (c, m, se, ref[c])
 
 
-def test_autograd_function_backward_is_the_tangent_replay():
+@pytest.mark.parametrize("replay", [False, True])
+def test_autograd_function_gives_the_tangent_runs_gradients(replay):
+    """One pass (the forward runs in tangent mode) or replay (the backward
+    reruns the forward in tangent mode): T is the run without tangents and
+    the gradients those of a direct tangent run."""
     import torch
     from paper_1709_02121_gb300 import grad
     wl = workloads.scaled(workloads.COLLISION_2D, precision="fp32", n_alpha=20000,
                           gamma0=2.0, resample_every=5)
     H = torch.tensor([1.0, 1.5], dtype=torch.float64, requires_grad=True)
     w = torch.tensor([0.5, 0.8], dtype=torch.float64, requires_grad=True)
-    T = grad.transmission(H, w, wl, 10, 1_000_000)
+    T = grad.transmission(H, w, wl, 10, 1_000_000, replay=replay)
     (T * torch.tensor([1.0, 2.0], dtype=torch.float64)).sum().backward()
     T2, g, _ = grad.run_batch(wl, [1.0, 1.5], [0.5, 0.8], 10, True, 1_000_000)
-    assert np.array_equal(T.detach().numpy(), T2)
+    T0, _, _ = grad.run_batch(wl, [1.0, 1.5], [0.5, 0.8], 10, False, 1_000_000)
+    assert np.array_equal(T.detach().numpy(), T2) and np.array_equal(T2, T0)
     assert np.array_equal(H.grad.numpy(), np.array([1.0, 2.0]) * g[:, 0])
     assert np.array_equal(w.grad.numpy(), np.array([1.0, 2.0]) * g[:, 1])
+    # without a gradient asked for, the forward pass runs no tangents
+    with torch.no_grad():
+        assert np.array_equal(grad.transmission(H, w, wl, 10, 1_000_000).numpy(), T0)
 
 
 @pytest.mark.parametrize("param, theta, reps", [("H", (1.0, 1.0), 48), ("w", (1.0, 0.5), 192)])
