@@ -574,6 +574,9 @@ def e2e_same_periods(sim, wl, P, steps, ckpt):
     import torch
     from paper_1709_02121_gb300 import wbrw
     grid_h, step, epoch = ckpt
+    # the observables are read into pinned host memory too
+    dens_h = torch.empty(wl["nx"] * wl["nk"], dtype=torch.float64).pin_memory()
+    marg_h = torch.empty(wl["nx"], dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
     pe0 = sim.counters()["particle_steps"]
     t0 = time.perf_counter()
@@ -585,7 +588,8 @@ def e2e_same_periods(sim, wl, P, steps, ckpt):
         if getattr(sim, "ninst", 1) > 1:
             T_last = float(sim.transmissions().mean())
         else:
-            _, _, T_last, _ = wbrw.wbrw_density(sim.ctx, wl["nx"], wl["nk"])
+            _, _, T_last, _ = wbrw.wbrw_density(sim.ctx, wl["nx"], wl["nk"], dens_h.numpy(),
+                                                marg_h.numpy())
     te = time.perf_counter() - t0
     pe = sim.counters()["particle_steps"] - pe0
     return pe / te, pe, T_last

@@ -257,8 +257,12 @@ wbrw_status wbrw_annihilate(wbrw_ctx* ctx);
  * a multiple of config.resample_every (the schedule of Sec. 4.3 with period
  * T_A).  Each period fuses regeneration, flight and histogram in one pass, so
  * particles only reach the arrays if nsteps ends between two resamplings.
- * Equivalent, bit for bit, to the same sequence of wbrw_step and
- * wbrw_annihilate.  Async. */
+ * FP64: equivalent, bit for bit, to the same sequence of wbrw_step and
+ * wbrw_annihilate.  FP32: equivalent in law; a regenerated particle takes
+ * its first candidate interval from the bits of its regeneration draw in a
+ * fused period and from a draw of its own once it is materialised in the
+ * arrays, so the two sequences draw different (equally distributed)
+ * numbers.  Async. */
 wbrw_status wbrw_run(wbrw_ctx* ctx, int nsteps);
 
 /* Observables (Eq. estimator) of the current state:
@@ -271,7 +275,9 @@ wbrw_status wbrw_run(wbrw_ctx* ctx, int nsteps);
  * probability of x1 > 0.
  * After a resampling c_nu is the grid.  Otherwise the current particles are
  * histogrammed on the fly (sp2: signed weights in Q1.31) without changing
- * the state.  Synchronises the stream. */
+ * the state.  The outputs are host memory; pinned (page-locked) buffers
+ * take the copies at full speed, pageable ones through a staging copy.
+ * Synchronises the stream. */
 wbrw_status wbrw_density(wbrw_ctx* ctx, double* density_host,
                          double* marginal_x_host, double* transmission,
                          long long* live_particles);

@@ -276,9 +276,16 @@ def wbrw_run(ctx, nsteps):
     _check(ctx, load().wbrw_run(ctx, nsteps))
 
 
-def wbrw_density(ctx, nx, nk):
-    dens = np.empty(nx * nk, np.float64)
-    marg = np.empty(nx, np.float64)
+def wbrw_density(ctx, nx, nk, dens=None, marg=None):
+    """(density, x-marginal, transmission, live particles) of the current
+    histogram.  dens (nx*nk doubles) and marg (nx doubles) may be given as
+    host arrays to write into, e.g. views of pinned memory, which the copies
+    from the device reach at full speed; new arrays otherwise."""
+    dens = np.empty(nx * nk, np.float64) if dens is None else dens.reshape(-1)
+    marg = np.empty(nx, np.float64) if marg is None else marg.reshape(-1)
+    if (dens.dtype != np.float64 or marg.dtype != np.float64 or dens.size != nx * nk
+            or marg.size != nx or not dens.flags.c_contiguous or not marg.flags.c_contiguous):
+        raise ValueError("density and marginal buffers must be contiguous float64 of nx*nk and nx")
     T = ctypes.c_double()
     live = ctypes.c_longlong()
     _check(ctx, load().wbrw_density(ctx, dens.ctypes.data, marg.ctypes.data,

@@ -217,6 +217,16 @@ def test_observables_match_oracle():
     dens, marg, T, live = sim.density()
     odens, omarg, oT = o.observables(o.grid())
     assert live == o.n and np.array_equal(dens, odens) and T == oT
+    # the same read into caller-given (pinned) host buffers
+    import torch
+    from paper_1709_02121_gb300 import wbrw
+    dh = torch.empty(wl["nx"] * wl["nk"], dtype=torch.float64).pin_memory()
+    mh = torch.empty(wl["nx"], dtype=torch.float64).pin_memory()
+    d2, m2, T2, live2 = wbrw.wbrw_density(sim.ctx, wl["nx"], wl["nk"], dh.numpy(), mh.numpy())
+    assert np.array_equal(d2, odens) and np.array_equal(mh.numpy(), omarg)
+    assert T2 == oT and live2 == live
+    with pytest.raises(ValueError):
+        wbrw.wbrw_density(sim.ctx, wl["nx"], wl["nk"], np.empty(3), mh.numpy())
 
 
 def test_particles_leaving_the_grid_are_tallied():
