@@ -754,6 +754,7 @@ __global__ void __launch_bounds__(kBlock) k_bootb_plan(Counters* c, BootInst* bi
                                                        const unsigned long long* pre1,
                                                        int ninst, int nhi,
                                                        unsigned long long* dpre) {
+  static_assert(kMaxInst <= kBlock, "one thread per instance");
   __shared__ unsigned long long red[kBlock / 32 + 1];
   const int i = threadIdx.x;  // ninst <= kBlock
   unsigned long long nr[2] = {0, 0};
