@@ -1154,7 +1154,7 @@ cudaError_t launch_scan_cells(Ctx* c, const int* grid) {
 
 // sp2 in a batch: every instance bootstrapped on its own (Alg. 2 per
 // instance and side), in the same launches.
-cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
+static cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
   const long long nh = c->nh, nb = c->scan_blocks;
   const int ni = c->ninst, nhi = (int)c->nhi;
   const uint32_t key0 = (uint32_t)c->cfg.seed, key1 = (uint32_t)(c->cfg.seed >> 32);
