@@ -744,6 +744,10 @@ def secondaries(args, local, flush, ceiling, peaks):
         # the batch of 256 against the plain per-instance path
         ("batch", lambda: _strip(batch_measure(args, workloads.BATCH_2D_FP32_256, K, W, local,
                                                flush, ceiling, peaks, plain=True))),
+        # the same batch with the signed bootstrap (every instance filtered on its own)
+        ("batch_sp2", lambda: _strip(batch_measure(
+            args, workloads.scaled(workloads.BATCH_2D_FP32_256, strategy="sp2"), K, W, local,
+            flush, ceiling, peaks, plain=True))),
         # the gradient of T(H, w) at the 64 points against the forward run
         ("grad", lambda: grad_measure(args, workloads.GRAD_2D_FP32_64, local, flush, ceiling,
                                       peaks, group=4, points=64)),
