@@ -47,7 +47,9 @@ typedef enum {
   WBRW_ERR_CAPACITY = -2, /* particle, queue, record or nesting capacity   */
   WBRW_ERR_CUDA = -3,     /* a CUDA runtime call failed                    */
   WBRW_ERR_STATE = -4,    /* context already failed, or call out of order  */
-  WBRW_ERR_TIMEOUT = -5,  /* reserved: a bounded device wait gave up       */
+  WBRW_ERR_TIMEOUT = -5,  /* reserved, never returned: no kernel waits on  */
+                          /* another block or launch (every queue segment  */
+                          /* has one producer and one consumer warp)       */
   WBRW_ERR_NUMERIC = -6   /* a non-finite position or wavevector reached   */
                           /* binning (latched by the device, reported by   */
                           /* the next synchronising call)                  */
