@@ -292,6 +292,8 @@ __global__ void __launch_bounds__(kBlock) k_u64_c(unsigned long long* a, long lo
 constexpr int kBootChunk = 1024;  // records per work item of k_boot_bin
 constexpr int kBootBinBlocks = 8; // resident blocks per SM k_boot_bin is built and launched for
 constexpr int kBootBinBatchBlocks = 6;  // the same for its batch form (shares from a table)
+constexpr int kTallyLoads = 4;          // groups of 32 records k_bootb_tally loads ahead
+constexpr int kTallyBlocks = 6;         // resident blocks per SM of k_bootb_tally (bound and grid)
 
 // The share q_i = a_i N^s / W^s of a record of side s (Alg. 2 on S^s), split
 // into its integer part and its Q0.32 residual.  fx (FP32 runs): in fixed
@@ -385,16 +387,17 @@ __global__ void __launch_bounds__(kBlock) k_boot_unit(Counters* c, const int* uc
   }
 }
 
-// Per-key sums of a warp: every lane calls with its key (-1: none) and its
-// value v < 2^32; the first lane of each key's group adds the group's sum to
-// acc[key] (shared memory), one atomic per key and warp.  (The sum is taken
-// in 16-bit halves, so that 32 values cannot overflow it.)
-__device__ __forceinline__ void warp_add(unsigned long long* acc, int key, unsigned v) {
-  const unsigned grp = __match_any_sync(0xFFFFFFFFu, key);
-  if (key < 0) return;
-  const unsigned lo = __reduce_add_sync(grp, v & 0xFFFFu), hi = __reduce_add_sync(grp, v >> 16);
-  const unsigned long long t = ((unsigned long long)hi << 16) + lo;
-  if ((int)(threadIdx.x & 31) == __ffs(grp) - 1 && t) atomicAdd(acc + key, t);
+// The instance of global cell nu (< 2^30) when every instance owns nhi
+// cells: floor(nu / nhi) from one multiply by mag = ceil(2^40 / nhi) (whose
+// estimate exceeds the quotient by at most one, since nu (mag - 2^40 / nhi)
+// < 2^-10 2^40) and one correction, instead of an integer division.
+__device__ __forceinline__ unsigned long long inst_magic(int nhi) {
+  return ((1ull << 40) + (unsigned long long)nhi - 1ull) / (unsigned long long)nhi;
+}
+__device__ __forceinline__ unsigned inst_of_cell(unsigned nu, int nhi, unsigned long long mag) {
+  unsigned q = (unsigned)(((unsigned long long)nu * mag) >> 40);
+  if (q * (unsigned)nhi > nu) --q;
+  return q;
 }
 
 // The offspring records' shares added to the cell tallies.  BATCH: the
@@ -406,6 +409,7 @@ __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBin
     k_boot_bin(Counters* c, const uint32_t* rec_cell, const uint32_t* rec_a, const unsigned* rcnt,
                int nseg, long long rseg, int* keep0, int* keep1, unsigned long long* res0,
                unsigned long long* res1, int fx, BootInst* bi, int ninst, int nhi) {
+  const unsigned long long mag = inst_magic(nhi);
   __shared__ unsigned long long red[kBlock / 32 + 1];
   __shared__ BootShare tab[BATCH ? kMaxInst : 1];
   BootShare sh;
@@ -444,7 +448,7 @@ __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBin
         const uint32_t rc = rcs[i];
         const int side = rc >> 31;
         const uint32_t cell = rc & 0x7FFFFFFFu;
-        if constexpr (BATCH) tab[cell / (unsigned)nhi].of(ras[i], side, kf, res);
+        if constexpr (BATCH) tab[inst_of_cell(cell, nhi, mag)].of(ras[i], side, kf, res);
         else sh.of(ras[i], side, kf, res);
         key = 2u * cell + (unsigned)side;
       }
@@ -598,12 +602,11 @@ __device__ __forceinline__ void flush_tally(unsigned long long* sn, unsigned lon
 // N^s and W^s of every instance: its offspring records (cell | side << 31,
 // a) and its unit-weight counts (a = 2^31 each), summed per block in shared
 // memory and added to the instances' records.
-__global__ void __launch_bounds__(kBlock) k_bootb_tally(const uint32_t* rec_cell,
-                                                        const uint32_t* rec_a,
-                                                        const unsigned* rcnt, int nseg,
-                                                        long long rseg, const int* ucnt,
-                                                        long long nh, int nhi, int ninst,
-                                                        BootInst* bi) {
+__global__ void __launch_bounds__(kBlock, kTallyBlocks)
+    k_bootb_tally(const uint32_t* rec_cell, const uint32_t* rec_a, const unsigned* rcnt, int nseg,
+                  long long rseg, const int* ucnt, long long nh, int nhi, int ninst,
+                  BootInst* bi) {
+  const unsigned long long mag = inst_magic(nhi);
   __shared__ unsigned long long sn[2 * kMaxInst], sw[2 * kMaxInst];
   for (int i = threadIdx.x; i < 2 * ninst; i += kBlock) sn[i] = sw[i] = 0;
   __syncthreads();
@@ -616,26 +619,50 @@ __global__ void __launch_bounds__(kBlock) k_bootb_tally(const uint32_t* rec_cell
     const unsigned b0 = (unsigned)((it - sg * cps) * kBootChunk);
     const unsigned n = min(min(rcnt[sg], (unsigned)rseg), b0 + (unsigned)kBootChunk);
     // a segment holds runs of one instance's records (of both signs, the
-    // pairs interleaved): runs of equal instances in consecutive lanes sum
-    // their counts and weights per side by shuffles, and a run's first lane
-    // adds them to the shared sums
+    // pairs interleaved)
     const uint32_t* rcs = rec_cell + sg * rseg;
     const uint32_t* ras = rec_a + sg * rseg;
-    for (unsigned b = b0; b < n; b += 32) {
-      const unsigned i = b + lane;
-      int inst = -1;
-      unsigned c0 = 0, c1 = 0;
-      unsigned long long w0 = 0, w1 = 0;
-      if (i < n) {
-        const uint32_t rc = __ldcs(rcs + i);
-        const uint32_t a = __ldcs(ras + i);
-        inst = (int)((rc & 0x7FFFFFFFu) / (unsigned)nhi);
-        if (rc >> 31) { c1 = 1; w1 = a; } else { c0 = 1; w0 = a; }
+    // kTallyLoads groups of 32 records are loaded before the first is used,
+    // so that each warp keeps that many loads in flight (the kernel streams
+    // the records once)
+    for (unsigned b = b0; b < n; b += 32u * kTallyLoads) {
+      uint32_t rcv[kTallyLoads], rav[kTallyLoads];
+#pragma unroll
+      for (int j = 0; j < kTallyLoads; ++j) {
+        const unsigned i = b + 32u * j + lane;
+        rcv[j] = i < n ? __ldcs(rcs + i) : ~0u;
+        rav[j] = i < n ? __ldcs(ras + i) : 0u;
       }
-      const int prev = __shfl_up_sync(0xFFFFFFFFu, inst, 1);
-      const bool head = lane == 0 || prev != inst;
-      const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
-      if (heads != 0xFFFFFFFFu) {
+#pragma unroll
+      for (int j = 0; j < kTallyLoads; ++j) {
+        if (b + 32u * j >= n) break;  // warp-uniform: lane 0's record exists below
+        const bool valid = rcv[j] != ~0u;
+        const int side = (int)(rcv[j] >> 31);
+        const int inst = valid ? (int)inst_of_cell(rcv[j] & 0x7FFFFFFFu, nhi, mag) : -1;
+        const unsigned a = rav[j];
+        const int inst0 = __shfl_sync(0xFFFFFFFFu, inst, 0);
+        if (__all_sync(0xFFFFFFFFu, inst == inst0 || inst < 0)) {
+          // the warp's records belong to one instance: counts by ballots,
+          // weight sums in 16-bit halves
+          const bool s0 = valid && side == 0, s1 = valid && side == 1;
+          const unsigned c0 = __popc(__ballot_sync(0xFFFFFFFFu, s0));
+          const unsigned c1 = __popc(__ballot_sync(0xFFFFFFFFu, s1));
+          const unsigned lo0 = __reduce_add_sync(0xFFFFFFFFu, s0 ? a & 0xFFFFu : 0u);
+          const unsigned hi0 = __reduce_add_sync(0xFFFFFFFFu, s0 ? a >> 16 : 0u);
+          const unsigned lo1 = __reduce_add_sync(0xFFFFFFFFu, s1 ? a & 0xFFFFu : 0u);
+          const unsigned hi1 = __reduce_add_sync(0xFFFFFFFFu, s1 ? a >> 16 : 0u);
+          if (lane == 0)
+            flush_tally(sn, sw, inst0, c0, c1, ((unsigned long long)hi0 << 16) + lo0,
+                        ((unsigned long long)hi1 << 16) + lo1);
+          continue;
+        }
+        // mixed instances: runs of equal instances in consecutive lanes, each
+        // run's first lane adding the run's sums
+        unsigned c0 = valid && side == 0, c1 = valid && side == 1;
+        unsigned long long w0 = c0 ? a : 0ull, w1 = c1 ? a : 0ull;
+        const int prev = __shfl_up_sync(0xFFFFFFFFu, inst, 1);
+        const bool head = lane == 0 || prev != inst;
+        const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
         const unsigned later = heads & ~((2u << lane) - 1u);
         const int end = later ? __ffs(later) - 1 : 32;  // the next run's first lane
 #pragma unroll
@@ -651,14 +678,14 @@ __global__ void __launch_bounds__(kBlock) k_bootb_tally(const uint32_t* rec_cell
             w1 += v1;
           }
         }
+        if (head && inst >= 0) flush_tally(sn, sw, inst, c0, c1, w0, w1);
       }
-      if (head && inst >= 0) flush_tally(sn, sw, inst, c0, c1, w0, w1);
     }
   }
   // unit counts: warps over consecutive cells
   for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
     const long long nu = c0 + lane;
-    const int inst = nu < nh ? (int)((unsigned)nu / (unsigned)nhi) : -1;
+    const int inst = nu < nh ? (int)inst_of_cell((unsigned)nu, nhi, mag) : -1;
     for (int sd = 0; sd < 2; ++sd) {
       const unsigned u = nu < nh ? (unsigned)ucnt[sd * nh + nu] : 0u;
       const int key = inst < 0 || u == 0 ? -1 : 2 * inst + sd;
@@ -711,9 +738,10 @@ __global__ void __launch_bounds__(kBlock) k_bootb_unit(const BootInst* bi, const
                                                        long long nh, int nhi, int* keep0,
                                                        int* keep1, unsigned long long* res0,
                                                        unsigned long long* res1) {
+  const unsigned long long mag = inst_magic(nhi);
   for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
        nu += (long long)gridDim.x * kBlock) {
-    const BootInst& b = bi[(unsigned)nu / (unsigned)nhi];
+    const BootInst& b = bi[inst_of_cell((unsigned)nu, nhi, mag)];
     const int u0 = ucnt[nu], u1 = ucnt[nh + nu];
     keep0[nu] = u0 * b.kf_unit[0];
     keep1[nu] = u1 * b.kf_unit[1];
@@ -722,27 +750,52 @@ __global__ void __launch_bounds__(kBlock) k_bootb_unit(const BootInst* bi, const
   }
 }
 
-// Each instance's sums of the kept integer parts, over its cells.
+// Each instance's sums of the kept integer parts, over its cells (a warp's
+// cells belong to one instance but at instance boundaries: the warp keeps
+// the running sums of its current instance, as k_bootb_tally does).
 __global__ void __launch_bounds__(kBlock) k_bootb_keep(BootInst* bi, const int* keep0,
-                                                       const int* keep1, long long nh, int nhi,
-                                                       int ninst) {
-  __shared__ unsigned long long ks[2 * kMaxInst];
-  for (int i = threadIdx.x; i < 2 * ninst; i += kBlock) ks[i] = 0;
-  __syncthreads();
+                                                       const int* keep1, long long nh, int nhi) {
+  const unsigned long long mag = inst_magic(nhi);
   const int lane = threadIdx.x & 31;
   const long long gw = ((long long)blockIdx.x * kBlock + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * kBlock) >> 5;
+  int ci = -1;
+  unsigned long long k0s = 0, k1s = 0;
+  auto flush = [&]() {
+    if (lane == 0 && ci >= 0) {
+      if (k0s) atomicAdd(&bi[ci].keep[0], k0s);
+      if (k1s) atomicAdd(&bi[ci].keep[1], k1s);
+    }
+    k0s = k1s = 0;
+  };
   for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
     const long long nu = c0 + lane;
-    const int inst = nu < nh ? (int)((unsigned)nu / (unsigned)nhi) : -1;
-    for (int sd = 0; sd < 2; ++sd) {
-      const unsigned k = inst >= 0 ? (unsigned)(sd ? keep1 : keep0)[nu] : 0u;
-      warp_add(ks, inst < 0 || k == 0 ? -1 : 2 * inst + sd, k);
+    const int inst = nu < nh ? (int)inst_of_cell((unsigned)nu, nhi, mag) : -1;
+    const unsigned k0 = nu < nh ? (unsigned)keep0[nu] : 0u;
+    const unsigned k1 = nu < nh ? (unsigned)keep1[nu] : 0u;
+    const int inst0 = __shfl_sync(0xFFFFFFFFu, inst, 0);
+    if (__all_sync(0xFFFFFFFFu, inst == inst0 || inst < 0)) {
+      // 32 kept counts of 32-bit cells: the sums taken in 16-bit halves
+      const unsigned long long t0 =
+          ((unsigned long long)__reduce_add_sync(0xFFFFFFFFu, k0 >> 16) << 16) +
+          __reduce_add_sync(0xFFFFFFFFu, k0 & 0xFFFFu);
+      const unsigned long long t1 =
+          ((unsigned long long)__reduce_add_sync(0xFFFFFFFFu, k1 >> 16) << 16) +
+          __reduce_add_sync(0xFFFFFFFFu, k1 & 0xFFFFu);
+      if (t0 | t1) {
+        if (inst0 != ci) {
+          flush();
+          ci = inst0;
+        }
+        k0s += t0;
+        k1s += t1;
+      }
+    } else if (inst >= 0) {  // an instance boundary inside the warp
+      if (k0) atomicAdd(&bi[inst].keep[0], (unsigned long long)k0);
+      if (k1) atomicAdd(&bi[inst].keep[1], (unsigned long long)k1);
     }
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 2 * ninst; i += kBlock)
-    if (ks[i]) atomicAdd(&bi[i >> 1].keep[i & 1], ks[i]);
+  flush();
 }
 
 // Per instance and side: the residual total R (from the inclusive prefix
@@ -871,10 +924,11 @@ __global__ void __launch_bounds__(kBlock) k_bootb_combine(const Counters* c, con
                                                           const int* keep0, const int* keep1,
                                                           int* grid, uint32_t key0,
                                                           uint32_t key1, int epoch_delta) {
+  const unsigned long long mag = inst_magic(nhi);
   const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
   for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
        nu += (long long)gridDim.x * kBlock) {
-    const int inst = (int)((unsigned)nu / (unsigned)nhi);  // nh < 2^30
+    const int inst = (int)inst_of_cell((unsigned)nu, nhi, mag);  // nh < 2^30
     const BootInst& b = bi[inst];
     const double m = __dsub_rn(__dmul_rn((double)keep0[nu], b.amp[0]),
                                __dmul_rn((double)keep1[nu], b.amp[1]));
@@ -897,13 +951,14 @@ __global__ void __launch_bounds__(kBlock) k_wp_round(const Counters* c, long lon
                                                      const long long* wsum, int* grid,
                                                      uint32_t key0, uint32_t key1,
                                                      int epoch_delta) {
+  const unsigned long long mag = inst_magic(nhi);
   const unsigned long long epoch = (c->per_regen_base >> 40) + (unsigned long long)epoch_delta;
   for (long long nu = (long long)blockIdx.x * kBlock + threadIdx.x; nu < nh;
        nu += (long long)gridDim.x * kBlock) {
     const double m = __dmul_rn((double)wsum[nu], 1.0 / 2147483648.0);
     const double am = fabs(m);
     const double fl = floor(am);
-    const int inst = (int)((unsigned)nu / (unsigned)nhi);  // nh < 2^30
+    const int inst = (int)inst_of_cell((unsigned)nu, nhi, mag);  // nh < 2^30
     const uint4 r = philox((uint32_t)(nu - (long long)inst * nhi), (uint32_t)inst, kStepRound,
                            (uint32_t)epoch, key0, key1);
     const double u = u53(r.x, r.y);
@@ -1161,9 +1216,8 @@ static cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
   const int fx = c->cfg.precision == WBRW_FP32;
   cudaError_t e = launch_zero(c, c->boot_inst, (size_t)ni * sizeof(BootInst));
   if (e != cudaSuccess) return e;
-  k_bootb_tally<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->rec_cell, c->rec_a, c->rcnt,
-                                                          c->nseg, c->rseg, c->boot_ucnt, nh,
-                                                          nhi, ni, c->boot_inst);
+  k_bootb_tally<<<grid_cap(c, kTallyBlocks), kBlock, 0, c->stream>>>(
+      c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg, c->boot_ucnt, nh, nhi, ni, c->boot_inst);
   k_bootb_share<<<1, kBlock, 0, c->stream>>>(c->boot_inst, ni, fx);
   k_bootb_unit<<<grid_cap(c, 8), kBlock, 0, c->stream>>>(c->boot_inst, c->boot_ucnt, nh, nhi,
                                                          c->boot_keep[0], c->boot_keep[1],
@@ -1172,7 +1226,7 @@ static cudaError_t launch_boot_batch(Ctx* c, int epoch_delta) {
       c->cnt, c->rec_cell, c->rec_a, c->rcnt, c->nseg, c->rseg, c->boot_keep[0], c->boot_keep[1],
       c->boot_res[0], c->boot_res[1], fx, c->boot_inst, ni, nhi);
   k_bootb_keep<<<grid_cap(c, 4), kBlock, 0, c->stream>>>(c->boot_inst, c->boot_keep[0],
-                                                         c->boot_keep[1], nh, nhi, ni);
+                                                         c->boot_keep[1], nh, nhi);
   c->launches += 5;
   for (int s = 0; s < 2; ++s) {
     k_u64_a<<<(unsigned)nb, kBlock, 0, c->stream>>>(c->boot_res[s], nh, c->scan_bsum);

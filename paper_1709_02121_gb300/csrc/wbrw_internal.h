@@ -17,7 +17,7 @@ constexpr int kTabGuideBits = 8;  // 4D kick rows (FP32): guide table of 2^8 buc
 constexpr int kTabGuide = 1 << kTabGuideBits;
 constexpr int kGuideBits = 16;  // sp2 draws: guide table of 2^16 buckets per side
 constexpr int kGuide = 1 << kGuideBits;
-constexpr int kGuideBitsB = 12;  // sp2 draws of a batch: 2^12 buckets per instance and side
+constexpr int kGuideBitsB = 14;  // sp2 draws of a batch: 2^14 buckets per instance and side
 constexpr int kGuideB = 1 << kGuideBitsB;
 constexpr int kMaxSeg = 8192;    // most queue segments (one per producer warp)
 constexpr int kMaxBlocksPerSm = WBRW_TUNE_BLOCKS_PER_SM_MAX;  // the largest launch bound of the
