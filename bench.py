@@ -160,7 +160,10 @@ class Clocks:
             except ValueError:
                 continue
         if not rows:
-            return None
+            # nvidia-smi takes longer to start than a few periods of a small
+            # workload last
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "the timed region ended before the first sample"}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
                           if v.lower() == "active"})
@@ -738,6 +741,9 @@ def secondaries(args, local, flush, ceiling, peaks):
         # sp2: the 1e8 workload with the signed bootstrap filter
         ("sp2", lambda: plain_like(workloads.scaled(workloads.GAUSS_2D_FP32_1E8, strategy="sp2"),
                                    Simulation, not args.no_graph)),
+        # the FP64 parity path at its own size (2e5 particles, 240 x 128 cells, dt = 0.1)
+        ("fp64", lambda: plain_like(workloads.scaled(workloads.GAUSS_2D_FP64_2E5), Simulation,
+                                    not args.no_graph)),
         # the 4D Helium-like system
         ("he4d", lambda: plain_like(workloads.scaled(workloads.HE_4D_FP32_5E7), Simulation4,
                                     not args.no_graph)),
