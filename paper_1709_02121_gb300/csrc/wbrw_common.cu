@@ -293,7 +293,7 @@ constexpr int kBootChunk = 1024;  // records per work item of k_boot_bin
 constexpr int kBootBinBlocks = 8; // resident blocks per SM k_boot_bin is built and launched for
 constexpr int kBootBinBatchBlocks = 6;  // the same for its batch form (shares from a table)
 constexpr int kTallyLoads = 4;          // groups of 32 records k_bootb_tally loads ahead
-constexpr int kTallyBlocks = 6;         // resident blocks per SM of k_bootb_tally (bound and grid)
+constexpr int kTallyBlocks = 5;         // resident blocks per SM of k_bootb_tally (bound and grid)
 
 // The share q_i = a_i N^s / W^s of a record of side s (Alg. 2 on S^s), split
 // into its integer part and its Q0.32 residual.  fx (FP32 runs): in fixed
@@ -624,7 +624,13 @@ __global__ void __launch_bounds__(kBlock, kTallyBlocks)
     const uint32_t* ras = rec_a + sg * rseg;
     // kTallyLoads groups of 32 records are loaded before the first is used,
     // so that each warp keeps that many loads in flight (the kernel streams
-    // the records once)
+    // the records once).  While consecutive groups belong to one instance
+    // their sums stay in registers (the same in every lane); they go to the
+    // block's shared sums when another instance's group comes and at the end
+    // of the chunk.
+    int cur = -1;
+    unsigned rc0 = 0, rc1 = 0;
+    unsigned long long rw0 = 0, rw1 = 0;
     for (unsigned b = b0; b < n; b += 32u * kTallyLoads) {
       uint32_t rcv[kTallyLoads], rav[kTallyLoads];
 #pragma unroll
@@ -651,9 +657,18 @@ __global__ void __launch_bounds__(kBlock, kTallyBlocks)
           const unsigned hi0 = __reduce_add_sync(0xFFFFFFFFu, s0 ? a >> 16 : 0u);
           const unsigned lo1 = __reduce_add_sync(0xFFFFFFFFu, s1 ? a & 0xFFFFu : 0u);
           const unsigned hi1 = __reduce_add_sync(0xFFFFFFFFu, s1 ? a >> 16 : 0u);
-          if (lane == 0)
-            flush_tally(sn, sw, inst0, c0, c1, ((unsigned long long)hi0 << 16) + lo0,
-                        ((unsigned long long)hi1 << 16) + lo1);
+          const unsigned long long w0 = ((unsigned long long)hi0 << 16) + lo0;
+          const unsigned long long w1 = ((unsigned long long)hi1 << 16) + lo1;
+          if (inst0 != cur) {  // a new run: the last one to the shared sums
+            if (lane == 0 && cur >= 0) flush_tally(sn, sw, cur, rc0, rc1, rw0, rw1);
+            cur = inst0;
+            rc0 = rc1 = 0;
+            rw0 = rw1 = 0;
+          }
+          rc0 += c0;
+          rc1 += c1;
+          rw0 += w0;
+          rw1 += w1;
           continue;
         }
         // mixed instances: runs of equal instances in consecutive lanes, each
@@ -681,6 +696,7 @@ __global__ void __launch_bounds__(kBlock, kTallyBlocks)
         if (head && inst >= 0) flush_tally(sn, sw, inst, c0, c1, w0, w1);
       }
     }
+    if (lane == 0 && cur >= 0) flush_tally(sn, sw, cur, rc0, rc1, rw0, rw1);
   }
   // unit counts: warps over consecutive cells
   for (long long c0 = gw * 32; c0 < nh; c0 += nw * 32) {
