@@ -439,17 +439,35 @@ __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBin
     const unsigned n = min(min(rcnt[sg], (unsigned)rseg), b0 + (unsigned)kBootChunk);
     const uint32_t* rcs = rec_cell + sg * rseg;  // the segment's records
     const uint32_t* ras = rec_a + sg * rseg;
-    for (unsigned b = b0; b < n; b += 32) {
-      const unsigned i = b + lane;
+    // the batch form loads kBinLoads groups of 32 records before it uses the
+    // first (its atomics scatter over arrays larger than L2, and it waits on
+    // the record loads otherwise)
+    constexpr int kBinLoads = BATCH ? 4 : 1;
+    for (unsigned b = b0; b < n; b += 32u * kBinLoads) {
+     uint32_t rcv[kBinLoads], rav[kBinLoads];
+#pragma unroll
+     for (int j = 0; j < kBinLoads; ++j) {
+       const unsigned i = b + 32u * j + lane;
+       if constexpr (BATCH) {
+         rcv[j] = i < n ? __ldcs(rcs + i) : ~0u;
+         rav[j] = i < n ? __ldcs(ras + i) : 0u;
+       } else {
+         rcv[j] = i < n ? rcs[i] : ~0u;
+         rav[j] = i < n ? ras[i] : 0u;
+       }
+     }
+#pragma unroll
+     for (int j = 0; j < kBinLoads; ++j) {
+      if (b + 32u * j >= n) break;  // warp-uniform
       unsigned key = ~0u;  // 2 cell + side, or none
       int kf = 0;
       unsigned long long res = 0;
-      if (i < n) {
-        const uint32_t rc = rcs[i];
+      if (rcv[j] != ~0u) {
+        const uint32_t rc = rcv[j];
         const int side = rc >> 31;
         const uint32_t cell = rc & 0x7FFFFFFFu;
-        if constexpr (BATCH) tab[inst_of_cell(cell, nhi, mag)].of(ras[i], side, kf, res);
-        else sh.of(ras[i], side, kf, res);
+        if constexpr (BATCH) tab[inst_of_cell(cell, nhi, mag)].of(rav[j], side, kf, res);
+        else sh.of(rav[j], side, kf, res);
         key = 2u * cell + (unsigned)side;
       }
       const unsigned prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
@@ -477,6 +495,7 @@ __global__ void __launch_bounds__(kBlock, BATCH ? kBootBinBatchBlocks : kBootBin
           if (side) ks1 += (unsigned long long)kf; else ks0 += (unsigned long long)kf;
         }
       }
+     }
     }
   }
   if constexpr (!BATCH) {
