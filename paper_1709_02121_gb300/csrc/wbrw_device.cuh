@@ -1584,9 +1584,12 @@ __device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc&
       }
       if (b0 + stride < nn) a0_next = tile_nz[(b0 + stride) >> 5];
     }
-    for (IX base = (IX)(g * 32ull); base < nn; base += stride) {
+    // one tile of 32 slots; a full tile (every tile but a warp's last) is
+    // compiled apart with every lane active, which drops the per-lane
+    // activity tests of the whole flight from the common path
+    auto tile = [&](const IX base, auto full) {
       const IX slot = base + lane;
-      const bool act = slot < nn;
+      const bool act = decltype(full)::value || slot < nn;
       PV<P> x, k;
 #pragma unroll
       for (int d = 0; d < P::D; ++d) x.c[d] = k.c[d] = (T)0;
@@ -1602,7 +1605,8 @@ __device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc&
         // in at most 32 nonzero cells, whose starts strictly increase.  Lane i
         // marks bit (start of a0 + i) - base when that start falls inside the
         // tile, and slot base + lane lies in cell a0 + (marks at or below lane).
-        const IX idx = idx_n, st = st_n;
+        [[maybe_unused]] const IX idx = idx_n;  // the tangent plan's tau index
+        const IX st = st_n;
         const uint32_t cw = cw_n;
         if (base + stride < nn) {
           idx_n = a0_next + lane;
@@ -1690,6 +1694,10 @@ __device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc&
       }
       flight_tile<P, SRC, DST>(p, wc, acc, act, slot, x, k, w, pid, act ? p.l0 : p.L, inst, tau,
                                gbits, ecount, eq_seg);
+    };
+    for (IX base = (IX)(g * 32ull); base < nn; base += stride) {
+      if (base + (IX)32 <= nn) tile(base, std::true_type{});
+      else tile(base, std::false_type{});
     }
   }
 
@@ -2244,7 +2252,7 @@ namespace wbrw {
 template <class P>
 KP<P> make_kp(const Ctx* c) {
   using T = typename P::T;
-  KP<P> p;
+  KP<P> p{};  // fields a kernel does not use stay zero (null pointers)
   const wbrw_config& g = c->cfg;
   p.dt = (T)g.dt;
   p.inv_dt = (T)(1.0 / g.dt);
