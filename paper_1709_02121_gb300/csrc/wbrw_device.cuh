@@ -290,7 +290,8 @@ struct KP {
   T xmin, kmin, kmax, dx, dk, inv_dx, inv_dk;
   int nx, nk;
   float inv_nk;     // 1/nk, for cell -> (ix, ik)
-  int nh_big;       // nx nk >= 2^24: use an integer division instead
+  int nh_big;       // cells per instance >= 2^24: an integer division instead
+  unsigned long long inst_mag;  // ceil(2^40 / nhi): the instance of a global cell
   int ninst;        // instances in the batch (1 for a single run)
   int nhi;          // cells per instance (nx nk); instance i owns [i nhi, (i+1) nhi)
   const Inst<T>* inst;                    // per-instance physics
@@ -1628,7 +1629,11 @@ __device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc&
         if (act) {
           int cell = (int)(cwl & 0x7FFFFFFFu);
           if (!P::SINGLE && p.ninst > 1) {
-            inst = (int)((unsigned)cell / (unsigned)p.nhi);
+            // floor(cell / nhi) from one multiply by ceil(2^40 / nhi): the
+            // estimate exceeds the quotient by at most one (cell < 2^30), and
+            // cell inst_mag < 2^64 (at most 256 instances)
+            inst = (int)(((unsigned long long)(unsigned)cell * p.inst_mag) >> 40);
+            if ((unsigned)inst * (unsigned)p.nhi > (unsigned)cell) --inst;
             cell -= inst * p.nhi;
           }
           // tangent particles: ids (epoch << 40) | (instance << 32) | 2^31 | j
@@ -2269,7 +2274,8 @@ KP<P> make_kp(const Ctx* c) {
   p.nx = g.nx;
   p.nk = g.nk;
   p.inv_nk = 1.0f / (float)g.nk;
-  p.nh_big = (long long)g.nx * g.nk >= (1ll << 24);
+  p.nh_big = (long long)c->nhi >= (1ll << 24);
+  p.inst_mag = ((1ull << 40) + (unsigned long long)c->nhi - 1ull) / (unsigned long long)c->nhi;
   p.ninst = c->ninst;
   p.nhi = (int)c->nhi;
   p.inst = (const Inst<T>*)c->inst_tab;
