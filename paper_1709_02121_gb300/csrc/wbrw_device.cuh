@@ -2457,12 +2457,12 @@ template <class P>
 cudaError_t period_any(Ctx* c, const KP<P>& p, int dst, size_t cnt_bytes) {
   if constexpr (fused_period<P>()) {
     if (dst == DST_BIN1) return period<P, DST_BIN1>(c, p, cnt_bytes);
-    // wp's weight sums too (one launch: 3.97 against 4.72 ms per period on the
-    // 1e8-particle workload).  sp2's record sink keeps the launch-per-round
-    // schedule: its record tallies, live through the whole one-launch kernel,
-    // make it spill (7.92 against 7.55 ms per period)
+    // the weighted sinks too: wp's weight sums and sp2's records (on the
+    // 1e8-particle workload 3.97 against 4.72 ms and 7.40 against 7.51 ms
+    // per period)
     if constexpr (P::D == 1 && !P::TG) {
       if (dst == DST_WSUM) return period<P, DST_WSUM>(c, p, cnt_bytes);
+      if (dst == DST_BIN2) return period<P, DST_BIN2>(c, p, cnt_bytes);
     }
   }
   return cudaErrorNotSupported;
@@ -2604,7 +2604,7 @@ struct DriverImpl {
     const int rounds = L > l0 ? L - l0 : 1;
     const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
     if constexpr (fused_period<P>()) {
-      if (c->one_launch && src == SRC_REGEN && L > l0 && (dst == DST_BIN1 || dst == DST_WSUM))
+      if (c->one_launch && src == SRC_REGEN && L > l0 && dst != DST_ARRAY)
         return period_any<P>(c, p, dst, cnt_bytes);
     }
     for (int r = 0; r < rounds; ++r) {
