@@ -349,10 +349,11 @@ wbrw_status wbrw_profile_read_events(wbrw_ctx* ctx, double* total_ms,
  * switches profiling on or off captures its period again. */
 wbrw_status wbrw_graph(wbrw_ctx* ctx, int enable);
 
-/* Schedule of the periods that regenerate from the histogram (every
- * strategy), in contexts whose kernels can run a period as one launch: the
- * 2D FP32 contexts with the static potential and no event log (tangent mode
- * included) and the FP32 4D contexts.  enable = 1 (the default): the first
+/* Schedule of the periods that regenerate from the histogram under sp1 or
+ * wp (sp2 periods always run launch per round), in contexts whose kernels
+ * can run a period as one launch: the 2D FP32 contexts with the static
+ * potential and no event log (tangent mode included) and the FP32 4D
+ * contexts.  enable = 1 (the default): the first
  * wave (or waves) and every event round of a period run in one kernel
  * launch, each warp on its own candidate segments (Alg. 1 over the period,
  * the resampling of Sec. 4.3 after it).  enable = 0: the launch-per-round
@@ -384,8 +385,9 @@ wbrw_status wbrw_one_launch_periods(wbrw_ctx* ctx, int enable);
  *                   tangent mode) and the FP32 4D contexts finish every such
  *                   segment in lockstep passes inside the event kernel
  *                   itself, so there event_passes changes nothing; their
- *                   regenerating periods run in one launch (first waves and
- *                   event rounds together), at most three blocks per SM.
+ *                   regenerating sp1 and wp periods run in one launch (first
+ *                   waves and event rounds together), at most three blocks
+ *                   per SM.
  * wbrw_set_tuning takes effect from the next call and releases captured
  * graphs; out-of-range values (including blocks_per_sm above the context's
  * maximum) give WBRW_ERR_ARG. */

@@ -1001,8 +1001,11 @@ __device__ __forceinline__ void comp_kick(const KP<P>& p, const Inst<typename P:
 
 // An accepted event: what its +/- pair needs (the parent's id, tangent
 // weight and weight, the event's position and time, the two wavevectors).
+// 16-byte aligned for vector shared-memory loads, except with tangents: the
+// per-warp buffers of the event kernels must stay within the 48 KB of static
+// shared memory a block may declare (64 records of 56 bytes rather than 64).
 template <class P>
-struct __align__(16) Birth : TanOf<P> {
+struct alignas(P::TG ? 8 : 16) Birth : TanOf<P> {
   using T = typename P::T;
   unsigned long long pid;
   PV<P> xe, kp, km;
@@ -1936,6 +1939,8 @@ __global__ void __launch_bounds__(kBlock, (max_blocks<P, DST>())) k_event(const 
   Birth<P>* buf = s_birth[CMP ? (threadIdx.x >> 5) : 0];
   unsigned nb = 0;  // births in the buffer (the same in every lane)
   __shared__ __align__(16) FEntry<P> s_stage[kWarps][2][32];
+  static_assert(sizeof(s_birth) + sizeof(s_stage) + sizeof(s_wc) + sizeof(red) <= 48 * 1024,
+                "a block declares at most 48 KB of static shared memory");
   FEntry<P>(*stage)[32] = s_stage[threadIdx.x >> 5];
   auto make_pairs = [&](unsigned lim) {
     while (nb >= lim) {
@@ -2089,6 +2094,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_period(const KP<P> p_) {
   constexpr unsigned kBirths = 64;
   __shared__ Birth<P> s_birth[CMP ? kWarps : 1][CMP ? kBirths : 1];
   __shared__ __align__(16) FEntry<P> s_stage[kWarps][2][32];
+  static_assert(sizeof(s_birth) + sizeof(s_stage) + sizeof(s_wc) + sizeof(red) <= 48 * 1024,
+                "a block declares at most 48 KB of static shared memory");
   unsigned first_pairs = 0;
   unsigned n = own ? min(ecount, p.eseg) : 0u;
   for (int r = 0; r < p.len && n > 0u; ++r) {
@@ -2457,12 +2464,10 @@ template <class P>
 cudaError_t period_any(Ctx* c, const KP<P>& p, int dst, size_t cnt_bytes) {
   if constexpr (fused_period<P>()) {
     if (dst == DST_BIN1) return period<P, DST_BIN1>(c, p, cnt_bytes);
-    // the weighted sinks too: wp's weight sums and sp2's records (on the
-    // 1e8-particle workload 3.97 against 4.72 ms and 7.40 against 7.51 ms
-    // per period)
+    // wp's weight sums too (on the 1e8-particle workload 3.97 against 4.72 ms
+    // per period); sp2's record sink runs launch per round
     if constexpr (P::D == 1 && !P::TG) {
       if (dst == DST_WSUM) return period<P, DST_WSUM>(c, p, cnt_bytes);
-      if (dst == DST_BIN2) return period<P, DST_BIN2>(c, p, cnt_bytes);
     }
   }
   return cudaErrorNotSupported;
@@ -2604,7 +2609,7 @@ struct DriverImpl {
     const int rounds = L > l0 ? L - l0 : 1;
     const size_t cnt_bytes = (size_t)c->nseg * sizeof(unsigned);
     if constexpr (fused_period<P>()) {
-      if (c->one_launch && src == SRC_REGEN && L > l0 && dst != DST_ARRAY)
+      if (c->one_launch && src == SRC_REGEN && L > l0 && (dst == DST_BIN1 || dst == DST_WSUM))
         return period_any<P>(c, p, dst, cnt_bytes);
     }
     for (int r = 0; r < rounds; ++r) {

@@ -124,13 +124,12 @@ def test_lean_tangent_kernels_equal_the_general_ones(torch, batch):
     gen.close()
 
 
-@pytest.mark.parametrize("kind,strategy", [("plain", "sp1"), ("plain", "sp2"), ("plain", "wp"),
-                                           ("batch", "sp1"), ("batch", "sp2"), ("batch", "wp"),
-                                           ("tangent", "sp1")])
+@pytest.mark.parametrize("kind,strategy", [("plain", "sp1"), ("plain", "wp"), ("batch", "sp1"),
+                                           ("batch", "wp"), ("tangent", "sp1")])
 def test_one_launch_periods_equal_the_launch_per_round_schedule(torch, kind, strategy):
-    """The lean kernels run a regenerating period (into the signed histogram,
-    the sp2 bootstrap records or the wp weight sums) as one launch; the
-    launch-per-round schedule of the same kernels gives the same results."""
+    """The lean kernels run a regenerating sp1 or wp period (into the signed
+    histogram or the weight sums) as one launch; the launch-per-round
+    schedule of the same kernels gives the same results."""
     from paper_1709_02121_gb300 import Batch, Simulation
     wl = workloads.scaled(workloads.GAUSS_2D_FP64_2E5, precision="fp32", n_alpha=20_000, nx=100,
                           nk=64, xmin=-25.0, xmax=25.0, kmin=-3.2, kmax=3.2, resample_every=5,
