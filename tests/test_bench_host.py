@@ -164,3 +164,24 @@ def test_one_launch_period_roofline_counts_both_phases(bench):
                                  {}, {})["traffic"] is None
     roof, roof2 = bench.rooflines(wl, c0, c1, (8.0, 2), (0.0, 0), 5e11, {"sm_mhz": 2070.0}, {})
     assert roof["kernel"] == "k_period<fp32>" and roof2 is None
+
+
+def test_clock_record_of_a_region_shorter_than_the_first_sample(bench, tmp_path):
+    """A timed region that ends before nvidia-smi's first sample gives an
+    empty clock record (no median, no reasons), not a missing one; the
+    rooflines then fall back to the maximum clock."""
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    c.fh = open(c.path, "w")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+    c.proc = Done()
+    rec = c.stop()
+    assert rec["samples"] == 0 and rec["sm_mhz"] is None and rec["reasons"] == []
+    r = bench.roofline({"precision": "fp32", "resample_every": 10}, 4.0, 2, 3.2e9, None, rec, {})
+    assert r["peak_derived"] == pytest.approx(152 * 64 * 2070e6 / 42.0 / 1e9)
