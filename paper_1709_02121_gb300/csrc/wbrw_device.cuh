@@ -1591,9 +1591,22 @@ __device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc&
     // one tile of 32 slots; a full tile (every tile but a warp's last) is
     // compiled apart with every lane active, which drops the per-lane
     // activity tests of the whole flight from the common path
+    // one instance: a slot's regeneration draw depends on the slot alone, so
+    // the draw of the warp's next tile is made while this tile is processed
+    constexpr bool PIPE = P::SINGLE && SRC == SRC_REGEN;
+    uint4 r_next = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (PIPE) {
+      const unsigned long long q0 = p.regen_base | (unsigned long long)((IX)(g * 32ull) + lane);
+      r_next = philox_ks(p.ks, (uint32_t)q0, (uint32_t)(q0 >> 32), kStepRegen, 0u);
+    }
     auto tile = [&](const IX base, auto full) {
       const IX slot = base + lane;
       const bool act = decltype(full)::value || slot < nn;
+      [[maybe_unused]] const uint4 r_pipe = r_next;
+      if constexpr (PIPE) {
+        const unsigned long long qn = p.regen_base | (unsigned long long)(slot + stride);
+        r_next = philox_ks(p.ks, (uint32_t)qn, (uint32_t)(qn >> 32), kStepRegen, 0u);
+      }
       PV<P> x, k;
 #pragma unroll
       for (int d = 0; d < P::D; ++d) x.c[d] = k.c[d] = (T)0;
@@ -1643,7 +1656,9 @@ __device__ __forceinline__ void flight_body(const KP<P>& p, WarpCounts& wc, Acc&
           const unsigned long long tag = TR ? 0x80000000ull : 0ull;
           pid = p.regen_base | tag | slot;
           if (!P::SINGLE && p.ninst > 1) pid = p.regen_base | ((unsigned long long)inst << 32) | tag | (slot - islot[inst]);
-          const uint4 r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
+          uint4 r;
+          if constexpr (PIPE) r = r_pipe;
+          else r = philox_ks(p.ks, (uint32_t)pid, (uint32_t)(pid >> 32), kStepRegen, 0u);
           if constexpr (P::D == 1) {
             int ix = (int)((float)cell * p.inv_nk);  // exact after one correction (cell < 2^24)
             if (p.nh_big) ix = cell / p.nk;
