@@ -332,7 +332,7 @@ TRAFFIC_PER_PSTEP = {"fp32": None, "fp64": None, "fp32_4d": 1.19, "fp64_4d": Non
 TRAFFIC_PER_CANDIDATE = {"fp32": None, "fp64": None, "fp32_4d": 49.2, "fp64_4d": None}
 # the one-launch period: its DRAM bytes per candidate interval (the queue
 # entries written by the first wave and read back by the rounds dominate)
-TRAFFIC_PERIOD_PER_CANDIDATE = {"fp32": 44.9, "fp32_4d": 69.3}
+TRAFFIC_PERIOD_PER_CANDIDATE = {"fp32": 44.2, "fp32_4d": 69.3}
 
 
 def _traffic(table, wl):
